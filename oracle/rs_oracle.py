@@ -429,7 +429,8 @@ def pose_gradients(model: RSModel, lig_xyz, lig_q, rotvec, trans, chunk: int = 1
     y = ligand_frame(lig_xyz)
     P, L = rotvec.shape[0], q.size
     out = {"E": np.zeros(P), "dE_dt": np.zeros((P, 3)), "dE_dw": np.zeros((P, 3)),
-           "flags": np.zeros(P, dtype=np.uint8), "S_ref": np.zeros(P), "G_ref": np.zeros(P)}
+           "flags": np.zeros(P, dtype=np.uint8), "S_ref": np.zeros(P), "T_ref": np.zeros(P),
+           "W_ref": np.zeros(P)}
     for s0 in range(0, P, chunk):
         sl = slice(s0, min(P, s0 + chunk))
         R = rotvec_to_rot(rotvec[sl])
@@ -444,7 +445,10 @@ def pose_gradients(model: RSModel, lig_xyz, lig_q, rotvec, trans, chunk: int = 1
         out["dE_dt"][sl] = qg.sum(axis=1)
         tau = np.cross(ry, qg).sum(axis=1)
         out["dE_dw"][sl] = np.einsum("pji,pj->pi", left_jacobian(rotvec[sl]), tau)
-        out["G_ref"][sl] = np.abs(qg).sum(axis=(1, 2))
+        # gradient scales: sum_j |q_j| |grad phi_j| and sum_j |q_j| |R y_j| |grad phi_j|
+        gn = np.linalg.norm(qg, axis=2)
+        out["T_ref"][sl] = gn.sum(axis=1)
+        out["W_ref"][sl] = (gn * np.linalg.norm(ry, axis=2)).sum(axis=1)
         out["flags"][sl], _ = _flags(model, x)
     return out
 
