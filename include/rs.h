@@ -1,0 +1,158 @@
+/*
+ * rs.h -- C ABI of librs: range-separated (RS) tensor electrostatics for
+ * rigid protein-ligand poses on one GB300 (sm_103a).
+ *
+ * Method: arXiv 2510.26611, "Fast tensor-based electrostatic energy
+ * calculations in the perspective of protein-ligand docking problem".
+ *   - rs_build_protein      : Algorithm TEP (Sec. 3.4): sinc sum of Gaussians for
+ *                             1/r (Sec. 2, Eq. sinc), range split (Eq. Split_Tens),
+ *                             shifted long-range Gaussians (Eq. Long-Range_Sum),
+ *                             rank reduction by RHOSVD (TEP step 4, Sec. 4.1).
+ *   - rs_energy_poses       : Algorithm PLIE (Sec. 3.4) over a batch of poses
+ *                             (Lemma 3.3, Eq. EnergySum_ligand) plus the short-range
+ *                             part (Def. 2.1) and the vdW constraint of
+ *                             Eq. Energy_Min (Sec. 3.4).
+ *   - rs_energy_grad_poses  : derivative of Eq. EnergySum_ligand with respect to the
+ *                             rigid-body parameters (Sec. 3.3 forces; Sec. 4.2,
+ *                             force on a rigid cluster, taken exactly).
+ *
+ * Conventions shared by every call
+ *   - Units: Angstrom and elementary charge; energies in e^2/Angstrom.
+ *   - The grid has n nodes per axis, x_i = -b + i*h, h = 2b/(n-1).
+ *   - Ligand coordinates are re-centred on their unweighted geometric centre
+ *     (Sec. 3.4); a pose's translation is the absolute position of that centre.
+ *     Rotations act about the centre.  Quaternions are (w, x, y, z) and are
+ *     normalised by the library; rotation vectors w give R = exp([w]x).
+ *   - The caller owns every input and output buffer; the library owns handles
+ *     (freed with the matching *_free / *_destroy).  Inputs are never modified.
+ *   - mem_flags: RS_MEM_HOST (all array pointers are host memory; the call
+ *     copies in, computes and copies out, and returns when results are in the
+ *     output buffers) or RS_MEM_DEVICE (all array pointers are device memory on
+ *     the context's GPU; the work is enqueued on `stream` and the call returns
+ *     after enqueue).  `stream` is a cudaStream_t passed as void* (NULL = the
+ *     context's own stream).
+ *   - Errors: every call returns an rs_status; on failure nothing is written to
+ *     the outputs that is meant to be used and rs_last_error() gives a message
+ *     (thread-local).  No exception crosses the ABI.  No call aborts.
+ */
+#ifndef RS_H_
+#define RS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int rs_status;
+#define RS_OK               0
+#define RS_ERR_INVALID     -1   /* bad argument: null pointer, size out of range */
+#define RS_ERR_OOM         -2   /* device or host allocation failed / budget exceeded */
+#define RS_ERR_CUDA        -3   /* a CUDA runtime call failed */
+#define RS_ERR_TIMEOUT     -4   /* a bounded wait ran out */
+#define RS_ERR_BUSY        -5   /* resource temporarily unavailable (queue full) */
+#define RS_ERR_NOT_READY   -6   /* result not available yet (serving poll) */
+#define RS_ERR_UNSUPPORTED -7   /* size or option outside what this build handles */
+
+#define RS_MEM_HOST   0
+#define RS_MEM_DEVICE 1
+
+/* Bits of the per-pose flag byte. */
+#define RS_FLAG_CLASH        1  /* some ligand-protein distance < sigma (Eq. Energy_Min) */
+#define RS_FLAG_OUT_OF_GRID  2  /* some ligand atom outside [-b, b]^3: clamped to the edge cell */
+
+typedef struct rs_ctx rs_ctx;
+typedef struct rs_protein rs_protein;
+
+/* Parameters of Algorithm TEP (Sec. 3.4: grid size n, box, vdW distance sigma)
+ * and of the sinc quadrature and reduction the paper leaves open.  Fill with
+ * rs_params_default() and override. */
+typedef struct rs_params {
+    int32_t n;          /* grid nodes per axis, 3 <= n <= 16385                       */
+    double  b;          /* box half-width: the grid spans [-b, b]^3, b > 0            */
+    double  sigma;      /* van der Waals distance (Remark 3.1), > 0                   */
+    int32_t R_l;        /* number of long-range sinc terms, 2 <= R_l <= 64            */
+    double  r_min;      /* smallest distance the quadrature targets (default 0.5)     */
+    double  tau;        /* narrowest long-range Gaussian has t*sigma = tau (default 4)*/
+    double  short_tol;  /* short-range cutoff: r*sum_short a_k e^{-t_k^2 r^2} <= tol  */
+    int32_t tucker_cap; /* 0: keep the unreduced canonical rank N*R_l; >0: RHOSVD to
+                           Tucker ranks <= tucker_cap (<= 32)                          */
+    double  eps_r;      /* RHOSVD keeps singular values > eps_r * s_1 (default 1e-7)  */
+} rs_params;
+
+/* Read-only description of a built protein potential. */
+typedef struct rs_protein_info {
+    int32_t n, N, R_l, K;       /* grid, atoms, long-range terms, total sinc terms  */
+    double  b, h, sigma, r_c;   /* box, spacing, vdW distance, short-range cutoff   */
+    double  h_s, quad_err;      /* quadrature step and measured max rel. error of 1/r */
+    int32_t kind;               /* 0 = canonical (unreduced), 1 = Tucker            */
+    int32_t rank[3];            /* canonical: {R, R, R}; Tucker: r_1, r_2, r_3       */
+    double  sv_gap[3];          /* Tucker: s_r / s_{r+1} per axis (0 if r = n)      */
+    double  sv_tail[3];         /* Tucker: (sum_{i>r} s_i^2)^(1/2) / s_1 per axis    */
+    size_t  device_bytes;       /* device memory held by the handle                 */
+} rs_protein_info;
+
+/* ---------------------------------------------------------------- context */
+void        rs_params_default(rs_params* p);
+/* Creates a context on CUDA device `device` (made current for every call that
+ * uses the context).  *out receives the handle. */
+rs_status   rs_ctx_create(int device, rs_ctx** out);
+void        rs_ctx_destroy(rs_ctx* ctx);
+/* Message of the last failing call on this thread ("" if none). */
+const char* rs_last_error(void);
+/* Library version string. */
+const char* rs_version(void);
+
+/* ------------------------------------------------------- Algorithm TEP */
+/* Builds the RS potential of a protein (Algorithm TEP, Sec. 3.4).
+ *   N     : number of protein atoms, 1 <= N <= 2^22
+ *   xyz   : [N][3] float64 positions (Angstrom); q: [N] float64 charges (e)
+ *   params: see rs_params
+ *   mem_flags/stream: where xyz and q live; the build itself always runs on the
+ *           context's GPU and the call returns when the handle is ready.
+ * On success *out owns the device-resident factors, the sinc table and a
+ * cell list of the atoms; free it with rs_protein_free. */
+rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz, const double* q,
+                           const rs_params* params, int mem_flags, void* stream,
+                           rs_protein** out);
+void      rs_protein_free(rs_protein* p);
+rs_status rs_protein_get_info(const rs_protein* p, rs_protein_info* out);
+/* Copies the sinc table: t[K], a[K] (float64) and is_long[K] (uint8), K from info. */
+rs_status rs_protein_get_table(const rs_protein* p, double* t, double* a, uint8_t* is_long);
+
+/* ------------------------------------------------------ Algorithm PLIE */
+/* Energies of P rigid poses of one ligand (Algorithm PLIE; Lemma 3.3):
+ *   E[p] = sum_j q_j (phi_long + phi_short)(R_p y_j + t_p)
+ * phi_long is the long-range RS tensor interpolated trilinearly (per 1D factor)
+ * at the atom, phi_short the short-range Gaussians of protein atoms closer than
+ * r_c, y_j the ligand atoms about their centre.
+ *   L        : ligand atoms, 1 <= L <= 4096; lig_xyz [L][3], lig_q [L] float64
+ *   P        : poses, 0 <= P <= 2^31-1 (P = 0 is a no-op)
+ *   quat     : [P][4] float64 (w,x,y,z); trans: [P][3] float64
+ *   E_out    : [P] float64;  flags_out: [P] uint8 (RS_FLAG_* bits), may be NULL
+ * Evaluation is FP32 with FP64 per-pose accumulation; vdW distances within
+ * 1e-5 relative of sigma are re-decided in FP64. */
+rs_status rs_energy_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
+                          const double* lig_xyz, const double* lig_q, int64_t P,
+                          const double* quat, const double* trans,
+                          double* E_out, uint8_t* flags_out, int mem_flags, void* stream);
+
+/* Energies and exact gradients for poses given by rotation vectors:
+ *   dE/dt = sum_j q_j grad phi(x_j)
+ *   dE/dw = J_l(w)^T sum_j q_j (R y_j) x grad phi(x_j)   (J_l: SO(3) left Jacobian)
+ * grad phi is the derivative of the piecewise-trilinear interpolant (difference
+ * quotient of adjacent factor rows, Eq. Gradients_Tens) plus the analytic
+ * derivative of the short-range Gaussians; it is 0 along an axis on which the
+ * atom is outside the grid.
+ *   rotvec: [P][3]; trans: [P][3]; dE_dt, dE_dw: [P][3] float64 outputs. */
+rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
+                               const double* lig_xyz, const double* lig_q, int64_t P,
+                               const double* rotvec, const double* trans,
+                               double* E_out, double* dE_dt, double* dE_dw,
+                               uint8_t* flags_out, int mem_flags, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RS_H_ */

@@ -1,0 +1,1215 @@
+// Algorithm TEP (Sec. 3.4): the RS potential of a protein on the device.
+//
+//   cell list  : protein atoms binned into cubes of side >= max(r_c, sigma)
+//   canonical  : U^(l)[i, (m,k)] = exp(-t_k^2 (x_i - x_m^l)^2), axis 3 times
+//                xi_(m,k) = z_m a_k  (Eq. Long-Range_Sum, TEP step 3)
+//   Tucker     : RHOSVD of the same tensor (TEP step 4):
+//                 1. Gram G = Z Z^T of Z = U diag(|xi|^(1/3)) by the Gaussian
+//                    product identity (exact, O(n N R_l) instead of O(n^2 N R_l))
+//                 2. block subspace iteration + Rayleigh-Ritz on G (FP64)
+//                 3. interpolative ("skeleton") rows S of V: V' = V V[S,:]^{-1};
+//                    the Tucker tensor is rewritten exactly in this basis
+//                 4. C' = (V V[S,:]^T)^T U and core beta' = sum_r xi_r C'1 o C'2 o C'3
+// The whole pipeline is FP64; factors are stored FP32 for evaluation.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "rs_common.cuh"
+
+namespace rs {
+namespace {
+
+constexpr int kBlock = 256;
+
+// A set of temporary device buffers freed when the build returns.
+struct Scratch {
+    std::vector<void*> bufs;
+    ~Scratch() {
+        for (void* p : bufs) cudaFree(p);
+    }
+    template <class T>
+    rs_status get(T** p, size_t count) {
+        void* v = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 256;
+        if (cudaMalloc(&v, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("build scratch: cudaMalloc of %zu bytes failed", bytes);
+            return RS_ERR_OOM;
+        }
+        bufs.push_back(v);
+        *p = (T*)v;
+        return RS_OK;
+    }
+};
+
+inline unsigned blocks_for(size_t n, int bs = kBlock) { return (unsigned)((n + bs - 1) / bs); }
+
+// ------------------------------------------------------------------ cell list
+__global__ void k_bbox(int N, const double* __restrict__ xyz, double* __restrict__ out) {
+    __shared__ double sm[6][kBlock];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            double v = xyz[3 * (size_t)i + a];
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    for (int a = 0; a < 3; ++a) {
+        sm[a][threadIdx.x] = lo[a];
+        sm[3 + a][threadIdx.x] = hi[a];
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int a = 0; a < 3; ++a) {
+                sm[a][threadIdx.x] = fmin(sm[a][threadIdx.x], sm[a][threadIdx.x + s]);
+                sm[3 + a][threadIdx.x] = fmax(sm[3 + a][threadIdx.x], sm[3 + a][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void k_cell_count(int N, const double* __restrict__ xyz, double co0, double co1,
+                             double co2, double inv_cell, int nc0, int nc1, int nc2,
+                             int* __restrict__ cell_of, int* __restrict__ count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int c0 = (int)floor((xyz[3 * (size_t)i + 0] - co0) * inv_cell);
+    int c1 = (int)floor((xyz[3 * (size_t)i + 1] - co1) * inv_cell);
+    int c2 = (int)floor((xyz[3 * (size_t)i + 2] - co2) * inv_cell);
+    c0 = min(max(c0, 0), nc0 - 1);
+    c1 = min(max(c1, 0), nc1 - 1);
+    c2 = min(max(c2, 0), nc2 - 1);
+    int id = (c2 * nc1 + c1) * nc0 + c0;
+    cell_of[i] = id;
+    atomicAdd(&count[id], 1);
+}
+
+// Exclusive prefix sum of n ints into out[0..n] (one CTA; the cell grids are small).
+__global__ void k_scan(int n, const int* __restrict__ in, int* __restrict__ out) {
+    __shared__ int sm[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < n ? in[i] : 0;
+        sm[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            int t = threadIdx.x >= off ? sm[threadIdx.x - off] : 0;
+            __syncthreads();
+            sm[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < n) out[i + 1] = carry + sm[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sm[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = 0;
+}
+
+__global__ void k_cell_fill(int N, const int* __restrict__ cell_of, const int* __restrict__ start,
+                            int* __restrict__ cursor, int* __restrict__ perm) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int c = cell_of[i];
+    int slot = start[c] + atomicAdd(&cursor[c], 1);
+    perm[slot] = i;
+}
+
+// Sorts each cell's atoms by original index (so the layout does not depend on
+// atomic ordering) and writes the FP32 and FP64 atom records.
+__global__ void k_cell_sort(int ncell, const int* __restrict__ start, int* __restrict__ perm,
+                            const double* __restrict__ xyz, const double* __restrict__ q,
+                            float4* __restrict__ atoms, D4* __restrict__ atoms64) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int s = start[c], e = start[c + 1];
+    for (int a = s + 1; a < e; ++a) {
+        int v = perm[a];
+        int b = a - 1;
+        while (b >= s && perm[b] > v) {
+            perm[b + 1] = perm[b];
+            --b;
+        }
+        perm[b + 1] = v;
+    }
+    for (int a = s; a < e; ++a) {
+        int i = perm[a];
+        double x = xyz[3 * (size_t)i], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
+        atoms[a] = make_float4((float)x, (float)y, (float)z, (float)q[i]);
+        atoms64[a] = D4{x, y, z, q[i]};
+    }
+}
+
+// ---------------------------------------------------- unreduced canonical factors
+__global__ void k_canon_factors(int n, double b, double h, int N, int Rl,
+                                const double* __restrict__ xyz, const double* __restrict__ q,
+                                const double* __restrict__ tl, const double* __restrict__ al,
+                                int ld, float* __restrict__ F0, float* __restrict__ F1,
+                                float* __restrict__ F2) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (r >= ld) return;
+    size_t o = (size_t)i * ld + r;
+    if (r >= N * Rl) {
+        F0[o] = 0.f;
+        F1[o] = 0.f;
+        F2[o] = 0.f;
+        return;
+    }
+    int m = r / Rl, k = r - m * Rl;
+    double xi = -b + i * h;
+    double t2 = tl[k] * tl[k];
+    double d0 = xi - xyz[3 * (size_t)m], d1 = xi - xyz[3 * (size_t)m + 1], d2 = xi - xyz[3 * (size_t)m + 2];
+    F0[o] = (float)exp(-t2 * d0 * d0);
+    F1[o] = (float)exp(-t2 * d1 * d1);
+    F2[o] = (float)(exp(-t2 * d2 * d2) * q[m] * al[k]);
+}
+
+// ------------------------------------------------------------- Gram by Gaussian products
+// G[i,i'] = sum_(m,k) |xi|^(2/3) e^{-t^2 (x_i-x_m)^2} e^{-t^2 (x_i'-x_m)^2}
+//         = sum_k |a_k|^(2/3) e^{-t^2 (x_i-x_i')^2 / 2} D_k(y_{i+i'}),
+// D_k(y) = sum_m |z_m|^(2/3) e^{-2 t^2 (y - x_m)^2},  y_s = -b + s h/2 (half grid).
+// One thread: SC half-grid points, one (axis, k), MC atoms.  Each Gaussian is
+// walked from its point nearest to x_m outwards with the exact ratio recurrence
+// g_{s+1} = g_s rho_s, rho_{s+1} = rho_s c, so every step is two multiplies.
+constexpr int kSC = 32;
+constexpr int kMC = 128;
+
+__global__ void __launch_bounds__(128) k_gauss_dsum(int n, double b, double h, int N, int Rl,
+                                                     const double* __restrict__ xyz,
+                                                     const double* __restrict__ cz,
+                                                     const double* __restrict__ tl, int nsc,
+                                                     int nmc, double* __restrict__ Dp) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long total = (long long)nsc * Rl * 3 * nmc;
+    if (idx >= total) return;
+    int sc = (int)(idx % nsc);
+    long long rest = idx / nsc;
+    int k = (int)(rest % Rl);
+    rest /= Rl;
+    int ax = (int)(rest % 3);
+    int mc = (int)(rest / 3);
+    const int S = 2 * n - 1;
+    const double delta = 0.5 * h;
+    const int s0 = sc * kSC;
+    const double y0 = -b + s0 * delta;
+    const double t2 = 2.0 * tl[k] * tl[k];
+    const double cq = exp(-2.0 * t2 * delta * delta);
+    double acc[kSC];
+#pragma unroll
+    for (int s = 0; s < kSC; ++s) acc[s] = 0.0;
+    int m_end = min(N, (mc + 1) * kMC);
+    for (int m = mc * kMC; m < m_end; ++m) {
+        double xm = xyz[3 * (size_t)m + ax];
+        double u = (xm - y0) / delta;
+        u = fmin(fmax(u, 0.0), (double)(kSC - 1));
+        int sp = (int)rint(u);
+        double dp = y0 + sp * delta - xm;
+        double arg = t2 * dp * dp;
+        if (arg > 50.0) continue;  // the whole chunk is below e^-50 of the peak
+        double g0 = cz[m] * exp(-arg);
+        double rf = exp(-t2 * (2.0 * dp * delta + delta * delta));
+        double rb = cq / rf;
+        double g = g0, r = rf;
+#pragma unroll
+        for (int s = 0; s < kSC; ++s) {
+            if (s == sp) acc[s] += g0;
+            if (s > sp) {
+                g *= r;
+                r *= cq;
+                acc[s] += g;
+            }
+        }
+        g = g0;
+        r = rb;
+#pragma unroll
+        for (int s = kSC - 1; s >= 0; --s) {
+            if (s < sp) {
+                g *= r;
+                r *= cq;
+                acc[s] += g;
+            }
+        }
+    }
+    double* out = Dp + (((size_t)mc * 3 + ax) * Rl + k) * S;
+#pragma unroll
+    for (int s = 0; s < kSC; ++s)
+        if (s0 + s < S) out[s0 + s] = acc[s];
+}
+
+__global__ void k_sum_chunks(size_t len, int nchunk, const double* __restrict__ in,
+                             double* __restrict__ out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += in[(size_t)c * len + i];
+    out[i] = s;
+}
+
+__global__ void k_exp_table(int n, double h, int Rl, const double* __restrict__ tl,
+                            double* __restrict__ E) {
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = blockIdx.y;
+    if (d >= n) return;
+    double x = d * h;
+    E[(size_t)k * n + d] = exp(-0.5 * tl[k] * tl[k] * x * x);
+}
+
+__global__ void k_gram(int n, int Rl, const double* __restrict__ w2, const double* __restrict__ E,
+                       const double* __restrict__ D, double* __restrict__ G) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    int ax = blockIdx.z;
+    if (j >= n) return;
+    const int S = 2 * n - 1;
+    int d = abs(i - j);
+    const double* Dax = D + (size_t)ax * Rl * S;
+    double s = 0.0;
+    for (int k = 0; k < Rl; ++k) s += w2[k] * E[(size_t)k * n + d] * Dax[(size_t)k * S + i + j];
+    G[((size_t)ax * n + i) * n + j] = s;
+}
+
+__global__ void k_trace(int n, const double* __restrict__ G, double* __restrict__ tr) {
+    __shared__ double sm[kBlock];
+    int ax = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += G[((size_t)ax * n + i) * n + i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tr[ax] = sm[0];
+}
+
+// --------------------------------------------------------- subspace iteration (FP64)
+// Deterministic start block: a hash of (axis, row, column) mapped to [-1, 1).
+__global__ void k_init_block(int n, int p, double* __restrict__ Q) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)3 * n * p;
+    if (idx >= total) return;
+    unsigned long long x = idx * 0x9E3779B97F4A7C15ull + 0x1234567ull;
+    x ^= x >> 30;
+    x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 27;
+    x *= 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    Q[idx] = (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// Y[ax] = G[ax] Q[ax]: G n x n, Q n x p (p <= 48).  CTA: 16 rows x p columns.
+__global__ void __launch_bounds__(256) k_gemm_gq(int n, int p, const double* __restrict__ G,
+                                                  const double* __restrict__ Q,
+                                                  double* __restrict__ Y) {
+    __shared__ double Gs[16][33];
+    __shared__ double Qs[32][48];
+    int ax = blockIdx.z;
+    int i0 = blockIdx.x * 16;
+    int r = threadIdx.x / 16, cg = threadIdx.x % 16;
+    const double* Ga = G + (size_t)ax * n * n;
+    const double* Qa = Q + (size_t)ax * n * p;
+    double acc[3] = {0, 0, 0};
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+            int rr = e / 32, kk = e % 32;
+            int gi = i0 + rr, gk = k0 + kk;
+            Gs[rr][kk] = (gi < n && gk < n) ? Ga[(size_t)gi * n + gk] : 0.0;
+        }
+        for (int e = threadIdx.x; e < 32 * p; e += 256) {
+            int kk = e / p, c = e % p;
+            int gk = k0 + kk;
+            Qs[kk][c] = gk < n ? Qa[(size_t)gk * p + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 32; ++kk) {
+            double g = Gs[r][kk];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                int c = cg + 16 * u;
+                if (c < p) acc[u] += g * Qs[kk][c];
+            }
+        }
+        __syncthreads();
+    }
+    int gi = i0 + r;
+    if (gi < n)
+        for (int u = 0; u < 3; ++u) {
+            int c = cg + 16 * u;
+            if (c < p) Y[((size_t)ax * n + gi) * p + c] = acc[u];
+        }
+}
+
+// S[ax] = A[ax]^T B[ax] (p x p), A and B n x p.  CTA per (row a, axis).
+__global__ void __launch_bounds__(256) k_atb(int n, int p, const double* __restrict__ A,
+                                              const double* __restrict__ B,
+                                              double* __restrict__ S) {
+    __shared__ double sm[4][64];
+    int a = blockIdx.x, ax = blockIdx.y;
+    int c = threadIdx.x % 64, part = threadIdx.x / 64;
+    const double* Aa = A + (size_t)ax * n * p;
+    const double* Ba = B + (size_t)ax * n * p;
+    double s = 0.0;
+    if (c < p)
+        for (int i = part; i < n; i += 4) s += Aa[(size_t)i * p + a] * Ba[(size_t)i * p + c];
+    sm[part][c] = s;
+    __syncthreads();
+    if (part == 0 && c < p)
+        S[((size_t)ax * p + a) * p + c] = ((sm[0][c] + sm[1][c]) + sm[2][c]) + sm[3][c];
+}
+
+// Cholesky S + shift*I = R^T R (R upper) and Rinv = R^{-1}; one CTA per axis.
+__global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restrict__ S,
+                                                    double rel_shift,
+                                                    double* __restrict__ Rinv,
+                                                    int* __restrict__ fail) {
+    __shared__ double A[48][49];
+    __shared__ double Ri[48][49];
+    __shared__ double shift;
+    int ax = blockIdx.x;
+    const double* Sa = S + (size_t)ax * p * p;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) A[e / p][e % p] = Sa[e];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0;
+        for (int i = 0; i < p; ++i) tr += A[i][i];
+        shift = rel_shift * tr;
+    }
+    __syncthreads();
+    if (threadIdx.x < p) A[threadIdx.x][threadIdx.x] += shift;
+    __syncthreads();
+    // right-looking Cholesky on the upper triangle: A = R^T R
+    for (int k = 0; k < p; ++k) {
+        if (threadIdx.x == 0) {
+            double d = A[k][k];
+            if (!(d > 0.0)) {
+                fail[ax] = 1;
+                d = 1e-300;
+            }
+            A[k][k] = sqrt(d);
+        }
+        __syncthreads();
+        double dk = A[k][k];
+        for (int j = k + 1 + threadIdx.x; j < p; j += blockDim.x) A[k][j] /= dk;
+        __syncthreads();
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+            int i = e / p, j = e % p;
+            if (i > k && j >= i) A[i][j] -= A[k][i] * A[k][j];
+        }
+        __syncthreads();
+    }
+    // inverse of upper-triangular R, column by column (back substitution)
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) Ri[e / p][e % p] = 0.0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        Ri[j][j] = 1.0 / A[j][j];
+        for (int i = j - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int k = i + 1; k <= j; ++k) s += A[i][k] * Ri[k][j];
+            Ri[i][j] = -s / A[i][i];
+        }
+    }
+    __syncthreads();
+    double* Ra = Rinv + (size_t)ax * p * p;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) Ra[e] = Ri[e / p][e % p];
+}
+
+// Q = Y Rinv (Rinv upper triangular), n x p.
+__global__ void k_apply_rinv(int n, int p, const double* __restrict__ Y,
+                             const double* __restrict__ Rinv, double* __restrict__ Q) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int ax = blockIdx.y;
+    if (idx >= (size_t)n * p) return;
+    int i = (int)(idx / p), c = (int)(idx % p);
+    const double* Ya = Y + ((size_t)ax * n + i) * p;
+    const double* Ra = Rinv + (size_t)ax * p * p;
+    double s = 0.0;
+    for (int k = 0; k <= c; ++k) s += Ya[k] * Ra[(size_t)k * p + c];
+    Q[((size_t)ax * n + i) * p + c] = s;
+}
+
+// Symmetric eigen-decomposition of H (p x p, p even, <= 48) by parallel cyclic
+// Jacobi with round-robin pairing; eigenvalues sorted in descending order.
+__global__ void __launch_bounds__(256) k_jacobi(int p, const double* __restrict__ H,
+                                                 double* __restrict__ lam,
+                                                 double* __restrict__ W) {
+    __shared__ double A[48][49];
+    __shared__ double V[48][49];
+    __shared__ double cs[24], sn[24];
+    __shared__ int pi[24], pj[24];
+    __shared__ int order[48];
+    __shared__ double off_sh;
+    int ax = blockIdx.x;
+    const double* Ha = H + (size_t)ax * p * p;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, j = e % p;
+        A[i][j] = 0.5 * (Ha[i * p + j] + Ha[j * p + i]);
+        V[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int half = p / 2;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (threadIdx.x == 0) {
+            double off = 0.0, tot = 0.0;
+            for (int i = 0; i < p; ++i)
+                for (int j = 0; j < p; ++j) {
+                    double v = A[i][j] * A[i][j];
+                    tot += v;
+                    if (i != j) off += v;
+                }
+            off_sh = (off <= 1e-32 * tot) ? -1.0 : off;
+        }
+        __syncthreads();
+        if (off_sh < 0.0) break;
+        for (int round = 0; round < p - 1; ++round) {
+            if (threadIdx.x < half) {
+                // round-robin: position 0 fixed, others rotate
+                int t = threadIdx.x;
+                int a = (t == 0) ? 0 : ((t - 1 + round) % (p - 1)) + 1;
+                int bpos = p - 1 - t;
+                int b = ((bpos - 1 + round) % (p - 1)) + 1;
+                int i = min(a, b), j = max(a, b);
+                double aij = A[i][j];
+                double c = 1.0, s = 0.0;
+                if (aij != 0.0) {
+                    double tau = (A[j][j] - A[i][i]) / (2.0 * aij);
+                    double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    c = 1.0 / sqrt(1.0 + tt * tt);
+                    s = tt * c;
+                }
+                cs[t] = c;
+                sn[t] = s;
+                pi[t] = i;
+                pj[t] = j;
+            }
+            __syncthreads();
+            // rows: A <- G^T A
+            for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
+                int t = e / p, k = e % p;
+                int i = pi[t], j = pj[t];
+                double c = cs[t], s = sn[t];
+                double ai = A[i][k], aj = A[j][k];
+                A[i][k] = c * ai - s * aj;
+                A[j][k] = s * ai + c * aj;
+            }
+            __syncthreads();
+            // columns: A <- A G, V <- V G
+            for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
+                int t = e / p, k = e % p;
+                int i = pi[t], j = pj[t];
+                double c = cs[t], s = sn[t];
+                double ai = A[k][i], aj = A[k][j];
+                A[k][i] = c * ai - s * aj;
+                A[k][j] = s * ai + c * aj;
+                double vi = V[k][i], vj = V[k][j];
+                V[k][i] = c * vi - s * vj;
+                V[k][j] = s * vi + c * vj;
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < p; ++i) order[i] = i;
+        for (int i = 1; i < p; ++i) {  // stable insertion sort, descending
+            int v = order[i];
+            int j = i - 1;
+            while (j >= 0 && A[order[j]][order[j]] < A[v][v]) {
+                order[j + 1] = order[j];
+                --j;
+            }
+            order[j + 1] = v;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < p; e += blockDim.x) lam[(size_t)ax * p + e] = A[order[e]][order[e]];
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        int i = e / p, c = e % p;
+        W[((size_t)ax * p + i) * p + c] = V[i][order[c]];
+    }
+}
+
+// V[ax][:, 0:RP] = Q[ax] W[ax][:, 0:r_ax] (zero columns r_ax..RP-1); n x RP.
+__global__ void k_ritz_vectors(int n, int p, int RP, const int* __restrict__ r_ax,
+                               const double* __restrict__ Q, const double* __restrict__ W,
+                               double* __restrict__ V) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int ax = blockIdx.y;
+    if (idx >= (size_t)n * RP) return;
+    int i = (int)(idx / RP), c = (int)(idx % RP);
+    double s = 0.0;
+    if (c < r_ax[ax]) {
+        const double* Qa = Q + ((size_t)ax * n + i) * p;
+        const double* Wa = W + (size_t)ax * p * p;
+        for (int k = 0; k < p; ++k) s += Qa[k] * Wa[(size_t)k * p + c];
+    }
+    V[((size_t)ax * n + i) * RP + c] = s;
+}
+
+// ------------------------------------------------------------------ skeleton basis
+// Pivoted Gram-Schmidt on the rows of V (n x r) picks r rows S (largest residual
+// norm first; ties to the lower index); A = V[S,:] sorted by row index; then
+// Vs = V A^{-1} (cardinal basis: Vs[S_a, b] = delta_ab) and Wp = V A^T.
+__global__ void __launch_bounds__(512) k_skeleton(int n, int RP, const int* __restrict__ r_ax,
+                                                   const double* __restrict__ V,
+                                                   double* __restrict__ M,
+                                                   int* __restrict__ Sidx,
+                                                   double* __restrict__ Ainv,
+                                                   int* __restrict__ fail) {
+    __shared__ double red_v[512];
+    __shared__ int red_i[512];
+    __shared__ double piv[RS_MAX_TUCKER];
+    __shared__ int sel[RS_MAX_TUCKER];
+    __shared__ double A[RS_MAX_TUCKER][2 * RS_MAX_TUCKER + 1];
+    int ax = blockIdx.x;
+    int r = r_ax[ax];
+    const double* Va = V + (size_t)ax * n * RP;
+    double* Ma = M + (size_t)ax * n * RP;
+    for (size_t e = threadIdx.x; e < (size_t)n * RP; e += blockDim.x) Ma[e] = Va[e];
+    __syncthreads();
+    for (int step = 0; step < r; ++step) {
+        double best = -1.0;
+        int bi = n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double s = 0.0;
+            for (int c = 0; c < r; ++c) s += Ma[(size_t)i * RP + c] * Ma[(size_t)i * RP + c];
+            if (s > best || (s == best && i < bi)) {
+                best = s;
+                bi = i;
+            }
+        }
+        red_v[threadIdx.x] = best;
+        red_i[threadIdx.x] = bi;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                double v2 = red_v[threadIdx.x + o];
+                int i2 = red_i[threadIdx.x + o];
+                if (v2 > red_v[threadIdx.x] || (v2 == red_v[threadIdx.x] && i2 < red_i[threadIdx.x])) {
+                    red_v[threadIdx.x] = v2;
+                    red_i[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        int pi = red_i[0];
+        double nrm = sqrt(red_v[0]);
+        if (threadIdx.x == 0) {
+            sel[step] = pi;
+            if (!(nrm > 0.0)) fail[ax] = 2;
+        }
+        if (threadIdx.x < r) piv[threadIdx.x] = nrm > 0.0 ? Ma[(size_t)pi * RP + threadIdx.x] / nrm : 0.0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double d = 0.0;
+            for (int c = 0; c < r; ++c) d += Ma[(size_t)i * RP + c] * piv[c];
+            for (int c = 0; c < r; ++c) Ma[(size_t)i * RP + c] -= d * piv[c];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {  // sort selected rows ascending
+        for (int i = 1; i < r; ++i) {
+            int v = sel[i];
+            int j = i - 1;
+            while (j >= 0 && sel[j] > v) {
+                sel[j + 1] = sel[j];
+                --j;
+            }
+            sel[j + 1] = v;
+        }
+    }
+    __syncthreads();
+    // [A | I] -> [I | A^{-1}] by Gauss-Jordan with partial pivoting
+    for (int e = threadIdx.x; e < r * 2 * r; e += blockDim.x) {
+        int i = e / (2 * r), j = e % (2 * r);
+        A[i][j] = (j < r) ? Va[(size_t)sel[i] * RP + j] : ((j - r) == i ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        if (threadIdx.x == 0) {
+            int best = k;
+            for (int i = k + 1; i < r; ++i)
+                if (fabs(A[i][k]) > fabs(A[best][k])) best = i;
+            if (best != k)
+                for (int j = 0; j < 2 * r; ++j) {
+                    double t = A[k][j];
+                    A[k][j] = A[best][j];
+                    A[best][j] = t;
+                }
+            if (!(fabs(A[k][k]) > 0.0)) fail[ax] = 3;
+        }
+        __syncthreads();
+        double d = A[k][k];
+        __syncthreads();
+        for (int j = threadIdx.x; j < 2 * r; j += blockDim.x) A[k][j] /= d;
+        __syncthreads();
+        for (int e = threadIdx.x; e < r * 2 * r; e += blockDim.x) {
+            int i = e / (2 * r), j = e % (2 * r);
+            if (i != k) {
+                double f = A[i][k];
+                if (j != k) A[i][j] -= f * A[k][j];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < r; i += blockDim.x)
+            if (i != k) A[i][k] = 0.0;
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) {
+        int i = e / RP, j = e % RP;
+        Ainv[((size_t)ax * RP + i) * RP + j] = (i < r && j < r) ? A[i][r + j] : 0.0;
+    }
+    for (int i = threadIdx.x; i < RP; i += blockDim.x) Sidx[ax * RS_MAX_TUCKER + i] = i < r ? sel[i] : -1;
+}
+
+// Vs = V Ainv (FP32 out, the evaluation basis) and Wp = V V[S,:]^T (FP64).
+__global__ void k_skeleton_apply(int n, int RP, const int* __restrict__ r_ax,
+                                 const double* __restrict__ V, const double* __restrict__ Ainv,
+                                 const int* __restrict__ Sidx, float* __restrict__ Vs0,
+                                 float* __restrict__ Vs1, float* __restrict__ Vs2,
+                                 double* __restrict__ Wp) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int ax = blockIdx.y;
+    if (idx >= (size_t)n * RP) return;
+    int i = (int)(idx / RP), c = (int)(idx % RP);
+    int r = r_ax[ax];
+    const double* Vr = V + ((size_t)ax * n + i) * RP;
+    double s = 0.0, w = 0.0;
+    if (c < r) {
+        const double* Ai = Ainv + (size_t)ax * RP * RP;
+        for (int k = 0; k < r; ++k) s += Vr[k] * Ai[(size_t)k * RP + c];
+        int srow = Sidx[ax * RS_MAX_TUCKER + c];
+        const double* Vsr = V + ((size_t)ax * n + srow) * RP;
+        for (int k = 0; k < r; ++k) w += Vr[k] * Vsr[k];
+    }
+    float* Vs = ax == 0 ? Vs0 : (ax == 1 ? Vs1 : Vs2);
+    Vs[(size_t)i * RP + c] = (float)s;
+    Wp[((size_t)ax * n + i) * RP + c] = w;
+}
+
+// C'[ax][a][(m,k)] = sum_i Wp[ax][i][a] exp(-t_k^2 (x_i - x_m^ax)^2)   (FP64).
+// CTA: 128 atoms, one (k, axis).  The CTA walks the union of the atoms' support
+// windows; each thread runs its Gaussian by the ratio recurrence from the first
+// row where the exponent is <= 700.
+template <int RP>
+__global__ void __launch_bounds__(128) k_project(int n, double b, double h, int N, int Rl,
+                                                  const double* __restrict__ xyz,
+                                                  const double* __restrict__ tl,
+                                                  const double* __restrict__ Wp,
+                                                  double* __restrict__ Cp) {
+    __shared__ double Ws[32][RP];
+    __shared__ int wlo[128], whi[128];
+    int k = blockIdx.y, ax = blockIdx.z;
+    int m = blockIdx.x * 128 + threadIdx.x;
+    bool valid = m < N;
+    double t2 = tl[k] * tl[k];
+    double xm = valid ? xyz[3 * (size_t)m + ax] : 0.0;
+    int lo = n, hi = -1;
+    bool direct = t2 * h * h > 50.0;  // narrower than the grid: no recurrence
+    if (valid) {
+        if (t2 == 0.0) {
+            lo = 0;
+            hi = n - 1;
+        } else {
+            double hw = sqrt(700.0 / t2);
+            double l = ceil((xm - hw + b) / h), u = floor((xm + hw + b) / h);
+            l = fmax(l, 0.0);
+            u = fmin(u, (double)(n - 1));
+            if (l <= u) {
+                lo = (int)l;
+                hi = (int)u;
+            }
+        }
+    }
+    wlo[threadIdx.x] = lo;
+    whi[threadIdx.x] = hi;
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            wlo[threadIdx.x] = min(wlo[threadIdx.x], wlo[threadIdx.x + o]);
+            whi[threadIdx.x] = max(whi[threadIdx.x], whi[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    int ulo = wlo[0], uhi = whi[0];
+    __syncthreads();
+    double acc[RP];
+#pragma unroll
+    for (int a = 0; a < RP; ++a) acc[a] = 0.0;
+    const double cq = exp(-2.0 * t2 * h * h);
+    double g = 0.0, rho = 0.0;
+    const double* Wa = Wp + (size_t)ax * n * RP;
+    for (int i0 = ulo; i0 <= uhi; i0 += 32) {
+        for (int e = threadIdx.x; e < 32 * RP; e += 128) {
+            int ii = e / RP, c = e % RP;
+            int gi = i0 + ii;
+            Ws[ii][c] = gi <= uhi ? Wa[(size_t)gi * RP + c] : 0.0;
+        }
+        __syncthreads();
+        int iend = min(32, uhi - i0 + 1);
+        for (int ii = 0; ii < iend; ++ii) {
+            int i = i0 + ii;
+            if (i < lo || i > hi) continue;
+            double d = (-b + i * h) - xm;
+            if (i == lo || direct) {
+                g = exp(-t2 * d * d);
+                rho = exp(-t2 * (2.0 * d * h + h * h));
+            } else {
+                g *= rho;
+                rho *= cq;
+            }
+#pragma unroll
+            for (int a = 0; a < RP; ++a) acc[a] += Ws[ii][a] * g;
+        }
+        __syncthreads();
+    }
+    if (valid) {
+        size_t Rp = (size_t)N * Rl;
+        size_t col = (size_t)m * Rl + k;
+#pragma unroll
+        for (int a = 0; a < RP; ++a) Cp[((size_t)ax * RP + a) * Rp + col] = acc[a];
+    }
+}
+
+// Partial cores over column chunks: Bp[chunk][a][b][c] = sum_r xi_r C'1[a,r] C'2[b,r] C'3[c,r].
+// CTA: RP*RP threads, thread = (a, b), CH columns per CTA.
+template <int RP>
+__global__ void __launch_bounds__(1024) k_core(int Rtot, int Rl, int CH,
+                                               const double* __restrict__ q,
+                                               const double* __restrict__ al,
+                                               const double* __restrict__ Cp,
+                                               double* __restrict__ Bp) {
+    __shared__ double C1s[32][RP], C2s[32][RP], C3s[32][RP], xis[32];
+    int chunk = blockIdx.x;
+    int a = threadIdx.x / RP, bb = threadIdx.x % RP;
+    double acc[RP];
+#pragma unroll
+    for (int c = 0; c < RP; ++c) acc[c] = 0.0;
+    int r0 = chunk * CH, r1 = min(Rtot, r0 + CH);
+    for (int t0 = r0; t0 < r1; t0 += 32) {
+        for (int e = threadIdx.x; e < 32 * RP; e += blockDim.x) {
+            int j = e / RP, c = e % RP;
+            int col = t0 + j;
+            bool ok = col < r1;
+            C1s[j][c] = ok ? Cp[((size_t)0 * RP + c) * Rtot + col] : 0.0;
+            C2s[j][c] = ok ? Cp[((size_t)1 * RP + c) * Rtot + col] : 0.0;
+            C3s[j][c] = ok ? Cp[((size_t)2 * RP + c) * Rtot + col] : 0.0;
+        }
+        for (int j = threadIdx.x; j < 32; j += blockDim.x) {
+            int col = t0 + j;
+            xis[j] = col < r1 ? q[col / Rl] * al[col % Rl] : 0.0;
+        }
+        __syncthreads();
+        int jend = min(32, r1 - t0);
+        for (int j = 0; j < jend; ++j) {
+            double u = xis[j] * C1s[j][a] * C2s[j][bb];
+#pragma unroll
+            for (int c = 0; c < RP; ++c) acc[c] += u * C3s[j][c];
+        }
+        __syncthreads();
+    }
+    double* out = Bp + (size_t)chunk * RP * RP * RP + ((size_t)a * RP + bb) * RP;
+#pragma unroll
+    for (int c = 0; c < RP; ++c) out[c] = acc[c];
+}
+
+__global__ void k_to_float(size_t len, const double* __restrict__ in, float* __restrict__ out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] = (float)in[i];
+}
+
+template <int RP>
+rs_status launch_project_core(cudaStream_t st, int n, double b, double h, int N, int Rl,
+                              const double* xyz, const double* q, const double* tl,
+                              const double* al, const double* Wp, double* Cp, double* Bp,
+                              int nchunk, int CH) {
+    dim3 gp((N + 127) / 128, Rl, 3);
+    k_project<RP><<<gp, 128, 0, st>>>(n, b, h, N, Rl, xyz, tl, Wp, Cp);
+    RS_TRY_CUDA(cudaGetLastError());
+    k_core<RP><<<nchunk, RP * RP, 0, st>>>(N * Rl, Rl, CH, q, al, Cp, Bp);
+    RS_TRY_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
+rs_status dispatch_project_core(int RP, cudaStream_t st, int n, double b, double h, int N, int Rl,
+                                const double* xyz, const double* q, const double* tl,
+                                const double* al, const double* Wp, double* Cp, double* Bp,
+                                int nchunk, int CH) {
+    switch (RP) {
+#define RS_CASE(R) \
+    case R: return launch_project_core<R>(st, n, b, h, N, Rl, xyz, q, tl, al, Wp, Cp, Bp, nchunk, CH);
+        RS_CASE(4) RS_CASE(8) RS_CASE(12) RS_CASE(16) RS_CASE(20) RS_CASE(24) RS_CASE(28) RS_CASE(32)
+#undef RS_CASE
+        default:
+            set_error("unsupported padded Tucker rank %d", RP);
+            return RS_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ build steps
+static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz,
+                             const double* d_q, Scratch& S) {
+    const int N = P->N;
+    double* d_bb;
+    RS_TRY(S.get(&d_bb, 6));
+    k_bbox<<<1, kBlock, 0, st>>>(N, d_xyz, d_bb);
+    RS_TRY_CUDA(cudaGetLastError());
+    double bb[6];
+    RS_TRY_CUDA(cudaMemcpyAsync(bb, d_bb, sizeof(bb), cudaMemcpyDeviceToHost, st));
+    RS_TRY_CUDA(cudaStreamSynchronize(st));
+    double cell = std::max(P->table.r_c, P->sigma) * (1.0 + 1e-4) + 1e-4;
+    int nc[3];
+    double co[3];
+    size_t ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        co[a] = bb[a] - cell;
+        nc[a] = (int)std::floor((bb[3 + a] - co[a]) / cell) + 2;
+        ncell *= (size_t)nc[a];
+    }
+    if (ncell > (size_t)1 << 26) {
+        set_error("protein extent needs %zu cells (max 2^26)", ncell);
+        return RS_ERR_UNSUPPORTED;
+    }
+    int *d_cell_of, *d_count, *d_cursor, *d_perm, *d_start;
+    RS_TRY(S.get(&d_cell_of, N));
+    RS_TRY(S.get(&d_count, ncell));
+    RS_TRY(S.get(&d_cursor, ncell));
+    RS_TRY(S.get(&d_perm, N));
+    RS_TRY(device_alloc(P, (void**)&d_start, (ncell + 1) * sizeof(int)));
+    float4* d_atoms;
+    D4* d_atoms64;
+    RS_TRY(device_alloc(P, (void**)&d_atoms, (size_t)N * sizeof(float4)));
+    RS_TRY(device_alloc(P, (void**)&d_atoms64, (size_t)N * sizeof(D4)));
+    RS_TRY_CUDA(cudaMemsetAsync(d_count, 0, ncell * sizeof(int), st));
+    RS_TRY_CUDA(cudaMemsetAsync(d_cursor, 0, ncell * sizeof(int), st));
+    k_cell_count<<<blocks_for(N), kBlock, 0, st>>>(N, d_xyz, co[0], co[1], co[2], 1.0 / cell, nc[0],
+                                                   nc[1], nc[2], d_cell_of, d_count);
+    k_scan<<<1, 1024, 0, st>>>((int)ncell, d_count, d_start);
+    k_cell_fill<<<blocks_for(N), kBlock, 0, st>>>(N, d_cell_of, d_start, d_cursor, d_perm);
+    k_cell_sort<<<blocks_for(ncell), kBlock, 0, st>>>((int)ncell, d_start, d_perm, d_xyz, d_q,
+                                                      d_atoms, d_atoms64);
+    RS_TRY_CUDA(cudaGetLastError());
+    ProteinView& v = P->view;
+    v.atoms = d_atoms;
+    v.atoms64 = d_atoms64;
+    v.cell_start = d_start;
+    v.nc0 = nc[0];
+    v.nc1 = nc[1];
+    v.nc2 = nc[2];
+    v.co0 = (float)co[0];
+    v.co1 = (float)co[1];
+    v.co2 = (float)co[2];
+    v.inv_cell = (float)(1.0 / cell);
+    return RS_OK;
+}
+
+static rs_status build_canonical(rs_protein* P, cudaStream_t st, const double* d_xyz,
+                                 const double* d_q, const double* d_tl, const double* d_al) {
+    const int N = P->N, Rl = P->R_l, n = P->n;
+    size_t R = (size_t)N * Rl;
+    size_t ld = (R + 127) / 128 * 128;
+    if (ld > (size_t)1 << 30 || (double)ld * n * 12.0 > 64e9) {
+        set_error("unreduced canonical factors need %.1f GB; use tucker_cap", ld * n * 12.0 / 1e9);
+        return RS_ERR_UNSUPPORTED;
+    }
+    float* F[3];
+    for (int a = 0; a < 3; ++a) RS_TRY(device_alloc(P, (void**)&F[a], (size_t)n * ld * sizeof(float)));
+    dim3 g(blocks_for(ld), n);
+    k_canon_factors<<<g, kBlock, 0, st>>>(n, P->b, P->h, N, Rl, d_xyz, d_q, d_tl, d_al, (int)ld,
+                                         F[0], F[1], F[2]);
+    RS_TRY_CUDA(cudaGetLastError());
+    ProteinView& v = P->view;
+    v.kind = 0;
+    v.ld = (int)ld;
+    v.R = (int)ld;
+    for (int a = 0; a < 3; ++a) v.F[a] = F[a];
+    v.core = nullptr;
+    P->kind = 0;
+    for (int a = 0; a < 3; ++a) P->rank[a] = (int)R;
+    return RS_OK;
+}
+
+static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xyz,
+                              const double* d_q, const double* d_tl, const double* d_al,
+                              const std::vector<double>& tl_host, const std::vector<double>& al_host,
+                              const std::vector<double>& q_host_abs23, int cap, double eps_r,
+                              Scratch& S) {
+    const int N = P->N, Rl = P->R_l, n = P->n;
+    const double b = P->b, h = P->h;
+    if (n > 4097) {
+        set_error("Tucker reduction supports n <= 4097 in this build (n=%d)", n);
+        return RS_ERR_UNSUPPORTED;
+    }
+    if (cap > RS_MAX_TUCKER) {
+        set_error("tucker_cap %d exceeds %d", cap, RS_MAX_TUCKER);
+        return RS_ERR_INVALID;
+    }
+    const int Sh = 2 * n - 1;
+    // 1. Gram matrices
+    double *d_cz, *d_w2, *d_E, *d_Dp, *d_D, *d_G, *d_tr;
+    RS_TRY(S.get(&d_cz, N));
+    RS_TRY(S.get(&d_w2, Rl));
+    RS_TRY_CUDA(cudaMemcpyAsync(d_cz, q_host_abs23.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+    std::vector<double> w2(Rl);
+    for (int k = 0; k < Rl; ++k) w2[k] = std::pow(std::fabs(al_host[k]), 2.0 / 3.0);
+    RS_TRY_CUDA(cudaMemcpyAsync(d_w2, w2.data(), Rl * sizeof(double), cudaMemcpyHostToDevice, st));
+    int nsc = (Sh + kSC - 1) / kSC;
+    int nmc = (N + kMC - 1) / kMC;
+    RS_TRY(S.get(&d_Dp, (size_t)nmc * 3 * Rl * Sh));
+    RS_TRY(S.get(&d_D, (size_t)3 * Rl * Sh));
+    RS_TRY(S.get(&d_E, (size_t)Rl * n));
+    RS_TRY(S.get(&d_G, (size_t)3 * n * n));
+    RS_TRY(S.get(&d_tr, 3));
+    long long threads = (long long)nsc * Rl * 3 * nmc;
+    k_gauss_dsum<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, b, h, N, Rl, d_xyz, d_cz,
+                                                                     d_tl, nsc, nmc, d_Dp);
+    RS_TRY_CUDA(cudaGetLastError());
+    size_t dlen = (size_t)3 * Rl * Sh;
+    k_sum_chunks<<<blocks_for(dlen), kBlock, 0, st>>>(dlen, nmc, d_Dp, d_D);
+    k_exp_table<<<dim3(blocks_for(n), Rl), kBlock, 0, st>>>(n, h, Rl, d_tl, d_E);
+    k_gram<<<dim3(blocks_for(n), n, 3), kBlock, 0, st>>>(n, Rl, d_w2, d_E, d_D, d_G);
+    k_trace<<<3, kBlock, 0, st>>>(n, d_G, d_tr);
+    RS_TRY_CUDA(cudaGetLastError());
+
+    // 2. block subspace iteration with CholQR2 and Rayleigh-Ritz
+    int p = std::min(n, cap + 12);
+    p = std::min(48, (p + 1) / 2 * 2);
+    if (p > n) p = n - (n % 2);
+    if (p < cap) {
+        set_error("grid too small for tucker_cap %d (n=%d)", cap, n);
+        return RS_ERR_UNSUPPORTED;
+    }
+    double *d_Q, *d_Y, *d_Sm, *d_Ri, *d_lam, *d_W;
+    int* d_fail;
+    RS_TRY(S.get(&d_Q, (size_t)3 * n * p));
+    RS_TRY(S.get(&d_Y, (size_t)3 * n * p));
+    RS_TRY(S.get(&d_Sm, (size_t)3 * p * p));
+    RS_TRY(S.get(&d_Ri, (size_t)3 * p * p));
+    RS_TRY(S.get(&d_lam, (size_t)3 * p));
+    RS_TRY(S.get(&d_W, (size_t)3 * p * p));
+    RS_TRY(S.get(&d_fail, 3));
+    RS_TRY_CUDA(cudaMemsetAsync(d_fail, 0, 3 * sizeof(int), st));
+    k_init_block<<<blocks_for((size_t)3 * n * p), kBlock, 0, st>>>(n, p, d_Q);
+    auto orthonormalize = [&](double* Yin) -> rs_status {
+        // shifted CholQR then plain CholQR: Q = Y R^{-1}
+        k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, Yin, Yin, d_Sm);
+        k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, 1e-13, d_Ri, d_fail);
+        k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, Yin, d_Ri, d_Q);
+        k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Q, d_Sm);
+        k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, 0.0, d_Ri, d_fail);
+        k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, d_Q, d_Ri, d_Y);
+        RS_TRY_CUDA(cudaMemcpyAsync(d_Q, d_Y, (size_t)3 * n * p * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, st));
+        RS_TRY_CUDA(cudaGetLastError());
+        return RS_OK;
+    };
+    RS_TRY(orthonormalize(d_Q));
+    dim3 gq((n + 15) / 16, 1, 3);
+    const int iters = 28;
+    for (int it = 0; it < iters; ++it) {
+        k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y);
+        RS_TRY(orthonormalize(d_Y));
+    }
+    k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y);
+    k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Y, d_Sm);
+    k_jacobi<<<3, 256, 0, st>>>(p, d_Sm, d_lam, d_W);
+    RS_TRY_CUDA(cudaGetLastError());
+    std::vector<double> lam((size_t)3 * p), tr(3);
+    int fail[3];
+    RS_TRY_CUDA(cudaMemcpyAsync(lam.data(), d_lam, lam.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RS_TRY_CUDA(cudaMemcpyAsync(tr.data(), d_tr, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RS_TRY_CUDA(cudaMemcpyAsync(fail, d_fail, sizeof(fail), cudaMemcpyDeviceToHost, st));
+    RS_TRY_CUDA(cudaStreamSynchronize(st));
+    if (fail[0] || fail[1] || fail[2]) {
+        set_error("orthonormalisation failed in the subspace iteration");
+        return RS_ERR_CUDA;
+    }
+    int r_ax[3];
+    int rmax = 0;
+    for (int a = 0; a < 3; ++a) {
+        const double* la = lam.data() + (size_t)a * p;
+        double s1 = std::sqrt(std::max(la[0], 0.0));
+        int r = 0;
+        for (int i = 0; i < p; ++i)
+            if (std::sqrt(std::max(la[i], 0.0)) > eps_r * s1) ++r;
+        r = std::min(r, cap);
+        r = std::max(r, 1);
+        r_ax[a] = r;
+        rmax = std::max(rmax, r);
+        double head = 0.0;
+        for (int i = 0; i < r; ++i) head += la[i];
+        P->sv_tail[a] = std::sqrt(std::max(tr[a] - head, 0.0) / std::max(la[0], 1e-300));
+        P->sv_gap[a] = (r < p && la[r] > 0) ? std::sqrt(la[r - 1] / la[r]) : 0.0;
+        P->rank[a] = r;
+    }
+    const int RP = (rmax + 3) / 4 * 4;
+    int* d_rax;
+    double *d_V, *d_M, *d_Ainv, *d_Wp;
+    int* d_S;
+    RS_TRY(S.get(&d_rax, 3));
+    RS_TRY_CUDA(cudaMemcpyAsync(d_rax, r_ax, sizeof(r_ax), cudaMemcpyHostToDevice, st));
+    RS_TRY(S.get(&d_V, (size_t)3 * n * RP));
+    RS_TRY(S.get(&d_M, (size_t)3 * n * RP));
+    RS_TRY(S.get(&d_Ainv, (size_t)3 * RP * RP));
+    RS_TRY(S.get(&d_Wp, (size_t)3 * n * RP));
+    RS_TRY(S.get(&d_S, (size_t)3 * RS_MAX_TUCKER));
+    k_ritz_vectors<<<dim3(blocks_for((size_t)n * RP), 3), kBlock, 0, st>>>(n, p, RP, d_rax, d_Q, d_W, d_V);
+    // 3. skeleton basis
+    k_skeleton<<<3, 512, 0, st>>>(n, RP, d_rax, d_V, d_M, d_S, d_Ainv, d_fail);
+    float* Vs[3];
+    for (int a = 0; a < 3; ++a) RS_TRY(device_alloc(P, (void**)&Vs[a], (size_t)n * RP * sizeof(float)));
+    k_skeleton_apply<<<dim3(blocks_for((size_t)n * RP), 3), kBlock, 0, st>>>(
+        n, RP, d_rax, d_V, d_Ainv, d_S, Vs[0], Vs[1], Vs[2], d_Wp);
+    RS_TRY_CUDA(cudaGetLastError());
+    // 4. projections and core
+    const int Rtot = N * Rl;
+    const int CH = 512;
+    const int nchunk = (Rtot + CH - 1) / CH;
+    double *d_Cp, *d_Bp, *d_B;
+    RS_TRY(S.get(&d_Cp, (size_t)3 * RP * Rtot));
+    RS_TRY(S.get(&d_Bp, (size_t)nchunk * RP * RP * RP));
+    RS_TRY(S.get(&d_B, (size_t)RP * RP * RP));
+    RS_TRY(dispatch_project_core(RP, st, n, b, h, N, Rl, d_xyz, d_q, d_tl, d_al, d_Wp, d_Cp, d_Bp,
+                                 nchunk, CH));
+    size_t blen = (size_t)RP * RP * RP;
+    k_sum_chunks<<<blocks_for(blen), kBlock, 0, st>>>(blen, nchunk, d_Bp, d_B);
+    float* core;
+    RS_TRY(device_alloc(P, (void**)&core, blen * sizeof(float)));
+    k_to_float<<<blocks_for(blen), kBlock, 0, st>>>(blen, d_B, core);
+    RS_TRY_CUDA(cudaGetLastError());
+    RS_TRY_CUDA(cudaMemcpyAsync(fail, d_fail, sizeof(fail), cudaMemcpyDeviceToHost, st));
+    RS_TRY_CUDA(cudaStreamSynchronize(st));
+    if (fail[0] || fail[1] || fail[2]) {
+        set_error("skeleton selection failed (rank-deficient factor basis)");
+        return RS_ERR_CUDA;
+    }
+    ProteinView& v = P->view;
+    v.kind = 1;
+    v.ld = RP;
+    v.R = RP;
+    for (int a = 0; a < 3; ++a) v.F[a] = Vs[a];
+    v.core = core;
+    P->kind = 1;
+    return RS_OK;
+}
+
+}  // namespace rs
+
+extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz, const double* q,
+                                      const rs_params* prm, int mem_flags, void* stream,
+                                      rs_protein** out) {
+    using namespace rs;
+    clear_error();
+    RS_CHECK_ARG(ctx && xyz && q && prm && out, "rs_build_protein: NULL argument");
+    *out = nullptr;
+    RS_CHECK_ARG(N >= 1 && N <= (1 << 22), "rs_build_protein: N=%d out of range [1, 2^22]", N);
+    RS_CHECK_ARG(prm->n >= 3 && prm->n <= 16385, "rs_build_protein: n=%d out of range [3, 16385]", prm->n);
+    RS_CHECK_ARG(prm->b > 0 && prm->sigma > 0, "rs_build_protein: b and sigma must be > 0");
+    RS_CHECK_ARG(prm->tucker_cap >= 0, "rs_build_protein: tucker_cap must be >= 0");
+    RS_CHECK_ARG(mem_flags == RS_MEM_HOST || mem_flags == RS_MEM_DEVICE,
+                 "rs_build_protein: bad mem_flags %d", mem_flags);
+    RS_TRY_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    if (stream && stream != (void*)ctx->stream) {
+        // the build is synchronous on the context stream; order after the caller's work
+        RS_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        st = ctx->stream;
+    }
+
+    rs_protein* P = new rs_protein();
+    P->device = ctx->device;
+    P->N = N;
+    P->n = prm->n;
+    P->b = prm->b;
+    P->h = 2.0 * prm->b / (prm->n - 1);
+    P->sigma = prm->sigma;
+    P->R_l = prm->R_l;
+    auto fail_out = [&](rs_status s) {
+        rs_protein_free(P);
+        return s;
+    };
+    rs_status s = make_sinc_table(prm->b, prm->sigma, prm->R_l, prm->r_min, prm->tau,
+                                  prm->short_tol, &P->table);
+    if (s != RS_OK) return fail_out(s);
+    P->K = (int)P->table.t.size();
+
+    Scratch S;
+    // inputs on the device (and on the host, for the small host-side parts)
+    std::vector<double> hq(N);
+    double *d_xyz = nullptr, *d_q = nullptr;
+    if ((s = S.get(&d_xyz, (size_t)3 * N)) != RS_OK) return fail_out(s);
+    if ((s = S.get(&d_q, (size_t)N)) != RS_OK) return fail_out(s);
+    cudaMemcpyKind kind = mem_flags == RS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(d_xyz, xyz, (size_t)3 * N * sizeof(double), kind, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_q, q, (size_t)N * sizeof(double), kind, st) != cudaSuccess ||
+        cudaMemcpyAsync(hq.data(), d_q, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("rs_build_protein: input copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail_out(RS_ERR_CUDA);
+    }
+    for (int i = 0; i < N; ++i)
+        if (!std::isfinite(hq[i])) {
+            set_error("rs_build_protein: charge %d is not finite", i);
+            return fail_out(RS_ERR_INVALID);
+        }
+
+    // sinc terms on the device
+    const int Rl = P->R_l;
+    std::vector<double> tl(Rl), al(Rl);
+    for (int k = 0; k < Rl; ++k) {
+        tl[k] = P->table.t[k];
+        al[k] = P->table.a[k];
+    }
+    double *d_tl, *d_al;
+    if ((s = S.get(&d_tl, Rl)) != RS_OK) return fail_out(s);
+    if ((s = S.get(&d_al, Rl)) != RS_OK) return fail_out(s);
+    cudaMemcpyAsync(d_tl, tl.data(), Rl * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_al, al.data(), Rl * sizeof(double), cudaMemcpyHostToDevice, st);
+
+    if ((s = build_cells(P, st, d_xyz, d_q, S)) != RS_OK) return fail_out(s);
+    if (prm->tucker_cap == 0) {
+        s = build_canonical(P, st, d_xyz, d_q, d_tl, d_al);
+    } else {
+        std::vector<double> cz(N);
+        for (int i = 0; i < N; ++i) cz[i] = std::pow(std::fabs(hq[i]), 2.0 / 3.0);
+        s = build_tucker(P, st, d_xyz, d_q, d_tl, d_al, tl, al, cz, prm->tucker_cap,
+                         prm->eps_r > 0 ? prm->eps_r : 0.0, S);
+    }
+    if (s != RS_OK) return fail_out(s);
+
+    // short-range terms and decision bands
+    ProteinView& v = P->view;
+    v.n = P->n;
+    v.b = P->b;
+    v.h = P->h;
+    v.inv_h = 1.0 / P->h;
+    v.Ks = 0;
+    for (int k = 0; k < P->K; ++k)
+        if (!P->table.is_long[k]) {
+            v.ts2[v.Ks] = (float)(P->table.t[k] * P->table.t[k]);
+            v.as[v.Ks] = (float)P->table.a[k];
+            ++v.Ks;
+        }
+    double rc = P->table.r_c;
+    v.rc2 = rc * rc;
+    v.rc2_hi = (float)(rc * rc * (1.0 + 1e-4));
+    v.sig2 = P->sigma * P->sigma;
+    v.sig2_lo = (float)(v.sig2 * (1.0 - 1e-4));
+    v.sig2_hi = (float)(v.sig2 * (1.0 + 1e-4));
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("rs_build_protein: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail_out(RS_ERR_CUDA);
+    }
+    *out = P;
+    return RS_OK;
+}

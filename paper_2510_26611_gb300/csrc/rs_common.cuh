@@ -1,0 +1,206 @@
+// Internal definitions shared by the librs translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/rs.h"
+
+#define RS_MAX_SHORT 24      // short-range sinc terms handled on the device
+#define RS_MAX_TUCKER 32     // largest Tucker rank per axis
+
+namespace rs {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define RS_TRY_CUDA(expr)                                                              \
+    do {                                                                               \
+        cudaError_t e__ = (expr);                                                      \
+        if (e__ != cudaSuccess) {                                                      \
+            ::rs::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e__),   \
+                            __FILE__, __LINE__);                                       \
+            return RS_ERR_CUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
+#define RS_TRY(expr)                           \
+    do {                                       \
+        rs_status s__ = (expr);                \
+        if (s__ != RS_OK) return s__;          \
+    } while (0)
+
+#define RS_CHECK_ARG(cond, ...)                \
+    do {                                       \
+        if (!(cond)) {                         \
+            ::rs::set_error(__VA_ARGS__);      \
+            return RS_ERR_INVALID;             \
+        }                                      \
+    } while (0)
+
+// Host copy of the sinc quadrature (Sec. 2, Eq. sinc) and its range split.
+struct SincTable {
+    std::vector<double> t, a;
+    std::vector<uint8_t> is_long;
+    double h_s = 0, box_len = 0, r_c = 0, quad_err = 0;
+    int R_l = 0;
+};
+rs_status make_sinc_table(double b, double sigma, int R_l, double r_min, double tau,
+                          double short_tol, SincTable* out);
+
+// FP64 atom record (x, y, z, q), 32-byte aligned.
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+
+// Everything a pose kernel needs about one protein, passed by value.
+struct ProteinView {
+    int n;
+    double b, h, inv_h;
+    int kind;            // 0: canonical factors, 1: Tucker (skeleton basis)
+    int ld;              // floats per factor row
+    int R;               // canonical: padded rank (multiple of 128); Tucker: padded rank RP
+    const float* F[3];   // factor rows [n][ld]; canonical axis 3 carries the weights xi
+    const float* core;   // Tucker core [RP][RP][RP]
+    int Ks;              // short-range terms
+    float ts2[RS_MAX_SHORT];
+    float as[RS_MAX_SHORT];
+    double rc2;          // r_c^2
+    float rc2_hi;        // r_c^2 (1 + 1e-4): FP32 pre-filter
+    double sig2;         // sigma^2
+    float sig2_lo, sig2_hi;  // sigma^2 (1 -/+ 1e-4): FP32 decision band
+    const float4* atoms;     // cell-sorted protein atoms (x, y, z, q) FP32
+    const D4* atoms64;       // same, FP64
+    const int* cell_start;   // [ncell + 1]
+    int nc0, nc1, nc2;
+    float co0, co1, co2;     // cell-grid origin
+    float inv_cell;
+};
+
+// A prepared ligand on the device: coordinates about the geometric centre.
+struct LigandView {
+    int L;
+    const float4* y;     // (y_x, y_y, y_z, q) FP32
+    const double* y64;   // [L][3] FP64
+    const double* q64;   // [L]
+};
+
+}  // namespace rs
+
+struct rs_protein {
+    int device = 0;
+    int n = 0, N = 0, R_l = 0, K = 0;
+    double b = 0, h = 0, sigma = 0;
+    rs::SincTable table;
+    int kind = 0;
+    int rank[3] = {0, 0, 0};
+    double sv_gap[3] = {0, 0, 0};
+    double sv_tail[3] = {0, 0, 0};
+    rs::ProteinView view{};
+    std::vector<void*> allocations;   // device buffers owned by the handle
+    size_t device_bytes = 0;
+};
+
+struct rs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    // Scratch owned by the context: prepared ligand and staging for host calls.
+    void* lig_buf = nullptr;
+    size_t lig_bytes = 0;
+    void* io_buf = nullptr;
+    size_t io_bytes = 0;
+};
+
+namespace rs {
+rs_status ensure_buffer(void** buf, size_t* cap, size_t need);
+rs_status device_alloc(rs_protein* p, void** ptr, size_t bytes);
+}  // namespace rs
+
+// ---------------------------------------------------------------- device helpers
+namespace rs {
+namespace dev {
+
+// Error-free sum of two floats (Knuth TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Accumulator of float values carried as an unevaluated pair hi + lo.
+struct FAcc {
+    float hi, lo;
+    __device__ __forceinline__ FAcc() : hi(0.f), lo(0.f) {}
+    __device__ __forceinline__ void add(float x) {
+        float s, e;
+        two_sum(hi, x, s, e);
+        lo += e;
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Rotation matrix of a (not necessarily unit) quaternion (w, x, y, z), FP64.
+__device__ __forceinline__ void quat_to_rot(double w, double x, double y, double z, double* R) {
+    double nrm = sqrt(w * w + x * x + y * y + z * z);
+    double s = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    w *= s; x *= s; y *= s; z *= s;
+    if (nrm == 0.0) w = 1.0;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// R = exp([w]x) by Rodrigues' formula; series coefficients for small angles.
+__device__ __forceinline__ void rotvec_to_rot(double wx, double wy, double wz, double* R) {
+    double th2 = wx * wx + wy * wy + wz * wz;
+    double th = sqrt(th2);
+    double A, B;
+    if (th < 1e-4) {
+        A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+        B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+    } else {
+        A = sin(th) / th;
+        B = (1.0 - cos(th)) / th2;
+    }
+    // K = [w]x ; K^2 = w w^T - th2 I
+    R[0] = 1 + B * (wx * wx - th2); R[1] = -A * wz + B * wx * wy; R[2] = A * wy + B * wx * wz;
+    R[3] = A * wz + B * wx * wy; R[4] = 1 + B * (wy * wy - th2); R[5] = -A * wx + B * wy * wz;
+    R[6] = -A * wy + B * wx * wz; R[7] = A * wx + B * wy * wz; R[8] = 1 + B * (wz * wz - th2);
+}
+
+// SO(3) left Jacobian J_l(w) = I + (1-cos t)/t^2 [w]x + (t - sin t)/t^3 [w]x^2.
+__device__ __forceinline__ void left_jacobian(double wx, double wy, double wz, double* J) {
+    double th2 = wx * wx + wy * wy + wz * wz;
+    double th = sqrt(th2);
+    double B, C;
+    if (th < 1e-4) {
+        B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+        C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+    } else {
+        B = (1.0 - cos(th)) / th2;
+        C = (th - sin(th)) / (th2 * th);
+    }
+    J[0] = 1 + C * (wx * wx - th2); J[1] = -B * wz + C * wx * wy; J[2] = B * wy + C * wx * wz;
+    J[3] = B * wz + C * wx * wy; J[4] = 1 + C * (wy * wy - th2); J[5] = -B * wx + C * wy * wz;
+    J[6] = -B * wy + C * wx * wz; J[7] = B * wx + C * wy * wz; J[8] = 1 + C * (wz * wz - th2);
+}
+
+// Cell index and fraction along one axis: s = s_pose + d (s_pose = (t + b)/h in
+// FP64, d = (R y)/h in FP32); i = clamp(floor(s), 0, n-2), f = clamp(s - i, 0, 1).
+__device__ __forceinline__ void axis_cell(double s_pose, float d, int n, int& i, float& f,
+                                          bool& inside) {
+    double s = s_pose + (double)d;
+    inside = (s >= 0.0) && (s <= (double)(n - 1));
+    double fl = floor(s);
+    fl = fmin(fmax(fl, 0.0), (double)(n - 2));
+    i = (int)fl;
+    double fr = s - fl;
+    fr = fmin(fmax(fr, 0.0), 1.0);
+    f = (float)fr;
+}
+
+}  // namespace dev
+}  // namespace rs

@@ -1,0 +1,691 @@
+// Pose kernels: Algorithm PLIE (Sec. 3.4) over a batch of rigid poses, the
+// short-range part and vdW check through the cell list, and the exact adjoint
+// with respect to (translation, rotation vector).
+//
+// Per ligand atom j of pose p:  x_j = R_p y_j + t_p
+//   phi_long(x) = trilinear interpolation of the long-range tensor, done per
+//                 1D factor (Sec. 2 entry evaluation; Lemma 3.3)
+//   phi_short   = sum over protein atoms closer than r_c (Def. 2.1)
+//   E_p = sum_j q_j (phi_long + phi_short)(x_j)             (Eq. EnergySum_ligand)
+// FP32 evaluation; per-atom sums carried as float pairs; per-pose sums FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "rs_common.cuh"
+#include "rs_eval.cuh"
+
+namespace rs {
+namespace {
+
+using dev::FAcc;
+
+struct PoseSetup {
+    double R[9];
+    double t[3];
+    double s[3];      // (t + b) / h
+    double J[9];      // left Jacobian (gradient kernels)
+    float Rf[9];
+    int valid;
+};
+
+__device__ __forceinline__ void setup_pose(const ProteinView& P, const double* __restrict__ rot,
+                                           const double* __restrict__ trans, long long p,
+                                           bool rotvec, PoseSetup& ps) {
+    if (rotvec) {
+        double wx = rot[3 * p], wy = rot[3 * p + 1], wz = rot[3 * p + 2];
+        dev::rotvec_to_rot(wx, wy, wz, ps.R);
+        dev::left_jacobian(wx, wy, wz, ps.J);
+    } else {
+        dev::quat_to_rot(rot[4 * p], rot[4 * p + 1], rot[4 * p + 2], rot[4 * p + 3], ps.R);
+    }
+    for (int a = 0; a < 9; ++a) ps.Rf[a] = (float)ps.R[a];
+    for (int a = 0; a < 3; ++a) {
+        ps.t[a] = trans[3 * p + a];
+        ps.s[a] = (ps.t[a] + P.b) * P.inv_h;
+    }
+    ps.valid = 1;
+}
+
+// Short-range part and vdW decision for one atom; candidates split over
+// `nl` cooperating lanes starting at `lane`.  Distances are screened in FP32;
+// pairs inside the cutoff, and vdW decisions within 1e-4 relative of sigma^2,
+// are taken in FP64 from x = t + R y evaluated in FP64.
+template <bool GRAD>
+__device__ __forceinline__ void short_vdw(const ProteinView& P, const float xf[3],
+                                          const PoseSetup& ps, const double* __restrict__ y64,
+                                          int lane, int nl, double& phi, double g[3],
+                                          int& clash) {
+    float u0 = (xf[0] - P.co0) * P.inv_cell, u1 = (xf[1] - P.co1) * P.inv_cell,
+          u2 = (xf[2] - P.co2) * P.inv_cell;
+    u0 = fminf(fmaxf(u0, -4.f), (float)P.nc0 + 4.f);
+    u1 = fminf(fmaxf(u1, -4.f), (float)P.nc1 + 4.f);
+    u2 = fminf(fmaxf(u2, -4.f), (float)P.nc2 + 4.f);
+    int c0 = (int)floorf(u0), c1 = (int)floorf(u1), c2 = (int)floorf(u2);
+    bool have64 = false;
+    double x64[3];
+    for (int dz = -1; dz <= 1; ++dz) {
+        int cz = c2 + dz;
+        if (cz < 0 || cz >= P.nc2) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int cy = c1 + dy;
+            if (cy < 0 || cy >= P.nc1) continue;
+            int x_lo = max(c0 - 1, 0), x_hi = min(c0 + 1, P.nc0 - 1);
+            if (x_lo > x_hi) continue;
+            int base = (cz * P.nc1 + cy) * P.nc0;
+            int s = P.cell_start[base + x_lo], e = P.cell_start[base + x_hi + 1];
+            for (int k = s + lane; k < e; k += nl) {
+                float4 a = P.atoms[k];
+                float e0 = xf[0] - a.x, e1 = xf[1] - a.y, e2 = xf[2] - a.z;
+                float d2 = e0 * e0 + e1 * e1 + e2 * e2;
+                bool near_sig = d2 < P.sig2_hi;
+                bool near_rc = d2 < P.rc2_hi;
+                if (!(near_sig || near_rc)) continue;
+                if (!have64) {
+                    for (int r = 0; r < 3; ++r)
+                        x64[r] = ps.t[r] + (ps.R[3 * r] * y64[0] + ps.R[3 * r + 1] * y64[1] +
+                                            ps.R[3 * r + 2] * y64[2]);
+                    have64 = true;
+                }
+                D4 a64 = P.atoms64[k];
+                double f0 = x64[0] - a64.x, f1 = x64[1] - a64.y, f2 = x64[2] - a64.z;
+                double d2d = f0 * f0 + f1 * f1 + f2 * f2;
+                if (near_sig && (d2 < P.sig2_lo || d2d < P.sig2)) clash = 1;
+                if (near_rc && d2d < P.rc2) {
+                    float d2f = (float)d2d;
+                    float sv = 0.f, sd = 0.f;
+                    for (int q = 0; q < P.Ks; ++q) {
+                        float ev = P.as[q] * expf(-P.ts2[q] * d2f);
+                        sv += ev;
+                        if constexpr (GRAD) sd += P.ts2[q] * ev;
+                    }
+                    phi += a64.w * (double)sv;
+                    if constexpr (GRAD) {
+                        double fgr = -2.0 * a64.w * (double)sd;
+                        g[0] += fgr * f0;
+                        g[1] += fgr * f1;
+                        g[2] += fgr * f2;
+                    }
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reduction of per-atom contributions to per-pose outputs (one warp per pose).
+template <int NC>
+__device__ void reduce_poses(const ProteinView& P, int PB, int L, long long p0, long long Ptot,
+                             const PoseSetup* ps, const double* contrib, const int* pflag,
+                             double* __restrict__ E, uint8_t* __restrict__ flags,
+                             double* __restrict__ gt, double* __restrict__ gw) {
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+    for (int pl = warp; pl < PB; pl += nw) {
+        long long p = p0 + pl;
+        if (p >= Ptot) break;
+        double s[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s[c] = 0.0;
+        for (int j = lane; j < L; j += 32) {
+            const double* cj = contrib + ((size_t)pl * L + j) * NC;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) s[c] += cj[c];
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s[c] = warp_sum(s[c]);
+        if (lane == 0) {
+            E[p] = s[0];
+            if (flags) flags[p] = (uint8_t)pflag[pl];
+            if (NC == 7) {
+                const PoseSetup& q = ps[pl];
+                for (int a = 0; a < 3; ++a) gt[3 * p + a] = s[1 + a];
+                // dE/dw = J_l^T tau
+                for (int a = 0; a < 3; ++a)
+                    gw[3 * p + a] = q.J[a] * s[4] + q.J[3 + a] * s[5] + q.J[6 + a] * s[6];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ Tucker path
+// Thread per atom.  Core [RP][RP][RP] in shared memory; per-thread factor
+// vectors v_l = lerp of two rows of the skeleton-basis factor V'^(l).
+template <int RP, bool GRAD>
+__global__ void __launch_bounds__(128) k_eval_tucker(ProteinView P, LigandView lig,
+                                                     const double* __restrict__ rot,
+                                                     const double* __restrict__ trans,
+                                                     long long Ptot, int PB,
+                                                     double* __restrict__ E,
+                                                     uint8_t* __restrict__ flags,
+                                                     double* __restrict__ gt,
+                                                     double* __restrict__ gw) {
+    constexpr int NC = GRAD ? 7 : 1;
+    constexpr int NT = 128;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* core = (float*)smem;
+    float* v1s = core + RP * RP * RP;                       // [RP][NT]
+    float* dv1s = v1s + RP * NT;                            // [RP][NT] (GRAD)
+    PoseSetup* ps = (PoseSetup*)(dv1s + (GRAD ? RP * NT : 0));
+    double* contrib = (double*)(ps + PB);
+    int* pflag = (int*)(contrib + (size_t)PB * lig.L * NC);
+
+    for (int e = threadIdx.x; e < RP * RP * RP / 4; e += NT)
+        ((float4*)core)[e] = ((const float4*)P.core)[e];
+    const int L = lig.L;
+    const long long nblocks = (Ptot + PB - 1) / PB;
+    const float inv_h = (float)P.inv_h;
+    for (long long pb = blockIdx.x; pb < nblocks; pb += gridDim.x) {
+        long long p0 = pb * PB;
+        __syncthreads();
+        for (int pl = threadIdx.x; pl < PB; pl += blockDim.x) {
+            long long p = p0 + pl;
+            pflag[pl] = 0;
+            if (p < Ptot) setup_pose(P, rot, trans, p, GRAD, ps[pl]);
+            else ps[pl].valid = 0;
+        }
+        __syncthreads();
+        for (int g = threadIdx.x; g < PB * L; g += NT) {
+            int pl = g / L, j = g - pl * L;
+            double* cj = contrib + (size_t)g * NC;
+            const PoseSetup& q = ps[pl];
+            if (!q.valid) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) cj[c] = 0.0;
+                continue;
+            }
+            float4 yq = lig.y[j];
+            float ry[3];
+            for (int r = 0; r < 3; ++r)
+                ry[r] = q.Rf[3 * r] * yq.x + q.Rf[3 * r + 1] * yq.y + q.Rf[3 * r + 2] * yq.z;
+            int ci[3];
+            float cf[3];
+            bool ins[3];
+            for (int a = 0; a < 3; ++a) dev::axis_cell(q.s[a], ry[a] * inv_h, P.n, ci[a], cf[a], ins[a]);
+            // factor vectors
+            float v2[RP], v3[RP], dv2[GRAD ? RP : 1], dv3[GRAD ? RP : 1];
+            {
+                const float4* r0 = (const float4*)(P.F[0] + (size_t)ci[0] * RP);
+                const float4* r1 = (const float4*)(P.F[0] + (size_t)(ci[0] + 1) * RP);
+#pragma unroll
+                for (int c4 = 0; c4 < RP / 4; ++c4) {
+                    float4 a = __ldg(r0 + c4), b = __ldg(r1 + c4);
+                    float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        v1s[(4 * c4 + u) * NT + threadIdx.x] = fmaf(cf[0], bv[u] - av[u], av[u]);
+                        if constexpr (GRAD) dv1s[(4 * c4 + u) * NT + threadIdx.x] = ins[0] ? bv[u] - av[u] : 0.f;
+                    }
+                }
+            }
+            {
+                const float4* r0 = (const float4*)(P.F[1] + (size_t)ci[1] * RP);
+                const float4* r1 = (const float4*)(P.F[1] + (size_t)(ci[1] + 1) * RP);
+#pragma unroll
+                for (int c4 = 0; c4 < RP / 4; ++c4) {
+                    float4 a = __ldg(r0 + c4), b = __ldg(r1 + c4);
+                    float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        v2[4 * c4 + u] = fmaf(cf[1], bv[u] - av[u], av[u]);
+                        if constexpr (GRAD) dv2[4 * c4 + u] = ins[1] ? bv[u] - av[u] : 0.f;
+                    }
+                }
+            }
+            {
+                const float4* r0 = (const float4*)(P.F[2] + (size_t)ci[2] * RP);
+                const float4* r1 = (const float4*)(P.F[2] + (size_t)(ci[2] + 1) * RP);
+#pragma unroll
+                for (int c4 = 0; c4 < RP / 4; ++c4) {
+                    float4 a = __ldg(r0 + c4), b = __ldg(r1 + c4);
+                    float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        v3[4 * c4 + u] = fmaf(cf[2], bv[u] - av[u], av[u]);
+                        if constexpr (GRAD) dv3[4 * c4 + u] = ins[2] ? bv[u] - av[u] : 0.f;
+                    }
+                }
+            }
+            // phi = sum_a v1_a sum_b v2_b sum_c core[a][b][c] v3_c
+            FAcc acc, acc1, acc2, acc3;
+            for (int a = 0; a < RP; ++a) {
+                float ia = 0.f, ia2 = 0.f, ia3 = 0.f;
+#pragma unroll
+                for (int bb = 0; bb < RP; ++bb) {
+                    const float4* row = (const float4*)(core + (a * RP + bb) * RP);
+                    float t = 0.f, t3 = 0.f;
+#pragma unroll
+                    for (int c4 = 0; c4 < RP / 4; ++c4) {
+                        float4 w = row[c4];
+                        t = fmaf(w.x, v3[4 * c4], t);
+                        t = fmaf(w.y, v3[4 * c4 + 1], t);
+                        t = fmaf(w.z, v3[4 * c4 + 2], t);
+                        t = fmaf(w.w, v3[4 * c4 + 3], t);
+                        if constexpr (GRAD) {
+                            t3 = fmaf(w.x, dv3[4 * c4], t3);
+                            t3 = fmaf(w.y, dv3[4 * c4 + 1], t3);
+                            t3 = fmaf(w.z, dv3[4 * c4 + 2], t3);
+                            t3 = fmaf(w.w, dv3[4 * c4 + 3], t3);
+                        }
+                    }
+                    ia = fmaf(v2[bb], t, ia);
+                    if constexpr (GRAD) {
+                        ia2 = fmaf(dv2[bb], t, ia2);
+                        ia3 = fmaf(v2[bb], t3, ia3);
+                    }
+                }
+                float va = v1s[a * NT + threadIdx.x];
+                acc.add(va * ia);
+                if constexpr (GRAD) {
+                    float dva = dv1s[a * NT + threadIdx.x];
+                    acc1.add(dva * ia);
+                    acc2.add(va * ia2);
+                    acc3.add(va * ia3);
+                }
+            }
+            double phi = acc.value();
+            double gl[3] = {0.0, 0.0, 0.0};
+            if constexpr (GRAD) {
+                gl[0] = acc1.value() * P.inv_h;
+                gl[1] = acc2.value() * P.inv_h;
+                gl[2] = acc3.value() * P.inv_h;
+            }
+            // short range and vdW
+            float xf[3];
+            for (int a = 0; a < 3; ++a) xf[a] = (float)(q.t[a] + (double)ry[a]);
+            int clash = 0;
+            short_vdw<GRAD>(P, xf, q, lig.y64 + 3 * j, 0, 1, phi, gl, clash);
+            int fl = clash ? RS_FLAG_CLASH : 0;
+            if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
+            if (fl) atomicOr(&pflag[pl], fl);
+            double qj = lig.q64[j];
+            cj[0] = qj * phi;
+            if constexpr (GRAD) {
+                double g0 = qj * gl[0], g1 = qj * gl[1], g2 = qj * gl[2];
+                cj[1] = g0;
+                cj[2] = g1;
+                cj[3] = g2;
+                double r0 = ry[0], r1 = ry[1], r2 = ry[2];
+                cj[4] = r1 * g2 - r2 * g1;
+                cj[5] = r2 * g0 - r0 * g2;
+                cj[6] = r0 * g1 - r1 * g0;
+            }
+        }
+        __syncthreads();
+        reduce_poses<NC>(P, PB, L, p0, Ptot, ps, contrib, pflag, E, flags, gt, gw);
+    }
+}
+
+// --------------------------------------------------------------- canonical path
+// Warp per atom; lanes stride over the rank in float4 columns, so each of the
+// six factor rows an atom needs is read as contiguous 512-byte segments.
+template <bool GRAD>
+__global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView lig,
+                                                    const double* __restrict__ rot,
+                                                    const double* __restrict__ trans,
+                                                    long long Ptot, int PB,
+                                                    double* __restrict__ E,
+                                                    uint8_t* __restrict__ flags,
+                                                    double* __restrict__ gt,
+                                                    double* __restrict__ gw) {
+    constexpr int NC = GRAD ? 7 : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    PoseSetup* ps = (PoseSetup*)smem;
+    double* contrib = (double*)(ps + PB);
+    int* pflag = (int*)(contrib + (size_t)PB * lig.L * NC);
+    const int L = lig.L;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+    const long long nblocks = (Ptot + PB - 1) / PB;
+    const float inv_h = (float)P.inv_h;
+    const int ld4 = P.ld / 4;
+    const float4* F0 = (const float4*)P.F[0];
+    const float4* F1 = (const float4*)P.F[1];
+    const float4* F2 = (const float4*)P.F[2];
+    for (long long pb = blockIdx.x; pb < nblocks; pb += gridDim.x) {
+        long long p0 = pb * PB;
+        __syncthreads();
+        for (int pl = threadIdx.x; pl < PB; pl += blockDim.x) {
+            long long p = p0 + pl;
+            pflag[pl] = 0;
+            if (p < Ptot) setup_pose(P, rot, trans, p, GRAD, ps[pl]);
+            else ps[pl].valid = 0;
+        }
+        __syncthreads();
+        for (int g = warp; g < PB * L; g += nw) {
+            int pl = g / L, j = g - pl * L;
+            double* cj = contrib + (size_t)g * NC;
+            const PoseSetup& q = ps[pl];
+            if (!q.valid) {
+                if (lane < NC) cj[lane] = 0.0;
+                continue;
+            }
+            float4 yq = lig.y[j];
+            float ry[3];
+            for (int r = 0; r < 3; ++r)
+                ry[r] = q.Rf[3 * r] * yq.x + q.Rf[3 * r + 1] * yq.y + q.Rf[3 * r + 2] * yq.z;
+            int ci[3];
+            float cf[3];
+            bool ins[3];
+            for (int a = 0; a < 3; ++a) dev::axis_cell(q.s[a], ry[a] * inv_h, P.n, ci[a], cf[a], ins[a]);
+            const float4* a0 = F0 + (size_t)ci[0] * ld4;
+            const float4* a1 = F1 + (size_t)ci[1] * ld4;
+            const float4* a2 = F2 + (size_t)ci[2] * ld4;
+            FAcc acc, acc1, acc2, acc3;
+            for (int r4 = lane; r4 < ld4; r4 += 32) {
+                float4 x0 = __ldg(a0 + r4), x0n = __ldg(a0 + ld4 + r4);
+                float4 x1 = __ldg(a1 + r4), x1n = __ldg(a1 + ld4 + r4);
+                float4 x2 = __ldg(a2 + r4), x2n = __ldg(a2 + ld4 + r4);
+                float u0[4] = {x0.x, x0.y, x0.z, x0.w}, w0[4] = {x0n.x, x0n.y, x0n.z, x0n.w};
+                float u1[4] = {x1.x, x1.y, x1.z, x1.w}, w1[4] = {x1n.x, x1n.y, x1n.z, x1n.w};
+                float u2[4] = {x2.x, x2.y, x2.z, x2.w}, w2[4] = {x2n.x, x2n.y, x2n.z, x2n.w};
+                float s = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float d0 = w0[u] - u0[u], d1 = w1[u] - u1[u], d2 = w2[u] - u2[u];
+                    float l0 = fmaf(cf[0], d0, u0[u]);
+                    float l1 = fmaf(cf[1], d1, u1[u]);
+                    float l2 = fmaf(cf[2], d2, u2[u]);
+                    float l12 = l1 * l2;
+                    s = fmaf(l0, l12, s);
+                    if constexpr (GRAD) {
+                        s1 = fmaf(d0, l12, s1);
+                        s2 = fmaf(l0 * d1, l2, s2);
+                        s3 = fmaf(l0 * l1, d2, s3);
+                    }
+                }
+                acc.add(s);
+                if constexpr (GRAD) {
+                    acc1.add(s1);
+                    acc2.add(s2);
+                    acc3.add(s3);
+                }
+            }
+            double phi = warp_sum(acc.value());
+            double gl[3] = {0.0, 0.0, 0.0};
+            if constexpr (GRAD) {
+                gl[0] = ins[0] ? warp_sum(acc1.value()) * P.inv_h : 0.0;
+                gl[1] = ins[1] ? warp_sum(acc2.value()) * P.inv_h : 0.0;
+                gl[2] = ins[2] ? warp_sum(acc3.value()) * P.inv_h : 0.0;
+            }
+            // short range split over lanes
+            float xf[3];
+            for (int a = 0; a < 3; ++a) xf[a] = (float)(q.t[a] + (double)ry[a]);
+            double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
+            int clash = 0;
+            short_vdw<GRAD>(P, xf, q, lig.y64 + 3 * j, lane, 32, phs, gs, clash);
+            phi += warp_sum(phs);
+            if constexpr (GRAD)
+                for (int a = 0; a < 3; ++a) gl[a] += warp_sum(gs[a]);
+            clash = __any_sync(0xffffffffu, clash);
+            if (lane == 0) {
+                int fl = clash ? RS_FLAG_CLASH : 0;
+                if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
+                if (fl) atomicOr(&pflag[pl], fl);
+                double qj = lig.q64[j];
+                cj[0] = qj * phi;
+                if constexpr (GRAD) {
+                    double g0 = qj * gl[0], g1 = qj * gl[1], g2 = qj * gl[2];
+                    cj[1] = g0;
+                    cj[2] = g1;
+                    cj[3] = g2;
+                    double r0 = ry[0], r1 = ry[1], r2 = ry[2];
+                    cj[4] = r1 * g2 - r2 * g1;
+                    cj[5] = r2 * g0 - r0 * g2;
+                    cj[6] = r0 * g1 - r1 * g0;
+                }
+            }
+        }
+        __syncthreads();
+        reduce_poses<NC>(P, PB, L, p0, Ptot, ps, contrib, pflag, E, flags, gt, gw);
+    }
+}
+
+// Ligand about its geometric centre (FP64 mean in a fixed order); one CTA.
+__global__ void k_prep_ligand(int L, const double* __restrict__ xyz, const double* __restrict__ q,
+                              float4* __restrict__ y, double* __restrict__ y64,
+                              double* __restrict__ q64) {
+    __shared__ double sm[3][256];
+    double s[3] = {0, 0, 0};
+    for (int j = threadIdx.x; j < L; j += blockDim.x)
+        for (int a = 0; a < 3; ++a) s[a] += xyz[3 * (size_t)j + a];
+    for (int a = 0; a < 3; ++a) sm[a][threadIdx.x] = s[a];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int a = 0; a < 3; ++a) sm[a][threadIdx.x] += sm[a][threadIdx.x + o];
+        __syncthreads();
+    }
+    double c0 = sm[0][0] / L, c1 = sm[1][0] / L, c2 = sm[2][0] / L;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+        double a = xyz[3 * (size_t)j] - c0, b = xyz[3 * (size_t)j + 1] - c1,
+               c = xyz[3 * (size_t)j + 2] - c2;
+        y64[3 * (size_t)j] = a;
+        y64[3 * (size_t)j + 1] = b;
+        y64[3 * (size_t)j + 2] = c;
+        q64[j] = q[j];
+        y[j] = make_float4((float)a, (float)b, (float)c, (float)q[j]);
+    }
+}
+
+template <int RP, bool GRAD>
+size_t tucker_smem(int PB, int L) {
+    size_t s = (size_t)RP * RP * RP * 4 + (size_t)RP * 128 * 4 * (GRAD ? 2 : 1);
+    s += (size_t)PB * sizeof(PoseSetup);
+    s += (size_t)PB * L * (GRAD ? 7 : 1) * 8;
+    s += (size_t)PB * 4;
+    return (s + 15) / 16 * 16;
+}
+
+template <bool GRAD>
+size_t canon_smem(int PB, int L) {
+    size_t s = (size_t)PB * sizeof(PoseSetup) + (size_t)PB * L * (GRAD ? 7 : 1) * 8 + (size_t)PB * 4;
+    return (s + 15) / 16 * 16;
+}
+
+int g_num_sms = 0;
+
+int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+template <int RP, bool GRAD>
+rs_status launch_tucker(const EvalLaunch& a, cudaStream_t st) {
+    int PB = a.PB > 0 ? a.PB : std::min(128, std::max(1, 512 / a.lig.L));
+    size_t sm = tucker_smem<RP, GRAD>(PB, a.lig.L);
+    while (sm > 160 * 1024 && PB > 1) {
+        PB = std::max(1, PB / 2);
+        sm = tucker_smem<RP, GRAD>(PB, a.lig.L);
+    }
+    if (sm > 220 * 1024) {
+        set_error("ligand too large for the pose kernel (L=%d)", a.lig.L);
+        return RS_ERR_UNSUPPORTED;
+    }
+    auto kern = k_eval_tucker<RP, GRAD>;
+    RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    RS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, sm));
+    long long nblocks = (a.P + PB - 1) / PB;
+    long long grid = std::min<long long>(nblocks, (long long)std::max(per_sm, 1) * num_sms());
+    if (a.grid > 0) grid = std::min<long long>(nblocks, a.grid);
+    if (grid < 1) return RS_OK;
+    kern<<<(unsigned)grid, 128, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
+                                          a.gt, a.gw);
+    RS_TRY_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
+template <bool GRAD>
+rs_status launch_canon(const EvalLaunch& a, cudaStream_t st) {
+    int PB = a.PB > 0 ? a.PB : std::min(64, std::max(1, 256 / a.lig.L));
+    size_t sm = canon_smem<GRAD>(PB, a.lig.L);
+    while (sm > 160 * 1024 && PB > 1) {
+        PB = std::max(1, PB / 2);
+        sm = canon_smem<GRAD>(PB, a.lig.L);
+    }
+    if (sm > 220 * 1024) {
+        set_error("ligand too large for the pose kernel (L=%d)", a.lig.L);
+        return RS_ERR_UNSUPPORTED;
+    }
+    auto kern = k_eval_canon<GRAD>;
+    RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    RS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm));
+    long long nblocks = (a.P + PB - 1) / PB;
+    long long grid = std::min<long long>(nblocks, (long long)std::max(per_sm, 1) * num_sms());
+    if (a.grid > 0) grid = std::min<long long>(nblocks, a.grid);
+    if (grid < 1) return RS_OK;
+    kern<<<(unsigned)grid, 256, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
+                                          a.gt, a.gw);
+    RS_TRY_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
+}  // namespace
+
+rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, double* y64,
+                             double* q64, cudaStream_t st) {
+    k_prep_ligand<<<1, 256, 0, st>>>(L, xyz, q, y, y64, q64);
+    RS_TRY_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
+rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st) {
+    if (a.P <= 0) return RS_OK;
+    if (a.prot.kind == 0) return grad ? launch_canon<true>(a, st) : launch_canon<false>(a, st);
+    switch (a.prot.R) {
+#define RS_CASE(R) \
+    case R: return grad ? launch_tucker<R, true>(a, st) : launch_tucker<R, false>(a, st);
+        RS_CASE(4) RS_CASE(8) RS_CASE(12) RS_CASE(16) RS_CASE(20) RS_CASE(24) RS_CASE(28) RS_CASE(32)
+#undef RS_CASE
+        default:
+            set_error("unsupported padded Tucker rank %d", a.prot.R);
+            return RS_ERR_UNSUPPORTED;
+    }
+}
+
+// Layout of the per-call ligand scratch inside the context buffer.
+size_t ligand_scratch_bytes(int L) {
+    return ((size_t)L * sizeof(float4) + (size_t)L * 3 * 8 + (size_t)L * 8 + 256 * 3);
+}
+
+LigandView carve_ligand(void* base, int L) {
+    char* p = (char*)base;
+    LigandView v;
+    v.L = L;
+    v.y = (const float4*)p;
+    p += ((size_t)L * sizeof(float4) + 255) / 256 * 256;
+    v.y64 = (const double*)p;
+    p += ((size_t)L * 24 + 255) / 256 * 256;
+    v.q64 = (const double*)p;
+    return v;
+}
+
+}  // namespace rs
+
+// ------------------------------------------------------------------ C ABI
+namespace {
+
+using namespace rs;
+
+rs_status run_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L, const double* lig_xyz,
+                    const double* lig_q, int64_t P, const double* rot, const double* trans,
+                    double* E_out, double* dE_dt, double* dE_dw, uint8_t* flags_out,
+                    int mem_flags, void* stream, bool grad) {
+    clear_error();
+    RS_CHECK_ARG(ctx && prot, "NULL context or protein");
+    RS_CHECK_ARG(L >= 1 && L <= 4096, "L=%d out of range [1, 4096]", L);
+    RS_CHECK_ARG(P >= 0 && P <= 0x7fffffffLL, "P=%lld out of range", (long long)P);
+    RS_CHECK_ARG(mem_flags == RS_MEM_HOST || mem_flags == RS_MEM_DEVICE, "bad mem_flags %d", mem_flags);
+    RS_CHECK_ARG(prot->device == ctx->device, "protein built on device %d, context on %d",
+                 prot->device, ctx->device);
+    if (P == 0) return RS_OK;
+    RS_CHECK_ARG(lig_xyz && lig_q && rot && trans && E_out, "NULL input or output pointer");
+    if (grad) RS_CHECK_ARG(dE_dt && dE_dw, "NULL gradient output");
+    RS_TRY_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    const int rdim = grad ? 3 : 4;
+    // ligand scratch
+    RS_TRY(ensure_buffer(&ctx->lig_buf, &ctx->lig_bytes, ligand_scratch_bytes(L) + 1024));
+    LigandView lig = carve_ligand(ctx->lig_buf, L);
+    const double *d_xyz = lig_xyz, *d_q = lig_q, *d_rot = rot, *d_trans = trans;
+    double *d_E = E_out, *d_gt = dE_dt, *d_gw = dE_dw;
+    uint8_t* d_flags = flags_out;
+    if (mem_flags == RS_MEM_HOST) {
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            size_t o = off;
+            off += (bytes + 255) / 256 * 256;
+            return o;
+        };
+        size_t o_xyz = take((size_t)L * 24), o_q = take((size_t)L * 8);
+        size_t o_rot = take((size_t)P * rdim * 8), o_tr = take((size_t)P * 24);
+        size_t o_E = take((size_t)P * 8), o_f = take((size_t)P);
+        size_t o_gt = grad ? take((size_t)P * 24) : 0, o_gw = grad ? take((size_t)P * 24) : 0;
+        RS_TRY(ensure_buffer(&ctx->io_buf, &ctx->io_bytes, off));
+        char* b = (char*)ctx->io_buf;
+        d_xyz = (const double*)(b + o_xyz);
+        d_q = (const double*)(b + o_q);
+        d_rot = (const double*)(b + o_rot);
+        d_trans = (const double*)(b + o_tr);
+        d_E = (double*)(b + o_E);
+        d_flags = (uint8_t*)(b + o_f);
+        if (grad) {
+            d_gt = (double*)(b + o_gt);
+            d_gw = (double*)(b + o_gw);
+        }
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_xyz, lig_xyz, (size_t)L * 24, cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_q, lig_q, (size_t)L * 8, cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_rot, rot, (size_t)P * rdim * 8, cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_trans, trans, (size_t)P * 24, cudaMemcpyHostToDevice, st));
+    }
+    RS_TRY(launch_prep_ligand(L, d_xyz, d_q, (float4*)lig.y, (double*)lig.y64, (double*)lig.q64, st));
+    EvalLaunch a;
+    a.prot = prot->view;
+    a.lig = lig;
+    a.rot = d_rot;
+    a.trans = d_trans;
+    a.P = P;
+    a.E = d_E;
+    a.flags = (mem_flags == RS_MEM_HOST || flags_out) ? d_flags : nullptr;
+    a.gt = d_gt;
+    a.gw = d_gw;
+    RS_TRY(launch_eval(a, grad, st));
+    if (mem_flags == RS_MEM_HOST) {
+        RS_TRY_CUDA(cudaMemcpyAsync(E_out, d_E, (size_t)P * 8, cudaMemcpyDeviceToHost, st));
+        if (flags_out) RS_TRY_CUDA(cudaMemcpyAsync(flags_out, d_flags, (size_t)P, cudaMemcpyDeviceToHost, st));
+        if (grad) {
+            RS_TRY_CUDA(cudaMemcpyAsync(dE_dt, d_gt, (size_t)P * 24, cudaMemcpyDeviceToHost, st));
+            RS_TRY_CUDA(cudaMemcpyAsync(dE_dw, d_gw, (size_t)P * 24, cudaMemcpyDeviceToHost, st));
+        }
+        RS_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    return RS_OK;
+}
+
+}  // namespace
+
+extern "C" rs_status rs_energy_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
+                                     const double* lig_xyz, const double* lig_q, int64_t P,
+                                     const double* quat, const double* trans, double* E_out,
+                                     uint8_t* flags_out, int mem_flags, void* stream) {
+    return run_poses(ctx, prot, L, lig_xyz, lig_q, P, quat, trans, E_out, nullptr, nullptr,
+                     flags_out, mem_flags, stream, false);
+}
+
+extern "C" rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
+                                          const double* lig_xyz, const double* lig_q, int64_t P,
+                                          const double* rotvec, const double* trans,
+                                          double* E_out, double* dE_dt, double* dE_dw,
+                                          uint8_t* flags_out, int mem_flags, void* stream) {
+    return run_poses(ctx, prot, L, lig_xyz, lig_q, P, rotvec, trans, E_out, dE_dt, dE_dw,
+                     flags_out, mem_flags, stream, true);
+}

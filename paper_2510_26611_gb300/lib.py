@@ -1,0 +1,293 @@
+"""Thin ctypes binding of librs (include/rs.h), same names as the C ABI.
+
+Only argument marshalling happens here: numpy arrays and CPU tensors are passed
+as host pointers (RS_MEM_HOST), CUDA tensors as device pointers on the current
+torch stream (RS_MEM_DEVICE).  Every computation runs in the library's kernels.
+The library is built on first use; if it cannot be built or loaded, import of
+this module raises -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import _build
+
+RS_OK = 0
+RS_ERR_INVALID = -1
+RS_ERR_OOM = -2
+RS_ERR_CUDA = -3
+RS_ERR_TIMEOUT = -4
+RS_ERR_BUSY = -5
+RS_ERR_NOT_READY = -6
+RS_ERR_UNSUPPORTED = -7
+RS_MEM_HOST = 0
+RS_MEM_DEVICE = 1
+RS_FLAG_CLASH = 1
+RS_FLAG_OUT_OF_GRID = 2
+
+_STATUS_NAMES = {0: "RS_OK", -1: "RS_ERR_INVALID", -2: "RS_ERR_OOM", -3: "RS_ERR_CUDA",
+                 -4: "RS_ERR_TIMEOUT", -5: "RS_ERR_BUSY", -6: "RS_ERR_NOT_READY",
+                 -7: "RS_ERR_UNSUPPORTED"}
+
+
+class RSError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class rs_params(C.Structure):
+    _fields_ = [("n", C.c_int32), ("b", C.c_double), ("sigma", C.c_double), ("R_l", C.c_int32),
+                ("r_min", C.c_double), ("tau", C.c_double), ("short_tol", C.c_double),
+                ("tucker_cap", C.c_int32), ("eps_r", C.c_double)]
+
+
+class rs_protein_info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("N", C.c_int32), ("R_l", C.c_int32), ("K", C.c_int32),
+                ("b", C.c_double), ("h", C.c_double), ("sigma", C.c_double), ("r_c", C.c_double),
+                ("h_s", C.c_double), ("quad_err", C.c_double), ("kind", C.c_int32),
+                ("rank", C.c_int32 * 3), ("sv_gap", C.c_double * 3), ("sv_tail", C.c_double * 3),
+                ("device_bytes", C.c_size_t)]
+
+
+def _load() -> C.CDLL:
+    path = os.environ.get("RS_LIBRARY") or _build.build()
+    lib = C.CDLL(path)
+    vp, i32, i64, st = C.c_void_p, C.c_int32, C.c_int64, C.c_int
+    sig = {
+        "rs_params_default": (None, [C.POINTER(rs_params)]),
+        "rs_ctx_create": (st, [C.c_int, C.POINTER(vp)]),
+        "rs_ctx_destroy": (None, [vp]),
+        "rs_last_error": (C.c_char_p, []),
+        "rs_version": (C.c_char_p, []),
+        "rs_build_protein": (st, [vp, i32, vp, vp, C.POINTER(rs_params), C.c_int, vp, C.POINTER(vp)]),
+        "rs_protein_free": (None, [vp]),
+        "rs_protein_get_info": (st, [vp, C.POINTER(rs_protein_info)]),
+        "rs_protein_get_table": (st, [vp, vp, vp, vp]),
+        "rs_energy_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
+        "rs_energy_grad_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIBRARY_PATH = _lib._name
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/rs.h."""
+    hdr = os.path.join(_build.ROOT, "include", "rs.h")
+    text = open(hdr).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rs_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status: int):
+    if status != RS_OK:
+        raise RSError(status, _lib.rs_last_error().decode())
+
+
+def rs_last_error() -> str:
+    return _lib.rs_last_error().decode()
+
+
+def rs_version() -> str:
+    return _lib.rs_version().decode()
+
+
+def rs_params_default(**overrides) -> rs_params:
+    p = rs_params()
+    _lib.rs_params_default(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def rs_ctx_create(device: int = 0) -> int:
+    h = C.c_void_p()
+    _check(_lib.rs_ctx_create(device, C.byref(h)))
+    return h.value
+
+
+def rs_ctx_destroy(ctx: int) -> None:
+    _lib.rs_ctx_destroy(ctx)
+
+
+# ------------------------------------------------------------------ marshalling
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _host(x, dtype) -> np.ndarray:
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(x, dtype=dtype))
+
+
+def _dev(x, dtype):
+    import torch
+    tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
+    if x.dtype != tdt or not x.is_contiguous():
+        x = x.to(tdt).contiguous()
+    return x
+
+
+def _ptr(x):
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def rs_build_protein(ctx: int, xyz, q, params: rs_params | None = None, stream=None) -> int:
+    """Algorithm TEP: returns a protein handle (free with rs_protein_free)."""
+    if params is None:
+        params = rs_params_default()
+    h = C.c_void_p()
+    if _is_cuda(xyz):
+        xyz_, q_ = _dev(xyz, np.float64), _dev(q, np.float64)
+        mem, sp = RS_MEM_DEVICE, _stream_ptr(stream)
+    else:
+        xyz_, q_ = _host(xyz, np.float64), _host(q, np.float64)
+        mem, sp = RS_MEM_HOST, None
+    N = int(q_.shape[0])
+    if tuple(xyz_.shape) != (N, 3):
+        raise RSError(RS_ERR_INVALID, f"xyz must be ({N}, 3), got {tuple(xyz_.shape)}")
+    _check(_lib.rs_build_protein(ctx, N, _ptr(xyz_), _ptr(q_), C.byref(params), mem, sp, C.byref(h)))
+    return h.value
+
+
+def rs_protein_free(prot: int) -> None:
+    _lib.rs_protein_free(prot)
+
+
+def rs_protein_get_info(prot: int) -> dict:
+    info = rs_protein_info()
+    _check(_lib.rs_protein_get_info(prot, C.byref(info)))
+    d = {k: getattr(info, k) for k, _ in info._fields_}
+    for k in ("rank", "sv_gap", "sv_tail"):
+        d[k] = list(d[k])
+    return d
+
+
+def rs_protein_get_table(prot: int):
+    K = rs_protein_get_info(prot)["K"]
+    t, a, il = np.zeros(K), np.zeros(K), np.zeros(K, dtype=np.uint8)
+    _check(_lib.rs_protein_get_table(prot, t.ctypes.data, a.ctypes.data, il.ctypes.data))
+    return t, a, il.astype(bool)
+
+
+def _pose_call(grad: bool, ctx, prot, lig_xyz, lig_q, rot, trans, E_out, flags_out,
+               dE_dt, dE_dw, stream):
+    rdim = 3 if grad else 4
+    if _is_cuda(rot):
+        import torch
+        dev = rot.device
+        lx, lq = _dev(lig_xyz.to(dev), np.float64), _dev(lig_q.to(dev), np.float64)
+        r, t = _dev(rot, np.float64), _dev(trans, np.float64)
+        P = int(r.shape[0])
+        E = E_out if E_out is not None else torch.empty(P, dtype=torch.float64, device=dev)
+        f = flags_out if flags_out is not None else torch.empty(P, dtype=torch.uint8, device=dev)
+        gt = gw = None
+        if grad:
+            gt = dE_dt if dE_dt is not None else torch.empty((P, 3), dtype=torch.float64, device=dev)
+            gw = dE_dw if dE_dw is not None else torch.empty((P, 3), dtype=torch.float64, device=dev)
+        mem, sp = RS_MEM_DEVICE, _stream_ptr(stream)
+    else:
+        lx, lq = _host(lig_xyz, np.float64), _host(lig_q, np.float64)
+        r, t = _host(rot, np.float64), _host(trans, np.float64)
+        P = int(r.shape[0])
+        E = E_out if E_out is not None else np.empty(P)
+        f = flags_out if flags_out is not None else np.empty(P, dtype=np.uint8)
+        gt = gw = None
+        if grad:
+            gt = dE_dt if dE_dt is not None else np.empty((P, 3))
+            gw = dE_dw if dE_dw is not None else np.empty((P, 3))
+        mem, sp = RS_MEM_HOST, None
+    L = int(lq.shape[0])
+    if tuple(lx.shape) != (L, 3) or tuple(r.shape) != (P, rdim) or tuple(t.shape) != (P, 3):
+        raise RSError(RS_ERR_INVALID, "shape mismatch in pose arguments")
+    if grad:
+        _check(_lib.rs_energy_grad_poses(ctx, prot, L, _ptr(lx), _ptr(lq), P, _ptr(r), _ptr(t),
+                                         _ptr(E), _ptr(gt), _ptr(gw), _ptr(f), mem, sp))
+        return E, gt, gw, f
+    _check(_lib.rs_energy_poses(ctx, prot, L, _ptr(lx), _ptr(lq), P, _ptr(r), _ptr(t),
+                                _ptr(E), _ptr(f), mem, sp))
+    return E, f
+
+
+def rs_energy_poses(ctx, prot, lig_xyz, lig_q, quat, trans, E_out=None, flags_out=None,
+                    stream=None):
+    """Algorithm PLIE over poses given by quaternions; returns (E, flags)."""
+    return _pose_call(False, ctx, prot, lig_xyz, lig_q, quat, trans, E_out, flags_out, None,
+                      None, stream)
+
+
+def rs_energy_grad_poses(ctx, prot, lig_xyz, lig_q, rotvec, trans, E_out=None, dE_dt=None,
+                         dE_dw=None, flags_out=None, stream=None):
+    """Energies and exact gradients for poses given by rotation vectors;
+    returns (E, dE_dt, dE_dw, flags)."""
+    return _pose_call(True, ctx, prot, lig_xyz, lig_q, rotvec, trans, E_out, flags_out, dE_dt,
+                      dE_dw, stream)
+
+
+# ------------------------------------------------------------------ handle owners
+class Context:
+    """Owns an rs_ctx."""
+
+    def __init__(self, device: int = 0):
+        self.handle = rs_ctx_create(device)
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            rs_ctx_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Protein:
+    """Owns an rs_protein built by Algorithm TEP."""
+
+    def __init__(self, ctx: Context, xyz, q, params: rs_params | None = None, stream=None):
+        self.ctx = ctx
+        self.handle = rs_build_protein(ctx.handle, xyz, q, params, stream)
+        self.info = rs_protein_get_info(self.handle)
+
+    def energies(self, lig_xyz, lig_q, quat, trans, **kw):
+        return rs_energy_poses(self.ctx.handle, self.handle, lig_xyz, lig_q, quat, trans, **kw)
+
+    def energies_grad(self, lig_xyz, lig_q, rotvec, trans, **kw):
+        return rs_energy_grad_poses(self.ctx.handle, self.handle, lig_xyz, lig_q, rotvec, trans, **kw)
+
+    def close(self):
+        if self.handle:
+            rs_protein_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
