@@ -232,7 +232,13 @@ def rhosvd(U, xi, cap: int, eps_r: float = 1e-7):
     V, svals = [], []
     for ax in range(3):
         Z = U[ax] * w[None, :]
-        Ul, s, _ = np.linalg.svd(Z, full_matrices=False)
+        # SVD of the wide Z through a QR of Z^T (Z = R^T Q^T): same left singular
+        # vectors and singular values, without forming the right factor of Z.
+        if Z.shape[1] > Z.shape[0]:
+            Rt = np.linalg.qr(Z.T, mode="r").T
+            Ul, s, _ = np.linalg.svd(Rt)
+        else:
+            Ul, s, _ = np.linalg.svd(Z, full_matrices=False)
         r = int(np.count_nonzero(s > eps_r * s[0]))
         if cap > 0:
             r = min(r, cap)
