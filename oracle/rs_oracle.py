@@ -299,10 +299,12 @@ def _lerp_rows(M, i, f):
     return (1.0 - f)[:, None] * M[i] + f[:, None] * M[i + 1]
 
 
-def _long_range(model: RSModel, pts: np.ndarray, grad: bool, chunk: int = 256):
+def _long_range(model: RSModel, pts: np.ndarray, grad: bool, chunk: int | None = None):
     """Trilinear interpolation of the long-range grid tensor at points, done per
     rank-1 term as a product of per-axis linear interpolations."""
     P = pts.shape[0]
+    if chunk is None:  # points per batch: bounded memory for large canonical ranks
+        chunk = 256 if model.kind == "canonical" else 16384
     h = model.h
     phi = np.zeros(P)
     g = np.zeros((P, 3)) if grad else None
@@ -325,12 +327,21 @@ def _long_range(model: RSModel, pts: np.ndarray, grad: bool, chunk: int = 256):
                 g[s0:s0 + chunk, 1] = (xi * vals[0] * ders[1] * vals[2]).sum(axis=1)
                 g[s0:s0 + chunk, 2] = (xi * vals[0] * vals[1] * ders[2]).sum(axis=1)
         else:
+            # phi = sum_a v1_a sum_b v2_b sum_c beta_abc v3_c (nested sums of the
+            # Tucker entry evaluation; the c-sum is a matrix product)
             B = model.beta
-            phi[s0:s0 + chunk] = np.einsum("abc,pa,pb,pc->p", B, *vals, optimize=True)
+            r1, r2, r3 = B.shape
+            Bm = B.reshape(r1 * r2, r3).T
+
+            def contract(x1, x2, x3):
+                t = (x3 @ Bm).reshape(-1, r1, r2)
+                return ((t * x2[:, None, :]).sum(axis=2) * x1).sum(axis=1)
+
+            phi[s0:s0 + chunk] = contract(*vals)
             if grad:
-                g[s0:s0 + chunk, 0] = np.einsum("abc,pa,pb,pc->p", B, ders[0], vals[1], vals[2], optimize=True)
-                g[s0:s0 + chunk, 1] = np.einsum("abc,pa,pb,pc->p", B, vals[0], ders[1], vals[2], optimize=True)
-                g[s0:s0 + chunk, 2] = np.einsum("abc,pa,pb,pc->p", B, vals[0], vals[1], ders[2], optimize=True)
+                g[s0:s0 + chunk, 0] = contract(ders[0], vals[1], vals[2])
+                g[s0:s0 + chunk, 1] = contract(vals[0], ders[1], vals[2])
+                g[s0:s0 + chunk, 2] = contract(vals[0], vals[1], ders[2])
     return phi, g
 
 
