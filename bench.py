@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput of the RS-tensor pose-energy path on GB300.
+
+One step = the whole hot path over one batch of the protein-scale workload:
+Algorithm TEP (sinc table, cell list, long-range factors, RHOSVD to Tucker rank
+<= 20) for N=3000 protein atoms on an n=1025 grid, then Algorithm PLIE energies,
+vdW flags and exact rigid-body gradients for P=1e5 poses of a 50-atom ligand.
+value = poses per second through that step (whole job over all ranks).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "poses/sec at <=1e-5 rel err vs FP64 oracle; served p50/p99 latency vs plain"
+UNIT = "poses/s"
+WORKLOAD = ("plain_protein: N=3000 charges on a jittered 1.5 A lattice in a (20,14,10) A "
+            "ellipsoid, 8% +-1; ligand L=50; n=1025 on [-64,64]^3; R_l=20; Tucker rank <= 20; "
+            "P=1e5 poses, |t| in [10,30] A; step = TEP build + energies + gradients")
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--poses", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def quat_to_rotvec(q: np.ndarray) -> np.ndarray:
+    """Rotation vector of a unit quaternion (w, x, y, z): input preparation for the
+    gradient pass, the same rotations as the energy pass."""
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    q = np.where(q[:, :1] < 0, -q, q)
+    v = q[:, 1:]
+    s = np.linalg.norm(v, axis=1)
+    ang = 2.0 * np.arctan2(s, q[:, 0])
+    scale = np.where(s > 1e-12, ang / np.where(s > 1e-12, s, 1.0), 2.0)
+    return v * scale[:, None]
+
+
+def workload(P: int, seed: int = 1):
+    import workloads as W
+    w = W.plain_protein(seed=seed, P=P)
+    return w, quat_to_rotvec(w.quat)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={SMI_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[4:]))
+                except ValueError:
+                    continue
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[2][1:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ roofline
+def peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        m = json.load(open(path))
+        return {"hbm_gbs": m["hbm_gbs"], "sm_max_mhz": m.get("sm_max_mhz", 2070.0), "src": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+# Kernel -> (bound, unit of its reported work).  FP32 ALU peak: 152 SMs x 128 FP32
+# lanes x 2 flops (FMA) x max SM clock; FP64 ALU peak: 1.25 TFLOP/s (GB300 table).
+KERNEL_KIND = {
+    "k_eval_wform": ("alu", "fp32"), "k_eval_wform_grad": ("alu", "fp32"),
+    "k_eval_canon": ("alu", "fp32"), "k_eval_canon_grad": ("alu", "fp32"),
+    "k_project": ("alu", "fp64"), "k_core": ("alu", "fp64"), "k_gauss_dsum": ("alu", "fp64"),
+    "k_gram": ("alu", "fp64"), "k_gemm_gq": ("alu", "fp64"), "k_canon_factors": ("hbm", "bytes"),
+}
+
+
+def roofline(timings: dict, pk: dict) -> dict:
+    if not timings:
+        return None
+    name, rec = max(timings.items(), key=lambda kv: kv[1]["ms"])
+    bound, unit = KERNEL_KIND.get(name, ("alu", "fp32"))
+    per_launch_s = rec["ms"] / 1e3 / max(rec["launches"], 1)
+    work = rec["work"] / max(rec["launches"], 1)
+    if unit == "bytes":
+        ach, peak, u = work / per_launch_s / 1e9, pk["hbm_gbs"], "GB/s"
+        note = "HBM, measured copy bandwidth"
+    elif unit == "fp64":
+        ach, peak, u = work / per_launch_s / 1e12, 1.25, "TFLOP/s"
+        note = "FP64 ALU, nominal 1.25 TFLOP/s"
+    else:
+        ach = work / per_launch_s / 1e12
+        peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        u = "TFLOP/s"
+        note = "FP32 ALU, 152 SMs x 128 lanes x 2 x max SM clock"
+    total = sum(r["ms"] for r in timings.values())
+    return {"kernel": name, "bound": bound, "achieved": round(ach, 4), "peak": round(peak, 3),
+            "unit": u, "frac": round(ach / peak, 4), "traffic": None, "peak_src": note + f" ({pk['src']})",
+            "avg_launch_ms": round(per_launch_s * 1e3, 4),
+            "share_of_timed_kernels": round(rec["ms"] / total, 4) if total > 0 else None}
+
+
+# ------------------------------------------------------------------ CPU baseline (the oracle)
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle as O
+sys.path.insert(0, {root!r})
+from bench import workload
+P_full, P_s = {P}, {Ps}
+w, rv = workload(P_full)
+idx = np.arange(P_s)
+t0 = time.perf_counter()
+m = O.build_model(w.prot_xyz, w.prot_q, w.n, w.b, w.sigma, w.R_l, tucker_cap=w.tucker_cap)
+t1 = time.perf_counter()
+O.pose_energies(m, w.lig_xyz, w.lig_q, w.quat[idx], w.trans[idx])
+t2 = time.perf_counter()
+O.pose_gradients(m, w.lig_xyz, w.lig_q, rv[idx], w.trans[idx])
+t3 = time.perf_counter()
+print(json.dumps({{"build_s": t1 - t0, "energy_s": t2 - t1, "grad_s": t3 - t2}}))
+"""
+
+
+def oracle_sample(P: int, P_s: int, threads: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = ORACLE_SNIPPET.format(root=ROOT, P=P, Ps=P_s)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    t = json.loads(r.stdout.strip().splitlines()[-1])
+    per_pose = (t["energy_s"] + t["grad_s"]) / P_s
+    step_s = t["build_s"] + per_pose * P
+    return {"value": P / step_s, "step_s": step_s, "timings": t, "P_s": P_s}
+
+
+def cpu_baseline(P: int) -> dict:
+    cores = os.cpu_count() or 1
+    P_s = 400
+    r = oracle_sample(P, P_s, cores)
+    return {"value": round(r["value"], 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one FP64 TEP build (RHOSVD) plus energies and gradients of the first "
+                       f"{P_s} poses, per-pose time scaled to P={P}; numpy/BLAS threads={cores}"),
+            "timings_s": {k: round(v, 3) for k, v in r["timings"].items()}}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    P = args.poses
+    cores = os.cpu_count() or 1
+    P_s = 100
+    vals, steps_s = [], []
+    for it in range(args.warmup + args.steps):
+        r = oracle_sample(P, P_s, cores)
+        if it >= args.warmup:
+            vals.append(r["value"])
+            steps_s.append(r["step_s"])
+    value = statistics.mean(vals)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * statistics.mean(steps_s), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "poses": P},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores,
+                             "kind": "oracle",
+                             "sample": (f"each step: one FP64 TEP build plus energies and gradients of "
+                                        f"{P_s} poses, per-pose time scaled to P={P}")},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2510_26611_gb300 import lib
+
+    P = args.poses
+    w, rv = workload(P, seed=1 + rank)
+    ctx = lib.Context(local)
+    params = lib.rs_params_default(n=w.n, b=w.b, sigma=w.sigma, R_l=w.R_l, tucker_cap=w.tucker_cap)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    xyz, q = T(w.prot_xyz), T(w.prot_q)
+    lx, lq = T(w.lig_xyz), T(w.lig_q)
+    quat, trans, rvec = T(w.quat), T(w.trans), T(rv)
+    E = torch.empty(P, dtype=torch.float64, device=dev)
+    F = torch.empty(P, dtype=torch.uint8, device=dev)
+    Eg = torch.empty(P, dtype=torch.float64, device=dev)
+    Fg = torch.empty(P, dtype=torch.uint8, device=dev)
+    gt = torch.empty((P, 3), dtype=torch.float64, device=dev)
+    gw = torch.empty((P, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        h = lib.rs_build_protein(ctx.handle, xyz, q, params)
+        lib.rs_energy_poses(ctx.handle, h, lx, lq, quat, trans, E_out=E, flags_out=F)
+        lib.rs_energy_grad_poses(ctx.handle, h, lx, lq, rvec, trans, E_out=Eg, dE_dt=gt, dE_dw=gw,
+                                 flags_out=Fg)
+        lib.rs_protein_free(h)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    lib.rs_timing_reset()
+    lib.rs_timing_enable(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = lib.rs_stats_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()                       # L2 flush between steps (untimed)
+            torch.cuda.synchronize()
+            ev[i][0].record()
+            step()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        barrier()
+    launches = lib.rs_stats_kernel_launches() - launches0
+    lib.rs_timing_enable(0)
+    timings = lib.rs_timing_all()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * P / (ms_max / 1e3)
+    clocks = clk.summary()
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+        hx, hq, hlx, hlq = pin(w.prot_xyz), pin(w.prot_q), pin(w.lig_xyz), pin(w.lig_q)
+        hquat, htr, hrv = pin(w.quat), pin(w.trans), pin(rv)
+        hE = torch.empty(P, dtype=torch.float64).pin_memory()
+        hF = torch.empty(P, dtype=torch.uint8).pin_memory()
+        hEg = torch.empty(P, dtype=torch.float64).pin_memory()
+        hFg = torch.empty(P, dtype=torch.uint8).pin_memory()
+        hgt = torch.empty((P, 3), dtype=torch.float64).pin_memory()
+        hgw = torch.empty((P, 3), dtype=torch.float64).pin_memory()
+
+        def host_step():
+            h = lib.rs_build_protein(ctx.handle, hx, hq, params)
+            lib.rs_energy_poses(ctx.handle, h, hlx, hlq, hquat, htr, E_out=hE, flags_out=hF)
+            lib.rs_energy_grad_poses(ctx.handle, h, hlx, hlq, hrv, htr, E_out=hEg, dE_dt=hgt,
+                                     dE_dw=hgw, flags_out=hFg)
+            lib.rs_protein_free(h)
+
+        host_step()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            host_step()
+        torch.cuda.synchronize()
+        t_e2e = (time.perf_counter() - t0) / args.steps
+        te = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        L = w.L
+        h2d = w.N * 32 + 2 * L * 32 + P * 32 + P * 24 + P * 24 + P * 24
+        d2h = P * 8 + P + P * 8 + P * 48 + P
+        e2e = {"value": round(world * P / float(te.item()), 3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": round(1e3 * float(te.item()), 3)}
+
+    if rank == 0:
+        pk = peaks()
+        rf = roofline(timings, pk)
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            try:
+                cpu = cpu_baseline(P)
+            except Exception as e:  # report, do not hide
+                cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                       "sample": f"failed: {type(e).__name__}: {str(e)[-300:]}"}
+        top = sorted(timings.values(), key=lambda r: -r["ms"])[:8]
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 build, f32-pair evaluation", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "poses_per_gpu": P, "ligand_atoms": w.L,
+                           "protein_atoms": w.N, "n": w.n, "b": w.b, "tucker_cap": w.tucker_cap,
+                           "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                           "parallelism": f"{world} independent ranks, poses split (no collective)"},
+                "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks,
+                "kernels_ms_per_step": {r["name"]: round(r["ms"] / args.steps, 4) for r in top}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -152,6 +152,25 @@ rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
                                double* E_out, double* dE_dt, double* dE_dw,
                                uint8_t* flags_out, int mem_flags, void* stream);
 
+/* ----------------------------------------------------------- diagnostics */
+/* These have no counterpart in the paper: they support measurement.
+ * Number of kernels this library has launched in the process (all devices). */
+unsigned long long rs_stats_kernel_launches(void);
+/* Per-kernel device timing: mode 0 off, 1 the pose kernels and the heavy build
+ * kernels, 2 every kernel.  While on, each timed launch is bracketed by a CUDA
+ * event pair recorded on the stream the kernel runs on (a small overhead). */
+rs_status rs_timing_enable(int mode);
+/* Drops all recorded timings (waits for pending events first). */
+rs_status rs_timing_reset(void);
+/* Number of kernel names with recorded timings. */
+int       rs_timing_count(void);
+/* Timing record `index` (0 <= index < rs_timing_count()): kernel name (copied,
+ * NUL-terminated, at most name_len bytes), total device milliseconds, launch
+ * count, and the summed algorithmic work the launches reported (FLOPs or bytes,
+ * per kernel; see the library's design notes).  Waits for pending events. */
+rs_status rs_timing_get(int index, char* name, size_t name_len, double* total_ms,
+                        unsigned long long* launches, double* work);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "rs_common.cuh"
+#include "rs_diag.cuh"
 
 namespace rs {
 namespace {
@@ -670,11 +671,10 @@ __global__ void __launch_bounds__(512) k_skeleton(int n, int RP, const int* __re
     for (int i = threadIdx.x; i < RP; i += blockDim.x) Sidx[ax * RS_MAX_TUCKER + i] = i < r ? sel[i] : -1;
 }
 
-// Vs = V Ainv (FP32 out, the evaluation basis) and Wp = V V[S,:]^T (FP64).
+// Vs = V Ainv (the cardinal evaluation basis) and Wp = V V[S,:]^T, both FP64.
 __global__ void k_skeleton_apply(int n, int RP, const int* __restrict__ r_ax,
                                  const double* __restrict__ V, const double* __restrict__ Ainv,
-                                 const int* __restrict__ Sidx, float* __restrict__ Vs0,
-                                 float* __restrict__ Vs1, float* __restrict__ Vs2,
+                                 const int* __restrict__ Sidx, double* __restrict__ Vs,
                                  double* __restrict__ Wp) {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     int ax = blockIdx.y;
@@ -690,9 +690,52 @@ __global__ void k_skeleton_apply(int n, int RP, const int* __restrict__ r_ax,
         const double* Vsr = V + ((size_t)ax * n + srow) * RP;
         for (int k = 0; k < r; ++k) w += Vr[k] * Vsr[k];
     }
-    float* Vs = ax == 0 ? Vs0 : (ax == 1 ? Vs1 : Vs2);
-    Vs[(size_t)i * RP + c] = (float)s;
+    Vs[((size_t)ax * n + i) * RP + c] = s;
     Wp[((size_t)ax * n + i) * RP + c] = w;
+}
+
+__device__ __forceinline__ void split_pair(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+// Float-pair rows of the axis-1 and axis-2 cardinal factors and their row
+// differences: Vh + Vl = V'[i][c], VDh + VDl = V'[i+1][c] - V'[i][c].
+__global__ void k_pair_rows(int n, int RP, const double* __restrict__ Vs, float* __restrict__ out0,
+                            float* __restrict__ out1) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int ax = blockIdx.y;
+    if (idx >= (size_t)n * RP) return;
+    int i = (int)(idx / RP), c = (int)(idx % RP);
+    const double* Va = Vs + (size_t)ax * n * RP;
+    double v = Va[(size_t)i * RP + c];
+    double d = i + 1 < n ? Va[(size_t)(i + 1) * RP + c] - v : 0.0;
+    float* o = ax == 0 ? out0 : out1;
+    size_t plane = (size_t)n * RP;
+    split_pair(v, o[idx], o[plane + idx]);
+    split_pair(d, o[2 * plane + idx], o[3 * plane + idx]);
+}
+
+// W[i][a][b] = sum_c V3'[i][c] core[a][b][c] and D[i] = W[i+1] - W[i] (FP64), split
+// into float pairs: out = [Wh | Wl | Dh | Dl], each [n][RP][RP].
+__global__ void k_wtable(int n, int RP, const double* __restrict__ Vs3,
+                         const double* __restrict__ B, float* __restrict__ out) {
+    int ab = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (ab >= RP * RP) return;
+    const double* row0 = Vs3 + (size_t)i * RP;
+    const double* row1 = Vs3 + (size_t)min(i + 1, n - 1) * RP;
+    const double* bc = B + (size_t)ab * RP;
+    double w0 = 0.0, w1 = 0.0;
+    for (int c = 0; c < RP; ++c) {
+        w0 += row0[c] * bc[c];
+        w1 += row1[c] * bc[c];
+    }
+    double d = i + 1 < n ? w1 - w0 : 0.0;
+    size_t plane = (size_t)n * RP * RP;
+    size_t o = (size_t)i * RP * RP + ab;
+    split_pair(w0, out[o], out[plane + o]);
+    split_pair(d, out[2 * plane + o], out[3 * plane + o]);
 }
 
 // C'[ax][a][(m,k)] = sum_i Wp[ax][i][a] exp(-t_k^2 (x_i - x_m^ax)^2)   (FP64).
@@ -830,11 +873,21 @@ template <int RP>
 rs_status launch_project_core(cudaStream_t st, int n, double b, double h, int N, int Rl,
                               const double* xyz, const double* q, const double* tl,
                               const double* al, const double* Wp, double* Cp, double* Bp,
-                              int nchunk, int CH) {
+                              int nchunk, int CH, double proj_points) {
     dim3 gp((N + 127) / 128, Rl, 3);
-    k_project<RP><<<gp, 128, 0, st>>>(n, b, h, N, Rl, xyz, tl, Wp, Cp);
+    // FP64 flops: per active (row, atom, term): 2 (recurrence) + 2 RP (accumulate)
+    double work = proj_points * (2.0 + 2.0 * RP);
+    {
+        ::rs::KernelTimer kt__("k_project", st, work, true);
+        k_project<RP><<<gp, 128, 0, st>>>(n, b, h, N, Rl, xyz, tl, Wp, Cp);
+    }
+    // FP64 flops: per column and (a, b): 2 (xi C1 C2) + 2 RP (accumulate over c)
+    work = (double)N * Rl * RP * RP * (2.0 + 2.0 * RP);
     RS_TRY_CUDA(cudaGetLastError());
-    k_core<RP><<<nchunk, RP * RP, 0, st>>>(N * Rl, Rl, CH, q, al, Cp, Bp);
+    {
+        ::rs::KernelTimer kt__("k_core", st, work, true);
+        k_core<RP><<<nchunk, RP * RP, 0, st>>>(N * Rl, Rl, CH, q, al, Cp, Bp);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     return RS_OK;
 }
@@ -842,10 +895,10 @@ rs_status launch_project_core(cudaStream_t st, int n, double b, double h, int N,
 rs_status dispatch_project_core(int RP, cudaStream_t st, int n, double b, double h, int N, int Rl,
                                 const double* xyz, const double* q, const double* tl,
                                 const double* al, const double* Wp, double* Cp, double* Bp,
-                                int nchunk, int CH) {
+                                int nchunk, int CH, double proj_points) {
     switch (RP) {
 #define RS_CASE(R) \
-    case R: return launch_project_core<R>(st, n, b, h, N, Rl, xyz, q, tl, al, Wp, Cp, Bp, nchunk, CH);
+    case R: return launch_project_core<R>(st, n, b, h, N, Rl, xyz, q, tl, al, Wp, Cp, Bp, nchunk, CH, proj_points);
         RS_CASE(4) RS_CASE(8) RS_CASE(12) RS_CASE(16) RS_CASE(20) RS_CASE(24) RS_CASE(28) RS_CASE(32)
 #undef RS_CASE
         default:
@@ -862,7 +915,10 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
     const int N = P->N;
     double* d_bb;
     RS_TRY(S.get(&d_bb, 6));
-    k_bbox<<<1, kBlock, 0, st>>>(N, d_xyz, d_bb);
+    {
+        ::rs::KernelTimer kt__("k_bbox", st, 0.0, false);
+        k_bbox<<<1, kBlock, 0, st>>>(N, d_xyz, d_bb);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     double bb[6];
     RS_TRY_CUDA(cudaMemcpyAsync(bb, d_bb, sizeof(bb), cudaMemcpyDeviceToHost, st));
@@ -892,12 +948,24 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
     RS_TRY(device_alloc(P, (void**)&d_atoms64, (size_t)N * sizeof(D4)));
     RS_TRY_CUDA(cudaMemsetAsync(d_count, 0, ncell * sizeof(int), st));
     RS_TRY_CUDA(cudaMemsetAsync(d_cursor, 0, ncell * sizeof(int), st));
-    k_cell_count<<<blocks_for(N), kBlock, 0, st>>>(N, d_xyz, co[0], co[1], co[2], 1.0 / cell, nc[0],
-                                                   nc[1], nc[2], d_cell_of, d_count);
-    k_scan<<<1, 1024, 0, st>>>((int)ncell, d_count, d_start);
-    k_cell_fill<<<blocks_for(N), kBlock, 0, st>>>(N, d_cell_of, d_start, d_cursor, d_perm);
-    k_cell_sort<<<blocks_for(ncell), kBlock, 0, st>>>((int)ncell, d_start, d_perm, d_xyz, d_q,
-                                                      d_atoms, d_atoms64);
+    {
+        ::rs::KernelTimer kt__("k_cell_count", st, 0.0, false);
+        k_cell_count<<<blocks_for(N), kBlock, 0, st>>>(N, d_xyz, co[0], co[1], co[2], 1.0 / cell, nc[0],
+                                                       nc[1], nc[2], d_cell_of, d_count);
+    }
+    {
+        ::rs::KernelTimer kt__("k_scan", st, 0.0, false);
+        k_scan<<<1, 1024, 0, st>>>((int)ncell, d_count, d_start);
+    }
+    {
+        ::rs::KernelTimer kt__("k_cell_fill", st, 0.0, false);
+        k_cell_fill<<<blocks_for(N), kBlock, 0, st>>>(N, d_cell_of, d_start, d_cursor, d_perm);
+    }
+    {
+        ::rs::KernelTimer kt__("k_cell_sort", st, 0.0, false);
+        k_cell_sort<<<blocks_for(ncell), kBlock, 0, st>>>((int)ncell, d_start, d_perm, d_xyz, d_q,
+                                                          d_atoms, d_atoms64);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     ProteinView& v = P->view;
     v.atoms = d_atoms;
@@ -925,8 +993,12 @@ static rs_status build_canonical(rs_protein* P, cudaStream_t st, const double* d
     float* F[3];
     for (int a = 0; a < 3; ++a) RS_TRY(device_alloc(P, (void**)&F[a], (size_t)n * ld * sizeof(float)));
     dim3 g(blocks_for(ld), n);
-    k_canon_factors<<<g, kBlock, 0, st>>>(n, P->b, P->h, N, Rl, d_xyz, d_q, d_tl, d_al, (int)ld,
-                                         F[0], F[1], F[2]);
+    double work = (double)n * ld * 3 * sizeof(float);  // bytes written
+    {
+        ::rs::KernelTimer kt__("k_canon_factors", st, work, true);
+        k_canon_factors<<<g, kBlock, 0, st>>>(n, P->b, P->h, N, Rl, d_xyz, d_q, d_tl, d_al, (int)ld,
+                                             F[0], F[1], F[2]);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     ProteinView& v = P->view;
     v.kind = 0;
@@ -942,7 +1014,8 @@ static rs_status build_canonical(rs_protein* P, cudaStream_t st, const double* d
 static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xyz,
                               const double* d_q, const double* d_tl, const double* d_al,
                               const std::vector<double>& tl_host, const std::vector<double>& al_host,
-                              const std::vector<double>& q_host_abs23, int cap, double eps_r,
+                              const std::vector<double>& q_host_abs23,
+                              const std::vector<double>& xyz_host, int cap, double eps_r,
                               Scratch& S) {
     const int N = P->N, Rl = P->R_l, n = P->n;
     const double b = P->b, h = P->h;
@@ -971,14 +1044,45 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY(S.get(&d_G, (size_t)3 * n * n));
     RS_TRY(S.get(&d_tr, 3));
     long long threads = (long long)nsc * Rl * 3 * nmc;
-    k_gauss_dsum<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, b, h, N, Rl, d_xyz, d_cz,
-                                                                     d_tl, nsc, nmc, d_Dp);
+    // FP64 flops of the ratio walks: 3 per half-grid point of every chunk that
+    // lies within e^-50 of a Gaussian's peak (counted in closed form per term)
+    double work = 0.0;
+    {
+        const double delta = 0.5 * h;
+        for (int k = 0; k < Rl; ++k) {
+            double t2 = 2.0 * tl_host[k] * tl_host[k];
+            double reach = t2 > 0 ? std::sqrt(50.0 / t2) : 1e300;
+            for (size_t e = 0; e < xyz_host.size(); ++e) {
+                double lo = std::max(0.0, std::floor((xyz_host[e] - reach + b) / delta / kSC));
+                double hi = std::min((double)(nsc - 1), std::floor((xyz_host[e] + reach + b) / delta / kSC));
+                if (hi >= lo) work += (hi - lo + 1) * kSC * 3.0;
+            }
+        }
+    }
+    {
+        ::rs::KernelTimer kt__("k_gauss_dsum", st, work, true);
+        k_gauss_dsum<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, b, h, N, Rl, d_xyz, d_cz,
+                                                                         d_tl, nsc, nmc, d_Dp);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     size_t dlen = (size_t)3 * Rl * Sh;
-    k_sum_chunks<<<blocks_for(dlen), kBlock, 0, st>>>(dlen, nmc, d_Dp, d_D);
-    k_exp_table<<<dim3(blocks_for(n), Rl), kBlock, 0, st>>>(n, h, Rl, d_tl, d_E);
-    k_gram<<<dim3(blocks_for(n), n, 3), kBlock, 0, st>>>(n, Rl, d_w2, d_E, d_D, d_G);
-    k_trace<<<3, kBlock, 0, st>>>(n, d_G, d_tr);
+    {
+        ::rs::KernelTimer kt__("k_sum_chunks", st, 0.0, false);
+        k_sum_chunks<<<blocks_for(dlen), kBlock, 0, st>>>(dlen, nmc, d_Dp, d_D);
+    }
+    {
+        ::rs::KernelTimer kt__("k_exp_table", st, 0.0, false);
+        k_exp_table<<<dim3(blocks_for(n), Rl), kBlock, 0, st>>>(n, h, Rl, d_tl, d_E);
+    }
+    work = 3.0 * n * (double)n * Rl * 3.0;  // FP64 flops
+    {
+        ::rs::KernelTimer kt__("k_gram", st, work, true);
+        k_gram<<<dim3(blocks_for(n), n, 3), kBlock, 0, st>>>(n, Rl, d_w2, d_E, d_D, d_G);
+    }
+    {
+        ::rs::KernelTimer kt__("k_trace", st, 0.0, false);
+        k_trace<<<3, kBlock, 0, st>>>(n, d_G, d_tr);
+    }
     RS_TRY_CUDA(cudaGetLastError());
 
     // 2. block subspace iteration with CholQR2 and Rayleigh-Ritz
@@ -999,15 +1103,36 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY(S.get(&d_W, (size_t)3 * p * p));
     RS_TRY(S.get(&d_fail, 3));
     RS_TRY_CUDA(cudaMemsetAsync(d_fail, 0, 3 * sizeof(int), st));
-    k_init_block<<<blocks_for((size_t)3 * n * p), kBlock, 0, st>>>(n, p, d_Q);
+    {
+        ::rs::KernelTimer kt__("k_init_block", st, 0.0, false);
+        k_init_block<<<blocks_for((size_t)3 * n * p), kBlock, 0, st>>>(n, p, d_Q);
+    }
     auto orthonormalize = [&](double* Yin) -> rs_status {
         // shifted CholQR then plain CholQR: Q = Y R^{-1}
-        k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, Yin, Yin, d_Sm);
-        k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, 1e-13, d_Ri, d_fail);
-        k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, Yin, d_Ri, d_Q);
-        k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Q, d_Sm);
-        k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, 0.0, d_Ri, d_fail);
-        k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, d_Q, d_Ri, d_Y);
+        {
+            ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
+            k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, Yin, Yin, d_Sm);
+        }
+        {
+            ::rs::KernelTimer kt__("k_chol_rinv", st, 0.0, false);
+            k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, 1e-13, d_Ri, d_fail);
+        }
+        {
+            ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
+            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, Yin, d_Ri, d_Q);
+        }
+        {
+            ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
+            k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Q, d_Sm);
+        }
+        {
+            ::rs::KernelTimer kt__("k_chol_rinv", st, 0.0, false);
+            k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, 0.0, d_Ri, d_fail);
+        }
+        {
+            ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
+            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, d_Q, d_Ri, d_Y);
+        }
         RS_TRY_CUDA(cudaMemcpyAsync(d_Q, d_Y, (size_t)3 * n * p * sizeof(double),
                                     cudaMemcpyDeviceToDevice, st));
         RS_TRY_CUDA(cudaGetLastError());
@@ -1015,14 +1140,27 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     };
     RS_TRY(orthonormalize(d_Q));
     dim3 gq((n + 15) / 16, 1, 3);
+    work = 3.0 * 2.0 * n * (double)n * p;  // FP64 flops per G Q
     const int iters = 28;
     for (int it = 0; it < iters; ++it) {
-        k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y);
+        {
+            ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
+            k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y);
+        }
         RS_TRY(orthonormalize(d_Y));
     }
-    k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y);
-    k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Y, d_Sm);
-    k_jacobi<<<3, 256, 0, st>>>(p, d_Sm, d_lam, d_W);
+    {
+        ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
+        k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y);
+    }
+    {
+        ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
+        k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Y, d_Sm);
+    }
+    {
+        ::rs::KernelTimer kt__("k_jacobi", st, 0.0, false);
+        k_jacobi<<<3, 256, 0, st>>>(p, d_Sm, d_lam, d_W);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     std::vector<double> lam((size_t)3 * p), tr(3);
     int fail[3];
@@ -1063,13 +1201,22 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY(S.get(&d_Ainv, (size_t)3 * RP * RP));
     RS_TRY(S.get(&d_Wp, (size_t)3 * n * RP));
     RS_TRY(S.get(&d_S, (size_t)3 * RS_MAX_TUCKER));
-    k_ritz_vectors<<<dim3(blocks_for((size_t)n * RP), 3), kBlock, 0, st>>>(n, p, RP, d_rax, d_Q, d_W, d_V);
+    {
+        ::rs::KernelTimer kt__("k_ritz_vectors", st, 0.0, false);
+        k_ritz_vectors<<<dim3(blocks_for((size_t)n * RP), 3), kBlock, 0, st>>>(n, p, RP, d_rax, d_Q, d_W, d_V);
+    }
     // 3. skeleton basis
-    k_skeleton<<<3, 512, 0, st>>>(n, RP, d_rax, d_V, d_M, d_S, d_Ainv, d_fail);
-    float* Vs[3];
-    for (int a = 0; a < 3; ++a) RS_TRY(device_alloc(P, (void**)&Vs[a], (size_t)n * RP * sizeof(float)));
-    k_skeleton_apply<<<dim3(blocks_for((size_t)n * RP), 3), kBlock, 0, st>>>(
-        n, RP, d_rax, d_V, d_Ainv, d_S, Vs[0], Vs[1], Vs[2], d_Wp);
+    {
+        ::rs::KernelTimer kt__("k_skeleton", st, 0.0, false);
+        k_skeleton<<<3, 512, 0, st>>>(n, RP, d_rax, d_V, d_M, d_S, d_Ainv, d_fail);
+    }
+    double* d_Vs;
+    RS_TRY(S.get(&d_Vs, (size_t)3 * n * RP));
+    {
+        ::rs::KernelTimer kt__("k_skeleton_apply", st, 0.0, false);
+        k_skeleton_apply<<<dim3(blocks_for((size_t)n * RP), 3), kBlock, 0, st>>>(
+            n, RP, d_rax, d_V, d_Ainv, d_S, d_Vs, d_Wp);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     // 4. projections and core
     const int Rtot = N * Rl;
@@ -1079,13 +1226,29 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY(S.get(&d_Cp, (size_t)3 * RP * Rtot));
     RS_TRY(S.get(&d_Bp, (size_t)nchunk * RP * RP * RP));
     RS_TRY(S.get(&d_B, (size_t)RP * RP * RP));
+    double proj_points = 0.0;
+    for (int k = 0; k < Rl; ++k) {
+        double t2 = tl_host[k] * tl_host[k];
+        double hw = t2 > 0 ? std::sqrt(700.0 / t2) : 1e300;
+        for (size_t e = 0; e < xyz_host.size(); ++e) {
+            double lo = std::max(0.0, std::ceil((xyz_host[e] - hw + b) / h));
+            double hi = std::min((double)(n - 1), std::floor((xyz_host[e] + hw + b) / h));
+            if (hi >= lo) proj_points += hi - lo + 1;
+        }
+    }
     RS_TRY(dispatch_project_core(RP, st, n, b, h, N, Rl, d_xyz, d_q, d_tl, d_al, d_Wp, d_Cp, d_Bp,
-                                 nchunk, CH));
+                                 nchunk, CH, proj_points));
     size_t blen = (size_t)RP * RP * RP;
-    k_sum_chunks<<<blocks_for(blen), kBlock, 0, st>>>(blen, nchunk, d_Bp, d_B);
+    {
+        ::rs::KernelTimer kt__("k_sum_chunks", st, 0.0, false);
+        k_sum_chunks<<<blocks_for(blen), kBlock, 0, st>>>(blen, nchunk, d_Bp, d_B);
+    }
     float* core;
     RS_TRY(device_alloc(P, (void**)&core, blen * sizeof(float)));
-    k_to_float<<<blocks_for(blen), kBlock, 0, st>>>(blen, d_B, core);
+    {
+        ::rs::KernelTimer kt__("k_to_float", st, 0.0, false);
+        k_to_float<<<blocks_for(blen), kBlock, 0, st>>>(blen, d_B, core);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     RS_TRY_CUDA(cudaMemcpyAsync(fail, d_fail, sizeof(fail), cudaMemcpyDeviceToHost, st));
     RS_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1093,11 +1256,32 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         set_error("skeleton selection failed (rank-deficient factor basis)");
         return RS_ERR_CUDA;
     }
+    // 5. evaluation tables: float-pair rows of V1', V2' and of W = V3' core_(3)^T
+    float *vt0, *vt1, *wt;
+    size_t vplane = (size_t)n * RP, wplane = (size_t)n * RP * RP;
+    RS_TRY(device_alloc(P, (void**)&vt0, 4 * vplane * sizeof(float)));
+    RS_TRY(device_alloc(P, (void**)&vt1, 4 * vplane * sizeof(float)));
+    RS_TRY(device_alloc(P, (void**)&wt, 4 * wplane * sizeof(float)));
+    {
+        ::rs::KernelTimer kt__("k_pair_rows", st, 0.0, false);
+        k_pair_rows<<<dim3(blocks_for(vplane), 2), kBlock, 0, st>>>(n, RP, d_Vs, vt0, vt1);
+    }
+    {
+        ::rs::KernelTimer kt__("k_wtable", st, 0.0, false);
+        k_wtable<<<dim3(blocks_for((size_t)RP * RP), n), kBlock, 0, st>>>(n, RP, d_Vs + 2 * vplane, d_B, wt);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
+    RS_TRY_CUDA(cudaStreamSynchronize(st));
     ProteinView& v = P->view;
     v.kind = 1;
     v.ld = RP;
     v.R = RP;
-    for (int a = 0; a < 3; ++a) v.F[a] = Vs[a];
+    for (int a = 0; a < 3; ++a) v.F[a] = nullptr;
+    for (int k = 0; k < 4; ++k) {
+        v.Wt[k] = wt + k * wplane;
+        v.Vt[0][k] = vt0 + k * vplane;
+        v.Vt[1][k] = vt1 + k * vplane;
+    }
     v.core = core;
     P->kind = 1;
     return RS_OK;
@@ -1182,7 +1366,12 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
     } else {
         std::vector<double> cz(N);
         for (int i = 0; i < N; ++i) cz[i] = std::pow(std::fabs(hq[i]), 2.0 / 3.0);
-        s = build_tucker(P, st, d_xyz, d_q, d_tl, d_al, tl, al, cz, prm->tucker_cap,
+        std::vector<double> hxyz((size_t)3 * N);
+        if (cudaMemcpy(hxyz.data(), d_xyz, hxyz.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            set_error("rs_build_protein: coordinate copy failed");
+            return fail_out(RS_ERR_CUDA);
+        }
+        s = build_tucker(P, st, d_xyz, d_q, d_tl, d_al, tl, al, cz, hxyz, prm->tucker_cap,
                          prm->eps_r > 0 ? prm->eps_r : 0.0, S);
     }
     if (s != RS_OK) return fail_out(s);

@@ -59,11 +59,16 @@ struct __align__(32) D4 {
 struct ProteinView {
     int n;
     double b, h, inv_h;
-    int kind;            // 0: canonical factors, 1: Tucker (skeleton basis)
+    int kind;            // 0: canonical factors, 1: Tucker (skeleton basis, W form)
     int ld;              // floats per factor row
     int R;               // canonical: padded rank (multiple of 128); Tucker: padded rank RP
-    const float* F[3];   // factor rows [n][ld]; canonical axis 3 carries the weights xi
-    const float* core;   // Tucker core [RP][RP][RP]
+    const float* F[3];   // canonical: factor rows [n][ld]; axis 3 carries the weights xi
+    // Tucker, evaluated through W[i][a][b] = sum_c V3'[i][c] core[a][b][c] (an exact
+    // rewrite of the Tucker form) and the row differences D[i] = W[i+1] - W[i],
+    // each stored as a float pair hi + lo:
+    const float* Wt[4];      // Wh, Wl, Dh, Dl   [n][RP][RP]
+    const float* Vt[2][4];   // axes 1, 2: Vh, Vl, VDh, VDl  [n][RP]
+    const float* core;   // Tucker core [RP][RP][RP] (FP32, diagnostics)
     int Ks;              // short-range terms
     float ts2[RS_MAX_SHORT];
     float as[RS_MAX_SHORT];
@@ -127,6 +132,38 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = a + b;
     float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
+}
+
+// Unevaluated float pair hi + lo (about 48 significant bits).
+struct F2 {
+    float h, l;
+};
+
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+
+// Pair value a + f*d with a, d pairs and f a float in [0, 1].
+__device__ __forceinline__ F2 df_lerp(F2 a, F2 d, float f) {
+    float p = f * d.h;
+    float ep = fmaf(f, d.h, -p);
+    float s, e;
+    two_sum(a.h, p, s, e);
+    float lo = e + ep + fmaf(f, d.l, a.l);
+    return fast_two_sum(s, lo);
+}
+
+// acc += x * y for pairs x, y, in the manner of the compensated dot product
+// Dot2 (Ogita, Rump, Oishi 2005): the rounding errors of the leading product and
+// sum are carried in acc.l (the lo*lo term is dropped).
+__device__ __forceinline__ void df_fma_acc(F2& acc, F2 x, F2 y) {
+    float p = x.h * y.h;
+    float ep = fmaf(x.h, y.h, -p);
+    float s, e;
+    two_sum(acc.h, p, s, e);
+    acc.h = s;
+    acc.l += e + ep + fmaf(x.h, y.l, x.l * y.h);
 }
 
 // Accumulator of float values carried as an unevaluated pair hi + lo.

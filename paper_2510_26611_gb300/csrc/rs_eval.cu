@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "rs_common.cuh"
+#include "rs_diag.cuh"
 #include "rs_eval.cuh"
 
 namespace rs {
@@ -152,43 +153,46 @@ __device__ void reduce_poses(const ProteinView& P, int PB, int L, long long p0, 
 }
 
 // ------------------------------------------------------------------ Tucker path
-// Thread per atom.  Core [RP][RP][RP] in shared memory; per-thread factor
-// vectors v_l = lerp of two rows of the skeleton-basis factor V'^(l).
+// Thread per atom.  The Tucker form phi = sum_abc core[a][b][c] v1_a v2_b v3_c is
+// evaluated through its exact rewrite W[i][a][b] = sum_c V3'[i][c] core[a][b][c]:
+//   t_ab = W[i3][a][b] + f3 D[i3][a][b]            (interpolation along axis 3)
+//   phi  = sum_a v1_a sum_b v2_b t_ab               (v_l = lerp of V'^(l) rows)
+// with every factor stored as a float pair and sums carried as pairs (Dot2), so the
+// per-atom value keeps ~2^-44 relative accuracy even where the terms cancel.
 template <int RP, bool GRAD>
-__global__ void __launch_bounds__(128) k_eval_tucker(ProteinView P, LigandView lig,
-                                                     const double* __restrict__ rot,
-                                                     const double* __restrict__ trans,
-                                                     long long Ptot, int PB,
-                                                     double* __restrict__ E,
-                                                     uint8_t* __restrict__ flags,
-                                                     double* __restrict__ gt,
-                                                     double* __restrict__ gw) {
+__global__ void __launch_bounds__(128) k_eval_wform(ProteinView P, LigandView lig,
+                                                    const double* __restrict__ rot,
+                                                    const double* __restrict__ trans,
+                                                    long long Ptot, int PB,
+                                                    double* __restrict__ E,
+                                                    uint8_t* __restrict__ flags,
+                                                    double* __restrict__ gt,
+                                                    double* __restrict__ gw) {
+    using dev::F2;
     constexpr int NC = GRAD ? 7 : 1;
     constexpr int NT = 128;
+    constexpr int NV = GRAD ? 4 : 2;  // per-thread smem planes: v1h, v1l (, dv1h, dv1l)
     extern __shared__ __align__(16) unsigned char smem[];
-    float* core = (float*)smem;
-    float* v1s = core + RP * RP * RP;                       // [RP][NT]
-    float* dv1s = v1s + RP * NT;                            // [RP][NT] (GRAD)
-    PoseSetup* ps = (PoseSetup*)(dv1s + (GRAD ? RP * NT : 0));
+    float* v1s = (float*)smem;                                   // [NV][RP][NT]
+    PoseSetup* ps = (PoseSetup*)(v1s + NV * RP * NT);
     double* contrib = (double*)(ps + PB);
     int* pflag = (int*)(contrib + (size_t)PB * lig.L * NC);
 
-    for (int e = threadIdx.x; e < RP * RP * RP / 4; e += NT)
-        ((float4*)core)[e] = ((const float4*)P.core)[e];
     const int L = lig.L;
     const long long nblocks = (Ptot + PB - 1) / PB;
     const float inv_h = (float)P.inv_h;
+    const int tid = threadIdx.x;
     for (long long pb = blockIdx.x; pb < nblocks; pb += gridDim.x) {
         long long p0 = pb * PB;
         __syncthreads();
-        for (int pl = threadIdx.x; pl < PB; pl += blockDim.x) {
+        for (int pl = tid; pl < PB; pl += blockDim.x) {
             long long p = p0 + pl;
             pflag[pl] = 0;
             if (p < Ptot) setup_pose(P, rot, trans, p, GRAD, ps[pl]);
             else ps[pl].valid = 0;
         }
         __syncthreads();
-        for (int g = threadIdx.x; g < PB * L; g += NT) {
+        for (int g = tid; g < PB * L; g += NT) {
             int pl = g / L, j = g - pl * L;
             double* cj = contrib + (size_t)g * NC;
             const PoseSetup& q = ps[pl];
@@ -205,113 +209,115 @@ __global__ void __launch_bounds__(128) k_eval_tucker(ProteinView P, LigandView l
             float cf[3];
             bool ins[3];
             for (int a = 0; a < 3; ++a) dev::axis_cell(q.s[a], ry[a] * inv_h, P.n, ci[a], cf[a], ins[a]);
-            // factor vectors
-            float v2[RP], v3[RP], dv2[GRAD ? RP : 1], dv3[GRAD ? RP : 1];
+            // v1 (axis 1) into this thread's shared-memory column; v2 (axis 2) in registers
             {
-                const float4* r0 = (const float4*)(P.F[0] + (size_t)ci[0] * RP);
-                const float4* r1 = (const float4*)(P.F[0] + (size_t)(ci[0] + 1) * RP);
+                size_t o = (size_t)ci[0] * RP;
+                const float4* vh = (const float4*)(P.Vt[0][0] + o);
+                const float4* vl = (const float4*)(P.Vt[0][1] + o);
+                const float4* dh = (const float4*)(P.Vt[0][2] + o);
+                const float4* dl = (const float4*)(P.Vt[0][3] + o);
 #pragma unroll
                 for (int c4 = 0; c4 < RP / 4; ++c4) {
-                    float4 a = __ldg(r0 + c4), b = __ldg(r1 + c4);
+                    float4 a = __ldg(vh + c4), b = __ldg(vl + c4), c = __ldg(dh + c4), d = __ldg(dl + c4);
                     float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                    float cv[4] = {c.x, c.y, c.z, c.w}, dv[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        v1s[(4 * c4 + u) * NT + threadIdx.x] = fmaf(cf[0], bv[u] - av[u], av[u]);
-                        if constexpr (GRAD) dv1s[(4 * c4 + u) * NT + threadIdx.x] = ins[0] ? bv[u] - av[u] : 0.f;
-                    }
-                }
-            }
-            {
-                const float4* r0 = (const float4*)(P.F[1] + (size_t)ci[1] * RP);
-                const float4* r1 = (const float4*)(P.F[1] + (size_t)(ci[1] + 1) * RP);
-#pragma unroll
-                for (int c4 = 0; c4 < RP / 4; ++c4) {
-                    float4 a = __ldg(r0 + c4), b = __ldg(r1 + c4);
-                    float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        v2[4 * c4 + u] = fmaf(cf[1], bv[u] - av[u], av[u]);
-                        if constexpr (GRAD) dv2[4 * c4 + u] = ins[1] ? bv[u] - av[u] : 0.f;
-                    }
-                }
-            }
-            {
-                const float4* r0 = (const float4*)(P.F[2] + (size_t)ci[2] * RP);
-                const float4* r1 = (const float4*)(P.F[2] + (size_t)(ci[2] + 1) * RP);
-#pragma unroll
-                for (int c4 = 0; c4 < RP / 4; ++c4) {
-                    float4 a = __ldg(r0 + c4), b = __ldg(r1 + c4);
-                    float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        v3[4 * c4 + u] = fmaf(cf[2], bv[u] - av[u], av[u]);
-                        if constexpr (GRAD) dv3[4 * c4 + u] = ins[2] ? bv[u] - av[u] : 0.f;
-                    }
-                }
-            }
-            // phi = sum_a v1_a sum_b v2_b sum_c core[a][b][c] v3_c
-            FAcc acc, acc1, acc2, acc3;
-            for (int a = 0; a < RP; ++a) {
-                float ia = 0.f, ia2 = 0.f, ia3 = 0.f;
-#pragma unroll
-                for (int bb = 0; bb < RP; ++bb) {
-                    const float4* row = (const float4*)(core + (a * RP + bb) * RP);
-                    float t = 0.f, t3 = 0.f;
-#pragma unroll
-                    for (int c4 = 0; c4 < RP / 4; ++c4) {
-                        float4 w = row[c4];
-                        t = fmaf(w.x, v3[4 * c4], t);
-                        t = fmaf(w.y, v3[4 * c4 + 1], t);
-                        t = fmaf(w.z, v3[4 * c4 + 2], t);
-                        t = fmaf(w.w, v3[4 * c4 + 3], t);
+                        F2 v = dev::df_lerp(F2{av[u], bv[u]}, F2{cv[u], dv[u]}, cf[0]);
+                        int col = 4 * c4 + u;
+                        v1s[(0 * RP + col) * NT + tid] = v.h;
+                        v1s[(1 * RP + col) * NT + tid] = v.l;
                         if constexpr (GRAD) {
-                            t3 = fmaf(w.x, dv3[4 * c4], t3);
-                            t3 = fmaf(w.y, dv3[4 * c4 + 1], t3);
-                            t3 = fmaf(w.z, dv3[4 * c4 + 2], t3);
-                            t3 = fmaf(w.w, dv3[4 * c4 + 3], t3);
+                            v1s[(2 * RP + col) * NT + tid] = ins[0] ? cv[u] : 0.f;
+                            v1s[(3 * RP + col) * NT + tid] = ins[0] ? dv[u] : 0.f;
                         }
                     }
-                    ia = fmaf(v2[bb], t, ia);
-                    if constexpr (GRAD) {
-                        ia2 = fmaf(dv2[bb], t, ia2);
-                        ia3 = fmaf(v2[bb], t3, ia3);
-                    }
-                }
-                float va = v1s[a * NT + threadIdx.x];
-                acc.add(va * ia);
-                if constexpr (GRAD) {
-                    float dva = dv1s[a * NT + threadIdx.x];
-                    acc1.add(dva * ia);
-                    acc2.add(va * ia2);
-                    acc3.add(va * ia3);
                 }
             }
-            double phi = acc.value();
+            F2 v2[RP];
+            F2 dv2[GRAD ? RP : 1];
+            {
+                size_t o = (size_t)ci[1] * RP;
+                const float4* vh = (const float4*)(P.Vt[1][0] + o);
+                const float4* vl = (const float4*)(P.Vt[1][1] + o);
+                const float4* dh = (const float4*)(P.Vt[1][2] + o);
+                const float4* dl = (const float4*)(P.Vt[1][3] + o);
+#pragma unroll
+                for (int c4 = 0; c4 < RP / 4; ++c4) {
+                    float4 a = __ldg(vh + c4), b = __ldg(vl + c4), c = __ldg(dh + c4), d = __ldg(dl + c4);
+                    float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                    float cv[4] = {c.x, c.y, c.z, c.w}, dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        v2[4 * c4 + u] = dev::df_lerp(F2{av[u], bv[u]}, F2{cv[u], dv[u]}, cf[1]);
+                        if constexpr (GRAD) dv2[4 * c4 + u] = ins[1] ? F2{cv[u], dv[u]} : F2{0.f, 0.f};
+                    }
+                }
+            }
+            const size_t wrow = (size_t)ci[2] * RP * RP;
+            const float* Wh = P.Wt[0] + wrow;
+            const float* Wl = P.Wt[1] + wrow;
+            const float* Dh = P.Wt[2] + wrow;
+            const float* Dl = P.Wt[3] + wrow;
+            const float f3 = cf[2];
+            const bool in3 = ins[2];
+            F2 phi{0.f, 0.f}, g1{0.f, 0.f}, g2{0.f, 0.f}, g3{0.f, 0.f};
+            for (int a = 0; a < RP; ++a) {
+                F2 u{0.f, 0.f}, u2{0.f, 0.f}, u3{0.f, 0.f};
+                const float4* wh = (const float4*)(Wh + a * RP);
+                const float4* wl = (const float4*)(Wl + a * RP);
+                const float4* dh = (const float4*)(Dh + a * RP);
+                const float4* dl = (const float4*)(Dl + a * RP);
+#pragma unroll
+                for (int b4 = 0; b4 < RP / 4; ++b4) {
+                    float4 xa = __ldg(wh + b4), xb = __ldg(wl + b4), xc = __ldg(dh + b4), xd = __ldg(dl + b4);
+                    float av[4] = {xa.x, xa.y, xa.z, xa.w}, bv[4] = {xb.x, xb.y, xb.z, xb.w};
+                    float cv[4] = {xc.x, xc.y, xc.z, xc.w}, dv[4] = {xd.x, xd.y, xd.z, xd.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        F2 t = dev::df_lerp(F2{av[k], bv[k]}, F2{cv[k], dv[k]}, f3);
+                        dev::df_fma_acc(u, v2[4 * b4 + k], t);
+                        if constexpr (GRAD) {
+                            dev::df_fma_acc(u2, dv2[4 * b4 + k], t);
+                            if (in3) dev::df_fma_acc(u3, v2[4 * b4 + k], F2{cv[k], dv[k]});
+                        }
+                    }
+                }
+                F2 va{v1s[(0 * RP + a) * NT + tid], v1s[(1 * RP + a) * NT + tid]};
+                dev::df_fma_acc(phi, va, u);
+                if constexpr (GRAD) {
+                    F2 dva{v1s[(2 * RP + a) * NT + tid], v1s[(3 * RP + a) * NT + tid]};
+                    dev::df_fma_acc(g1, dva, u);
+                    dev::df_fma_acc(g2, va, u2);
+                    dev::df_fma_acc(g3, va, u3);
+                }
+            }
+            double ph = (double)phi.h + (double)phi.l;
             double gl[3] = {0.0, 0.0, 0.0};
             if constexpr (GRAD) {
-                gl[0] = acc1.value() * P.inv_h;
-                gl[1] = acc2.value() * P.inv_h;
-                gl[2] = acc3.value() * P.inv_h;
+                gl[0] = ((double)g1.h + (double)g1.l) * P.inv_h;
+                gl[1] = ((double)g2.h + (double)g2.l) * P.inv_h;
+                gl[2] = ((double)g3.h + (double)g3.l) * P.inv_h;
             }
             // short range and vdW
             float xf[3];
             for (int a = 0; a < 3; ++a) xf[a] = (float)(q.t[a] + (double)ry[a]);
             int clash = 0;
-            short_vdw<GRAD>(P, xf, q, lig.y64 + 3 * j, 0, 1, phi, gl, clash);
+            short_vdw<GRAD>(P, xf, q, lig.y64 + 3 * j, 0, 1, ph, gl, clash);
             int fl = clash ? RS_FLAG_CLASH : 0;
             if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
             if (fl) atomicOr(&pflag[pl], fl);
             double qj = lig.q64[j];
-            cj[0] = qj * phi;
+            cj[0] = qj * ph;
             if constexpr (GRAD) {
-                double g0 = qj * gl[0], g1 = qj * gl[1], g2 = qj * gl[2];
+                double g0 = qj * gl[0], g1d = qj * gl[1], g2d = qj * gl[2];
                 cj[1] = g0;
-                cj[2] = g1;
-                cj[3] = g2;
+                cj[2] = g1d;
+                cj[3] = g2d;
                 double r0 = ry[0], r1 = ry[1], r2 = ry[2];
-                cj[4] = r1 * g2 - r2 * g1;
-                cj[5] = r2 * g0 - r0 * g2;
-                cj[6] = r0 * g1 - r1 * g0;
+                cj[4] = r1 * g2d - r2 * g1d;
+                cj[5] = r2 * g0 - r0 * g2d;
+                cj[6] = r0 * g1d - r1 * g0;
             }
         }
         __syncthreads();
@@ -471,12 +477,20 @@ __global__ void k_prep_ligand(int L, const double* __restrict__ xyz, const doubl
 }
 
 template <int RP, bool GRAD>
-size_t tucker_smem(int PB, int L) {
-    size_t s = (size_t)RP * RP * RP * 4 + (size_t)RP * 128 * 4 * (GRAD ? 2 : 1);
+size_t wform_smem(int PB, int L) {
+    size_t s = (size_t)(GRAD ? 4 : 2) * RP * 128 * 4;
     s += (size_t)PB * sizeof(PoseSetup);
     s += (size_t)PB * L * (GRAD ? 7 : 1) * 8;
     s += (size_t)PB * 4;
     return (s + 15) / 16 * 16;
+}
+
+// FP32 operations per atom of the W-form evaluation: per (a, b) a pair lerp (13)
+// and one (energy) or three (gradient) Dot2 steps (11 each); per a one or four
+// Dot2 steps; two pair lerps per factor column; ~60 for pose transform and cells.
+inline double wform_flops_per_atom(int RP, bool grad) {
+    double ab = (double)RP * RP, a = RP;
+    return grad ? ab * (13 + 3 * 11) + a * 4 * 11 + 2 * a * 13 + 60 : ab * (13 + 11) + a * 11 + 2 * a * 13 + 60;
 }
 
 template <bool GRAD>
@@ -500,16 +514,17 @@ int num_sms() {
 template <int RP, bool GRAD>
 rs_status launch_tucker(const EvalLaunch& a, cudaStream_t st) {
     int PB = a.PB > 0 ? a.PB : std::min(128, std::max(1, 512 / a.lig.L));
-    size_t sm = tucker_smem<RP, GRAD>(PB, a.lig.L);
+    size_t sm = wform_smem<RP, GRAD>(PB, a.lig.L);
     while (sm > 160 * 1024 && PB > 1) {
         PB = std::max(1, PB / 2);
-        sm = tucker_smem<RP, GRAD>(PB, a.lig.L);
+        sm = wform_smem<RP, GRAD>(PB, a.lig.L);
     }
     if (sm > 220 * 1024) {
         set_error("ligand too large for the pose kernel (L=%d)", a.lig.L);
         return RS_ERR_UNSUPPORTED;
     }
-    auto kern = k_eval_tucker<RP, GRAD>;
+    auto kern = k_eval_wform<RP, GRAD>;
+    const char* kname = GRAD ? "k_eval_wform_grad" : "k_eval_wform";
     RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0;
     RS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, sm));
@@ -517,8 +532,12 @@ rs_status launch_tucker(const EvalLaunch& a, cudaStream_t st) {
     long long grid = std::min<long long>(nblocks, (long long)std::max(per_sm, 1) * num_sms());
     if (a.grid > 0) grid = std::min<long long>(nblocks, a.grid);
     if (grid < 1) return RS_OK;
-    kern<<<(unsigned)grid, 128, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
-                                          a.gt, a.gw);
+    double work = (double)a.P * a.lig.L * wform_flops_per_atom(RP, GRAD);
+    {
+        ::rs::KernelTimer kt__(kname, st, work, true);
+        kern<<<(unsigned)grid, 128, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
+                                              a.gt, a.gw);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     return RS_OK;
 }
@@ -536,6 +555,10 @@ rs_status launch_canon(const EvalLaunch& a, cudaStream_t st) {
         return RS_ERR_UNSUPPORTED;
     }
     auto kern = k_eval_canon<GRAD>;
+    const char* kname = GRAD ? "k_eval_canon_grad" : "k_eval_canon";
+    // FP32 operations per (atom, rank term): 3 differences, 3 lerp FMAs, 2 products,
+    // 1 accumulate (energy); the gradient adds 5 products/accumulates
+    double work = (double)a.P * a.lig.L * (double)a.prot.R * (GRAD ? 14.0 : 9.0);
     RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0;
     RS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, sm));
@@ -543,8 +566,11 @@ rs_status launch_canon(const EvalLaunch& a, cudaStream_t st) {
     long long grid = std::min<long long>(nblocks, (long long)std::max(per_sm, 1) * num_sms());
     if (a.grid > 0) grid = std::min<long long>(nblocks, a.grid);
     if (grid < 1) return RS_OK;
-    kern<<<(unsigned)grid, 256, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
-                                          a.gt, a.gw);
+    {
+        ::rs::KernelTimer kt__(kname, st, work, true);
+        kern<<<(unsigned)grid, 256, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
+                                              a.gt, a.gw);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     return RS_OK;
 }
@@ -553,7 +579,10 @@ rs_status launch_canon(const EvalLaunch& a, cudaStream_t st) {
 
 rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, double* y64,
                              double* q64, cudaStream_t st) {
-    k_prep_ligand<<<1, 256, 0, st>>>(L, xyz, q, y, y64, q64);
+    {
+        ::rs::KernelTimer kt__("k_prep_ligand", st, 0.0, false);
+        k_prep_ligand<<<1, 256, 0, st>>>(L, xyz, q, y, y64, q64);
+    }
     RS_TRY_CUDA(cudaGetLastError());
     return RS_OK;
 }

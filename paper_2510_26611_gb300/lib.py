@@ -70,6 +70,12 @@ def _load() -> C.CDLL:
         "rs_protein_get_table": (st, [vp, vp, vp, vp]),
         "rs_energy_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
         "rs_energy_grad_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
+        "rs_stats_kernel_launches": (C.c_ulonglong, []),
+        "rs_timing_enable": (st, [C.c_int]),
+        "rs_timing_reset": (st, []),
+        "rs_timing_count": (C.c_int, []),
+        "rs_timing_get": (st, [C.c_int, C.c_char_p, C.c_size_t, C.POINTER(C.c_double),
+                               C.POINTER(C.c_ulonglong), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -245,6 +251,38 @@ def rs_energy_grad_poses(ctx, prot, lig_xyz, lig_q, rotvec, trans, E_out=None, d
     returns (E, dE_dt, dE_dw, flags)."""
     return _pose_call(True, ctx, prot, lig_xyz, lig_q, rotvec, trans, E_out, flags_out, dE_dt,
                       dE_dw, stream)
+
+
+def rs_stats_kernel_launches() -> int:
+    return int(_lib.rs_stats_kernel_launches())
+
+
+def rs_timing_enable(mode: int = 1) -> None:
+    _check(_lib.rs_timing_enable(mode))
+
+
+def rs_timing_reset() -> None:
+    _check(_lib.rs_timing_reset())
+
+
+def rs_timing_count() -> int:
+    return int(_lib.rs_timing_count())
+
+
+def rs_timing_get(index: int) -> dict:
+    buf = C.create_string_buffer(128)
+    ms, n, work = C.c_double(), C.c_ulonglong(), C.c_double()
+    _check(_lib.rs_timing_get(index, buf, 128, C.byref(ms), C.byref(n), C.byref(work)))
+    return {"name": buf.value.decode(), "ms": ms.value, "launches": int(n.value), "work": work.value}
+
+
+def rs_timing_all() -> dict:
+    """All timing records keyed by kernel name."""
+    out = {}
+    for i in range(rs_timing_count()):
+        r = rs_timing_get(i)
+        out[r["name"]] = r
+    return out
 
 
 # ------------------------------------------------------------------ handle owners
