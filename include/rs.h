@@ -29,8 +29,9 @@
  *     copies in, computes and copies out, and returns when results are in the
  *     output buffers) or RS_MEM_DEVICE (all array pointers are device memory on
  *     the context's GPU; the work is enqueued on `stream` and the call returns
- *     after enqueue).  `stream` is a cudaStream_t passed as void* (NULL = the
- *     context's own stream).
+ *     after enqueue).  `stream` is a cudaStream_t passed as void*, used exactly
+ *     as given: NULL is the CUDA default stream.  Work of one call is ordered
+ *     after earlier work on that stream.
  *   - Errors: every call returns an rs_status; on failure nothing is written to
  *     the outputs that is meant to be used and rs_last_error() gives a message
  *     (thread-local).  No exception crosses the ABI.  No call aborts.
@@ -109,8 +110,8 @@ const char* rs_version(void);
  *   N     : number of protein atoms, 1 <= N <= 2^22
  *   xyz   : [N][3] float64 positions (Angstrom); q: [N] float64 charges (e)
  *   params: see rs_params
- *   mem_flags/stream: where xyz and q live; the build itself always runs on the
- *           context's GPU and the call returns when the handle is ready.
+ *   mem_flags/stream: where xyz and q live; the build runs on `stream` (after
+ *           earlier work on it) and the call returns when the handle is ready.
  * On success *out owns the device-resident factors, the sinc table and a
  * cell list of the atoms; free it with rs_protein_free. */
 rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz, const double* q,

@@ -24,23 +24,41 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// A set of temporary device buffers freed when the build returns.
+// Temporary device buffers of one build.  They are carved from the context's
+// workspace (a grow-only device buffer); what does not fit is allocated and freed
+// at the end, and the workspace is grown to the high-water mark for the next build.
 struct Scratch {
-    std::vector<void*> bufs;
+    rs_ctx* ctx = nullptr;
+    size_t used = 0;
+    std::vector<void*> extra;
+    explicit Scratch(rs_ctx* c) : ctx(c) {}
     ~Scratch() {
-        for (void* p : bufs) cudaFree(p);
+        for (void* p : extra) cudaFree(p);
+        if (ctx && used > ctx->ws_bytes) {
+            if (ctx->ws_buf) cudaFree(ctx->ws_buf);
+            ctx->ws_buf = nullptr;
+            ctx->ws_bytes = 0;
+            if (cudaMalloc(&ctx->ws_buf, used) == cudaSuccess) ctx->ws_bytes = used;
+            else cudaGetLastError();
+        }
     }
     template <class T>
     rs_status get(T** p, size_t count) {
-        void* v = nullptr;
-        size_t bytes = count * sizeof(T);
+        size_t bytes = (count * sizeof(T) + 255) / 256 * 256;
         if (bytes == 0) bytes = 256;
+        size_t off = used;
+        used += bytes;
+        if (ctx && ctx->ws_buf && used <= ctx->ws_bytes) {
+            *p = (T*)((char*)ctx->ws_buf + off);
+            return RS_OK;
+        }
+        void* v = nullptr;
         if (cudaMalloc(&v, bytes) != cudaSuccess) {
             cudaGetLastError();
             set_error("build scratch: cudaMalloc of %zu bytes failed", bytes);
             return RS_ERR_OOM;
         }
-        bufs.push_back(v);
+        extra.push_back(v);
         *p = (T*)v;
         return RS_OK;
     }
@@ -348,6 +366,75 @@ __global__ void __launch_bounds__(256) k_gemm_gq(int n, int p, const double* __r
             int c = cg + 16 * u;
             if (c < p) Y[((size_t)ax * n + gi) * p + c] = acc[u];
         }
+}
+
+// Y[ax] = G[ax] Q[ax] as k_gemm_gq, and the CTA's partial Gram of its 16 rows,
+// Sp[ax][blk] = Y_blk^T Y_blk (p x p), so CholQR needs no separate pass over Y.
+__global__ void __launch_bounds__(256) k_gemm_gq_gram(int n, int p, const double* __restrict__ G,
+                                                       const double* __restrict__ Q,
+                                                       double* __restrict__ Y,
+                                                       double* __restrict__ Sp) {
+    __shared__ double Gs[16][33];
+    __shared__ double Qs[32][48];
+    __shared__ double Ys[16][49];
+    int ax = blockIdx.z;
+    int i0 = blockIdx.x * 16;
+    int r = threadIdx.x / 16, cg = threadIdx.x % 16;
+    const double* Ga = G + (size_t)ax * n * n;
+    const double* Qa = Q + (size_t)ax * n * p;
+    double acc[3] = {0, 0, 0};
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+            int rr = e / 32, kk = e % 32;
+            int gi = i0 + rr, gk = k0 + kk;
+            Gs[rr][kk] = (gi < n && gk < n) ? Ga[(size_t)gi * n + gk] : 0.0;
+        }
+        for (int e = threadIdx.x; e < 32 * p; e += 256) {
+            int kk = e / p, c = e % p;
+            int gk = k0 + kk;
+            Qs[kk][c] = gk < n ? Qa[(size_t)gk * p + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 32; ++kk) {
+            double g = Gs[r][kk];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                int c = cg + 16 * u;
+                if (c < p) acc[u] += g * Qs[kk][c];
+            }
+        }
+        __syncthreads();
+    }
+    int gi = i0 + r;
+    for (int u = 0; u < 3; ++u) {
+        int c = cg + 16 * u;
+        if (c < p) {
+            double v = gi < n ? acc[u] : 0.0;
+            Ys[r][c] = v;
+            if (gi < n) Y[((size_t)ax * n + gi) * p + c] = v;
+        }
+    }
+    __syncthreads();
+    double* out = Sp + ((size_t)ax * gridDim.x + blockIdx.x) * p * p;
+    for (int e = threadIdx.x; e < p * p; e += 256) {
+        int a = e / p, c = e % p;
+        double s = 0.0;
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) s += Ys[rr][a] * Ys[rr][c];
+        out[e] = s;
+    }
+}
+
+// S[ax] = sum over blocks of Sp[ax][blk] in a fixed order.
+__global__ void k_sum_gram(int nblk, int p, const double* __restrict__ Sp, double* __restrict__ S) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int ax = blockIdx.y;
+    if (e >= p * p) return;
+    const double* src = Sp + (size_t)ax * nblk * p * p + e;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += src[(size_t)b * p * p];
+    S[(size_t)ax * p * p + e] = s;
 }
 
 // S[ax] = A[ax]^T B[ax] (p x p), A and B n x p.  CTA per (row a, axis).
@@ -1044,25 +1131,27 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY(S.get(&d_G, (size_t)3 * n * n));
     RS_TRY(S.get(&d_tr, 3));
     long long threads = (long long)nsc * Rl * 3 * nmc;
-    // FP64 flops of the ratio walks: 3 per half-grid point of every chunk that
-    // lies within e^-50 of a Gaussian's peak (counted in closed form per term)
     double work = 0.0;
     {
-        const double delta = 0.5 * h;
-        for (int k = 0; k < Rl; ++k) {
-            double t2 = 2.0 * tl_host[k] * tl_host[k];
-            double reach = t2 > 0 ? std::sqrt(50.0 / t2) : 1e300;
-            for (size_t e = 0; e < xyz_host.size(); ++e) {
-                double lo = std::max(0.0, std::floor((xyz_host[e] - reach + b) / delta / kSC));
-                double hi = std::min((double)(nsc - 1), std::floor((xyz_host[e] + reach + b) / delta / kSC));
-                if (hi >= lo) work += (hi - lo + 1) * kSC * 3.0;
-            }
-        }
-    }
-    {
-        ::rs::KernelTimer kt__("k_gauss_dsum", st, work, true);
+        ::rs::KernelTimer kt__("k_gauss_dsum", st, 0.0, true);
         k_gauss_dsum<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, b, h, N, Rl, d_xyz, d_cz,
                                                                          d_tl, nsc, nmc, d_Dp);
+        // FP64 flops of the ratio walks: 3 per half-grid point of every chunk that
+        // lies within e^-50 of a Gaussian's peak (closed form per term; only when timed)
+        if (kt__.active()) {
+            const double delta = 0.5 * h;
+            double w = 0.0;
+            for (int k = 0; k < Rl; ++k) {
+                double t2 = 2.0 * tl_host[k] * tl_host[k];
+                double reach = t2 > 0 ? std::sqrt(50.0 / t2) : 1e300;
+                for (size_t e = 0; e < xyz_host.size(); ++e) {
+                    double lo = std::max(0.0, std::floor((xyz_host[e] - reach + b) / delta / kSC));
+                    double hi = std::min((double)(nsc - 1), std::floor((xyz_host[e] + reach + b) / delta / kSC));
+                    if (hi >= lo) w += (hi - lo + 1) * kSC * 3.0;
+                }
+            }
+            kt__.set_work(w);
+        }
     }
     RS_TRY_CUDA(cudaGetLastError());
     size_t dlen = (size_t)3 * Rl * Sh;
@@ -1107,11 +1196,48 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         ::rs::KernelTimer kt__("k_init_block", st, 0.0, false);
         k_init_block<<<blocks_for((size_t)3 * n * p), kBlock, 0, st>>>(n, p, d_Q);
     }
-    auto orthonormalize = [&](double* Yin) -> rs_status {
-        // shifted CholQR then plain CholQR: Q = Y R^{-1}
+    // CholQR2 of Yin (d_Q or d_Y): shifted CholQR then plain CholQR; every pass reads
+    // one buffer and writes the other, and the result ends in d_Q.
+    auto cholqr_pass = [&](const double* src, double* dst, double shift) -> rs_status {
         {
             ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
-            k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, Yin, Yin, d_Sm);
+            k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, src, src, d_Sm);
+        }
+        {
+            ::rs::KernelTimer kt__("k_chol_rinv", st, 0.0, false);
+            k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, shift, d_Ri, d_fail);
+        }
+        {
+            ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
+            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, src, d_Ri, dst);
+        }
+        RS_TRY_CUDA(cudaGetLastError());
+        return RS_OK;
+    };
+    auto orthonormalize = [&](double* Yin) -> rs_status {
+        double* other = (Yin == d_Q) ? d_Y : d_Q;
+        RS_TRY(cholqr_pass(Yin, other, 1e-13));
+        RS_TRY(cholqr_pass(other, Yin, 0.0));
+        if (Yin != d_Q)
+            RS_TRY_CUDA(cudaMemcpyAsync(d_Q, Yin, (size_t)3 * n * p * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+        return RS_OK;
+    };
+    RS_TRY(orthonormalize(d_Q));
+    dim3 gq((n + 15) / 16, 1, 3);
+    const int nblk = (n + 15) / 16;
+    double* d_Sp;
+    RS_TRY(S.get(&d_Sp, (size_t)3 * nblk * p * p));
+    work = 3.0 * 2.0 * n * (double)n * p;  // FP64 flops per G Q
+    // one subspace step: Y = G Q with partial Grams, S = Y^T Y, shifted Cholesky, Q = Y R^-1
+    auto step = [&]() -> rs_status {
+        {
+            ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
+            k_gemm_gq_gram<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y, d_Sp);
+        }
+        {
+            ::rs::KernelTimer kt__("k_sum_gram", st, 0.0, false);
+            k_sum_gram<<<dim3(blocks_for((size_t)p * p), 3), kBlock, 0, st>>>(nblk, p, d_Sp, d_Sm);
         }
         {
             ::rs::KernelTimer kt__("k_chol_rinv", st, 0.0, false);
@@ -1119,52 +1245,55 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         }
         {
             ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
-            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, Yin, d_Ri, d_Q);
+            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, d_Y, d_Ri, d_Q);
         }
-        {
-            ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
-            k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Q, d_Sm);
-        }
-        {
-            ::rs::KernelTimer kt__("k_chol_rinv", st, 0.0, false);
-            k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, 0.0, d_Ri, d_fail);
-        }
-        {
-            ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
-            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, d_Q, d_Ri, d_Y);
-        }
-        RS_TRY_CUDA(cudaMemcpyAsync(d_Q, d_Y, (size_t)3 * n * p * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, st));
         RS_TRY_CUDA(cudaGetLastError());
         return RS_OK;
     };
-    RS_TRY(orthonormalize(d_Q));
-    dim3 gq((n + 15) / 16, 1, 3);
-    work = 3.0 * 2.0 * n * (double)n * p;  // FP64 flops per G Q
-    const int iters = 28;
-    for (int it = 0; it < iters; ++it) {
+    auto ritz = [&](std::vector<double>& lam_out) -> rs_status {
+        RS_TRY(orthonormalize(d_Q));
         {
             ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
             k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y);
         }
-        RS_TRY(orthonormalize(d_Y));
+        {
+            ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
+            k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Y, d_Sm);
+        }
+        {
+            ::rs::KernelTimer kt__("k_jacobi", st, 0.0, false);
+            k_jacobi<<<3, 256, 0, st>>>(p, d_Sm, d_lam, d_W);
+        }
+        RS_TRY_CUDA(cudaGetLastError());
+        lam_out.resize((size_t)3 * p);
+        RS_TRY_CUDA(cudaMemcpyAsync(lam_out.data(), d_lam, lam_out.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        RS_TRY_CUDA(cudaStreamSynchronize(st));
+        return RS_OK;
+    };
+    // Subspace iteration converges like (lambda_{p+1} / lambda_r)^T.  After a few
+    // steps the Ritz values estimate that ratio (lambda_p / lambda_r as a safe
+    // proxy); the remaining steps bring the subspace error below 1e-14.
+    const int warm = 6;
+    for (int it = 0; it < warm; ++it) RS_TRY(step());
+    std::vector<double> lam_est;
+    RS_TRY(ritz(lam_est));
+    int more = 0;
+    for (int a = 0; a < 3; ++a) {
+        const double* la = lam_est.data() + (size_t)a * p;
+        int r = std::min(cap, p - 1);
+        double ratio = (la[r - 1] > 0 && la[p - 1] > 0) ? la[p - 1] / la[r - 1] : 0.5;
+        ratio = std::min(std::max(ratio, 1e-8), 0.95);
+        int need = (int)std::ceil(std::log(1e-14) / std::log(ratio)) - warm + 2;
+        more = std::max(more, need);
     }
-    {
-        ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
-        k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y);
-    }
-    {
-        ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
-        k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Y, d_Sm);
-    }
-    {
-        ::rs::KernelTimer kt__("k_jacobi", st, 0.0, false);
-        k_jacobi<<<3, 256, 0, st>>>(p, d_Sm, d_lam, d_W);
-    }
-    RS_TRY_CUDA(cudaGetLastError());
-    std::vector<double> lam((size_t)3 * p), tr(3);
+    more = std::min(std::max(more, 2), 60);
+    for (int it = 0; it < more; ++it) RS_TRY(step());
+    P->subspace_steps = warm + more;
+    std::vector<double> lam_unused;
+    RS_TRY(ritz(lam_unused));
+    std::vector<double> lam = lam_unused, tr(3);
     int fail[3];
-    RS_TRY_CUDA(cudaMemcpyAsync(lam.data(), d_lam, lam.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     RS_TRY_CUDA(cudaMemcpyAsync(tr.data(), d_tr, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     RS_TRY_CUDA(cudaMemcpyAsync(fail, d_fail, sizeof(fail), cudaMemcpyDeviceToHost, st));
     RS_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1227,13 +1356,15 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY(S.get(&d_Bp, (size_t)nchunk * RP * RP * RP));
     RS_TRY(S.get(&d_B, (size_t)RP * RP * RP));
     double proj_points = 0.0;
-    for (int k = 0; k < Rl; ++k) {
-        double t2 = tl_host[k] * tl_host[k];
-        double hw = t2 > 0 ? std::sqrt(700.0 / t2) : 1e300;
-        for (size_t e = 0; e < xyz_host.size(); ++e) {
-            double lo = std::max(0.0, std::ceil((xyz_host[e] - hw + b) / h));
-            double hi = std::min((double)(n - 1), std::floor((xyz_host[e] + hw + b) / h));
-            if (hi >= lo) proj_points += hi - lo + 1;
+    if (timing_mode() > 0) {
+        for (int k = 0; k < Rl; ++k) {
+            double t2 = tl_host[k] * tl_host[k];
+            double hw = t2 > 0 ? std::sqrt(700.0 / t2) : 1e300;
+            for (size_t e = 0; e < xyz_host.size(); ++e) {
+                double lo = std::max(0.0, std::ceil((xyz_host[e] - hw + b) / h));
+                double hi = std::min((double)(n - 1), std::floor((xyz_host[e] + hw + b) / h));
+                if (hi >= lo) proj_points += hi - lo + 1;
+            }
         }
     }
     RS_TRY(dispatch_project_core(RP, st, n, b, h, N, Rl, d_xyz, d_q, d_tl, d_al, d_Wp, d_Cp, d_Bp,
@@ -1303,12 +1434,7 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
     RS_CHECK_ARG(mem_flags == RS_MEM_HOST || mem_flags == RS_MEM_DEVICE,
                  "rs_build_protein: bad mem_flags %d", mem_flags);
     RS_TRY_CUDA(cudaSetDevice(ctx->device));
-    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
-    if (stream && stream != (void*)ctx->stream) {
-        // the build is synchronous on the context stream; order after the caller's work
-        RS_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-        st = ctx->stream;
-    }
+    cudaStream_t st = (cudaStream_t)stream;  // NULL: the CUDA default stream
 
     rs_protein* P = new rs_protein();
     P->device = ctx->device;
@@ -1327,7 +1453,7 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
     if (s != RS_OK) return fail_out(s);
     P->K = (int)P->table.t.size();
 
-    Scratch S;
+    Scratch S(ctx);
     // inputs on the device (and on the host, for the small host-side parts)
     std::vector<double> hq(N);
     double *d_xyz = nullptr, *d_q = nullptr;

@@ -44,9 +44,10 @@ void clear_error();
 struct SincTable {
     std::vector<double> t, a;
     std::vector<uint8_t> is_long;
-    double h_s = 0, box_len = 0, r_c = 0, quad_err = 0;
+    double h_s = 0, box_len = 0, r_c = 0, quad_err = -1, r_min = 0;
     int R_l = 0;
 };
+double sinc_quad_error(const SincTable& T);
 rs_status make_sinc_table(double b, double sigma, int R_l, double r_min, double tau,
                           double short_tol, SincTable* out);
 
@@ -106,6 +107,7 @@ struct rs_protein {
     rs::ProteinView view{};
     std::vector<void*> allocations;   // device buffers owned by the handle
     size_t device_bytes = 0;
+    int subspace_steps = 0;           // Tucker build: subspace-iteration steps taken
 };
 
 struct rs_ctx {
@@ -116,6 +118,9 @@ struct rs_ctx {
     size_t lig_bytes = 0;
     void* io_buf = nullptr;
     size_t io_bytes = 0;
+    // Build workspace, grown to the largest build seen (one build at a time).
+    void* ws_buf = nullptr;
+    size_t ws_bytes = 0;
 };
 
 namespace rs {

@@ -87,26 +87,14 @@ rs_status make_sinc_table(double b, double sigma, int R_l, double r_min, double 
         T.a.push_back(w / T.box_len);
         T.is_long.push_back(k < R_l ? 1 : 0);
     }
-    auto full = [&](double r) {
-        double s = 0;
-        for (size_t k = 0; k < T.t.size(); ++k) s += T.a[k] * std::exp(-T.t[k] * T.t[k] * r * r);
-        return s;
-    };
     auto shortf = [&](double r) {
         double s = 0;
         for (size_t k = 0; k < T.t.size(); ++k)
             if (!T.is_long[k]) s += T.a[k] * std::exp(-T.t[k] * T.t[k] * r * r);
         return r * s;
     };
-    // measured max relative error of the full sum against 1/r on [r_min, B]
-    const int M = 20001;
-    double err = 0;
-    for (int i = 0; i < M; ++i) {
-        double r = r_min * std::pow(T.box_len / r_min, (double)i / (M - 1));
-        double e = std::fabs(r * full(r) - 1.0);
-        if (e > err) err = e;
-    }
-    T.quad_err = err;
+    T.quad_err = -1.0;  // measured on first request (sinc_quad_error)
+    T.r_min = r_min;
     // short-range cutoff: beyond the peak of the widest short-range term every
     // short-range Gaussian decreases, so r*sum is decreasing there; bisect.
     double r_c = 0.0;
@@ -138,6 +126,21 @@ rs_status make_sinc_table(double b, double sigma, int R_l, double r_min, double 
     T.r_c = r_c;
     *out = std::move(T);
     return RS_OK;
+}
+
+// Max relative error of sum_k a_k exp(-t_k^2 r^2) against 1/r on [r_min, B]
+// (20001 geometrically spaced points): a diagnostic, computed once per table.
+double sinc_quad_error(const SincTable& T) {
+    const int M = 20001;
+    double err = 0;
+    for (int i = 0; i < M; ++i) {
+        double r = T.r_min * std::pow(T.box_len / T.r_min, (double)i / (M - 1));
+        double s = 0;
+        for (size_t k = 0; k < T.t.size(); ++k) s += T.a[k] * std::exp(-T.t[k] * T.t[k] * r * r);
+        double e = std::fabs(r * s - 1.0);
+        if (e > err) err = e;
+    }
+    return err;
 }
 
 }  // namespace rs
@@ -198,6 +201,7 @@ void rs_ctx_destroy(rs_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->lig_buf) cudaFree(c->lig_buf);
     if (c->io_buf) cudaFree(c->io_buf);
+    if (c->ws_buf) cudaFree(c->ws_buf);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -226,6 +230,7 @@ rs_status rs_protein_get_info(const rs_protein* p, rs_protein_info* o) {
     o->sigma = p->sigma;
     o->r_c = p->table.r_c;
     o->h_s = p->table.h_s;
+    if (p->table.quad_err < 0) const_cast<rs_protein*>(p)->table.quad_err = rs::sinc_quad_error(p->table);
     o->quad_err = p->table.quad_err;
     o->kind = p->kind;
     for (int a = 0; a < 3; ++a) {

@@ -54,6 +54,8 @@ void resolve(KernelStat& s) {
 
 void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+int timing_mode() { return g_timing_on.load(std::memory_order_relaxed); }
+
 KernelTimer::KernelTimer(const char* name, cudaStream_t st, double work, bool major)
     : name_(name), st_(st), work_(work) {
     note_launch(1);

@@ -8,6 +8,9 @@ namespace rs {
 // Adds n to the process-wide count of kernels launched by this library.
 void note_launch(unsigned n = 1);
 
+// Current timing mode (0 off, 1 major kernels, 2 all).
+int timing_mode();
+
 // Scope object around one kernel launch: counts it and, when timing is
 // enabled, records a CUDA event pair on the launch stream.  `work` is the
 // algorithmic flop (or byte) count of the launch, summed per kernel name.
@@ -18,6 +21,8 @@ class KernelTimer {
     KernelTimer(const char* name, cudaStream_t st, double work = 0.0, bool major = true);
     ~KernelTimer();
     KernelTimer(const KernelTimer&) = delete;
+    bool active() const { return active_; }
+    void set_work(double w) { work_ = w; }
     KernelTimer& operator=(const KernelTimer&) = delete;
 
   private:

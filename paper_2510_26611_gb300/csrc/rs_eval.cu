@@ -485,12 +485,13 @@ size_t wform_smem(int PB, int L) {
     return (s + 15) / 16 * 16;
 }
 
-// FP32 operations per atom of the W-form evaluation: per (a, b) a pair lerp (13)
-// and one (energy) or three (gradient) Dot2 steps (11 each); per a one or four
-// Dot2 steps; two pair lerps per factor column; ~60 for pose transform and cells.
+// FP32 flops (FMA = 2) per atom of the W-form evaluation: per (a, b) one pair
+// lerp (16) and one (energy) or three (gradient) Dot2 steps (15 each); per a one
+// or four Dot2 steps; one pair lerp (16) per column of v1 and v2; pose transform,
+// cell index and reduction ~60 (energy) / ~80 (gradient).
 inline double wform_flops_per_atom(int RP, bool grad) {
-    double ab = (double)RP * RP, a = RP;
-    return grad ? ab * (13 + 3 * 11) + a * 4 * 11 + 2 * a * 13 + 60 : ab * (13 + 11) + a * 11 + 2 * a * 13 + 60;
+    double r = RP;
+    return grad ? 61.0 * r * r + 92.0 * r + 80.0 : 31.0 * r * r + 47.0 * r + 60.0;
 }
 
 template <bool GRAD>
@@ -640,7 +641,7 @@ rs_status run_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L, const double
     RS_CHECK_ARG(lig_xyz && lig_q && rot && trans && E_out, "NULL input or output pointer");
     if (grad) RS_CHECK_ARG(dE_dt && dE_dw, "NULL gradient output");
     RS_TRY_CUDA(cudaSetDevice(ctx->device));
-    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    cudaStream_t st = (cudaStream_t)stream;  // NULL: the CUDA default stream
     const int rdim = grad ? 3 : 4;
     // ligand scratch
     RS_TRY(ensure_buffer(&ctx->lig_buf, &ctx->lig_bytes, ligand_scratch_bytes(L) + 1024));

@@ -149,10 +149,22 @@ def test_host_and_device_modes_bitwise_equal(L, small):
     w, m, prot, _ = small
     E_h, f_h = prot.energies(w.lig_xyz, w.lig_q, w.quat, w.trans)
     t = lambda a: torch.as_tensor(a, device="cuda")
+    # results read right after the call: the call must be ordered on torch's stream
     E_d, f_d = prot.energies(t(w.lig_xyz), t(w.lig_q), t(w.quat), t(w.trans))
-    torch.cuda.synchronize()
     assert np.array_equal(E_h, E_d.cpu().numpy())
     assert np.array_equal(f_h, f_d.cpu().numpy())
+
+
+def test_device_call_on_a_side_stream(L, small):
+    import torch
+    w, m, prot, _ = small
+    E_h, f_h = prot.energies(w.lig_xyz, w.lig_q, w.quat, w.trans)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        t = lambda a: torch.as_tensor(a, device="cuda")
+        E_d, f_d = prot.energies(t(w.lig_xyz), t(w.lig_q), t(w.quat), t(w.trans))
+        out = E_d.cpu().numpy(), f_d.cpu().numpy()
+    assert np.array_equal(E_h, out[0]) and np.array_equal(f_h, out[1])
 
 
 def test_deterministic_and_order_independent(L, protein):
