@@ -153,6 +153,29 @@ rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
                                double* E_out, double* dE_dt, double* dE_dw,
                                uint8_t* flags_out, int mem_flags, void* stream);
 
+/* Same energies and flags as rs_energy_poses, for callers that must not cause any
+ * device allocation during the call (for example a thread that may never run
+ * cudaMalloc/cudaFree because those can synchronise the device, or a plug-in whose
+ * host application owns all device memory).  The paper has no counterpart: this
+ * is an interface choice.  Differences from rs_energy_poses:
+ *   - every array pointer is device memory on the protein's GPU (no host mode);
+ *     no context is needed; the call sets the protein's device current and
+ *     enqueues on `stream` (NULL = the CUDA default stream);
+ *   - the per-call scratch is a fixed array in the library's device image
+ *     (about 197 KB on every GPU that loads the library, kept until exit), so
+ *     L may be at most 4096; larger L returns RS_ERR_UNSUPPORTED;
+ *   - the first call on a device looks the array's address up once; make that
+ *     first call before any stream capture;
+ *   - all calls share the array and it keeps the last call's contents (each call
+ *     writes everything it reads first), so calls that overlap on the GPU, e.g.
+ *     on two streams at once, race and must be serialised by the caller;
+ *   - no timing events are recorded for these launches (the launch counter
+ *     still counts them). */
+rs_status rs_energy_poses_noalloc(const rs_protein* prot, int32_t L, const double* lig_xyz,
+                                  const double* lig_q, int64_t P, const double* quat,
+                                  const double* trans, double* E_out, uint8_t* flags_out,
+                                  void* stream);
+
 /* ----------------------------------------------------------- diagnostics */
 /* These have no counterpart in the paper: they support measurement.
  * Number of kernels this library has launched in the process (all devices). */

@@ -56,11 +56,12 @@ void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed
 
 int timing_mode() { return g_timing_on.load(std::memory_order_relaxed); }
 
-KernelTimer::KernelTimer(const char* name, cudaStream_t st, double work, bool major)
+KernelTimer::KernelTimer(const char* name, cudaStream_t st, double work, bool major,
+                         bool allow_events)
     : name_(name), st_(st), work_(work) {
     note_launch(1);
     int mode = g_timing_on.load(std::memory_order_relaxed);
-    if (mode == 0 || (mode == 1 && !major)) return;
+    if (!allow_events || mode == 0 || (mode == 1 && !major)) return;
     if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
         cudaGetLastError();
         return;

@@ -15,10 +15,12 @@ int timing_mode();
 // enabled, records a CUDA event pair on the launch stream.  `work` is the
 // algorithmic flop (or byte) count of the launch, summed per kernel name.
 // Timing mode 1 times only `major` launches (the pose kernels and the heavy
-// build kernels); mode 2 times every launch.
+// build kernels); mode 2 times every launch.  With allow_events false the launch
+// is only counted (no CUDA events are created).
 class KernelTimer {
   public:
-    KernelTimer(const char* name, cudaStream_t st, double work = 0.0, bool major = true);
+    KernelTimer(const char* name, cudaStream_t st, double work = 0.0, bool major = true,
+                bool allow_events = true);
     ~KernelTimer();
     KernelTimer(const KernelTimer&) = delete;
     bool active() const { return active_; }

@@ -535,7 +535,7 @@ rs_status launch_tucker(const EvalLaunch& a, cudaStream_t st) {
     if (grid < 1) return RS_OK;
     double work = (double)a.P * a.lig.L * wform_flops_per_atom(RP, GRAD);
     {
-        ::rs::KernelTimer kt__(kname, st, work, true);
+        ::rs::KernelTimer kt__(kname, st, work, true, a.events);
         kern<<<(unsigned)grid, 128, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
                                               a.gt, a.gw);
     }
@@ -568,7 +568,7 @@ rs_status launch_canon(const EvalLaunch& a, cudaStream_t st) {
     if (a.grid > 0) grid = std::min<long long>(nblocks, a.grid);
     if (grid < 1) return RS_OK;
     {
-        ::rs::KernelTimer kt__(kname, st, work, true);
+        ::rs::KernelTimer kt__(kname, st, work, true, a.events);
         kern<<<(unsigned)grid, 256, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
                                               a.gt, a.gw);
     }
@@ -579,9 +579,9 @@ rs_status launch_canon(const EvalLaunch& a, cudaStream_t st) {
 }  // namespace
 
 rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, double* y64,
-                             double* q64, cudaStream_t st) {
+                             double* q64, cudaStream_t st, bool events) {
     {
-        ::rs::KernelTimer kt__("k_prep_ligand", st, 0.0, false);
+        ::rs::KernelTimer kt__("k_prep_ligand", st, 0.0, false, events);
         k_prep_ligand<<<1, 256, 0, st>>>(L, xyz, q, y, y64, q64);
     }
     RS_TRY_CUDA(cudaGetLastError());

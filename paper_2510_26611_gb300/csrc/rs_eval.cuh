@@ -17,10 +17,11 @@ struct EvalLaunch {
     double* gw = nullptr;
     int PB = 0;                     // poses per block (0: heuristic)
     int grid = 0;                   // CTAs (0: persistent, fill the GPU)
+    bool events = true;             // allow timing events (off for the no-allocation path)
 };
 
 rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, double* y64,
-                             double* q64, cudaStream_t st);
+                             double* q64, cudaStream_t st, bool events = true);
 rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st);
 size_t ligand_scratch_bytes(int L);
 LigandView carve_ligand(void* base, int L);

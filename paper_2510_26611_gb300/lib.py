@@ -70,6 +70,7 @@ def _load() -> C.CDLL:
         "rs_protein_get_table": (st, [vp, vp, vp, vp]),
         "rs_energy_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
         "rs_energy_grad_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
+        "rs_energy_poses_noalloc": (st, [vp, i32, vp, vp, i64, vp, vp, vp, vp, vp]),
         "rs_stats_kernel_launches": (C.c_ulonglong, []),
         "rs_timing_enable": (st, [C.c_int]),
         "rs_timing_reset": (st, []),
@@ -251,6 +252,28 @@ def rs_energy_grad_poses(ctx, prot, lig_xyz, lig_q, rotvec, trans, E_out=None, d
     returns (E, dE_dt, dE_dw, flags)."""
     return _pose_call(True, ctx, prot, lig_xyz, lig_q, rotvec, trans, E_out, flags_out, dE_dt,
                       dE_dw, stream)
+
+
+def rs_energy_poses_noalloc(prot, lig_xyz, lig_q, quat, trans, E_out=None, flags_out=None,
+                            stream=None):
+    """rs_energy_poses for callers that must not trigger any device allocation
+    during the call: every argument is a CUDA tensor on the protein's GPU, the
+    library's scratch is a fixed array (ligands of at most 4096 atoms), and
+    concurrent calls must not overlap on the GPU.  Returns (E, flags)."""
+    import torch
+    for x in (lig_xyz, lig_q, quat, trans):
+        if not _is_cuda(x):
+            raise RSError(RS_ERR_INVALID, "rs_energy_poses_noalloc takes CUDA tensors only")
+    lx, lq = _dev(lig_xyz, np.float64), _dev(lig_q, np.float64)
+    r, t = _dev(quat, np.float64), _dev(trans, np.float64)
+    P, L = int(r.shape[0]), int(lq.shape[0])
+    if tuple(lx.shape) != (L, 3) or tuple(r.shape) != (P, 4) or tuple(t.shape) != (P, 3):
+        raise RSError(RS_ERR_INVALID, "shape mismatch in pose arguments")
+    E = E_out if E_out is not None else torch.empty(P, dtype=torch.float64, device=r.device)
+    f = flags_out if flags_out is not None else torch.empty(P, dtype=torch.uint8, device=r.device)
+    _check(_lib.rs_energy_poses_noalloc(prot, L, _ptr(lx), _ptr(lq), P, _ptr(r), _ptr(t),
+                                        _ptr(E), _ptr(f), _stream_ptr(stream)))
+    return E, f
 
 
 def rs_stats_kernel_launches() -> int:
