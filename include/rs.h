@@ -153,6 +153,46 @@ rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
                                double* E_out, double* dE_dt, double* dE_dw,
                                uint8_t* flags_out, int mem_flags, void* stream);
 
+/* ------------------------------------------------------------- batching */
+/* One protein-ligand pair of a batch.  All arrays are device memory on the
+ * context's GPU; the pair's protein must be Tucker-reduced (tucker_cap > 0). */
+typedef struct rs_pair {
+    const rs_protein* prot;
+    int32_t L;              /* ligand atoms, 1..4096                              */
+    const double* lig_xyz;  /* [L][3], read once by rs_batch_create              */
+    const double* lig_q;    /* [L]                                               */
+    int64_t P;              /* poses                                             */
+    const double* quat;     /* [P][4] (w,x,y,z), read at every rs_batch_run      */
+    const double* trans;    /* [P][3], read at every rs_batch_run                */
+    double* E_out;          /* [P]                                               */
+    uint8_t* flags_out;     /* [P] or NULL                                       */
+} rs_pair;
+
+typedef struct rs_batch rs_batch;
+
+typedef struct rs_batch_info {
+    int32_t npairs, ngroups;  /* pairs; launches (one per padded Tucker rank)     */
+    int32_t nitems;           /* work items (pose blocks) over all pairs          */
+    int32_t grid;             /* persistent CTAs over all groups                  */
+    int32_t threads;          /* chosen threads per CTA (first group)             */
+    int32_t atoms_per_item;   /* chosen target atoms per item (first group)       */
+    double  tune_ms;          /* device time the autotuner spent                  */
+} rs_batch_info;
+
+/* Algorithm PLIE (Sec. 3.4) for many pairs of uneven size in one persistent
+ * launch per padded rank, captured once in a CUDA graph.  Ligands are prepared
+ * now; poses are read from the given pointers at each rs_batch_run, so a caller
+ * may rewrite them in place between runs.  With autotune != 0 the threads per
+ * CTA and atoms per work item are chosen by timing candidates on a quarter of
+ * the batch (this writes the output arrays; cached per padded rank for the
+ * process).  Energies and flags equal rs_energy_poses bit for bit. */
+rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int32_t autotune,
+                          rs_batch** out);
+/* Replays the batch's graph on `stream` (NULL = the CUDA default stream). */
+rs_status rs_batch_run(rs_batch* batch, void* stream);
+void      rs_batch_free(rs_batch* batch);
+rs_status rs_batch_get_info(const rs_batch* batch, rs_batch_info* out);
+
 /* Same energies and flags as rs_energy_poses, for callers that must not cause any
  * device allocation during the call (for example a thread that may never run
  * cudaMalloc/cudaFree because those can synchronise the device, or a plug-in whose

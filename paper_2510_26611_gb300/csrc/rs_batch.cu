@@ -1,0 +1,410 @@
+// Batched pose evaluation: many protein-ligand pairs of uneven sizes in one
+// persistent launch, captured once in a CUDA graph and replayed.
+//
+// Each pair's poses are cut into items of PB poses (PB ~ atoms-per-item / L);
+// items are ordered by work, largest first, and persistent CTAs take them from
+// a device counter.  Every item is computed exactly as the plain kernel computes
+// a pose block, so results do not depend on the mix or on which CTA ran them.
+// The block shape (threads per CTA, atoms per item) is chosen per padded rank by
+// a small autotuner that times the candidates on the batch itself.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "rs_common.cuh"
+#include "rs_diag.cuh"
+#include "rs_eval.cuh"
+#include "rs_pose_dev.cuh"
+
+namespace rs {
+namespace {
+
+struct PairDesc {
+    ProteinView prot;
+    LigandView lig;
+    const double* rot;
+    const double* trans;
+    long long P;
+    double* E;
+    uint8_t* flags;
+};
+
+struct BatchItem {
+    int pair;
+    int PB;
+    long long p0;
+};
+
+template <int RP, int NT>
+__global__ void __launch_bounds__(NT) k_eval_batch(const PairDesc* __restrict__ pairs,
+                                                   const BatchItem* __restrict__ items, int nitems,
+                                                   int* __restrict__ counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int cur;
+    __shared__ __align__(16) PairDesc pd;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = cur;
+        if (it >= nitems) break;
+        const BatchItem bi = items[it];
+        const int* src = (const int*)(pairs + bi.pair);
+        for (int e = threadIdx.x; e < (int)(sizeof(PairDesc) / sizeof(int)); e += NT)
+            ((int*)&pd)[e] = src[e];
+        __syncthreads();
+        wform_block<RP, false, NT>(pd.prot, pd.lig, pd.rot, pd.trans, pd.P, bi.PB, bi.p0, pd.E,
+                                   pd.flags, nullptr, nullptr, smem);
+    }
+}
+
+struct Shape {
+    int nt;      // threads per CTA
+    int atoms;   // target atoms per item
+};
+
+const Shape kCandidates[] = {{128, 256}, {128, 512}, {128, 1024}, {256, 512}, {256, 1024}};
+
+std::mutex g_tune_mu;
+std::map<int, Shape> g_tuned;  // padded rank -> best shape (process-wide cache)
+
+int pb_for(int L, int atoms) { return std::min(128, std::max(1, atoms / L)); }
+
+template <int RP, int NT>
+size_t batch_smem(const std::vector<int>& Ls, int atoms) {
+    size_t m = 0;
+    for (int L : Ls) m = std::max(m, wform_smem<RP, false, NT>(pb_for(L, atoms), L));
+    return m;
+}
+
+struct Group {
+    int RP;
+    std::vector<int> pairs;  // indices into the batch's pair list
+    Shape shape{128, 512};
+    int nitems = 0;
+    int grid = 0;
+    size_t smem = 0;
+    BatchItem* d_items = nullptr;
+    int* d_counter = nullptr;
+};
+
+}  // namespace
+}  // namespace rs
+
+struct rs_batch {
+    int device = 0;
+    std::vector<rs::PairDesc> pairs;
+    std::vector<int> Ls;
+    rs::PairDesc* d_pairs = nullptr;
+    void* d_lig = nullptr;
+    std::vector<rs::Group> groups;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    double tune_ms = 0.0;
+    std::vector<void*> allocs;
+};
+
+namespace rs {
+namespace {
+
+template <int RP, int NT>
+rs_status launch_group(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) {
+    auto kern = k_eval_batch<RP, NT>;
+    size_t sm = batch_smem<RP, NT>(B->Ls, g.shape.atoms);
+    if (sm > 200 * 1024) {
+        set_error("batch: shared memory %zu exceeds the limit", sm);
+        return RS_ERR_UNSUPPORTED;
+    }
+    if (set_attr) {
+        RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int per_sm = 0;
+        RS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm));
+        int sms = 0;
+        RS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device));
+        g.grid = std::max(1, std::min(g.nitems, std::max(per_sm, 1) * sms));
+        g.smem = sm;
+    }
+    RS_TRY_CUDA(cudaMemsetAsync(g.d_counter, 0, sizeof(int), st));
+    {
+        ::rs::KernelTimer kt__("k_eval_batch", st, 0.0, true, false);
+        kern<<<g.grid, NT, g.smem, st>>>(B->d_pairs, g.d_items, g.nitems, g.d_counter);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
+template <int RP>
+rs_status launch_group_nt(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) {
+    return g.shape.nt == 256 ? launch_group<RP, 256>(B, g, st, set_attr)
+                             : launch_group<RP, 128>(B, g, st, set_attr);
+}
+
+rs_status dispatch_group(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) {
+    switch (g.RP) {
+#define RS_CASE(R) \
+    case R: return launch_group_nt<R>(B, g, st, set_attr);
+        RS_CASE(4) RS_CASE(8) RS_CASE(12) RS_CASE(16) RS_CASE(20) RS_CASE(24) RS_CASE(28) RS_CASE(32)
+#undef RS_CASE
+        default:
+            set_error("batch: unsupported padded rank %d", g.RP);
+            return RS_ERR_UNSUPPORTED;
+    }
+}
+
+// Work items of a group for a shape: per pair, blocks of PB poses; largest
+// items first so the tail of the persistent launch is short.
+rs_status build_items(rs_batch* B, Group& g, double pose_fraction) {
+    std::vector<BatchItem> items;
+    std::vector<double> cost;
+    for (int pi : g.pairs) {
+        const PairDesc& d = B->pairs[pi];
+        int PB = pb_for(d.lig.L, g.shape.atoms);
+        long long P = std::max<long long>(1, (long long)(d.P * pose_fraction));
+        if (pose_fraction >= 1.0) P = d.P;
+        for (long long p0 = 0; p0 < P; p0 += PB) {
+            items.push_back({pi, PB, p0});
+            long long np = std::min<long long>(PB, d.P - p0);
+            cost.push_back((double)np * d.lig.L);
+        }
+    }
+    std::vector<size_t> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<BatchItem> sorted(items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    g.nitems = (int)sorted.size();
+    if (g.d_items) {
+        cudaFree(g.d_items);
+        B->allocs.erase(std::remove(B->allocs.begin(), B->allocs.end(), (void*)g.d_items), B->allocs.end());
+        g.d_items = nullptr;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(1, sorted.size()) * sizeof(BatchItem)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("batch: item list allocation failed");
+        return RS_ERR_OOM;
+    }
+    B->allocs.push_back(p);
+    g.d_items = (BatchItem*)p;
+    RS_TRY_CUDA(cudaMemcpy(g.d_items, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    return RS_OK;
+}
+
+// Times every candidate shape on a fraction of the group's poses (results are
+// written to the real outputs and overwritten by the real run) and keeps the best.
+rs_status tune_group(rs_batch* B, Group& g, cudaStream_t st) {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(g.RP);
+        if (it != g_tuned.end()) {
+            g.shape = it->second;
+            return RS_OK;
+        }
+    }
+    cudaEvent_t a, b;
+    RS_TRY_CUDA(cudaEventCreate(&a));
+    RS_TRY_CUDA(cudaEventCreate(&b));
+    float best = 1e30f;
+    Shape best_shape = g.shape;
+    for (const Shape& c : kCandidates) {
+        g.shape = c;
+        RS_TRY(build_items(B, g, 0.25));
+        RS_TRY(dispatch_group(B, g, st, true));  // warm-up
+        float total = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            RS_TRY_CUDA(cudaEventRecord(a, st));
+            RS_TRY(dispatch_group(B, g, st, false));
+            RS_TRY_CUDA(cudaEventRecord(b, st));
+            RS_TRY_CUDA(cudaEventSynchronize(b));
+            float ms = 0.f;
+            RS_TRY_CUDA(cudaEventElapsedTime(&ms, a, b));
+            total += ms;
+        }
+        B->tune_ms += total;
+        if (total < best) {
+            best = total;
+            best_shape = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    g.shape = best_shape;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[g.RP] = best_shape;
+    return RS_OK;
+}
+
+void batch_destroy(rs_batch* B) {
+    if (!B) return;
+    cudaSetDevice(B->device);
+    cudaDeviceSynchronize();
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+    for (void* p : B->allocs) cudaFree(p);
+    delete B;
+}
+
+}  // namespace
+}  // namespace rs
+
+extern "C" {
+
+rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int32_t autotune,
+                          rs_batch** out) {
+    using namespace rs;
+    clear_error();
+    RS_CHECK_ARG(ctx && pairs && out, "rs_batch_create: NULL argument");
+    RS_CHECK_ARG(npairs >= 1 && npairs <= (1 << 20), "rs_batch_create: npairs=%d out of range", npairs);
+    *out = nullptr;
+    for (int i = 0; i < npairs; ++i) {
+        const rs_pair& p = pairs[i];
+        RS_CHECK_ARG(p.prot, "rs_batch_create: pair %d has no protein", i);
+        RS_CHECK_ARG(p.prot->device == ctx->device, "rs_batch_create: pair %d on another device", i);
+        RS_CHECK_ARG(p.L >= 1 && p.L <= 4096, "rs_batch_create: pair %d L=%d out of range", i, p.L);
+        RS_CHECK_ARG(p.P >= 0 && p.P <= 0x7fffffffLL, "rs_batch_create: pair %d P out of range", i);
+        RS_CHECK_ARG(p.lig_xyz && p.lig_q && (p.P == 0 || (p.quat && p.trans && p.E_out)),
+                     "rs_batch_create: pair %d has a NULL pointer", i);
+        if (p.prot->kind != 1) {
+            set_error("rs_batch_create: pair %d: batching takes Tucker-reduced proteins", i);
+            return RS_ERR_UNSUPPORTED;
+        }
+    }
+    RS_TRY_CUDA(cudaSetDevice(ctx->device));
+    rs_batch* B = new rs_batch();
+    B->device = ctx->device;
+    auto fail = [&](rs_status s) {
+        batch_destroy(B);
+        return s;
+    };
+    if (cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("rs_batch_create: stream creation failed");
+        return fail(RS_ERR_CUDA);
+    }
+    cudaStream_t st = B->cap_stream;
+    // prepared ligands, one region per pair
+    std::vector<size_t> off(npairs);
+    size_t total = 0;
+    for (int i = 0; i < npairs; ++i) {
+        off[i] = total;
+        total += (ligand_scratch_bytes(pairs[i].L) + 1023) / 256 * 256;
+    }
+    if (cudaMalloc(&B->d_lig, total) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("rs_batch_create: ligand scratch allocation failed");
+        return fail(RS_ERR_OOM);
+    }
+    B->allocs.push_back(B->d_lig);
+    for (int i = 0; i < npairs; ++i) {
+        const rs_pair& p = pairs[i];
+        LigandView lig = carve_ligand((char*)B->d_lig + off[i], p.L);
+        rs_status s = launch_prep_ligand(p.L, p.lig_xyz, p.lig_q, (float4*)lig.y, (double*)lig.y64,
+                                         (double*)lig.q64, st, false);
+        if (s != RS_OK) return fail(s);
+        PairDesc d;
+        d.prot = p.prot->view;
+        d.lig = lig;
+        d.rot = p.quat;
+        d.trans = p.trans;
+        d.P = p.P;
+        d.E = p.E_out;
+        d.flags = p.flags_out;
+        B->pairs.push_back(d);
+        B->Ls.push_back(p.L);
+    }
+    if (cudaMalloc((void**)&B->d_pairs, npairs * sizeof(PairDesc)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("rs_batch_create: descriptor allocation failed");
+        return fail(RS_ERR_OOM);
+    }
+    B->allocs.push_back(B->d_pairs);
+    if (cudaMemcpy(B->d_pairs, B->pairs.data(), npairs * sizeof(PairDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("rs_batch_create: descriptor copy failed");
+        return fail(RS_ERR_CUDA);
+    }
+    // groups by padded rank
+    std::map<int, std::vector<int>> by_rp;
+    for (int i = 0; i < npairs; ++i)
+        if (pairs[i].P > 0) by_rp[pairs[i].prot->view.R].push_back(i);
+    for (auto& kv : by_rp) {
+        Group g;
+        g.RP = kv.first;
+        g.pairs = kv.second;
+        void* c = nullptr;
+        if (cudaMalloc(&c, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("rs_batch_create: counter allocation failed");
+            return fail(RS_ERR_OOM);
+        }
+        B->allocs.push_back(c);
+        g.d_counter = (int*)c;
+        B->groups.push_back(g);
+    }
+    rs_status s;
+    for (Group& g : B->groups) {
+        if (autotune && (s = tune_group(B, g, st)) != RS_OK) return fail(s);
+        if ((s = build_items(B, g, 1.0)) != RS_OK) return fail(s);
+        if ((s = dispatch_group(B, g, st, true)) != RS_OK) return fail(s);  // sets attributes, grid
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("rs_batch_create: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(RS_ERR_CUDA);
+    }
+    // capture the whole batch once
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        set_error("rs_batch_create: stream capture failed to start");
+        return fail(RS_ERR_CUDA);
+    }
+    for (Group& g : B->groups) {
+        s = dispatch_group(B, g, st, false);
+        if (s != RS_OK) {
+            cudaGraph_t dummy;
+            cudaStreamEndCapture(st, &dummy);
+            if (dummy) cudaGraphDestroy(dummy);
+            return fail(s);
+        }
+    }
+    if (cudaStreamEndCapture(st, &B->graph) != cudaSuccess ||
+        cudaGraphInstantiate(&B->exec, B->graph, 0) != cudaSuccess) {
+        set_error("rs_batch_create: graph capture failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(RS_ERR_CUDA);
+    }
+    *out = B;
+    return RS_OK;
+}
+
+rs_status rs_batch_run(rs_batch* B, void* stream) {
+    rs::clear_error();
+    RS_CHECK_ARG(B && B->exec, "rs_batch_run: NULL batch");
+    RS_TRY_CUDA(cudaSetDevice(B->device));
+    RS_TRY_CUDA(cudaGraphLaunch(B->exec, (cudaStream_t)stream));
+    rs::note_launch((unsigned)B->groups.size());
+    return RS_OK;
+}
+
+void rs_batch_free(rs_batch* B) { rs::batch_destroy(B); }
+
+rs_status rs_batch_get_info(const rs_batch* B, rs_batch_info* o) {
+    rs::clear_error();
+    RS_CHECK_ARG(B && o, "rs_batch_get_info: NULL argument");
+    memset(o, 0, sizeof(*o));
+    o->npairs = (int32_t)B->pairs.size();
+    o->ngroups = (int32_t)B->groups.size();
+    for (const rs::Group& g : B->groups) {
+        o->nitems += g.nitems;
+        o->grid += g.grid;
+    }
+    if (!B->groups.empty()) {
+        o->threads = B->groups[0].shape.nt;
+        o->atoms_per_item = B->groups[0].shape.atoms;
+    }
+    o->tune_ms = B->tune_ms;
+    return RS_OK;
+}
+
+}  // extern "C"

@@ -951,6 +951,20 @@ __global__ void __launch_bounds__(1024) k_core(int Rtot, int Rl, int CH,
     for (int c = 0; c < RP; ++c) out[c] = acc[c];
 }
 
+// Table of the short-range radial function f(s) = sum_short a_k exp(-t_k^2 s) and of
+// hs * f'(s) at s = j*hs (FP64), for cubic Hermite interpolation in the pose kernels.
+__global__ void k_short_table(ProteinView v, int M, double hs, double2* __restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    double sv = j * hs, f = 0.0, fp = 0.0;
+    for (int q = 0; q < v.Ks; ++q) {
+        double e = v.as[q] * exp(-v.ts2[q] * sv);
+        f += e;
+        fp -= v.ts2[q] * e;
+    }
+    out[j] = make_double2(f, hs * fp);
+}
+
 __global__ void k_to_float(size_t len, const double* __restrict__ in, float* __restrict__ out) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < len) out[i] = (float)in[i];
@@ -1511,13 +1525,45 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
     v.Ks = 0;
     for (int k = 0; k < P->K; ++k)
         if (!P->table.is_long[k]) {
-            v.ts2[v.Ks] = (float)(P->table.t[k] * P->table.t[k]);
-            v.as[v.Ks] = (float)P->table.a[k];
+            v.ts2[v.Ks] = P->table.t[k] * P->table.t[k];
+            v.as[v.Ks] = P->table.a[k];
             ++v.Ks;
         }
     double rc = P->table.r_c;
     v.rc2 = rc * rc;
     v.rc2_hi = (float)(rc * rc * (1.0 + 1e-4));
+    v.stab = nullptr;
+    v.stab_n = 0;
+    v.stab_inv_h = 0.0;
+    if (v.Ks > 0 && rc > 0) {
+        // spacing from the cubic Hermite bound |f - p| <= hs^4/384 max|f''''| with
+        // max|f''''| <= sum a_k t_k^8 (at s = 0), for 1e-10 relative to f(0)
+        double f0 = 0.0, f4 = 0.0;
+        for (int q = 0; q < v.Ks; ++q) {
+            f0 += v.as[q];
+            f4 += v.as[q] * std::pow(v.ts2[q], 4.0);
+        }
+        double hs = std::pow(384.0 * 1e-10 * f0 / std::max(f4, 1e-300), 0.25);
+        double smax = (double)v.rc2_hi * (1.0 + 1e-6);
+        int M = (int)std::ceil(smax / hs) + 2;
+        if (M > (1 << 22)) {
+            set_error("rs_build_protein: short-range table of %d entries is too large", M);
+            return fail_out(RS_ERR_UNSUPPORTED);
+        }
+        double2* tab = nullptr;
+        if ((s = device_alloc(P, (void**)&tab, (size_t)M * sizeof(double2))) != RS_OK) return fail_out(s);
+        {
+            ::rs::KernelTimer kt__("k_short_table", st, 0.0, false);
+            k_short_table<<<blocks_for((size_t)M), kBlock, 0, st>>>(v, M, hs, tab);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("rs_build_protein: short-range table launch failed");
+            return fail_out(RS_ERR_CUDA);
+        }
+        v.stab = tab;
+        v.stab_n = M;
+        v.stab_inv_h = 1.0 / hs;
+    }
     v.sig2 = P->sigma * P->sigma;
     v.sig2_lo = (float)(v.sig2 * (1.0 - 1e-4));
     v.sig2_hi = (float)(v.sig2 * (1.0 + 1e-4));

@@ -70,9 +70,14 @@ struct ProteinView {
     const float* Wt[4];      // Wh, Wl, Dh, Dl   [n][RP][RP]
     const float* Vt[2][4];   // axes 1, 2: Vh, Vl, VDh, VDl  [n][RP]
     const float* core;   // Tucker core [RP][RP][RP] (FP32, diagnostics)
-    int Ks;              // short-range terms
-    float ts2[RS_MAX_SHORT];
-    float as[RS_MAX_SHORT];
+    int Ks;              // short-range terms: t_k^2 and a_k (FP64)
+    double ts2[RS_MAX_SHORT];
+    double as[RS_MAX_SHORT];
+    // short-range radial function f(s) = sum_short a_k exp(-t_k^2 s), s = d^2, as a
+    // cubic Hermite table: stab[j] = (f(j hs), hs f'(j hs)), j = 0..stab_n-1
+    const double2* stab;
+    int stab_n;
+    double stab_inv_h;
     double rc2;          // r_c^2
     float rc2_hi;        // r_c^2 (1 + 1e-4): FP32 pre-filter
     double sig2;         // sigma^2
@@ -230,11 +235,11 @@ __device__ __forceinline__ void left_jacobian(double wx, double wy, double wz, d
     J[6] = -B * wy + C * wx * wz; J[7] = B * wx + C * wy * wz; J[8] = 1 + C * (wz * wz - th2);
 }
 
-// Cell index and fraction along one axis: s = s_pose + d (s_pose = (t + b)/h in
-// FP64, d = (R y)/h in FP32); i = clamp(floor(s), 0, n-2), f = clamp(s - i, 0, 1).
-__device__ __forceinline__ void axis_cell(double s_pose, float d, int n, int& i, float& f,
+// Cell index and fraction along one axis from the FP64 coordinate x:
+// s = (x + b)/h; i = clamp(floor(s), 0, n-2), f = clamp(s - i, 0, 1).
+__device__ __forceinline__ void axis_cell(double x, double b, double inv_h, int n, int& i, float& f,
                                           bool& inside) {
-    double s = s_pose + (double)d;
+    double s = (x + b) * inv_h;
     inside = (s >= 0.0) && (s <= (double)(n - 1));
     double fl = floor(s);
     fl = fmin(fmax(fl, 0.0), (double)(n - 2));

@@ -54,6 +54,18 @@ class rs_protein_info(C.Structure):
                 ("device_bytes", C.c_size_t)]
 
 
+class rs_pair(C.Structure):
+    _fields_ = [("prot", C.c_void_p), ("L", C.c_int32), ("lig_xyz", C.c_void_p),
+                ("lig_q", C.c_void_p), ("P", C.c_int64), ("quat", C.c_void_p),
+                ("trans", C.c_void_p), ("E_out", C.c_void_p), ("flags_out", C.c_void_p)]
+
+
+class rs_batch_info(C.Structure):
+    _fields_ = [("npairs", C.c_int32), ("ngroups", C.c_int32), ("nitems", C.c_int32),
+                ("grid", C.c_int32), ("threads", C.c_int32), ("atoms_per_item", C.c_int32),
+                ("tune_ms", C.c_double)]
+
+
 def _load() -> C.CDLL:
     path = os.environ.get("RS_LIBRARY") or _build.build()
     lib = C.CDLL(path)
@@ -71,6 +83,10 @@ def _load() -> C.CDLL:
         "rs_energy_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
         "rs_energy_grad_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
         "rs_energy_poses_noalloc": (st, [vp, i32, vp, vp, i64, vp, vp, vp, vp, vp]),
+        "rs_batch_create": (st, [vp, i32, C.POINTER(rs_pair), i32, C.POINTER(vp)]),
+        "rs_batch_run": (st, [vp, vp]),
+        "rs_batch_free": (None, [vp]),
+        "rs_batch_get_info": (st, [vp, C.POINTER(rs_batch_info)]),
         "rs_stats_kernel_launches": (C.c_ulonglong, []),
         "rs_timing_enable": (st, [C.c_int]),
         "rs_timing_reset": (st, []),
@@ -274,6 +290,37 @@ def rs_energy_poses_noalloc(prot, lig_xyz, lig_q, quat, trans, E_out=None, flags
     _check(_lib.rs_energy_poses_noalloc(prot, L, _ptr(lx), _ptr(lq), P, _ptr(r), _ptr(t),
                                         _ptr(E), _ptr(f), _stream_ptr(stream)))
     return E, f
+
+
+def rs_batch_create(ctx: int, pairs: list, autotune: bool = True):
+    """pairs: list of dicts with keys prot (handle), lig_xyz, lig_q, quat, trans, E_out,
+    flags_out (CUDA tensors; outputs preallocated).  Returns (handle, keepalive)."""
+    arr = (rs_pair * len(pairs))()
+    keep = []
+    for i, p in enumerate(pairs):
+        lx, lq = _dev(p["lig_xyz"], np.float64), _dev(p["lig_q"], np.float64)
+        qu, tr = _dev(p["quat"], np.float64), _dev(p["trans"], np.float64)
+        keep += [lx, lq, qu, tr, p["E_out"], p.get("flags_out")]
+        arr[i] = rs_pair(p["prot"], int(lq.shape[0]), _ptr(lx), _ptr(lq), int(qu.shape[0]),
+                         _ptr(qu), _ptr(tr), _ptr(p["E_out"]),
+                         _ptr(p["flags_out"]) if p.get("flags_out") is not None else None)
+    h = C.c_void_p()
+    _check(_lib.rs_batch_create(ctx, len(pairs), arr, 1 if autotune else 0, C.byref(h)))
+    return h.value, keep
+
+
+def rs_batch_run(batch: int, stream=None) -> None:
+    _check(_lib.rs_batch_run(batch, _stream_ptr(stream)))
+
+
+def rs_batch_free(batch: int) -> None:
+    _lib.rs_batch_free(batch)
+
+
+def rs_batch_get_info(batch: int) -> dict:
+    info = rs_batch_info()
+    _check(_lib.rs_batch_get_info(batch, C.byref(info)))
+    return {k: getattr(info, k) for k, _ in info._fields_}
 
 
 def rs_stats_kernel_launches() -> int:
