@@ -153,6 +153,22 @@ rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
                                double* E_out, double* dE_dt, double* dE_dw,
                                uint8_t* flags_out, int mem_flags, void* stream);
 
+/* Constrained energy minimisation of Eq. Energy_Min (Sec. 3.4) by projected
+ * gradient descent on (translation, rotation vector), `nsteps` steps for every
+ * pose.  Each step: gradient g by rs_energy_grad_poses; trial poses
+ * (t - s eta_t g_t/|g_t|, w - s eta_r g_w/|g_w|) with s = 1, 1/2, ..., 2^-max_halvings;
+ * the first trial that is feasible (no flag) and does not raise E replaces the
+ * pose, otherwise the pose is kept.  All arrays are device memory:
+ *   rotvec, trans : [P][3] in/out (updated in place)
+ *   E_out, flags_out : [P] energy and flags of the final poses
+ *   accepted_out  : [P] int32, halving level accepted at the last step, -1 if kept
+ * Runs on the context's stream, ordered after `stream` and before later work on
+ * it; returns when the work is enqueued. */
+rs_status rs_pgd_run(rs_ctx* ctx, const rs_protein* prot, int32_t L, const double* lig_xyz,
+                     const double* lig_q, int64_t P, double* rotvec, double* trans,
+                     int32_t nsteps, double eta_t, double eta_r, int32_t max_halvings,
+                     double* E_out, uint8_t* flags_out, int32_t* accepted_out, void* stream);
+
 /* ------------------------------------------------------------- batching */
 /* One protein-ligand pair of a batch.  All arrays are device memory on the
  * context's GPU; the pair's protein must be Tucker-reduced (tucker_cap > 0). */

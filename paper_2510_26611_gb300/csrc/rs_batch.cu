@@ -18,67 +18,15 @@
 #include "rs_diag.cuh"
 #include "rs_eval.cuh"
 #include "rs_pose_dev.cuh"
+#include "rs_batch_dev.cuh"
 
 namespace rs {
 namespace {
-
-struct PairDesc {
-    ProteinView prot;
-    LigandView lig;
-    const double* rot;
-    const double* trans;
-    long long P;
-    double* E;
-    uint8_t* flags;
-};
-
-struct BatchItem {
-    int pair;
-    int PB;
-    long long p0;
-};
-
-template <int RP, int NT>
-__global__ void __launch_bounds__(NT) k_eval_batch(const PairDesc* __restrict__ pairs,
-                                                   const BatchItem* __restrict__ items, int nitems,
-                                                   int* __restrict__ counter) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int cur;
-    __shared__ __align__(16) PairDesc pd;
-    while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = cur;
-        if (it >= nitems) break;
-        const BatchItem bi = items[it];
-        const int* src = (const int*)(pairs + bi.pair);
-        for (int e = threadIdx.x; e < (int)(sizeof(PairDesc) / sizeof(int)); e += NT)
-            ((int*)&pd)[e] = src[e];
-        __syncthreads();
-        wform_block<RP, false, NT>(pd.prot, pd.lig, pd.rot, pd.trans, pd.P, bi.PB, bi.p0, pd.E,
-                                   pd.flags, nullptr, nullptr, smem);
-    }
-}
-
-struct Shape {
-    int nt;      // threads per CTA
-    int atoms;   // target atoms per item
-};
 
 const Shape kCandidates[] = {{128, 256}, {128, 512}, {128, 1024}, {256, 512}, {256, 1024}};
 
 std::mutex g_tune_mu;
 std::map<int, Shape> g_tuned;  // padded rank -> best shape (process-wide cache)
-
-int pb_for(int L, int atoms) { return std::min(128, std::max(1, atoms / L)); }
-
-template <int RP, int NT>
-size_t batch_smem(const std::vector<int>& Ls, int atoms) {
-    size_t m = 0;
-    for (int L : Ls) m = std::max(m, wform_smem<RP, false, NT>(pb_for(L, atoms), L));
-    return m;
-}
 
 struct Group {
     int RP;
@@ -250,6 +198,14 @@ void batch_destroy(rs_batch* B) {
 }
 
 }  // namespace
+
+void batch_shape_for(int RP, int* nt, int* atoms) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(RP);
+    *nt = it != g_tuned.end() ? it->second.nt : 128;
+    *atoms = it != g_tuned.end() ? it->second.atoms : 512;
+}
+
 }  // namespace rs
 
 extern "C" {

@@ -123,6 +123,9 @@ struct rs_ctx {
     size_t lig_bytes = 0;
     void* io_buf = nullptr;
     size_t io_bytes = 0;
+    // Projected-gradient workspace (per-pose state of rs_pgd_run).
+    void* pgd_buf = nullptr;
+    size_t pgd_bytes = 0;
     // Build workspace, grown to the largest build seen (one build at a time).
     void* ws_buf = nullptr;
     size_t ws_bytes = 0;

@@ -27,11 +27,12 @@ __global__ void __launch_bounds__(NT) k_eval_wform(ProteinView P, LigandView lig
                                                    double* __restrict__ E,
                                                    uint8_t* __restrict__ flags,
                                                    double* __restrict__ gt,
-                                                   double* __restrict__ gw) {
+                                                   double* __restrict__ gw,
+                                                   const uint8_t* __restrict__ skip) {
     extern __shared__ __align__(16) unsigned char smem[];
     const long long nblocks = (Ptot + PB - 1) / PB;
     for (long long pb = blockIdx.x; pb < nblocks; pb += gridDim.x)
-        wform_block<RP, GRAD, NT>(P, lig, rot, trans, Ptot, PB, pb * PB, E, flags, gt, gw, smem);
+        wform_block<RP, GRAD, NT>(P, lig, rot, trans, Ptot, PB, pb * PB, E, flags, gt, gw, smem, skip);
 }
 
 // --------------------------------------------------------------- canonical path
@@ -45,7 +46,8 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
                                                     double* __restrict__ E,
                                                     uint8_t* __restrict__ flags,
                                                     double* __restrict__ gt,
-                                                    double* __restrict__ gw) {
+                                                    double* __restrict__ gw,
+                                                    const uint8_t* __restrict__ skip) {
     constexpr int NC = GRAD ? 7 : 1;
     extern __shared__ __align__(16) unsigned char smem[];
     PoseSetup* ps = (PoseSetup*)smem;
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
         for (int pl = threadIdx.x; pl < PB; pl += blockDim.x) {
             long long p = p0 + pl;
             pflag[pl] = 0;
-            if (p < Ptot) setup_pose(P, rot, trans, p, GRAD, ps[pl]);
+            if (p < Ptot && !(skip && skip[p])) setup_pose(P, rot, trans, p, GRAD, ps[pl]);
             else ps[pl].valid = 0;
         }
         __syncthreads();
@@ -229,7 +231,7 @@ rs_status launch_tucker(const EvalLaunch& a, cudaStream_t st) {
     {
         ::rs::KernelTimer kt__(kname, st, work, true, a.events);
         kern<<<(unsigned)grid, 128, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
-                                              a.gt, a.gw);
+                                              a.gt, a.gw, a.skip);
     }
     RS_TRY_CUDA(cudaGetLastError());
     return RS_OK;
@@ -262,7 +264,7 @@ rs_status launch_canon(const EvalLaunch& a, cudaStream_t st) {
     {
         ::rs::KernelTimer kt__(kname, st, work, true, a.events);
         kern<<<(unsigned)grid, 256, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,
-                                              a.gt, a.gw);
+                                              a.gt, a.gw, a.skip);
     }
     RS_TRY_CUDA(cudaGetLastError());
     return RS_OK;

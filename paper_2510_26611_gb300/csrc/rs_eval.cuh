@@ -18,6 +18,7 @@ struct EvalLaunch {
     int PB = 0;                     // poses per block (0: heuristic)
     int grid = 0;                   // CTAs (0: persistent, fill the GPU)
     bool events = true;             // allow timing events (off for the no-allocation path)
+    const uint8_t* skip = nullptr;  // [P] nonzero: skip the pose, leave its outputs untouched
 };
 
 rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, double* y64,

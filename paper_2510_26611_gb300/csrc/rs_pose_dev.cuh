@@ -121,6 +121,7 @@ __device__ void reduce_poses(const ProteinView& P, int PB, int L, long long p0, 
     for (int pl = warp; pl < PB; pl += nw) {
         long long p = p0 + pl;
         if (p >= Ptot) break;
+        if (!ps[pl].valid) continue;  // skipped pose: outputs untouched
         double s[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) s[c] = 0.0;
@@ -160,7 +161,8 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
                                             const double* __restrict__ trans, long long Ptot,
                                             int PB, long long p0, double* __restrict__ E,
                                             uint8_t* __restrict__ flags, double* __restrict__ gt,
-                                            double* __restrict__ gw, unsigned char* smem) {
+                                            double* __restrict__ gw, unsigned char* smem,
+                                            const uint8_t* __restrict__ skip = nullptr) {
     using dev::F2;
     constexpr int NC = GRAD ? 7 : 1;
     constexpr int NV = GRAD ? 4 : 2;  // per-thread smem planes: v1h, v1l (, dv1h, dv1l)
@@ -174,7 +176,7 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
     for (int pl = tid; pl < PB; pl += blockDim.x) {
         long long p = p0 + pl;
         pflag[pl] = 0;
-        if (p < Ptot) setup_pose(P, rot, trans, p, GRAD, ps[pl]);
+        if (p < Ptot && !(skip && skip[p])) setup_pose(P, rot, trans, p, GRAD, ps[pl]);
         else ps[pl].valid = 0;
     }
     __syncthreads();

@@ -83,6 +83,8 @@ def _load() -> C.CDLL:
         "rs_energy_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
         "rs_energy_grad_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
         "rs_energy_poses_noalloc": (st, [vp, i32, vp, vp, i64, vp, vp, vp, vp, vp]),
+        "rs_pgd_run": (st, [vp, vp, i32, vp, vp, i64, vp, vp, i32, C.c_double, C.c_double, i32,
+                            vp, vp, vp, vp]),
         "rs_batch_create": (st, [vp, i32, C.POINTER(rs_pair), i32, C.POINTER(vp)]),
         "rs_batch_run": (st, [vp, vp]),
         "rs_batch_free": (None, [vp]),
@@ -290,6 +292,28 @@ def rs_energy_poses_noalloc(prot, lig_xyz, lig_q, quat, trans, E_out=None, flags
     _check(_lib.rs_energy_poses_noalloc(prot, L, _ptr(lx), _ptr(lq), P, _ptr(r), _ptr(t),
                                         _ptr(E), _ptr(f), _stream_ptr(stream)))
     return E, f
+
+
+def rs_pgd_run(ctx: int, prot: int, lig_xyz, lig_q, rotvec, trans, nsteps: int,
+               eta_t: float = 0.1, eta_r: float = 0.02, max_halvings: int = 5, stream=None):
+    """Projected gradient descent of Eq. Energy_Min; rotvec and trans (CUDA float64
+    tensors [P, 3]) are updated in place.  Returns (E, flags, accepted_level)."""
+    import torch
+    for x in (lig_xyz, lig_q, rotvec, trans):
+        if not _is_cuda(x):
+            raise RSError(RS_ERR_INVALID, "rs_pgd_run takes CUDA tensors")
+    if rotvec.dtype != torch.float64 or trans.dtype != torch.float64 or not rotvec.is_contiguous() \
+            or not trans.is_contiguous():
+        raise RSError(RS_ERR_INVALID, "rotvec and trans must be contiguous float64 (updated in place)")
+    lx, lq = _dev(lig_xyz, np.float64), _dev(lig_q, np.float64)
+    P, L = int(rotvec.shape[0]), int(lq.shape[0])
+    E = torch.empty(P, dtype=torch.float64, device=rotvec.device)
+    f = torch.empty(P, dtype=torch.uint8, device=rotvec.device)
+    acc = torch.empty(P, dtype=torch.int32, device=rotvec.device)
+    _check(_lib.rs_pgd_run(ctx, prot, L, _ptr(lx), _ptr(lq), P, _ptr(rotvec), _ptr(trans), nsteps,
+                           eta_t, eta_r, max_halvings, _ptr(E), _ptr(f), _ptr(acc),
+                           _stream_ptr(stream)))
+    return E, f, acc
 
 
 def rs_batch_create(ctx: int, pairs: list, autotune: bool = True):
