@@ -97,7 +97,12 @@ typedef struct rs_protein_info {
 /* ---------------------------------------------------------------- context */
 void        rs_params_default(rs_params* p);
 /* Creates a context on CUDA device `device` (made current for every call that
- * uses the context).  *out receives the handle. */
+ * uses the context).  *out receives the handle.  A context owns device scratch
+ * (prepared ligand, staging, the per-atom arrays of the pose path) that every
+ * call through it reuses: calls through one context must not run on the GPU at
+ * the same time (issue them on one stream, or order the streams); use one
+ * context per concurrent stream.  Growing the scratch frees the old buffer,
+ * which waits for the device. */
 rs_status   rs_ctx_create(int device, rs_ctx** out);
 void        rs_ctx_destroy(rs_ctx* ctx);
 /* Message of the last failing call on this thread ("" if none). */
@@ -132,8 +137,12 @@ rs_status rs_protein_get_table(const rs_protein* p, double* t, double* a, uint8_
  *   P        : poses, 0 <= P <= 2^31-1 (P = 0 is a no-op)
  *   quat     : [P][4] float64 (w,x,y,z); trans: [P][3] float64
  *   E_out    : [P] float64;  flags_out: [P] uint8 (RS_FLAG_* bits), may be NULL
- * Evaluation is FP32 with FP64 per-pose accumulation; vdW distances within
- * 1e-5 relative of sigma are re-decided in FP64. */
+ * The long range is evaluated on the FP32 pipes in float-pair arithmetic
+ * (about 48 significant bits); atom positions, the short range and the vdW
+ * decisions near sigma are FP64; pose sums are FP64.  For a Tucker-reduced
+ * protein the ligand atoms of all poses are grouped by grid cell first (device
+ * scratch of about 110 bytes per pose-atom, 190 with gradients, in chunks of at
+ * most 2^23 pose-atoms); the results do not depend on that grouping. */
 rs_status rs_energy_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
                           const double* lig_xyz, const double* lig_q, int64_t P,
                           const double* quat, const double* trans,
@@ -231,6 +240,83 @@ rs_status rs_energy_poses_noalloc(const rs_protein* prot, int32_t L, const doubl
                                   const double* lig_q, int64_t P, const double* quat,
                                   const double* trans, double* E_out, uint8_t* flags_out,
                                   void* stream);
+
+/* -------------------------------------------------------------- serving */
+/* A request loop with continuous batching (the paper has no counterpart: this is
+ * the deployment of Algorithm PLIE for a stream of docking jobs).  A server owns
+ * its own context on one GPU and one scheduler thread.  Requests of any protein,
+ * ligand and grid size are queued by rs_serve_submit; the scheduler admits them in
+ * arrival order while a device-memory budget allows, keeps each protein's RS factors
+ * resident (keyed by protein_id; least recently used idle proteins are evicted
+ * under memory pressure), and launches all newly admitted requests together as one
+ * batched pose launch (one per padded Tucker rank), on alternating streams, so
+ * requests that arrive while others run on the GPU are admitted and overlap with
+ * them.  A request's energies and flags equal rs_energy_poses bit for bit, alone or
+ * in any mix. */
+typedef struct rs_server rs_server;
+
+typedef struct rs_request {
+    uint64_t protein_id;     /* cache key; 0: build for this request only       */
+    int32_t N;               /* protein atoms (read only when the key misses)   */
+    const double* prot_xyz;  /* [N][3] host                                     */
+    const double* prot_q;    /* [N] host                                        */
+    rs_params params;        /* Algorithm TEP parameters of the protein         */
+    int32_t L;               /* ligand atoms, 1..4096                           */
+    const double* lig_xyz;   /* [L][3] host                                     */
+    const double* lig_q;     /* [L] host                                        */
+    int64_t P;               /* poses, 0..2^26                                  */
+    const double* quat;      /* [P][4] host (w,x,y,z)                           */
+    const double* trans;     /* [P][3] host                                     */
+} rs_request;
+
+typedef struct rs_result {
+    rs_status status;        /* RS_OK, RS_ERR_OOM (over budget / allocation failed), ... */
+    int64_t t_submit_ns;     /* steady-clock times: submitted, admitted,        */
+    int64_t t_admit_ns;      /* its launch enqueued, results copied out         */
+    int64_t t_start_ns;
+    int64_t t_end_ns;
+    char message[160];       /* error text when status != RS_OK                 */
+} rs_result;
+
+typedef struct rs_serve_params {
+    uint64_t mem_budget_bytes;     /* device bytes for factors + request buffers; 0: half
+                                      of the free device memory at creation             */
+    int32_t max_queue;             /* queued requests before submit returns RS_ERR_BUSY  */
+    int32_t max_inflight_launches; /* launches on the GPU at once (>= 1)                 */
+    int32_t idle_wait_ms;          /* scheduler sleep when idle                          */
+    int32_t inject_alloc_failures; /* test hook: fail the next k device allocations      */
+} rs_serve_params;
+
+typedef struct rs_serve_stats {
+    uint64_t done, failed;         /* finished requests                              */
+    uint64_t launches;             /* batched launches                               */
+    uint64_t builds, cache_hits;   /* protein builds; requests served from the cache */
+    uint64_t evictions;            /* cached proteins freed under memory pressure    */
+    uint64_t queued, cached_proteins;
+    uint64_t budget_bytes, used_bytes;
+    double   mean_requests_per_launch;
+} rs_serve_stats;
+
+void      rs_serve_params_default(rs_serve_params* p);
+/* Checks a request's sizes and pointers without a GPU (RS_OK or RS_ERR_INVALID). */
+rs_status rs_request_validate(const rs_request* r);
+rs_status rs_serve_create(int device, const rs_serve_params* params, rs_server** out);
+/* Queues a request.  Every pointer of the request and E_out [P] / flags_out [P]
+ * (may be NULL) are host memory owned by the caller, which keeps them valid and
+ * untouched until the request is finished (poll/wait returns it) or cancelled.
+ * Returns RS_ERR_BUSY when the queue is full. */
+rs_status rs_serve_submit(rs_server* s, const rs_request* r, double* E_out, uint8_t* flags_out,
+                          uint64_t* req_id);
+/* RS_ERR_NOT_READY while pending; otherwise RS_OK and fills `out` (may be NULL)
+ * and releases the request id.  The request's own outcome is out->status. */
+rs_status rs_serve_poll(rs_server* s, uint64_t req_id, rs_result* out);
+/* Like poll, waiting at most timeout_ms (RS_ERR_TIMEOUT if still pending). */
+rs_status rs_serve_wait(rs_server* s, uint64_t req_id, int32_t timeout_ms, rs_result* out);
+/* Removes a request that has not been admitted yet (RS_ERR_BUSY once admitted). */
+rs_status rs_serve_cancel(rs_server* s, uint64_t req_id);
+rs_status rs_serve_get_stats(rs_server* s, rs_serve_stats* out);
+/* Finishes launched work, drops queued requests and frees everything. */
+void      rs_serve_destroy(rs_server* s);
 
 /* ----------------------------------------------------------- diagnostics */
 /* These have no counterpart in the paper: they support measurement.

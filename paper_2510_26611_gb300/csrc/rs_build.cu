@@ -1120,10 +1120,6 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
                               Scratch& S) {
     const int N = P->N, Rl = P->R_l, n = P->n;
     const double b = P->b, h = P->h;
-    if (n > 4097) {
-        set_error("Tucker reduction supports n <= 4097 in this build (n=%d)", n);
-        return RS_ERR_UNSUPPORTED;
-    }
     if (cap > RS_MAX_TUCKER) {
         set_error("tucker_cap %d exceeds %d", cap, RS_MAX_TUCKER);
         return RS_ERR_INVALID;

@@ -126,6 +126,9 @@ struct rs_ctx {
     // Projected-gradient workspace (per-pose state of rs_pgd_run).
     void* pgd_buf = nullptr;
     size_t pgd_bytes = 0;
+    // Per-atom arrays of the cell-grouped pose path.
+    void* eval_buf = nullptr;
+    size_t eval_bytes = 0;
     // Build workspace, grown to the largest build seen (one build at a time).
     void* ws_buf = nullptr;
     size_t ws_bytes = 0;
@@ -140,11 +143,16 @@ rs_status device_alloc(rs_protein* p, void** ptr, size_t bytes);
 namespace rs {
 namespace dev {
 
+// The pair arithmetic below is written with explicit round-to-nearest intrinsics:
+// the compiler may not fuse a product into a following sum there, which keeps the
+// error-free transformations exact and makes every kernel that uses them compute
+// the same bits from the same inputs.
+
 // Error-free sum of two floats (Knuth TwoSum).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 // Unevaluated float pair hi + lo (about 48 significant bits).
@@ -153,17 +161,17 @@ struct F2 {
 };
 
 __device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
-    float s = a + b;
-    return {s, b - (s - a)};
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 
 // Pair value a + f*d with a, d pairs and f a float in [0, 1].
 __device__ __forceinline__ F2 df_lerp(F2 a, F2 d, float f) {
-    float p = f * d.h;
-    float ep = fmaf(f, d.h, -p);
+    float p = __fmul_rn(f, d.h);
+    float ep = __fmaf_rn(f, d.h, -p);
     float s, e;
     two_sum(a.h, p, s, e);
-    float lo = e + ep + fmaf(f, d.l, a.l);
+    float lo = __fadd_rn(__fadd_rn(e, ep), __fmaf_rn(f, d.l, a.l));
     return fast_two_sum(s, lo);
 }
 
@@ -171,12 +179,12 @@ __device__ __forceinline__ F2 df_lerp(F2 a, F2 d, float f) {
 // Dot2 (Ogita, Rump, Oishi 2005): the rounding errors of the leading product and
 // sum are carried in acc.l (the lo*lo term is dropped).
 __device__ __forceinline__ void df_fma_acc(F2& acc, F2 x, F2 y) {
-    float p = x.h * y.h;
-    float ep = fmaf(x.h, y.h, -p);
+    float p = __fmul_rn(x.h, y.h);
+    float ep = __fmaf_rn(x.h, y.h, -p);
     float s, e;
     two_sum(acc.h, p, s, e);
     acc.h = s;
-    acc.l += e + ep + fmaf(x.h, y.l, x.l * y.h);
+    acc.l = __fadd_rn(acc.l, __fadd_rn(__fadd_rn(e, ep), __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.h))));
 }
 
 // Accumulator of float values carried as an unevaluated pair hi + lo.

@@ -284,6 +284,7 @@ rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* 
 
 rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st) {
     if (a.P <= 0) return RS_OK;
+    if (a.prot.kind == 1 && a.ws && a.PB == 0 && a.grid == 0) return launch_sorted(a, grad, st);
     if (a.prot.kind == 0) return grad ? launch_canon<true>(a, st) : launch_canon<false>(a, st);
     switch (a.prot.R) {
 #define RS_CASE(R) \
@@ -382,6 +383,11 @@ rs_status run_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L, const double
     a.flags = (mem_flags == RS_MEM_HOST || flags_out) ? d_flags : nullptr;
     a.gt = d_gt;
     a.gw = d_gw;
+    if (prot->view.kind == 1) {
+        RS_TRY(ensure_buffer(&ctx->eval_buf, &ctx->eval_bytes, sorted_scratch_bytes(P, L, prot->n, grad)));
+        a.ws = ctx->eval_buf;
+        a.ws_bytes = ctx->eval_bytes;
+    }
     RS_TRY(launch_eval(a, grad, st));
     if (mem_flags == RS_MEM_HOST) {
         RS_TRY_CUDA(cudaMemcpyAsync(E_out, d_E, (size_t)P * 8, cudaMemcpyDeviceToHost, st));

@@ -19,12 +19,19 @@ struct EvalLaunch {
     int grid = 0;                   // CTAs (0: persistent, fill the GPU)
     bool events = true;             // allow timing events (off for the no-allocation path)
     const uint8_t* skip = nullptr;  // [P] nonzero: skip the pose, leave its outputs untouched
+    void* ws = nullptr;             // scratch of the cell-grouped Tucker path (NULL: one pass
+    size_t ws_bytes = 0;            //   per block of poses, no scratch)
 };
 
 rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, double* y64,
                              double* q64, cudaStream_t st, bool events = true);
 rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st);
 size_t ligand_scratch_bytes(int L);
+// Cell-grouped Tucker path (rs_sorted.cu): scratch for P poses (capped at one chunk)
+// and the number of poses one chunk of ws_bytes holds.
+size_t sorted_scratch_bytes(long long P, int L, int n, bool grad);
+long long sorted_chunk_poses(size_t ws_bytes, int L, int n, bool grad);
+rs_status launch_sorted(const EvalLaunch& a, bool grad, cudaStream_t st);
 LigandView carve_ligand(void* base, int L);
 
 }  // namespace rs

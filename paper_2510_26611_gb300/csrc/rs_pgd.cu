@@ -157,6 +157,15 @@ extern "C" rs_status rs_pgd_run(rs_ctx* ctx, const rs_protein* prot, int32_t L, 
     g.gt = gt;
     g.gw = gw;
     g.events = false;
+    if (prot->view.kind == 1) {  // scratch of the cell-grouped path, shared by both passes
+        s = ensure_buffer(&ctx->eval_buf, &ctx->eval_bytes, sorted_scratch_bytes(P, L, prot->n, true));
+        if (s != RS_OK) {
+            cleanup();
+            return s;
+        }
+        g.ws = ctx->eval_buf;
+        g.ws_bytes = ctx->eval_bytes;
+    }
     EvalLaunch e = g;
     e.rot = tq;
     e.trans = ttr;

@@ -40,11 +40,12 @@ __device__ __forceinline__ void setup_pose(const ProteinView& P, const double* _
 // Short-range part and vdW decision for one atom; candidates split over
 // `nl` cooperating lanes starting at `lane`.  Distances are screened in FP32;
 // pairs inside the cutoff, and vdW decisions within 1e-4 relative of sigma^2,
-// are taken in FP64 from x = t + R y evaluated in FP64.
+// are taken in FP64 from x = t + R y evaluated in FP64.  phi and g are added to
+// (callers pass zeros); products are fused explicitly, so every kernel that
+// inlines this computes the same bits.
 template <bool GRAD>
-__device__ __forceinline__ void short_vdw(const ProteinView& P, const float xf[3],
-                                          const double x64[3], int lane, int nl, double& phi,
-                                          double g[3], int& clash) {
+__device__ __noinline__ void short_vdw(const ProteinView& P, const float xf[3], const double x64[3],
+                                       int lane, int nl, double& phi, double g[3], int& clash) {
     float u0 = (xf[0] - P.co0) * P.inv_cell, u1 = (xf[1] - P.co1) * P.inv_cell,
           u2 = (xf[2] - P.co2) * P.inv_cell;
     u0 = fminf(fmaxf(u0, -4.f), (float)P.nc0 + 4.f);
@@ -69,31 +70,55 @@ __device__ __forceinline__ void short_vdw(const ProteinView& P, const float xf[3
                 bool near_rc = d2 < P.rc2_hi;
                 if (!(near_sig || near_rc)) continue;
                 D4 a64 = P.atoms64[k];
-                double f0 = x64[0] - a64.x, f1 = x64[1] - a64.y, f2 = x64[2] - a64.z;
-                double d2d = f0 * f0 + f1 * f1 + f2 * f2;
+                double f0 = __dsub_rn(x64[0], a64.x), f1 = __dsub_rn(x64[1], a64.y),
+                       f2 = __dsub_rn(x64[2], a64.z);
+                double d2d = fma(f2, f2, fma(f1, f1, __dmul_rn(f0, f0)));
                 if (near_sig && (d2 < P.sig2_lo || d2d < P.sig2)) clash = 1;
                 if (near_rc && d2d < P.rc2) {
                     // cubic Hermite interpolation of the tabulated radial function (FP64)
-                    double xs = d2d * P.stab_inv_h;
+                    double xs = __dmul_rn(d2d, P.stab_inv_h);
                     int j = min((int)xs, P.stab_n - 2);
-                    double u = xs - j;
+                    double u = __dsub_rn(xs, (double)j);
                     double2 A = P.stab[j], B = P.stab[j + 1];
-                    double u2 = u * u, u3 = u2 * u;
-                    double fv = (2.0 * u3 - 3.0 * u2 + 1.0) * A.x + (u3 - 2.0 * u2 + u) * A.y +
-                                (3.0 * u2 - 2.0 * u3) * B.x + (u3 - u2) * B.y;
-                    phi += a64.w * fv;
+                    double u2 = __dmul_rn(u, u), u3 = __dmul_rn(u2, u);
+                    // Hermite basis h00 = 2u^3 - 3u^2 + 1, h10 = u^3 - 2u^2 + u,
+                    // h01 = 3u^2 - 2u^3, h11 = u^3 - u^2
+                    double h00 = fma(2.0, u3, fma(-3.0, u2, 1.0));
+                    double h10 = fma(-2.0, u2, __dadd_rn(u3, u));
+                    double h01 = fma(-2.0, u3, __dmul_rn(3.0, u2));
+                    double h11 = __dsub_rn(u3, u2);
+                    double fv = fma(h11, B.y, fma(h01, B.x, fma(h10, A.y, __dmul_rn(h00, A.x))));
+                    phi = fma(a64.w, fv, phi);
                     if constexpr (GRAD) {
-                        double dp = (6.0 * u2 - 6.0 * u) * (A.x - B.x) + (3.0 * u2 - 4.0 * u + 1.0) * A.y +
-                                    (3.0 * u2 - 2.0 * u) * B.y;
-                        double fgr = 2.0 * a64.w * dp * P.stab_inv_h;  // grad_x f(|x-x_m|^2)
-                        g[0] += fgr * f0;
-                        g[1] += fgr * f1;
-                        g[2] += fgr * f2;
+                        // d/du of the basis: 6u^2 - 6u, 3u^2 - 4u + 1, -(6u^2 - 6u), 3u^2 - 2u
+                        double d00 = fma(6.0, u2, -6.0 * u);
+                        double d10 = fma(3.0, u2, fma(-4.0, u, 1.0));
+                        double d11 = fma(3.0, u2, -2.0 * u);
+                        double dp = fma(d11, B.y, fma(d10, A.y, __dmul_rn(d00, __dsub_rn(A.x, B.x))));
+                        // grad_x f(|x - x_m|^2) = 2 f'(s) (x - x_m)
+                        double fgr = __dmul_rn(__dmul_rn(2.0 * a64.w, dp), P.stab_inv_h);
+                        g[0] = fma(fgr, f0, g[0]);
+                        g[1] = fma(fgr, f1, g[1]);
+                        g[2] = fma(fgr, f2, g[2]);
                     }
                 }
             }
         }
     }
+}
+
+// Short-range sums and flag bits of one atom (FP32 copy of the position for the
+// screen, FP64 for the decisions and values).
+template <bool GRAD>
+__device__ __forceinline__ int atom_short(const ProteinView& P, const double x64[3], const bool ins[3],
+                                          double& phs, double gs[3]) {
+    float xf[3];
+    for (int a = 0; a < 3; ++a) xf[a] = (float)x64[a];
+    int clash = 0;
+    short_vdw<GRAD>(P, xf, x64, 0, 1, phs, gs, clash);
+    int fl = clash ? RS_FLAG_CLASH : 0;
+    if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
+    return fl;
 }
 
 // FP64 atom position x = R y + t (the interpolation coordinates and the
@@ -102,13 +127,80 @@ __device__ __forceinline__ void atom_position(const PoseSetup& q, const double* 
                                               double x64[3]) {
     double y0 = y64[0], y1 = y64[1], y2 = y64[2];
     for (int r = 0; r < 3; ++r)
-        x64[r] = q.t[r] + (q.R[3 * r] * y0 + q.R[3 * r + 1] * y1 + q.R[3 * r + 2] * y2);
+        x64[r] = __dadd_rn(q.t[r], fma(q.R[3 * r + 2], y2, fma(q.R[3 * r + 1], y1, __dmul_rn(q.R[3 * r], y0))));
+}
+
+// Geometry of ligand atom j in pose q: rotated offset R y in FP32 (torque arm of
+// the gradient), FP64 position, and per axis the interpolation cell, fraction and
+// whether the coordinate lies inside [-b, b].
+__device__ __forceinline__ void atom_geometry(const ProteinView& P, const LigandView& lig,
+                                              const PoseSetup& q, int j, float ry[3],
+                                              double x64[3], int ci[3], float cf[3], bool ins[3]) {
+    float4 yq = lig.y[j];
+    for (int r = 0; r < 3; ++r)
+        ry[r] = __fmaf_rn(q.Rf[3 * r + 2], yq.z, __fmaf_rn(q.Rf[3 * r + 1], yq.y, __fmul_rn(q.Rf[3 * r], yq.x)));
+    atom_position(q, lig.y64 + 3 * j, x64);
+    for (int a = 0; a < 3; ++a) dev::axis_cell(x64[a], P.b, P.inv_h, P.n, ci[a], cf[a], ins[a]);
+}
+
+// Per-atom contributions to the pose sums from the long-range value (pair sums
+// phi, g1..g3 of the W-form loop) and the short-range sums: q_j phi_j and, for
+// gradients, q_j grad phi_j and the torque arm (R y_j) x q_j grad phi_j.
+template <bool GRAD>
+__device__ __forceinline__ void atom_contrib(const ProteinView& P, dev::F2 phi, dev::F2 g1, dev::F2 g2,
+                                             dev::F2 g3, double phs, const double gs[3], double qj,
+                                             const float ry[3], double* cj) {
+    double ph = __dadd_rn(__dadd_rn((double)phi.h, (double)phi.l), phs);
+    cj[0] = __dmul_rn(qj, ph);
+    if constexpr (GRAD) {
+        double gl0 = __dadd_rn(__dmul_rn(__dadd_rn((double)g1.h, (double)g1.l), P.inv_h), gs[0]);
+        double gl1 = __dadd_rn(__dmul_rn(__dadd_rn((double)g2.h, (double)g2.l), P.inv_h), gs[1]);
+        double gl2 = __dadd_rn(__dmul_rn(__dadd_rn((double)g3.h, (double)g3.l), P.inv_h), gs[2]);
+        double g0 = __dmul_rn(qj, gl0), g1d = __dmul_rn(qj, gl1), g2d = __dmul_rn(qj, gl2);
+        cj[1] = g0;
+        cj[2] = g1d;
+        cj[3] = g2d;
+        double r0 = ry[0], r1 = ry[1], r2 = ry[2];
+        cj[4] = __dsub_rn(__dmul_rn(r1, g2d), __dmul_rn(r2, g1d));
+        cj[5] = __dsub_rn(__dmul_rn(r2, g0), __dmul_rn(r0, g2d));
+        cj[6] = __dsub_rn(__dmul_rn(r0, g1d), __dmul_rn(r1, g0));
+    }
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Sum over the atoms of one pose of its per-atom contributions [L][NC], by one
+// warp: lane-strided partial sums, then a butterfly; every lane ends with s.
+template <int NC>
+__device__ __forceinline__ void pose_sums(const double* __restrict__ cpose, int L, int lane, double s[NC]) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) s[c] = 0.0;
+    for (int j = lane; j < L; j += 32) {
+        const double* cj = cpose + (size_t)j * NC;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s[c] = __dadd_rn(s[c], cj[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) s[c] = warp_sum(s[c]);
+}
+
+// Outputs of one pose from its sums: E, flags and, for gradients, dE/dt and
+// dE/dw = J_l(w)^T tau.
+template <int NC>
+__device__ __forceinline__ void write_pose(const PoseSetup& q, const double s[NC], int pflag, long long p,
+                                           double* __restrict__ E, uint8_t* __restrict__ flags,
+                                           double* __restrict__ gt, double* __restrict__ gw) {
+    E[p] = s[0];
+    if (flags) flags[p] = (uint8_t)pflag;
+    if constexpr (NC == 7) {
+        for (int a = 0; a < 3; ++a) gt[3 * p + a] = s[1 + a];
+        for (int a = 0; a < 3; ++a)
+            gw[3 * p + a] = fma(q.J[6 + a], s[6], fma(q.J[3 + a], s[5], __dmul_rn(q.J[a], s[4])));
+    }
 }
 
 // Reduction of per-atom contributions to per-pose outputs (one warp per pose).
@@ -123,26 +215,8 @@ __device__ void reduce_poses(const ProteinView& P, int PB, int L, long long p0, 
         if (p >= Ptot) break;
         if (!ps[pl].valid) continue;  // skipped pose: outputs untouched
         double s[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) s[c] = 0.0;
-        for (int j = lane; j < L; j += 32) {
-            const double* cj = contrib + ((size_t)pl * L + j) * NC;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) s[c] += cj[c];
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) s[c] = warp_sum(s[c]);
-        if (lane == 0) {
-            E[p] = s[0];
-            if (flags) flags[p] = (uint8_t)pflag[pl];
-            if (NC == 7) {
-                const PoseSetup& q = ps[pl];
-                for (int a = 0; a < 3; ++a) gt[3 * p + a] = s[1 + a];
-                // dE/dw = J_l^T tau
-                for (int a = 0; a < 3; ++a)
-                    gw[3 * p + a] = q.J[a] * s[4] + q.J[3 + a] * s[5] + q.J[6 + a] * s[6];
-            }
-        }
+        pose_sums<NC>(contrib + (size_t)pl * L * NC, L, lane, s);
+        if (lane == 0) write_pose<NC>(ps[pl], s, pflag[pl], p, E, flags, gt, gw);
     }
 }
 
@@ -189,16 +263,12 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
             for (int c = 0; c < NC; ++c) cj[c] = 0.0;
             continue;
         }
-        float4 yq = lig.y[j];
         float ry[3];
-        for (int r = 0; r < 3; ++r)
-            ry[r] = q.Rf[3 * r] * yq.x + q.Rf[3 * r + 1] * yq.y + q.Rf[3 * r + 2] * yq.z;
         int ci[3];
         float cf[3];
         bool ins[3];
         double x64[3];
-        atom_position(q, lig.y64 + 3 * j, x64);
-        for (int a = 0; a < 3; ++a) dev::axis_cell(x64[a], P.b, P.inv_h, P.n, ci[a], cf[a], ins[a]);
+        atom_geometry(P, lig, q, j, ry, x64, ci, cf, ins);
         // v1 (axis 1) into this thread's shared-memory column; v2 (axis 2) in registers
         {
             size_t o = (size_t)ci[0] * RP;
@@ -282,33 +352,11 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
                 dev::df_fma_acc(g3, va, u3);
             }
         }
-        double ph = (double)phi.h + (double)phi.l;
-        double gl[3] = {0.0, 0.0, 0.0};
-        if constexpr (GRAD) {
-            gl[0] = ((double)g1.h + (double)g1.l) * P.inv_h;
-            gl[1] = ((double)g2.h + (double)g2.l) * P.inv_h;
-            gl[2] = ((double)g3.h + (double)g3.l) * P.inv_h;
-        }
         // short range and vdW
-        float xf[3];
-        for (int a = 0; a < 3; ++a) xf[a] = (float)x64[a];
-        int clash = 0;
-        short_vdw<GRAD>(P, xf, x64, 0, 1, ph, gl, clash);
-        int fl = clash ? RS_FLAG_CLASH : 0;
-        if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
+        double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
+        int fl = atom_short<GRAD>(P, x64, ins, phs, gs);
         if (fl) atomicOr(&pflag[pl], fl);
-        double qj = lig.q64[j];
-        cj[0] = qj * ph;
-        if constexpr (GRAD) {
-            double g0 = qj * gl[0], g1d = qj * gl[1], g2d = qj * gl[2];
-            cj[1] = g0;
-            cj[2] = g1d;
-            cj[3] = g2d;
-            double r0 = ry[0], r1 = ry[1], r2 = ry[2];
-            cj[4] = r1 * g2d - r2 * g1d;
-            cj[5] = r2 * g0 - r0 * g2d;
-            cj[6] = r0 * g1d - r1 * g0;
-        }
+        atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, lig.q64[j], ry, cj);
     }
     __syncthreads();
     reduce_poses<NC>(P, PB, L, p0, Ptot, ps, contrib, pflag, E, flags, gt, gw);

@@ -1,0 +1,421 @@
+// Algorithm PLIE (Sec. 3.4) for a Tucker-reduced protein with the ligand atoms of
+// all poses grouped by their interpolation cell along axis 3.
+//
+// The W-form evaluation of one atom reads the whole slab W[i3], D[i3] (4 RP^2
+// floats) of its axis-3 cell.  Taken atom by atom in pose order those reads are
+// scattered over the table and the L1 cache cannot hold them; grouped by cell, a
+// warp stages a slab in shared memory once and every atom of that cell reads it
+// there as a broadcast.  The launch sequence per chunk of poses is
+//   k_sorted_poses   pose setups (rotation, Jacobian) of the chunk
+//   k_sorted_atoms   per atom: FP64 position, cells, fractions, short range and
+//                    vdW (flags), a 48-byte record, and its rank in a per-cell count
+//   k_cell_scan      exclusive scan of the per-cell counts
+//   k_sorted_scatter records to their cell-sorted positions
+//   k_sorted_wform   per warp: a contiguous run of sorted atoms; slab of the current
+//                    cell in shared memory; long range + contributions per atom
+//   k_sorted_reduce  per pose: sums over its atoms (one warp per pose)
+// Every per-atom value is computed by the same helpers, in the same order, as the
+// one-block-per-pose-batch path (wform_block), and the pose sums are taken in the
+// same order, so both paths give the same bits; the order of atoms within a cell
+// (set by atomics) never enters any arithmetic.
+#include <algorithm>
+#include <climits>
+
+#include "rs_common.cuh"
+#include "rs_diag.cuh"
+#include "rs_eval.cuh"
+#include "rs_pose_dev.cuh"
+
+namespace rs {
+namespace {
+
+struct __align__(16) AtomRec {
+    int i1, i2, i3;       // interpolation cells (i3 = n - 1: pose skipped)
+    float f1, f2, f3;     // fractions in the cells
+    int slot;             // pl * L + j within the chunk
+    int bits;             // bit a set: coordinate a inside [-b, b]
+    float ry0, ry1, ry2;  // R y (FP32), the torque arm
+    int rank;             // position among the atoms of its cell
+};
+static_assert(sizeof(AtomRec) == 48, "AtomRec layout");
+
+constexpr int kWarpsPerBlock = 4;
+
+__global__ void k_sorted_poses(ProteinView P, const double* __restrict__ rot,
+                               const double* __restrict__ trans, long long p0, int PC, bool rotvec,
+                               const uint8_t* __restrict__ skip, PoseSetup* __restrict__ ps,
+                               int* __restrict__ pflag) {
+    int pl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pl >= PC) return;
+    long long p = p0 + pl;
+    pflag[pl] = 0;
+    if (!(skip && skip[p])) setup_pose(P, rot, trans, p, rotvec, ps[pl]);
+    else ps[pl].valid = 0;
+}
+
+template <bool GRAD>
+__global__ void k_sorted_atoms(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
+                               int* __restrict__ pflag, AtomRec* __restrict__ rec,
+                               double* __restrict__ shortv, int* __restrict__ count) {
+    const int L = lig.L;
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)PC * L) return;
+    int pl = (int)(g / L), j = (int)(g - (long long)pl * L);
+    const PoseSetup& q = ps[pl];
+    AtomRec r;
+    r.slot = (int)g;
+    if (!q.valid) {
+        r.i3 = P.n - 1;
+        r.rank = atomicAdd(&count[P.n - 1], 1);
+        rec[g] = r;
+        return;
+    }
+    float ry[3];
+    double x64[3];
+    int ci[3];
+    float cf[3];
+    bool ins[3];
+    atom_geometry(P, lig, q, j, ry, x64, ci, cf, ins);
+    double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
+    int fl = atom_short<GRAD>(P, x64, ins, phs, gs);
+    if (fl) atomicOr(&pflag[pl], fl);
+    if constexpr (GRAD) {
+        double4 v = make_double4(phs, gs[0], gs[1], gs[2]);
+        reinterpret_cast<double4*>(shortv)[g] = v;
+    } else {
+        shortv[g] = phs;
+    }
+    r.i1 = ci[0];
+    r.i2 = ci[1];
+    r.i3 = ci[2];
+    r.f1 = cf[0];
+    r.f2 = cf[1];
+    r.f3 = cf[2];
+    r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0);
+    r.ry0 = ry[0];
+    r.ry1 = ry[1];
+    r.ry2 = ry[2];
+    r.rank = atomicAdd(&count[ci[2]], 1);
+    rec[g] = r;
+}
+
+// Exclusive scan of count[0..m) into off[0..m]; one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_cell_scan(int m, const int* __restrict__ count, int* __restrict__ off) {
+    __shared__ int part[1024];
+    const int per = (m + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(m, lo + per);
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += count[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int base = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int i = lo; i < hi; ++i) {
+        off[i] = base;
+        base += count[i];
+    }
+    if (threadIdx.x == 1023) off[m] = part[1023];
+}
+
+__global__ void k_sorted_scatter(long long M, const AtomRec* __restrict__ rec, const int* __restrict__ off,
+                                 AtomRec* __restrict__ srt) {
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M) return;
+    AtomRec r = rec[g];
+    srt[off[r.i3] + r.rank] = r;
+}
+
+// Long range of one atom from its record, with the axis-3 slab of its cell in
+// shared memory (planes Wh, Wl, Dh, Dl of RP x RP floats); writes its contributions.
+template <int RP, bool GRAD>
+__device__ __forceinline__ void sorted_atom(const ProteinView& P, const LigandView& lig, const AtomRec& r,
+                                            const float* __restrict__ slab, const double* __restrict__ shortv,
+                                            double* __restrict__ contrib) {
+    using dev::F2;
+    constexpr int NC = GRAD ? 7 : 1;
+    const bool in1 = r.bits & 1, in2 = r.bits & 2, in3 = r.bits & 4;
+    F2 v2[RP];
+    F2 dv2[GRAD ? RP : 1];
+    {
+        size_t o = (size_t)r.i2 * RP;
+        const float4* vh = (const float4*)(P.Vt[1][0] + o);
+        const float4* vl = (const float4*)(P.Vt[1][1] + o);
+        const float4* dh = (const float4*)(P.Vt[1][2] + o);
+        const float4* dl = (const float4*)(P.Vt[1][3] + o);
+#pragma unroll
+        for (int c4 = 0; c4 < RP / 4; ++c4) {
+            float4 a = __ldg(vh + c4), b = __ldg(vl + c4), c = __ldg(dh + c4), d = __ldg(dl + c4);
+            float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+            float cv[4] = {c.x, c.y, c.z, c.w}, dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v2[4 * c4 + u] = dev::df_lerp(F2{av[u], bv[u]}, F2{cv[u], dv[u]}, r.f2);
+                if constexpr (GRAD) dv2[4 * c4 + u] = in2 ? F2{cv[u], dv[u]} : F2{0.f, 0.f};
+            }
+        }
+    }
+    const size_t o1 = (size_t)r.i1 * RP;
+    const float* V1h = P.Vt[0][0] + o1;
+    const float* V1l = P.Vt[0][1] + o1;
+    const float* V1dh = P.Vt[0][2] + o1;
+    const float* V1dl = P.Vt[0][3] + o1;
+    const float* Wh = slab;
+    const float* Wl = slab + RP * RP;
+    const float* Dh = slab + 2 * RP * RP;
+    const float* Dl = slab + 3 * RP * RP;
+    const float f3 = r.f3;
+    F2 phi{0.f, 0.f}, g1{0.f, 0.f}, g2{0.f, 0.f}, g3{0.f, 0.f};
+    for (int a = 0; a < RP; ++a) {
+        const float ch = __ldg(V1dh + a), cl = __ldg(V1dl + a);
+        const F2 va = dev::df_lerp(F2{__ldg(V1h + a), __ldg(V1l + a)}, F2{ch, cl}, r.f1);
+        F2 u{0.f, 0.f}, u2{0.f, 0.f}, u3{0.f, 0.f};
+        const float4* wh = (const float4*)(Wh + a * RP);
+        const float4* wl = (const float4*)(Wl + a * RP);
+        const float4* dh = (const float4*)(Dh + a * RP);
+        const float4* dl = (const float4*)(Dl + a * RP);
+#pragma unroll
+        for (int b4 = 0; b4 < RP / 4; ++b4) {
+            float4 xa = wh[b4], xb = wl[b4], xc = dh[b4], xd = dl[b4];
+            float av[4] = {xa.x, xa.y, xa.z, xa.w}, bv[4] = {xb.x, xb.y, xb.z, xb.w};
+            float cv[4] = {xc.x, xc.y, xc.z, xc.w}, dv[4] = {xd.x, xd.y, xd.z, xd.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                F2 t = dev::df_lerp(F2{av[k], bv[k]}, F2{cv[k], dv[k]}, f3);
+                dev::df_fma_acc(u, v2[4 * b4 + k], t);
+                if constexpr (GRAD) {
+                    dev::df_fma_acc(u2, dv2[4 * b4 + k], t);
+                    if (in3) dev::df_fma_acc(u3, v2[4 * b4 + k], F2{cv[k], dv[k]});
+                }
+            }
+        }
+        dev::df_fma_acc(phi, va, u);
+        if constexpr (GRAD) {
+            const F2 dva = in1 ? F2{ch, cl} : F2{0.f, 0.f};
+            dev::df_fma_acc(g1, dva, u);
+            dev::df_fma_acc(g2, va, u2);
+            dev::df_fma_acc(g3, va, u3);
+        }
+    }
+    const int L = lig.L;
+    const int j = r.slot % L;
+    double phs, gs[3] = {0.0, 0.0, 0.0};
+    if constexpr (GRAD) {
+        double4 v = reinterpret_cast<const double4*>(shortv)[r.slot];
+        phs = v.x;
+        gs[0] = v.y;
+        gs[1] = v.z;
+        gs[2] = v.w;
+    } else {
+        phs = shortv[r.slot];
+    }
+    const float ry[3] = {r.ry0, r.ry1, r.ry2};
+    atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, lig.q64[j], ry, contrib + (size_t)r.slot * NC);
+}
+
+template <int RP, bool GRAD>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+    k_sorted_wform(ProteinView P, LigandView lig, const AtomRec* __restrict__ srt, const int* __restrict__ off,
+                   const double* __restrict__ shortv, double* __restrict__ contrib) {
+    extern __shared__ float4 sm4[];
+    constexpr int SLAB4 = RP * RP / 4;  // float4 per plane
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float4* slab4 = sm4 + (size_t)wib * 4 * SLAB4;
+    const int Mv = off[P.n - 1];  // atoms of evaluated poses
+    const long long nw = (long long)gridDim.x * kWarpsPerBlock;
+    const long long w = (long long)blockIdx.x * kWarpsPerBlock + wib;
+    const long long per = ((Mv + nw - 1) / nw + 31) / 32 * 32;
+    const long long s0 = w * per, s1 = std::min<long long>(Mv, s0 + per);
+    int cur = -1;
+    for (long long base = s0; base < s1; base += 32) {
+        const long long idx = base + lane;
+        AtomRec r;
+        int c = INT_MAX;
+        if (idx < s1) {
+            r = srt[idx];
+            c = r.i3;
+        }
+        for (;;) {
+            const int cm = __reduce_min_sync(0xffffffffu, c);
+            if (cm == INT_MAX) break;
+            if (cm != cur) {
+                __syncwarp();
+                const size_t o = (size_t)cm * RP * RP;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float4* src = (const float4*)(P.Wt[k] + o);
+                    for (int e = lane; e < SLAB4; e += 32) slab4[k * SLAB4 + e] = __ldg(src + e);
+                }
+                __syncwarp();
+                cur = cm;
+            }
+            if (c == cm) {
+                sorted_atom<RP, GRAD>(P, lig, r, (const float*)slab4, shortv, contrib);
+                c = INT_MAX;
+            }
+        }
+    }
+}
+
+template <int NC>
+__global__ void k_sorted_reduce(const PoseSetup* __restrict__ ps, int PC, int L, long long p0,
+                                const double* __restrict__ contrib, const int* __restrict__ pflag,
+                                double* __restrict__ E, uint8_t* __restrict__ flags, double* __restrict__ gt,
+                                double* __restrict__ gw) {
+    const int lane = threadIdx.x & 31;
+    const long long pl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (pl >= PC || !ps[pl].valid) return;
+    double s[NC];
+    pose_sums<NC>(contrib + (size_t)pl * L * NC, L, lane, s);
+    if (lane == 0) write_pose<NC>(ps[pl], s, pflag[pl], p0 + pl, E, flags, gt, gw);
+}
+
+// Scratch of one chunk of PC poses (M = PC L atoms), carved in this order.
+struct SortedScratch {
+    PoseSetup* ps;
+    int* pflag;
+    AtomRec* rec;
+    AtomRec* srt;
+    double* shortv;
+    double* contrib;
+    int* count;
+    int* off;
+};
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t chunk_bytes(long long PC, int L, int n, bool grad) {
+    const long long M = PC * L;
+    const int NC = grad ? 7 : 1;
+    return align256(PC * sizeof(PoseSetup)) + align256(PC * 4) + 2 * align256(M * sizeof(AtomRec)) +
+           align256(M * 8 * (grad ? 4 : 1)) + align256(M * 8 * NC) + align256((size_t)n * 4) +
+           align256((size_t)(n + 1) * 4);
+}
+
+SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
+    const long long M = PC * L;
+    const int NC = grad ? 7 : 1;
+    char* p = (char*)base;
+    SortedScratch s;
+    auto take = [&](size_t b) {
+        char* q = p;
+        p += align256(b);
+        return q;
+    };
+    s.ps = (PoseSetup*)take(PC * sizeof(PoseSetup));
+    s.pflag = (int*)take(PC * 4);
+    s.rec = (AtomRec*)take(M * sizeof(AtomRec));
+    s.srt = (AtomRec*)take(M * sizeof(AtomRec));
+    s.shortv = (double*)take(M * 8 * (grad ? 4 : 1));
+    s.contrib = (double*)take(M * 8 * NC);
+    s.count = (int*)take((size_t)n * 4);
+    s.off = (int*)take((size_t)(n + 1) * 4);
+    return s;
+}
+
+template <int RP, bool GRAD>
+rs_status launch_sorted_wform(const EvalLaunch& a, const SortedScratch& s, long long M, cudaStream_t st) {
+    auto kern = k_sorted_wform<RP, GRAD>;
+    const size_t smem = (size_t)kWarpsPerBlock * 4 * RP * RP * sizeof(float);
+    RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0, sms = 0, dev = 0;
+    RS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kWarpsPerBlock, smem));
+    RS_TRY_CUDA(cudaGetDevice(&dev));
+    RS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    long long want = (M + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock);
+    long long grid = std::max<long long>(1, std::min<long long>(want, (long long)std::max(per_sm, 1) * sms));
+    double work = (double)M * wform_flops_per_atom(RP, GRAD);
+    {
+        ::rs::KernelTimer kt__(GRAD ? "k_sorted_wform_grad" : "k_sorted_wform", st, work, true, a.events);
+        kern<<<(unsigned)grid, 32 * kWarpsPerBlock, smem, st>>>(a.prot, a.lig, s.srt, s.off, s.shortv, s.contrib);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
+template <bool GRAD>
+rs_status dispatch_sorted_wform(const EvalLaunch& a, const SortedScratch& s, long long M, cudaStream_t st) {
+    switch (a.prot.R) {
+#define RS_CASE(R) \
+    case R: return launch_sorted_wform<R, GRAD>(a, s, M, st);
+        RS_CASE(4) RS_CASE(8) RS_CASE(12) RS_CASE(16) RS_CASE(20) RS_CASE(24) RS_CASE(28) RS_CASE(32)
+#undef RS_CASE
+        default:
+            set_error("unsupported padded Tucker rank %d", a.prot.R);
+            return RS_ERR_UNSUPPORTED;
+    }
+}
+
+template <bool GRAD>
+rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
+    const int L = a.lig.L, n = a.prot.n;
+    const long long PC = sorted_chunk_poses(a.ws_bytes, L, n, GRAD);
+    if (PC < 1) {
+        set_error("sorted pose path: scratch of %zu bytes too small", a.ws_bytes);
+        return RS_ERR_INVALID;
+    }
+    constexpr int NC = GRAD ? 7 : 1;
+    for (long long p0 = 0; p0 < a.P; p0 += PC) {
+        const int pc = (int)std::min<long long>(PC, a.P - p0);
+        const long long M = (long long)pc * L;
+        SortedScratch s = carve(a.ws, pc, L, n, GRAD);
+        RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)n * 4, st));
+        {
+            ::rs::KernelTimer kt__("k_sorted_poses", st, 0.0, false, a.events);
+            k_sorted_poses<<<(pc + 127) / 128, 128, 0, st>>>(a.prot, a.rot, a.trans, p0, pc, GRAD, a.skip, s.ps,
+                                                              s.pflag);
+        }
+        {
+            ::rs::KernelTimer kt__(GRAD ? "k_sorted_atoms_grad" : "k_sorted_atoms", st, 0.0, true, a.events);
+            k_sorted_atoms<GRAD><<<(unsigned)((M + 127) / 128), 128, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag,
+                                                                             s.rec, s.shortv, s.count);
+        }
+        {
+            ::rs::KernelTimer kt__("k_cell_scan", st, 0.0, false, a.events);
+            k_cell_scan<<<1, 1024, 0, st>>>(n, s.count, s.off);
+        }
+        {
+            ::rs::KernelTimer kt__("k_sorted_scatter", st, 0.0, false, a.events);
+            k_sorted_scatter<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, s.rec, s.off, s.srt);
+        }
+        RS_TRY_CUDA(cudaGetLastError());
+        RS_TRY(dispatch_sorted_wform<GRAD>(a, s, M, st));
+        {
+            ::rs::KernelTimer kt__("k_sorted_reduce", st, 0.0, false, a.events);
+            k_sorted_reduce<NC><<<(unsigned)((pc * 32LL + 255) / 256), 256, 0, st>>>(
+                s.ps, pc, L, p0, s.contrib, s.pflag, a.E, a.flags, a.gt, a.gw);
+        }
+        RS_TRY_CUDA(cudaGetLastError());
+    }
+    return RS_OK;
+}
+
+}  // namespace
+
+long long sorted_chunk_poses(size_t ws_bytes, int L, int n, bool grad) {
+    long long lo = 0, hi = std::max<long long>(1, (long long)(ws_bytes / ((size_t)L * 96 + 256)) + 1);
+    // largest PC whose carve fits (chunk_bytes is increasing in PC)
+    while (lo < hi) {
+        long long mid = (lo + hi + 1) / 2;
+        if (chunk_bytes(mid, L, n, grad) <= ws_bytes) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+size_t sorted_scratch_bytes(long long P, int L, int n, bool grad) {
+    const long long max_atoms = 1LL << 23;  // a chunk holds at most ~8.4M atoms
+    long long PC = std::max<long long>(1, std::min<long long>(P, max_atoms / std::max(L, 1)));
+    return chunk_bytes(PC, L, n, grad);
+}
+
+rs_status launch_sorted(const EvalLaunch& a, bool grad, cudaStream_t st) {
+    if (a.P <= 0) return RS_OK;
+    return grad ? run_sorted<true>(a, st) : run_sorted<false>(a, st);
+}
+
+}  // namespace rs

@@ -66,6 +66,32 @@ class rs_batch_info(C.Structure):
                 ("tune_ms", C.c_double)]
 
 
+class rs_request(C.Structure):
+    _fields_ = [("protein_id", C.c_uint64), ("N", C.c_int32), ("prot_xyz", C.c_void_p),
+                ("prot_q", C.c_void_p), ("params", rs_params), ("L", C.c_int32),
+                ("lig_xyz", C.c_void_p), ("lig_q", C.c_void_p), ("P", C.c_int64),
+                ("quat", C.c_void_p), ("trans", C.c_void_p)]
+
+
+class rs_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("t_submit_ns", C.c_int64), ("t_admit_ns", C.c_int64),
+                ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64), ("message", C.c_char * 160)]
+
+
+class rs_serve_params(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_queue", C.c_int32),
+                ("max_inflight_launches", C.c_int32), ("idle_wait_ms", C.c_int32),
+                ("inject_alloc_failures", C.c_int32)]
+
+
+class rs_serve_stats(C.Structure):
+    _fields_ = [("done", C.c_uint64), ("failed", C.c_uint64), ("launches", C.c_uint64),
+                ("builds", C.c_uint64), ("cache_hits", C.c_uint64), ("evictions", C.c_uint64),
+                ("queued", C.c_uint64), ("cached_proteins", C.c_uint64),
+                ("budget_bytes", C.c_uint64), ("used_bytes", C.c_uint64),
+                ("mean_requests_per_launch", C.c_double)]
+
+
 def _load() -> C.CDLL:
     path = os.environ.get("RS_LIBRARY") or _build.build()
     lib = C.CDLL(path)
@@ -89,6 +115,15 @@ def _load() -> C.CDLL:
         "rs_batch_run": (st, [vp, vp]),
         "rs_batch_free": (None, [vp]),
         "rs_batch_get_info": (st, [vp, C.POINTER(rs_batch_info)]),
+        "rs_serve_params_default": (None, [C.POINTER(rs_serve_params)]),
+        "rs_request_validate": (st, [C.POINTER(rs_request)]),
+        "rs_serve_create": (st, [C.c_int, C.POINTER(rs_serve_params), C.POINTER(vp)]),
+        "rs_serve_submit": (st, [vp, C.POINTER(rs_request), vp, vp, C.POINTER(C.c_uint64)]),
+        "rs_serve_poll": (st, [vp, C.c_uint64, C.POINTER(rs_result)]),
+        "rs_serve_wait": (st, [vp, C.c_uint64, i32, C.POINTER(rs_result)]),
+        "rs_serve_cancel": (st, [vp, C.c_uint64]),
+        "rs_serve_get_stats": (st, [vp, C.POINTER(rs_serve_stats)]),
+        "rs_serve_destroy": (None, [vp]),
         "rs_stats_kernel_launches": (C.c_ulonglong, []),
         "rs_timing_enable": (st, [C.c_int]),
         "rs_timing_reset": (st, []),
@@ -377,6 +412,138 @@ def rs_timing_all() -> dict:
         r = rs_timing_get(i)
         out[r["name"]] = r
     return out
+
+
+# ------------------------------------------------------------------ serving
+def rs_serve_params_default(**overrides) -> rs_serve_params:
+    p = rs_serve_params()
+    _lib.rs_serve_params_default(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def make_request(protein_id: int, prot_xyz, prot_q, params: rs_params, lig_xyz, lig_q, quat,
+                 trans):
+    """An rs_request over host arrays, plus the float64 arrays it points into (the
+    caller keeps them alive until the request is finished)."""
+    arrs = [_host(prot_xyz, np.float64), _host(prot_q, np.float64), _host(lig_xyz, np.float64),
+            _host(lig_q, np.float64), _host(quat, np.float64), _host(trans, np.float64)]
+    px, pq, lx, lq, qu, tr = arrs
+    r = rs_request()
+    r.protein_id = protein_id
+    r.N = pq.shape[0]
+    r.prot_xyz, r.prot_q = px.ctypes.data, pq.ctypes.data
+    r.params = params
+    r.L = lq.shape[0]
+    r.lig_xyz, r.lig_q = lx.ctypes.data, lq.ctypes.data
+    r.P = tr.shape[0]
+    r.quat, r.trans = (qu.ctypes.data if r.P else None), (tr.ctypes.data if r.P else None)
+    return r, arrs
+
+
+def rs_request_validate(r: rs_request) -> int:
+    return _lib.rs_request_validate(C.byref(r) if r is not None else None)
+
+
+def rs_serve_create(device: int = 0, params: rs_serve_params | None = None) -> int:
+    h = C.c_void_p()
+    _check(_lib.rs_serve_create(device, C.byref(params) if params is not None else None,
+                                C.byref(h)))
+    return h.value
+
+
+def rs_serve_submit(server: int, req: rs_request, E_out: np.ndarray, flags_out: np.ndarray | None):
+    rid = C.c_uint64()
+    _check(_lib.rs_serve_submit(server, C.byref(req), E_out.ctypes.data,
+                                flags_out.ctypes.data if flags_out is not None else None,
+                                C.byref(rid)))
+    return rid.value
+
+
+def _result_dict(r: rs_result) -> dict:
+    return {"status": r.status, "t_submit_ns": r.t_submit_ns, "t_admit_ns": r.t_admit_ns,
+            "t_start_ns": r.t_start_ns, "t_end_ns": r.t_end_ns, "message": r.message.decode()}
+
+
+def rs_serve_poll(server: int, req_id: int):
+    """None while pending, else the result record (its 'status' is the request's)."""
+    r = rs_result()
+    s = _lib.rs_serve_poll(server, req_id, C.byref(r))
+    if s == RS_ERR_NOT_READY:
+        return None
+    _check(s)
+    return _result_dict(r)
+
+
+def rs_serve_wait(server: int, req_id: int, timeout_ms: int = 60000) -> dict:
+    r = rs_result()
+    _check(_lib.rs_serve_wait(server, req_id, timeout_ms, C.byref(r)))
+    return _result_dict(r)
+
+
+def rs_serve_cancel(server: int, req_id: int) -> int:
+    return _lib.rs_serve_cancel(server, req_id)
+
+
+def rs_serve_get_stats(server: int) -> dict:
+    st = rs_serve_stats()
+    _check(_lib.rs_serve_get_stats(server, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in rs_serve_stats._fields_}
+
+
+def rs_serve_destroy(server: int) -> None:
+    _lib.rs_serve_destroy(server)
+
+
+class Server:
+    """Owns an rs_server; keeps each request's host arrays alive until it finishes."""
+
+    def __init__(self, device: int = 0, **params):
+        self.handle = rs_serve_create(device, rs_serve_params_default(**params))
+        self._keep = {}
+
+    def submit(self, protein_id, prot_xyz, prot_q, params, lig_xyz, lig_q, quat, trans):
+        req, arrs = make_request(protein_id, prot_xyz, prot_q, params, lig_xyz, lig_q, quat, trans)
+        P = req.P
+        E = np.empty(P, dtype=np.float64)
+        f = np.empty(P, dtype=np.uint8)
+        rid = rs_serve_submit(self.handle, req, E, f)
+        self._keep[rid] = (arrs, E, f)
+        return rid
+
+    def _finish(self, rid, res):
+        arrs, E, f = self._keep.pop(rid)
+        res["E"], res["flags"] = E, f
+        return res
+
+    def poll(self, rid):
+        res = rs_serve_poll(self.handle, rid)
+        return None if res is None else self._finish(rid, res)
+
+    def wait(self, rid, timeout_ms: int = 60000):
+        return self._finish(rid, rs_serve_wait(self.handle, rid, timeout_ms))
+
+    def cancel(self, rid) -> int:
+        s = rs_serve_cancel(self.handle, rid)
+        if s == RS_OK:
+            self._keep.pop(rid, None)
+        return s
+
+    def stats(self) -> dict:
+        return rs_serve_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            rs_serve_destroy(self.handle)
+            self.handle = 0
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ handle owners

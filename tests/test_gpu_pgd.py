@@ -6,6 +6,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from oracle.rs_oracle import _rotvec_to_quat
 from tests.parity import E_TOL, away_from_planes
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +48,7 @@ def test_one_step_matches_oracle(setup):
     assert np.allclose(tr[same], ref["trans"][same], rtol=0, atol=1e-5)
     assert np.allclose(rv[same], ref["rotvec"][same], rtol=0, atol=1e-5)
     # energies reported for the GPU's new poses equal the oracle's at those poses
-    chk = O.pose_energies(m, w.lig_xyz, w.lig_q, O._rotvec_to_quat(rv), tr)
+    chk = O.pose_energies(m, w.lig_xyz, w.lig_q, _rotvec_to_quat(rv), tr)
     ok = chk["flags"] == 0
     scale = O.tolerance_scale(chk["E"], chk["S_ref"])
     assert np.all((np.abs(E - chk["E"]) <= E_TOL * scale)[ok])
@@ -77,7 +78,7 @@ def test_many_steps_monotone_and_feasible(setup):
         assert np.all(f[feas] == 0)
         prev, prev_f = E, f
     # final energies are those of the final poses
-    q = O._rotvec_to_quat(rv.cpu().numpy())
+    q = _rotvec_to_quat(rv.cpu().numpy())
     ref = O.pose_energies(m, w.lig_xyz, w.lig_q, q, tr.cpu().numpy())
     keep = ref["flags"] == 0
     assert np.all(np.abs(prev[keep] - ref["E"][keep]) <= E_TOL * np.maximum(np.abs(ref["E"][keep]),
@@ -99,20 +100,32 @@ def test_autograd_matches_adjoint_and_fd(setup):
     assert torch.equal(E.detach(), Eg)
     assert torch.allclose(tr.grad, weights[:, None] * gt, rtol=0, atol=0)
     assert torch.allclose(rv.grad, weights[:, None] * gw, rtol=0, atol=0)
-    # central differences of the GPU energy, on poses away from grid planes
+    # central differences of the FP64 oracle energy (both kinds), and of the GPU
+    # energy itself where its evaluation is smooth to ~1e-12 relative (the Tucker
+    # W-form path in pair arithmetic; the canonical path sums FP32 blocks, whose
+    # rounding a 1e-4 step amplifies beyond the tolerance)
     keep = away_from_planes(m, w.lig_xyz, O.rotvec_to_rot(rv0[:n]), w.trans[:n], eps=2e-3)
     h = 1e-4
+    rvn, trn = rv0[:n], w.trans[:n]
     fd_t, fd_w = np.zeros((n, 3)), np.zeros((n, 3))
+    ofd_t, ofd_w = np.zeros((n, 3)), np.zeros((n, 3))
+    oE = lambda r, t: O.pose_gradients(m, w.lig_xyz, w.lig_q, r, t)["E"]
     for a in range(3):
         d = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
         d[:, a] = h
-        Ep, _ = lib.rs_energy_grad_poses(ctx.handle, prot.handle, lx, lq, rv.detach(), tr.detach() + d)[0::3]
-        Em, _ = lib.rs_energy_grad_poses(ctx.handle, prot.handle, lx, lq, rv.detach(), tr.detach() - d)[0::3]
+        dn = d.cpu().numpy()
+        Ep = lib.rs_energy_grad_poses(ctx.handle, prot.handle, lx, lq, rv.detach(), tr.detach() + d)[0]
+        Em = lib.rs_energy_grad_poses(ctx.handle, prot.handle, lx, lq, rv.detach(), tr.detach() - d)[0]
         fd_t[:, a] = ((Ep - Em) / (2 * h)).cpu().numpy()
-        Ep, _ = lib.rs_energy_grad_poses(ctx.handle, prot.handle, lx, lq, rv.detach() + d, tr.detach())[0::3]
-        Em, _ = lib.rs_energy_grad_poses(ctx.handle, prot.handle, lx, lq, rv.detach() - d, tr.detach())[0::3]
+        Ep = lib.rs_energy_grad_poses(ctx.handle, prot.handle, lx, lq, rv.detach() + d, tr.detach())[0]
+        Em = lib.rs_energy_grad_poses(ctx.handle, prot.handle, lx, lq, rv.detach() - d, tr.detach())[0]
         fd_w[:, a] = ((Ep - Em) / (2 * h)).cpu().numpy()
+        ofd_t[:, a] = (oE(rvn, trn + dn) - oE(rvn, trn - dn)) / (2 * h)
+        ofd_w[:, a] = (oE(rvn + dn, trn) - oE(rvn - dn, trn)) / (2 * h)
     gt, gw = gt.cpu().numpy(), gw.cpu().numpy()
     sc = np.maximum(np.abs(gt).max(axis=1), np.abs(gw).max(axis=1))[:, None] + 1e-12
-    assert np.all((np.abs(gt - fd_t) / sc)[keep] <= 1e-4)
-    assert np.all((np.abs(gw - fd_w) / sc)[keep] <= 1e-4)
+    assert np.all((np.abs(gt - ofd_t) / sc)[keep] <= 1e-4)
+    assert np.all((np.abs(gw - ofd_w) / sc)[keep] <= 1e-4)
+    if prot.info["kind"] == 1:
+        assert np.all((np.abs(gt - fd_t) / sc)[keep] <= 1e-4)
+        assert np.all((np.abs(gw - fd_w) / sc)[keep] <= 1e-4)

@@ -28,7 +28,7 @@ __all__ = [
     "Workload", "ball_uniform", "mixed_charges", "shoemake_quaternions",
     "shell_translations", "ellipsoid_lattice", "sphere_lattice",
     "plain_small", "plain_protein", "batch_pairs", "pgd_start", "tiny",
-    "random_rotvecs", "WORKLOADS",
+    "random_rotvecs", "serve_pool", "serve_request", "poisson_arrivals", "WORKLOADS",
 ]
 
 
@@ -233,6 +233,53 @@ def pgd_start(seed: int = 3, P: int = 4096, N: int = 10000, L: int = 100, n: int
     trans = np.concatenate(transs)[:P]
     return Workload("pgd_start", prot, zq, lig, lq, quat, trans, n=n, b=b, sigma=3.0,
                     R_l=20, tucker_cap=tucker_cap, meta={"seed": seed})
+
+
+_SERVE_N_CHOICES = (1025, 2049, 4097, 8193, 16385)
+_SERVE_L_MAX = 200
+
+
+def serve_pool(seed: int = 5, proteins: int = 64, n_max: int = 16385, tucker_cap: int = 20) -> list[dict]:
+    """Proteins of a serving stream: N log-uniform in [500, 20000] on jittered lattice
+    spheres, charges as elsewhere; the box fits the largest ligand of the stream
+    (L = 200) and the grid n is picked by quintile of the box half-width b from
+    1025 ... 16385 (capped at n_max)."""
+    rng = np.random.default_rng(seed)
+    r_l_max = 5.0 * (_SERVE_L_MAX / 20.0) ** (1.0 / 3.0)
+    out = []
+    for p in range(proteins):
+        N = int(round(math.exp(rng.uniform(math.log(500.0), math.log(20000.0)))))
+        prot, r_p = sphere_lattice(rng, N)
+        zq = mixed_charges(rng, N, 0.3, 0.08)
+        out.append({"id": p + 1, "xyz": prot, "q": zq, "r_p": r_p,
+                    "b": r_p + 2.0 * r_l_max + 8.0, "sigma": 3.0, "R_l": 20,
+                    "tucker_cap": tucker_cap})
+    qs = np.quantile(np.asarray([e["b"] for e in out]), [0.2, 0.4, 0.6, 0.8])
+    for e in out:
+        k = int(np.searchsorted(qs, e["b"], side="right"))
+        e["n"] = min(_SERVE_N_CHOICES[k], n_max)
+    return out
+
+
+def serve_request(rng: np.random.Generator, prot: dict, P: int = 2048) -> dict:
+    """One docking request against a pool protein: a new ligand (L uniform in
+    [10, 200], ball of radius 5 (L/20)^(1/3), charges N(0, 0.3)) and P poses
+    (uniform rotations, centres on the shell outside the protein)."""
+    L = int(rng.integers(10, _SERVE_L_MAX + 1))
+    r_l = 5.0 * (L / 20.0) ** (1.0 / 3.0)
+    return {"lig_xyz": ball_uniform(rng, L, r_l), "lig_q": rng.normal(0.0, 0.3, L),
+            "quat": shoemake_quaternions(rng, P),
+            "trans": shell_translations(rng, P, prot["r_p"], prot["r_p"] + 2.0 * r_l + 3.0)}
+
+
+def poisson_arrivals(rng: np.random.Generator, rate: float, duration: float) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream of the given rate over [0, duration)."""
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return np.asarray(out)
+        out.append(t)
 
 
 WORKLOADS = {
