@@ -37,88 +37,230 @@ __device__ __forceinline__ void setup_pose(const ProteinView& P, const double* _
     ps.valid = 1;
 }
 
+// Cell of the short-range cell list holding an FP32 position (may lie outside
+// the list's range by up to 4 cells; the neighbour walk skips those).
+__device__ __forceinline__ void short_cell(const ProteinView& P, const float xf[3], int& c0, int& c1, int& c2) {
+    float u0 = __fmul_rn(__fsub_rn(xf[0], P.co0), P.inv_cell);
+    float u1 = __fmul_rn(__fsub_rn(xf[1], P.co1), P.inv_cell);
+    float u2 = __fmul_rn(__fsub_rn(xf[2], P.co2), P.inv_cell);
+    u0 = fminf(fmaxf(u0, -4.f), (float)P.nc0 + 4.f);
+    u1 = fminf(fmaxf(u1, -4.f), (float)P.nc1 + 4.f);
+    u2 = fminf(fmaxf(u2, -4.f), (float)P.nc2 + 4.f);
+    c0 = (int)floorf(u0);
+    c1 = (int)floorf(u1);
+    c2 = (int)floorf(u2);
+}
+
+// Range [s, e) of cell-sorted atoms in row (dz, dy) of the 3 x 3 x 3 neighbourhood of
+// cell (c0, c1, c2): the row's three x-cells are contiguous.  Empty when off the list.
+__device__ __forceinline__ void short_row(const ProteinView& P, int c0, int c1, int c2, int row, int& s, int& e) {
+    const int dz = row / 3 - 1, dy = row % 3 - 1;
+    const int cz = c2 + dz, cy = c1 + dy;
+    const int x_lo = max(c0 - 1, 0), x_hi = min(c0 + 1, P.nc0 - 1);
+    s = e = 0;
+    if (cz < 0 || cz >= P.nc2 || cy < 0 || cy >= P.nc1 || x_lo > x_hi) return;
+    const int base = (cz * P.nc1 + cy) * P.nc0;
+    s = P.cell_start[base + x_lo];
+    e = P.cell_start[base + x_hi + 1];
+}
+
+// FP32 screen of one candidate: squared distance and its band bits
+// (1: within the vdW band, 2: within the cutoff band, 4: surely closer than sigma).
+__device__ __forceinline__ int short_screen(const ProteinView& P, const float xf[3], float4 a) {
+    float e0 = __fsub_rn(xf[0], a.x), e1 = __fsub_rn(xf[1], a.y), e2 = __fsub_rn(xf[2], a.z);
+    float d2 = __fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0)));
+    return (d2 < P.sig2_hi ? 1 : 0) | (d2 < P.rc2_hi ? 2 : 0) | (d2 < P.sig2_lo ? 4 : 0);
+}
+
+// FP64 decision and term of a screened pair: f = x - x_m, d2d = |f|^2; sets clash
+// bit 1 and, when inside the cutoff, bit 2 with the radial function value fv and
+// (gradients) fgr = 2 w f'(d2d), so the pair adds w fv to phi and fgr f to grad phi.
+template <bool GRAD>
+__device__ __forceinline__ int short_pair(const ProteinView& P, const double x64[3], D4 a64, int bits,
+                                          double f[3], double& fv, double& fgr) {
+    f[0] = __dsub_rn(x64[0], a64.x);
+    f[1] = __dsub_rn(x64[1], a64.y);
+    f[2] = __dsub_rn(x64[2], a64.z);
+    const double d2d = fma(f[2], f[2], fma(f[1], f[1], __dmul_rn(f[0], f[0])));
+    int out = ((bits & 1) && ((bits & 4) || d2d < P.sig2)) ? 1 : 0;
+    if ((bits & 2) && d2d < P.rc2) {
+        out |= 2;
+        // cubic Hermite interpolation of the tabulated radial function (FP64)
+        double xs = __dmul_rn(d2d, P.stab_inv_h);
+        int j = min((int)xs, P.stab_n - 2);
+        double u = __dsub_rn(xs, (double)j);
+        double2 A = P.stab[j], B = P.stab[j + 1];
+        double u2 = __dmul_rn(u, u), u3 = __dmul_rn(u2, u);
+        // Hermite basis h00 = 2u^3 - 3u^2 + 1, h10 = u^3 - 2u^2 + u,
+        // h01 = 3u^2 - 2u^3, h11 = u^3 - u^2
+        double h00 = fma(2.0, u3, fma(-3.0, u2, 1.0));
+        double h10 = fma(-2.0, u2, __dadd_rn(u3, u));
+        double h01 = fma(-2.0, u3, __dmul_rn(3.0, u2));
+        double h11 = __dsub_rn(u3, u2);
+        fv = fma(h11, B.y, fma(h01, B.x, fma(h10, A.y, __dmul_rn(h00, A.x))));
+        if constexpr (GRAD) {
+            // d/du of the basis: 6u^2 - 6u, 3u^2 - 4u + 1, -(6u^2 - 6u), 3u^2 - 2u
+            double d00 = fma(6.0, u2, __dmul_rn(-6.0, u));
+            double d10 = fma(3.0, u2, fma(-4.0, u, 1.0));
+            double d11 = fma(3.0, u2, __dmul_rn(-2.0, u));
+            double dp = fma(d11, B.y, fma(d10, A.y, __dmul_rn(d00, __dsub_rn(A.x, B.x))));
+            // grad_x f(|x - x_m|^2) = 2 f'(s) (x - x_m)
+            fgr = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a64.w), dp), P.stab_inv_h);
+        }
+    }
+    return out;
+}
+
+// Accumulation of one pair's term into an atom's sums, in candidate order.
+template <bool GRAD>
+__device__ __forceinline__ void short_accumulate(double w, double fv, double fgr, const double f[3], double& phi,
+                                                 double g[3]) {
+    phi = fma(w, fv, phi);
+    if constexpr (GRAD) {
+        g[0] = fma(fgr, f[0], g[0]);
+        g[1] = fma(fgr, f[1], g[1]);
+        g[2] = fma(fgr, f[2], g[2]);
+    }
+}
+
 // Short-range part and vdW decision for one atom; candidates split over
 // `nl` cooperating lanes starting at `lane`.  Distances are screened in FP32;
 // pairs inside the cutoff, and vdW decisions within 1e-4 relative of sigma^2,
 // are taken in FP64 from x = t + R y evaluated in FP64.  phi and g are added to
-// (callers pass zeros); products are fused explicitly, so every kernel that
-// inlines this computes the same bits.
+// (callers pass zeros) in candidate order; with nl = 1 the sums equal those of
+// short_coop for the same atom bit for bit.
 template <bool GRAD>
 __device__ __noinline__ void short_vdw(const ProteinView& P, const float xf[3], const double x64[3],
                                        int lane, int nl, double& phi, double g[3], int& clash) {
-    float u0 = (xf[0] - P.co0) * P.inv_cell, u1 = (xf[1] - P.co1) * P.inv_cell,
-          u2 = (xf[2] - P.co2) * P.inv_cell;
-    u0 = fminf(fmaxf(u0, -4.f), (float)P.nc0 + 4.f);
-    u1 = fminf(fmaxf(u1, -4.f), (float)P.nc1 + 4.f);
-    u2 = fminf(fmaxf(u2, -4.f), (float)P.nc2 + 4.f);
-    int c0 = (int)floorf(u0), c1 = (int)floorf(u1), c2 = (int)floorf(u2);
-    for (int dz = -1; dz <= 1; ++dz) {
-        int cz = c2 + dz;
-        if (cz < 0 || cz >= P.nc2) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            int cy = c1 + dy;
-            if (cy < 0 || cy >= P.nc1) continue;
-            int x_lo = max(c0 - 1, 0), x_hi = min(c0 + 1, P.nc0 - 1);
-            if (x_lo > x_hi) continue;
-            int base = (cz * P.nc1 + cy) * P.nc0;
-            int s = P.cell_start[base + x_lo], e = P.cell_start[base + x_hi + 1];
-            for (int k = s + lane; k < e; k += nl) {
-                float4 a = P.atoms[k];
-                float e0 = xf[0] - a.x, e1 = xf[1] - a.y, e2 = xf[2] - a.z;
-                float d2 = e0 * e0 + e1 * e1 + e2 * e2;
-                bool near_sig = d2 < P.sig2_hi;
-                bool near_rc = d2 < P.rc2_hi;
-                if (!(near_sig || near_rc)) continue;
-                D4 a64 = P.atoms64[k];
-                double f0 = __dsub_rn(x64[0], a64.x), f1 = __dsub_rn(x64[1], a64.y),
-                       f2 = __dsub_rn(x64[2], a64.z);
-                double d2d = fma(f2, f2, fma(f1, f1, __dmul_rn(f0, f0)));
-                if (near_sig && (d2 < P.sig2_lo || d2d < P.sig2)) clash = 1;
-                if (near_rc && d2d < P.rc2) {
-                    // cubic Hermite interpolation of the tabulated radial function (FP64)
-                    double xs = __dmul_rn(d2d, P.stab_inv_h);
-                    int j = min((int)xs, P.stab_n - 2);
-                    double u = __dsub_rn(xs, (double)j);
-                    double2 A = P.stab[j], B = P.stab[j + 1];
-                    double u2 = __dmul_rn(u, u), u3 = __dmul_rn(u2, u);
-                    // Hermite basis h00 = 2u^3 - 3u^2 + 1, h10 = u^3 - 2u^2 + u,
-                    // h01 = 3u^2 - 2u^3, h11 = u^3 - u^2
-                    double h00 = fma(2.0, u3, fma(-3.0, u2, 1.0));
-                    double h10 = fma(-2.0, u2, __dadd_rn(u3, u));
-                    double h01 = fma(-2.0, u3, __dmul_rn(3.0, u2));
-                    double h11 = __dsub_rn(u3, u2);
-                    double fv = fma(h11, B.y, fma(h01, B.x, fma(h10, A.y, __dmul_rn(h00, A.x))));
-                    phi = fma(a64.w, fv, phi);
-                    if constexpr (GRAD) {
-                        // d/du of the basis: 6u^2 - 6u, 3u^2 - 4u + 1, -(6u^2 - 6u), 3u^2 - 2u
-                        double d00 = fma(6.0, u2, -6.0 * u);
-                        double d10 = fma(3.0, u2, fma(-4.0, u, 1.0));
-                        double d11 = fma(3.0, u2, -2.0 * u);
-                        double dp = fma(d11, B.y, fma(d10, A.y, __dmul_rn(d00, __dsub_rn(A.x, B.x))));
-                        // grad_x f(|x - x_m|^2) = 2 f'(s) (x - x_m)
-                        double fgr = __dmul_rn(__dmul_rn(2.0 * a64.w, dp), P.stab_inv_h);
-                        g[0] = fma(fgr, f0, g[0]);
-                        g[1] = fma(fgr, f1, g[1]);
-                        g[2] = fma(fgr, f2, g[2]);
-                    }
-                }
-            }
+    int c0, c1, c2;
+    short_cell(P, xf, c0, c1, c2);
+    for (int row = 0; row < 9; ++row) {
+        int s, e;
+        short_row(P, c0, c1, c2, row, s, e);
+        for (int k = s + lane; k < e; k += nl) {
+            const int bits = short_screen(P, xf, P.atoms[k]);
+            if (!(bits & 3)) continue;
+            double f[3], fv = 0.0, fgr = 0.0;
+            const int out = short_pair<GRAD>(P, x64, P.atoms64[k], bits, f, fv, fgr);
+            if (out & 1) clash = 1;
+            if (out & 2) short_accumulate<GRAD>(P.atoms64[k].w, fv, fgr, f, phi, g);
         }
     }
 }
 
-// Short-range sums and flag bits of one atom (FP32 copy of the position for the
-// screen, FP64 for the decisions and values).
+// Per-warp queue of screened near pairs (short_coop).
 template <bool GRAD>
-__device__ __forceinline__ int atom_short(const ProteinView& P, const double x64[3], const bool ins[3],
-                                          double& phs, double gs[3]) {
+struct NearQueue {
+    int owner[64];   // lane whose atom the pair belongs to
+    int k[64];       // protein atom (cell-sorted index)
+    int bits[64];    // screen bits, then the pair's outcome bits
+    double w[32], fv[32], fgr[GRAD ? 32 : 1];
+    double f[GRAD ? 3 : 1][32];
+    double x[3][32]; // FP64 positions of the warp's atoms
+    int rs[9][32], re[9][32];
+};
+
+// Short range and vdW decision for the 32 atoms of a warp (one per lane), with the
+// FP32 screen run by all lanes in step and the FP64 work of near pairs packed one
+// pair per lane: a warp whose atoms see different numbers of near pairs keeps
+// every lane busy.  Every lane of the warp must call it; lanes with active = false
+// contribute no atom.  Each atom's sums are accumulated in its own candidate order,
+// so they equal short_vdw's (nl = 1) bit for bit.
+template <bool GRAD>
+__device__ void short_coop(const ProteinView& P, bool active, const double x64[3], NearQueue<GRAD>& Q,
+                           double& phi, double g[3], int& clash) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
     float xf[3];
-    for (int a = 0; a < 3; ++a) xf[a] = (float)x64[a];
-    int clash = 0;
-    short_vdw<GRAD>(P, xf, x64, 0, 1, phs, gs, clash);
-    int fl = clash ? RS_FLAG_CLASH : 0;
-    if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
-    return fl;
+    int total = 0;
+    if (active) {
+        for (int a = 0; a < 3; ++a) {
+            xf[a] = (float)x64[a];
+            Q.x[a][lane] = x64[a];
+        }
+        int c0, c1, c2;
+        short_cell(P, xf, c0, c1, c2);
+        for (int row = 0; row < 9; ++row) {
+            int s, e;
+            short_row(P, c0, c1, c2, row, s, e);
+            Q.rs[row][lane] = s;
+            Q.re[row][lane] = e;
+            total += e - s;
+        }
+    }
+    const int maxlen = __reduce_max_sync(full, total);
+    int row = 0, pos = 0;
+    if (active) {
+        while (row < 9 && Q.rs[row][lane] == Q.re[row][lane]) ++row;
+        if (row < 9) pos = Q.rs[row][lane];
+    }
+    int qn = 0;  // entries in the queue (the same in every lane)
+    auto process = [&](int m) {
+        __syncwarp();
+        if (lane < m) {
+            const int o = Q.owner[lane];
+            const double xo[3] = {Q.x[0][o], Q.x[1][o], Q.x[2][o]};
+            const D4 a64 = P.atoms64[Q.k[lane]];
+            double f[3], fv = 0.0, fgr = 0.0;
+            const int out = short_pair<GRAD>(P, xo, a64, Q.bits[lane], f, fv, fgr);
+            Q.bits[lane] = out;
+            Q.w[lane] = a64.w;
+            Q.fv[lane] = fv;
+            if constexpr (GRAD) {
+                Q.fgr[lane] = fgr;
+                for (int a = 0; a < 3; ++a) Q.f[a][lane] = f[a];
+            }
+        }
+        __syncwarp();
+        if (active)
+            for (int e = 0; e < m; ++e) {
+                if (Q.owner[e] != lane) continue;
+                const int out = Q.bits[e];
+                if (out & 1) clash = 1;
+                if (out & 2) {
+                    double f[3] = {0.0, 0.0, 0.0};
+                    double fgr = 0.0;
+                    if constexpr (GRAD) {
+                        fgr = Q.fgr[e];
+                        for (int a = 0; a < 3; ++a) f[a] = Q.f[a][e];
+                    }
+                    short_accumulate<GRAD>(Q.w[e], Q.fv[e], fgr, f, phi, g);
+                }
+            }
+        __syncwarp();
+    };
+    for (int it = 0; it < maxlen; ++it) {
+        int bits = 0, k = 0;
+        if (it < total) {
+            k = pos;
+            bits = short_screen(P, xf, P.atoms[k]);
+            if (++pos == Q.re[row][lane]) {
+                ++row;
+                while (row < 9 && Q.rs[row][lane] == Q.re[row][lane]) ++row;
+                if (row < 9) pos = Q.rs[row][lane];
+            }
+        }
+        const bool near = (bits & 3) != 0;
+        const unsigned m = __ballot_sync(full, near);
+        if (near) {
+            const int slot = qn + __popc(m & ((1u << lane) - 1u));
+            Q.owner[slot] = lane;
+            Q.k[slot] = k;
+            Q.bits[slot] = bits;
+        }
+        qn += __popc(m);
+        if (qn >= 32) {
+            process(32);
+            qn -= 32;
+            if (lane < qn) {  // move the overflow to the front
+                Q.owner[lane] = Q.owner[32 + lane];
+                Q.k[lane] = Q.k[32 + lane];
+                Q.bits[lane] = Q.bits[32 + lane];
+            }
+            __syncwarp();
+        }
+    }
+    if (qn > 0) process(qn);
 }
 
 // FP64 atom position x = R y + t (the interpolation coordinates and the
@@ -244,6 +386,7 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
     PoseSetup* ps = (PoseSetup*)(v1s + NV * RP * NT);
     double* contrib = (double*)(ps + PB);
     int* pflag = (int*)(contrib + (size_t)PB * lig.L * NC);
+    NearQueue<GRAD>* queues = (NearQueue<GRAD>*)((((uintptr_t)(pflag + PB)) + 15) / 16 * 16);
     const int L = lig.L;
     const int tid = threadIdx.x;
     __syncthreads();
@@ -254,21 +397,28 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
         else ps[pl].valid = 0;
     }
     __syncthreads();
-    for (int g = tid; g < PB * L; g += NT) {
-        int pl = g / L, j = g - pl * L;
+    // every lane of a warp runs the same number of iterations (short_coop needs all 32)
+    for (int base = 0; base < PB * L; base += NT) {
+        const int g = base + tid;
+        const bool in_range = g < PB * L;
+        const int pl = in_range ? g / L : 0, j = in_range ? g - pl * L : 0;
         double* cj = contrib + (size_t)g * NC;
-        const PoseSetup& q = ps[pl];
-        if (!q.valid) {
+        const bool valid = in_range && ps[pl].valid;
+        if (in_range && !valid) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) cj[c] = 0.0;
-            continue;
         }
-        float ry[3];
-        int ci[3];
-        float cf[3];
-        bool ins[3];
-        double x64[3];
-        atom_geometry(P, lig, q, j, ry, x64, ci, cf, ins);
+        float ry[3] = {0.f, 0.f, 0.f};
+        int ci[3] = {0, 0, 0};
+        float cf[3] = {0.f, 0.f, 0.f};
+        bool ins[3] = {true, true, true};
+        double x64[3] = {0.0, 0.0, 0.0};
+        if (valid) atom_geometry(P, lig, ps[pl], j, ry, x64, ci, cf, ins);
+        // short range and vdW of the warp's atoms
+        double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
+        int clash = 0;
+        short_coop<GRAD>(P, valid, x64, queues[tid >> 5], phs, gs, clash);
+        if (!valid) continue;
         // v1 (axis 1) into this thread's shared-memory column; v2 (axis 2) in registers
         {
             size_t o = (size_t)ci[0] * RP;
@@ -352,9 +502,8 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
                 dev::df_fma_acc(g3, va, u3);
             }
         }
-        // short range and vdW
-        double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
-        int fl = atom_short<GRAD>(P, x64, ins, phs, gs);
+        int fl = clash ? RS_FLAG_CLASH : 0;
+        if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
         if (fl) atomicOr(&pflag[pl], fl);
         atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, lig.q64[j], ry, cj);
     }
@@ -368,6 +517,7 @@ size_t wform_smem(int PB, int L) {
     s += (size_t)PB * sizeof(PoseSetup);
     s += (size_t)PB * L * (GRAD ? 7 : 1) * 8;
     s += (size_t)PB * 4;
+    s = (s + 15) / 16 * 16 + (size_t)(NT / 32) * sizeof(NearQueue<GRAD>);
     return (s + 15) / 16 * 16;
 }
 

@@ -53,31 +53,40 @@ __global__ void k_sorted_poses(ProteinView P, const double* __restrict__ rot,
     else ps[pl].valid = 0;
 }
 
+// One thread per pose-atom; the short range of a warp's 32 atoms is taken
+// together (short_coop), so the FP64 work of near pairs keeps all lanes busy.
 template <bool GRAD>
-__global__ void k_sorted_atoms(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
-                               int* __restrict__ pflag, AtomRec* __restrict__ rec,
-                               double* __restrict__ shortv, int* __restrict__ count) {
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+    k_sorted_atoms(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
+                   int* __restrict__ pflag, AtomRec* __restrict__ rec, double* __restrict__ shortv,
+                   int* __restrict__ count) {
+    __shared__ NearQueue<GRAD> queues[kWarpsPerBlock];
     const int L = lig.L;
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= (long long)PC * L) return;
-    int pl = (int)(g / L), j = (int)(g - (long long)pl * L);
-    const PoseSetup& q = ps[pl];
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in_range = g < (long long)PC * L;
+    const int pl = in_range ? (int)(g / L) : 0;
+    const int j = in_range ? (int)(g - (long long)pl * L) : 0;
+    const bool valid = in_range && ps[pl].valid;
+    float ry[3] = {0.f, 0.f, 0.f};
+    double x64[3] = {0.0, 0.0, 0.0};
+    int ci[3] = {0, 0, 0};
+    float cf[3] = {0.f, 0.f, 0.f};
+    bool ins[3] = {true, true, true};
+    if (valid) atom_geometry(P, lig, ps[pl], j, ry, x64, ci, cf, ins);
+    double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
+    int clash = 0;
+    short_coop<GRAD>(P, valid, x64, queues[threadIdx.x >> 5], phs, gs, clash);
+    if (!in_range) return;
     AtomRec r;
     r.slot = (int)g;
-    if (!q.valid) {
+    if (!valid) {
         r.i3 = P.n - 1;
         r.rank = atomicAdd(&count[P.n - 1], 1);
         rec[g] = r;
         return;
     }
-    float ry[3];
-    double x64[3];
-    int ci[3];
-    float cf[3];
-    bool ins[3];
-    atom_geometry(P, lig, q, j, ry, x64, ci, cf, ins);
-    double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
-    int fl = atom_short<GRAD>(P, x64, ins, phs, gs);
+    int fl = clash ? RS_FLAG_CLASH : 0;
+    if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
     if (fl) atomicOr(&pflag[pl], fl);
     if constexpr (GRAD) {
         double4 v = make_double4(phs, gs[0], gs[1], gs[2]);
@@ -371,8 +380,9 @@ rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
         }
         {
             ::rs::KernelTimer kt__(GRAD ? "k_sorted_atoms_grad" : "k_sorted_atoms", st, 0.0, true, a.events);
-            k_sorted_atoms<GRAD><<<(unsigned)((M + 127) / 128), 128, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag,
-                                                                             s.rec, s.shortv, s.count);
+            k_sorted_atoms<GRAD><<<(unsigned)((M + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock)),
+                                   32 * kWarpsPerBlock, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag, s.rec,
+                                                                 s.shortv, s.count);
         }
         {
             ::rs::KernelTimer kt__("k_cell_scan", st, 0.0, false, a.events);
