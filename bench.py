@@ -144,21 +144,26 @@ def peaks() -> dict:
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
 
 
-# Kernel -> (bound, unit of its reported work).  FP32 ALU peak: 152 SMs x 128 FP32
-# lanes x 2 flops (FMA) x max SM clock; FP64 ALU peak: 1.25 TFLOP/s (GB300 table).
+# Kernel -> (bound, unit of its reported work).  "fp32ops": FP32 pipe operations
+# (FADD, FMUL, FFMA each 1), peak 152 SMs x 128 lanes x max SM clock; "fp32": FP32
+# flops (FMA = 2), peak twice that; FP64 ALU peak: 1.25 TFLOP/s (GB300 table).
 KERNEL_KIND = {
-    "k_eval_wform": ("alu", "fp32"), "k_eval_wform_grad": ("alu", "fp32"),
+    "k_eval_wform": ("alu", "fp32ops"), "k_eval_wform_grad": ("alu", "fp32ops"),
     "k_eval_canon": ("alu", "fp32"), "k_eval_canon_grad": ("alu", "fp32"),
-    "k_sorted_wform": ("alu", "fp32"), "k_sorted_wform_grad": ("alu", "fp32"),
+    "k_sorted_wform": ("alu", "fp32ops"), "k_sorted_wform_grad": ("alu", "fp32ops"),
     "k_project": ("alu", "fp64"), "k_core": ("alu", "fp64"), "k_gauss_dsum": ("alu", "fp64"),
     "k_gram": ("alu", "fp64"), "k_gemm_gq": ("alu", "fp64"), "k_canon_factors": ("hbm", "bytes"),
 }
 
 
-def roofline(timings: dict, pk: dict) -> dict:
-    if not timings:
+def roofline(timings: dict, pk: dict, name: str | None = None) -> dict:
+    """Roofline of the kernel with the largest timed share (or of `name`)."""
+    if not timings or (name is not None and name not in timings):
         return None
-    name, rec = max(timings.items(), key=lambda kv: kv[1]["ms"])
+    if name is None:
+        name, rec = max(timings.items(), key=lambda kv: kv[1]["ms"])
+    else:
+        rec = timings[name]
     bound, unit = KERNEL_KIND.get(name, ("alu", "fp32"))
     per_launch_s = rec["ms"] / 1e3 / max(rec["launches"], 1)
     work = rec["work"] / max(rec["launches"], 1)
@@ -168,6 +173,11 @@ def roofline(timings: dict, pk: dict) -> dict:
     elif unit == "fp64":
         ach, peak, u = work / per_launch_s / 1e12, 1.25, "TFLOP/s"
         note = "FP64 ALU, nominal 1.25 TFLOP/s"
+    elif unit == "fp32ops":
+        ach = work / per_launch_s / 1e12
+        peak = 152 * 128 * pk["sm_max_mhz"] * 1e6 / 1e12
+        u = "Top/s"
+        note = "FP32 pipe, 152 SMs x 128 lanes x max SM clock (FADD/FMUL/FFMA = 1 op)"
     else:
         ach = work / per_launch_s / 1e12
         peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
@@ -690,6 +700,8 @@ def run_ours(args):
                            "l2": "flushed between steps (256 MiB write, outside the timed events)",
                            "parallelism": f"{world} independent ranks, poses split (no collective)"},
                 "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline_pose_kernels": {k: roofline(timings, pk, k) for k in
+                                          ("k_sorted_wform_grad", "k_sorted_wform") if k in timings},
                 "clocks": clocks,
                 "kernels_ms_per_step": {r["name"]: round(r["ms"] / args.steps, 4) for r in top}}
         print(json.dumps(line), flush=True)

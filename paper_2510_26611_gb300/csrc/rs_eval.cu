@@ -227,7 +227,7 @@ rs_status launch_tucker(const EvalLaunch& a, cudaStream_t st) {
     long long grid = std::min<long long>(nblocks, (long long)std::max(per_sm, 1) * num_sms());
     if (a.grid > 0) grid = std::min<long long>(nblocks, a.grid);
     if (grid < 1) return RS_OK;
-    double work = (double)a.P * a.lig.L * wform_flops_per_atom(RP, GRAD);
+    double work = (double)a.P * a.lig.L * wform_ops_per_atom(RP, GRAD);
     {
         ::rs::KernelTimer kt__(kname, st, work, true, a.events);
         kern<<<(unsigned)grid, 128, sm, st>>>(a.prot, a.lig, a.rot, a.trans, a.P, PB, a.E, a.flags,

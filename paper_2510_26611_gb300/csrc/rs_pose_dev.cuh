@@ -521,13 +521,14 @@ size_t wform_smem(int PB, int L) {
     return (s + 15) / 16 * 16;
 }
 
-// FP32 flops (FMA = 2) per atom of the W-form evaluation: per (a, b) one pair
-// lerp (16) and one (energy) or three (gradient) Dot2 steps (15 each); per a one
-// or four Dot2 steps; one pair lerp (16) per column of v1 and v2; pose transform,
-// cell index and reduction ~60 (energy) / ~80 (gradient).
-inline double wform_flops_per_atom(int RP, bool grad) {
+// FP32 pipe operations (FADD, FMUL and FFMA each count 1) per atom of the W-form
+// evaluation: per (a, b) one pair lerp (14) and one (energy) or three (gradient)
+// Dot2 steps (13 each); per a one or four Dot2 steps; one pair lerp per column of
+// v1 and v2; pose transform, cell index and reduction ~60 (energy) / ~80 (gradient).
+// The counts match the FP32 instruction counters of the kernels within 1%.
+inline double wform_ops_per_atom(int RP, bool grad) {
     double r = RP;
-    return grad ? 61.0 * r * r + 92.0 * r + 80.0 : 31.0 * r * r + 47.0 * r + 60.0;
+    return grad ? 53.0 * r * r + 80.0 * r + 80.0 : 27.0 * r * r + 41.0 * r + 60.0;
 }
 
 }  // namespace

@@ -337,7 +337,7 @@ rs_status launch_sorted_wform(const EvalLaunch& a, const SortedScratch& s, long 
     RS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     long long want = (M + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock);
     long long grid = std::max<long long>(1, std::min<long long>(want, (long long)std::max(per_sm, 1) * sms));
-    double work = (double)M * wform_flops_per_atom(RP, GRAD);
+    double work = (double)M * wform_ops_per_atom(RP, GRAD);
     {
         ::rs::KernelTimer kt__(GRAD ? "k_sorted_wform_grad" : "k_sorted_wform", st, work, true, a.events);
         kern<<<(unsigned)grid, 32 * kWarpsPerBlock, smem, st>>>(a.prot, a.lig, s.srt, s.off, s.shortv, s.contrib);
