@@ -151,8 +151,8 @@ KERNEL_KIND = {
     "k_eval_wform": ("alu", "fp32ops"), "k_eval_wform_grad": ("alu", "fp32ops"),
     "k_eval_canon": ("alu", "fp32"), "k_eval_canon_grad": ("alu", "fp32"),
     "k_sorted_wform": ("alu", "fp32ops"), "k_sorted_wform_grad": ("alu", "fp32ops"),
-    "k_project": ("alu", "fp64"), "k_core": ("alu", "fp64"), "k_gauss_dsum": ("alu", "fp64"),
-    "k_gram": ("alu", "fp64"), "k_gemm_gq": ("alu", "fp64"), "k_canon_factors": ("hbm", "bytes"),
+    "k_project": ("alu", "fp32ops"), "k_core": ("alu", "fp32ops"), "k_gauss_dsum": ("alu", "fp32ops"),
+    "k_gram": ("alu", "fp64"), "k_gemm_gq": ("alu", "fp32ops"), "k_canon_factors": ("hbm", "bytes"),
 }
 
 

@@ -10,7 +10,9 @@
 //                 3. interpolative ("skeleton") rows S of V: V' = V V[S,:]^{-1};
 //                    the Tucker tensor is rewritten exactly in this basis
 //                 4. C' = (V V[S,:]^T)^T U and core beta' = sum_r xi_r C'1 o C'2 o C'3
-// The whole pipeline is FP64; factors are stored FP32 for evaluation.
+// The Gram, the subspace iteration and the skeleton are FP64; the projections and
+// the core run in float-pair arithmetic on the FP32 pipes (about 2^-47 relative per
+// operation); factors are stored as float pairs for evaluation.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -198,7 +200,9 @@ __global__ void k_canon_factors(int n, double b, double h, int N, int Rl,
 // D_k(y) = sum_m |z_m|^(2/3) e^{-2 t^2 (y - x_m)^2},  y_s = -b + s h/2 (half grid).
 // One thread: SC half-grid points, one (axis, k), MC atoms.  Each Gaussian is
 // walked from its point nearest to x_m outwards with the exact ratio recurrence
-// g_{s+1} = g_s rho_s, rho_{s+1} = rho_s c, so every step is two multiplies.
+// g_{s+1} = g_s rho_s, rho_{s+1} = rho_s c; the two seeds per (atom, chunk) are
+// FP64 exponentials, the walk and the sums are float pairs on the FP32 pipes
+// (about 2^-47 relative per step, at most 31 steps from a seed).
 constexpr int kSC = 32;
 constexpr int kMC = 128;
 
@@ -207,6 +211,7 @@ __global__ void __launch_bounds__(128) k_gauss_dsum(int n, double b, double h, i
                                                      const double* __restrict__ cz,
                                                      const double* __restrict__ tl, int nsc,
                                                      int nmc, double* __restrict__ Dp) {
+    using dev::F2;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long total = (long long)nsc * Rl * 3 * nmc;
     if (idx >= total) return;
@@ -218,33 +223,36 @@ __global__ void __launch_bounds__(128) k_gauss_dsum(int n, double b, double h, i
     int mc = (int)(rest / 3);
     const int S = 2 * n - 1;
     const double delta = 0.5 * h;
+    const double inv_delta = 1.0 / delta;
     const int s0 = sc * kSC;
     const double y0 = -b + s0 * delta;
     const double t2 = 2.0 * tl[k] * tl[k];
     const double cq = exp(-2.0 * t2 * delta * delta);
-    double acc[kSC];
+    const F2 cqp = dev::df_from(cq);
+    F2 acc[kSC];
 #pragma unroll
-    for (int s = 0; s < kSC; ++s) acc[s] = 0.0;
+    for (int s = 0; s < kSC; ++s) acc[s] = F2{0.f, 0.f};
     int m_end = min(N, (mc + 1) * kMC);
     for (int m = mc * kMC; m < m_end; ++m) {
         double xm = xyz[3 * (size_t)m + ax];
-        double u = (xm - y0) / delta;
+        double u = (xm - y0) * inv_delta;
         u = fmin(fmax(u, 0.0), (double)(kSC - 1));
         int sp = (int)rint(u);
         double dp = y0 + sp * delta - xm;
         double arg = t2 * dp * dp;
         if (arg > 50.0) continue;  // the whole chunk is below e^-50 of the peak
-        double g0 = cz[m] * exp(-arg);
-        double rf = exp(-t2 * (2.0 * dp * delta + delta * delta));
-        double rb = cq / rf;
-        double g = g0, r = rf;
+        double e1 = exp(-t2 * (2.0 * dp * delta + delta * delta));
+        const F2 g0 = dev::df_from(cz[m] * exp(-arg));
+        const F2 rf = dev::df_from(e1);
+        const F2 rb = dev::df_from(cq / e1);
+        F2 g = g0, r = rf;
 #pragma unroll
         for (int s = 0; s < kSC; ++s) {
-            if (s == sp) acc[s] += g0;
+            if (s == sp) dev::df_acc(acc[s], g0);
             if (s > sp) {
-                g *= r;
-                r *= cq;
-                acc[s] += g;
+                g = dev::df_mul(g, r);
+                r = dev::df_mul(r, cqp);
+                dev::df_acc(acc[s], g);
             }
         }
         g = g0;
@@ -252,16 +260,16 @@ __global__ void __launch_bounds__(128) k_gauss_dsum(int n, double b, double h, i
 #pragma unroll
         for (int s = kSC - 1; s >= 0; --s) {
             if (s < sp) {
-                g *= r;
-                r *= cq;
-                acc[s] += g;
+                g = dev::df_mul(g, r);
+                r = dev::df_mul(r, cqp);
+                dev::df_acc(acc[s], g);
             }
         }
     }
     double* out = Dp + (((size_t)mc * 3 + ax) * Rl + k) * S;
 #pragma unroll
     for (int s = 0; s < kSC; ++s)
-        if (s0 + s < S) out[s0 + s] = acc[s];
+        if (s0 + s < S) out[s0 + s] = dev::df_to(acc[s]);
 }
 
 __global__ void k_sum_chunks(size_t len, int nchunk, const double* __restrict__ in,
@@ -283,7 +291,7 @@ __global__ void k_exp_table(int n, double h, int Rl, const double* __restrict__ 
 }
 
 __global__ void k_gram(int n, int Rl, const double* __restrict__ w2, const double* __restrict__ E,
-                       const double* __restrict__ D, double* __restrict__ G) {
+                       const double* __restrict__ D, float2* __restrict__ G) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     int ax = blockIdx.z;
@@ -293,14 +301,18 @@ __global__ void k_gram(int n, int Rl, const double* __restrict__ w2, const doubl
     const double* Dax = D + (size_t)ax * Rl * S;
     double s = 0.0;
     for (int k = 0; k < Rl; ++k) s += w2[k] * E[(size_t)k * n + d] * Dax[(size_t)k * S + i + j];
-    G[((size_t)ax * n + i) * n + j] = s;
+    const dev::F2 g = dev::df_from(s);
+    G[((size_t)ax * n + i) * n + j] = make_float2(g.h, g.l);
 }
 
-__global__ void k_trace(int n, const double* __restrict__ G, double* __restrict__ tr) {
+__global__ void k_trace(int n, const float2* __restrict__ G, double* __restrict__ tr) {
     __shared__ double sm[kBlock];
     int ax = blockIdx.x;
     double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += G[((size_t)ax * n + i) * n + i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 g = G[((size_t)ax * n + i) * n + i];
+        s += dev::df_to(dev::F2{g.x, g.y});
+    }
     sm[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -325,83 +337,43 @@ __global__ void k_init_block(int n, int p, double* __restrict__ Q) {
     Q[idx] = (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-// Y[ax] = G[ax] Q[ax]: G n x n, Q n x p (p <= 48).  CTA: 16 rows x p columns.
-__global__ void __launch_bounds__(256) k_gemm_gq(int n, int p, const double* __restrict__ G,
-                                                  const double* __restrict__ Q,
-                                                  double* __restrict__ Y) {
-    __shared__ double Gs[16][33];
-    __shared__ double Qs[32][48];
-    int ax = blockIdx.z;
-    int i0 = blockIdx.x * 16;
-    int r = threadIdx.x / 16, cg = threadIdx.x % 16;
-    const double* Ga = G + (size_t)ax * n * n;
-    const double* Qa = Q + (size_t)ax * n * p;
-    double acc[3] = {0, 0, 0};
-    for (int k0 = 0; k0 < n; k0 += 32) {
-        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
-            int rr = e / 32, kk = e % 32;
-            int gi = i0 + rr, gk = k0 + kk;
-            Gs[rr][kk] = (gi < n && gk < n) ? Ga[(size_t)gi * n + gk] : 0.0;
-        }
-        for (int e = threadIdx.x; e < 32 * p; e += 256) {
-            int kk = e / p, c = e % p;
-            int gk = k0 + kk;
-            Qs[kk][c] = gk < n ? Qa[(size_t)gk * p + c] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < 32; ++kk) {
-            double g = Gs[r][kk];
-#pragma unroll
-            for (int u = 0; u < 3; ++u) {
-                int c = cg + 16 * u;
-                if (c < p) acc[u] += g * Qs[kk][c];
-            }
-        }
-        __syncthreads();
-    }
-    int gi = i0 + r;
-    if (gi < n)
-        for (int u = 0; u < 3; ++u) {
-            int c = cg + 16 * u;
-            if (c < p) Y[((size_t)ax * n + gi) * p + c] = acc[u];
-        }
-}
-
-// Y[ax] = G[ax] Q[ax] as k_gemm_gq, and the CTA's partial Gram of its 16 rows,
-// Sp[ax][blk] = Y_blk^T Y_blk (p x p), so CholQR needs no separate pass over Y.
-__global__ void __launch_bounds__(256) k_gemm_gq_gram(int n, int p, const double* __restrict__ G,
-                                                       const double* __restrict__ Q,
-                                                       double* __restrict__ Y,
-                                                       double* __restrict__ Sp) {
-    __shared__ double Gs[16][33];
-    __shared__ double Qs[32][48];
+// Y[ax] = G[ax] Q[ax]: G n x n, Q n x p (p <= 48), both as float pairs; Dot2
+// accumulation on the FP32 pipes, Y written FP64.  CTA: 16 rows x p columns.
+// With Sp != nullptr the CTA also writes the partial Gram of its 16 rows,
+// Sp[ax][blk] = Y_blk^T Y_blk (p x p, FP64), so CholQR needs no separate pass over Y.
+__global__ void __launch_bounds__(256) k_gemm_gq(int n, int p, const float2* __restrict__ G,
+                                                  const float2* __restrict__ Q,
+                                                  double* __restrict__ Y, double* __restrict__ Sp) {
+    using dev::F2;
+    __shared__ float2 Gs[16][33];
+    __shared__ float2 Qs[32][48];
     __shared__ double Ys[16][49];
     int ax = blockIdx.z;
     int i0 = blockIdx.x * 16;
     int r = threadIdx.x / 16, cg = threadIdx.x % 16;
-    const double* Ga = G + (size_t)ax * n * n;
-    const double* Qa = Q + (size_t)ax * n * p;
-    double acc[3] = {0, 0, 0};
+    const float2* Ga = G + (size_t)ax * n * n;
+    const float2* Qa = Q + (size_t)ax * n * p;
+    F2 acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    const float2 z = make_float2(0.f, 0.f);
     for (int k0 = 0; k0 < n; k0 += 32) {
         for (int e = threadIdx.x; e < 16 * 32; e += 256) {
             int rr = e / 32, kk = e % 32;
             int gi = i0 + rr, gk = k0 + kk;
-            Gs[rr][kk] = (gi < n && gk < n) ? Ga[(size_t)gi * n + gk] : 0.0;
+            Gs[rr][kk] = (gi < n && gk < n) ? Ga[(size_t)gi * n + gk] : z;
         }
         for (int e = threadIdx.x; e < 32 * p; e += 256) {
             int kk = e / p, c = e % p;
             int gk = k0 + kk;
-            Qs[kk][c] = gk < n ? Qa[(size_t)gk * p + c] : 0.0;
+            Qs[kk][c] = gk < n ? Qa[(size_t)gk * p + c] : z;
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < 32; ++kk) {
-            double g = Gs[r][kk];
+            const F2 g{Gs[r][kk].x, Gs[r][kk].y};
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
                 int c = cg + 16 * u;
-                if (c < p) acc[u] += g * Qs[kk][c];
+                if (c < p) dev::df_fma_acc(acc[u], g, F2{Qs[kk][c].x, Qs[kk][c].y});
             }
         }
         __syncthreads();
@@ -410,11 +382,12 @@ __global__ void __launch_bounds__(256) k_gemm_gq_gram(int n, int p, const double
     for (int u = 0; u < 3; ++u) {
         int c = cg + 16 * u;
         if (c < p) {
-            double v = gi < n ? acc[u] : 0.0;
+            double v = gi < n ? dev::df_to(acc[u]) : 0.0;
             Ys[r][c] = v;
             if (gi < n) Y[((size_t)ax * n + gi) * p + c] = v;
         }
     }
+    if (Sp == nullptr) return;
     __syncthreads();
     double* out = Sp + ((size_t)ax * gridDim.x + blockIdx.x) * p * p;
     for (int e = threadIdx.x; e < p * p; e += 256) {
@@ -511,9 +484,10 @@ __global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restri
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) Ra[e] = Ri[e / p][e % p];
 }
 
-// Q = Y Rinv (Rinv upper triangular), n x p.
+// Q = Y Rinv (Rinv upper triangular), n x p; Q2 (if not null) gets Q as float pairs.
 __global__ void k_apply_rinv(int n, int p, const double* __restrict__ Y,
-                             const double* __restrict__ Rinv, double* __restrict__ Q) {
+                             const double* __restrict__ Rinv, double* __restrict__ Q,
+                             float2* __restrict__ Q2) {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     int ax = blockIdx.y;
     if (idx >= (size_t)n * p) return;
@@ -523,6 +497,10 @@ __global__ void k_apply_rinv(int n, int p, const double* __restrict__ Y,
     double s = 0.0;
     for (int k = 0; k <= c; ++k) s += Ya[k] * Ra[(size_t)k * p + c];
     Q[((size_t)ax * n + i) * p + c] = s;
+    if (Q2) {
+        const dev::F2 q = dev::df_from(s);
+        Q2[((size_t)ax * n + i) * p + c] = make_float2(q.h, q.l);
+    }
 }
 
 // Symmetric eigen-decomposition of H (p x p, p even, <= 48) by parallel cyclic
@@ -758,11 +736,11 @@ __global__ void __launch_bounds__(512) k_skeleton(int n, int RP, const int* __re
     for (int i = threadIdx.x; i < RP; i += blockDim.x) Sidx[ax * RS_MAX_TUCKER + i] = i < r ? sel[i] : -1;
 }
 
-// Vs = V Ainv (the cardinal evaluation basis) and Wp = V V[S,:]^T, both FP64.
+// Vs = V Ainv (the cardinal evaluation basis, FP64) and Wp = V V[S,:]^T (float pairs).
 __global__ void k_skeleton_apply(int n, int RP, const int* __restrict__ r_ax,
                                  const double* __restrict__ V, const double* __restrict__ Ainv,
                                  const int* __restrict__ Sidx, double* __restrict__ Vs,
-                                 double* __restrict__ Wp) {
+                                 float2* __restrict__ Wp2) {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     int ax = blockIdx.y;
     if (idx >= (size_t)n * RP) return;
@@ -778,7 +756,8 @@ __global__ void k_skeleton_apply(int n, int RP, const int* __restrict__ r_ax,
         for (int k = 0; k < r; ++k) w += Vr[k] * Vsr[k];
     }
     Vs[((size_t)ax * n + i) * RP + c] = s;
-    Wp[((size_t)ax * n + i) * RP + c] = w;
+    const dev::F2 wp = dev::df_from(w);
+    Wp2[((size_t)ax * n + i) * RP + c] = make_float2(wp.h, wp.l);
 }
 
 __device__ __forceinline__ void split_pair(double v, float& h, float& l) {
@@ -825,17 +804,24 @@ __global__ void k_wtable(int n, int RP, const double* __restrict__ Vs3,
     split_pair(d, out[2 * plane + o], out[3 * plane + o]);
 }
 
-// C'[ax][a][(m,k)] = sum_i Wp[ax][i][a] exp(-t_k^2 (x_i - x_m^ax)^2)   (FP64).
-// CTA: 128 atoms, one (k, axis).  The CTA walks the union of the atoms' support
-// windows; each thread runs its Gaussian by the ratio recurrence from the first
-// row where the exponent is <= 700.
+// C'[ax][a][(m,k)] = sum_i Wp[ax][i][a] exp(-t_k^2 (x_i - x_m^ax)^2), in float-pair
+// arithmetic on the FP32 pipes (GB300's FP64 rate is 1/64 of its FP32 rate).
+// CTA: 128 atoms, one (k, axis).  The CTA walks the union of the atoms' windows
+// (rows where the exponent is <= 46, i.e. the Gaussian is >= 1e-20 of its peak);
+// each thread runs its Gaussian by the ratio recurrence g <- g rho, rho <- rho q
+// (q = exp(-2 t^2 h^2)) in pairs, re-seeded from FP64 exponentials every 256 rows
+// so the recurrence error stays ~1e-12; Gaussians narrower than the grid
+// (t^2 h^2 > 8) are evaluated directly at every row.
+constexpr int kProjReseed = 256;
+
 template <int RP>
 __global__ void __launch_bounds__(128) k_project(int n, double b, double h, int N, int Rl,
                                                   const double* __restrict__ xyz,
                                                   const double* __restrict__ tl,
-                                                  const double* __restrict__ Wp,
-                                                  double* __restrict__ Cp) {
-    __shared__ double Ws[32][RP];
+                                                  const float2* __restrict__ Wp2,
+                                                  float2* __restrict__ Cp2) {
+    using dev::F2;
+    __shared__ float2 Ws[32][RP];
     __shared__ int wlo[128], whi[128];
     int k = blockIdx.y, ax = blockIdx.z;
     int m = blockIdx.x * 128 + threadIdx.x;
@@ -843,13 +829,13 @@ __global__ void __launch_bounds__(128) k_project(int n, double b, double h, int 
     double t2 = tl[k] * tl[k];
     double xm = valid ? xyz[3 * (size_t)m + ax] : 0.0;
     int lo = n, hi = -1;
-    bool direct = t2 * h * h > 50.0;  // narrower than the grid: no recurrence
+    const bool direct = t2 * h * h > 8.0;
     if (valid) {
         if (t2 == 0.0) {
             lo = 0;
             hi = n - 1;
         } else {
-            double hw = sqrt(700.0 / t2);
+            double hw = sqrt(46.0 / t2);
             double l = ceil((xm - hw + b) / h), u = floor((xm + hw + b) / h);
             l = fmax(l, 0.0);
             u = fmin(u, (double)(n - 1));
@@ -871,33 +857,36 @@ __global__ void __launch_bounds__(128) k_project(int n, double b, double h, int 
     }
     int ulo = wlo[0], uhi = whi[0];
     __syncthreads();
-    double acc[RP];
+    F2 acc[RP];
 #pragma unroll
-    for (int a = 0; a < RP; ++a) acc[a] = 0.0;
-    const double cq = exp(-2.0 * t2 * h * h);
-    double g = 0.0, rho = 0.0;
-    const double* Wa = Wp + (size_t)ax * n * RP;
+    for (int a = 0; a < RP; ++a) acc[a] = F2{0.f, 0.f};
+    const F2 cq = dev::df_from(direct ? 0.0 : exp(-2.0 * t2 * h * h));
+    F2 g{0.f, 0.f}, rho{0.f, 0.f};
+    int since = 0;
+    const float2* Wa = Wp2 + (size_t)ax * n * RP;
     for (int i0 = ulo; i0 <= uhi; i0 += 32) {
         for (int e = threadIdx.x; e < 32 * RP; e += 128) {
             int ii = e / RP, c = e % RP;
             int gi = i0 + ii;
-            Ws[ii][c] = gi <= uhi ? Wa[(size_t)gi * RP + c] : 0.0;
+            Ws[ii][c] = gi <= uhi ? Wa[(size_t)gi * RP + c] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         int iend = min(32, uhi - i0 + 1);
         for (int ii = 0; ii < iend; ++ii) {
             int i = i0 + ii;
             if (i < lo || i > hi) continue;
-            double d = (-b + i * h) - xm;
-            if (i == lo || direct) {
-                g = exp(-t2 * d * d);
-                rho = exp(-t2 * (2.0 * d * h + h * h));
+            if (i == lo || direct || since == kProjReseed) {
+                double d = (-b + i * h) - xm;
+                g = dev::df_from(exp(-t2 * d * d));
+                rho = dev::df_from(exp(-t2 * (2.0 * d * h + h * h)));
+                since = 0;
             } else {
-                g *= rho;
-                rho *= cq;
+                g = dev::df_mul(g, rho);
+                rho = dev::df_mul(rho, cq);
             }
+            ++since;
 #pragma unroll
-            for (int a = 0; a < RP; ++a) acc[a] += Ws[ii][a] * g;
+            for (int a = 0; a < RP; ++a) dev::df_fma_acc(acc[a], F2{Ws[ii][a].x, Ws[ii][a].y}, g);
         }
         __syncthreads();
     }
@@ -905,50 +894,58 @@ __global__ void __launch_bounds__(128) k_project(int n, double b, double h, int 
         size_t Rp = (size_t)N * Rl;
         size_t col = (size_t)m * Rl + k;
 #pragma unroll
-        for (int a = 0; a < RP; ++a) Cp[((size_t)ax * RP + a) * Rp + col] = acc[a];
+        for (int a = 0; a < RP; ++a) {
+            float sh, sl;
+            dev::two_sum(acc[a].h, acc[a].l, sh, sl);
+            Cp2[((size_t)ax * RP + a) * Rp + col] = make_float2(sh, sl);
+        }
     }
 }
 
-// Partial cores over column chunks: Bp[chunk][a][b][c] = sum_r xi_r C'1[a,r] C'2[b,r] C'3[c,r].
-// CTA: RP*RP threads, thread = (a, b), CH columns per CTA.
+// Partial cores over column chunks: Bp[chunk][a][b][c] = sum_r xi_r C'1[a,r] C'2[b,r] C'3[c,r],
+// in float-pair arithmetic; CTA: RP*RP threads, thread = (a, b), CH columns per CTA.
 template <int RP>
 __global__ void __launch_bounds__(1024) k_core(int Rtot, int Rl, int CH,
                                                const double* __restrict__ q,
                                                const double* __restrict__ al,
-                                               const double* __restrict__ Cp,
+                                               const float2* __restrict__ Cp2,
                                                double* __restrict__ Bp) {
-    __shared__ double C1s[32][RP], C2s[32][RP], C3s[32][RP], xis[32];
+    using dev::F2;
+    __shared__ float2 C1s[32][RP], C2s[32][RP], C3s[32][RP], xis[32];
     int chunk = blockIdx.x;
     int a = threadIdx.x / RP, bb = threadIdx.x % RP;
-    double acc[RP];
+    F2 acc[RP];
 #pragma unroll
-    for (int c = 0; c < RP; ++c) acc[c] = 0.0;
+    for (int c = 0; c < RP; ++c) acc[c] = F2{0.f, 0.f};
     int r0 = chunk * CH, r1 = min(Rtot, r0 + CH);
     for (int t0 = r0; t0 < r1; t0 += 32) {
         for (int e = threadIdx.x; e < 32 * RP; e += blockDim.x) {
             int j = e / RP, c = e % RP;
             int col = t0 + j;
             bool ok = col < r1;
-            C1s[j][c] = ok ? Cp[((size_t)0 * RP + c) * Rtot + col] : 0.0;
-            C2s[j][c] = ok ? Cp[((size_t)1 * RP + c) * Rtot + col] : 0.0;
-            C3s[j][c] = ok ? Cp[((size_t)2 * RP + c) * Rtot + col] : 0.0;
+            float2 z = make_float2(0.f, 0.f);
+            C1s[j][c] = ok ? Cp2[((size_t)0 * RP + c) * Rtot + col] : z;
+            C2s[j][c] = ok ? Cp2[((size_t)1 * RP + c) * Rtot + col] : z;
+            C3s[j][c] = ok ? Cp2[((size_t)2 * RP + c) * Rtot + col] : z;
         }
         for (int j = threadIdx.x; j < 32; j += blockDim.x) {
             int col = t0 + j;
-            xis[j] = col < r1 ? q[col / Rl] * al[col % Rl] : 0.0;
+            F2 x = dev::df_from(col < r1 ? q[col / Rl] * al[col % Rl] : 0.0);
+            xis[j] = make_float2(x.h, x.l);
         }
         __syncthreads();
         int jend = min(32, r1 - t0);
         for (int j = 0; j < jend; ++j) {
-            double u = xis[j] * C1s[j][a] * C2s[j][bb];
+            F2 u = dev::df_mul(dev::df_mul(F2{xis[j].x, xis[j].y}, F2{C1s[j][a].x, C1s[j][a].y}),
+                               F2{C2s[j][bb].x, C2s[j][bb].y});
 #pragma unroll
-            for (int c = 0; c < RP; ++c) acc[c] += u * C3s[j][c];
+            for (int c = 0; c < RP; ++c) dev::df_fma_acc(acc[c], u, F2{C3s[j][c].x, C3s[j][c].y});
         }
         __syncthreads();
     }
     double* out = Bp + (size_t)chunk * RP * RP * RP + ((size_t)a * RP + bb) * RP;
 #pragma unroll
-    for (int c = 0; c < RP; ++c) out[c] = acc[c];
+    for (int c = 0; c < RP; ++c) out[c] = dev::df_to(acc[c]);
 }
 
 // Table of the short-range radial function f(s) = sum_short a_k exp(-t_k^2 s) and of
@@ -973,21 +970,22 @@ __global__ void k_to_float(size_t len, const double* __restrict__ in, float* __r
 template <int RP>
 rs_status launch_project_core(cudaStream_t st, int n, double b, double h, int N, int Rl,
                               const double* xyz, const double* q, const double* tl,
-                              const double* al, const double* Wp, double* Cp, double* Bp,
+                              const double* al, const float2* Wp2, float2* Cp2, double* Bp,
                               int nchunk, int CH, double proj_points) {
     dim3 gp((N + 127) / 128, Rl, 3);
-    // FP64 flops: per active (row, atom, term): 2 (recurrence) + 2 RP (accumulate)
-    double work = proj_points * (2.0 + 2.0 * RP);
+    // FP32 pipe ops per active (row, atom, term): two pair products (9 each) and RP
+    // Dot2 steps (13 each)
+    double work = proj_points * (18.0 + 13.0 * RP);
     {
         ::rs::KernelTimer kt__("k_project", st, work, true);
-        k_project<RP><<<gp, 128, 0, st>>>(n, b, h, N, Rl, xyz, tl, Wp, Cp);
+        k_project<RP><<<gp, 128, 0, st>>>(n, b, h, N, Rl, xyz, tl, Wp2, Cp2);
     }
-    // FP64 flops: per column and (a, b): 2 (xi C1 C2) + 2 RP (accumulate over c)
-    work = (double)N * Rl * RP * RP * (2.0 + 2.0 * RP);
+    // FP32 pipe ops per column and (a, b): two pair products (9 each) and RP Dot2 steps
+    work = (double)N * Rl * RP * RP * (18.0 + 13.0 * RP);
     RS_TRY_CUDA(cudaGetLastError());
     {
         ::rs::KernelTimer kt__("k_core", st, work, true);
-        k_core<RP><<<nchunk, RP * RP, 0, st>>>(N * Rl, Rl, CH, q, al, Cp, Bp);
+        k_core<RP><<<nchunk, RP * RP, 0, st>>>(N * Rl, Rl, CH, q, al, Cp2, Bp);
     }
     RS_TRY_CUDA(cudaGetLastError());
     return RS_OK;
@@ -995,11 +993,11 @@ rs_status launch_project_core(cudaStream_t st, int n, double b, double h, int N,
 
 rs_status dispatch_project_core(int RP, cudaStream_t st, int n, double b, double h, int N, int Rl,
                                 const double* xyz, const double* q, const double* tl,
-                                const double* al, const double* Wp, double* Cp, double* Bp,
+                                const double* al, const float2* Wp2, float2* Cp2, double* Bp,
                                 int nchunk, int CH, double proj_points) {
     switch (RP) {
 #define RS_CASE(R) \
-    case R: return launch_project_core<R>(st, n, b, h, N, Rl, xyz, q, tl, al, Wp, Cp, Bp, nchunk, CH, proj_points);
+    case R: return launch_project_core<R>(st, n, b, h, N, Rl, xyz, q, tl, al, Wp2, Cp2, Bp, nchunk, CH, proj_points);
         RS_CASE(4) RS_CASE(8) RS_CASE(12) RS_CASE(16) RS_CASE(20) RS_CASE(24) RS_CASE(28) RS_CASE(32)
 #undef RS_CASE
         default:
@@ -1126,7 +1124,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     }
     const int Sh = 2 * n - 1;
     // 1. Gram matrices
-    double *d_cz, *d_w2, *d_E, *d_Dp, *d_D, *d_G, *d_tr;
+    double *d_cz, *d_w2, *d_E, *d_Dp, *d_D, *d_tr;
+    float2* d_G;
     RS_TRY(S.get(&d_cz, N));
     RS_TRY(S.get(&d_w2, Rl));
     RS_TRY_CUDA(cudaMemcpyAsync(d_cz, q_host_abs23.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1146,8 +1145,9 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         ::rs::KernelTimer kt__("k_gauss_dsum", st, 0.0, true);
         k_gauss_dsum<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, b, h, N, Rl, d_xyz, d_cz,
                                                                          d_tl, nsc, nmc, d_Dp);
-        // FP64 flops of the ratio walks: 3 per half-grid point of every chunk that
-        // lies within e^-50 of a Gaussian's peak (closed form per term; only when timed)
+        // FP32 pipe ops of the pair walks: 26 per half-grid point (two pair products,
+        // one pair sum) of every chunk within e^-50 of a Gaussian's peak (closed form
+        // per term; only when timed).  The two FP64 seeds per chunk are not counted.
         if (kt__.active()) {
             const double delta = 0.5 * h;
             double w = 0.0;
@@ -1157,7 +1157,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
                 for (size_t e = 0; e < xyz_host.size(); ++e) {
                     double lo = std::max(0.0, std::floor((xyz_host[e] - reach + b) / delta / kSC));
                     double hi = std::min((double)(nsc - 1), std::floor((xyz_host[e] + reach + b) / delta / kSC));
-                    if (hi >= lo) w += (hi - lo + 1) * kSC * 3.0;
+                    if (hi >= lo) w += (hi - lo + 1) * kSC * 26.0;
                 }
             }
             kt__.set_work(w);
@@ -1200,6 +1200,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY(S.get(&d_Ri, (size_t)3 * p * p));
     RS_TRY(S.get(&d_lam, (size_t)3 * p));
     RS_TRY(S.get(&d_W, (size_t)3 * p * p));
+    float2* d_Q2;  // Q as float pairs, the operand of the pair GEMM
+    RS_TRY(S.get(&d_Q2, (size_t)3 * n * p));
     RS_TRY(S.get(&d_fail, 3));
     RS_TRY_CUDA(cudaMemsetAsync(d_fail, 0, 3 * sizeof(int), st));
     {
@@ -1219,7 +1221,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         }
         {
             ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
-            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, src, d_Ri, dst);
+            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, src, d_Ri, dst,
+                                                                                 dst == d_Q ? d_Q2 : nullptr);
         }
         RS_TRY_CUDA(cudaGetLastError());
         return RS_OK;
@@ -1238,12 +1241,12 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     const int nblk = (n + 15) / 16;
     double* d_Sp;
     RS_TRY(S.get(&d_Sp, (size_t)3 * nblk * p * p));
-    work = 3.0 * 2.0 * n * (double)n * p;  // FP64 flops per G Q
+    work = 3.0 * 13.0 * n * (double)n * p;  // FP32 pipe ops per G Q (one Dot2 step per product)
     // one subspace step: Y = G Q with partial Grams, S = Y^T Y, shifted Cholesky, Q = Y R^-1
     auto step = [&]() -> rs_status {
         {
             ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
-            k_gemm_gq_gram<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y, d_Sp);
+            k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q2, d_Y, d_Sp);
         }
         {
             ::rs::KernelTimer kt__("k_sum_gram", st, 0.0, false);
@@ -1255,7 +1258,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         }
         {
             ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
-            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, d_Y, d_Ri, d_Q);
+            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, d_Y, d_Ri, d_Q, d_Q2);
         }
         RS_TRY_CUDA(cudaGetLastError());
         return RS_OK;
@@ -1264,7 +1267,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         RS_TRY(orthonormalize(d_Q));
         {
             ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
-            k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q, d_Y);
+            k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q2, d_Y, nullptr);
         }
         {
             ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
@@ -1331,7 +1334,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     }
     const int RP = (rmax + 3) / 4 * 4;
     int* d_rax;
-    double *d_V, *d_M, *d_Ainv, *d_Wp;
+    double *d_V, *d_M, *d_Ainv;
+    float2* d_Wp;
     int* d_S;
     RS_TRY(S.get(&d_rax, 3));
     RS_TRY_CUDA(cudaMemcpyAsync(d_rax, r_ax, sizeof(r_ax), cudaMemcpyHostToDevice, st));
@@ -1361,7 +1365,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     const int Rtot = N * Rl;
     const int CH = 512;
     const int nchunk = (Rtot + CH - 1) / CH;
-    double *d_Cp, *d_Bp, *d_B;
+    double *d_Bp, *d_B;
+    float2* d_Cp;
     RS_TRY(S.get(&d_Cp, (size_t)3 * RP * Rtot));
     RS_TRY(S.get(&d_Bp, (size_t)nchunk * RP * RP * RP));
     RS_TRY(S.get(&d_B, (size_t)RP * RP * RP));
@@ -1369,7 +1374,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     if (timing_mode() > 0) {
         for (int k = 0; k < Rl; ++k) {
             double t2 = tl_host[k] * tl_host[k];
-            double hw = t2 > 0 ? std::sqrt(700.0 / t2) : 1e300;
+            double hw = t2 > 0 ? std::sqrt(46.0 / t2) : 1e300;
             for (size_t e = 0; e < xyz_host.size(); ++e) {
                 double lo = std::max(0.0, std::ceil((xyz_host[e] - hw + b) / h));
                 double hi = std::min((double)(n - 1), std::floor((xyz_host[e] + hw + b) / h));

@@ -187,6 +187,31 @@ __device__ __forceinline__ void df_fma_acc(F2& acc, F2 x, F2 y) {
     acc.l = __fadd_rn(acc.l, __fadd_rn(__fadd_rn(e, ep), __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.h))));
 }
 
+// Pair product a*b (the lo*lo term dropped; about 2^-47 relative).
+__device__ __forceinline__ F2 df_mul(F2 a, F2 b) {
+    float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+
+// acc += x for pairs (the rounding error of the leading sum is carried in acc.l).
+__device__ __forceinline__ void df_acc(F2& acc, F2 x) {
+    float s, e;
+    two_sum(acc.h, x.h, s, e);
+    acc.h = s;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(e, x.l));
+}
+
+// Pair nearest a double (hi = the float nearest v, lo = the float nearest v - hi),
+// and back.  Values must stay inside the float range.
+__device__ __forceinline__ F2 df_from(double v) {
+    float h = __double2float_rn(v);
+    return {h, __double2float_rn(__dsub_rn(v, (double)h))};
+}
+__device__ __forceinline__ double df_to(F2 a) { return __dadd_rn((double)a.h, (double)a.l); }
+
 // Accumulator of float values carried as an unevaluated pair hi + lo.
 struct FAcc {
     float hi, lo;
