@@ -196,21 +196,30 @@ typedef struct rs_pair {
 typedef struct rs_batch rs_batch;
 
 typedef struct rs_batch_info {
-    int32_t npairs, ngroups;  /* pairs; launches (one per padded Tucker rank)     */
-    int32_t nitems;           /* work items (pose blocks) over all pairs          */
-    int32_t grid;             /* persistent CTAs over all groups                  */
-    int32_t threads;          /* chosen threads per CTA (first group)             */
-    int32_t atoms_per_item;   /* chosen target atoms per item (first group)       */
+    int32_t npairs, ngroups;  /* pairs; groups (one per padded Tucker rank)       */
+    int32_t nitems;           /* per-block path: work items over its groups       */
+    int32_t grid;             /* per-block path: persistent CTAs over its groups  */
+    int32_t threads;          /* per-block path: threads per CTA (first group)    */
+    int32_t atoms_per_item;   /* per-block path: target atoms per item           */
     double  tune_ms;          /* device time the autotuner spent                  */
+    int32_t mode;             /* first group: 0 per-block, 1 cell-grouped         */
+    int32_t warps_per_cta;    /* cell-grouped: warps per CTA of the W-form kernel */
+    int64_t chunk_atoms;      /* cell-grouped: pose-atoms per chunk (at most)     */
+    int32_t nchunks;          /* cell-grouped: chunks over its groups             */
 } rs_batch_info;
 
-/* Algorithm PLIE (Sec. 3.4) for many pairs of uneven size in one persistent
- * launch per padded rank, captured once in a CUDA graph.  Ligands are prepared
- * now; poses are read from the given pointers at each rs_batch_run, so a caller
- * may rewrite them in place between runs.  With autotune != 0 the threads per
- * CTA and atoms per work item are chosen by timing candidates on a quarter of
- * the batch (this writes the output arrays; cached per padded rank for the
- * process).  Energies and flags equal rs_energy_poses bit for bit. */
+/* Algorithm PLIE (Sec. 3.4) for many pairs of uneven size, grouped by padded
+ * rank and captured once in a CUDA graph.  Per group either the cell-grouped
+ * multi-pair pipeline (pose-atoms of all pairs sorted by (pair, grid cell)) or one
+ * persistent per-block launch runs.  autotune = 1: the path and its shape (warps
+ * per CTA and chunk size, or threads per CTA and atoms per work item) are chosen
+ * by timing the candidates on a quarter of the group's poses (this writes the
+ * output arrays; cached per padded rank for the process); 0: the cell-grouped
+ * pipeline with 4 warps per CTA; 2: the per-block launch with its default shape.  Ligands are prepared now;
+ * poses are read from the given pointers at each rs_batch_run, so a caller may
+ * rewrite them in place between runs.  Device scratch: about 110 bytes per
+ * pose-atom of the largest chunk (at most 2^23 pose-atoms).  Energies and flags
+ * equal rs_energy_poses bit for bit. */
 rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int32_t autotune,
                           rs_batch** out);
 /* Replays the batch's graph on `stream` (NULL = the CUDA default stream). */
@@ -227,7 +236,7 @@ rs_status rs_batch_get_info(const rs_batch* batch, rs_batch_info* out);
  *     no context is needed; the call sets the protein's device current and
  *     enqueues on `stream` (NULL = the CUDA default stream);
  *   - the per-call scratch is a fixed array in the library's device image
- *     (about 197 KB on every GPU that loads the library, kept until exit), so
+ *     (288 KiB on every GPU that loads the library, kept until exit), so
  *     L may be at most 4096; larger L returns RS_ERR_UNSUPPORTED;
  *   - the first call on a device looks the array's address up once; make that
  *     first call before any stream capture;
@@ -319,6 +328,13 @@ rs_status rs_serve_get_stats(rs_server* s, rs_serve_stats* out);
 void      rs_serve_destroy(rs_server* s);
 
 /* ----------------------------------------------------------- diagnostics */
+/* The host FP64 symmetric eigensolver the Tucker build uses for its Rayleigh-Ritz
+ * step (Householder tridiagonalisation + implicit QL), exported so that it can be
+ * tested without a GPU.  A: n x n row-major (its symmetric part is used), host
+ * memory; lam: [n] eigenvalues in descending order; W: n x n row-major, column c
+ * the unit eigenvector of lam[c].  RS_ERR_UNSUPPORTED if the iteration does not
+ * converge. */
+rs_status rs_symeig_host(int32_t n, const double* A, double* lam, double* W);
 /* These have no counterpart in the paper: they support measurement.
  * Number of kernels this library has launched in the process (all devices). */
 unsigned long long rs_stats_kernel_launches(void);

@@ -1,12 +1,15 @@
-// Batched pose evaluation: many protein-ligand pairs of uneven sizes in one
-// persistent launch, captured once in a CUDA graph and replayed.
-//
-// Each pair's poses are cut into items of PB poses (PB ~ atoms-per-item / L);
-// items are ordered by work, largest first, and persistent CTAs take them from
-// a device counter.  Every item is computed exactly as the plain kernel computes
-// a pose block, so results do not depend on the mix or on which CTA ran them.
-// The block shape (threads per CTA, atoms per item) is chosen per padded rank by
-// a small autotuner that times the candidates on the batch itself.
+// Batched pose evaluation: many protein-ligand pairs of uneven sizes, captured
+// once in a CUDA graph and replayed.  Pairs are grouped by padded Tucker rank; for
+// each group an autotuner times the candidates on a quarter of the group's poses
+// and keeps the fastest:
+//   * the cell-grouped multi-pair pipeline (rs_group.cu): the pose-atoms of all
+//     pairs sorted by (pair, axis-3 cell), each cell's W slab staged once per warp;
+//     candidates differ in warps per CTA of the W-form kernel and in chunk size;
+//   * one persistent per-block launch: each pair's poses cut into items of PB poses
+//     (PB ~ atoms-per-item / L), largest first, taken from a device counter;
+//     candidates differ in threads per CTA and atoms per item.
+// Both compute every pose exactly as rs_energy_poses does, so results do not depend
+// on the mix, on the choice, or on which CTA ran them.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -19,24 +22,40 @@
 #include "rs_eval.cuh"
 #include "rs_pose_dev.cuh"
 #include "rs_batch_dev.cuh"
+#include "rs_group.cuh"
 
 namespace rs {
 namespace {
 
-const Shape kCandidates[] = {{128, 256}, {128, 512}, {128, 1024}, {256, 512}, {256, 1024}};
+// mode 0: per-block launch with `shape`; mode 1: cell-grouped pipeline with `wpb`
+// warps per W-form CTA and chunks of at most `chunk` pose-atoms.
+struct Choice {
+    int mode;
+    Shape shape;
+    int wpb;
+    long long chunk;
+};
+
+const Choice kCandidates[] = {
+    {1, {128, 512}, 4, 1LL << 23}, {1, {128, 512}, 8, 1LL << 23}, {1, {128, 512}, 4, 1LL << 21},
+    {0, {128, 256}, 0, 0},         {0, {128, 512}, 0, 0},         {0, {128, 1024}, 0, 0},
+    {0, {256, 512}, 0, 0},         {0, {256, 1024}, 0, 0}};
 
 std::mutex g_tune_mu;
-std::map<int, Shape> g_tuned;  // padded rank -> best shape (process-wide cache)
+std::map<int, Choice> g_tuned;  // padded rank -> best choice (process-wide cache)
 
 struct Group {
     int RP;
     std::vector<int> pairs;  // indices into the batch's pair list
+    Choice choice{1, {128, 512}, 4, 1LL << 23};
     Shape shape{128, 512};
     int nitems = 0;
     int grid = 0;
     size_t smem = 0;
     BatchItem* d_items = nullptr;
     int* d_counter = nullptr;
+    GroupPlan plan;
+    GroupSeg* d_segs = nullptr;
 };
 
 }  // namespace
@@ -48,6 +67,8 @@ struct rs_batch {
     std::vector<int> Ls;
     rs::PairDesc* d_pairs = nullptr;
     void* d_lig = nullptr;
+    void* d_ws = nullptr;  // scratch of the cell-grouped pipeline (largest group chunk)
+    size_t ws_bytes = 0;
     std::vector<rs::Group> groups;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -91,7 +112,7 @@ rs_status launch_group_nt(rs_batch* B, Group& g, cudaStream_t st, bool set_attr)
                              : launch_group<RP, 128>(B, g, st, set_attr);
 }
 
-rs_status dispatch_group(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) {
+rs_status dispatch_block(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) {
     switch (g.RP) {
 #define RS_CASE(R) \
     case R: return launch_group_nt<R>(B, g, st, set_attr);
@@ -101,6 +122,51 @@ rs_status dispatch_group(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) 
             set_error("batch: unsupported padded rank %d", g.RP);
             return RS_ERR_UNSUPPORTED;
     }
+}
+
+rs_status dispatch_group(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) {
+    if (g.choice.mode == 0) return dispatch_block(B, g, st, set_attr);
+    return group_launch(g.plan, B->d_pairs, g.d_segs, B->d_ws, B->ws_bytes, g.choice.wpb, st, false);
+}
+
+// Plan of the cell-grouped pipeline over a fraction of each pair's poses, with its
+// segments on the device and the batch scratch grown to fit.
+rs_status build_plan(rs_batch* B, Group& g, double pose_fraction) {
+    std::vector<PairDesc> pairs = B->pairs;
+    if (pose_fraction < 1.0)
+        for (int pi : g.pairs) pairs[pi].P = std::max<long long>(1, (long long)(pairs[pi].P * pose_fraction));
+    RS_TRY(group_plan(pairs, g.pairs, g.choice.chunk, &g.plan));
+    if (g.d_segs) {
+        cudaFree(g.d_segs);
+        B->allocs.erase(std::remove(B->allocs.begin(), B->allocs.end(), (void*)g.d_segs), B->allocs.end());
+        g.d_segs = nullptr;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(1, g.plan.segs.size()) * sizeof(GroupSeg)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("batch: segment table allocation failed");
+        return RS_ERR_OOM;
+    }
+    B->allocs.push_back(p);
+    g.d_segs = (GroupSeg*)p;
+    RS_TRY_CUDA(cudaMemcpy(g.d_segs, g.plan.segs.data(), g.plan.segs.size() * sizeof(GroupSeg),
+                           cudaMemcpyHostToDevice));
+    if (g.plan.scratch > B->ws_bytes) {
+        if (B->d_ws) {
+            cudaFree(B->d_ws);
+            B->allocs.erase(std::remove(B->allocs.begin(), B->allocs.end(), B->d_ws), B->allocs.end());
+            B->d_ws = nullptr;
+            B->ws_bytes = 0;
+        }
+        if (cudaMalloc(&B->d_ws, g.plan.scratch) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("batch: scratch allocation of %zu bytes failed", g.plan.scratch);
+            return RS_ERR_OOM;
+        }
+        B->allocs.push_back(B->d_ws);
+        B->ws_bytes = g.plan.scratch;
+    }
+    return RS_OK;
 }
 
 // Work items of a group for a shape: per pair, blocks of PB poses; largest
@@ -142,14 +208,19 @@ rs_status build_items(rs_batch* B, Group& g, double pose_fraction) {
     return RS_OK;
 }
 
-// Times every candidate shape on a fraction of the group's poses (results are
-// written to the real outputs and overwritten by the real run) and keeps the best.
+rs_status prepare(rs_batch* B, Group& g, double pose_fraction) {
+    g.shape = g.choice.shape;
+    return g.choice.mode == 0 ? build_items(B, g, pose_fraction) : build_plan(B, g, pose_fraction);
+}
+
+// Times every candidate on a fraction of the group's poses (results are written to
+// the real outputs and overwritten by the real run) and keeps the best.
 rs_status tune_group(rs_batch* B, Group& g, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(g.RP);
         if (it != g_tuned.end()) {
-            g.shape = it->second;
+            g.choice = it->second;
             return RS_OK;
         }
     }
@@ -157,10 +228,10 @@ rs_status tune_group(rs_batch* B, Group& g, cudaStream_t st) {
     RS_TRY_CUDA(cudaEventCreate(&a));
     RS_TRY_CUDA(cudaEventCreate(&b));
     float best = 1e30f;
-    Shape best_shape = g.shape;
-    for (const Shape& c : kCandidates) {
-        g.shape = c;
-        RS_TRY(build_items(B, g, 0.25));
+    Choice best_choice = g.choice;
+    for (const Choice& c : kCandidates) {
+        g.choice = c;
+        RS_TRY(prepare(B, g, 0.25));
         RS_TRY(dispatch_group(B, g, st, true));  // warm-up
         float total = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
@@ -175,14 +246,14 @@ rs_status tune_group(rs_batch* B, Group& g, cudaStream_t st) {
         B->tune_ms += total;
         if (total < best) {
             best = total;
-            best_shape = c;
+            best_choice = c;
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    g.shape = best_shape;
+    g.choice = best_choice;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[g.RP] = best_shape;
+    g_tuned[g.RP] = best_choice;
     return RS_OK;
 }
 
@@ -202,8 +273,9 @@ void batch_destroy(rs_batch* B) {
 void batch_shape_for(int RP, int* nt, int* atoms) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(RP);
-    *nt = it != g_tuned.end() ? it->second.nt : 128;
-    *atoms = it != g_tuned.end() ? it->second.atoms : 512;
+    const bool tuned = it != g_tuned.end() && it->second.mode == 0;
+    *nt = tuned ? it->second.shape.nt : 128;
+    *atoms = tuned ? it->second.shape.atoms : 512;
 }
 
 }  // namespace rs
@@ -216,6 +288,7 @@ rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int
     clear_error();
     RS_CHECK_ARG(ctx && pairs && out, "rs_batch_create: NULL argument");
     RS_CHECK_ARG(npairs >= 1 && npairs <= (1 << 20), "rs_batch_create: npairs=%d out of range", npairs);
+    RS_CHECK_ARG(autotune >= 0 && autotune <= 2, "rs_batch_create: autotune=%d not in {0, 1, 2}", autotune);
     *out = nullptr;
     for (int i = 0; i < npairs; ++i) {
         const rs_pair& p = pairs[i];
@@ -259,7 +332,7 @@ rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int
     for (int i = 0; i < npairs; ++i) {
         const rs_pair& p = pairs[i];
         LigandView lig = carve_ligand((char*)B->d_lig + off[i], p.L);
-        rs_status s = launch_prep_ligand(p.L, p.lig_xyz, p.lig_q, (float4*)lig.y, (double*)lig.y64,
+        rs_status s = launch_prep_ligand(p.L, p.lig_xyz, p.lig_q, (float4*)lig.y, (float2*)lig.yd, (double*)lig.y64,
                                          (double*)lig.q64, st, false);
         if (s != RS_OK) return fail(s);
         PairDesc d;
@@ -303,8 +376,9 @@ rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int
     }
     rs_status s;
     for (Group& g : B->groups) {
-        if (autotune && (s = tune_group(B, g, st)) != RS_OK) return fail(s);
-        if ((s = build_items(B, g, 1.0)) != RS_OK) return fail(s);
+        if (autotune == 2) g.choice = Choice{0, {128, 512}, 0, 0};  // per-block path, default shape
+        if (autotune == 1 && (s = tune_group(B, g, st)) != RS_OK) return fail(s);
+        if ((s = prepare(B, g, 1.0)) != RS_OK) return fail(s);
         if ((s = dispatch_group(B, g, st, true)) != RS_OK) return fail(s);  // sets attributes, grid
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) {
@@ -352,12 +426,20 @@ rs_status rs_batch_get_info(const rs_batch* B, rs_batch_info* o) {
     o->npairs = (int32_t)B->pairs.size();
     o->ngroups = (int32_t)B->groups.size();
     for (const rs::Group& g : B->groups) {
-        o->nitems += g.nitems;
-        o->grid += g.grid;
+        if (g.choice.mode == 0) {
+            o->nitems += g.nitems;
+            o->grid += g.grid;
+        } else {
+            o->nchunks += (int32_t)g.plan.chunks.size();
+        }
     }
     if (!B->groups.empty()) {
-        o->threads = B->groups[0].shape.nt;
-        o->atoms_per_item = B->groups[0].shape.atoms;
+        const rs::Group& g = B->groups[0];
+        o->mode = g.choice.mode;
+        o->threads = g.choice.mode == 0 ? g.shape.nt : 0;
+        o->atoms_per_item = g.choice.mode == 0 ? g.shape.atoms : 0;
+        o->warps_per_cta = g.choice.mode == 1 ? g.choice.wpb : 0;
+        o->chunk_atoms = g.choice.mode == 1 ? g.choice.chunk : 0;
     }
     o->tune_ms = B->tune_ms;
     return RS_OK;

@@ -12,16 +12,6 @@
 namespace rs {
 namespace {
 
-struct PairDesc {
-    ProteinView prot;
-    LigandView lig;
-    const double* rot;
-    const double* trans;
-    long long P;
-    double* E;
-    uint8_t* flags;
-};
-
 struct BatchItem {
     int pair;
     int PB;

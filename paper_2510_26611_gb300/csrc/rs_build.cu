@@ -6,7 +6,8 @@
 //   Tucker     : RHOSVD of the same tensor (TEP step 4):
 //                 1. Gram G = Z Z^T of Z = U diag(|xi|^(1/3)) by the Gaussian
 //                    product identity (exact, O(n N R_l) instead of O(n^2 N R_l))
-//                 2. block subspace iteration + Rayleigh-Ritz on G (FP64)
+//                 2. block subspace iteration on G (pair GEMM, FP64 CholQR2) and
+//                    Rayleigh-Ritz (p x p eigenproblems on the host, FP64)
 //                 3. interpolative ("skeleton") rows S of V: V' = V V[S,:]^{-1};
 //                    the Tucker tensor is rewritten exactly in this basis
 //                 4. C' = (V V[S,:]^T)^T U and core beta' = sum_r xi_r C'1 o C'2 o C'3
@@ -66,7 +67,18 @@ struct Scratch {
     }
 };
 
+}  // namespace
+bool symeig_host(int n, const double* A, double* lam, double* W);
+namespace {
+
 inline unsigned blocks_for(size_t n, int bs = kBlock) { return (unsigned)((n + bs - 1) / bs); }
+
+// Float pair (hi, lo) of a double on the host: hi the nearest float, lo the nearest
+// float to the remainder.
+inline void split_host(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
 
 // ------------------------------------------------------------------ cell list
 __global__ void k_bbox(int N, const double* __restrict__ xyz, double* __restrict__ out) {
@@ -145,10 +157,12 @@ __global__ void k_cell_fill(int N, const int* __restrict__ cell_of, const int* _
 }
 
 // Sorts each cell's atoms by original index (so the layout does not depend on
-// atomic ordering) and writes the FP32 and FP64 atom records.
+// atomic ordering) and writes the atom records as float pairs: atoms holds the
+// floats nearest (x, y, z, q), atoms_lo the remainders; atoms64 the FP64 record.
 __global__ void k_cell_sort(int ncell, const int* __restrict__ start, int* __restrict__ perm,
                             const double* __restrict__ xyz, const double* __restrict__ q,
-                            float4* __restrict__ atoms, D4* __restrict__ atoms64) {
+                            float4* __restrict__ atoms, float4* __restrict__ atoms_lo,
+                            double4* __restrict__ atoms64) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     int s = start[c], e = start[c + 1];
@@ -163,9 +177,11 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ start, int* __res
     }
     for (int a = s; a < e; ++a) {
         int i = perm[a];
-        double x = xyz[3 * (size_t)i], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
-        atoms[a] = make_float4((float)x, (float)y, (float)z, (float)q[i]);
-        atoms64[a] = D4{x, y, z, q[i]};
+        const dev::F2 x = dev::df_from(xyz[3 * (size_t)i]), y = dev::df_from(xyz[3 * (size_t)i + 1]),
+                      z = dev::df_from(xyz[3 * (size_t)i + 2]), w = dev::df_from(q[i]);
+        atoms[a] = make_float4(x.h, y.h, z.h, w.h);
+        atoms_lo[a] = make_float4(x.l, y.l, z.l, w.l);
+        atoms64[a] = make_double4(xyz[3 * (size_t)i], xyz[3 * (size_t)i + 1], xyz[3 * (size_t)i + 2], q[i]);
     }
 }
 
@@ -337,55 +353,87 @@ __global__ void k_init_block(int n, int p, double* __restrict__ Q) {
     Q[idx] = (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-// Y[ax] = G[ax] Q[ax]: G n x n, Q n x p (p <= 48), both as float pairs; Dot2
-// accumulation on the FP32 pipes, Y written FP64.  CTA: 16 rows x p columns.
-// With Sp != nullptr the CTA also writes the partial Gram of its 16 rows,
-// Sp[ax][blk] = Y_blk^T Y_blk (p x p, FP64), so CholQR needs no separate pass over Y.
+// Y[ax] = G[ax] Q[ax] (G n x n, Q n x p, p <= 48, both float pairs), split over K:
+// CTA (row block of 32, K slice ks, axis) writes the partial product of its K slice
+// to Yp[ks][ax] (FP64).  Thread tile 2 rows x 3 columns (six independent Dot2
+// accumulators); KS slices give enough CTAs to fill the GPU for n ~ 1000.
+constexpr int kGemmKS = 4;
+
 __global__ void __launch_bounds__(256) k_gemm_gq(int n, int p, const float2* __restrict__ G,
-                                                  const float2* __restrict__ Q,
-                                                  double* __restrict__ Y, double* __restrict__ Sp) {
+                                                  const float2* __restrict__ Q, double* __restrict__ Yp) {
     using dev::F2;
-    __shared__ float2 Gs[16][33];
+    __shared__ float2 Gs[32][33];
     __shared__ float2 Qs[32][48];
-    __shared__ double Ys[16][49];
-    int ax = blockIdx.z;
-    int i0 = blockIdx.x * 16;
-    int r = threadIdx.x / 16, cg = threadIdx.x % 16;
+    const int ax = blockIdx.z, ks = blockIdx.y;
+    const int i0 = blockIdx.x * 32;
+    const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+    const int kchunk = ((n + kGemmKS - 1) / kGemmKS + 31) / 32 * 32;
+    const int kbeg = ks * kchunk, kend = min(n, kbeg + kchunk);
     const float2* Ga = G + (size_t)ax * n * n;
     const float2* Qa = Q + (size_t)ax * n * p;
-    F2 acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    F2 acc[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int u = 0; u < 3; ++u) acc[a][u] = F2{0.f, 0.f};
     const float2 z = make_float2(0.f, 0.f);
-    for (int k0 = 0; k0 < n; k0 += 32) {
-        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+    for (int k0 = kbeg; k0 < kend; k0 += 32) {
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
             int rr = e / 32, kk = e % 32;
             int gi = i0 + rr, gk = k0 + kk;
-            Gs[rr][kk] = (gi < n && gk < n) ? Ga[(size_t)gi * n + gk] : z;
+            Gs[rr][kk] = (gi < n && gk < kend) ? Ga[(size_t)gi * n + gk] : z;
         }
         for (int e = threadIdx.x; e < 32 * p; e += 256) {
             int kk = e / p, c = e % p;
             int gk = k0 + kk;
-            Qs[kk][c] = gk < n ? Qa[(size_t)gk * p + c] : z;
+            Qs[kk][c] = gk < kend ? Qa[(size_t)gk * p + c] : z;
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < 32; ++kk) {
-            const F2 g{Gs[r][kk].x, Gs[r][kk].y};
+            const F2 g0{Gs[2 * tr][kk].x, Gs[2 * tr][kk].y}, g1{Gs[2 * tr + 1][kk].x, Gs[2 * tr + 1][kk].y};
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
-                int c = cg + 16 * u;
-                if (c < p) dev::df_fma_acc(acc[u], g, F2{Qs[kk][c].x, Qs[kk][c].y});
+                const int c = tc + 16 * u;
+                if (c < p) {
+                    const F2 q{Qs[kk][c].x, Qs[kk][c].y};
+                    dev::df_fma_acc(acc[0][u], g0, q);
+                    dev::df_fma_acc(acc[1][u], g1, q);
+                }
             }
         }
         __syncthreads();
     }
-    int gi = i0 + r;
-    for (int u = 0; u < 3; ++u) {
-        int c = cg + 16 * u;
-        if (c < p) {
-            double v = gi < n ? dev::df_to(acc[u]) : 0.0;
-            Ys[r][c] = v;
-            if (gi < n) Y[((size_t)ax * n + gi) * p + c] = v;
+    double* out = Yp + ((size_t)ks * 3 + ax) * n * p;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int gi = i0 + 2 * tr + a;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int c = tc + 16 * u;
+            if (c < p) out[(size_t)gi * p + c] = dev::df_to(acc[a][u]);
         }
+    }
+}
+
+// Y = sum over the K slices of Yp (fixed order), and with Sp != nullptr the partial
+// Gram of each 16-row block, Sp[ax][blk] = Y_blk^T Y_blk (p x p, FP64), so CholQR
+// needs no separate pass over Y.  CTA: 16 rows of one axis.
+__global__ void __launch_bounds__(256) k_gemm_reduce(int n, int p, const double* __restrict__ Yp,
+                                                      double* __restrict__ Y, double* __restrict__ Sp) {
+    __shared__ double Ys[16][49];
+    const int ax = blockIdx.y;
+    const int i0 = blockIdx.x * 16;
+    for (int e = threadIdx.x; e < 16 * p; e += 256) {
+        const int r = e / p, c = e % p;
+        const int gi = i0 + r;
+        double v = 0.0;
+        if (gi < n) {
+            for (int ks = 0; ks < kGemmKS; ++ks) v += Yp[(((size_t)ks * 3 + ax) * n + gi) * p + c];
+            Y[((size_t)ax * n + gi) * p + c] = v;
+        }
+        Ys[r][c] = v;
     }
     if (Sp == nullptr) return;
     __syncthreads();
@@ -500,106 +548,6 @@ __global__ void k_apply_rinv(int n, int p, const double* __restrict__ Y,
     if (Q2) {
         const dev::F2 q = dev::df_from(s);
         Q2[((size_t)ax * n + i) * p + c] = make_float2(q.h, q.l);
-    }
-}
-
-// Symmetric eigen-decomposition of H (p x p, p even, <= 48) by parallel cyclic
-// Jacobi with round-robin pairing; eigenvalues sorted in descending order.
-__global__ void __launch_bounds__(256) k_jacobi(int p, const double* __restrict__ H,
-                                                 double* __restrict__ lam,
-                                                 double* __restrict__ W) {
-    __shared__ double A[48][49];
-    __shared__ double V[48][49];
-    __shared__ double cs[24], sn[24];
-    __shared__ int pi[24], pj[24];
-    __shared__ int order[48];
-    __shared__ double off_sh;
-    int ax = blockIdx.x;
-    const double* Ha = H + (size_t)ax * p * p;
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-        int i = e / p, j = e % p;
-        A[i][j] = 0.5 * (Ha[i * p + j] + Ha[j * p + i]);
-        V[i][j] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    const int half = p / 2;
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        if (threadIdx.x == 0) {
-            double off = 0.0, tot = 0.0;
-            for (int i = 0; i < p; ++i)
-                for (int j = 0; j < p; ++j) {
-                    double v = A[i][j] * A[i][j];
-                    tot += v;
-                    if (i != j) off += v;
-                }
-            off_sh = (off <= 1e-32 * tot) ? -1.0 : off;
-        }
-        __syncthreads();
-        if (off_sh < 0.0) break;
-        for (int round = 0; round < p - 1; ++round) {
-            if (threadIdx.x < half) {
-                // round-robin: position 0 fixed, others rotate
-                int t = threadIdx.x;
-                int a = (t == 0) ? 0 : ((t - 1 + round) % (p - 1)) + 1;
-                int bpos = p - 1 - t;
-                int b = ((bpos - 1 + round) % (p - 1)) + 1;
-                int i = min(a, b), j = max(a, b);
-                double aij = A[i][j];
-                double c = 1.0, s = 0.0;
-                if (aij != 0.0) {
-                    double tau = (A[j][j] - A[i][i]) / (2.0 * aij);
-                    double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + tt * tt);
-                    s = tt * c;
-                }
-                cs[t] = c;
-                sn[t] = s;
-                pi[t] = i;
-                pj[t] = j;
-            }
-            __syncthreads();
-            // rows: A <- G^T A
-            for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
-                int t = e / p, k = e % p;
-                int i = pi[t], j = pj[t];
-                double c = cs[t], s = sn[t];
-                double ai = A[i][k], aj = A[j][k];
-                A[i][k] = c * ai - s * aj;
-                A[j][k] = s * ai + c * aj;
-            }
-            __syncthreads();
-            // columns: A <- A G, V <- V G
-            for (int e = threadIdx.x; e < half * p; e += blockDim.x) {
-                int t = e / p, k = e % p;
-                int i = pi[t], j = pj[t];
-                double c = cs[t], s = sn[t];
-                double ai = A[k][i], aj = A[k][j];
-                A[k][i] = c * ai - s * aj;
-                A[k][j] = s * ai + c * aj;
-                double vi = V[k][i], vj = V[k][j];
-                V[k][i] = c * vi - s * vj;
-                V[k][j] = s * vi + c * vj;
-            }
-            __syncthreads();
-        }
-    }
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < p; ++i) order[i] = i;
-        for (int i = 1; i < p; ++i) {  // stable insertion sort, descending
-            int v = order[i];
-            int j = i - 1;
-            while (j >= 0 && A[order[j]][order[j]] < A[v][v]) {
-                order[j + 1] = order[j];
-                --j;
-            }
-            order[j + 1] = v;
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < p; e += blockDim.x) lam[(size_t)ax * p + e] = A[order[e]][order[e]];
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-        int i = e / p, c = e % p;
-        W[((size_t)ax * p + i) * p + c] = V[i][order[c]];
     }
 }
 
@@ -948,18 +896,33 @@ __global__ void __launch_bounds__(1024) k_core(int Rtot, int Rl, int CH,
     for (int c = 0; c < RP; ++c) out[c] = dev::df_to(acc[c]);
 }
 
-// Table of the short-range radial function f(s) = sum_short a_k exp(-t_k^2 s) and of
-// hs * f'(s) at s = j*hs (FP64), for cubic Hermite interpolation in the pose kernels.
-__global__ void k_short_table(ProteinView v, int M, double hs, double2* __restrict__ out) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= M) return;
-    double sv = j * hs, f = 0.0, fp = 0.0;
+// Piecewise-cubic table of the short-range radial function f(s) = sum_short a_k
+// exp(-t_k^2 s): on [j hs, (j+1) hs] the Hermite cubic of f and hs f' at both ends,
+// in u = s/hs - j, as Horner coefficients (FP64, stored as float pairs):
+//   c0 = f_j, c1 = hs f'_j, c2 = 3(f_{j+1} - f_j) - 2 hs f'_j - hs f'_{j+1},
+//   c3 = 2(f_j - f_{j+1}) + hs f'_j + hs f'_{j+1}.
+__device__ __forceinline__ void short_f(const ProteinView& v, double sv, double hs, double& f, double& fp) {
+    f = 0.0;
+    fp = 0.0;
     for (int q = 0; q < v.Ks; ++q) {
         double e = v.as[q] * exp(-v.ts2[q] * sv);
         f += e;
         fp -= v.ts2[q] * e;
     }
-    out[j] = make_double2(f, hs * fp);
+    fp *= hs;
+}
+
+__global__ void k_short_table(ProteinView v, int M, double hs, float4* __restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M - 1) return;
+    double fa, da, fb, db;
+    short_f(v, j * hs, hs, fa, da);
+    short_f(v, (j + 1) * hs, hs, fb, db);
+    const dev::F2 c0 = dev::df_from(fa), c1 = dev::df_from(da);
+    const dev::F2 c2 = dev::df_from(3.0 * (fb - fa) - 2.0 * da - db);
+    const dev::F2 c3 = dev::df_from(2.0 * (fa - fb) + da + db);
+    out[2 * (size_t)j] = make_float4(c0.h, c0.l, c1.h, c1.l);
+    out[2 * (size_t)j + 1] = make_float4(c2.h, c2.l, c3.h, c3.l);
 }
 
 __global__ void k_to_float(size_t len, const double* __restrict__ in, float* __restrict__ out) {
@@ -1041,10 +1004,11 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
     RS_TRY(S.get(&d_cursor, ncell));
     RS_TRY(S.get(&d_perm, N));
     RS_TRY(device_alloc(P, (void**)&d_start, (ncell + 1) * sizeof(int)));
-    float4* d_atoms;
-    D4* d_atoms64;
+    float4 *d_atoms, *d_atoms_lo;
+    double4* d_atoms64;
     RS_TRY(device_alloc(P, (void**)&d_atoms, (size_t)N * sizeof(float4)));
-    RS_TRY(device_alloc(P, (void**)&d_atoms64, (size_t)N * sizeof(D4)));
+    RS_TRY(device_alloc(P, (void**)&d_atoms_lo, (size_t)N * sizeof(float4)));
+    RS_TRY(device_alloc(P, (void**)&d_atoms64, (size_t)N * sizeof(double4)));
     RS_TRY_CUDA(cudaMemsetAsync(d_count, 0, ncell * sizeof(int), st));
     RS_TRY_CUDA(cudaMemsetAsync(d_cursor, 0, ncell * sizeof(int), st));
     {
@@ -1063,11 +1027,12 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
     {
         ::rs::KernelTimer kt__("k_cell_sort", st, 0.0, false);
         k_cell_sort<<<blocks_for(ncell), kBlock, 0, st>>>((int)ncell, d_start, d_perm, d_xyz, d_q,
-                                                          d_atoms, d_atoms64);
+                                                          d_atoms, d_atoms_lo, d_atoms64);
     }
     RS_TRY_CUDA(cudaGetLastError());
     ProteinView& v = P->view;
     v.atoms = d_atoms;
+    v.atoms_lo = d_atoms_lo;
     v.atoms64 = d_atoms64;
     v.cell_start = d_start;
     v.nc0 = nc[0];
@@ -1192,13 +1157,12 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         set_error("grid too small for tucker_cap %d (n=%d)", cap, n);
         return RS_ERR_UNSUPPORTED;
     }
-    double *d_Q, *d_Y, *d_Sm, *d_Ri, *d_lam, *d_W;
+    double *d_Q, *d_Y, *d_Sm, *d_Ri, *d_W;
     int* d_fail;
     RS_TRY(S.get(&d_Q, (size_t)3 * n * p));
     RS_TRY(S.get(&d_Y, (size_t)3 * n * p));
     RS_TRY(S.get(&d_Sm, (size_t)3 * p * p));
     RS_TRY(S.get(&d_Ri, (size_t)3 * p * p));
-    RS_TRY(S.get(&d_lam, (size_t)3 * p));
     RS_TRY(S.get(&d_W, (size_t)3 * p * p));
     float2* d_Q2;  // Q as float pairs, the operand of the pair GEMM
     RS_TRY(S.get(&d_Q2, (size_t)3 * n * p));
@@ -1237,16 +1201,21 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         return RS_OK;
     };
     RS_TRY(orthonormalize(d_Q));
-    dim3 gq((n + 15) / 16, 1, 3);
+    dim3 gq((n + 31) / 32, kGemmKS, 3);
     const int nblk = (n + 15) / 16;
-    double* d_Sp;
+    double *d_Sp, *d_Yp;
     RS_TRY(S.get(&d_Sp, (size_t)3 * nblk * p * p));
+    RS_TRY(S.get(&d_Yp, (size_t)kGemmKS * 3 * n * p));
     work = 3.0 * 13.0 * n * (double)n * p;  // FP32 pipe ops per G Q (one Dot2 step per product)
     // one subspace step: Y = G Q with partial Grams, S = Y^T Y, shifted Cholesky, Q = Y R^-1
     auto step = [&]() -> rs_status {
         {
             ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
-            k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q2, d_Y, d_Sp);
+            k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q2, d_Yp);
+        }
+        {
+            ::rs::KernelTimer kt__("k_gemm_reduce", st, 0.0, false);
+            k_gemm_reduce<<<dim3(nblk, 3), 256, 0, st>>>(n, p, d_Yp, d_Y, d_Sp);
         }
         {
             ::rs::KernelTimer kt__("k_sum_gram", st, 0.0, false);
@@ -1267,21 +1236,30 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         RS_TRY(orthonormalize(d_Q));
         {
             ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
-            k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q2, d_Y, nullptr);
+            k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q2, d_Yp);
+        }
+        {
+            ::rs::KernelTimer kt__("k_gemm_reduce", st, 0.0, false);
+            k_gemm_reduce<<<dim3(nblk, 3), 256, 0, st>>>(n, p, d_Yp, d_Y, nullptr);
         }
         {
             ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
             k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Y, d_Sm);
         }
-        {
-            ::rs::KernelTimer kt__("k_jacobi", st, 0.0, false);
-            k_jacobi<<<3, 256, 0, st>>>(p, d_Sm, d_lam, d_W);
-        }
         RS_TRY_CUDA(cudaGetLastError());
-        lam_out.resize((size_t)3 * p);
-        RS_TRY_CUDA(cudaMemcpyAsync(lam_out.data(), d_lam, lam_out.size() * sizeof(double),
-                                    cudaMemcpyDeviceToHost, st));
+        // p x p eigenproblems on the host (FP64): a few microseconds each
+        std::vector<double> H((size_t)3 * p * p), Wh((size_t)3 * p * p);
+        RS_TRY_CUDA(cudaMemcpyAsync(H.data(), d_Sm, H.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         RS_TRY_CUDA(cudaStreamSynchronize(st));
+        lam_out.resize((size_t)3 * p);
+        for (int a = 0; a < 3; ++a)
+            if (!symeig_host(p, H.data() + (size_t)a * p * p, lam_out.data() + (size_t)a * p,
+                             Wh.data() + (size_t)a * p * p)) {
+                set_error("Rayleigh-Ritz eigen-decomposition did not converge");
+                return RS_ERR_CUDA;
+            }
+        RS_TRY_CUDA(cudaMemcpyAsync(d_W, Wh.data(), Wh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaStreamSynchronize(st));  // Wh is released on return
         return RS_OK;
     };
     // Subspace iteration converges like (lambda_{p+1} / lambda_r)^T.  After a few
@@ -1533,7 +1511,7 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
     double rc = P->table.r_c;
     v.rc2 = rc * rc;
     v.rc2_hi = (float)(rc * rc * (1.0 + 1e-4));
-    v.stab = nullptr;
+    v.stab2 = nullptr;
     v.stab_n = 0;
     v.stab_inv_h = 0.0;
     if (v.Ks > 0 && rc > 0) {
@@ -1551,8 +1529,9 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
             set_error("rs_build_protein: short-range table of %d entries is too large", M);
             return fail_out(RS_ERR_UNSUPPORTED);
         }
-        double2* tab = nullptr;
-        if ((s = device_alloc(P, (void**)&tab, (size_t)M * sizeof(double2))) != RS_OK) return fail_out(s);
+        float4* tab = nullptr;
+        if ((s = device_alloc(P, (void**)&tab, (size_t)2 * (M - 1) * sizeof(float4))) != RS_OK)
+            return fail_out(s);
         {
             ::rs::KernelTimer kt__("k_short_table", st, 0.0, false);
             k_short_table<<<blocks_for((size_t)M), kBlock, 0, st>>>(v, M, hs, tab);
@@ -1561,13 +1540,18 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
             set_error("rs_build_protein: short-range table launch failed");
             return fail_out(RS_ERR_CUDA);
         }
-        v.stab = tab;
+        v.stab2 = tab;
         v.stab_n = M;
         v.stab_inv_h = 1.0 / hs;
+        split_host(v.stab_inv_h, v.stab_ih_h, v.stab_ih_l);
     }
     v.sig2 = P->sigma * P->sigma;
     v.sig2_lo = (float)(v.sig2 * (1.0 - 1e-4));
     v.sig2_hi = (float)(v.sig2 * (1.0 + 1e-4));
+    split_host(v.sig2, v.sig2_ph, v.sig2_pl);
+    split_host(v.rc2, v.rc2_ph, v.rc2_pl);
+    split_host(v.b, v.b_h, v.b_l);
+    split_host(v.inv_h, v.inv_h_h, v.inv_h_l);
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("rs_build_protein: %s", cudaGetErrorString(cudaGetLastError()));
         return fail_out(RS_ERR_CUDA);

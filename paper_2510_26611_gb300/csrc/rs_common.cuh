@@ -51,11 +51,6 @@ double sinc_quad_error(const SincTable& T);
 rs_status make_sinc_table(double b, double sigma, int R_l, double r_min, double tau,
                           double short_tol, SincTable* out);
 
-// FP64 atom record (x, y, z, q), 32-byte aligned.
-struct __align__(32) D4 {
-    double x, y, z, w;
-};
-
 // Everything a pose kernel needs about one protein, passed by value.
 struct ProteinView {
     int n;
@@ -73,17 +68,25 @@ struct ProteinView {
     int Ks;              // short-range terms: t_k^2 and a_k (FP64)
     double ts2[RS_MAX_SHORT];
     double as[RS_MAX_SHORT];
-    // short-range radial function f(s) = sum_short a_k exp(-t_k^2 s), s = d^2, as a
-    // cubic Hermite table: stab[j] = (f(j hs), hs f'(j hs)), j = 0..stab_n-1
-    const double2* stab;
+    // short-range radial function f(s) = sum_short a_k exp(-t_k^2 s), s = d^2, as
+    // piecewise cubics on s in [j hs, (j+1) hs], j = 0..stab_n-2: the Hermite cubic
+    // of f and hs f' at both ends in the local variable u = s/hs - j, stored as
+    // Horner coefficients c0..c3 in float pairs, two float4 per interval:
+    // stab2[2j] = (c0.h, c0.l, c1.h, c1.l), stab2[2j+1] = (c2.h, c2.l, c3.h, c3.l)
+    const float4* stab2;
     int stab_n;
     double stab_inv_h;
+    float stab_ih_h, stab_ih_l;  // 1/hs as a float pair
     double rc2;          // r_c^2
     float rc2_hi;        // r_c^2 (1 + 1e-4): FP32 pre-filter
+    float rc2_ph, rc2_pl;    // r_c^2 as a float pair
     double sig2;         // sigma^2
     float sig2_lo, sig2_hi;  // sigma^2 (1 -/+ 1e-4): FP32 decision band
-    const float4* atoms;     // cell-sorted protein atoms (x, y, z, q) FP32
-    const D4* atoms64;       // same, FP64
+    float sig2_ph, sig2_pl;  // sigma^2 as a float pair
+    float b_h, b_l, inv_h_h, inv_h_l;  // b and 1/h as float pairs
+    const float4* atoms;     // cell-sorted protein atoms (x, y, z, q), FP32 nearest
+    const float4* atoms_lo;  // remainders: atoms + atoms_lo = the record to ~2^-48
+    const double4* atoms64;  // the FP64 record (vdW decisions inside the sigma band)
     const int* cell_start;   // [ncell + 1]
     int nc0, nc1, nc2;
     float co0, co1, co2;     // cell-grid origin
@@ -94,8 +97,21 @@ struct ProteinView {
 struct LigandView {
     int L;
     const float4* y;     // (y_x, y_y, y_z, q) FP32
-    const double* y64;   // [L][3] FP64
+    const float2* yd;    // [L][3] coordinates as float pairs (hi, lo)
+    const double* y64;   // [L][3] FP64 (vdW decisions inside the sigma band)
     const double* q64;   // [L]
+};
+
+// One protein-ligand pair of a batched launch: views, pose inputs (quaternions) and
+// outputs, all device memory.
+struct PairDesc {
+    ProteinView prot;
+    LigandView lig;
+    const double* rot;
+    const double* trans;
+    long long P;
+    double* E;
+    uint8_t* flags;
 };
 
 }  // namespace rs
@@ -204,6 +220,25 @@ __device__ __forceinline__ void df_acc(F2& acc, F2 x) {
     acc.l = __fadd_rn(acc.l, __fadd_rn(e, x.l));
 }
 
+// Renormalised pair (hi = the float nearest hi + lo) of an accumulator.
+__device__ __forceinline__ F2 df_norm(F2 a) {
+    float s, e;
+    two_sum(a.h, a.l, s, e);
+    return {s, e};
+}
+
+// a + b and a - b for pairs (results renormalised).
+__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    return fast_two_sum(s, e);
+}
+__device__ __forceinline__ F2 df_sub(F2 a, F2 b) { return df_add(a, F2{-b.h, -b.l}); }
+
+// a < b for renormalised pairs.
+__device__ __forceinline__ bool df_lt(F2 a, F2 b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+
 // Pair nearest a double (hi = the float nearest v, lo = the float nearest v - hi),
 // and back.  Values must stay inside the float range.
 __device__ __forceinline__ F2 df_from(double v) {
@@ -271,18 +306,19 @@ __device__ __forceinline__ void left_jacobian(double wx, double wy, double wz, d
     J[6] = -B * wy + C * wx * wz; J[7] = B * wx + C * wy * wz; J[8] = 1 + C * (wz * wz - th2);
 }
 
-// Cell index and fraction along one axis from the FP64 coordinate x:
-// s = (x + b)/h; i = clamp(floor(s), 0, n-2), f = clamp(s - i, 0, 1).
-__device__ __forceinline__ void axis_cell(double x, double b, double inv_h, int n, int& i, float& f,
-                                          bool& inside) {
-    double s = (x + b) * inv_h;
-    inside = (s >= 0.0) && (s <= (double)(n - 1));
-    double fl = floor(s);
-    fl = fmin(fmax(fl, 0.0), (double)(n - 2));
+// Cell index and fraction along one axis from a coordinate x given as a float pair:
+// s = (x + b)/h (pair arithmetic); i = clamp(floor(s), 0, n-2), f = clamp(s - i, 0, 1);
+// inside = 0 <= s <= n-1, decided on the pair.
+__device__ __forceinline__ void axis_cell(F2 x, F2 b, F2 inv_h, int n, int& i, float& f, bool& inside) {
+    const F2 s = df_mul(df_add(x, b), inv_h);
+    const float top = (float)(n - 1);
+    inside = (s.h > 0.f || (s.h == 0.f && s.l >= 0.f)) && (s.h < top || (s.h == top && s.l <= 0.f));
+    float fl = floorf(s.h);
+    if (fl == s.h && s.l < 0.f) fl = __fsub_rn(fl, 1.f);
+    fl = fminf(fmaxf(fl, 0.f), (float)(n - 2));
     i = (int)fl;
-    double fr = s - fl;
-    fr = fmin(fmax(fr, 0.0), 1.0);
-    f = (float)fr;
+    const float fr = __fadd_rn(__fsub_rn(s.h, fl), s.l);
+    f = fminf(fmaxf(fr, 0.f), 1.f);
 }
 
 }  // namespace dev

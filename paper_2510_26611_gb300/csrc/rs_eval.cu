@@ -57,9 +57,9 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
     const long long nblocks = (Ptot + PB - 1) / PB;
     const int ld4 = P.ld / 4;
-    const float4* F0 = (const float4*)P.F[0];
-    const float4* F1 = (const float4*)P.F[1];
-    const float4* F2 = (const float4*)P.F[2];
+    const float4* Fa0 = (const float4*)P.F[0];
+    const float4* Fa1 = (const float4*)P.F[1];
+    const float4* Fa2 = (const float4*)P.F[2];
     for (long long pb = blockIdx.x; pb < nblocks; pb += gridDim.x) {
         long long p0 = pb * PB;
         __syncthreads();
@@ -78,19 +78,16 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
                 if (lane < NC) cj[lane] = 0.0;
                 continue;
             }
-            float4 yq = lig.y[j];
             float ry[3];
-            for (int r = 0; r < 3; ++r)
-                ry[r] = q.Rf[3 * r] * yq.x + q.Rf[3 * r + 1] * yq.y + q.Rf[3 * r + 2] * yq.z;
             int ci[3];
             float cf[3];
             bool ins[3];
+            F2 x[3];
             double x64[3];
-            atom_position(q, lig.y64 + 3 * j, x64);
-            for (int a = 0; a < 3; ++a) dev::axis_cell(x64[a], P.b, P.inv_h, P.n, ci[a], cf[a], ins[a]);
-            const float4* a0 = F0 + (size_t)ci[0] * ld4;
-            const float4* a1 = F1 + (size_t)ci[1] * ld4;
-            const float4* a2 = F2 + (size_t)ci[2] * ld4;
+            atom_geometry(P, lig, q, j, ry, x, x64, ci, cf, ins);
+            const float4* a0 = Fa0 + (size_t)ci[0] * ld4;
+            const float4* a1 = Fa1 + (size_t)ci[1] * ld4;
+            const float4* a2 = Fa2 + (size_t)ci[2] * ld4;
             FAcc acc, acc1, acc2, acc3;
             for (int r4 = lane; r4 < ld4; r4 += 32) {
                 float4 x0 = __ldg(a0 + r4), x0n = __ldg(a0 + ld4 + r4);
@@ -129,14 +126,12 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
                 gl[2] = ins[2] ? warp_sum(acc3.value()) * P.inv_h : 0.0;
             }
             // short range split over lanes
-            float xf[3];
-            for (int a = 0; a < 3; ++a) xf[a] = (float)x64[a];
-            double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
+            F2 phs{0.f, 0.f}, gs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             int clash = 0;
-            short_vdw<GRAD>(P, xf, x64, lane, 32, phs, gs, clash);
-            phi += warp_sum(phs);
+            short_vdw<GRAD>(P, x, x64, lane, 32, phs, gs, clash);
+            phi += warp_sum(dev::df_to(phs));
             if constexpr (GRAD)
-                for (int a = 0; a < 3; ++a) gl[a] += warp_sum(gs[a]);
+                for (int a = 0; a < 3; ++a) gl[a] += warp_sum(dev::df_to(gs[a]));
             clash = __any_sync(0xffffffffu, clash);
             if (lane == 0) {
                 int fl = clash ? RS_FLAG_CLASH : 0;
@@ -163,7 +158,7 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
 
 // Ligand about its geometric centre (FP64 mean in a fixed order); one CTA.
 __global__ void k_prep_ligand(int L, const double* __restrict__ xyz, const double* __restrict__ q,
-                              float4* __restrict__ y, double* __restrict__ y64,
+                              float4* __restrict__ y, float2* __restrict__ yd, double* __restrict__ y64,
                               double* __restrict__ q64) {
     __shared__ double sm[3][256];
     double s[3] = {0, 0, 0};
@@ -180,6 +175,10 @@ __global__ void k_prep_ligand(int L, const double* __restrict__ xyz, const doubl
     for (int j = threadIdx.x; j < L; j += blockDim.x) {
         double a = xyz[3 * (size_t)j] - c0, b = xyz[3 * (size_t)j + 1] - c1,
                c = xyz[3 * (size_t)j + 2] - c2;
+        const dev::F2 pa = dev::df_from(a), pb = dev::df_from(b), pc = dev::df_from(c);
+        yd[3 * (size_t)j] = make_float2(pa.h, pa.l);
+        yd[3 * (size_t)j + 1] = make_float2(pb.h, pb.l);
+        yd[3 * (size_t)j + 2] = make_float2(pc.h, pc.l);
         y64[3 * (size_t)j] = a;
         y64[3 * (size_t)j + 1] = b;
         y64[3 * (size_t)j + 2] = c;
@@ -272,11 +271,11 @@ rs_status launch_canon(const EvalLaunch& a, cudaStream_t st) {
 
 }  // namespace
 
-rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, double* y64,
+rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, float2* yd, double* y64,
                              double* q64, cudaStream_t st, bool events) {
     {
         ::rs::KernelTimer kt__("k_prep_ligand", st, 0.0, false, events);
-        k_prep_ligand<<<1, 256, 0, st>>>(L, xyz, q, y, y64, q64);
+        k_prep_ligand<<<1, 256, 0, st>>>(L, xyz, q, y, yd, y64, q64);
     }
     RS_TRY_CUDA(cudaGetLastError());
     return RS_OK;
@@ -284,7 +283,14 @@ rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* 
 
 rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st) {
     if (a.P <= 0) return RS_OK;
-    if (a.prot.kind == 1 && a.ws && a.PB == 0 && a.grid == 0) return launch_sorted(a, grad, st);
+    // the cell-grouped path pays six launches and a sort per chunk and one slab load
+    // per (warp, cell): it is taken for batches of at least 2^17 pose-atoms that
+    // average at least 64 per axis-3 grid cell, without a skip mask (the masked
+    // trial passes of rs_pgd_run evaluate few poses; the per-block kernel skips them)
+    const long long atoms = a.P * a.lig.L;
+    if (a.prot.kind == 1 && a.ws && a.PB == 0 && a.grid == 0 && !a.skip && atoms >= (1LL << 17) &&
+        atoms >= 64LL * a.prot.n)
+        return launch_sorted(a, grad, st);
     if (a.prot.kind == 0) return grad ? launch_canon<true>(a, st) : launch_canon<false>(a, st);
     switch (a.prot.R) {
 #define RS_CASE(R) \
@@ -299,7 +305,7 @@ rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st) {
 
 // Layout of the per-call ligand scratch inside the context buffer.
 size_t ligand_scratch_bytes(int L) {
-    return ((size_t)L * sizeof(float4) + (size_t)L * 3 * 8 + (size_t)L * 8 + 256 * 3);
+    return ((size_t)L * sizeof(float4) + 2 * (size_t)L * 3 * 8 + (size_t)L * 8 + 256 * 4);
 }
 
 LigandView carve_ligand(void* base, int L) {
@@ -308,6 +314,8 @@ LigandView carve_ligand(void* base, int L) {
     v.L = L;
     v.y = (const float4*)p;
     p += ((size_t)L * sizeof(float4) + 255) / 256 * 256;
+    v.yd = (const float2*)p;
+    p += ((size_t)L * 24 + 255) / 256 * 256;
     v.y64 = (const double*)p;
     p += ((size_t)L * 24 + 255) / 256 * 256;
     v.q64 = (const double*)p;
@@ -372,7 +380,7 @@ rs_status run_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L, const double
         RS_TRY_CUDA(cudaMemcpyAsync((void*)d_rot, rot, (size_t)P * rdim * 8, cudaMemcpyHostToDevice, st));
         RS_TRY_CUDA(cudaMemcpyAsync((void*)d_trans, trans, (size_t)P * 24, cudaMemcpyHostToDevice, st));
     }
-    RS_TRY(launch_prep_ligand(L, d_xyz, d_q, (float4*)lig.y, (double*)lig.y64, (double*)lig.q64, st));
+    RS_TRY(launch_prep_ligand(L, d_xyz, d_q, (float4*)lig.y, (float2*)lig.yd, (double*)lig.y64, (double*)lig.q64, st));
     EvalLaunch a;
     a.prot = prot->view;
     a.lig = lig;

@@ -23,7 +23,7 @@ struct EvalLaunch {
     size_t ws_bytes = 0;            //   per block of poses, no scratch)
 };
 
-rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, double* y64,
+rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, float2* yd, double* y64,
                              double* q64, cudaStream_t st, bool events = true);
 rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st);
 size_t ligand_scratch_bytes(int L);

@@ -18,10 +18,10 @@ namespace {
 
 constexpr int kNoAllocMaxL = 4096;
 constexpr int kMaxDevices = 64;
-// Prepared-ligand layout (see carve_ligand): float4 y[L], double y64[L][3], double q64[L],
-// each part 256-byte aligned.
+// Prepared-ligand layout (see carve_ligand): float4 y[L], float2 yd[L][3] (coordinate
+// pairs), double y64[L][3], double q64[L], each part 256-byte aligned.
 constexpr size_t kNoAllocBytes = ((size_t)kNoAllocMaxL * 16 + 255) / 256 * 256 +
-                                 ((size_t)kNoAllocMaxL * 24 + 255) / 256 * 256 +
+                                 2 * (((size_t)kNoAllocMaxL * 24 + 255) / 256 * 256) +
                                  ((size_t)kNoAllocMaxL * 8 + 255) / 256 * 256;
 
 // One copy per GPU that loads the library; it lives until the process exits.
@@ -80,7 +80,7 @@ extern "C" rs_status rs_energy_poses_noalloc(const rs_protein* prot, int32_t L,
     RS_TRY(scratch_for(prot->device, &scratch));
     cudaStream_t st = (cudaStream_t)stream;
     LigandView lig = carve_ligand(scratch, L);
-    RS_TRY(launch_prep_ligand(L, lig_xyz, lig_q, (float4*)lig.y, (double*)lig.y64,
+    RS_TRY(launch_prep_ligand(L, lig_xyz, lig_q, (float4*)lig.y, (float2*)lig.yd, (double*)lig.y64,
                               (double*)lig.q64, st, false));
     EvalLaunch a;
     a.prot = prot->view;

@@ -140,7 +140,7 @@ extern "C" rs_status rs_pgd_run(rs_ctx* ctx, const rs_protein* prot, int32_t L, 
         set_error("rs_pgd_run: stream ordering failed");
         return RS_ERR_CUDA;
     }
-    rs_status s = launch_prep_ligand(L, lig_xyz, lig_q, (float4*)lig.y, (double*)lig.y64, (double*)lig.q64, st);
+    rs_status s = launch_prep_ligand(L, lig_xyz, lig_q, (float4*)lig.y, (float2*)lig.yd, (double*)lig.y64, (double*)lig.q64, st);
     if (s != RS_OK) {
         cleanup();
         return s;

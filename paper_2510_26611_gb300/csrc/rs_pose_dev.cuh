@@ -10,12 +10,15 @@ namespace {
 
 using dev::FAcc;
 
+using dev::F2;
+
 struct PoseSetup {
     double R[9];
     double t[3];
-    double s[3];      // (t + b) / h
     double J[9];      // left Jacobian (gradient kernels)
-    float Rf[9];
+    F2 Rd[9];         // R and t as float pairs (atom positions)
+    F2 td[3];
+    float Rf[9];      // R in FP32 (torque arm)
     int valid;
 };
 
@@ -29,10 +32,13 @@ __device__ __forceinline__ void setup_pose(const ProteinView& P, const double* _
     } else {
         dev::quat_to_rot(rot[4 * p], rot[4 * p + 1], rot[4 * p + 2], rot[4 * p + 3], ps.R);
     }
-    for (int a = 0; a < 9; ++a) ps.Rf[a] = (float)ps.R[a];
+    for (int a = 0; a < 9; ++a) {
+        ps.Rf[a] = (float)ps.R[a];
+        ps.Rd[a] = dev::df_from(ps.R[a]);
+    }
     for (int a = 0; a < 3; ++a) {
         ps.t[a] = trans[3 * p + a];
-        ps.s[a] = (ps.t[a] + P.b) * P.inv_h;
+        ps.td[a] = dev::df_from(ps.t[a]);
     }
     ps.valid = 1;
 }
@@ -72,66 +78,82 @@ __device__ __forceinline__ int short_screen(const ProteinView& P, const float xf
     return (d2 < P.sig2_hi ? 1 : 0) | (d2 < P.rc2_hi ? 2 : 0) | (d2 < P.sig2_lo ? 4 : 0);
 }
 
-// FP64 decision and term of a screened pair: f = x - x_m, d2d = |f|^2; sets clash
-// bit 1 and, when inside the cutoff, bit 2 with the radial function value fv and
-// (gradients) fgr = 2 w f'(d2d), so the pair adds w fv to phi and fgr f to grad phi.
+// Decision and term of a screened pair in float-pair arithmetic (about 2^-47
+// relative): f = x - x_m, d2 = |f|^2; bit 1 = clash, bit 2 = inside the cutoff with
+// w = z_m, the radial function value fv = f(d2) and (gradients) fgr = 2 w f'(d2),
+// so the pair adds w fv to phi and fgr f to grad phi.
 template <bool GRAD>
-__device__ __forceinline__ int short_pair(const ProteinView& P, const double x64[3], D4 a64, int bits,
-                                          double f[3], double& fv, double& fgr) {
-    f[0] = __dsub_rn(x64[0], a64.x);
-    f[1] = __dsub_rn(x64[1], a64.y);
-    f[2] = __dsub_rn(x64[2], a64.z);
-    const double d2d = fma(f[2], f[2], fma(f[1], f[1], __dmul_rn(f[0], f[0])));
-    int out = ((bits & 1) && ((bits & 4) || d2d < P.sig2)) ? 1 : 0;
-    if ((bits & 2) && d2d < P.rc2) {
+__device__ __forceinline__ int short_pair(const ProteinView& P, const F2 x[3], const double x64[3], int k,
+                                          int bits, F2 f[3], F2& w, F2& fv, F2& fgr) {
+    const float4 ah = P.atoms[k], al = P.atoms_lo[k];
+    f[0] = dev::df_sub(x[0], F2{ah.x, al.x});
+    f[1] = dev::df_sub(x[1], F2{ah.y, al.y});
+    f[2] = dev::df_sub(x[2], F2{ah.z, al.z});
+    F2 d2{0.f, 0.f};
+    dev::df_fma_acc(d2, f[0], f[0]);
+    dev::df_fma_acc(d2, f[1], f[1]);
+    dev::df_fma_acc(d2, f[2], f[2]);
+    d2 = dev::df_norm(d2);
+    w = F2{ah.w, al.w};
+    int out = 0;
+    if (bits & 1) {
+        if (bits & 4) {
+            out = 1;
+        } else {
+            // inside the +-1e-4 sigma^2 band: the decision is taken in FP64 from the
+            // FP64 position and atom record (C-11)
+            const double4 a64 = P.atoms64[k];
+            const double e0 = __dsub_rn(x64[0], a64.x), e1 = __dsub_rn(x64[1], a64.y),
+                         e2 = __dsub_rn(x64[2], a64.z);
+            const double d2d = fma(e2, e2, fma(e1, e1, __dmul_rn(e0, e0)));
+            out = d2d < P.sig2 ? 1 : 0;
+        }
+    }
+    if ((bits & 2) && dev::df_lt(d2, F2{P.rc2_ph, P.rc2_pl})) {
         out |= 2;
-        // cubic Hermite interpolation of the tabulated radial function (FP64)
-        double xs = __dmul_rn(d2d, P.stab_inv_h);
-        int j = min((int)xs, P.stab_n - 2);
-        double u = __dsub_rn(xs, (double)j);
-        double2 A = P.stab[j], B = P.stab[j + 1];
-        double u2 = __dmul_rn(u, u), u3 = __dmul_rn(u2, u);
-        // Hermite basis h00 = 2u^3 - 3u^2 + 1, h10 = u^3 - 2u^2 + u,
-        // h01 = 3u^2 - 2u^3, h11 = u^3 - u^2
-        double h00 = fma(2.0, u3, fma(-3.0, u2, 1.0));
-        double h10 = fma(-2.0, u2, __dadd_rn(u3, u));
-        double h01 = fma(-2.0, u3, __dmul_rn(3.0, u2));
-        double h11 = __dsub_rn(u3, u2);
-        fv = fma(h11, B.y, fma(h01, B.x, fma(h10, A.y, __dmul_rn(h00, A.x))));
+        // local variable of the interval: u = d2/hs - j in [0, 1]
+        const F2 xs = dev::df_mul(d2, F2{P.stab_ih_h, P.stab_ih_l});
+        float jf = floorf(xs.h);
+        if (jf == xs.h && xs.l < 0.f) jf = __fsub_rn(jf, 1.f);
+        const int j = max(0, min((int)jf, P.stab_n - 2));
+        const F2 u = dev::df_norm(F2{__fsub_rn(xs.h, (float)j), xs.l});
+        const float4 c01 = P.stab2[2 * j], c23 = P.stab2[2 * j + 1];
+        const F2 c0{c01.x, c01.y}, c1{c01.z, c01.w}, c2{c23.x, c23.y}, c3{c23.z, c23.w};
+        // Horner: fv = ((c3 u + c2) u + c1) u + c0
+        F2 v = dev::df_add(dev::df_mul(c3, u), c2);
+        v = dev::df_add(dev::df_mul(v, u), c1);
+        fv = dev::df_add(dev::df_mul(v, u), c0);
         if constexpr (GRAD) {
-            // d/du of the basis: 6u^2 - 6u, 3u^2 - 4u + 1, -(6u^2 - 6u), 3u^2 - 2u
-            double d00 = fma(6.0, u2, __dmul_rn(-6.0, u));
-            double d10 = fma(3.0, u2, fma(-4.0, u, 1.0));
-            double d11 = fma(3.0, u2, __dmul_rn(-2.0, u));
-            double dp = fma(d11, B.y, fma(d10, A.y, __dmul_rn(d00, __dsub_rn(A.x, B.x))));
-            // grad_x f(|x - x_m|^2) = 2 f'(s) (x - x_m)
-            fgr = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a64.w), dp), P.stab_inv_h);
+            // dp/du = (3 c3 u + 2 c2) u + c1 = hs f'(d2); grad_x f(|x - x_m|^2) = 2 f' (x - x_m)
+            F2 dv = dev::df_add(dev::df_mul(dev::df_mul(c3, F2{3.f, 0.f}), u), dev::df_mul(c2, F2{2.f, 0.f}));
+            dv = dev::df_add(dev::df_mul(dv, u), c1);
+            fgr = dev::df_mul(dev::df_mul(w, dv), F2{2.f * P.stab_ih_h, 2.f * P.stab_ih_l});
         }
     }
     return out;
 }
 
-// Accumulation of one pair's term into an atom's sums, in candidate order.
+// Accumulation of one pair's term into an atom's sums (Dot2), in candidate order.
 template <bool GRAD>
-__device__ __forceinline__ void short_accumulate(double w, double fv, double fgr, const double f[3], double& phi,
-                                                 double g[3]) {
-    phi = fma(w, fv, phi);
+__device__ __forceinline__ void short_accumulate(F2 w, F2 fv, F2 fgr, const F2 f[3], F2& phi, F2 g[3]) {
+    dev::df_fma_acc(phi, w, fv);
     if constexpr (GRAD) {
-        g[0] = fma(fgr, f[0], g[0]);
-        g[1] = fma(fgr, f[1], g[1]);
-        g[2] = fma(fgr, f[2], g[2]);
+        dev::df_fma_acc(g[0], fgr, f[0]);
+        dev::df_fma_acc(g[1], fgr, f[1]);
+        dev::df_fma_acc(g[2], fgr, f[2]);
     }
 }
 
 // Short-range part and vdW decision for one atom; candidates split over
 // `nl` cooperating lanes starting at `lane`.  Distances are screened in FP32;
 // pairs inside the cutoff, and vdW decisions within 1e-4 relative of sigma^2,
-// are taken in FP64 from x = t + R y evaluated in FP64.  phi and g are added to
+// are taken in pair arithmetic from the pair position x.  phi and g are added to
 // (callers pass zeros) in candidate order; with nl = 1 the sums equal those of
 // short_coop for the same atom bit for bit.
 template <bool GRAD>
-__device__ __noinline__ void short_vdw(const ProteinView& P, const float xf[3], const double x64[3],
-                                       int lane, int nl, double& phi, double g[3], int& clash) {
+__device__ __noinline__ void short_vdw(const ProteinView& P, const F2 x[3], const double x64[3], int lane,
+                                       int nl, F2& phi, F2 g[3], int& clash) {
+    const float xf[3] = {x[0].h, x[1].h, x[2].h};
     int c0, c1, c2;
     short_cell(P, xf, c0, c1, c2);
     for (int row = 0; row < 9; ++row) {
@@ -140,10 +162,10 @@ __device__ __noinline__ void short_vdw(const ProteinView& P, const float xf[3], 
         for (int k = s + lane; k < e; k += nl) {
             const int bits = short_screen(P, xf, P.atoms[k]);
             if (!(bits & 3)) continue;
-            double f[3], fv = 0.0, fgr = 0.0;
-            const int out = short_pair<GRAD>(P, x64, P.atoms64[k], bits, f, fv, fgr);
+            F2 f[3], w, fv{0.f, 0.f}, fgr{0.f, 0.f};
+            const int out = short_pair<GRAD>(P, x, x64, k, bits, f, w, fv, fgr);
             if (out & 1) clash = 1;
-            if (out & 2) short_accumulate<GRAD>(P.atoms64[k].w, fv, fgr, f, phi, g);
+            if (out & 2) short_accumulate<GRAD>(w, fv, fgr, f, phi, g);
         }
     }
 }
@@ -154,29 +176,33 @@ struct NearQueue {
     int owner[64];   // lane whose atom the pair belongs to
     int k[64];       // protein atom (cell-sorted index)
     int bits[64];    // screen bits, then the pair's outcome bits
-    double w[32], fv[32], fgr[GRAD ? 32 : 1];
-    double f[GRAD ? 3 : 1][32];
-    double x[3][32]; // FP64 positions of the warp's atoms
+    float2 w[32], fv[32], fgr[GRAD ? 32 : 1];
+    float2 f[GRAD ? 3 : 1][32];
+    float2 x[3][32]; // pair positions of the warp's atoms
+    double x64[3][32];  // FP64 positions (decisions inside the sigma band)
     int rs[9][32], re[9][32];
 };
 
 // Short range and vdW decision for the 32 atoms of a warp (one per lane), with the
-// FP32 screen run by all lanes in step and the FP64 work of near pairs packed one
-// pair per lane: a warp whose atoms see different numbers of near pairs keeps
-// every lane busy.  Every lane of the warp must call it; lanes with active = false
-// contribute no atom.  Each atom's sums are accumulated in its own candidate order,
-// so they equal short_vdw's (nl = 1) bit for bit.
-template <bool GRAD>
-__device__ void short_coop(const ProteinView& P, bool active, const double x64[3], NearQueue<GRAD>& Q,
-                           double& phi, double g[3], int& clash) {
+// FP32 screen run by all lanes in step and the pair-arithmetic work of near pairs
+// packed one pair per lane: a warp whose atoms see different numbers of near pairs
+// keeps every lane busy.  Every lane of the warp must call it; lanes with
+// active = false contribute no atom.  prot_of(l) is the protein of lane l's atom
+// (lanes may belong to different proteins).  Each atom's sums are accumulated in
+// its own candidate order, so they equal short_vdw's (nl = 1) bit for bit.
+template <bool GRAD, class ProtOf>
+__device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], const double x64[3],
+                                NearQueue<GRAD>& Q, F2& phi, F2 g[3], int& clash) {
     const int lane = threadIdx.x & 31;
+    const ProteinView& P = prot_of(lane);
     const unsigned full = 0xffffffffu;
-    float xf[3];
+    float xf[3] = {0.f, 0.f, 0.f};
     int total = 0;
     if (active) {
         for (int a = 0; a < 3; ++a) {
-            xf[a] = (float)x64[a];
-            Q.x[a][lane] = x64[a];
+            xf[a] = x[a].h;
+            Q.x[a][lane] = make_float2(x[a].h, x[a].l);
+            Q.x64[a][lane] = x64[a];
         }
         int c0, c1, c2;
         short_cell(P, xf, c0, c1, c2);
@@ -199,16 +225,17 @@ __device__ void short_coop(const ProteinView& P, bool active, const double x64[3
         __syncwarp();
         if (lane < m) {
             const int o = Q.owner[lane];
-            const double xo[3] = {Q.x[0][o], Q.x[1][o], Q.x[2][o]};
-            const D4 a64 = P.atoms64[Q.k[lane]];
-            double f[3], fv = 0.0, fgr = 0.0;
-            const int out = short_pair<GRAD>(P, xo, a64, Q.bits[lane], f, fv, fgr);
+            const F2 xo[3] = {F2{Q.x[0][o].x, Q.x[0][o].y}, F2{Q.x[1][o].x, Q.x[1][o].y},
+                              F2{Q.x[2][o].x, Q.x[2][o].y}};
+            const double xo64[3] = {Q.x64[0][o], Q.x64[1][o], Q.x64[2][o]};
+            F2 f[3], w, fv{0.f, 0.f}, fgr{0.f, 0.f};
+            const int out = short_pair<GRAD>(prot_of(o), xo, xo64, Q.k[lane], Q.bits[lane], f, w, fv, fgr);
             Q.bits[lane] = out;
-            Q.w[lane] = a64.w;
-            Q.fv[lane] = fv;
+            Q.w[lane] = make_float2(w.h, w.l);
+            Q.fv[lane] = make_float2(fv.h, fv.l);
             if constexpr (GRAD) {
-                Q.fgr[lane] = fgr;
-                for (int a = 0; a < 3; ++a) Q.f[a][lane] = f[a];
+                Q.fgr[lane] = make_float2(fgr.h, fgr.l);
+                for (int a = 0; a < 3; ++a) Q.f[a][lane] = make_float2(f[a].h, f[a].l);
             }
         }
         __syncwarp();
@@ -218,13 +245,13 @@ __device__ void short_coop(const ProteinView& P, bool active, const double x64[3
                 const int out = Q.bits[e];
                 if (out & 1) clash = 1;
                 if (out & 2) {
-                    double f[3] = {0.0, 0.0, 0.0};
-                    double fgr = 0.0;
+                    F2 f[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                    F2 fgr{0.f, 0.f};
                     if constexpr (GRAD) {
-                        fgr = Q.fgr[e];
-                        for (int a = 0; a < 3; ++a) f[a] = Q.f[a][e];
+                        fgr = F2{Q.fgr[e].x, Q.fgr[e].y};
+                        for (int a = 0; a < 3; ++a) f[a] = F2{Q.f[a][e].x, Q.f[a][e].y};
                     }
-                    short_accumulate<GRAD>(Q.w[e], Q.fv[e], fgr, f, phi, g);
+                    short_accumulate<GRAD>(F2{Q.w[e].x, Q.w[e].y}, F2{Q.fv[e].x, Q.fv[e].y}, fgr, f, phi, g);
                 }
             }
         __syncwarp();
@@ -263,26 +290,48 @@ __device__ void short_coop(const ProteinView& P, bool active, const double x64[3
     if (qn > 0) process(qn);
 }
 
-// FP64 atom position x = R y + t (the interpolation coordinates and the
-// short-range distances use it; FP32 rotation alone misplaces atoms by ~1e-6 A).
-__device__ __forceinline__ void atom_position(const PoseSetup& q, const double* __restrict__ y64,
-                                              double x64[3]) {
-    double y0 = y64[0], y1 = y64[1], y2 = y64[2];
+// The same for a warp whose atoms all belong to protein P.
+template <bool GRAD>
+__device__ __forceinline__ void short_coop(const ProteinView& P, bool active, const F2 x[3], const double x64[3],
+                                           NearQueue<GRAD>& Q, F2& phi, F2 g[3], int& clash) {
+    short_coop_with<GRAD>([&](int) -> const ProteinView& { return P; }, active, x, x64, Q, phi, g, clash);
+}
+
+// Atom position x = R y + t in float-pair arithmetic (Dot2 of the pair rows of R
+// with the pair coordinates; FP32 rotation alone misplaces atoms by ~1e-6 A).
+__device__ __forceinline__ void atom_position(const PoseSetup& q, const float2* __restrict__ yd, F2 x[3]) {
+    const F2 y[3] = {F2{yd[0].x, yd[0].y}, F2{yd[1].x, yd[1].y}, F2{yd[2].x, yd[2].y}};
+    for (int r = 0; r < 3; ++r) {
+        F2 acc = q.td[r];
+        dev::df_fma_acc(acc, q.Rd[3 * r], y[0]);
+        dev::df_fma_acc(acc, q.Rd[3 * r + 1], y[1]);
+        dev::df_fma_acc(acc, q.Rd[3 * r + 2], y[2]);
+        x[r] = dev::df_norm(acc);
+    }
+}
+
+// FP64 position x = t + R y (12 FP64 operations; used only for vdW decisions
+// inside the sigma band, where the FP64 oracle's decision must be reproduced).
+__device__ __forceinline__ void atom_position64(const PoseSetup& q, const double* __restrict__ y64,
+                                                double x64[3]) {
+    const double y0 = y64[0], y1 = y64[1], y2 = y64[2];
     for (int r = 0; r < 3; ++r)
         x64[r] = __dadd_rn(q.t[r], fma(q.R[3 * r + 2], y2, fma(q.R[3 * r + 1], y1, __dmul_rn(q.R[3 * r], y0))));
 }
 
 // Geometry of ligand atom j in pose q: rotated offset R y in FP32 (torque arm of
-// the gradient), FP64 position, and per axis the interpolation cell, fraction and
-// whether the coordinate lies inside [-b, b].
+// the gradient), pair and FP64 positions, and per axis the interpolation cell,
+// fraction and whether the coordinate lies inside [-b, b].
 __device__ __forceinline__ void atom_geometry(const ProteinView& P, const LigandView& lig,
                                               const PoseSetup& q, int j, float ry[3],
-                                              double x64[3], int ci[3], float cf[3], bool ins[3]) {
+                                              F2 x[3], double x64[3], int ci[3], float cf[3], bool ins[3]) {
     float4 yq = lig.y[j];
     for (int r = 0; r < 3; ++r)
         ry[r] = __fmaf_rn(q.Rf[3 * r + 2], yq.z, __fmaf_rn(q.Rf[3 * r + 1], yq.y, __fmul_rn(q.Rf[3 * r], yq.x)));
-    atom_position(q, lig.y64 + 3 * j, x64);
-    for (int a = 0; a < 3; ++a) dev::axis_cell(x64[a], P.b, P.inv_h, P.n, ci[a], cf[a], ins[a]);
+    atom_position(q, lig.yd + 3 * j, x);
+    atom_position64(q, lig.y64 + 3 * j, x64);
+    for (int a = 0; a < 3; ++a)
+        dev::axis_cell(x[a], F2{P.b_h, P.b_l}, F2{P.inv_h_h, P.inv_h_l}, P.n, ci[a], cf[a], ins[a]);
 }
 
 // Per-atom contributions to the pose sums from the long-range value (pair sums
@@ -412,12 +461,13 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
         int ci[3] = {0, 0, 0};
         float cf[3] = {0.f, 0.f, 0.f};
         bool ins[3] = {true, true, true};
+        F2 x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         double x64[3] = {0.0, 0.0, 0.0};
-        if (valid) atom_geometry(P, lig, ps[pl], j, ry, x64, ci, cf, ins);
+        if (valid) atom_geometry(P, lig, ps[pl], j, ry, x, x64, ci, cf, ins);
         // short range and vdW of the warp's atoms
-        double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
+        F2 phs{0.f, 0.f}, gs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         int clash = 0;
-        short_coop<GRAD>(P, valid, x64, queues[tid >> 5], phs, gs, clash);
+        short_coop<GRAD>(P, valid, x, x64, queues[tid >> 5], phs, gs, clash);
         if (!valid) continue;
         // v1 (axis 1) into this thread's shared-memory column; v2 (axis 2) in registers
         {
@@ -505,7 +555,8 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
         int fl = clash ? RS_FLAG_CLASH : 0;
         if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
         if (fl) atomicOr(&pflag[pl], fl);
-        atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, lig.q64[j], ry, cj);
+        const double gsd[3] = {dev::df_to(gs[0]), dev::df_to(gs[1]), dev::df_to(gs[2])};
+        atom_contrib<GRAD>(P, phi, g1, g2, g3, dev::df_to(phs), gsd, lig.q64[j], ry, cj);
     }
     __syncthreads();
     reduce_poses<NC>(P, PB, L, p0, Ptot, ps, contrib, pflag, E, flags, gt, gw);

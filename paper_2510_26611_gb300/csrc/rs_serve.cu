@@ -1,7 +1,8 @@
 // Serving: a request loop with continuous batching around Algorithm PLIE (Sec. 3.4).
 //
 // Requests (protein + ligand + poses, host memory) are queued by rs_serve_submit.
-// One scheduler thread owns a private context and loops:
+// A builder thread builds missing proteins on its own context; the scheduler thread
+// owns another context and loops:
 //   1. retire: launches whose completion event fired hand their results (already
 //      staged in pinned host memory by the launch's stream) to the callers'
 //      buffers and give their device blocks back to the pool;
@@ -12,8 +13,9 @@
 //      size-class pool that keeps its slabs while serving, so no cudaFree stalls the
 //      device between launches;
 //   3. launch: every request admitted in this pass goes into one batched pose launch
-//      (a persistent work-list kernel per padded Tucker rank, the same per-pose-block
-//      code as rs_energy_poses) on the next free stream.  Up to
+//      per padded Tucker rank (the cell-grouped multi-pair pipeline for requests
+//      with many pose-atoms per grid cell, one persistent per-block kernel for the
+//      rest; both compute every pose as rs_energy_poses does) on the next free stream.  Up to
 //      max_inflight_launches launches run at once, so work that arrives while the
 //      GPU is busy is admitted into the next launch and overlaps with the running one.
 // All host waits are bounded (condition-variable timeouts, event queries); no device
@@ -34,6 +36,7 @@
 #include "rs_diag.cuh"
 #include "rs_eval.cuh"
 #include "rs_batch_dev.cuh"
+#include "rs_group.cuh"
 
 namespace rs {
 namespace {
@@ -469,6 +472,14 @@ void admit(rs_server* S, std::vector<Request*>& ready, bool can_launch) {
     }
 }
 
+// Pose-atoms per chunk of a serving launch (bounds its scratch to ~230 MB).
+constexpr long long kServeChunkAtoms = 1LL << 21;
+
+// A request takes the cell-grouped path when its pose-atoms average at least this
+// many per grid cell along axis 3 (each staged W slab then serves many atoms);
+// sparser requests (fine grids, few poses) take the per-block kernel.
+constexpr double kDenseAtomsPerCell = 64.0;
+
 template <int RP, int NT>
 rs_status launch_group(const PairDesc* d_desc, const BatchItem* d_items, int nitems, int* d_counter,
                        size_t smem, cudaStream_t st) {
@@ -505,6 +516,7 @@ rs_status dispatch(int RP, int NT, const PairDesc* d_desc, const BatchItem* d_it
     }
 }
 
+
 // Uploads the inputs of the requests admitted in this pass and launches them
 // together on stream `si`; results are staged to pinned memory on the same stream.
 void launch(rs_server* S, std::vector<Request*>& ready, int si) {
@@ -531,7 +543,7 @@ void launch(rs_server* S, std::vector<Request*>& ready, int si) {
             good = cudaMemcpyAsync(qu, q.quat, (size_t)q.P * 32, cudaMemcpyHostToDevice, st) == cudaSuccess &&
                    cudaMemcpyAsync(tr, q.trans, (size_t)q.P * 24, cudaMemcpyHostToDevice, st) == cudaSuccess;
         if (good)
-            good = launch_prep_ligand(q.L, lx, lq, (float4*)lig.y, (double*)lig.y64, (double*)lig.q64, st) == RS_OK;
+            good = launch_prep_ligand(q.L, lx, lq, (float4*)lig.y, (float2*)lig.yd, (double*)lig.y64, (double*)lig.q64, st) == RS_OK;
         if (!good) {
             cudaGetLastError();
             r->fail(RS_ERR_CUDA, "input upload failed");
@@ -576,33 +588,73 @@ void launch(rs_server* S, std::vector<Request*>& ready, int si) {
     int64_t t_start = now_ns();
     for (auto& g : groups) {
         if (status != RS_OK) break;
-        int nt = 128, atoms = 512;
-        batch_shape_for(g.first, &nt, &atoms);
-        std::vector<BatchItem> items;
-        std::vector<int> Ls;
-        for (int i : g.second) {
-            int PB = pb_for(desc[i].lig.L, atoms);
-            Ls.push_back(desc[i].lig.L);
-            for (long long p0 = 0; p0 < desc[i].P; p0 += PB) items.push_back({i, PB, p0});
+        std::vector<int> dense, sparse;
+        for (int i : g.second)
+            ((double)desc[i].P * desc[i].lig.L >= kDenseAtomsPerCell * desc[i].prot.n ? dense : sparse).push_back(i);
+        if (!dense.empty()) {
+            // the cell-grouped multi-pair pipeline over the dense requests
+            GroupPlan plan;
+            status = group_plan(desc, dense, kServeChunkAtoms, &plan);
+            if (status != RS_OK) {
+                why = "launch plan failed";
+                break;
+            }
+            void* segs = nullptr;
+            void* ws = nullptr;
+            const size_t sb = plan.segs.size() * sizeof(GroupSeg);
+            if (S->dev.get(sb, (size_t)-1, &segs) != POOL_OK || S->dev.get(plan.scratch, (size_t)-1, &ws) != POOL_OK) {
+                S->dev.put(segs);
+                status = RS_ERR_OOM;
+                why = "launch scratch allocation failed";
+                break;
+            }
+            Lh.blocks.push_back(segs);
+            Lh.blocks.push_back(ws);
+            if (cudaMemcpyAsync(segs, plan.segs.data(), sb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+                status = RS_ERR_CUDA;
+                why = "segment upload failed";
+                break;
+            }
+            status = group_launch(plan, (const PairDesc*)d_desc, (const GroupSeg*)segs, ws, Pool::cls(plan.scratch),
+                                  4, st, true);
+            if (status != RS_OK) {
+                why = "batched launch failed";
+                break;
+            }
         }
-        size_t ib = round256(items.size() * sizeof(BatchItem)) + 256;
-        void* blk = nullptr;
-        if (S->dev.get(ib, (size_t)-1, &blk) != POOL_OK) {
-            status = RS_ERR_OOM;
-            why = "work-list allocation failed";
-            break;
+        if (!sparse.empty()) {
+            // one persistent per-block launch over the sparse requests' pose blocks
+            int nt = 128, atoms = 512;
+            batch_shape_for(g.first, &nt, &atoms);
+            std::vector<BatchItem> items;
+            std::vector<int> Ls;
+            for (int i : sparse) {
+                int PB = pb_for(desc[i].lig.L, atoms);
+                Ls.push_back(desc[i].lig.L);
+                for (long long p0 = 0; p0 < desc[i].P; p0 += PB) items.push_back({i, PB, p0});
+            }
+            size_t ib = round256(items.size() * sizeof(BatchItem)) + 256;
+            void* blk = nullptr;
+            if (S->dev.get(ib, (size_t)-1, &blk) != POOL_OK) {
+                status = RS_ERR_OOM;
+                why = "work-list allocation failed";
+                break;
+            }
+            Lh.blocks.push_back(blk);
+            int* counter = (int*)((char*)blk + round256(items.size() * sizeof(BatchItem)));
+            if (cudaMemcpyAsync(blk, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess) {
+                status = RS_ERR_CUDA;
+                why = "work-list upload failed";
+                break;
+            }
+            status = dispatch(g.first, nt, (const PairDesc*)d_desc, (const BatchItem*)blk, (int)items.size(),
+                              counter, Ls, atoms, st);
+            if (status != RS_OK) {
+                why = "batched launch failed";
+                break;
+            }
         }
-        Lh.blocks.push_back(blk);
-        int* counter = (int*)((char*)blk + round256(items.size() * sizeof(BatchItem)));
-        if (cudaMemcpyAsync(blk, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess) {
-            status = RS_ERR_CUDA;
-            why = "work-list upload failed";
-            break;
-        }
-        status = dispatch(g.first, nt, (const PairDesc*)d_desc, (const BatchItem*)blk, (int)items.size(),
-                          counter, Ls, atoms, st);
-        if (status != RS_OK) why = "batched launch failed";
     }
     for (int i : canon) {
         if (status != RS_OK) break;

@@ -63,7 +63,8 @@ class rs_pair(C.Structure):
 class rs_batch_info(C.Structure):
     _fields_ = [("npairs", C.c_int32), ("ngroups", C.c_int32), ("nitems", C.c_int32),
                 ("grid", C.c_int32), ("threads", C.c_int32), ("atoms_per_item", C.c_int32),
-                ("tune_ms", C.c_double)]
+                ("tune_ms", C.c_double), ("mode", C.c_int32), ("warps_per_cta", C.c_int32),
+                ("chunk_atoms", C.c_int64), ("nchunks", C.c_int32)]
 
 
 class rs_request(C.Structure):
@@ -124,6 +125,7 @@ def _load() -> C.CDLL:
         "rs_serve_cancel": (st, [vp, C.c_uint64]),
         "rs_serve_get_stats": (st, [vp, C.POINTER(rs_serve_stats)]),
         "rs_serve_destroy": (None, [vp]),
+        "rs_symeig_host": (st, [i32, vp, vp, vp]),
         "rs_stats_kernel_launches": (C.c_ulonglong, []),
         "rs_timing_enable": (st, [C.c_int]),
         "rs_timing_reset": (st, []),
@@ -351,7 +353,7 @@ def rs_pgd_run(ctx: int, prot: int, lig_xyz, lig_q, rotvec, trans, nsteps: int,
     return E, f, acc
 
 
-def rs_batch_create(ctx: int, pairs: list, autotune: bool = True):
+def rs_batch_create(ctx: int, pairs: list, autotune: int | bool = True):
     """pairs: list of dicts with keys prot (handle), lig_xyz, lig_q, quat, trans, E_out,
     flags_out (CUDA tensors; outputs preallocated).  Returns (handle, keepalive)."""
     arr = (rs_pair * len(pairs))()
@@ -364,7 +366,7 @@ def rs_batch_create(ctx: int, pairs: list, autotune: bool = True):
                          _ptr(qu), _ptr(tr), _ptr(p["E_out"]),
                          _ptr(p["flags_out"]) if p.get("flags_out") is not None else None)
     h = C.c_void_p()
-    _check(_lib.rs_batch_create(ctx, len(pairs), arr, 1 if autotune else 0, C.byref(h)))
+    _check(_lib.rs_batch_create(ctx, len(pairs), arr, int(autotune), C.byref(h)))
     return h.value, keep
 
 
@@ -380,6 +382,17 @@ def rs_batch_get_info(batch: int) -> dict:
     info = rs_batch_info()
     _check(_lib.rs_batch_get_info(batch, C.byref(info)))
     return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def rs_symeig_host(A: np.ndarray):
+    """Eigenvalues (descending) and eigenvectors (columns) of the symmetric part of A,
+    by the library's host eigensolver."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    lam = np.empty(n)
+    W = np.empty((n, n))
+    _check(_lib.rs_symeig_host(n, A.ctypes.data, lam.ctypes.data, W.ctypes.data))
+    return lam, W
 
 
 def rs_stats_kernel_launches() -> int:

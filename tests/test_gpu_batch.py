@@ -67,12 +67,35 @@ def test_batch_equals_plain_calls(setup):
     import torch
     lib, ctx, ws, prots, pairs, b = setup
     info = lib.rs_batch_get_info(b)
-    assert info["npairs"] == len(ws) and info["nitems"] > 0
-    assert info["threads"] in (128, 256)
+    assert info["npairs"] == len(ws)
+    if info["mode"] == 0:
+        assert info["nitems"] > 0 and info["threads"] in (128, 256)
+    else:
+        assert info["nchunks"] > 0 and info["warps_per_cta"] in (4, 8)
     lib.rs_batch_run(b)
     torch.cuda.synchronize()
     ref = _plain(lib, prots, pairs)
     for p, (E, f) in zip(pairs, ref):
+        assert np.array_equal(p["E_out"].cpu().numpy(), E)
+        assert np.array_equal(p["flags_out"].cpu().numpy(), f)
+
+
+@pytest.mark.parametrize("mode", [0, 2], ids=["cell-grouped", "per-block"])
+def test_both_batch_paths_equal_plain_calls(setup, mode):
+    import torch
+    lib, ctx, ws, prots, pairs, b = setup
+    outs = [dict(p, E_out=torch.full_like(p["E_out"], float("nan")),
+                 flags_out=torch.full_like(p["flags_out"], 255)) for p in pairs]
+    b2, keep = lib.rs_batch_create(ctx.handle, outs, autotune=mode)
+    try:
+        info = lib.rs_batch_get_info(b2)
+        assert info["mode"] == (1 if mode == 0 else 0)
+        lib.rs_batch_run(b2)
+        torch.cuda.synchronize()
+    finally:
+        lib.rs_batch_free(b2)
+    ref = _plain(lib, prots, pairs)
+    for p, (E, f) in zip(outs, ref):
         assert np.array_equal(p["E_out"].cpu().numpy(), E)
         assert np.array_equal(p["flags_out"].cpu().numpy(), f)
 
