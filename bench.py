@@ -53,6 +53,7 @@ def parse_args():
                          "projected gradient descent; serve: Poisson request stream through "
                          "the serving loop vs the plain per-request path")
     ap.add_argument("--pairs", type=int, default=64)
+    ap.add_argument("--pair-poses", type=int, default=10_000, help="batch: poses per pair")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--serve-n-max", type=int, default=16385, help="serve: largest grid")
@@ -279,7 +280,7 @@ def run_batch(args):
     from paper_2510_26611_gb300 import lib
     dev = torch.device("cuda", 0)
     ctx = lib.Context(0)
-    ws = W.batch_pairs(seed=2, pairs=args.pairs, P=10_000)
+    ws = W.batch_pairs(seed=2, pairs=args.pairs, P=args.pair_poses)
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
     t0 = time.perf_counter()
     prots, pairs = [], []
@@ -331,11 +332,12 @@ def run_batch(args):
                       "launches": len(pairs)},
             "speedup_vs_plain": round(ms_plain / ms_batch, 3), "bitwise_equal_to_plain": bool(same),
             "config": {"workload": "batch_pairs: N log-uniform [500,20000], L uniform [10,200], "
-                                   "n in {513,1025,2049,4097} by box quartile, 1e4 poses per pair, "
-                                   "Tucker rank <= 20",
+                                   "n in {513,1025,2049,4097} by box quartile, "
+                                   f"{args.pair_poses} poses per pair, Tucker rank <= 20",
                        "pairs": len(ws), "poses": P_tot, "atom_evaluations": atoms,
                        "n_hist": {str(n): sum(1 for w in ws if w.n == n) for n in sorted({w.n for w in ws})}},
-            "batch_info": info, "build_s_total": round(build_s, 3)}
+            "batch_info": info, "build_s_total": round(build_s, 3),
+            "launch_calls": {"batched": 1, "plain": len(pairs)}}
     print(json.dumps(line), flush=True)
     lib.rs_batch_free(b)
     for h in prots:
@@ -387,6 +389,17 @@ def run_pgd(args):
     torch.cuda.synchronize()
     ms = a.elapsed_time(c)
     launches = lib.rs_stats_kernel_launches() - launches0
+    # what one step is made of: a gradient pass and an energy pass over all poses
+    # (per-kernel device times, timing events on; not part of the timed run)
+    lib.rs_timing_reset()
+    lib.rs_timing_enable(2)
+    for _ in range(5):
+        lib.rs_energy_grad_poses(ctx.handle, holder["prot"], lx, lq, rv, tr)
+        lib.rs_energy_poses(ctx.handle, holder["prot"], lx, lq, T(w.quat), tr)
+    torch.cuda.synchronize()
+    kernels = {k: round(v["ms"] / 5, 4) for k, v in
+               sorted(lib.rs_timing_all().items(), key=lambda kv: -kv[1]["ms"])}
+    lib.rs_timing_enable(0)
     E0, E1 = E0.cpu().numpy(), E.cpu().numpy()
     line = {"metric": "gradients/s through projected gradient descent (Eq. Energy_Min)",
             "value": round(w.P * nsteps / (ms / 1e3), 3), "unit": "pose-gradients/s", "n_gpus": 1,
@@ -400,7 +413,8 @@ def run_pgd(args):
             "result": {"mean_E_start": float(E0.mean()), "mean_E_end": float(E1.mean()),
                        "all_final_feasible": bool((f.cpu().numpy() == 0).all()),
                        "accepted_last_step": float((acc.cpu().numpy() >= 0).mean())},
-            "gpu_launches": int(launches), "build_s": round(build_s, 3)}
+            "gpu_launches": int(launches), "build_s": round(build_s, 3),
+            "kernels_ms_one_gradient_and_one_energy_pass": kernels}
     print(json.dumps(line), flush=True)
     lib.rs_protein_free(holder["prot"])
     ctx.close()

@@ -458,35 +458,49 @@ __global__ void k_sum_gram(int nblk, int p, const double* __restrict__ Sp, doubl
     S[(size_t)ax * p * p + e] = s;
 }
 
-// S[ax] = A[ax]^T B[ax] (p x p), A and B n x p.  CTA per (row a, axis).
+// Partial products Sp[ax][blk] = A_blk^T B_blk (p x p) of 16-row blocks of A and
+// B (n x p); k_sum_gram adds the blocks in a fixed order.  CTA: one block of one axis.
 __global__ void __launch_bounds__(256) k_atb(int n, int p, const double* __restrict__ A,
-                                              const double* __restrict__ B,
-                                              double* __restrict__ S) {
-    __shared__ double sm[4][64];
-    int a = blockIdx.x, ax = blockIdx.y;
-    int c = threadIdx.x % 64, part = threadIdx.x / 64;
+                                              const double* __restrict__ B, double* __restrict__ Sp) {
+    __shared__ double As[16][49], Bs[16][49];
+    const int ax = blockIdx.y, i0 = blockIdx.x * 16;
     const double* Aa = A + (size_t)ax * n * p;
     const double* Ba = B + (size_t)ax * n * p;
-    double s = 0.0;
-    if (c < p)
-        for (int i = part; i < n; i += 4) s += Aa[(size_t)i * p + a] * Ba[(size_t)i * p + c];
-    sm[part][c] = s;
+    for (int e = threadIdx.x; e < 16 * p; e += 256) {
+        const int r = e / p, c = e % p, gi = i0 + r;
+        As[r][c] = gi < n ? Aa[(size_t)gi * p + c] : 0.0;
+        Bs[r][c] = gi < n ? Ba[(size_t)gi * p + c] : 0.0;
+    }
     __syncthreads();
-    if (part == 0 && c < p)
-        S[((size_t)ax * p + a) * p + c] = ((sm[0][c] + sm[1][c]) + sm[2][c]) + sm[3][c];
+    double* out = Sp + ((size_t)ax * gridDim.x + blockIdx.x) * p * p;
+    for (int e = threadIdx.x; e < p * p; e += 256) {
+        const int a = e / p, c = e % p;
+        double s = 0.0;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) s += As[r][a] * Bs[r][c];
+        out[e] = s;
+    }
 }
 
 // Cholesky S + shift*I = R^T R (R upper) and Rinv = R^{-1}; one CTA per axis.
+// Right-looking, column k at a time: the pivot's square root (one thread), the
+// row scaling (one thread per column), the trailing update over a 16 x 16 thread
+// tile (no index division); then R^{-1} by back substitution, one thread per column.
 __global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restrict__ S,
                                                     double rel_shift,
                                                     double* __restrict__ Rinv,
                                                     int* __restrict__ fail) {
     __shared__ double A[48][49];
     __shared__ double Ri[48][49];
-    __shared__ double shift;
-    int ax = blockIdx.x;
+    __shared__ double shift, piv;
+    const int ax = blockIdx.x;
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
     const double* Sa = S + (size_t)ax * p * p;
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) A[e / p][e % p] = Sa[e];
+    for (int i = ty; i < p; i += 16)
+        for (int j = tx; j < p; j += 16) {
+            A[i][j] = Sa[i * p + j];
+            Ri[i][j] = 0.0;
+        }
     __syncthreads();
     if (threadIdx.x == 0) {
         double tr = 0;
@@ -496,7 +510,6 @@ __global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restri
     __syncthreads();
     if (threadIdx.x < p) A[threadIdx.x][threadIdx.x] += shift;
     __syncthreads();
-    // right-looking Cholesky on the upper triangle: A = R^T R
     for (int k = 0; k < p; ++k) {
         if (threadIdx.x == 0) {
             double d = A[k][k];
@@ -504,22 +517,23 @@ __global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restri
                 fail[ax] = 1;
                 d = 1e-300;
             }
-            A[k][k] = sqrt(d);
+            d = sqrt(d);
+            A[k][k] = d;
+            piv = 1.0 / d;
         }
         __syncthreads();
-        double dk = A[k][k];
-        for (int j = k + 1 + threadIdx.x; j < p; j += blockDim.x) A[k][j] /= dk;
+        if (threadIdx.x > k && threadIdx.x < p) A[k][threadIdx.x] *= piv;
         __syncthreads();
-        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-            int i = e / p, j = e % p;
-            if (i > k && j >= i) A[i][j] -= A[k][i] * A[k][j];
+        for (int i = k + 1 + ty; i < p; i += 16) {
+            const double aki = A[k][i];
+            for (int j = k + 1 + tx; j < p; j += 16)
+                if (j >= i) A[i][j] -= aki * A[k][j];
         }
         __syncthreads();
     }
     // inverse of upper-triangular R, column by column (back substitution)
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) Ri[e / p][e % p] = 0.0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    if (threadIdx.x < p) {
+        const int j = threadIdx.x;
         Ri[j][j] = 1.0 / A[j][j];
         for (int i = j - 1; i >= 0; --i) {
             double s = 0.0;
@@ -529,7 +543,8 @@ __global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restri
     }
     __syncthreads();
     double* Ra = Rinv + (size_t)ax * p * p;
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) Ra[e] = Ri[e / p][e % p];
+    for (int i = ty; i < p; i += 16)
+        for (int j = tx; j < p; j += 16) Ra[i * p + j] = Ri[i][j];
 }
 
 // Q = Y Rinv (Rinv upper triangular), n x p; Q2 (if not null) gets Q as float pairs.
@@ -1172,12 +1187,21 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         ::rs::KernelTimer kt__("k_init_block", st, 0.0, false);
         k_init_block<<<blocks_for((size_t)3 * n * p), kBlock, 0, st>>>(n, p, d_Q);
     }
+    dim3 gq((n + 31) / 32, kGemmKS, 3);
+    const int nblk = (n + 15) / 16;
+    double *d_Sp, *d_Yp;
+    RS_TRY(S.get(&d_Sp, (size_t)3 * nblk * p * p));
+    RS_TRY(S.get(&d_Yp, (size_t)kGemmKS * 3 * n * p));
     // CholQR2 of Yin (d_Q or d_Y): shifted CholQR then plain CholQR; every pass reads
     // one buffer and writes the other, and the result ends in d_Q.
     auto cholqr_pass = [&](const double* src, double* dst, double shift) -> rs_status {
         {
             ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
-            k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, src, src, d_Sm);
+            k_atb<<<dim3(nblk, 3), 256, 0, st>>>(n, p, src, src, d_Sp);
+        }
+        {
+            ::rs::KernelTimer kt__("k_sum_gram", st, 0.0, false);
+            k_sum_gram<<<dim3(blocks_for((size_t)p * p), 3), kBlock, 0, st>>>(nblk, p, d_Sp, d_Sm);
         }
         {
             ::rs::KernelTimer kt__("k_chol_rinv", st, 0.0, false);
@@ -1201,11 +1225,6 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         return RS_OK;
     };
     RS_TRY(orthonormalize(d_Q));
-    dim3 gq((n + 31) / 32, kGemmKS, 3);
-    const int nblk = (n + 15) / 16;
-    double *d_Sp, *d_Yp;
-    RS_TRY(S.get(&d_Sp, (size_t)3 * nblk * p * p));
-    RS_TRY(S.get(&d_Yp, (size_t)kGemmKS * 3 * n * p));
     work = 3.0 * 13.0 * n * (double)n * p;  // FP32 pipe ops per G Q (one Dot2 step per product)
     // one subspace step: Y = G Q with partial Grams, S = Y^T Y, shifted Cholesky, Q = Y R^-1
     auto step = [&]() -> rs_status {
@@ -1244,7 +1263,11 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         }
         {
             ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
-            k_atb<<<dim3(p, 3), 256, 0, st>>>(n, p, d_Q, d_Y, d_Sm);
+            k_atb<<<dim3(nblk, 3), 256, 0, st>>>(n, p, d_Q, d_Y, d_Sp);
+        }
+        {
+            ::rs::KernelTimer kt__("k_sum_gram", st, 0.0, false);
+            k_sum_gram<<<dim3(blocks_for((size_t)p * p), 3), kBlock, 0, st>>>(nblk, p, d_Sp, d_Sm);
         }
         RS_TRY_CUDA(cudaGetLastError());
         // p x p eigenproblems on the host (FP64): a few microseconds each

@@ -180,13 +180,16 @@ struct NearQueue {
     float2 f[GRAD ? 3 : 1][32];
     float2 x[3][32]; // pair positions of the warp's atoms
     double x64[3][32];  // FP64 positions (decisions inside the sigma band)
-    int rs[9][32], re[9][32];
+    int rs[9][32];      // first candidate of each neighbourhood row
+    int rp[10][32];     // prefix of the rows' lengths (rp[9] = the lane's total)
+    int lstart[32];     // prefix of the lanes' totals over the warp
 };
 
-// Short range and vdW decision for the 32 atoms of a warp (one per lane), with the
-// FP32 screen run by all lanes in step and the pair-arithmetic work of near pairs
-// packed one pair per lane: a warp whose atoms see different numbers of near pairs
-// keeps every lane busy.  Every lane of the warp must call it; lanes with
+// Short range and vdW decision for the 32 atoms of a warp (one per lane).  The
+// candidates of all 32 atoms form one list (lane by lane, each lane's in its own
+// candidate order) that the lanes screen in FP32 32 at a time, and the near pairs
+// are then evaluated in pair arithmetic one pair per lane: atoms with very
+// different numbers of candidates or near pairs still keep every lane busy.  Every lane of the warp must call it; lanes with
 // active = false contribute no atom.  prot_of(l) is the protein of lane l's atom
 // (lanes may belong to different proteins).  Each atom's sums are accumulated in
 // its own candidate order, so they equal short_vdw's (nl = 1) bit for bit.
@@ -196,9 +199,9 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
     const int lane = threadIdx.x & 31;
     const ProteinView& P = prot_of(lane);
     const unsigned full = 0xffffffffu;
-    float xf[3] = {0.f, 0.f, 0.f};
     int total = 0;
     if (active) {
+        float xf[3];
         for (int a = 0; a < 3; ++a) {
             xf[a] = x[a].h;
             Q.x[a][lane] = make_float2(x[a].h, x[a].l);
@@ -210,16 +213,23 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
             int s, e;
             short_row(P, c0, c1, c2, row, s, e);
             Q.rs[row][lane] = s;
-            Q.re[row][lane] = e;
+            Q.rp[row][lane] = total;
             total += e - s;
         }
+    } else {
+        for (int row = 0; row < 9; ++row) Q.rp[row][lane] = 0;
     }
-    const int maxlen = __reduce_max_sync(full, total);
-    int row = 0, pos = 0;
-    if (active) {
-        while (row < 9 && Q.rs[row][lane] == Q.re[row][lane]) ++row;
-        if (row < 9) pos = Q.rs[row][lane];
+    Q.rp[9][lane] = total;
+    // warp prefix of the totals: lane l's candidates are list entries [lstart, lstart + total)
+    int incl = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += v;
     }
+    Q.lstart[lane] = incl - total;
+    const int grand = __shfl_sync(full, incl, 31);
+    __syncwarp();
     int qn = 0;  // entries in the queue (the same in every lane)
     auto process = [&](int m) {
         __syncwarp();
@@ -256,22 +266,31 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
             }
         __syncwarp();
     };
-    for (int it = 0; it < maxlen; ++it) {
-        int bits = 0, k = 0;
-        if (it < total) {
-            k = pos;
-            bits = short_screen(P, xf, P.atoms[k]);
-            if (++pos == Q.re[row][lane]) {
-                ++row;
-                while (row < 9 && Q.rs[row][lane] == Q.re[row][lane]) ++row;
-                if (row < 9) pos = Q.rs[row][lane];
+    for (int base = 0; base < grand; base += 32) {
+        const int e = base + lane;
+        int bits = 0, k = 0, o = 0;
+        if (e < grand) {
+            // owner: the last lane whose list starts at or before e
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (Q.lstart[mid] <= e) lo = mid;
+                else hi = mid - 1;
             }
+            o = lo;
+            const int off = e - Q.lstart[o];
+            int r = 0;
+            while (Q.rp[r + 1][o] <= off) ++r;
+            k = Q.rs[r][o] + (off - Q.rp[r][o]);
+            const float xo[3] = {Q.x[0][o].x, Q.x[1][o].x, Q.x[2][o].x};
+            const ProteinView& Po = prot_of(o);
+            bits = short_screen(Po, xo, Po.atoms[k]);
         }
         const bool near = (bits & 3) != 0;
         const unsigned m = __ballot_sync(full, near);
         if (near) {
             const int slot = qn + __popc(m & ((1u << lane) - 1u));
-            Q.owner[slot] = lane;
+            Q.owner[slot] = o;
             Q.k[slot] = k;
             Q.bits[slot] = bits;
         }

@@ -475,10 +475,12 @@ void admit(rs_server* S, std::vector<Request*>& ready, bool can_launch) {
 // Pose-atoms per chunk of a serving launch (bounds its scratch to ~230 MB).
 constexpr long long kServeChunkAtoms = 1LL << 21;
 
-// A request takes the cell-grouped path when its pose-atoms average at least this
-// many per grid cell along axis 3 (each staged W slab then serves many atoms);
-// sparser requests (fine grids, few poses) take the per-block kernel.
+// A request takes the cell-grouped path when it has at least 2^20 pose-atoms and
+// they average at least 64 per grid cell along axis 3 (each staged W slab then
+// serves many atoms and the pipeline's launches are amortised); other requests take
+// the per-block kernel (measured faster for 2048-pose requests).
 constexpr double kDenseAtomsPerCell = 64.0;
+constexpr double kDenseMinAtoms = 1048576.0;
 
 template <int RP, int NT>
 rs_status launch_group(const PairDesc* d_desc, const BatchItem* d_items, int nitems, int* d_counter,
@@ -590,7 +592,10 @@ void launch(rs_server* S, std::vector<Request*>& ready, int si) {
         if (status != RS_OK) break;
         std::vector<int> dense, sparse;
         for (int i : g.second)
-            ((double)desc[i].P * desc[i].lig.L >= kDenseAtomsPerCell * desc[i].prot.n ? dense : sparse).push_back(i);
+            ((double)desc[i].P * desc[i].lig.L >= std::max(kDenseMinAtoms, kDenseAtomsPerCell * desc[i].prot.n)
+                 ? dense
+                 : sparse)
+                .push_back(i);
         if (!dense.empty()) {
             // the cell-grouped multi-pair pipeline over the dense requests
             GroupPlan plan;
