@@ -152,6 +152,7 @@ KERNEL_KIND = {
     "k_eval_wform": ("alu", "fp32ops"), "k_eval_wform_grad": ("alu", "fp32ops"),
     "k_eval_canon": ("alu", "fp32"), "k_eval_canon_grad": ("alu", "fp32"),
     "k_sorted_wform": ("alu", "fp32ops"), "k_sorted_wform_grad": ("alu", "fp32ops"),
+    "k_sorted_tc": ("alu", "fp32ops"), "k_sorted_tc_grad": ("alu", "fp32ops"), "k_group_tc": ("alu", "fp32ops"),
     "k_project": ("alu", "fp32ops"), "k_core": ("alu", "fp32ops"), "k_gauss_dsum": ("alu", "fp32ops"),
     "k_gram": ("alu", "fp64"), "k_gemm_gq": ("alu", "fp32ops"), "k_canon_factors": ("hbm", "bytes"),
 }
@@ -708,14 +709,15 @@ def run_ours(args):
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64 build, f32-pair evaluation", "data": "synthetic",
+                "dtype": "f64 build, f32-pair + bf16-slice tensor-core evaluation", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "poses_per_gpu": P, "ligand_atoms": w.L,
                            "protein_atoms": w.N, "n": w.n, "b": w.b, "tucker_cap": w.tucker_cap,
                            "l2": "flushed between steps (256 MiB write, outside the timed events)",
                            "parallelism": f"{world} independent ranks, poses split (no collective)"},
                 "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "roofline_pose_kernels": {k: roofline(timings, pk, k) for k in
-                                          ("k_sorted_wform_grad", "k_sorted_wform") if k in timings},
+                                          ("k_sorted_tc_grad", "k_sorted_tc", "k_sorted_wform_grad",
+                                           "k_sorted_wform") if k in timings},
                 "clocks": clocks,
                 "kernels_ms_per_step": {r["name"]: round(r["ms"] / args.steps, 4) for r in top}}
         print(json.dumps(line), flush=True)

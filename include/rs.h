@@ -353,6 +353,26 @@ int       rs_timing_count(void);
 rs_status rs_timing_get(int index, char* name, size_t name_len, double* total_ms,
                         unsigned long long* launches, double* work);
 
+/* Long-range (W form, Sec. 3 Tucker interpolation) kernel of the cell-grouped pose
+ * paths that rs_energy_poses, rs_energy_grad_poses, rs_batch_run and the server
+ * take for large calls: mode 1 (default) runs the per-cell contraction on the
+ * tensor cores (tcgen05 MMAs on exact BF16 slices, ~2^-31 relative accuracy of each
+ * contraction); mode 0 runs it in float-pair arithmetic on the FP32 pipes
+ * (~2^-47).  Both agree with the FP64 definition far inside the 1e-5 energy
+ * tolerance; the per-block path of small calls is float-pair in both modes.
+ * Process-wide; takes effect for launches (and batch plans) made afterwards.
+ * Returns the previous mode. */
+int       rs_set_wform_kernel(int mode);
+/* Number of tensor-core tiles on `device` whose MMAs did not complete within the
+ * kernel's bounded wait (their energies were set to NaN); 0 in normal operation. */
+rs_status rs_tc_error_count(int device, int32_t* out);
+/* Diagnostics of the tensor-core contraction alone: for one cell with W, D
+ * (RP x RP, row-major FP64, host) and `rows` <= 128 rows v (rows x RP, host), computes
+ * X = v W^T and Xd = v D^T (rows x RP, host) by the same slicing, MMAs and
+ * combination the pose kernels use.  RP in {4, 8, ..., 32}.  Synchronous. */
+rs_status rs_diag_tc_contract(int32_t RP, int32_t rows, const double* v, const double* W,
+                              const double* D, double* X, double* Xd);
+
 #ifdef __cplusplus
 }
 #endif

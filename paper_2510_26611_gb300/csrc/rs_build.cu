@@ -483,32 +483,39 @@ __global__ void __launch_bounds__(256) k_atb(int n, int p, const double* __restr
 }
 
 // Cholesky S + shift*I = R^T R (R upper) and Rinv = R^{-1}; one CTA per axis.
-// Right-looking, column k at a time: the pivot's square root (one thread), the
-// row scaling (one thread per column), the trailing update over a 16 x 16 thread
-// tile (no index division); then R^{-1} by back substitution, one thread per column.
+// GB300 runs FP64 at 1/64 of its FP32 rate, so a p x p factorisation is bound by the
+// latency of its sequential FP64 chain: each of the p steps keeps one pivot
+// operation (one reciprocal square root, by one thread) and one barrier, and every
+// other operation is spread over the 16 x 16 thread tile.
+//   Cholesky, right-looking: step k takes rk = 1/sqrt(A[k][k]), writes row k of R
+//   (A[k][j] rk) and updates the trailing upper triangle by A[k][i] A[k][j] rk^2.
+//   Inverse, by rows from the bottom: X[k][k] = rk, X[k][j] = -rk acc[k][j], and
+//   acc[i][j] += R[i][k] X[k][j] for i < k <= j, one barrier per row.
 __global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restrict__ S,
                                                     double rel_shift,
                                                     double* __restrict__ Rinv,
                                                     int* __restrict__ fail) {
-    __shared__ double A[48][49];
-    __shared__ double Ri[48][49];
-    __shared__ double shift, piv;
+    __shared__ double A[48][49];   // factorised in place; upper triangle ends as R
+    __shared__ double X[48][49];   // accumulators, then R^{-1}
+    __shared__ double rk[48];      // 1 / R[k][k]
+    __shared__ double red[32];
     const int ax = blockIdx.x;
     const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
     const double* Sa = S + (size_t)ax * p * p;
     for (int i = ty; i < p; i += 16)
         for (int j = tx; j < p; j += 16) {
             A[i][j] = Sa[i * p + j];
-            Ri[i][j] = 0.0;
+            X[i][j] = 0.0;
         }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double tr = 0;
-        for (int i = 0; i < p; ++i) tr += A[i][i];
-        shift = rel_shift * tr;
+    if (threadIdx.x < 32) {  // shift = rel_shift * trace, a warp reduction
+        double t = 0.0;
+        for (int i = threadIdx.x; i < p; i += 32) t += A[i][i];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) red[0] = rel_shift * t;
     }
     __syncthreads();
-    if (threadIdx.x < p) A[threadIdx.x][threadIdx.x] += shift;
+    if (threadIdx.x < p) A[threadIdx.x][threadIdx.x] += red[0];
     __syncthreads();
     for (int k = 0; k < p; ++k) {
         if (threadIdx.x == 0) {
@@ -517,34 +524,37 @@ __global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restri
                 fail[ax] = 1;
                 d = 1e-300;
             }
-            d = sqrt(d);
-            A[k][k] = d;
-            piv = 1.0 / d;
+            const double r = rsqrt(d);
+            rk[k] = r;
+            A[k][k] = d * r;
         }
         __syncthreads();
-        if (threadIdx.x > k && threadIdx.x < p) A[k][threadIdx.x] *= piv;
-        __syncthreads();
+        const double r = rk[k], r2 = r * r;
+        // row k of R (read below only through the unscaled A[k][.] of this step)
         for (int i = k + 1 + ty; i < p; i += 16) {
-            const double aki = A[k][i];
+            const double aki = A[k][i] * r2;
             for (int j = k + 1 + tx; j < p; j += 16)
                 if (j >= i) A[i][j] -= aki * A[k][j];
         }
         __syncthreads();
-    }
-    // inverse of upper-triangular R, column by column (back substitution)
-    if (threadIdx.x < p) {
-        const int j = threadIdx.x;
-        Ri[j][j] = 1.0 / A[j][j];
-        for (int i = j - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int k = i + 1; k <= j; ++k) s += A[i][k] * Ri[k][j];
-            Ri[i][j] = -s / A[i][i];
-        }
+        if (threadIdx.x > k && threadIdx.x < p) A[k][threadIdx.x] *= r;
     }
     __syncthreads();
+    // R^{-1}, rows from the bottom; X[k][.] is final once acc[k][.] has all rows > k
+    for (int k = p - 1; k >= 0; --k) {
+        const double r = rk[k];
+        for (int i = ty; i < k; i += 16)
+            for (int j = k + tx; j < p; j += 16) {
+                const double xkj = j == k ? r : -r * X[k][j];
+                X[i][j] += A[i][k] * xkj;
+            }
+        __syncthreads();
+        if (threadIdx.x >= k && threadIdx.x < p) X[k][threadIdx.x] = threadIdx.x == k ? r : -r * X[k][threadIdx.x];
+        __syncthreads();
+    }
     double* Ra = Rinv + (size_t)ax * p * p;
     for (int i = ty; i < p; i += 16)
-        for (int j = tx; j < p; j += 16) Ra[i * p + j] = Ri[i][j];
+        for (int j = tx; j < p; j += 16) Ra[i * p + j] = j >= i ? X[i][j] : 0.0;
 }
 
 // Q = Y Rinv (Rinv upper triangular), n x p; Q2 (if not null) gets Q as float pairs.
@@ -1418,9 +1428,16 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         k_wtable<<<dim3(blocks_for((size_t)RP * RP), n), kBlock, 0, st>>>(n, RP, d_Vs + 2 * vplane, d_B, wt);
     }
     RS_TRY_CUDA(cudaGetLastError());
+    uint16_t* wtc;
+    float* wsc;
+    RS_TRY(device_alloc(P, (void**)&wtc, tc_bimage_bytes(n, RP)));
+    RS_TRY(device_alloc(P, (void**)&wsc, tc_bscale_bytes(n, RP)));
+    RS_TRY(tc_build_bimage(n, RP, wt, wtc, wsc, st));
     RS_TRY_CUDA(cudaStreamSynchronize(st));
     ProteinView& v = P->view;
     v.kind = 1;
+    v.Wtc = wtc;
+    v.Wsc = wsc;
     v.ld = RP;
     v.R = RP;
     for (int a = 0; a < 3; ++a) v.F[a] = nullptr;

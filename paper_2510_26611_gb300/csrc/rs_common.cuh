@@ -64,6 +64,10 @@ struct ProteinView {
     // each stored as a float pair hi + lo:
     const float* Wt[4];      // Wh, Wl, Dh, Dl   [n][RP][RP]
     const float* Vt[2][4];   // axes 1, 2: Vh, Vl, VDh, VDl  [n][RP]
+    // the same W form as BF16-sliced MMA operands (rs_tc.cuh): per axis-3 cell the
+    // B image (4 slices of NP x KP, canonical K-major layout) and NP inverse scales
+    const uint16_t* Wtc;
+    const float* Wsc;
     const float* core;   // Tucker core [RP][RP][RP] (FP32, diagnostics)
     int Ks;              // short-range terms: t_k^2 and a_k (FP64)
     double ts2[RS_MAX_SHORT];
@@ -152,6 +156,16 @@ struct rs_ctx {
 
 namespace rs {
 rs_status ensure_buffer(void** buf, size_t* cap, size_t need);
+// Device int counting tensor-core tiles whose MMA did not complete in the bounded
+// wait (allocated once per device, on first use from a context's creation).
+int* tc_error_flag(int device);
+// W-form kernel of the cell-grouped pose paths: 1 tensor cores, 0 float pairs.
+int wform_kernel_mode();
+// B images of the W form for the tensor-core path (rs_tc.cu): sizes for n cells of
+// padded rank RP, and the build from the W-form planes wt ([Wh|Wl|Dh|Dl][n][RP][RP]).
+size_t tc_bimage_bytes(int n, int RP);
+size_t tc_bscale_bytes(int n, int RP);
+rs_status tc_build_bimage(int n, int RP, const float* wt, uint16_t* img, float* csc, cudaStream_t st);
 rs_status device_alloc(rs_protein* p, void** ptr, size_t bytes);
 }  // namespace rs
 

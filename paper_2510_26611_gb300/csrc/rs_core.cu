@@ -2,7 +2,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "rs_common.cuh"
@@ -21,6 +23,34 @@ void set_error(const char* fmt, ...) {
 }
 
 void clear_error() { g_last_error.clear(); }
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_tc_mu;
+int* g_tc_flag[kMaxDevices] = {};
+std::atomic<int> g_wform_mode{1};
+}  // namespace
+
+int* tc_error_flag(int device) {
+    if (device < 0 || device >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    if (!g_tc_flag[device]) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, 256) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaMemset(p, 0, 256) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(p);
+            return nullptr;
+        }
+        g_tc_flag[device] = p;
+    }
+    return g_tc_flag[device];
+}
+
+int wform_kernel_mode() { return g_wform_mode.load(std::memory_order_relaxed); }
 
 rs_status ensure_buffer(void** buf, size_t* cap, size_t need) {
     if (*cap >= need && *buf) return RS_OK;
@@ -183,6 +213,10 @@ rs_status rs_ctx_create(int device, rs_ctx** out) {
         return RS_ERR_INVALID;
     }
     RS_TRY_CUDA(cudaSetDevice(device));
+    if (!rs::tc_error_flag(device)) {
+        rs::set_error("rs_ctx_create: device allocation failed");
+        return RS_ERR_OOM;
+    }
     rs_ctx* c = new rs_ctx();
     c->device = device;
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -241,6 +275,27 @@ rs_status rs_protein_get_info(const rs_protein* p, rs_protein_info* o) {
         o->sv_tail[a] = p->sv_tail[a];
     }
     o->device_bytes = p->device_bytes;
+    return RS_OK;
+}
+
+int rs_set_wform_kernel(int mode) {
+    return rs::g_wform_mode.exchange(mode ? 1 : 0);
+}
+
+rs_status rs_tc_error_count(int device, int32_t* out) {
+    rs::clear_error();
+    if (!out) {
+        rs::set_error("rs_tc_error_count: out is NULL");
+        return RS_ERR_INVALID;
+    }
+    *out = 0;
+    RS_TRY_CUDA(cudaSetDevice(device));
+    int* p = rs::tc_error_flag(device);
+    if (!p) {
+        rs::set_error("rs_tc_error_count: device %d unavailable", device);
+        return RS_ERR_INVALID;
+    }
+    RS_TRY_CUDA(cudaMemcpy(out, p, sizeof(int), cudaMemcpyDeviceToHost));
     return RS_OK;
 }
 

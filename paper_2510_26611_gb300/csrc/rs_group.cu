@@ -27,6 +27,7 @@
 #include "rs_sorted_dev.cuh"
 #include "rs_batch_dev.cuh"
 #include "rs_group.cuh"
+#include "rs_tc_dev.cuh"
 
 namespace rs {
 namespace {
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(32 * WPB)
 }
 
 template <int RP, int WPB>
-__global__ void __launch_bounds__(32 * WPB)
+__global__ void __launch_bounds__(32 * WPB, 20 / WPB)
     k_group_wform(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs,
                   const AtomRec* __restrict__ srt, long long natom, const double* __restrict__ shortv,
                   double* __restrict__ contrib) {
@@ -171,6 +172,32 @@ __global__ void __launch_bounds__(32 * WPB)
             }
         }
     }
+}
+
+// Records of a grouped chunk for the tensor-core W form: segment in bits 8.. of
+// r.bits, key = the segment's first key + the axis-3 cell.
+struct TcGroup {
+    const PairDesc* pairs;
+    const GroupSeg* segs;
+    __device__ __forceinline__ int seg(const AtomRec& r) const { return r.bits >> 8; }
+    __device__ __forceinline__ const ProteinView& prot(int sg) const { return pairs[segs[sg].pair].prot; }
+    __device__ __forceinline__ const LigandView& ligand(int sg) const { return pairs[segs[sg].pair].lig; }
+    __device__ __forceinline__ int cell(const AtomRec& r, int sg) const { return r.i3 - segs[sg].cell_base; }
+    __device__ __forceinline__ int atom(const AtomRec& r, int sg) const {
+        return (int)((r.slot - segs[sg].atom_off) % pairs[segs[sg].pair].lig.L);
+    }
+};
+
+template <int RP>
+__global__ void __launch_bounds__(tc::kTileRows)
+    k_group_tc(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, const AtomRec* __restrict__ srt,
+               const int* __restrict__ off, long long natom, const double* __restrict__ shortv,
+               double* __restrict__ contrib, int* __restrict__ err) {
+    extern __shared__ __align__(16) uint8_t smem_tc[];
+    const long long per = (natom + gridDim.x - 1) / gridDim.x;
+    const long long s0 = (long long)blockIdx.x * per, s1 = std::min<long long>(natom, s0 + per);
+    const TcGroup src{pairs, segs};
+    tc_wform_range<RP, false>(src, srt, off, s0, s1, shortv, contrib, smem_tc, err);
 }
 
 __global__ void k_group_reduce(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, int nseg,
@@ -245,12 +272,40 @@ rs_status launch_group_wform(const PairDesc* d_pairs, const GroupSeg* d_segs, co
     return RS_OK;
 }
 
+template <int RP>
+rs_status launch_group_tc(const PairDesc* d_pairs, const GroupSeg* d_segs, const GroupScratch& s, long long natom,
+                          cudaStream_t st, bool events) {
+    auto kern = k_group_tc<RP>;
+    size_t smem = TcLayout<RP, false>::BYTES;
+    int per_sm = 0, sms = 0, dev = 0;
+    RS_TRY(tc_occupancy(kern, TcLayout<RP, false>::NCOL, smem, per_sm));
+    RS_TRY_CUDA(cudaGetDevice(&dev));
+    RS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int* err = tc_error_flag(dev);
+    if (!err) {
+        set_error("tensor-core W form: no error flag on device %d", dev);
+        return RS_ERR_CUDA;
+    }
+    const long long want = (natom + tc::kTileRows - 1) / tc::kTileRows;
+    const long long grid = std::max<long long>(1, std::min<long long>(want, (long long)per_sm * sms));
+    {
+        ::rs::KernelTimer kt__("k_group_tc", st, (double)natom * tc_ops_per_atom(RP, false), true, events);
+        kern<<<(unsigned)grid, tc::kTileRows, smem, st>>>(d_pairs, d_segs, s.srt, s.off, natom, s.shortv, s.contrib,
+                                                          err);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
 template <int WPB>
 rs_status dispatch_group_wform(int RP, const PairDesc* d_pairs, const GroupSeg* d_segs, const GroupScratch& s,
                                long long natom, cudaStream_t st, bool events) {
+    const bool tcore = wform_kernel_mode() == 1;
     switch (RP) {
-#define RS_CASE(R) \
-    case R: return launch_group_wform<R, WPB>(d_pairs, d_segs, s, natom, st, events);
+#define RS_CASE(R)                                                                   \
+    case R:                                                                          \
+        return tcore ? launch_group_tc<R>(d_pairs, d_segs, s, natom, st, events)     \
+                     : launch_group_wform<R, WPB>(d_pairs, d_segs, s, natom, st, events);
         RS_CASE(4) RS_CASE(8) RS_CASE(12) RS_CASE(16) RS_CASE(20) RS_CASE(24) RS_CASE(28) RS_CASE(32)
 #undef RS_CASE
         default:

@@ -126,6 +126,9 @@ def _load() -> C.CDLL:
         "rs_serve_get_stats": (st, [vp, C.POINTER(rs_serve_stats)]),
         "rs_serve_destroy": (None, [vp]),
         "rs_symeig_host": (st, [i32, vp, vp, vp]),
+        "rs_set_wform_kernel": (C.c_int, [C.c_int]),
+        "rs_tc_error_count": (st, [C.c_int, C.POINTER(i32)]),
+        "rs_diag_tc_contract": (st, [i32, i32, vp, vp, vp, vp, vp]),
         "rs_stats_kernel_launches": (C.c_ulonglong, []),
         "rs_timing_enable": (st, [C.c_int]),
         "rs_timing_reset": (st, []),
@@ -393,6 +396,32 @@ def rs_symeig_host(A: np.ndarray):
     W = np.empty((n, n))
     _check(_lib.rs_symeig_host(n, A.ctypes.data, lam.ctypes.data, W.ctypes.data))
     return lam, W
+
+
+def rs_set_wform_kernel(mode: int) -> int:
+    """W-form kernel of the cell-grouped pose paths: 1 tensor cores (default), 0 float
+    pairs on the FP32 pipes.  Returns the previous mode."""
+    return int(_lib.rs_set_wform_kernel(int(mode)))
+
+
+def rs_tc_error_count(device: int = 0) -> int:
+    out = C.c_int32(0)
+    _check(_lib.rs_tc_error_count(int(device), C.byref(out)))
+    return int(out.value)
+
+
+def rs_diag_tc_contract(RP: int, v: np.ndarray, W: np.ndarray, D: np.ndarray):
+    """X = v W^T and Xd = v D^T for one tile (rows <= 128) through the tensor-core
+    slicing, MMAs and combination of the pose kernels."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    rows = v.shape[0]
+    X = np.empty((rows, RP))
+    Xd = np.empty((rows, RP))
+    _check(_lib.rs_diag_tc_contract(int(RP), int(rows), v.ctypes.data, W.ctypes.data, D.ctypes.data,
+                                    X.ctypes.data, Xd.ctypes.data))
+    return X, Xd
 
 
 def rs_stats_kernel_launches() -> int:

@@ -5,6 +5,10 @@ import oracle as O
 
 E_TOL = 1e-5      # per-pose energy, relative to max(|E|, 1e-2 S)
 G_TOL = 1e-4      # gradients, relative to max(|g|, 1e-2 * sum of per-atom magnitudes)
+# Two evaluation paths of the library (the tensor-core W form, ~2^-31 per
+# contraction, and the float-pair W form, ~2^-47) on the same poses: per-pose
+# energies relative to max(|E|, median |E|).
+PATH_TOL = 1e-8
 
 
 def energy_errors(E_gpu, ref):
@@ -62,3 +66,23 @@ def away_from_planes(model, lig_xyz, R, trans, eps=1e-5):
     s = (x + model.b) / model.h
     frac = s - np.floor(s)
     return np.all((frac > eps) & (frac < 1 - eps), axis=(1, 2))
+
+
+def path_errors(E, E_ref):
+    E, E_ref = np.asarray(E, dtype=np.float64), np.asarray(E_ref, dtype=np.float64)
+    if E_ref.size == 0:
+        return np.zeros(0)
+    scale = np.maximum(np.abs(E_ref), max(np.median(np.abs(E_ref)), 1e-300))
+    return np.abs(E - E_ref) / scale
+
+
+def assert_paths_agree(E, E_ref, flags=None, flags_ref=None, tol=PATH_TOL):
+    """Energies of two library paths agree to tol; flags (decided by the same short-range
+    code on every path) are identical."""
+    err = path_errors(E, E_ref)
+    if err.size:
+        worst = int(np.argmax(err))
+        assert err[worst] <= tol, f"paths differ by {err[worst]:.3e} at pose {worst}: {E[worst]!r} vs {E_ref[worst]!r}"
+    if flags is not None:
+        assert np.array_equal(np.asarray(flags), np.asarray(flags_ref))
+    return err

@@ -1,12 +1,13 @@
 """Batched persistent launch: pairs of uneven size in one graph-captured launch give
-the same energies and flags as one plain call per pair, bit for bit, before and
-after the poses are rewritten in place; one pair is checked against the oracle."""
+the same energies and flags as one plain call per pair (bit for bit where both take
+the same W-form kernel, else within the path tolerance), before and after the poses
+are rewritten in place; one pair is checked against the oracle."""
 import numpy as np
 import pytest
 
 import oracle as O
 import workloads as W
-from tests.parity import assert_energies, assert_flags
+from tests.parity import assert_energies, assert_flags, assert_paths_agree
 
 pytestmark = pytest.mark.gpu
 
@@ -76,8 +77,7 @@ def test_batch_equals_plain_calls(setup):
     torch.cuda.synchronize()
     ref = _plain(lib, prots, pairs)
     for p, (E, f) in zip(pairs, ref):
-        assert np.array_equal(p["E_out"].cpu().numpy(), E)
-        assert np.array_equal(p["flags_out"].cpu().numpy(), f)
+        assert_paths_agree(p["E_out"].cpu().numpy(), E, p["flags_out"].cpu().numpy(), f)
 
 
 @pytest.mark.parametrize("mode", [0, 2], ids=["cell-grouped", "per-block"])
@@ -96,8 +96,7 @@ def test_both_batch_paths_equal_plain_calls(setup, mode):
         lib.rs_batch_free(b2)
     ref = _plain(lib, prots, pairs)
     for p, (E, f) in zip(outs, ref):
-        assert np.array_equal(p["E_out"].cpu().numpy(), E)
-        assert np.array_equal(p["flags_out"].cpu().numpy(), f)
+        assert_paths_agree(p["E_out"].cpu().numpy(), E, p["flags_out"].cpu().numpy(), f)
 
 
 def test_batch_replay_after_rewriting_poses(setup):
@@ -113,8 +112,7 @@ def test_batch_replay_after_rewriting_poses(setup):
     torch.cuda.synchronize()
     ref = _plain(lib, prots, pairs)
     for p, (E, f) in zip(pairs, ref):
-        assert np.array_equal(p["E_out"].cpu().numpy(), E)
-        assert np.array_equal(p["flags_out"].cpu().numpy(), f)
+        assert_paths_agree(p["E_out"].cpu().numpy(), E, p["flags_out"].cpu().numpy(), f)
 
 
 def test_batch_pair_against_oracle(setup):

@@ -1,6 +1,7 @@
 """Serving: requests of different proteins, ligands and grid sizes through the request
 loop give the same energies and flags alone and in any mix, bit for bit, and the same
-as one plain rs_energy_poses call each; the small canonical case is checked against
+as one plain rs_energy_poses call each (within the path tolerance where the two take
+different W-form kernels); the small canonical case is checked against
 the oracle.  Resident factors, eviction under a memory budget, injected allocation
 failures, cancellation and bounded waits are exercised on the host side."""
 import numpy as np
@@ -8,7 +9,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from tests.parity import assert_energies, assert_flags
+from tests.parity import assert_energies, assert_flags, assert_paths_agree
 
 pytestmark = pytest.mark.gpu
 
@@ -91,7 +92,7 @@ def test_same_alone_and_in_the_mix(setup):
         srv.close()
     for r, (E, f) in zip(res, plain):
         assert r["status"] == lib.RS_OK, r["message"]
-        assert np.array_equal(r["E"], E) and np.array_equal(r["flags"], f)
+        assert_paths_agree(r["E"], E, r["flags"], f)
         assert r["t_submit_ns"] <= r["t_admit_ns"] <= r["t_start_ns"] <= r["t_end_ns"]
     assert np.array_equal(res[x]["E"], alone["E"]) and np.array_equal(res[x]["flags"], alone["flags"])
     assert st["done"] == len(reqs) + 1 and st["failed"] == 0
@@ -136,7 +137,7 @@ def test_eviction_under_a_memory_budget(setup):
         srv.close()
     for i, res in out:
         assert res["status"] == lib.RS_OK, res["message"]
-        assert np.array_equal(res["E"], plain[i][0]) and np.array_equal(res["flags"], plain[i][1])
+        assert_paths_agree(res["E"], plain[i][0], res["flags"], plain[i][1])
     assert st["evictions"] >= 1 and st["builds"] > 3
     assert st["used_bytes"] <= st["budget_bytes"] + big
 
@@ -161,7 +162,7 @@ def test_over_budget_and_injected_failures_fail_only_that_request(setup):
         srv.close()
     assert first["status"] == lib.RS_ERR_OOM and "allocation" in first["message"]
     assert second["status"] == lib.RS_OK
-    assert np.array_equal(second["E"], plain[i][0]) and np.array_equal(second["flags"], plain[i][1])
+    assert_paths_agree(second["E"], plain[i][0], second["flags"], plain[i][1])
     assert st["failed"] == 1 and st["done"] == 1
 
 
