@@ -366,6 +366,9 @@ int       rs_set_wform_kernel(int mode);
 /* Number of tensor-core tiles on `device` whose MMAs did not complete within the
  * kernel's bounded wait (their energies were set to NaN); 0 in normal operation. */
 rs_status rs_tc_error_count(int device, int32_t* out);
+/* Launch shape of the latest tensor-core W-form launch in the process: CTAs,
+ * dynamic shared memory per CTA (bytes) and CTAs per SM the occupancy allows. */
+rs_status rs_diag_tc_launch(int64_t* grid, int64_t* smem, int32_t* per_sm);
 /* Diagnostics of the tensor-core contraction alone: for one cell with W, D
  * (RP x RP, row-major FP64, host) and `rows` <= 128 rows v (rows x RP, host), computes
  * X = v W^T and Xd = v D^T (rows x RP, host) by the same slicing, MMAs and

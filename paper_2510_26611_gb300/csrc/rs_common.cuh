@@ -161,6 +161,8 @@ rs_status ensure_buffer(void** buf, size_t* cap, size_t need);
 int* tc_error_flag(int device);
 // W-form kernel of the cell-grouped pose paths: 1 tensor cores, 0 float pairs.
 int wform_kernel_mode();
+// Launch shape of the latest tensor-core W-form launch (diagnostics).
+void note_tc_launch(long long grid, size_t smem, int per_sm);
 // B images of the W form for the tensor-core path (rs_tc.cu): sizes for n cells of
 // padded rank RP, and the build from the W-form planes wt ([Wh|Wl|Dh|Dl][n][RP][RP]).
 size_t tc_bimage_bytes(int n, int RP);

@@ -52,6 +52,18 @@ int* tc_error_flag(int device) {
 
 int wform_kernel_mode() { return g_wform_mode.load(std::memory_order_relaxed); }
 
+namespace {
+std::atomic<long long> g_tc_grid{0};
+std::atomic<long long> g_tc_smem{0};
+std::atomic<int> g_tc_per_sm{0};
+}  // namespace
+
+void note_tc_launch(long long grid, size_t smem, int per_sm) {
+    g_tc_grid.store(grid, std::memory_order_relaxed);
+    g_tc_smem.store((long long)smem, std::memory_order_relaxed);
+    g_tc_per_sm.store(per_sm, std::memory_order_relaxed);
+}
+
 rs_status ensure_buffer(void** buf, size_t* cap, size_t need) {
     if (*cap >= need && *buf) return RS_OK;
     if (*buf) {
@@ -296,6 +308,18 @@ rs_status rs_tc_error_count(int device, int32_t* out) {
         return RS_ERR_INVALID;
     }
     RS_TRY_CUDA(cudaMemcpy(out, p, sizeof(int), cudaMemcpyDeviceToHost));
+    return RS_OK;
+}
+
+rs_status rs_diag_tc_launch(int64_t* grid, int64_t* smem, int32_t* per_sm) {
+    rs::clear_error();
+    if (!grid || !smem || !per_sm) {
+        rs::set_error("rs_diag_tc_launch: NULL argument");
+        return RS_ERR_INVALID;
+    }
+    *grid = rs::g_tc_grid.load();
+    *smem = rs::g_tc_smem.load();
+    *per_sm = rs::g_tc_per_sm.load();
     return RS_OK;
 }
 

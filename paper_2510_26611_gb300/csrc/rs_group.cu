@@ -288,6 +288,7 @@ rs_status launch_group_tc(const PairDesc* d_pairs, const GroupSeg* d_segs, const
     }
     const long long want = (natom + tc::kTileRows - 1) / tc::kTileRows;
     const long long grid = std::max<long long>(1, std::min<long long>(want, (long long)per_sm * sms));
+    note_tc_launch(grid, smem, per_sm);
     {
         ::rs::KernelTimer kt__("k_group_tc", st, (double)natom * tc_ops_per_atom(RP, false), true, events);
         kern<<<(unsigned)grid, tc::kTileRows, smem, st>>>(d_pairs, d_segs, s.srt, s.off, natom, s.shortv, s.contrib,

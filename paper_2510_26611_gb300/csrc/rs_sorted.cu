@@ -255,6 +255,7 @@ rs_status launch_sorted_tc(const EvalLaunch& a, const SortedScratch& s, long lon
     }
     const long long want = (M + tc::kTileRows - 1) / tc::kTileRows;
     const long long grid = std::max<long long>(1, std::min<long long>(want, (long long)per_sm * sms));
+    note_tc_launch(grid, smem, per_sm);
     const double work = (double)M * tc_ops_per_atom(RP, GRAD);
     {
         ::rs::KernelTimer kt__(GRAD ? "k_sorted_tc_grad" : "k_sorted_tc", st, work, true, a.events);

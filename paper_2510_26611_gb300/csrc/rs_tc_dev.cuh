@@ -83,13 +83,14 @@ __device__ __forceinline__ void tc_axis2_row(const ProteinView& P, const AtomRec
     }
 }
 
-// One contraction round of a tile: every thread writes its row (or a zero row), thread
-// 0 issues the MMAs, all wait (bounded).  Returns false on a timed-out wait (then
-// uniformly in the CTA).
+// One contraction round of a tile, in two halves so that independent work can run
+// between them.  tc_issue: every thread writes its row (or a zero row), thread 0
+// issues the MMAs and commits them to the barrier.  tc_wait: loads the next tile's
+// record (rn) while the MMAs run, then waits (bounded); returns false on a timed-out
+// wait (then uniformly in the CTA).
 template <int RP>
-__device__ __forceinline__ bool tc_round(uint8_t* sA, uint32_t a_saddr, uint32_t b_saddr, uint32_t tmem,
-                                         uint64_t* bar, uint32_t& phase, bool write, const dev::F2 (&x)[RP],
-                                         float& inv) {
+__device__ __forceinline__ void tc_issue(uint8_t* sA, uint32_t a_saddr, uint32_t b_saddr, uint32_t tmem,
+                                         uint64_t* bar, bool write, const dev::F2 (&x)[RP], float& inv) {
     const int tid = threadIdx.x;
     if (write) inv = tc::write_row<RP>(x, sA, tid);
     else tc::zero_row<RP>(sA, tid);
@@ -100,6 +101,12 @@ __device__ __forceinline__ bool tc_round(uint8_t* sA, uint32_t a_saddr, uint32_t
         tc::issue_products<RP>(tmem, a_saddr, b_saddr);
         tc::mma_commit(bar);
     }
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t& phase, const AtomRec* __restrict__ srt,
+                                        long long t1, long long s1, AtomRec& rn) {
+    const int tid = threadIdx.x;
+    if (t1 + tid < s1) rn = srt[t1 + tid];
     const bool ok = tc::mbar_wait_bounded(bar, phase);
     phase ^= 1u;
     const bool failed = __syncthreads_or(!ok);
@@ -137,6 +144,10 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
     const uint32_t a_saddr = tc::smem_u32(sA), b_saddr = tc::smem_u32(sB);
     int cur = -1;
     uint32_t phase = 0;
+    // software pipeline: the next tile's record is loaded during this tile's MMAs, and
+    // every global load a tile needs is issued before its MMA wait
+    AtomRec rn;
+    if (s0 + tid < s1) rn = srt[s0 + tid];
     for (long long t0 = s0; t0 < s1;) {
         const AtomRec r0 = srt[t0];
         const int key = r0.i3;
@@ -151,21 +162,47 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
             for (int e = tid; e < S::NP; e += tc::kTileRows) sCs[e] = __ldg(P.Wsc + cell * S::NP + e);
             cur = key;
         }
-        const long long s = t0 + tid;
-        const bool act = s < t1;
-        const AtomRec r = act ? srt[s] : r0;
+        const bool act = t0 + tid < t1;
+        const AtomRec r = act ? rn : r0;
         const bool in1 = r.bits & 1, in2 = r.bits & 2, in3 = r.bits & 4;
         (void)in1;
         (void)in2;
         (void)in3;
         const float f3 = r.f3;
-        const size_t o1 = (size_t)r.i1 * RP;
-        const float* V1h = P.Vt[0][0] + o1;
-        const float* V1l = P.Vt[0][1] + o1;
-        const float* V1dh = P.Vt[0][2] + o1;
-        const float* V1dl = P.Vt[0][3] + o1;
+        // short-range value (DRAM) and the axis-1 rows (L2), issued now
+        double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
+        if (act) {
+            if constexpr (GRAD) {
+                const double4 v = reinterpret_cast<const double4*>(shortv)[r.slot];
+                phs = v.x;
+                gs[0] = v.y;
+                gs[1] = v.z;
+                gs[2] = v.w;
+            } else {
+                phs = shortv[r.slot];
+            }
+        }
+        // axis-1 rows (L2): loaded now, interpolated while the MMAs run
+        F2 va[RP], dva[RP];
+        {
+            const size_t o1 = (size_t)r.i1 * RP;
+            const float4* v1h = (const float4*)(P.Vt[0][0] + o1);
+            const float4* v1l = (const float4*)(P.Vt[0][1] + o1);
+            const float4* v1dh = (const float4*)(P.Vt[0][2] + o1);
+            const float4* v1dl = (const float4*)(P.Vt[0][3] + o1);
+#pragma unroll
+            for (int c4 = 0; c4 < RP / 4; ++c4) {
+                const float4 a = __ldg(v1h + c4), b = __ldg(v1l + c4), c = __ldg(v1dh + c4), d = __ldg(v1dl + c4);
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                const float cv[4] = {c.x, c.y, c.z, c.w}, dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    va[4 * c4 + u] = F2{av[u], bv[u]};
+                    dva[4 * c4 + u] = F2{cv[u], dv[u]};
+                }
+            }
+        }
         F2 phi{0.f, 0.f}, g1{0.f, 0.f}, g2{0.f, 0.f}, g3{0.f, 0.f};
-        F2 va[GRAD ? RP : 1];
         bool ok;
         // round 1: X = v2 W^T, X' = v2 D^T
         {
@@ -173,8 +210,14 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
             {
                 F2 v2[RP];
                 tc_axis2_row<RP>(P, r, false, v2);
-                ok = tc_round<RP>(sA, a_saddr, b_saddr, tmem, bar, phase, act, v2, inv);
+                tc_issue<RP>(sA, a_saddr, b_saddr, tmem, bar, act, v2, inv);
             }
+#pragma unroll
+            for (int a = 0; a < RP; ++a) {
+                va[a] = dev::df_lerp(va[a], dva[a], r.f1);
+                if (!in1) dva[a] = F2{0.f, 0.f};
+            }
+            ok = tc_wait(bar, phase, srt, t1, s1, rn);
             if (ok) {
 #pragma unroll
                 for (int ch = 0; ch < S::NP / 16; ++ch) {
@@ -187,15 +230,11 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
                             const F2 X = tc::combine(x0[2 * q], x1[2 * q], x2[2 * q], __fmul_rn(inv, sCs[2 * a]));
                             const F2 Xd = tc::combine(x0[2 * q + 1], x1[2 * q + 1], x2[2 * q + 1],
                                                       __fmul_rn(inv, sCs[2 * a + 1]));
-                            const float vdh = __ldg(V1dh + a), vdl = __ldg(V1dl + a);
-                            const F2 v1 = dev::df_lerp(F2{__ldg(V1h + a), __ldg(V1l + a)}, F2{vdh, vdl}, r.f1);
                             const F2 u = dev::df_lerp(X, Xd, f3);
-                            dev::df_fma_acc(phi, v1, u);
+                            dev::df_fma_acc(phi, va[a], u);
                             if constexpr (GRAD) {
-                                va[a] = v1;
-                                const F2 dva = in1 ? F2{vdh, vdl} : F2{0.f, 0.f};
-                                dev::df_fma_acc(g1, dva, u);
-                                if (in3) dev::df_fma_acc(g3, v1, Xd);
+                                dev::df_fma_acc(g1, dva[a], u);
+                                if (in3) dev::df_fma_acc(g3, va[a], Xd);
                             }
                         }
                     }
@@ -211,8 +250,9 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
                 {
                     F2 dv2[RP];
                     tc_axis2_row<RP>(P, r, true, dv2);
-                    ok = tc_round<RP>(sA, a_saddr, b_saddr, tmem, bar, phase, act && in2, dv2, inv);
+                    tc_issue<RP>(sA, a_saddr, b_saddr, tmem, bar, act && in2, dv2, inv);
                 }
+                ok = tc_wait(bar, phase, srt, t1, s1, rn);
                 if (ok) {
 #pragma unroll
                     for (int ch = 0; ch < S::NP / 16; ++ch) {
@@ -241,16 +281,6 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
         }
         if (act) {
             const int j = src.atom(r, sg);
-            double phs, gs[3] = {0.0, 0.0, 0.0};
-            if constexpr (GRAD) {
-                const double4 v = reinterpret_cast<const double4*>(shortv)[r.slot];
-                phs = v.x;
-                gs[0] = v.y;
-                gs[1] = v.z;
-                gs[2] = v.w;
-            } else {
-                phs = shortv[r.slot];
-            }
             const float ry[3] = {r.ry0, r.ry1, r.ry2};
             atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, src.ligand(sg).q64[j], ry,
                                contrib + (size_t)r.slot * NC);
@@ -263,23 +293,37 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
     if (warp == 0) tc::tmem_dealloc(tmem, Lay::NCOL);
 }
 
-// Dynamic shared memory for a tensor-core W-form kernel such that no more CTAs fit on
-// an SM than its TMEM holds (512 columns / ncol): an allocation beyond that would
-// wait for a resident CTA to finish.  smem grows in 1 KB steps until the occupancy
-// is within the cap; per_sm returns the occupancy.
+// Dynamic shared memory and CTAs per SM for a tensor-core W-form kernel.  No more
+// CTAs may fit on an SM than its TMEM holds (512 columns / ncol): an allocation
+// beyond that would wait for a resident CTA to finish.  The count comes from the
+// device's shared-memory and register limits (the runtime's occupancy query
+// reports one CTA per SM for kernels that allocate TMEM); smem is padded until the
+// shared-memory limit alone caps the residency at the TMEM share.
 template <class K>
 rs_status tc_occupancy(K kern, uint32_t ncol, size_t& smem, int& per_sm) {
     const int cap = 512 / (int)ncol;
-    RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    for (;;) {
-        RS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tc::kTileRows, smem));
-        if (per_sm <= cap || smem >= 227 * 1024) break;
-        smem += 1024;
-    }
-    if (per_sm < 1 || per_sm > cap) {
-        set_error("tensor-core W form: occupancy %d outside [1, %d]", per_sm, cap);
+    int dev = 0, sm_smem = 0, reserved = 0, sm_regs = 0, sm_threads = 0;
+    RS_TRY_CUDA(cudaGetDevice(&dev));
+    RS_TRY_CUDA(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    RS_TRY_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    RS_TRY_CUDA(cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    RS_TRY_CUDA(cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+    cudaFuncAttributes fa{};
+    RS_TRY_CUDA(cudaFuncGetAttributes(&fa, kern));
+    const size_t per_cta = (size_t)fa.sharedSizeBytes + (size_t)reserved;
+    auto by_smem = [&](size_t dyn) { return (int)((size_t)sm_smem / (dyn + per_cta)); };
+    while (by_smem(smem) > cap) smem += 1024;
+    const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = sm_regs / (regs_per_warp * (tc::kTileRows / 32));
+    per_sm = std::min(std::min(by_smem(smem), by_regs), sm_threads / tc::kTileRows);
+    if (per_sm < 1 || smem > 227 * 1024) {
+        set_error("tensor-core W form: no residency (smem %zu, regs %d)", smem, fa.numRegs);
         return RS_ERR_UNSUPPORTED;
     }
+    RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the whole unified L1/shared array as shared memory, so per_sm CTAs fit
+    RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
     return RS_OK;
 }
 

@@ -129,6 +129,7 @@ def _load() -> C.CDLL:
         "rs_set_wform_kernel": (C.c_int, [C.c_int]),
         "rs_tc_error_count": (st, [C.c_int, C.POINTER(i32)]),
         "rs_diag_tc_contract": (st, [i32, i32, vp, vp, vp, vp, vp]),
+        "rs_diag_tc_launch": (st, [C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
         "rs_stats_kernel_launches": (C.c_ulonglong, []),
         "rs_timing_enable": (st, [C.c_int]),
         "rs_timing_reset": (st, []),
@@ -408,6 +409,14 @@ def rs_tc_error_count(device: int = 0) -> int:
     out = C.c_int32(0)
     _check(_lib.rs_tc_error_count(int(device), C.byref(out)))
     return int(out.value)
+
+
+def rs_diag_tc_launch() -> dict:
+    """Launch shape of the latest tensor-core W-form launch: CTAs, shared memory per
+    CTA and CTAs per SM."""
+    g, m, p = C.c_int64(0), C.c_int64(0), C.c_int32(0)
+    _check(_lib.rs_diag_tc_launch(C.byref(g), C.byref(m), C.byref(p)))
+    return {"grid": int(g.value), "smem": int(m.value), "per_sm": int(p.value)}
 
 
 def rs_diag_tc_contract(RP: int, v: np.ndarray, W: np.ndarray, D: np.ndarray):

@@ -103,6 +103,19 @@ def test_sorted_energies_tc_vs_pairs_and_oracle(L, protein):
     assert L.rs_tc_error_count(0) == 0
 
 
+def test_sorted_tc_launch_fills_tmem(L, protein):
+    # rank 20: three accumulators of 48 columns -> 256 TMEM columns per CTA, so two
+    # CTAs per SM and a grid of two CTAs per SM for a large call
+    import torch
+    w, m, prot, _ = protein
+    prot.energies(w.lig_xyz, w.lig_q, w.quat, w.trans)
+    info = L.rs_diag_tc_launch()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    print("tensor-core launch:", info)
+    assert info["per_sm"] == 2
+    assert info["grid"] == 2 * sms
+
+
 def test_sorted_gradients_tc_vs_pairs_and_oracle(L, protein):
     w, m, prot, _ = protein
     P = 4000
