@@ -17,6 +17,7 @@
 // Per-atom and per-pose arithmetic is that of the single-pair path, in the same
 // order, so every pair's results equal rs_energy_poses bit for bit.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <vector>
 
@@ -70,53 +71,60 @@ __global__ void __launch_bounds__(32 * WPB)
                   AtomRec* __restrict__ rec, double* __restrict__ shortv, int* __restrict__ count) {
     __shared__ NearQueue<false> queues[WPB];
     __shared__ int lane_pair[WPB][32];
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in_range = g < natom;
-    int s = 0, q = 0, j = 0;
-    if (in_range) {
-        s = seg_of_atom(segs, nseg, g);
-        const int L = pairs[segs[s].pair].lig.L;
-        const long long local = g - segs[s].atom_off;
-        q = segs[s].pose_off + (int)(local / L);
-        j = (int)(local % L);
+    // persistent warps: warp w takes the 32-atom chunks w, w + W, ...
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long nchunk = (natom + 31) / 32;
+    const long long nw = (long long)gridDim.x * WPB;
+    for (long long c = (long long)blockIdx.x * WPB + wib; c < nchunk; c += nw) {
+        const long long g = c * 32 + lane;
+        const bool in_range = g < natom;
+        int s = 0, q = 0, j = 0;
+        if (in_range) {
+            s = seg_of_atom(segs, nseg, g);
+            const int L = pairs[segs[s].pair].lig.L;
+            const long long local = g - segs[s].atom_off;
+            q = segs[s].pose_off + (int)(local / L);
+            j = (int)(local % L);
+        }
+        const GroupSeg sg = segs[s];
+        const PairDesc& pd = pairs[sg.pair];
+        float ry[3] = {0.f, 0.f, 0.f};
+        F2 x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        double x64[3] = {0.0, 0.0, 0.0};
+        int ci[3] = {0, 0, 0};
+        float cf[3] = {0.f, 0.f, 0.f};
+        bool ins[3] = {true, true, true};
+        if (in_range) atom_geometry(pd.prot, pd.lig, ps[q], j, ry, x, x64, ci, cf, ins);
+        F2 php{0.f, 0.f}, gp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        int clash = 0;
+        // the lanes of a warp may belong to different pairs: each near pair is evaluated
+        // against its owner's protein
+        int* lp = lane_pair[wib];
+        __syncwarp();
+        lp[lane] = sg.pair;
+        __syncwarp();
+        short_coop_with<false>([&](int l) -> const ProteinView& { return pairs[lp[l]].prot; }, in_range, x, x64,
+                               queues[wib], php, gp, clash);
+        if (!in_range) continue;
+        AtomRec r;
+        r.slot = (int)g;
+        int fl = clash ? RS_FLAG_CLASH : 0;
+        if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
+        if (fl) atomicOr(&pflag[q], fl);
+        shortv[g] = dev::df_to(php);
+        r.i1 = ci[0];
+        r.i2 = ci[1];
+        r.i3 = sg.cell_base + ci[2];
+        r.f1 = cf[0];
+        r.f2 = cf[1];
+        r.f3 = cf[2];
+        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0) | (s << 8);
+        r.ry0 = ry[0];
+        r.ry1 = ry[1];
+        r.ry2 = ry[2];
+        r.rank = atomicAdd(&count[r.i3], 1);
+        rec[g] = r;
     }
-    const GroupSeg sg = segs[s];
-    const PairDesc& pd = pairs[sg.pair];
-    float ry[3] = {0.f, 0.f, 0.f};
-    F2 x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    double x64[3] = {0.0, 0.0, 0.0};
-    int ci[3] = {0, 0, 0};
-    float cf[3] = {0.f, 0.f, 0.f};
-    bool ins[3] = {true, true, true};
-    if (in_range) atom_geometry(pd.prot, pd.lig, ps[q], j, ry, x, x64, ci, cf, ins);
-    F2 php{0.f, 0.f}, gp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    int clash = 0;
-    // the lanes of a warp may belong to different pairs: each near pair is evaluated
-    // against its owner's protein
-    int* lp = lane_pair[threadIdx.x >> 5];
-    lp[threadIdx.x & 31] = sg.pair;
-    __syncwarp();
-    short_coop_with<false>([&](int l) -> const ProteinView& { return pairs[lp[l]].prot; }, in_range, x, x64,
-                           queues[threadIdx.x >> 5], php, gp, clash);
-    if (!in_range) return;
-    AtomRec r;
-    r.slot = (int)g;
-    int fl = clash ? RS_FLAG_CLASH : 0;
-    if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
-    if (fl) atomicOr(&pflag[q], fl);
-    shortv[g] = dev::df_to(php);
-    r.i1 = ci[0];
-    r.i2 = ci[1];
-    r.i3 = sg.cell_base + ci[2];
-    r.f1 = cf[0];
-    r.f2 = cf[1];
-    r.f3 = cf[2];
-    r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0) | (s << 8);
-    r.ry0 = ry[0];
-    r.ry1 = ry[1];
-    r.ry2 = ry[2];
-    r.rank = atomicAdd(&count[r.i3], 1);
-    rec[g] = r;
 }
 
 template <int RP, int WPB>
@@ -189,7 +197,7 @@ struct TcGroup {
 };
 
 template <int RP>
-__global__ void __launch_bounds__(tc::kTileRows)
+__global__ void __launch_bounds__(tc::kTileRows, 4)
     k_group_tc(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, const AtomRec* __restrict__ srt,
                const int* __restrict__ off, long long natom, const double* __restrict__ shortv,
                double* __restrict__ contrib, int* __restrict__ err) {
@@ -381,9 +389,20 @@ rs_status group_launch(const GroupPlan& G, const PairDesc* d_pairs, const GroupS
             k_group_poses<<<(ch.npose + 127) / 128, 128, 0, st>>>(d_pairs, segs, nseg, ch.npose, s.ps, s.pflag);
         }
         {
+            static std::atomic<int> resident{0};  // CTAs that fit on the device at once
+            int res = resident.load(std::memory_order_relaxed);
+            if (res == 0) {
+                int per_sm = 0, sms = 0, dev = 0;
+                RS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_atoms<4>, 128, 0));
+                RS_TRY_CUDA(cudaGetDevice(&dev));
+                RS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+                res = std::max(per_sm, 1) * sms;
+                resident.store(res, std::memory_order_relaxed);
+            }
+            const long long grid = std::max<long long>(1, std::min<long long>((ch.natom + 127) / 128, res));
             ::rs::KernelTimer kt__("k_group_atoms", st, 0.0, true, events);
-            k_group_atoms<4><<<(unsigned)((ch.natom + 127) / 128), 128, 0, st>>>(
-                d_pairs, segs, nseg, ch.natom, s.ps, s.pflag, s.rec, s.shortv, s.count);
+            k_group_atoms<4><<<(unsigned)grid, 128, 0, st>>>(d_pairs, segs, nseg, ch.natom, s.ps, s.pflag, s.rec,
+                                                            s.shortv, s.count);
         }
         {
             ::rs::KernelTimer kt__("k_cell_scan", st, 0.0, false, events);

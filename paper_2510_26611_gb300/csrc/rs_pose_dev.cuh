@@ -183,6 +183,7 @@ struct NearQueue {
     int rs[9][32];      // first candidate of each neighbourhood row
     int rp[10][32];     // prefix of the rows' lengths (rp[9] = the lane's total)
     int lstart[32];     // prefix of the lanes' totals over the warp
+    int seg0[32], seg1[32];  // per owner lane: its entries [seg0, seg1) of a processed batch
 };
 
 // Short range and vdW decision for the 32 atoms of a warp (one per lane).  The
@@ -233,8 +234,14 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
     int qn = 0;  // entries in the queue (the same in every lane)
     auto process = [&](int m) {
         __syncwarp();
+        Q.seg0[lane] = 0;
+        Q.seg1[lane] = 0;
+        __syncwarp();
         if (lane < m) {
             const int o = Q.owner[lane];
+            // a batch holds its entries in list order, so each owner's are contiguous
+            if (lane == 0 || Q.owner[lane - 1] != o) Q.seg0[o] = lane;
+            if (lane == m - 1 || Q.owner[lane + 1] != o) Q.seg1[o] = lane + 1;
             const F2 xo[3] = {F2{Q.x[0][o].x, Q.x[0][o].y}, F2{Q.x[1][o].x, Q.x[1][o].y},
                               F2{Q.x[2][o].x, Q.x[2][o].y}};
             const double xo64[3] = {Q.x64[0][o], Q.x64[1][o], Q.x64[2][o]};
@@ -250,8 +257,7 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
         }
         __syncwarp();
         if (active)
-            for (int e = 0; e < m; ++e) {
-                if (Q.owner[e] != lane) continue;
+            for (int e = Q.seg0[lane], e1 = Q.seg1[lane]; e < e1; ++e) {
                 const int out = Q.bits[e];
                 if (out & 1) clash = 1;
                 if (out & 2) {

@@ -19,6 +19,7 @@
 // same order, so both paths give the same bits; the order of atoms within a cell
 // (set by atomics) never enters any arithmetic.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 
 #include "rs_common.cuh"
@@ -46,7 +47,10 @@ __global__ void k_sorted_poses(ProteinView P, const double* __restrict__ rot,
 }
 
 // One thread per pose-atom; the short range of a warp's 32 atoms is taken
-// together (short_coop), so the FP64 work of near pairs keeps all lanes busy.
+// together (short_coop), so the pair work of near pairs keeps all lanes busy.  Warps
+// are persistent: warp w takes the 32-atom chunks w, w + W, ... (W warps in the
+// grid), so a warp whose atoms had few neighbours moves on at once instead of
+// idling until its CTA's slowest warp is done.
 template <bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     k_sorted_atoms(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
@@ -54,51 +58,57 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
                    int* __restrict__ count) {
     __shared__ NearQueue<GRAD> queues[kWarpsPerBlock];
     const int L = lig.L;
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in_range = g < (long long)PC * L;
-    const int pl = in_range ? (int)(g / L) : 0;
-    const int j = in_range ? (int)(g - (long long)pl * L) : 0;
-    const bool valid = in_range && ps[pl].valid;
-    float ry[3] = {0.f, 0.f, 0.f};
-    F2 x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    double x64[3] = {0.0, 0.0, 0.0};
-    int ci[3] = {0, 0, 0};
-    float cf[3] = {0.f, 0.f, 0.f};
-    bool ins[3] = {true, true, true};
-    if (valid) atom_geometry(P, lig, ps[pl], j, ry, x, x64, ci, cf, ins);
-    F2 php{0.f, 0.f}, gp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    int clash = 0;
-    short_coop<GRAD>(P, valid, x, x64, queues[threadIdx.x >> 5], php, gp, clash);
-    if (!in_range) return;
-    AtomRec r;
-    r.slot = (int)g;
-    if (!valid) {
-        r.i3 = P.n - 1;
-        r.rank = atomicAdd(&count[P.n - 1], 1);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long M = (long long)PC * L;
+    const long long nchunk = (M + 31) / 32;
+    const long long nw = (long long)gridDim.x * kWarpsPerBlock;
+    for (long long c = (long long)blockIdx.x * kWarpsPerBlock + wib; c < nchunk; c += nw) {
+        const long long g = c * 32 + lane;
+        const bool in_range = g < M;
+        const int pl = in_range ? (int)(g / L) : 0;
+        const int j = in_range ? (int)(g - (long long)pl * L) : 0;
+        const bool valid = in_range && ps[pl].valid;
+        float ry[3] = {0.f, 0.f, 0.f};
+        F2 x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        double x64[3] = {0.0, 0.0, 0.0};
+        int ci[3] = {0, 0, 0};
+        float cf[3] = {0.f, 0.f, 0.f};
+        bool ins[3] = {true, true, true};
+        if (valid) atom_geometry(P, lig, ps[pl], j, ry, x, x64, ci, cf, ins);
+        F2 php{0.f, 0.f}, gp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        int clash = 0;
+        short_coop<GRAD>(P, valid, x, x64, queues[wib], php, gp, clash);
+        if (!in_range) continue;
+        AtomRec r;
+        r.slot = (int)g;
+        if (!valid) {
+            r.i3 = P.n - 1;
+            r.rank = atomicAdd(&count[P.n - 1], 1);
+            rec[g] = r;
+            continue;
+        }
+        int fl = clash ? RS_FLAG_CLASH : 0;
+        if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
+        if (fl) atomicOr(&pflag[pl], fl);
+        if constexpr (GRAD) {
+            double4 v = make_double4(dev::df_to(php), dev::df_to(gp[0]), dev::df_to(gp[1]), dev::df_to(gp[2]));
+            reinterpret_cast<double4*>(shortv)[g] = v;
+        } else {
+            shortv[g] = dev::df_to(php);
+        }
+        r.i1 = ci[0];
+        r.i2 = ci[1];
+        r.i3 = ci[2];
+        r.f1 = cf[0];
+        r.f2 = cf[1];
+        r.f3 = cf[2];
+        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0);
+        r.ry0 = ry[0];
+        r.ry1 = ry[1];
+        r.ry2 = ry[2];
+        r.rank = atomicAdd(&count[ci[2]], 1);
         rec[g] = r;
-        return;
     }
-    int fl = clash ? RS_FLAG_CLASH : 0;
-    if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
-    if (fl) atomicOr(&pflag[pl], fl);
-    if constexpr (GRAD) {
-        double4 v = make_double4(dev::df_to(php), dev::df_to(gp[0]), dev::df_to(gp[1]), dev::df_to(gp[2]));
-        reinterpret_cast<double4*>(shortv)[g] = v;
-    } else {
-        shortv[g] = dev::df_to(php);
-    }
-    r.i1 = ci[0];
-    r.i2 = ci[1];
-    r.i3 = ci[2];
-    r.f1 = cf[0];
-    r.f2 = cf[1];
-    r.f3 = cf[2];
-    r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0);
-    r.ry0 = ry[0];
-    r.ry1 = ry[1];
-    r.ry2 = ry[2];
-    r.rank = atomicAdd(&count[ci[2]], 1);
-    rec[g] = r;
 }
 
 template <int RP, bool GRAD>
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, GRAD ? 3 : 5)
 // Tensor-core W form (rs_tc_dev.cuh): CTA b walks a contiguous run of the sorted
 // records of evaluated poses.
 template <int RP, bool GRAD>
-__global__ void __launch_bounds__(tc::kTileRows)
+__global__ void __launch_bounds__(tc::kTileRows, GRAD ? 3 : 4)
     k_sorted_tc(const __grid_constant__ ProteinView P, const __grid_constant__ LigandView lig,
                 const AtomRec* __restrict__ srt, const int* __restrict__ off, const double* __restrict__ shortv,
                 double* __restrict__ contrib, int* __restrict__ err) {
@@ -280,6 +290,29 @@ rs_status dispatch_sorted_wform(const EvalLaunch& a, const SortedScratch& s, lon
     }
 }
 
+// CTAs of the persistent atoms kernel: as many as fit on the device at once (at most
+// one per 32-atom chunk of warps).
+template <bool GRAD>
+unsigned atoms_grid(long long M) {
+    static std::atomic<int> cached{0};  // CTAs per SM x SMs, computed once per instance
+    int resident = cached.load(std::memory_order_relaxed);
+    if (resident == 0) {
+        int per_sm = 0, sms = 0, dev = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sorted_atoms<GRAD>, 32 * kWarpsPerBlock, 0) !=
+                cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 4;
+            sms = 152;
+        }
+        resident = std::max(per_sm, 1) * std::max(sms, 1);
+        cached.store(resident, std::memory_order_relaxed);
+    }
+    const long long need = (M + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock);
+    return (unsigned)std::max<long long>(1, std::min<long long>(need, resident));
+}
+
 template <bool GRAD>
 rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
     const int L = a.lig.L, n = a.prot.n;
@@ -300,10 +333,10 @@ rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
                                                               s.pflag);
         }
         {
+            const unsigned grid = atoms_grid<GRAD>(M);
             ::rs::KernelTimer kt__(GRAD ? "k_sorted_atoms_grad" : "k_sorted_atoms", st, 0.0, true, a.events);
-            k_sorted_atoms<GRAD><<<(unsigned)((M + 32 * kWarpsPerBlock - 1) / (32 * kWarpsPerBlock)),
-                                   32 * kWarpsPerBlock, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag, s.rec,
-                                                                 s.shortv, s.count);
+            k_sorted_atoms<GRAD><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag, s.rec,
+                                                                        s.shortv, s.count);
         }
         {
             ::rs::KernelTimer kt__("k_cell_scan", st, 0.0, false, a.events);

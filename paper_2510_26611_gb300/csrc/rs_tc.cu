@@ -96,15 +96,14 @@ __global__ void __launch_bounds__(tc::kTileRows)
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
         for (int ch = 0; ch < S::NP / 16; ++ch) {
-            float x0[16], x1[16], x2[16];
-            tc::tmem_ld16x3(tl + ch * 16, tl + S::NP + ch * 16, tl + 2 * S::NP + ch * 16, x0, x1, x2);
+            float x0[16], x1[16];
+            tc::tmem_ld16x2(tl + ch * 16, tl + S::NP + ch * 16, x0, x1);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int a = ch * 8 + q;
                 if (a < RP && tid < rows) {
-                    const dev::F2 w = tc::combine(x0[2 * q], x1[2 * q], x2[2 * q], __fmul_rn(inv, csc[2 * a]));
-                    const dev::F2 d =
-                        tc::combine(x0[2 * q + 1], x1[2 * q + 1], x2[2 * q + 1], __fmul_rn(inv, csc[2 * a + 1]));
+                    const dev::F2 w = tc::combine(x0[2 * q], x1[2 * q], __fmul_rn(inv, csc[2 * a]));
+                    const dev::F2 d = tc::combine(x0[2 * q + 1], x1[2 * q + 1], __fmul_rn(inv, csc[2 * a + 1]));
                     X[(size_t)tid * RP + a] = dev::df_to(w);
                     Xd[(size_t)tid * RP + a] = dev::df_to(d);
                 }

@@ -10,14 +10,15 @@
 // power of two 2^(5-E) so that |x| < 32, then written as kSlices = 5 integers
 // d_0 + d_1 2^-8 + d_2 2^-16 + d_3 2^-24 + d_4 2^-32 (|d_0| <= 32, |d_j| <= 128, each
 // exact in BF16, stored with its weight 2^-8j).  A product of two rows is the sum of
-// the slice products (i, j); those with i + j <= 5 are formed, in three FP32
+// the slice products (i, j); those with i + j <= 4 are formed, in two FP32
 // accumulators of TMEM:
 //   diagonals 0 and 1: multiples of 2^-8 whose K-sums stay below 2^15 -> exact;
-//   diagonal 2:        multiples of 2^-16 below 2^4                  -> exact;
-//   diagonals 3 to 5:  terms ~2^-22 below the top; FP32 rounding there is ~2^-46.
-// The three are combined with error-free sums into a float pair.  The result
-// carries ~2^-37 of the row and column maxima (slicing; the dropped products with
-// i + j >= 6 are smaller); the CUDA-core pair arithmetic carries ~2^-47.
+//   diagonals 2 to 4:  terms ~2^-14 below the top, rounded in FP32.
+// The two are combined with an error-free sum into a float pair.  The result
+// carries ~2^-33 of K times the row and column maxima (the second accumulator's
+// rounding and the dropped products with i + j >= 5, measured on an FP32-accumulated
+// CPU emulation of the scheme); the CUDA-core pair arithmetic carries ~2^-47.  Two
+// accumulators keep a tile within 128 TMEM columns, so four CTAs share an SM.
 #pragma once
 
 #include <cstdint>
@@ -230,22 +231,22 @@ __device__ __forceinline__ void zero_row(uint8_t* tile, int row) {
                 make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Accumulators of one contraction in TMEM: columns [0, NP) diagonals 0-1, [NP, 2NP)
-// diagonal 2, [2NP, 3NP) diagonals 3-5.
-constexpr int kAccs = 3;
+// Accumulators of one contraction in TMEM: columns [0, NP) diagonals 0-1 (exact),
+// [NP, 2NP) diagonals 2-4.
+constexpr int kAccs = 2;
 
-// The nineteen slice products (i, j) with i + j <= 5, in a fixed order, each into the
+// The fifteen slice products (i, j) with i + j <= 4, in a fixed order, each into the
 // accumulator of its diagonal (the first product of an accumulator overwrites it).
 template <int RP>
 __device__ __forceinline__ void issue_products(uint32_t tmem_d, uint32_t a_saddr, uint32_t b_saddr) {
     using S = Shape<RP>;
     constexpr uint32_t idesc = idesc_bf16_f32(kTileRows, S::NP);
-    constexpr int kI[19] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 1, 2, 3, 4};
-    constexpr int kJ[19] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 4, 3, 2, 1};
+    constexpr int kI[15] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
+    constexpr int kJ[15] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
 #pragma unroll
-    for (int p = 0; p < 19; ++p) {
-        const int acc = p < 3 ? 0 : p < 6 ? 1 : 2;
-        const bool first = p == 0 || p == 3 || p == 6;
+    for (int p = 0; p < 15; ++p) {
+        const int acc = p < 3 ? 0 : 1;
+        const bool first = p == 0 || p == 3;
         const uint32_t d = tmem_d + (uint32_t)(acc * S::NP);
 #pragma unroll
         for (int ks = 0; ks < S::KP / 16; ++ks) {
@@ -256,41 +257,35 @@ __device__ __forceinline__ void issue_products(uint32_t tmem_d, uint32_t a_saddr
     }
 }
 
-// Pair value of one output column: (acc0 + acc1 + acc2) * scale, acc0 + acc1 taken
-// error-free, acc2 (the small diagonals) folded into the low word (scale is a
-// power of two).
-__device__ __forceinline__ dev::F2 combine(float acc0, float acc1, float acc2, float scale) {
+// Pair value of one output column: (acc0 + acc1) * scale, the sum taken error-free
+// (scale is a power of two).
+__device__ __forceinline__ dev::F2 combine(float acc0, float acc1, float scale) {
     float s, e;
     dev::two_sum(acc0, acc1, s, e);
-    const dev::F2 r = dev::fast_two_sum(s, __fadd_rn(e, acc2));
-    return dev::F2{__fmul_rn(r.h, scale), __fmul_rn(r.l, scale)};
+    return dev::F2{__fmul_rn(s, scale), __fmul_rn(e, scale)};
 }
 
-// Three 16-column TMEM loads (one per accumulator) and the wait for them.
-__device__ __forceinline__ void tmem_ld16x3(uint32_t ta, uint32_t tb, uint32_t tc_, float (&a)[16], float (&b)[16],
-                                            float (&c)[16]) {
-    uint32_t x[48];
+// Two 16-column TMEM loads (32 lanes x 32 bits: thread t reads lane base + t, one load
+// per accumulator) and the wait for them, in one statement so no use of the values
+// precedes the wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&a)[16], float (&b)[16]) {
+    uint32_t x[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%48];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
-        "[%49];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, "
-        "[%50];\n\t"
+        "[%33];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7]),
           "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]), "=r"(x[14]), "=r"(x[15]),
           "=r"(x[16]), "=r"(x[17]), "=r"(x[18]), "=r"(x[19]), "=r"(x[20]), "=r"(x[21]), "=r"(x[22]),
           "=r"(x[23]), "=r"(x[24]), "=r"(x[25]), "=r"(x[26]), "=r"(x[27]), "=r"(x[28]), "=r"(x[29]),
-          "=r"(x[30]), "=r"(x[31]), "=r"(x[32]), "=r"(x[33]), "=r"(x[34]), "=r"(x[35]), "=r"(x[36]),
-          "=r"(x[37]), "=r"(x[38]), "=r"(x[39]), "=r"(x[40]), "=r"(x[41]), "=r"(x[42]), "=r"(x[43]),
-          "=r"(x[44]), "=r"(x[45]), "=r"(x[46]), "=r"(x[47])
-        : "r"(ta), "r"(tb), "r"(tc_)
+          "=r"(x[30]), "=r"(x[31])
+        : "r"(ta), "r"(tb)
         : "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         a[i] = __uint_as_float(x[i]);
         b[i] = __uint_as_float(x[16 + i]);
-        c[i] = __uint_as_float(x[32 + i]);
     }
 }
 

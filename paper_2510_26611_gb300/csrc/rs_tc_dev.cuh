@@ -182,26 +182,8 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
                 phs = shortv[r.slot];
             }
         }
-        // axis-1 rows (L2): loaded now, interpolated while the MMAs run
-        F2 va[RP], dva[RP];
-        {
-            const size_t o1 = (size_t)r.i1 * RP;
-            const float4* v1h = (const float4*)(P.Vt[0][0] + o1);
-            const float4* v1l = (const float4*)(P.Vt[0][1] + o1);
-            const float4* v1dh = (const float4*)(P.Vt[0][2] + o1);
-            const float4* v1dl = (const float4*)(P.Vt[0][3] + o1);
-#pragma unroll
-            for (int c4 = 0; c4 < RP / 4; ++c4) {
-                const float4 a = __ldg(v1h + c4), b = __ldg(v1l + c4), c = __ldg(v1dh + c4), d = __ldg(v1dl + c4);
-                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-                const float cv[4] = {c.x, c.y, c.z, c.w}, dv[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    va[4 * c4 + u] = F2{av[u], bv[u]};
-                    dva[4 * c4 + u] = F2{cv[u], dv[u]};
-                }
-            }
-        }
+        F2 va[RP];
+        F2 dva[GRAD ? RP : 1];
         F2 phi{0.f, 0.f}, g1{0.f, 0.f}, g2{0.f, 0.f}, g3{0.f, 0.f};
         bool ok;
         // round 1: X = v2 W^T, X' = v2 D^T
@@ -212,24 +194,39 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
                 tc_axis2_row<RP>(P, r, false, v2);
                 tc_issue<RP>(sA, a_saddr, b_saddr, tmem, bar, act, v2, inv);
             }
+            // axis-1 rows (L2), loaded and interpolated while the MMAs run
+            {
+                const size_t o1 = (size_t)r.i1 * RP;
+                const float4* v1h = (const float4*)(P.Vt[0][0] + o1);
+                const float4* v1l = (const float4*)(P.Vt[0][1] + o1);
+                const float4* v1dh = (const float4*)(P.Vt[0][2] + o1);
+                const float4* v1dl = (const float4*)(P.Vt[0][3] + o1);
 #pragma unroll
-            for (int a = 0; a < RP; ++a) {
-                va[a] = dev::df_lerp(va[a], dva[a], r.f1);
-                if (!in1) dva[a] = F2{0.f, 0.f};
+                for (int c4 = 0; c4 < RP / 4; ++c4) {
+                    const float4 a = __ldg(v1h + c4), b = __ldg(v1l + c4), c = __ldg(v1dh + c4),
+                                 d = __ldg(v1dl + c4);
+                    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                    const float cv[4] = {c.x, c.y, c.z, c.w}, dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const F2 dv1{cv[u], dv[u]};
+                        va[4 * c4 + u] = dev::df_lerp(F2{av[u], bv[u]}, dv1, r.f1);
+                        if constexpr (GRAD) dva[4 * c4 + u] = in1 ? dv1 : F2{0.f, 0.f};
+                    }
+                }
             }
             ok = tc_wait(bar, phase, srt, t1, s1, rn);
             if (ok) {
 #pragma unroll
                 for (int ch = 0; ch < S::NP / 16; ++ch) {
-                    float x0[16], x1[16], x2[16];
-                    tc::tmem_ld16x3(tl + ch * 16, tl + S::NP + ch * 16, tl + 2 * S::NP + ch * 16, x0, x1, x2);
+                    float x0[16], x1[16];
+                    tc::tmem_ld16x2(tl + ch * 16, tl + S::NP + ch * 16, x0, x1);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int a = ch * 8 + q;
                         if (a < RP) {
-                            const F2 X = tc::combine(x0[2 * q], x1[2 * q], x2[2 * q], __fmul_rn(inv, sCs[2 * a]));
-                            const F2 Xd = tc::combine(x0[2 * q + 1], x1[2 * q + 1], x2[2 * q + 1],
-                                                      __fmul_rn(inv, sCs[2 * a + 1]));
+                            const F2 X = tc::combine(x0[2 * q], x1[2 * q], __fmul_rn(inv, sCs[2 * a]));
+                            const F2 Xd = tc::combine(x0[2 * q + 1], x1[2 * q + 1], __fmul_rn(inv, sCs[2 * a + 1]));
                             const F2 u = dev::df_lerp(X, Xd, f3);
                             dev::df_fma_acc(phi, va[a], u);
                             if constexpr (GRAD) {
@@ -256,16 +253,14 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
                 if (ok) {
 #pragma unroll
                     for (int ch = 0; ch < S::NP / 16; ++ch) {
-                        float x0[16], x1[16], x2[16];
-                        tc::tmem_ld16x3(tl + ch * 16, tl + S::NP + ch * 16, tl + 2 * S::NP + ch * 16, x0, x1, x2);
+                        float x0[16], x1[16];
+                        tc::tmem_ld16x2(tl + ch * 16, tl + S::NP + ch * 16, x0, x1);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const int a = ch * 8 + q;
                             if (a < RP) {
-                                const F2 Z =
-                                    tc::combine(x0[2 * q], x1[2 * q], x2[2 * q], __fmul_rn(inv, sCs[2 * a]));
-                                const F2 Zd = tc::combine(x0[2 * q + 1], x1[2 * q + 1], x2[2 * q + 1],
-                                                          __fmul_rn(inv, sCs[2 * a + 1]));
+                                const F2 Z = tc::combine(x0[2 * q], x1[2 * q], __fmul_rn(inv, sCs[2 * a]));
+                                const F2 Zd = tc::combine(x0[2 * q + 1], x1[2 * q + 1], __fmul_rn(inv, sCs[2 * a + 1]));
                                 dev::df_fma_acc(g2, va[a], dev::df_lerp(Z, Zd, f3));
                             }
                         }
@@ -329,13 +324,13 @@ rs_status tc_occupancy(K kern, uint32_t ncol, size_t& smem, int& per_sm) {
 
 // FP32 pipe operations per atom of the tensor-core W form (the MMAs excluded), per
 // column of the rank r: energy: the axis-2 pair lerp (14), its five slices (~20),
-// two column combinations (2 x 12), the axis-1 and axis-3 pair lerps (2 x 14) and one
+// two column combinations (2 x 8), the axis-1 and axis-3 pair lerps (2 x 14) and one
 // Dot2 step (13); gradient: the same round plus two more Dot2 steps, then the slope
 // row's slices, two combinations, one lerp and one Dot2 step; ~60 / ~100 per atom for
 // the rest (record, contributions).
 inline double tc_ops_per_atom(int RP, bool grad) {
     double r = RP;
-    return grad ? 224.0 * r + 100.0 : 101.0 * r + 60.0;
+    return grad ? 200.0 * r + 100.0 : 89.0 * r + 60.0;
 }
 
 }  // namespace

@@ -57,17 +57,17 @@ def test_contract_random_within_slicing_bound(L, RP, rows):
     X, Xd = L.rs_diag_tc_contract(RP, v, Wm, Dm)
     for out, B in ((X, Wm), (Xd, Dm)):
         ref = v @ B.T
-        # slicing keeps ~2^-37 of each row's and column's maximum, the dropped slice
-        # products (i + j >= 6) and the rounding of the third accumulator are smaller;
-        # an FP32-accumulated emulation of the scheme stays below 0.4 of 2^-36 K max max
-        bound = 2.0 ** -35 * RP * np.abs(v).max(axis=1, keepdims=True) * np.abs(B).max(axis=1)[None, :]
+        # the second accumulator's FP32 rounding and the dropped slice products
+        # (i + j >= 5) leave ~2^-33 of K max max; an FP32-accumulated CPU emulation of
+        # the scheme stays below 0.32 of this bound on these cases
+        bound = 2.0 ** -31 * RP * np.abs(v).max(axis=1, keepdims=True) * np.abs(B).max(axis=1)[None, :]
         err = np.abs(out - ref)
         assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
         if rows > 2:
             assert np.all(out[1] == 0.0)
-        # far better than FP32 in practice
+        # far better than FP32 in practice (the emulation: median 6e-4 .. 3e-3 of it)
         fp32 = (v.astype(np.float32) @ B.T.astype(np.float32)).astype(np.float64)
-        assert np.median(err) < 1e-3 * max(np.median(np.abs(fp32 - ref)), 1e-300) or np.median(err) == 0.0
+        assert np.median(err) < 2e-2 * max(np.median(np.abs(fp32 - ref)), 1e-300) or np.median(err) == 0.0
 
 
 @pytest.fixture(scope="module")
@@ -104,16 +104,16 @@ def test_sorted_energies_tc_vs_pairs_and_oracle(L, protein):
 
 
 def test_sorted_tc_launch_fills_tmem(L, protein):
-    # rank 20: three accumulators of 48 columns -> 256 TMEM columns per CTA, so two
-    # CTAs per SM and a grid of two CTAs per SM for a large call
+    # rank 20: two accumulators of 48 columns -> 128 TMEM columns per CTA, so four
+    # CTAs per SM and a grid of four CTAs per SM for a large energy call
     import torch
     w, m, prot, _ = protein
     prot.energies(w.lig_xyz, w.lig_q, w.quat, w.trans)
     info = L.rs_diag_tc_launch()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     print("tensor-core launch:", info)
-    assert info["per_sm"] == 2
-    assert info["grid"] == 2 * sms
+    assert info["per_sm"] == 4
+    assert info["grid"] == 4 * sms
 
 
 def test_sorted_gradients_tc_vs_pairs_and_oracle(L, protein):
