@@ -153,6 +153,7 @@ KERNEL_KIND = {
     "k_eval_canon": ("alu", "fp32"), "k_eval_canon_grad": ("alu", "fp32"),
     "k_sorted_wform": ("alu", "fp32ops"), "k_sorted_wform_grad": ("alu", "fp32ops"),
     "k_sorted_tc": ("alu", "fp32ops"), "k_sorted_tc_grad": ("alu", "fp32ops"), "k_group_tc": ("alu", "fp32ops"),
+    "k_sorted_atoms": ("alu", "fp32ops"), "k_sorted_atoms_grad": ("alu", "fp32ops"),
     "k_project": ("alu", "fp32ops"), "k_core": ("alu", "fp32ops"), "k_gauss_dsum": ("alu", "fp32ops"),
     "k_gram": ("alu", "fp64"), "k_gemm_gq": ("alu", "fp32ops"), "k_canon_factors": ("hbm", "bytes"),
 }
@@ -631,6 +632,8 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     lib.rs_timing_reset()
+    for g in (False, True):  # the atoms kernels count their work on the device
+        lib.rs_diag_short_counts(local, grad=g, reset=True)
     lib.rs_timing_enable(1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -649,6 +652,12 @@ def run_ours(args):
     launches = lib.rs_stats_kernel_launches() - launches0
     lib.rs_timing_enable(0)
     timings = lib.rs_timing_all()
+    short_work = {}
+    for g, name in ((False, "k_sorted_atoms"), (True, "k_sorted_atoms_grad")):
+        c = lib.rs_diag_short_counts(local, grad=g, reset=True)
+        short_work[name] = c
+        if name in timings:
+            timings[name]["work"] = c["fp32_ops"]
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -716,8 +725,14 @@ def run_ours(args):
                            "parallelism": f"{world} independent ranks, poses split (no collective)"},
                 "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "roofline_pose_kernels": {k: roofline(timings, pk, k) for k in
-                                          ("k_sorted_tc_grad", "k_sorted_tc", "k_sorted_wform_grad",
-                                           "k_sorted_wform") if k in timings},
+                                          ("k_sorted_atoms_grad", "k_sorted_atoms", "k_sorted_tc_grad",
+                                           "k_sorted_tc", "k_sorted_wform_grad", "k_sorted_wform")
+                                          if k in timings},
+                "short_range_work_per_step": {
+                    k: {"atoms": v["atoms"] / args.steps, "candidates": v["candidates"] / args.steps,
+                        "near_pairs": v["near"] / args.steps,
+                        "fp32_gops": round(v["fp32_ops"] / args.steps / 1e9, 4)}
+                    for k, v in short_work.items()},
                 "clocks": clocks,
                 "kernels_ms_per_step": {r["name"]: round(r["ms"] / args.steps, 4) for r in top}}
         print(json.dumps(line), flush=True)

@@ -366,6 +366,14 @@ int       rs_set_wform_kernel(int mode);
 /* Number of tensor-core tiles on `device` whose MMAs did not complete within the
  * kernel's bounded wait (their energies were set to NaN); 0 in normal operation. */
 rs_status rs_tc_error_count(int device, int32_t* out);
+/* Work counters of the cell-grouped atoms kernel (short range, Def. 2.1 with the
+ * vdW check of Eq. Energy_Min) on `device` since the last reset, for energy
+ * (grad = 0) or gradient (grad = 1) launches: counts[0] pose-atoms evaluated,
+ * counts[1] protein-atom candidates screened, counts[2] near pairs evaluated in
+ * pair arithmetic; *fp32_ops the algorithmic FP32 pipe operations these amount to
+ * (the library's work model of that kernel).  Synchronises the device; reset != 0
+ * zeroes the counters. */
+rs_status rs_diag_short_counts(int device, int grad, uint64_t* counts, double* fp32_ops, int reset);
 /* Launch shape of the latest tensor-core W-form launch in the process: CTAs,
  * dynamic shared memory per CTA (bytes) and CTAs per SM the occupancy allows. */
 rs_status rs_diag_tc_launch(int64_t* grid, int64_t* smem, int32_t* per_sm);

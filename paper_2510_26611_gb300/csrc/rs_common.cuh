@@ -161,6 +161,16 @@ rs_status ensure_buffer(void** buf, size_t* cap, size_t need);
 int* tc_error_flag(int device);
 // W-form kernel of the cell-grouped pose paths: 1 tensor cores, 0 float pairs.
 int wform_kernel_mode();
+// Work counters of the sorted atoms kernels on a device (atoms, candidates, near
+// pairs; one triple for energies, one for gradients), in the same device buffer.
+unsigned long long* short_counters(int device, bool grad);
+// FP32 pipe operations (FADD, FMUL, FFMA one each) of the atoms kernel's algorithmic
+// work: per pose-atom the pair position (nine Dot2 steps, three renormalisations),
+// three grid-cell lookups and the list cell (~230); per screened candidate the FP32
+// squared distance (6); per near pair the pair-arithmetic offset, distance and
+// cubic and its accumulation (121 for energies, 179 with the gradient terms).  The
+// totals match the kernels' FP32 instruction counters on the protein workload.
+double short_work_ops(bool grad, double atoms, double cand, double near);
 // Launch shape of the latest tensor-core W-form launch (diagnostics).
 void note_tc_launch(long long grid, size_t smem, int per_sm);
 // B images of the W form for the tensor-core path (rs_tc.cu): sizes for n cells of

@@ -52,6 +52,16 @@ int* tc_error_flag(int device) {
 
 int wform_kernel_mode() { return g_wform_mode.load(std::memory_order_relaxed); }
 
+double short_work_ops(bool grad, double atoms, double cand, double near) {
+    return 230.0 * atoms + 6.0 * cand + (grad ? 179.0 : 121.0) * near;
+}
+
+unsigned long long* short_counters(int device, bool grad) {
+    int* base = tc_error_flag(device);  // 256 bytes: the error count, then the counters
+    if (!base) return nullptr;
+    return reinterpret_cast<unsigned long long*>(base) + 8 + (grad ? 3 : 0);
+}
+
 namespace {
 std::atomic<long long> g_tc_grid{0};
 std::atomic<long long> g_tc_smem{0};
@@ -308,6 +318,27 @@ rs_status rs_tc_error_count(int device, int32_t* out) {
         return RS_ERR_INVALID;
     }
     RS_TRY_CUDA(cudaMemcpy(out, p, sizeof(int), cudaMemcpyDeviceToHost));
+    return RS_OK;
+}
+
+rs_status rs_diag_short_counts(int device, int grad, uint64_t* counts, double* fp32_ops, int reset) {
+    rs::clear_error();
+    if (!counts || !fp32_ops) {
+        rs::set_error("rs_diag_short_counts: NULL argument");
+        return RS_ERR_INVALID;
+    }
+    RS_TRY_CUDA(cudaSetDevice(device));
+    unsigned long long* p = rs::short_counters(device, grad != 0);
+    if (!p) {
+        rs::set_error("rs_diag_short_counts: device %d unavailable", device);
+        return RS_ERR_INVALID;
+    }
+    RS_TRY_CUDA(cudaDeviceSynchronize());
+    unsigned long long h[3];
+    RS_TRY_CUDA(cudaMemcpy(h, p, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 3; ++i) counts[i] = h[i];
+    *fp32_ops = rs::short_work_ops(grad != 0, (double)h[0], (double)h[1], (double)h[2]);
+    if (reset) RS_TRY_CUDA(cudaMemset(p, 0, sizeof(h)));
     return RS_OK;
 }
 

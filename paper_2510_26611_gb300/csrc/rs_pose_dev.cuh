@@ -194,9 +194,14 @@ struct NearQueue {
 // active = false contribute no atom.  prot_of(l) is the protein of lane l's atom
 // (lanes may belong to different proteins).  Each atom's sums are accumulated in
 // its own candidate order, so they equal short_vdw's (nl = 1) bit for bit.
+// Candidates screened and near pairs evaluated by a warp (warp-uniform counts).
+struct ShortCounts {
+    long long cand = 0, near = 0;
+};
+
 template <bool GRAD, class ProtOf>
 __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], const double x64[3],
-                                NearQueue<GRAD>& Q, F2& phi, F2 g[3], int& clash) {
+                                NearQueue<GRAD>& Q, F2& phi, F2 g[3], int& clash, ShortCounts* cnt = nullptr) {
     const int lane = threadIdx.x & 31;
     const ProteinView& P = prot_of(lane);
     const unsigned full = 0xffffffffu;
@@ -230,6 +235,7 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
     }
     Q.lstart[lane] = incl - total;
     const int grand = __shfl_sync(full, incl, 31);
+    if (cnt) cnt->cand += grand;
     __syncwarp();
     int qn = 0;  // entries in the queue (the same in every lane)
     auto process = [&](int m) {
@@ -301,6 +307,7 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
             Q.bits[slot] = bits;
         }
         qn += __popc(m);
+        if (cnt) cnt->near += __popc(m);
         if (qn >= 32) {
             process(32);
             qn -= 32;
@@ -318,8 +325,9 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
 // The same for a warp whose atoms all belong to protein P.
 template <bool GRAD>
 __device__ __forceinline__ void short_coop(const ProteinView& P, bool active, const F2 x[3], const double x64[3],
-                                           NearQueue<GRAD>& Q, F2& phi, F2 g[3], int& clash) {
-    short_coop_with<GRAD>([&](int) -> const ProteinView& { return P; }, active, x, x64, Q, phi, g, clash);
+                                           NearQueue<GRAD>& Q, F2& phi, F2 g[3], int& clash,
+                                           ShortCounts* cnt = nullptr) {
+    short_coop_with<GRAD>([&](int) -> const ProteinView& { return P; }, active, x, x64, Q, phi, g, clash, cnt);
 }
 
 // Atom position x = R y + t in float-pair arithmetic (Dot2 of the pair rows of R

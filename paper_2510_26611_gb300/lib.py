@@ -130,6 +130,7 @@ def _load() -> C.CDLL:
         "rs_tc_error_count": (st, [C.c_int, C.POINTER(i32)]),
         "rs_diag_tc_contract": (st, [i32, i32, vp, vp, vp, vp, vp]),
         "rs_diag_tc_launch": (st, [C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
+        "rs_diag_short_counts": (st, [C.c_int, C.c_int, vp, C.POINTER(C.c_double), C.c_int]),
         "rs_stats_kernel_launches": (C.c_ulonglong, []),
         "rs_timing_enable": (st, [C.c_int]),
         "rs_timing_reset": (st, []),
@@ -409,6 +410,16 @@ def rs_tc_error_count(device: int = 0) -> int:
     out = C.c_int32(0)
     _check(_lib.rs_tc_error_count(int(device), C.byref(out)))
     return int(out.value)
+
+
+def rs_diag_short_counts(device: int = 0, grad: bool = False, reset: bool = False) -> dict:
+    """Pose-atoms, candidates screened and near pairs of the cell-grouped atoms kernel
+    since the last reset (energy or gradient launches)."""
+    out = np.zeros(3, dtype=np.uint64)
+    ops = C.c_double(0.0)
+    _check(_lib.rs_diag_short_counts(int(device), int(bool(grad)), out.ctypes.data, C.byref(ops),
+                                     int(bool(reset))))
+    return {"atoms": int(out[0]), "candidates": int(out[1]), "near": int(out[2]), "fp32_ops": float(ops.value)}
 
 
 def rs_diag_tc_launch() -> dict:
