@@ -118,11 +118,12 @@ __global__ void __launch_bounds__(32 * WPB)
         r.f1 = cf[0];
         r.f2 = cf[1];
         r.f3 = cf[2];
-        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0) | (s << 8);
+        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0) | (sub_bucket(ci[1], pd.prot.n) << 3) |
+                 (s << 8);
         r.ry0 = ry[0];
         r.ry1 = ry[1];
         r.ry2 = ry[2];
-        r.rank = atomicAdd(&count[r.i3], 1);
+        r.rank = atomicAdd(&count[rec_key(r)], 1);
         rec[g] = r;
     }
 }
@@ -235,13 +236,16 @@ struct GroupScratch {
     int* off;
 };
 
+// nkey counts cells; the sort uses nkey * kSub sub-bucket keys.
 size_t chunk_scratch(int npose, long long natom, int nkey) {
+    nkey *= kSub;
     return align256((size_t)npose * sizeof(PoseSetup)) + align256((size_t)npose * 4) +
            2 * align256((size_t)natom * sizeof(AtomRec)) + 2 * align256((size_t)natom * 8) +
            align256((size_t)nkey * 4) + align256((size_t)(nkey + 1) * 4);
 }
 
 GroupScratch carve_group(void* base, int npose, long long natom, int nkey) {
+    nkey *= kSub;
     char* p = (char*)base;
     auto take = [&](size_t b) {
         char* q = p;
@@ -383,7 +387,7 @@ rs_status group_launch(const GroupPlan& G, const PairDesc* d_pairs, const GroupS
         const GroupSeg* segs = d_segs + ch.seg_begin;
         const int nseg = ch.seg_end - ch.seg_begin;
         GroupScratch s = carve_group(ws, ch.npose, ch.natom, ch.nkey);
-        RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)ch.nkey * 4, st));
+        RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)ch.nkey * kSub * 4, st));
         {
             ::rs::KernelTimer kt__("k_group_poses", st, 0.0, false, events);
             k_group_poses<<<(ch.npose + 127) / 128, 128, 0, st>>>(d_pairs, segs, nseg, ch.npose, s.ps, s.pflag);
@@ -406,7 +410,7 @@ rs_status group_launch(const GroupPlan& G, const PairDesc* d_pairs, const GroupS
         }
         {
             ::rs::KernelTimer kt__("k_cell_scan", st, 0.0, false, events);
-            k_cell_scan<<<1, 1024, 0, st>>>(ch.nkey, s.count, s.off);
+            k_cell_scan<<<1, 1024, 0, st>>>(ch.nkey * kSub, s.count, s.off);
         }
         {
             ::rs::KernelTimer kt__("k_sorted_scatter", st, 0.0, false, events);

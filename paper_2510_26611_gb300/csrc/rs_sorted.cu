@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
         r.slot = (int)g;
         if (!valid) {
             r.i3 = P.n - 1;
-            r.rank = atomicAdd(&count[P.n - 1], 1);
+            r.bits = 0;
+            r.rank = atomicAdd(&count[(P.n - 1) * kSub], 1);
             rec[g] = r;
             continue;
         }
@@ -105,11 +106,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
         r.f1 = cf[0];
         r.f2 = cf[1];
         r.f3 = cf[2];
-        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0);
+        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0) | (sub_bucket(ci[1], P.n) << 3);
         r.ry0 = ry[0];
         r.ry1 = ry[1];
         r.ry2 = ry[2];
-        r.rank = atomicAdd(&count[ci[2]], 1);
+        r.rank = atomicAdd(&count[rec_key(r)], 1);
         rec[g] = r;
     }
     if (lane == 0 && natoms > 0) {  // work counters of the launch (diagnostics)
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, GRAD ? 3 : 5)
     constexpr int SLAB4 = RP * RP / 4;  // float4 per plane
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float4* slab4 = sm4 + (size_t)wib * 4 * SLAB4;
-    const int Mv = off[P.n - 1];  // atoms of evaluated poses
+    const int Mv = off[(P.n - 1) * kSub];  // atoms of evaluated poses
     const long long nw = (long long)gridDim.x * kWarpsPerBlock;
     const long long w = (long long)blockIdx.x * kWarpsPerBlock + wib;
     const long long per = ((Mv + nw - 1) / nw + 31) / 32 * 32;
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(tc::kTileRows, GRAD ? 3 : 4)
                 const AtomRec* __restrict__ srt, const int* __restrict__ off, const double* __restrict__ shortv,
                 double* __restrict__ contrib, int* __restrict__ err) {
     extern __shared__ __align__(16) uint8_t smem_tc[];
-    const long long Mv = off[P.n - 1];
+    const long long Mv = off[(P.n - 1) * kSub];
     const long long per = (Mv + gridDim.x - 1) / gridDim.x;
     const long long s0 = (long long)blockIdx.x * per, s1 = std::min<long long>(Mv, s0 + per);
     const TcSingle src{&P, &lig};
@@ -213,8 +214,8 @@ size_t chunk_bytes(long long PC, int L, int n, bool grad) {
     const long long M = PC * L;
     const int NC = grad ? 7 : 1;
     return align256(PC * sizeof(PoseSetup)) + align256(PC * 4) + 2 * align256(M * sizeof(AtomRec)) +
-           align256(M * 8 * (grad ? 4 : 1)) + align256(M * 8 * NC) + align256((size_t)n * 4) +
-           align256((size_t)(n + 1) * 4);
+           align256(M * 8 * (grad ? 4 : 1)) + align256(M * 8 * NC) + align256((size_t)n * kSub * 4) +
+           align256(((size_t)n * kSub + 1) * 4);
 }
 
 SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
@@ -233,8 +234,8 @@ SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
     s.srt = (AtomRec*)take(M * sizeof(AtomRec));
     s.shortv = (double*)take(M * 8 * (grad ? 4 : 1));
     s.contrib = (double*)take(M * 8 * NC);
-    s.count = (int*)take((size_t)n * 4);
-    s.off = (int*)take((size_t)(n + 1) * 4);
+    s.count = (int*)take((size_t)n * kSub * 4);
+    s.off = (int*)take(((size_t)n * kSub + 1) * 4);
     return s;
 }
 
@@ -334,7 +335,7 @@ rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
         const int pc = (int)std::min<long long>(PC, a.P - p0);
         const long long M = (long long)pc * L;
         SortedScratch s = carve(a.ws, pc, L, n, GRAD);
-        RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)n * 4, st));
+        RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)n * kSub * 4, st));
         {
             ::rs::KernelTimer kt__("k_sorted_poses", st, 0.0, false, a.events);
             k_sorted_poses<<<(pc + 127) / 128, 128, 0, st>>>(a.prot, a.rot, a.trans, p0, pc, GRAD, a.skip, s.ps,
@@ -355,7 +356,7 @@ rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
         }
         {
             ::rs::KernelTimer kt__("k_cell_scan", st, 0.0, false, a.events);
-            k_cell_scan<<<1, 1024, 0, st>>>(n, s.count, s.off);
+            k_cell_scan<<<1, 1024, 0, st>>>(n * kSub, s.count, s.off);
         }
         {
             ::rs::KernelTimer kt__("k_sorted_scatter", st, 0.0, false, a.events);

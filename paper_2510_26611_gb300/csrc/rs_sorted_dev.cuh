@@ -15,11 +15,21 @@ struct __align__(16) AtomRec {
     int i1, i2, i3;       // interpolation cells (i3 = n - 1: pose skipped)
     float f1, f2, f3;     // fractions in the cells
     int slot;             // pl * L + j within the chunk
-    int bits;             // bit a set: coordinate a inside [-b, b]
+    int bits;             // bits 0-2: coordinate a inside [-b, b]; 3-7: sub-bucket; 8-: segment
     float ry0, ry1, ry2;  // R y (FP32), the torque arm
-    int rank;             // position among the atoms of its cell
+    int rank;             // position among the atoms of its sort key
 };
 static_assert(sizeof(AtomRec) == 48, "AtomRec layout");
+
+// Sort keys: each axis-3 cell is split into kSub sub-buckets by the axis-2 row, so
+// the atoms of a cell come out grouped by i2 and neighbouring atoms of a tile read
+// the same axis-2 factor rows (L1 hits instead of L2 round trips).  key = cell key *
+// kSub + sub-bucket; a cell's records are [off[c kSub], off[(c + 1) kSub]).
+constexpr int kSub = 32;
+__device__ __forceinline__ int sub_bucket(int i2, int n) {
+    return min(kSub - 1, (int)(((long long)i2 * kSub) / max(n - 1, 1)));
+}
+__device__ __forceinline__ int rec_key(const AtomRec& r) { return r.i3 * kSub + ((r.bits >> 3) & (kSub - 1)); }
 
 
 // Exclusive scan of count[0..m) into off[0..m]; one block of 1024 threads.
@@ -50,7 +60,7 @@ __global__ void k_sorted_scatter(long long M, const AtomRec* __restrict__ rec, c
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= M) return;
     AtomRec r = rec[g];
-    srt[off[r.i3] + r.rank] = r;
+    srt[off[rec_key(r)] + r.rank] = r;
 }
 
 

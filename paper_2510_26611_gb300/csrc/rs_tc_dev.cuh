@@ -104,9 +104,14 @@ __device__ __forceinline__ void tc_issue(uint8_t* sA, uint32_t a_saddr, uint32_t
 }
 
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t& phase, const AtomRec* __restrict__ srt,
-                                        long long t1, long long s1, AtomRec& rn) {
+                                        const int* __restrict__ off, long long t1, long long s1, AtomRec& rn,
+                                        AtomRec& hn, int& endn) {
     const int tid = threadIdx.x;
     if (t1 + tid < s1) rn = srt[t1 + tid];
+    if (t1 < s1) {  // the next tile's first record and the end of its cell
+        hn = srt[t1];
+        endn = off[(hn.i3 + 1) * kSub];
+    }
     const bool ok = tc::mbar_wait_bounded(bar, phase);
     phase ^= 1u;
     const bool failed = __syncthreads_or(!ok);
@@ -114,8 +119,8 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t& phase, const At
     return !failed;
 }
 
-// Walks the sorted records [s0, s1) (keys ascending, off[key + 1] = end of the key's
-// records) with the whole CTA (128 threads) and writes each atom's contributions.
+// Walks the sorted records [s0, s1) (cell keys ascending, off[(key + 1) kSub] = end of
+// the cell's records) with the whole CTA (128 threads) and writes each atom's contributions.
 // smem: TcLayout<RP, GRAD>::BYTES bytes, 16-byte aligned.  On an MMA that does not
 // complete within the bounded wait the tile's contributions are set to NaN, *err is
 // set and the CTA stops.
@@ -146,12 +151,17 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
     uint32_t phase = 0;
     // software pipeline: the next tile's record is loaded during this tile's MMAs, and
     // every global load a tile needs is issued before its MMA wait
-    AtomRec rn;
+    AtomRec rn, hn;
+    int endn = 0;
     if (s0 + tid < s1) rn = srt[s0 + tid];
+    if (s0 < s1) {
+        hn = srt[s0];
+        endn = off[(hn.i3 + 1) * kSub];
+    }
     for (long long t0 = s0; t0 < s1;) {
-        const AtomRec r0 = srt[t0];
+        const AtomRec r0 = hn;
         const int key = r0.i3;
-        const long long t1 = min(s1, min(t0 + tc::kTileRows, (long long)off[key + 1]));
+        const long long t1 = min(s1, min(t0 + tc::kTileRows, (long long)endn));
         const int sg = src.seg(r0);
         const ProteinView& P = src.prot(sg);
         if (key != cur) {
@@ -215,7 +225,7 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
                     }
                 }
             }
-            ok = tc_wait(bar, phase, srt, t1, s1, rn);
+            ok = tc_wait(bar, phase, srt, off, t1, s1, rn, hn, endn);
             if (ok) {
 #pragma unroll
                 for (int ch = 0; ch < S::NP / 16; ++ch) {
@@ -249,7 +259,7 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
                     tc_axis2_row<RP>(P, r, true, dv2);
                     tc_issue<RP>(sA, a_saddr, b_saddr, tmem, bar, act && in2, dv2, inv);
                 }
-                ok = tc_wait(bar, phase, srt, t1, s1, rn);
+                ok = tc_wait(bar, phase, srt, off, t1, s1, rn, hn, endn);
                 if (ok) {
 #pragma unroll
                     for (int ch = 0; ch < S::NP / 16; ++ch) {
