@@ -185,6 +185,55 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ start, int* __res
     }
 }
 
+// Short-range candidate lists.  Fine cell c (box [lo, lo + f] per axis) lists every
+// atom whose FP64 distance to the box is at most R, visiting the coarse cells (side
+// >= R) that can hold such atoms in increasing id order, so each list is in
+// cell-sorted atom order.  pass 0 counts, pass 1 writes at start[c].
+__global__ void k_nb_lists(int pass, int nf0, int nf1, int nf2, double fo0, double fo1, double fo2, double f,
+                           int nc0, int nc1, int nc2, double co0, double co1, double co2, double cell, double R,
+                           const int* __restrict__ cell_start, const double4* __restrict__ atoms64,
+                           const float4* __restrict__ atoms, int* __restrict__ count,
+                           const int* __restrict__ start, float4* __restrict__ nb_atoms,
+                           int* __restrict__ nb_idx) {
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)nf0 * nf1 * nf2) return;
+    const int cx = (int)(id % nf0), cy = (int)((id / nf0) % nf1), cz = (int)(id / ((long long)nf0 * nf1));
+    const double lo[3] = {fo0 + cx * f, fo1 + cy * f, fo2 + cz * f};
+    const double co[3] = {co0, co1, co2};
+    const int nc[3] = {nc0, nc1, nc2};
+    int c_lo[3], c_hi[3];
+    for (int a = 0; a < 3; ++a) {
+        c_lo[a] = max(0, (int)floor((lo[a] - R - co[a]) / cell));
+        c_hi[a] = min(nc[a] - 1, (int)floor((lo[a] + f + R - co[a]) / cell));
+    }
+    const double R2 = R * R;
+    int n = 0;
+    const int out = pass ? start[id] : 0;
+    for (int z = c_lo[2]; z <= c_hi[2]; ++z)
+        for (int y = c_lo[1]; y <= c_hi[1]; ++y) {
+            if (c_lo[0] > c_hi[0]) continue;
+            const int row = (z * nc1 + y) * nc0;
+            const int s = cell_start[row + c_lo[0]], e = cell_start[row + c_hi[0] + 1];
+            for (int k = s; k < e; ++k) {
+                const double4 a = atoms64[k];
+                const double p[3] = {a.x, a.y, a.z};
+                double d2 = 0.0;
+                for (int q = 0; q < 3; ++q) {
+                    const double d = fmax(fmax(lo[q] - p[q], p[q] - (lo[q] + f)), 0.0);
+                    d2 += d * d;
+                }
+                if (d2 <= R2) {
+                    if (pass) {
+                        nb_atoms[out + n] = atoms[k];
+                        nb_idx[out + n] = k;
+                    }
+                    ++n;
+                }
+            }
+        }
+    if (!pass) count[id] = n;
+}
+
 // ---------------------------------------------------- unreduced canonical factors
 __global__ void k_canon_factors(int n, double b, double h, int N, int Rl,
                                 const double* __restrict__ xyz, const double* __restrict__ q,
@@ -1028,7 +1077,7 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
     RS_TRY(S.get(&d_count, ncell));
     RS_TRY(S.get(&d_cursor, ncell));
     RS_TRY(S.get(&d_perm, N));
-    RS_TRY(device_alloc(P, (void**)&d_start, (ncell + 1) * sizeof(int)));
+    RS_TRY(S.get(&d_start, ncell + 1));
     float4 *d_atoms, *d_atoms_lo;
     double4* d_atoms64;
     RS_TRY(device_alloc(P, (void**)&d_atoms, (size_t)N * sizeof(float4)));
@@ -1055,18 +1104,65 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
                                                           d_atoms, d_atoms_lo, d_atoms64);
     }
     RS_TRY_CUDA(cudaGetLastError());
+    // candidate lists on fine cells of side R/2 over the box grown by R (the radius
+    // with a margin for the FP32 cell lookup of a query and the screen's bands)
+    const double R = std::max(P->table.r_c, P->sigma) * (1.0 + 1e-4) + 1e-3;
+    const double f = 0.5 * R;
+    int nf[3];
+    double fo[3];
+    size_t nfine = 1;
+    for (int a = 0; a < 3; ++a) {
+        fo[a] = bb[a] - R;
+        nf[a] = (int)std::floor((bb[3 + a] + R - fo[a]) / f) + 1;
+        nfine *= (size_t)nf[a];
+    }
+    if (nfine > (size_t)1 << 26) {
+        set_error("protein extent needs %zu candidate-list cells (max 2^26)", nfine);
+        return RS_ERR_UNSUPPORTED;
+    }
+    int *d_nb_count, *d_nb_start;
+    RS_TRY(S.get(&d_nb_count, nfine));
+    RS_TRY(device_alloc(P, (void**)&d_nb_start, (nfine + 1) * sizeof(int)));
+    {
+        ::rs::KernelTimer kt__("k_nb_lists", st, 0.0, false);
+        k_nb_lists<<<blocks_for(nfine), kBlock, 0, st>>>(0, nf[0], nf[1], nf[2], fo[0], fo[1], fo[2], f, nc[0],
+                                                        nc[1], nc[2], co[0], co[1], co[2], cell, R, d_start,
+                                                        d_atoms64, d_atoms, d_nb_count, nullptr, nullptr,
+                                                        nullptr);
+    }
+    {
+        ::rs::KernelTimer kt__("k_scan", st, 0.0, false);
+        k_scan<<<1, 1024, 0, st>>>((int)nfine, d_nb_count, d_nb_start);
+    }
+    int total = 0;
+    RS_TRY_CUDA(cudaMemcpyAsync(&total, d_nb_start + nfine, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RS_TRY_CUDA(cudaStreamSynchronize(st));
+    float4* d_nb_atoms;
+    int* d_nb_idx;
+    RS_TRY(device_alloc(P, (void**)&d_nb_atoms, (size_t)std::max(total, 1) * sizeof(float4)));
+    RS_TRY(device_alloc(P, (void**)&d_nb_idx, (size_t)std::max(total, 1) * sizeof(int)));
+    {
+        ::rs::KernelTimer kt__("k_nb_lists", st, 0.0, false);
+        k_nb_lists<<<blocks_for(nfine), kBlock, 0, st>>>(1, nf[0], nf[1], nf[2], fo[0], fo[1], fo[2], f, nc[0],
+                                                        nc[1], nc[2], co[0], co[1], co[2], cell, R, d_start,
+                                                        d_atoms64, d_atoms, nullptr, d_nb_start, d_nb_atoms,
+                                                        d_nb_idx);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
     ProteinView& v = P->view;
     v.atoms = d_atoms;
     v.atoms_lo = d_atoms_lo;
     v.atoms64 = d_atoms64;
-    v.cell_start = d_start;
-    v.nc0 = nc[0];
-    v.nc1 = nc[1];
-    v.nc2 = nc[2];
-    v.co0 = (float)co[0];
-    v.co1 = (float)co[1];
-    v.co2 = (float)co[2];
-    v.inv_cell = (float)(1.0 / cell);
+    v.nb_start = d_nb_start;
+    v.nb_atoms = d_nb_atoms;
+    v.nb_idx = d_nb_idx;
+    v.nf0 = nf[0];
+    v.nf1 = nf[1];
+    v.nf2 = nf[2];
+    v.fo0 = (float)fo[0];
+    v.fo1 = (float)fo[1];
+    v.fo2 = (float)fo[2];
+    v.inv_fine = (float)(1.0 / f);
     return RS_OK;
 }
 

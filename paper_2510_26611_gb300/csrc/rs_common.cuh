@@ -91,10 +91,15 @@ struct ProteinView {
     const float4* atoms;     // cell-sorted protein atoms (x, y, z, q), FP32 nearest
     const float4* atoms_lo;  // remainders: atoms + atoms_lo = the record to ~2^-48
     const double4* atoms64;  // the FP64 record (vdW decisions inside the sigma band)
-    const int* cell_start;   // [ncell + 1]
-    int nc0, nc1, nc2;
-    float co0, co1, co2;     // cell-grid origin
-    float inv_cell;
+    // Short-range candidate lists: fine cells of side f over the protein's box grown by
+    // the neighbour radius R; cell c lists, in cell-sorted atom order, every atom within
+    // R (plus a margin) of its box, so a query reads one contiguous list.
+    const int* nb_start;     // [nf0 nf1 nf2 + 1]
+    const float4* nb_atoms;  // the listed atoms' FP32 records (list order)
+    const int* nb_idx;       // their indices into atoms / atoms_lo / atoms64
+    int nf0, nf1, nf2;
+    float fo0, fo1, fo2;     // fine-grid origin
+    float inv_fine;          // 1 / f
 };
 
 // A prepared ligand on the device: coordinates about the geometric centre.

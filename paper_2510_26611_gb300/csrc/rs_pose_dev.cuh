@@ -43,31 +43,18 @@ __device__ __forceinline__ void setup_pose(const ProteinView& P, const double* _
     ps.valid = 1;
 }
 
-// Cell of the short-range cell list holding an FP32 position (may lie outside
-// the list's range by up to 4 cells; the neighbour walk skips those).
-__device__ __forceinline__ void short_cell(const ProteinView& P, const float xf[3], int& c0, int& c1, int& c2) {
-    float u0 = __fmul_rn(__fsub_rn(xf[0], P.co0), P.inv_cell);
-    float u1 = __fmul_rn(__fsub_rn(xf[1], P.co1), P.inv_cell);
-    float u2 = __fmul_rn(__fsub_rn(xf[2], P.co2), P.inv_cell);
-    u0 = fminf(fmaxf(u0, -4.f), (float)P.nc0 + 4.f);
-    u1 = fminf(fmaxf(u1, -4.f), (float)P.nc1 + 4.f);
-    u2 = fminf(fmaxf(u2, -4.f), (float)P.nc2 + 4.f);
-    c0 = (int)floorf(u0);
-    c1 = (int)floorf(u1);
-    c2 = (int)floorf(u2);
-}
-
-// Range [s, e) of cell-sorted atoms in row (dz, dy) of the 3 x 3 x 3 neighbourhood of
-// cell (c0, c1, c2): the row's three x-cells are contiguous.  Empty when off the list.
-__device__ __forceinline__ void short_row(const ProteinView& P, int c0, int c1, int c2, int row, int& s, int& e) {
-    const int dz = row / 3 - 1, dy = row % 3 - 1;
-    const int cz = c2 + dz, cy = c1 + dy;
-    const int x_lo = max(c0 - 1, 0), x_hi = min(c0 + 1, P.nc0 - 1);
+// Candidate list [s, e) of the fine cell holding an FP32 position (empty outside the
+// fine grid: no protein atom lies within the neighbour radius there).
+__device__ __forceinline__ void short_list(const ProteinView& P, const float xf[3], int& s, int& e) {
+    const float u0 = __fmul_rn(__fsub_rn(xf[0], P.fo0), P.inv_fine);
+    const float u1 = __fmul_rn(__fsub_rn(xf[1], P.fo1), P.inv_fine);
+    const float u2 = __fmul_rn(__fsub_rn(xf[2], P.fo2), P.inv_fine);
     s = e = 0;
-    if (cz < 0 || cz >= P.nc2 || cy < 0 || cy >= P.nc1 || x_lo > x_hi) return;
-    const int base = (cz * P.nc1 + cy) * P.nc0;
-    s = P.cell_start[base + x_lo];
-    e = P.cell_start[base + x_hi + 1];
+    if (!(u0 >= 0.f && u1 >= 0.f && u2 >= 0.f && u0 < (float)P.nf0 && u1 < (float)P.nf1 && u2 < (float)P.nf2))
+        return;
+    const int c = ((int)u2 * P.nf1 + (int)u1) * P.nf0 + (int)u0;
+    s = P.nb_start[c];
+    e = P.nb_start[c + 1];
 }
 
 // FP32 screen of one candidate: squared distance and its band bits
@@ -154,19 +141,15 @@ template <bool GRAD>
 __device__ __noinline__ void short_vdw(const ProteinView& P, const F2 x[3], const double x64[3], int lane,
                                        int nl, F2& phi, F2 g[3], int& clash) {
     const float xf[3] = {x[0].h, x[1].h, x[2].h};
-    int c0, c1, c2;
-    short_cell(P, xf, c0, c1, c2);
-    for (int row = 0; row < 9; ++row) {
-        int s, e;
-        short_row(P, c0, c1, c2, row, s, e);
-        for (int k = s + lane; k < e; k += nl) {
-            const int bits = short_screen(P, xf, P.atoms[k]);
-            if (!(bits & 3)) continue;
-            F2 f[3], w, fv{0.f, 0.f}, fgr{0.f, 0.f};
-            const int out = short_pair<GRAD>(P, x, x64, k, bits, f, w, fv, fgr);
-            if (out & 1) clash = 1;
-            if (out & 2) short_accumulate<GRAD>(w, fv, fgr, f, phi, g);
-        }
+    int s, e;
+    short_list(P, xf, s, e);
+    for (int j = s + lane; j < e; j += nl) {
+        const int bits = short_screen(P, xf, P.nb_atoms[j]);
+        if (!(bits & 3)) continue;
+        F2 f[3], w, fv{0.f, 0.f}, fgr{0.f, 0.f};
+        const int out = short_pair<GRAD>(P, x, x64, P.nb_idx[j], bits, f, w, fv, fgr);
+        if (out & 1) clash = 1;
+        if (out & 2) short_accumulate<GRAD>(w, fv, fgr, f, phi, g);
     }
 }
 
@@ -180,14 +163,13 @@ struct NearQueue {
     float2 f[GRAD ? 3 : 1][32];
     float2 x[3][32]; // pair positions of the warp's atoms
     double x64[3][32];  // FP64 positions (decisions inside the sigma band)
-    int rs[9][32];      // first candidate of each neighbourhood row
-    int rp[10][32];     // prefix of the rows' lengths (rp[9] = the lane's total)
-    int lstart[32];     // prefix of the lanes' totals over the warp
+    int ls[32];         // first entry of each lane's candidate list
+    int lstart[32];     // prefix of the lanes' list lengths over the warp
     int seg0[32], seg1[32];  // per owner lane: its entries [seg0, seg1) of a processed batch
 };
 
 // Short range and vdW decision for the 32 atoms of a warp (one per lane).  The
-// candidates of all 32 atoms form one list (lane by lane, each lane's in its own
+// candidate lists of all 32 atoms form one list (lane by lane, each lane's in its own
 // candidate order) that the lanes screen in FP32 32 at a time, and the near pairs
 // are then evaluated in pair arithmetic one pair per lane: atoms with very
 // different numbers of candidates or near pairs still keep every lane busy.  Every lane of the warp must call it; lanes with
@@ -206,6 +188,7 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
     const ProteinView& P = prot_of(lane);
     const unsigned full = 0xffffffffu;
     int total = 0;
+    int ls = 0;
     if (active) {
         float xf[3];
         for (int a = 0; a < 3; ++a) {
@@ -213,19 +196,11 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
             Q.x[a][lane] = make_float2(x[a].h, x[a].l);
             Q.x64[a][lane] = x64[a];
         }
-        int c0, c1, c2;
-        short_cell(P, xf, c0, c1, c2);
-        for (int row = 0; row < 9; ++row) {
-            int s, e;
-            short_row(P, c0, c1, c2, row, s, e);
-            Q.rs[row][lane] = s;
-            Q.rp[row][lane] = total;
-            total += e - s;
-        }
-    } else {
-        for (int row = 0; row < 9; ++row) Q.rp[row][lane] = 0;
+        int le;
+        short_list(P, xf, ls, le);
+        total = le - ls;
     }
-    Q.rp[9][lane] = total;
+    Q.ls[lane] = ls;
     // warp prefix of the totals: lane l's candidates are list entries [lstart, lstart + total)
     int incl = total;
 #pragma unroll
@@ -290,13 +265,11 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
                 else hi = mid - 1;
             }
             o = lo;
-            const int off = e - Q.lstart[o];
-            int r = 0;
-            while (Q.rp[r + 1][o] <= off) ++r;
-            k = Q.rs[r][o] + (off - Q.rp[r][o]);
+            const int j = Q.ls[o] + (e - Q.lstart[o]);
             const float xo[3] = {Q.x[0][o].x, Q.x[1][o].x, Q.x[2][o].x};
             const ProteinView& Po = prot_of(o);
-            bits = short_screen(Po, xo, Po.atoms[k]);
+            bits = short_screen(Po, xo, Po.nb_atoms[j]);
+            if (bits & 3) k = Po.nb_idx[j];
         }
         const bool near = (bits & 3) != 0;
         const unsigned m = __ballot_sync(full, near);
