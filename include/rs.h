@@ -374,6 +374,11 @@ rs_status rs_tc_error_count(int device, int32_t* out);
  * (the library's work model of that kernel).  Synchronises the device; reset != 0
  * zeroes the counters. */
 rs_status rs_diag_short_counts(int device, int grad, uint64_t* counts, double* fp32_ops, int reset);
+/* Diagnostics of the float-pair exponential of the build's Gaussian sums (Sec. 2,
+ * the shifted Gaussians of the factor assembly): out[i] = exp(x[i]) evaluated on the
+ * GPU from the pair nearest x[i] (|x[i]| <= 80; ~2^-46 relative for x[i] >= -60, where
+ * both words of the result are normal floats), returned as FP64.  Synchronous. */
+rs_status rs_diag_pair_exp(int32_t n, const double* x, double* out);
 /* Launch shape of the latest tensor-core W-form launch in the process: CTAs,
  * dynamic shared memory per CTA (bytes) and CTAs per SM the occupancy allows. */
 rs_status rs_diag_tc_launch(int64_t* grid, int64_t* smem, int32_t* per_sm);

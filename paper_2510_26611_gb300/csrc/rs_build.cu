@@ -186,17 +186,19 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ start, int* __res
 }
 
 // Short-range candidate lists.  Fine cell c (box [lo, lo + f] per axis) lists every
-// atom whose FP64 distance to the box is at most R, visiting the coarse cells (side
-// >= R) that can hold such atoms in increasing id order, so each list is in
-// cell-sorted atom order.  pass 0 counts, pass 1 writes at start[c].
+// atom whose distance to the box is at most R, visiting the coarse cells (side >= R)
+// that can hold such atoms in increasing id order, so each list is in cell-sorted
+// atom order.  One warp per fine cell: the lanes test a coarse row's atoms 32 at a
+// time (FP32 distance against R + 1e-3 A, a superset of the FP64 test) and a ballot
+// keeps their order.  pass 0 counts, pass 1 writes at start[c].
 __global__ void k_nb_lists(int pass, int nf0, int nf1, int nf2, double fo0, double fo1, double fo2, double f,
                            int nc0, int nc1, int nc2, double co0, double co1, double co2, double cell, double R,
-                           const int* __restrict__ cell_start, const double4* __restrict__ atoms64,
-                           const float4* __restrict__ atoms, int* __restrict__ count,
-                           const int* __restrict__ start, float4* __restrict__ nb_atoms,
+                           const int* __restrict__ cell_start, const float4* __restrict__ atoms,
+                           int* __restrict__ count, const int* __restrict__ start, float4* __restrict__ nb_atoms,
                            int* __restrict__ nb_idx) {
-    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (long long)nf0 * nf1 * nf2) return;
+    const long long id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (id >= (long long)nf0 * nf1 * nf2) return;  // warp-uniform
     const int cx = (int)(id % nf0), cy = (int)((id / nf0) % nf1), cz = (int)(id / ((long long)nf0 * nf1));
     const double lo[3] = {fo0 + cx * f, fo1 + cy * f, fo2 + cz * f};
     const double co[3] = {co0, co1, co2};
@@ -206,7 +208,10 @@ __global__ void k_nb_lists(int pass, int nf0, int nf1, int nf2, double fo0, doub
         c_lo[a] = max(0, (int)floor((lo[a] - R - co[a]) / cell));
         c_hi[a] = min(nc[a] - 1, (int)floor((lo[a] + f + R - co[a]) / cell));
     }
-    const double R2 = R * R;
+    const float blo[3] = {(float)lo[0], (float)lo[1], (float)lo[2]};
+    const float bhi[3] = {(float)(lo[0] + f), (float)(lo[1] + f), (float)(lo[2] + f)};
+    const float Rf = (float)(R + 1e-3);
+    const float R2 = Rf * Rf;
     int n = 0;
     const int out = pass ? start[id] : 0;
     for (int z = c_lo[2]; z <= c_hi[2]; ++z)
@@ -214,24 +219,30 @@ __global__ void k_nb_lists(int pass, int nf0, int nf1, int nf2, double fo0, doub
             if (c_lo[0] > c_hi[0]) continue;
             const int row = (z * nc1 + y) * nc0;
             const int s = cell_start[row + c_lo[0]], e = cell_start[row + c_hi[0] + 1];
-            for (int k = s; k < e; ++k) {
-                const double4 a = atoms64[k];
-                const double p[3] = {a.x, a.y, a.z};
-                double d2 = 0.0;
-                for (int q = 0; q < 3; ++q) {
-                    const double d = fmax(fmax(lo[q] - p[q], p[q] - (lo[q] + f)), 0.0);
-                    d2 += d * d;
-                }
-                if (d2 <= R2) {
-                    if (pass) {
-                        nb_atoms[out + n] = atoms[k];
-                        nb_idx[out + n] = k;
+            for (int k0 = s; k0 < e; k0 += 32) {
+                const int k = k0 + lane;
+                bool in = false;
+                float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < e) {
+                    a = atoms[k];
+                    const float p[3] = {a.x, a.y, a.z};
+                    float d2 = 0.f;
+                    for (int q = 0; q < 3; ++q) {
+                        const float d = fmaxf(fmaxf(blo[q] - p[q], p[q] - bhi[q]), 0.f);
+                        d2 = fmaf(d, d, d2);
                     }
-                    ++n;
+                    in = d2 <= R2;
                 }
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (pass && in) {
+                    const int o = out + n + __popc(m & ((1u << lane) - 1u));
+                    nb_atoms[o] = a;
+                    nb_idx[o] = k;
+                }
+                n += __popc(m);
             }
         }
-    if (!pass) count[id] = n;
+    if (!pass && lane == 0) count[id] = n;
 }
 
 // ---------------------------------------------------- unreduced canonical factors
@@ -259,23 +270,84 @@ __global__ void k_canon_factors(int n, double b, double h, int N, int Rl,
     F2[o] = (float)(exp(-t2 * d2 * d2) * q[m] * al[k]);
 }
 
+// ------------------------------------------------------------- pair exponential
+// exp(x) for a float pair x, |x| <= 80, on the FP32 pipes, by the table-driven method
+// of P. T. P. Tang ("Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic", ACM TOMS 15, 1989): x = (256 n + j) ln2/256 + r with
+// |r| <= ln2/512, exp(x) = 2^n 2^(j/256) exp(r); ln2/256 is split into C1 (8
+// significant bits, so m C1 is exact for |m| < 2^16), C2 and C3; the 256 table values
+// 2^(j/256) are float pairs of FP64 values; exp(r) is its Taylor polynomial to degree 4
+// (the omitted r^5/120 is below 2^-54).  Relative error ~2^-46.
+__global__ void k_exp2_table(float2* __restrict__ tab) {
+    const int j = threadIdx.x;
+    const double v = exp2(j / 256.0);
+    const dev::F2 p = dev::df_from(v);
+    tab[j] = make_float2(p.h, p.l);
+}
+
+__device__ __forceinline__ dev::F2 df_exp(dev::F2 x, const float2* __restrict__ tab) {
+    using dev::F2;
+    const float m = rintf(__fmul_rn(x.h, 0x1.715476p+8f));  // x 256 / ln2
+    F2 r = dev::df_add(x, F2{-__fmul_rn(m, 0x1.62p-9f), 0.f});  // m C1 exact
+    const float p2 = __fmul_rn(m, 0x1.c85fep-18f);
+    const float e2 = __fmaf_rn(m, 0x1.c85fep-18f, -p2);          // m C2 = p2 + e2 exactly
+    r = dev::df_add(r, F2{-p2, -e2});
+    r = dev::df_add(r, F2{__fmul_rn(m, 0x1.71844p-43f), 0.f});    // - m C3 (C3 < 0)
+    const int mi = (int)m;
+    const int j = mi & 255, n = mi >> 8;
+    F2 t = dev::df_add(F2{0x1.555556p-3f, -0x1.555556p-28f}, dev::df_mul(r, F2{0x1.555556p-5f, -0x1.555556p-30f}));
+    t = dev::df_add(F2{0.5f, 0.f}, dev::df_mul(r, t));
+    t = dev::df_add(F2{1.f, 0.f}, dev::df_mul(r, t));
+    t = dev::df_add(F2{1.f, 0.f}, dev::df_mul(r, t));
+    const float2 tj = tab[j];
+    const F2 v = dev::df_mul(F2{tj.x, tj.y}, t);
+    const float sc = __int_as_float((n + 127) << 23);
+    return F2{__fmul_rn(v.h, sc), __fmul_rn(v.l, sc)};
+}
+
+__global__ void k_diag_pair_exp(int n, const double* __restrict__ x, const float2* __restrict__ tab,
+                                double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = dev::df_to(df_exp(dev::df_from(x[i]), tab));
+}
+
+// a / b for float pairs (one Newton correction of the FP32 quotient).
+__device__ __forceinline__ dev::F2 df_div(dev::F2 a, dev::F2 b) {
+    const float q1 = __fdiv_rn(a.h, b.h);
+    const dev::F2 rem = dev::df_sub(a, dev::df_mul(b, dev::F2{q1, 0.f}));
+    const float q2 = __fdiv_rn(rem.h, b.h);
+    return dev::fast_two_sum(q1, q2);
+}
+
 // ------------------------------------------------------------- Gram by Gaussian products
 // G[i,i'] = sum_(m,k) |xi|^(2/3) e^{-t^2 (x_i-x_m)^2} e^{-t^2 (x_i'-x_m)^2}
 //         = sum_k |a_k|^(2/3) e^{-t^2 (x_i-x_i')^2 / 2} D_k(y_{i+i'}),
 // D_k(y) = sum_m |z_m|^(2/3) e^{-2 t^2 (y - x_m)^2},  y_s = -b + s h/2 (half grid).
 // One thread: SC half-grid points, one (axis, k), MC atoms.  Each Gaussian is
 // walked from its point nearest to x_m outwards with the exact ratio recurrence
-// g_{s+1} = g_s rho_s, rho_{s+1} = rho_s c; the two seeds per (atom, chunk) are
-// FP64 exponentials, the walk and the sums are float pairs on the FP32 pipes
-// (about 2^-47 relative per step, at most 31 steps from a seed).
+// g_{s+1} = g_s rho_s, rho_{s+1} = rho_s c, all in float pairs on the FP32 pipes:
+// the atom records are float pairs (k_dsum_atoms), the two seeds per (atom, chunk)
+// are pair exponentials (df_exp) and the backward ratio a pair quotient, so the loop
+// runs no FP64 instruction (GB300's FP64 rate is 1/64 of FP32); about 2^-46 relative
+// per seed and 2^-47 per step, at most 31 steps from a seed.
 constexpr int kSC = 32;
 constexpr int kMC = 128;
 
+// Atom records of the Gaussian sums: per axis (x_a as a pair, |z|^(2/3) as a pair).
+__global__ void k_dsum_atoms(int N, const double* __restrict__ xyz, const double* __restrict__ cz,
+                             float4* __restrict__ pk) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ax = blockIdx.y;
+    if (m >= N) return;
+    const dev::F2 x = dev::df_from(xyz[3 * (size_t)m + ax]), c = dev::df_from(cz[m]);
+    pk[(size_t)ax * N + m] = make_float4(x.h, x.l, c.h, c.l);
+}
+
 __global__ void __launch_bounds__(128) k_gauss_dsum(int n, double b, double h, int N, int Rl,
-                                                     const double* __restrict__ xyz,
-                                                     const double* __restrict__ cz,
-                                                     const double* __restrict__ tl, int nsc,
-                                                     int nmc, double* __restrict__ Dp) {
+                                                     const float4* __restrict__ pk,
+                                                     const double* __restrict__ tl,
+                                                     const float2* __restrict__ etab, int nsc, int nmc,
+                                                     double* __restrict__ Dp) {
     using dev::F2;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long total = (long long)nsc * Rl * 3 * nmc;
@@ -288,29 +360,33 @@ __global__ void __launch_bounds__(128) k_gauss_dsum(int n, double b, double h, i
     int mc = (int)(rest / 3);
     const int S = 2 * n - 1;
     const double delta = 0.5 * h;
-    const double inv_delta = 1.0 / delta;
     const int s0 = sc * kSC;
-    const double y0 = -b + s0 * delta;
     const double t2 = 2.0 * tl[k] * tl[k];
-    const double cq = exp(-2.0 * t2 * delta * delta);
-    const F2 cqp = dev::df_from(cq);
+    // per-thread constants (FP64 once, then pairs)
+    const F2 y0 = dev::df_from(-b + s0 * delta), dl = dev::df_from(delta), t2p = dev::df_from(t2);
+    const F2 t2d = dev::df_from(t2 * delta), cqp = dev::df_from(exp(-2.0 * t2 * delta * delta));
+    const float inv_delta = (float)(1.0 / delta);
     F2 acc[kSC];
 #pragma unroll
     for (int s = 0; s < kSC; ++s) acc[s] = F2{0.f, 0.f};
+    const float4* pa = pk + (size_t)ax * N;
     int m_end = min(N, (mc + 1) * kMC);
     for (int m = mc * kMC; m < m_end; ++m) {
-        double xm = xyz[3 * (size_t)m + ax];
-        double u = (xm - y0) * inv_delta;
-        u = fmin(fmax(u, 0.0), (double)(kSC - 1));
-        int sp = (int)rint(u);
-        double dp = y0 + sp * delta - xm;
-        double arg = t2 * dp * dp;
-        if (arg > 50.0) continue;  // the whole chunk is below e^-50 of the peak
-        double e1 = exp(-t2 * (2.0 * dp * delta + delta * delta));
-        const F2 g0 = dev::df_from(cz[m] * exp(-arg));
-        const F2 rf = dev::df_from(e1);
-        const F2 rb = dev::df_from(cq / e1);
-        F2 g = g0, r = rf;
+        const float4 a = pa[m];
+        float u = __fmul_rn(__fsub_rn(a.x, y0.h), inv_delta);
+        u = fminf(fmaxf(u, 0.f), (float)(kSC - 1));
+        const float sp_f = rintf(u);
+        const int sp = (int)sp_f;
+        // dp = y0 + sp delta - x_m; arg = t2 dp^2
+        const F2 dp = dev::df_sub(dev::df_add(y0, dev::df_mul(F2{sp_f, 0.f}, dl)), F2{a.x, a.y});
+        const F2 arg = dev::df_mul(t2p, dev::df_mul(dp, dp));
+        if (arg.h > 50.f) continue;  // the whole chunk is below e^-50 of the peak
+        // forward ratio e1 = exp(-t2 (2 dp delta + delta^2)) = exp(-t2 delta (2 dp + delta))
+        const F2 a1 = dev::df_mul(t2d, dev::df_add(F2{2.f * dp.h, 2.f * dp.l}, dl));
+        const F2 e1 = df_exp(F2{-a1.h, -a1.l}, etab);
+        const F2 g0 = dev::df_mul(F2{a.z, a.w}, df_exp(F2{-arg.h, -arg.l}, etab));
+        const F2 rb = df_div(cqp, e1);
+        F2 g = g0, r = e1;
 #pragma unroll
         for (int s = 0; s < kSC; ++s) {
             if (s == sp) dev::df_acc(acc[s], g0);
@@ -655,23 +731,26 @@ __global__ void __launch_bounds__(512) k_skeleton(int n, int RP, const int* __re
                                                    int* __restrict__ Sidx,
                                                    double* __restrict__ Ainv,
                                                    int* __restrict__ fail) {
-    __shared__ double red_v[512];
+    __shared__ float red_v[512];
     __shared__ int red_i[512];
-    __shared__ double piv[RS_MAX_TUCKER];
+    __shared__ float piv[RS_MAX_TUCKER];
     __shared__ int sel[RS_MAX_TUCKER];
     __shared__ double A[RS_MAX_TUCKER][2 * RS_MAX_TUCKER + 1];
     int ax = blockIdx.x;
     int r = r_ax[ax];
     const double* Va = V + (size_t)ax * n * RP;
-    double* Ma = M + (size_t)ax * n * RP;
-    for (size_t e = threadIdx.x; e < (size_t)n * RP; e += blockDim.x) Ma[e] = Va[e];
+    // The selection runs in FP32: it only has to pick well-conditioned rows (the
+    // basis change V V[S,:]^-1 and the core transform use the exact FP64 rows), and
+    // GB300's FP64 rate made the FP64 version the build's slowest serial kernel.
+    float* Ma = reinterpret_cast<float*>(M) + (size_t)ax * n * RP;
+    for (size_t e = threadIdx.x; e < (size_t)n * RP; e += blockDim.x) Ma[e] = (float)Va[e];
     __syncthreads();
     for (int step = 0; step < r; ++step) {
-        double best = -1.0;
+        float best = -1.f;
         int bi = n;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            double s = 0.0;
-            for (int c = 0; c < r; ++c) s += Ma[(size_t)i * RP + c] * Ma[(size_t)i * RP + c];
+            float s = 0.f;
+            for (int c = 0; c < r; ++c) s = fmaf(Ma[(size_t)i * RP + c], Ma[(size_t)i * RP + c], s);
             if (s > best || (s == best && i < bi)) {
                 best = s;
                 bi = i;
@@ -682,7 +761,7 @@ __global__ void __launch_bounds__(512) k_skeleton(int n, int RP, const int* __re
         __syncthreads();
         for (int o = blockDim.x / 2; o > 0; o >>= 1) {
             if (threadIdx.x < o) {
-                double v2 = red_v[threadIdx.x + o];
+                float v2 = red_v[threadIdx.x + o];
                 int i2 = red_i[threadIdx.x + o];
                 if (v2 > red_v[threadIdx.x] || (v2 == red_v[threadIdx.x] && i2 < red_i[threadIdx.x])) {
                     red_v[threadIdx.x] = v2;
@@ -692,17 +771,17 @@ __global__ void __launch_bounds__(512) k_skeleton(int n, int RP, const int* __re
             __syncthreads();
         }
         int pi = red_i[0];
-        double nrm = sqrt(red_v[0]);
+        float nrm = sqrtf(red_v[0]);
         if (threadIdx.x == 0) {
             sel[step] = pi;
-            if (!(nrm > 0.0)) fail[ax] = 2;
+            if (!(nrm > 0.f)) fail[ax] = 2;
         }
-        if (threadIdx.x < r) piv[threadIdx.x] = nrm > 0.0 ? Ma[(size_t)pi * RP + threadIdx.x] / nrm : 0.0;
+        if (threadIdx.x < r) piv[threadIdx.x] = nrm > 0.f ? Ma[(size_t)pi * RP + threadIdx.x] / nrm : 0.f;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            double d = 0.0;
-            for (int c = 0; c < r; ++c) d += Ma[(size_t)i * RP + c] * piv[c];
-            for (int c = 0; c < r; ++c) Ma[(size_t)i * RP + c] -= d * piv[c];
+            float d = 0.f;
+            for (int c = 0; c < r; ++c) d = fmaf(Ma[(size_t)i * RP + c], piv[c], d);
+            for (int c = 0; c < r; ++c) Ma[(size_t)i * RP + c] = fmaf(-d, piv[c], Ma[(size_t)i * RP + c]);
         }
         __syncthreads();
     }
@@ -1128,10 +1207,10 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
     RS_TRY(device_alloc(P, (void**)&d_nb_start, (nfine + 1) * sizeof(int)));
     {
         ::rs::KernelTimer kt__("k_nb_lists", st, 0.0, false);
-        k_nb_lists<<<blocks_for(nfine), kBlock, 0, st>>>(0, nf[0], nf[1], nf[2], fo[0], fo[1], fo[2], f, nc[0],
-                                                        nc[1], nc[2], co[0], co[1], co[2], cell, R, d_start,
-                                                        d_atoms64, d_atoms, d_nb_count, nullptr, nullptr,
-                                                        nullptr);
+        k_nb_lists<<<blocks_for(nfine * 32), kBlock, 0, st>>>(0, nf[0], nf[1], nf[2], fo[0], fo[1], fo[2], f,
+                                                             nc[0], nc[1], nc[2], co[0], co[1], co[2], cell, R,
+                                                             d_start, d_atoms, d_nb_count, nullptr, nullptr,
+                                                             nullptr);
     }
     {
         ::rs::KernelTimer kt__("k_scan", st, 0.0, false);
@@ -1146,10 +1225,10 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
     RS_TRY(device_alloc(P, (void**)&d_nb_idx, (size_t)std::max(total, 1) * sizeof(int)));
     {
         ::rs::KernelTimer kt__("k_nb_lists", st, 0.0, false);
-        k_nb_lists<<<blocks_for(nfine), kBlock, 0, st>>>(1, nf[0], nf[1], nf[2], fo[0], fo[1], fo[2], f, nc[0],
-                                                        nc[1], nc[2], co[0], co[1], co[2], cell, R, d_start,
-                                                        d_atoms64, d_atoms, nullptr, d_nb_start, d_nb_atoms,
-                                                        d_nb_idx);
+        k_nb_lists<<<blocks_for(nfine * 32), kBlock, 0, st>>>(1, nf[0], nf[1], nf[2], fo[0], fo[1], fo[2], f,
+                                                             nc[0], nc[1], nc[2], co[0], co[1], co[2], cell, R,
+                                                             d_start, d_atoms, nullptr, d_nb_start, d_nb_atoms,
+                                                             d_nb_idx);
     }
     RS_TRY_CUDA(cudaGetLastError());
     ProteinView& v = P->view;
@@ -1230,13 +1309,23 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY(S.get(&d_tr, 3));
     long long threads = (long long)nsc * Rl * 3 * nmc;
     double work = 0.0;
+    float4* d_pk;
+    float2* d_etab;
+    RS_TRY(S.get(&d_pk, (size_t)3 * N));
+    RS_TRY(S.get(&d_etab, 256));
+    {
+        ::rs::KernelTimer kt__("k_dsum_atoms", st, 0.0, false);
+        k_dsum_atoms<<<dim3(blocks_for(N), 3), kBlock, 0, st>>>(N, d_xyz, d_cz, d_pk);
+        k_exp2_table<<<1, 256, 0, st>>>(d_etab);
+    }
     {
         ::rs::KernelTimer kt__("k_gauss_dsum", st, 0.0, true);
-        k_gauss_dsum<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, b, h, N, Rl, d_xyz, d_cz,
-                                                                         d_tl, nsc, nmc, d_Dp);
-        // FP32 pipe ops of the pair walks: 26 per half-grid point (two pair products,
-        // one pair sum) of every chunk within e^-50 of a Gaussian's peak (closed form
-        // per term; only when timed).  The two FP64 seeds per chunk are not counted.
+        k_gauss_dsum<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, b, h, N, Rl, d_pk, d_tl, d_etab,
+                                                                         nsc, nmc, d_Dp);
+        // FP32 pipe ops: 26 per half-grid point of the pair walks (two pair products,
+        // one pair sum) plus ~320 for the seeds (two pair exponentials, a pair
+        // quotient, the offsets) of every chunk within e^-50 of a Gaussian's peak
+        // (closed form per term; only when timed).
         if (kt__.active()) {
             const double delta = 0.5 * h;
             double w = 0.0;
@@ -1246,7 +1335,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
                 for (size_t e = 0; e < xyz_host.size(); ++e) {
                     double lo = std::max(0.0, std::floor((xyz_host[e] - reach + b) / delta / kSC));
                     double hi = std::min((double)(nsc - 1), std::floor((xyz_host[e] + reach + b) / delta / kSC));
-                    if (hi >= lo) w += (hi - lo + 1) * kSC * 26.0;
+                    if (hi >= lo) w += (hi - lo + 1) * (kSC * 26.0 + 320.0);
                 }
             }
             kt__.set_work(w);
@@ -1552,6 +1641,35 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
 }
 
 }  // namespace rs
+
+extern "C" rs_status rs_diag_pair_exp(int32_t n, const double* x, double* out) {
+    using namespace rs;
+    clear_error();
+    RS_CHECK_ARG(x && out && n >= 1 && n <= (1 << 24), "rs_diag_pair_exp: bad argument");
+    for (int i = 0; i < n; ++i)
+        RS_CHECK_ARG(std::fabs(x[i]) <= 80.0, "rs_diag_pair_exp: |x| = %g exceeds 80", std::fabs(x[i]));
+    char* buf = nullptr;
+    const size_t vb = (size_t)n * sizeof(double);
+    RS_TRY_CUDA(cudaMalloc(&buf, 2 * vb + 256 * sizeof(float2) + 512));
+    double* d_x = (double*)buf;
+    double* d_o = (double*)(buf + vb);
+    float2* d_t = (float2*)(buf + 2 * vb + 256);
+    rs_status st = RS_OK;
+    if (cudaMemcpy(d_x, x, vb, cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("rs_diag_pair_exp: copy failed");
+        st = RS_ERR_CUDA;
+    } else {
+        k_exp2_table<<<1, 256>>>(d_t);
+        k_diag_pair_exp<<<(n + 255) / 256, 256>>>(n, d_x, d_t, d_o);
+        note_launch(2);
+        if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(out, d_o, vb, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            set_error("rs_diag_pair_exp: %s", cudaGetErrorString(cudaGetLastError()));
+            st = RS_ERR_CUDA;
+        }
+    }
+    cudaFree(buf);
+    return st;
+}
 
 extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz, const double* q,
                                       const rs_params* prm, int mem_flags, void* stream,

@@ -131,6 +131,7 @@ def _load() -> C.CDLL:
         "rs_diag_tc_contract": (st, [i32, i32, vp, vp, vp, vp, vp]),
         "rs_diag_tc_launch": (st, [C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
         "rs_diag_short_counts": (st, [C.c_int, C.c_int, vp, C.POINTER(C.c_double), C.c_int]),
+        "rs_diag_pair_exp": (st, [i32, vp, vp]),
         "rs_stats_kernel_launches": (C.c_ulonglong, []),
         "rs_timing_enable": (st, [C.c_int]),
         "rs_timing_reset": (st, []),
@@ -420,6 +421,14 @@ def rs_diag_short_counts(device: int = 0, grad: bool = False, reset: bool = Fals
     _check(_lib.rs_diag_short_counts(int(device), int(bool(grad)), out.ctypes.data, C.byref(ops),
                                      int(bool(reset))))
     return {"atoms": int(out[0]), "candidates": int(out[1]), "near": int(out[2]), "fp32_ops": float(ops.value)}
+
+
+def rs_diag_pair_exp(x: np.ndarray) -> np.ndarray:
+    """exp(x) by the build's float-pair exponential on the GPU (|x| <= 80)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    _check(_lib.rs_diag_pair_exp(int(x.size), x.ctypes.data, out.ctypes.data))
+    return out
 
 
 def rs_diag_tc_launch() -> dict:

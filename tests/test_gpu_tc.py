@@ -186,3 +186,17 @@ def test_path_errors_helper_scale():
     # is judged on the batch's typical magnitude
     e = path_errors(np.array([1.0, 1e-12, -3.0]), np.array([1.0, 0.0, -3.0]))
     assert e[1] == pytest.approx(1e-12, rel=1e-9)
+
+
+def test_pair_exponential_against_fp64(L):
+    # the build's Gaussian seeds: exp of a float pair, ~2^-46 relative over the range
+    # they use (exponents >= -50; below about -70 the low word of the result is an FP32
+    # subnormal and the pair loses precision)
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.uniform(-60.0, 60.0, 20000), rng.uniform(-1e-3, 1e-3, 2000),
+                        np.array([0.0, -50.0, 50.0, np.log(2.0), -np.log(2.0) / 512])])
+    y = L.rs_diag_pair_exp(x)
+    h = x.astype(np.float32).astype(np.float64)
+    xp = h + (x - h).astype(np.float32).astype(np.float64)  # the float pair the kernel reads
+    rel = np.abs(y - np.exp(xp)) / np.exp(xp)
+    assert rel.max() < 2.0 ** -44, rel.max()
