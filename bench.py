@@ -322,8 +322,17 @@ def run_batch(args):
 
     ms_plain = timeit(plain)
     ms_batch = timeit(batched)
-    same = all(torch.equal(p["E_out"], e) and torch.equal(p["flags_out"], f)
-               for p, e, f in zip(pairs, E2, F2))
+    # batched vs plain: flags identical; energies equal, or within the W-form path
+    # tolerance where the two take different long-range kernels (relative to
+    # max(|E|, median |E|) per pair)
+    same_flags = all(torch.equal(p["flags_out"], f) for p, f in zip(pairs, F2))
+    bitwise = all(torch.equal(p["E_out"], e) for p, e in zip(pairs, E2))
+    rel = 0.0
+    for p, e in zip(pairs, E2):
+        if e.numel():
+            ref = e.abs()
+            scale = torch.clamp(ref, min=float(ref.median()))
+            rel = max(rel, float(((p["E_out"] - e).abs() / scale).max()))
     P_tot = sum(w.P for w in ws)
     atoms = sum(w.P * w.L for w in ws)
     line = {"metric": "batched poses/s, 64 uneven pairs in one persistent graph launch",
@@ -332,7 +341,8 @@ def run_batch(args):
             "higher_is_better": True, "data": "synthetic",
             "plain": {"value": round(P_tot / (ms_plain / 1e3), 3), "ms_per_step": round(ms_plain, 4),
                       "launches": len(pairs)},
-            "speedup_vs_plain": round(ms_plain / ms_batch, 3), "bitwise_equal_to_plain": bool(same),
+            "speedup_vs_plain": round(ms_plain / ms_batch, 3), "flags_equal_to_plain": bool(same_flags),
+            "energies_bitwise_equal_to_plain": bool(bitwise), "max_rel_diff_to_plain": rel,
             "config": {"workload": "batch_pairs: N log-uniform [500,20000], L uniform [10,200], "
                                    "n in {513,1025,2049,4097} by box quartile, "
                                    f"{args.pair_poses} poses per pair, Tucker rank <= 20",

@@ -211,11 +211,11 @@ typedef struct rs_batch_info {
 /* Algorithm PLIE (Sec. 3.4) for many pairs of uneven size, grouped by padded
  * rank and captured once in a CUDA graph.  Per group either the cell-grouped
  * multi-pair pipeline (pose-atoms of all pairs sorted by (pair, grid cell)) or one
- * persistent per-block launch runs.  autotune = 1: the path and its shape (warps
- * per CTA and chunk size, or threads per CTA and atoms per work item) are chosen
- * by timing the candidates on a quarter of the group's poses (this writes the
- * output arrays; cached per padded rank for the process); 0: the cell-grouped
- * pipeline with 4 warps per CTA; 2: the per-block launch with its default shape.  Ligands are prepared now;
+ * persistent per-block launch runs.  autotune = 1: the path and its shape (chunk
+ * size, or threads per CTA and atoms per work item) are chosen by timing the
+ * candidates on all of the group's poses (this writes the output arrays; cached per
+ * padded rank for the process); 0: the cell-grouped pipeline; 2: the per-block
+ * launch with its default shape.  Ligands are prepared now;
  * poses are read from the given pointers at each rs_batch_run, so a caller may
  * rewrite them in place between runs.  Device scratch: about 110 bytes per
  * pose-atom of the largest chunk (at most 2^23 pose-atoms).  Energies and flags
@@ -356,9 +356,10 @@ rs_status rs_timing_get(int index, char* name, size_t name_len, double* total_ms
 /* Long-range (W form, Sec. 3 Tucker interpolation) kernel of the cell-grouped pose
  * paths that rs_energy_poses, rs_energy_grad_poses, rs_batch_run and the server
  * take for large calls: mode 1 (default) runs the per-cell contraction on the
- * tensor cores (tcgen05 MMAs on exact BF16 slices, ~2^-31 relative accuracy of each
- * contraction); mode 0 runs it in float-pair arithmetic on the FP32 pipes
- * (~2^-47).  Both agree with the FP64 definition far inside the 1e-5 energy
+ * tensor cores (tcgen05 MMAs on exact BF16 slices, ~2^-33 relative accuracy of each
+ * contraction) for launches whose axis-3 grid cells hold at least 96 pose-atoms on
+ * average, and in float-pair arithmetic on the FP32 pipes (~2^-47) below that;
+ * mode 0 always runs the float-pair kernel.  Both agree with the FP64 definition far inside the 1e-5 energy
  * tolerance; the per-block path of small calls is float-pair in both modes.
  * Process-wide; takes effect for launches (and batch plans) made afterwards.
  * Returns the previous mode. */

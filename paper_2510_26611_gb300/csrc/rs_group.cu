@@ -9,7 +9,7 @@
 //   k_group_poses    pose setups
 //   k_group_atoms    per pose-atom: position, cells, short range and vdW, record
 //                    keyed by the segment's first cell + the axis-3 cell
-//   k_cell_scan      exclusive scan of the per-key counts
+//   key scan         exclusive scan of the per-key counts (three kernels)
 //   k_sorted_scatter records in key order
 //   k_group_wform    per warp: a run of sorted atoms, the slab of the current
 //                    (pair, cell) in shared memory, long range + contributions
@@ -67,7 +67,7 @@ __global__ void k_group_poses(const PairDesc* __restrict__ pairs, const GroupSeg
 template <int WPB>
 __global__ void __launch_bounds__(32 * WPB)
     k_group_atoms(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, int nseg, long long natom,
-                  const PoseSetup* __restrict__ ps, int* __restrict__ pflag,
+                  int ksub, const PoseSetup* __restrict__ ps, int* __restrict__ pflag,
                   AtomRec* __restrict__ rec, double* __restrict__ shortv, int* __restrict__ count) {
     __shared__ NearQueue<false> queues[WPB];
     __shared__ int lane_pair[WPB][32];
@@ -118,12 +118,12 @@ __global__ void __launch_bounds__(32 * WPB)
         r.f1 = cf[0];
         r.f2 = cf[1];
         r.f3 = cf[2];
-        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0) | (sub_bucket(ci[1], pd.prot.n) << 3) |
+        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0) | (sub_bucket(ci[1], pd.prot.n, ksub) << 3) |
                  (s << 8);
         r.ry0 = ry[0];
         r.ry1 = ry[1];
         r.ry2 = ry[2];
-        r.rank = atomicAdd(&count[rec_key(r)], 1);
+        r.rank = atomicAdd(&count[rec_key(r, ksub)], 1);
         rec[g] = r;
     }
 }
@@ -200,13 +200,13 @@ struct TcGroup {
 template <int RP>
 __global__ void __launch_bounds__(tc::kTileRows, 4)
     k_group_tc(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, const AtomRec* __restrict__ srt,
-               const int* __restrict__ off, long long natom, const double* __restrict__ shortv,
+               const int* __restrict__ off, int ksub, long long natom, const double* __restrict__ shortv,
                double* __restrict__ contrib, int* __restrict__ err) {
     extern __shared__ __align__(16) uint8_t smem_tc[];
     const long long per = (natom + gridDim.x - 1) / gridDim.x;
     const long long s0 = (long long)blockIdx.x * per, s1 = std::min<long long>(natom, s0 + per);
     const TcGroup src{pairs, segs};
-    tc_wform_range<RP, false>(src, srt, off, s0, s1, shortv, contrib, smem_tc, err);
+    tc_wform_range<RP, false>(src, srt, off, ksub, s0, s1, shortv, contrib, smem_tc, err);
 }
 
 __global__ void k_group_reduce(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, int nseg,
@@ -234,18 +234,19 @@ struct GroupScratch {
     double* contrib;
     int* count;
     int* off;
+    int* bsum;
 };
 
-// nkey counts cells; the sort uses nkey * kSub sub-bucket keys.
-size_t chunk_scratch(int npose, long long natom, int nkey) {
-    nkey *= kSub;
+// nkey counts cells; the sort uses nkey * ksub sub-bucket keys.
+size_t chunk_scratch(int npose, long long natom, int nkey, int ksub) {
+    nkey *= ksub;
     return align256((size_t)npose * sizeof(PoseSetup)) + align256((size_t)npose * 4) +
            2 * align256((size_t)natom * sizeof(AtomRec)) + 2 * align256((size_t)natom * 8) +
-           align256((size_t)nkey * 4) + align256((size_t)(nkey + 1) * 4);
+           align256((size_t)nkey * 4) + align256((size_t)(nkey + 1) * 4) + align256(key_scan_ints(nkey) * 4);
 }
 
-GroupScratch carve_group(void* base, int npose, long long natom, int nkey) {
-    nkey *= kSub;
+GroupScratch carve_group(void* base, int npose, long long natom, int nkey, int ksub) {
+    nkey *= ksub;
     char* p = (char*)base;
     auto take = [&](size_t b) {
         char* q = p;
@@ -261,6 +262,7 @@ GroupScratch carve_group(void* base, int npose, long long natom, int nkey) {
     s.contrib = (double*)take((size_t)natom * 8);
     s.count = (int*)take((size_t)nkey * 4);
     s.off = (int*)take((size_t)(nkey + 1) * 4);
+    s.bsum = (int*)take(key_scan_ints(nkey) * 4);
     return s;
 }
 
@@ -285,7 +287,7 @@ rs_status launch_group_wform(const PairDesc* d_pairs, const GroupSeg* d_segs, co
 }
 
 template <int RP>
-rs_status launch_group_tc(const PairDesc* d_pairs, const GroupSeg* d_segs, const GroupScratch& s, long long natom,
+rs_status launch_group_tc(const PairDesc* d_pairs, const GroupSeg* d_segs, const GroupScratch& s, int ksub, long long natom,
                           cudaStream_t st, bool events) {
     auto kern = k_group_tc<RP>;
     size_t smem = TcLayout<RP, false>::BYTES;
@@ -303,7 +305,7 @@ rs_status launch_group_tc(const PairDesc* d_pairs, const GroupSeg* d_segs, const
     note_tc_launch(grid, smem, per_sm);
     {
         ::rs::KernelTimer kt__("k_group_tc", st, (double)natom * tc_ops_per_atom(RP, false), true, events);
-        kern<<<(unsigned)grid, tc::kTileRows, smem, st>>>(d_pairs, d_segs, s.srt, s.off, natom, s.shortv, s.contrib,
+        kern<<<(unsigned)grid, tc::kTileRows, smem, st>>>(d_pairs, d_segs, s.srt, s.off, ksub, natom, s.shortv, s.contrib,
                                                           err);
     }
     RS_TRY_CUDA(cudaGetLastError());
@@ -312,12 +314,12 @@ rs_status launch_group_tc(const PairDesc* d_pairs, const GroupSeg* d_segs, const
 
 template <int WPB>
 rs_status dispatch_group_wform(int RP, const PairDesc* d_pairs, const GroupSeg* d_segs, const GroupScratch& s,
-                               long long natom, cudaStream_t st, bool events) {
-    const bool tcore = wform_kernel_mode() == 1;
+                               int ksub, int ncell, long long natom, cudaStream_t st, bool events) {
+    const bool tcore = wform_kernel_mode() == 1 && (double)natom >= kTcMinAtomsPerCell * (double)ncell;
     switch (RP) {
 #define RS_CASE(R)                                                                   \
     case R:                                                                          \
-        return tcore ? launch_group_tc<R>(d_pairs, d_segs, s, natom, st, events)     \
+        return tcore ? launch_group_tc<R>(d_pairs, d_segs, s, ksub, natom, st, events) \
                      : launch_group_wform<R, WPB>(d_pairs, d_segs, s, natom, st, events);
         RS_CASE(4) RS_CASE(8) RS_CASE(12) RS_CASE(16) RS_CASE(20) RS_CASE(24) RS_CASE(28) RS_CASE(32)
 #undef RS_CASE
@@ -338,10 +340,13 @@ rs_status group_plan(const std::vector<PairDesc>& pairs, const std::vector<int>&
     GroupChunk ch{0, 0, 0, 0, 0};
     auto close_chunk = [&]() {
         if (ch.seg_end > ch.seg_begin) {
-            G.scratch = std::max(G.scratch, chunk_scratch(ch.npose, ch.natom, ch.nkey));
+            // sub-buckets per cell: as many as keep the chunk's keys near 2^20
+            ch.ksub = kSub;
+            while (ch.ksub > 1 && (long long)ch.nkey * ch.ksub > (1LL << 20)) ch.ksub >>= 1;
+            G.scratch = std::max(G.scratch, chunk_scratch(ch.npose, ch.natom, ch.nkey, ch.ksub));
             G.chunks.push_back(ch);
         }
-        ch = GroupChunk{(int)G.segs.size(), (int)G.segs.size(), 0, 0, 0};
+        ch = GroupChunk{(int)G.segs.size(), (int)G.segs.size(), 0, 0, 0, kSub};
     };
     for (int m : members) {
         const PairDesc& pd = pairs[m];
@@ -386,8 +391,8 @@ rs_status group_launch(const GroupPlan& G, const PairDesc* d_pairs, const GroupS
     for (const GroupChunk& ch : G.chunks) {
         const GroupSeg* segs = d_segs + ch.seg_begin;
         const int nseg = ch.seg_end - ch.seg_begin;
-        GroupScratch s = carve_group(ws, ch.npose, ch.natom, ch.nkey);
-        RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)ch.nkey * kSub * 4, st));
+        GroupScratch s = carve_group(ws, ch.npose, ch.natom, ch.nkey, ch.ksub);
+        RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)ch.nkey * ch.ksub * 4, st));
         {
             ::rs::KernelTimer kt__("k_group_poses", st, 0.0, false, events);
             k_group_poses<<<(ch.npose + 127) / 128, 128, 0, st>>>(d_pairs, segs, nseg, ch.npose, s.ps, s.pflag);
@@ -405,20 +410,22 @@ rs_status group_launch(const GroupPlan& G, const PairDesc* d_pairs, const GroupS
             }
             const long long grid = std::max<long long>(1, std::min<long long>((ch.natom + 127) / 128, res));
             ::rs::KernelTimer kt__("k_group_atoms", st, 0.0, true, events);
-            k_group_atoms<4><<<(unsigned)grid, 128, 0, st>>>(d_pairs, segs, nseg, ch.natom, s.ps, s.pflag, s.rec,
+            k_group_atoms<4><<<(unsigned)grid, 128, 0, st>>>(d_pairs, segs, nseg, ch.natom, ch.ksub, s.ps, s.pflag, s.rec,
                                                             s.shortv, s.count);
         }
         {
-            ::rs::KernelTimer kt__("k_cell_scan", st, 0.0, false, events);
-            k_cell_scan<<<1, 1024, 0, st>>>(ch.nkey * kSub, s.count, s.off);
+            ::rs::KernelTimer kt__("k_key_scan", st, 0.0, false, events);
+            launch_key_scan(ch.nkey * ch.ksub, s.count, s.bsum, s.off, st);
+            note_launch(2);  // three kernels under one timer
         }
         {
             ::rs::KernelTimer kt__("k_sorted_scatter", st, 0.0, false, events);
-            k_sorted_scatter<<<(unsigned)((ch.natom + 255) / 256), 256, 0, st>>>(ch.natom, s.rec, s.off, s.srt);
+            k_sorted_scatter<<<(unsigned)((ch.natom + 255) / 256), 256, 0, st>>>(ch.natom, ch.ksub, s.rec, s.off,
+                                                                                   s.srt);
         }
         RS_TRY_CUDA(cudaGetLastError());
-        if (wpb == 8) RS_TRY(dispatch_group_wform<8>(G.RP, d_pairs, segs, s, ch.natom, st, events));
-        else RS_TRY(dispatch_group_wform<4>(G.RP, d_pairs, segs, s, ch.natom, st, events));
+        if (wpb == 8) RS_TRY(dispatch_group_wform<8>(G.RP, d_pairs, segs, s, ch.ksub, ch.nkey, ch.natom, st, events));
+        else RS_TRY(dispatch_group_wform<4>(G.RP, d_pairs, segs, s, ch.ksub, ch.nkey, ch.natom, st, events));
         {
             ::rs::KernelTimer kt__("k_group_reduce", st, 0.0, false, events);
             k_group_reduce<<<(unsigned)((ch.npose * 32LL + 255) / 256), 256, 0, st>>>(d_pairs, segs, nseg, ch.npose,

@@ -21,7 +21,8 @@ struct GroupChunk {
     int seg_begin, seg_end;  // segments [seg_begin, seg_end) of the plan
     int npose;
     long long natom;
-    int nkey;                // record keys (sum over segments of n - 1)
+    int nkey;                // cells (sum over segments of n - 1)
+    int ksub;                // sort sub-buckets per cell (a power of two <= 32)
 };
 
 // Chunks and segments of the pairs `members` (all Tucker-reduced, one padded rank).

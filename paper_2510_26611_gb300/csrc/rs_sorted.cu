@@ -9,7 +9,7 @@
 //   k_sorted_poses   pose setups (rotation, Jacobian) of the chunk
 //   k_sorted_atoms   per atom: FP64 position, cells, fractions, short range and
 //                    vdW (flags), a 48-byte record, and its rank in a per-cell count
-//   k_cell_scan      exclusive scan of the per-cell counts
+//   key scan         exclusive scan of the per-key counts (three kernels)
 //   k_sorted_scatter records to their cell-sorted positions
 //   k_sorted_wform   per warp: a contiguous run of sorted atoms; slab of the current
 //                    cell in shared memory; long range + contributions per atom
@@ -106,11 +106,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
         r.f1 = cf[0];
         r.f2 = cf[1];
         r.f3 = cf[2];
-        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0) | (sub_bucket(ci[1], P.n) << 3);
+        r.bits = (ins[0] ? 1 : 0) | (ins[1] ? 2 : 0) | (ins[2] ? 4 : 0) | (sub_bucket(ci[1], P.n, kSub) << 3);
         r.ry0 = ry[0];
         r.ry1 = ry[1];
         r.ry2 = ry[2];
-        r.rank = atomicAdd(&count[rec_key(r)], 1);
+        r.rank = atomicAdd(&count[rec_key(r, kSub)], 1);
         rec[g] = r;
     }
     if (lane == 0 && natoms > 0) {  // work counters of the launch (diagnostics)
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(tc::kTileRows, GRAD ? 3 : 4)
     const long long per = (Mv + gridDim.x - 1) / gridDim.x;
     const long long s0 = (long long)blockIdx.x * per, s1 = std::min<long long>(Mv, s0 + per);
     const TcSingle src{&P, &lig};
-    tc_wform_range<RP, GRAD>(src, srt, off, s0, s1, shortv, contrib, smem_tc, err);
+    tc_wform_range<RP, GRAD>(src, srt, off, kSub, s0, s1, shortv, contrib, smem_tc, err);
 }
 
 template <int NC>
@@ -206,6 +206,7 @@ struct SortedScratch {
     double* contrib;
     int* count;
     int* off;
+    int* bsum;  // segment sums of the key scan
 };
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -215,7 +216,7 @@ size_t chunk_bytes(long long PC, int L, int n, bool grad) {
     const int NC = grad ? 7 : 1;
     return align256(PC * sizeof(PoseSetup)) + align256(PC * 4) + 2 * align256(M * sizeof(AtomRec)) +
            align256(M * 8 * (grad ? 4 : 1)) + align256(M * 8 * NC) + align256((size_t)n * kSub * 4) +
-           align256(((size_t)n * kSub + 1) * 4);
+           align256(((size_t)n * kSub + 1) * 4) + align256(key_scan_ints((long long)n * kSub) * 4);
 }
 
 SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
@@ -236,6 +237,7 @@ SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
     s.contrib = (double*)take(M * 8 * NC);
     s.count = (int*)take((size_t)n * kSub * 4);
     s.off = (int*)take(((size_t)n * kSub + 1) * 4);
+    s.bsum = (int*)take(key_scan_ints((long long)n * kSub) * 4);
     return s;
 }
 
@@ -286,7 +288,8 @@ rs_status launch_sorted_tc(const EvalLaunch& a, const SortedScratch& s, long lon
 
 template <bool GRAD>
 rs_status dispatch_sorted_wform(const EvalLaunch& a, const SortedScratch& s, long long M, cudaStream_t st) {
-    const bool tcore = wform_kernel_mode() == 1 && a.prot.Wtc != nullptr;
+    const bool tcore = wform_kernel_mode() == 1 && a.prot.Wtc != nullptr &&
+                       (double)M >= kTcMinAtomsPerCell * (double)(a.prot.n - 1);
     switch (a.prot.R) {
 #define RS_CASE(R)                                                                          \
     case R:                                                                                 \
@@ -355,12 +358,13 @@ rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
                                                                         s.shortv, s.count, ctr);
         }
         {
-            ::rs::KernelTimer kt__("k_cell_scan", st, 0.0, false, a.events);
-            k_cell_scan<<<1, 1024, 0, st>>>(n * kSub, s.count, s.off);
+            ::rs::KernelTimer kt__("k_key_scan", st, 0.0, false, a.events);
+            launch_key_scan(n * kSub, s.count, s.bsum, s.off, st);
+            note_launch(2);  // three kernels under one timer
         }
         {
             ::rs::KernelTimer kt__("k_sorted_scatter", st, 0.0, false, a.events);
-            k_sorted_scatter<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, s.rec, s.off, s.srt);
+            k_sorted_scatter<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, kSub, s.rec, s.off, s.srt);
         }
         RS_TRY_CUDA(cudaGetLastError());
         RS_TRY(dispatch_sorted_wform<GRAD>(a, s, M, st));

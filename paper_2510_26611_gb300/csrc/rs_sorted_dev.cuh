@@ -25,42 +25,118 @@ static_assert(sizeof(AtomRec) == 48, "AtomRec layout");
 // the atoms of a cell come out grouped by i2 and neighbouring atoms of a tile read
 // the same axis-2 factor rows (L1 hits instead of L2 round trips).  key = cell key *
 // kSub + sub-bucket; a cell's records are [off[c kSub], off[(c + 1) kSub]).
+// The single-pair path uses kSub; the grouped path fewer when its chunks hold many
+// cells (a power of two ksub <= kSub, the same for the whole chunk).
 constexpr int kSub = 32;
-__device__ __forceinline__ int sub_bucket(int i2, int n) {
-    return min(kSub - 1, (int)(((long long)i2 * kSub) / max(n - 1, 1)));
+__device__ __forceinline__ int sub_bucket(int i2, int n, int ksub) {
+    return min(ksub - 1, (int)(((long long)i2 * ksub) / max(n - 1, 1)));
 }
-__device__ __forceinline__ int rec_key(const AtomRec& r) { return r.i3 * kSub + ((r.bits >> 3) & (kSub - 1)); }
+__device__ __forceinline__ int rec_key(const AtomRec& r, int ksub) {
+    return r.i3 * ksub + ((r.bits >> 3) & (ksub - 1));
+}
 
 
-// Exclusive scan of count[0..m) into off[0..m]; one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_cell_scan(int m, const int* __restrict__ count, int* __restrict__ off) {
-    __shared__ int part[1024];
-    const int per = (m + 1023) / 1024;
-    const int lo = threadIdx.x * per, hi = min(m, lo + per);
-    int s = 0;
-    for (int i = lo; i < hi; ++i) s += count[i];
-    part[threadIdx.x] = s;
+// Exclusive scan of count[0..m) into off[0..m] over the whole GPU: blocks of
+// kScanT threads x kScanE keys reduce their segments (k_scan_blocks), one block
+// scans the segment sums (k_scan_sums), and every block rescans its segment from its
+// base (k_scan_apply).  Fixed order, so the offsets do not depend on scheduling.
+constexpr int kScanT = 512, kScanE = 16, kScanSeg = kScanT * kScanE;
+
+__device__ __forceinline__ int block_exclusive(int v, int* sm_warp, int& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) sm_warp[w] = inc;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        int x = lane < nw ? sm_warp[lane] : 0, xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += t;
+        }
+        if (lane < nw) sm_warp[lane] = xi - x;  // exclusive prefix of the warp totals
+        if (lane == nw - 1) sm_warp[32] = xi;
     }
-    int base = threadIdx.x ? part[threadIdx.x - 1] : 0;
-    for (int i = lo; i < hi; ++i) {
-        off[i] = base;
-        base += count[i];
-    }
-    if (threadIdx.x == 1023) off[m] = part[1023];
+    __syncthreads();
+    total = sm_warp[32];
+    const int r = sm_warp[w] + inc - v;
+    __syncthreads();
+    return r;
 }
 
-__global__ void k_sorted_scatter(long long M, const AtomRec* __restrict__ rec, const int* __restrict__ off,
-                                 AtomRec* __restrict__ srt) {
+__global__ void __launch_bounds__(kScanT) k_scan_blocks(int m, const int* __restrict__ count, int* __restrict__ bsum) {
+    __shared__ int smw[33];
+    const long long base = (long long)blockIdx.x * kScanSeg + (long long)threadIdx.x * kScanE;
+    int s = 0;
+#pragma unroll
+    for (int e = 0; e < kScanE; ++e)
+        if (base + e < m) s += count[base + e];
+    int total;
+    block_exclusive(s, smw, total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// In place: bsum[0..nb) -> exclusive prefix, bsum[nb] = total; one block.
+__global__ void __launch_bounds__(1024) k_scan_sums(int nb, int* __restrict__ bsum) {
+    __shared__ int smw[33];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < nb ? bsum[i] : 0;
+        int total;
+        const int ex = block_exclusive(v, smw, total);
+        if (i < nb) bsum[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_apply(int m, int nb, const int* __restrict__ count,
+                                                       const int* __restrict__ bsum, int* __restrict__ off) {
+    __shared__ int smw[33];
+    const long long base = (long long)blockIdx.x * kScanSeg + (long long)threadIdx.x * kScanE;
+    int v[kScanE], s = 0;
+#pragma unroll
+    for (int e = 0; e < kScanE; ++e) {
+        v[e] = base + e < m ? count[base + e] : 0;
+        s += v[e];
+    }
+    int total;
+    int run = bsum[blockIdx.x] + block_exclusive(s, smw, total);
+#pragma unroll
+    for (int e = 0; e < kScanE; ++e) {
+        if (base + e < m) off[base + e] = run;
+        run += v[e];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[m] = bsum[nb];
+}
+
+// Scratch ints of the scan for m keys, and the launch (three kernels).
+inline size_t key_scan_ints(long long m) { return (size_t)((m + kScanSeg - 1) / kScanSeg) + 1; }
+inline void launch_key_scan(int m, const int* count, int* bsum, int* off, cudaStream_t st) {
+    const int nb = (int)((m + kScanSeg - 1) / kScanSeg);
+    if (nb > 0) k_scan_blocks<<<nb, kScanT, 0, st>>>(m, count, bsum);
+    k_scan_sums<<<1, 1024, 0, st>>>(nb, bsum);
+    if (nb > 0) k_scan_apply<<<nb, kScanT, 0, st>>>(m, nb, count, bsum, off);
+    else k_scan_apply<<<1, kScanT, 0, st>>>(m, 0, count, bsum, off);
+}
+
+__global__ void k_sorted_scatter(long long M, int ksub, const AtomRec* __restrict__ rec,
+                                 const int* __restrict__ off, AtomRec* __restrict__ srt) {
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= M) return;
     AtomRec r = rec[g];
-    srt[off[rec_key(r)] + r.rank] = r;
+    srt[off[rec_key(r, ksub)] + r.rank] = r;
 }
 
 

@@ -29,6 +29,13 @@
 namespace rs {
 namespace {
 
+// A tile holds up to 128 records of one cell, and its cost barely depends on how
+// many rows are filled.  A launch whose cells hold fewer atoms than this on average
+// (pose-atoms / grid cells along axis 3) takes the float-pair W form instead, which
+// walks the records 32 at a time per warp (measured on GB300: 0.27 ns per pose-atom
+// for full tensor-core tiles, 0.46 ns for the float-pair kernel at any fill).
+constexpr double kTcMinAtomsPerCell = 96.0;
+
 template <int RP, bool GRAD>
 struct TcLayout {
     using S = tc::Shape<RP>;
@@ -104,13 +111,13 @@ __device__ __forceinline__ void tc_issue(uint8_t* sA, uint32_t a_saddr, uint32_t
 }
 
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t& phase, const AtomRec* __restrict__ srt,
-                                        const int* __restrict__ off, long long t1, long long s1, AtomRec& rn,
-                                        AtomRec& hn, int& endn) {
+                                        const int* __restrict__ off, int ksub, long long t1, long long s1,
+                                        AtomRec& rn, AtomRec& hn, int& endn) {
     const int tid = threadIdx.x;
     if (t1 + tid < s1) rn = srt[t1 + tid];
     if (t1 < s1) {  // the next tile's first record and the end of its cell
         hn = srt[t1];
-        endn = off[(hn.i3 + 1) * kSub];
+        endn = off[(hn.i3 + 1) * ksub];
     }
     const bool ok = tc::mbar_wait_bounded(bar, phase);
     phase ^= 1u;
@@ -119,14 +126,14 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t& phase, const At
     return !failed;
 }
 
-// Walks the sorted records [s0, s1) (cell keys ascending, off[(key + 1) kSub] = end of
+// Walks the sorted records [s0, s1) (cell keys ascending, off[(key + 1) ksub] = end of
 // the cell's records) with the whole CTA (128 threads) and writes each atom's contributions.
 // smem: TcLayout<RP, GRAD>::BYTES bytes, 16-byte aligned.  On an MMA that does not
 // complete within the bounded wait the tile's contributions are set to NaN, *err is
 // set and the CTA stops.
 template <int RP, bool GRAD, class Src>
 __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __restrict__ srt,
-                                               const int* __restrict__ off, long long s0, long long s1,
+                                               const int* __restrict__ off, int ksub, long long s0, long long s1,
                                                const double* __restrict__ shortv, double* __restrict__ contrib,
                                                uint8_t* smem, int* __restrict__ err) {
     using S = tc::Shape<RP>;
@@ -156,7 +163,7 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
     if (s0 + tid < s1) rn = srt[s0 + tid];
     if (s0 < s1) {
         hn = srt[s0];
-        endn = off[(hn.i3 + 1) * kSub];
+        endn = off[(hn.i3 + 1) * ksub];
     }
     for (long long t0 = s0; t0 < s1;) {
         const AtomRec r0 = hn;
@@ -225,7 +232,7 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
                     }
                 }
             }
-            ok = tc_wait(bar, phase, srt, off, t1, s1, rn, hn, endn);
+            ok = tc_wait(bar, phase, srt, off, ksub, t1, s1, rn, hn, endn);
             if (ok) {
 #pragma unroll
                 for (int ch = 0; ch < S::NP / 16; ++ch) {
@@ -259,7 +266,7 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
                     tc_axis2_row<RP>(P, r, true, dv2);
                     tc_issue<RP>(sA, a_saddr, b_saddr, tmem, bar, act && in2, dv2, inv);
                 }
-                ok = tc_wait(bar, phase, srt, off, t1, s1, rn, hn, endn);
+                ok = tc_wait(bar, phase, srt, off, ksub, t1, s1, rn, hn, endn);
                 if (ok) {
 #pragma unroll
                     for (int ch = 0; ch < S::NP / 16; ++ch) {
