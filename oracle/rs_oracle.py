@@ -45,7 +45,7 @@ __all__ = [
     "quat_to_rot", "rotvec_to_rot", "left_jacobian", "posed_atoms",
     "long_range_factors", "rhosvd", "RSModel", "build_model", "potential",
     "short_range", "min_distances", "energies_from_atoms", "pose_energies", "pose_gradients",
-    "coulomb_energies", "coulomb_gradients", "pgd_step", "feasible_topk",
+    "coulomb_energies", "coulomb_gradients", "pgd_step", "feasible_topk", "fd_forces",
     "FLAG_CLASH", "FLAG_OUT_OF_GRID", "tolerance_scale",
 ]
 
@@ -466,6 +466,73 @@ def pose_gradients(model: RSModel, lig_xyz, lig_q, rotvec, trans, chunk: int = 1
         gn = np.linalg.norm(qg, axis=2)
         out["T_ref"][sl] = gn.sum(axis=1)
         out["W_ref"][sl] = (gn * np.linalg.norm(ry, axis=2)).sum(axis=1)
+        out["flags"][sl], _ = _flags(model, x)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# The paper's finite-difference force (Sec. 3.3, Eq. differ_ligand) and its
+# resultants on a rigid cluster (Sec. 5.2, Eq. Field_Xcenter and Eq. Field_phi)
+# ----------------------------------------------------------------------------
+def fd_forces(model: RSModel, lig_xyz, lig_q, rotvec, trans, h: float | None = None,
+              r0: float | None = None, chunk: int = 512):
+    """Per-atom forces by the backward difference of Eq. differ_ligand and their
+    rigid-cluster resultants.
+
+    For ligand atom l at x_l and axis i:  F_{l,i} = q_l (phi(x_l) - phi(x_l - h e_i)) / h,
+    phi the RS potential (long range + short range), h the grid step unless given.
+    The quotient is taken as printed, so F_l approximates +grad_x of the energy.
+    With r_l = x_l - x0 (x0 = the ligand's geometric centre = the translation),
+    v_l = r_l / |r_l|:
+      radial part      F_rad,l = (F_l . v_l) v_l   (F_l itself when |r_l| = 0)
+      tangential part  F_tan,l = F_l - F_rad,l
+      F0   = sum_l F_rad,l                         (Eq. Field_Xcenter)
+      Fphi = sum_l (|r_l| / r0) F_tan,l            (Eq. Field_phi: each tangential
+             part moved along v_l to radius r0 and scaled to keep its moment)
+      M    = sum_l r_l x F_l                       (moment about x0; the 3-D form of
+             summing the moved tangential parts along the sphere: r0 sum_l v_l x
+             (|r_l|/r0) F_tan,l)
+    and Fsum = sum_l F_l, dE_dw = J_l(w)^T M (the rotation-vector derivative that M
+    stands for).  r0 defaults to the RMS distance of the ligand atoms from x0 (when
+    that is 0 every atom sits at x0 and Fphi = 0)."""
+    rotvec = np.asarray(rotvec, dtype=np.float64)
+    trans = np.asarray(trans, dtype=np.float64)
+    q = np.asarray(lig_q, dtype=np.float64)
+    y = ligand_frame(lig_xyz)
+    if h is None:
+        h = model.h
+    if r0 is None:
+        r0 = math.sqrt(float((y * y).sum(axis=1).mean()))
+    P, L = rotvec.shape[0], q.size
+    out = {k: np.zeros((P, 3)) for k in ("Fsum", "F0", "Fphi", "M", "dE_dw")}
+    out["E"] = np.zeros(P)
+    out["flags"] = np.zeros(P, dtype=np.uint8)
+    out["h"], out["r0"] = h, r0
+    for s0 in range(0, P, chunk):
+        sl = slice(s0, min(P, s0 + chunk))
+        ry = np.einsum("pij,lj->pli", rotvec_to_rot(rotvec[sl]), y)
+        x = ry + trans[sl][:, None, :]
+        pl, ps, _, _ = potential(model, x.reshape(-1, 3))
+        phi0 = (pl + ps).reshape(-1, L)
+        F = np.zeros(x.shape)
+        for i in range(3):
+            xs = x.copy()
+            xs[..., i] -= h
+            pl, ps, _, _ = potential(model, xs.reshape(-1, 3))
+            F[..., i] = q[None, :] * (phi0 - (pl + ps).reshape(-1, L)) / h
+        rn = np.linalg.norm(ry, axis=2)
+        at_centre = rn == 0.0
+        v = ry / np.where(at_centre, 1.0, rn)[..., None]
+        F_rad = np.where(at_centre[..., None], F, (F * v).sum(axis=2)[..., None] * v)
+        F_tan = F - F_rad
+        out["E"][sl] = (q[None, :] * phi0).sum(axis=1)
+        out["Fsum"][sl] = F.sum(axis=1)
+        out["F0"][sl] = F_rad.sum(axis=1)
+        scale = rn / r0 if r0 > 0.0 else np.zeros_like(rn)  # r0 = 0: every atom at x0
+        out["Fphi"][sl] = (scale[..., None] * F_tan).sum(axis=1)
+        M = np.cross(ry, F).sum(axis=1)
+        out["M"][sl] = M
+        out["dE_dw"][sl] = np.einsum("pji,pj->pi", left_jacobian(rotvec[sl]), M)
         out["flags"][sl], _ = _flags(model, x)
     return out
 
