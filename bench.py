@@ -47,16 +47,22 @@ def parse_args():
     ap.add_argument("--poses", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batch", "pgd", "serve"], default="step",
+    ap.add_argument("--mode", choices=["step", "batch", "pgd", "serve", "fd"], default="step",
                     help="step: the protein-scale hot-path step (default); batch: 64 uneven "
                          "pairs in one persistent graph launch vs 64 plain launches; pgd: "
                          "projected gradient descent; serve: Poisson request stream through "
-                         "the serving loop vs the plain per-request path")
+                         "the serving loop vs the plain per-request path; fd: the paper's "
+                         "finite-difference forces and rigid-cluster resultants vs the exact "
+                         "gradient on the same poses")
     ap.add_argument("--pairs", type=int, default=64)
     ap.add_argument("--pair-poses", type=int, default=10_000, help="batch: poses per pair")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--serve-n-max", type=int, default=16385, help="serve: largest grid")
+    ap.add_argument("--group-min-atoms", type=int, default=None,
+                    help="serve: pose-atoms from which a request joins the cell-grouped pipeline")
+    ap.add_argument("--group-atoms-per-cell", type=float, default=None,
+                    help="serve: pose-atoms per axis-3 cell from which a request is grouped")
     return ap.parse_args()
 
 
@@ -433,6 +439,107 @@ def run_pgd(args):
     return 0
 
 
+def _left_jacobian(w: np.ndarray) -> np.ndarray:
+    """SO(3) left Jacobian of rotation vectors (Sola et al. 2018), for comparing the
+    moment of the finite-difference forces with dE/dw; host-side analysis only."""
+    th = np.linalg.norm(w, axis=1)
+    K = np.zeros((w.shape[0], 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -w[:, 2], w[:, 1], -w[:, 0]
+    K[:, 1, 0], K[:, 2, 0], K[:, 2, 1] = w[:, 2], -w[:, 1], w[:, 0]
+    small = th < 1e-4
+    ts = np.where(small, 1.0, th)
+    B = np.where(small, 0.5 - th ** 2 / 24, (1 - np.cos(ts)) / ts ** 2)
+    C = np.where(small, 1.0 / 6 - th ** 2 / 120, (ts - np.sin(ts)) / ts ** 3)
+    return np.eye(3)[None] + B[:, None, None] * K + C[:, None, None] * (K @ K)
+
+
+def run_fd(args):
+    """The paper's finite-difference force (Eq. differ_ligand, four potential
+    evaluations per atom) with its radial/tangential resultants (Eq. Field_Xcenter,
+    Eq. Field_phi), timed beside the exact adjoint gradient on the same poses of the
+    protein-scale workload, and the relative deviation of each from the adjoint."""
+    import torch
+    from paper_2510_26611_gb300 import lib
+    dev = torch.device("cuda", 0)
+    P = args.poses
+    w, rv = workload(P, seed=1)
+    ctx = lib.Context(0)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    prm = lib.rs_params_default(n=w.n, b=w.b, sigma=w.sigma, R_l=w.R_l, tucker_cap=w.tucker_cap)
+    prot = lib.Protein(ctx, T(w.prot_xyz), T(w.prot_q), prm)
+    lx, lq, rvec, trans = T(w.lig_xyz), T(w.lig_q), T(rv), T(w.trans)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        l0 = lib.rs_stats_kernel_launches()
+        with ClockSampler(0) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                ev[i][0].record()
+                out = fn()
+                ev[i][1].record()
+            torch.cuda.synchronize()
+        launches = (lib.rs_stats_kernel_launches() - l0) // args.steps
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps, out, clk.summary(), launches
+
+    ms_fd, fd, clocks, launches_fd = timed(lambda: prot.fd_forces(lx, lq, rvec, trans))
+    ms_ex, ex, _, launches_ex = timed(lambda: prot.energies_grad(lx, lq, rvec, trans))
+    lib.rs_timing_reset()
+    lib.rs_timing_enable(2)
+    for _ in range(3):
+        prot.fd_forces(lx, lq, rvec, trans)
+    torch.cuda.synchronize()
+    kernels = {k: round(v["ms"] / 3, 4) for k, v in
+               sorted(lib.rs_timing_all().items(), key=lambda kv: -kv[1]["ms"])}
+    lib.rs_timing_enable(0)
+    fd = {k: v.cpu().numpy() for k, v in fd.items()}
+    E, gt, gw, f = (x.cpu().numpy() for x in ex)
+    ok = f == 0
+    nt = np.linalg.norm(gt, axis=1)
+    nw = np.linalg.norm(gw, axis=1)
+    rel = lambda a, b, n: np.linalg.norm(a - b, axis=1)[ok] / n[ok]
+    dw_fd = np.einsum("pji,pj->pi", _left_jacobian(rv), fd["M"])
+    yc = w.lig_xyz - w.lig_xyz.mean(axis=0)
+    r0 = float(np.sqrt((yc * yc).sum(axis=1).mean()))
+    stats = lambda e: {"median": float(np.median(e)), "p95": float(np.percentile(e, 95)), "max": float(e.max())}
+    line = {"metric": "finite-difference pose forces/s (Eq. differ_ligand + rigid-cluster resultants)",
+            "value": round(P / (ms_fd / 1e3), 3), "unit": "pose-forces/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_fd, 4),
+            "higher_is_better": True, "data": "synthetic",
+            "dtype": "f64 build, f32-pair + bf16-slice tensor-core evaluation",
+            "config": {"workload": "plain_protein: N=3000 (1.5 A lattice in a (20,14,10) A ellipsoid), "
+                                   "L=50, n=1025 on [-64,64]^3, Tucker rank <= 20, P poses (uniform "
+                                   "rotations as rotation vectors), |t| in [10,30] A; h = grid step, "
+                                   "r0 = RMS ligand radius",
+                       "poses": P, "l2": "flushed between steps (256 MiB write, outside the timed events)"},
+            "exact_adjoint": {"value": round(P / (ms_ex / 1e3), 3), "unit": "pose-gradients/s",
+                              "ms_per_step": round(ms_ex, 4), "gpu_launches": int(launches_ex)},
+            "fd_over_exact_time": round(ms_fd / ms_ex, 3),
+            "deviation_from_exact_adjoint_feasible_poses": {
+                "poses": int(ok.sum()),
+                "E_max_rel": float((np.abs(fd["E"] - E)[ok] / np.maximum(np.abs(E[ok]), 1e-300)).max()),
+                "Fsum_vs_dE_dt": stats(rel(fd["F"], gt, nt)),
+                "F0_radial_only_vs_dE_dt": stats(rel(fd["F0"], gt, nt)),
+                "JT_M_vs_dE_dw": stats(rel(dw_fd, gw, nw)),
+                # the tangential resultant read as a plain vector sum (Eq. Field_phi) against
+                # the moment it stands for: r0 |Fphi| / |M| (1 only when the moved
+                # tangential parts are parallel)
+                "r0_Fphi_over_moment": stats(r0 * np.linalg.norm(fd["Fphi"], axis=1)[ok] /
+                                             np.maximum(np.linalg.norm(fd["M"], axis=1)[ok], 1e-300)),
+            },
+            "gpu_launches": int(launches_fd), "clocks": clocks, "kernels_ms_per_call": kernels}
+    print(json.dumps(line), flush=True)
+    prot.close()
+    ctx.close()
+    return 0
+
+
 # ------------------------------------------------------------------ serving mode
 def _percentiles(x):
     x = np.asarray(x, dtype=np.float64)
@@ -461,7 +568,9 @@ def _run_served(args, lib, pool, arrivals, picks):
     submission order.  Latency = end - submit, from the library's own timestamps."""
     import queue
     import workloads as W
-    srv = lib.Server(0)
+    knobs = {k: v for k, v in (("group_min_atoms", args.group_min_atoms),
+                                ("group_atoms_per_cell", args.group_atoms_per_cell)) if v is not None}
+    srv = lib.Server(0, **knobs)
     ids = queue.Queue()
     results = []
 
@@ -586,7 +695,10 @@ def run_serve(args):
                                    "memory, factors resident (a cold phase first builds every "
                                    "pool protein once; the stream is timed after it)",
                        "offered_poses_per_s":
-                       round(args.rate * 2048, 1)},
+                       round(args.rate * 2048, 1),
+                       "grouping": {k: v for k, v in (("group_min_atoms", args.group_min_atoms),
+                                                      ("group_atoms_per_cell", args.group_atoms_per_cell))
+                                    if v is not None} or "library defaults"},
             "served": served, "plain": plain,
             "p50_ratio_plain_over_served": (round(plain["latency"]["p50_ms"] / served["latency"]["p50_ms"], 3)
                                             if served["latency"]["p50_ms"] and plain["latency"]["p50_ms"] else None),
@@ -762,6 +874,8 @@ def main():
         return run_pgd(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "fd":
+        return run_fd(args)
     return run_ours(args)
 
 

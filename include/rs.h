@@ -162,6 +162,32 @@ rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
                                double* E_out, double* dE_dt, double* dE_dw,
                                uint8_t* flags_out, int mem_flags, void* stream);
 
+/* The paper's finite-difference force and its rigid-cluster resultants, for
+ * comparison with the exact gradient of rs_energy_grad_poses.
+ *   Per atom l and axis i (Eq. differ_ligand, Sec. 3.3):
+ *     F_{l,i} = q_l (phi(x_l) - phi(x_l - h e_i)) / h,
+ *   phi the RS potential (long + short range), h the grid step when h = 0.  The
+ *   quotient is taken as printed, so F_l approximates +grad of the energy.
+ *   With r_l = R y_l (offset from the ligand centre x0 = the translation) and
+ *   v_l = r_l / |r_l|, the pose outputs are
+ *     E_out    [P]    sum_l q_l phi(x_l)
+ *     F_out    [P][3] sum_l F_l                          (compare with dE/dt)
+ *     F0_out   [P][3] sum_l (F_l . v_l) v_l              (Eq. Field_Xcenter, Sec. 5.2)
+ *     Fphi_out [P][3] sum_l (|r_l| / r0) (F_l - (F_l . v_l) v_l)   (Eq. Field_phi)
+ *     M_out    [P][3] sum_l r_l x F_l   (J_l(w)^T M compares with dE/dw)
+ *   An atom at the centre (r_l = 0) puts all of F_l into F0.  r0 = 0 takes the RMS
+ *   distance of the ligand atoms from their centre (Fphi = 0 if that is 0 too).
+ * Each pose costs four evaluations of the potential at every atom (the pose and
+ * its translations by -h e_i), on the cell-grouped path: the protein must be
+ * Tucker-reduced (RS_ERR_UNSUPPORTED otherwise).  rotvec, trans: [P][3]; h, r0 >= 0
+ * and finite (RS_ERR_INVALID otherwise); flags_out may be NULL; mem_flags and
+ * stream as for rs_energy_poses. */
+rs_status rs_fd_forces_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
+                             const double* lig_xyz, const double* lig_q, int64_t P,
+                             const double* rotvec, const double* trans, double h, double r0,
+                             double* E_out, double* F_out, double* F0_out, double* Fphi_out,
+                             double* M_out, uint8_t* flags_out, int mem_flags, void* stream);
+
 /* Constrained energy minimisation of Eq. Energy_Min (Sec. 3.4) by projected
  * gradient descent on (translation, rotation vector), `nsteps` steps for every
  * pose.  Each step: gradient g by rs_energy_grad_poses; trial poses
@@ -294,6 +320,10 @@ typedef struct rs_serve_params {
     int32_t max_inflight_launches; /* launches on the GPU at once (>= 1)                 */
     int32_t idle_wait_ms;          /* scheduler sleep when idle                          */
     int32_t inject_alloc_failures; /* test hook: fail the next k device allocations      */
+    int64_t group_min_atoms;       /* a Tucker request joins the cell-grouped pipeline when
+                                      it has at least this many pose-atoms and ...       */
+    double  group_atoms_per_cell;  /* ... at least this many per axis-3 grid cell; other
+                                      requests take the per-block kernel (both >= 0)     */
 } rs_serve_params;
 
 typedef struct rs_serve_stats {

@@ -506,6 +506,8 @@ def fd_forces(model: RSModel, lig_xyz, lig_q, rotvec, trans, h: float | None = N
     P, L = rotvec.shape[0], q.size
     out = {k: np.zeros((P, 3)) for k in ("Fsum", "F0", "Fphi", "M", "dE_dw")}
     out["E"] = np.zeros(P)
+    # scales for tolerances: sum_l |q_l phi_l|, sum_l |F_l| and sum_l |r_l| |F_l|
+    out["S_ref"], out["T_ref"], out["W_ref"] = np.zeros(P), np.zeros(P), np.zeros(P)
     out["flags"] = np.zeros(P, dtype=np.uint8)
     out["h"], out["r0"] = h, r0
     for s0 in range(0, P, chunk):
@@ -526,10 +528,14 @@ def fd_forces(model: RSModel, lig_xyz, lig_q, rotvec, trans, h: float | None = N
         F_rad = np.where(at_centre[..., None], F, (F * v).sum(axis=2)[..., None] * v)
         F_tan = F - F_rad
         out["E"][sl] = (q[None, :] * phi0).sum(axis=1)
+        out["S_ref"][sl] = np.abs(q[None, :] * phi0).sum(axis=1)
         out["Fsum"][sl] = F.sum(axis=1)
         out["F0"][sl] = F_rad.sum(axis=1)
         scale = rn / r0 if r0 > 0.0 else np.zeros_like(rn)  # r0 = 0: every atom at x0
         out["Fphi"][sl] = (scale[..., None] * F_tan).sum(axis=1)
+        fn = np.linalg.norm(F, axis=2)
+        out["T_ref"][sl] = fn.sum(axis=1)
+        out["W_ref"][sl] = (fn * rn).sum(axis=1)
         M = np.cross(ry, F).sum(axis=1)
         out["M"][sl] = M
         out["dE_dw"][sl] = np.einsum("pji,pj->pi", left_jacobian(rotvec[sl]), M)

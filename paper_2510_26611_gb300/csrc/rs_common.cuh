@@ -154,6 +154,9 @@ struct rs_ctx {
     // Per-atom arrays of the cell-grouped pose path.
     void* eval_buf = nullptr;
     size_t eval_bytes = 0;
+    // Evaluation poses of the finite-difference forces.
+    void* fd_buf = nullptr;
+    size_t fd_bytes = 0;
     // Build workspace, grown to the largest build seen (one build at a time).
     void* ws_buf = nullptr;
     size_t ws_bytes = 0;

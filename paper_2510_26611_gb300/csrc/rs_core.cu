@@ -260,6 +260,7 @@ void rs_ctx_destroy(rs_ctx* c) {
     if (c->ws_buf) cudaFree(c->ws_buf);
     if (c->pgd_buf) cudaFree(c->pgd_buf);
     if (c->eval_buf) cudaFree(c->eval_buf);
+    if (c->fd_buf) cudaFree(c->fd_buf);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

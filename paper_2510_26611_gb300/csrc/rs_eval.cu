@@ -427,3 +427,82 @@ extern "C" rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, i
     return run_poses(ctx, prot, L, lig_xyz, lig_q, P, rotvec, trans, E_out, dE_dt, dE_dw,
                      flags_out, mem_flags, stream, true);
 }
+
+// Finite-difference forces of Eq. differ_ligand and the rigid-cluster resultants of
+// Eq. Field_Xcenter / Eq. Field_phi (Tucker-reduced proteins, cell-grouped path).
+extern "C" rs_status rs_fd_forces_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L, const double* lig_xyz,
+                                        const double* lig_q, int64_t P, const double* rotvec,
+                                        const double* trans, double h, double r0, double* E_out, double* F_out,
+                                        double* F0_out, double* Fphi_out, double* M_out, uint8_t* flags_out,
+                                        int mem_flags, void* stream) {
+    using namespace rs;
+    clear_error();
+    RS_CHECK_ARG(ctx && prot, "NULL context or protein");
+    RS_CHECK_ARG(L >= 1 && L <= 4096, "L=%d out of range [1, 4096]", L);
+    RS_CHECK_ARG(P >= 0 && P <= (1LL << 29), "P=%lld out of range", (long long)P);
+    RS_CHECK_ARG(mem_flags == RS_MEM_HOST || mem_flags == RS_MEM_DEVICE, "bad mem_flags %d", mem_flags);
+    RS_CHECK_ARG(prot->device == ctx->device, "protein built on device %d, context on %d", prot->device,
+                 ctx->device);
+    RS_CHECK_ARG(std::isfinite(h) && h >= 0.0, "finite-difference step h=%g must be finite and >= 0", h);
+    RS_CHECK_ARG(std::isfinite(r0) && r0 >= 0.0, "reference radius r0=%g must be finite and >= 0", r0);
+    if (prot->view.kind != 1) {
+        set_error("finite-difference forces need a Tucker-reduced protein (tucker_cap > 0)");
+        return RS_ERR_UNSUPPORTED;
+    }
+    if (P == 0) return RS_OK;
+    RS_CHECK_ARG(lig_xyz && lig_q && rotvec && trans && E_out && F_out && F0_out && Fphi_out && M_out,
+                 "NULL input or output pointer");
+    RS_TRY_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const double hs = h > 0.0 ? h : prot->view.h;
+    RS_TRY(ensure_buffer(&ctx->lig_buf, &ctx->lig_bytes, ligand_scratch_bytes(L) + 1024));
+    LigandView lig = carve_ligand(ctx->lig_buf, L);
+    const double *d_xyz = lig_xyz, *d_q = lig_q, *d_rot = rotvec, *d_trans = trans;
+    FdOut o{E_out, flags_out, F_out, F0_out, Fphi_out, M_out};
+    if (mem_flags == RS_MEM_HOST) {
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            size_t at = off;
+            off += (bytes + 255) / 256 * 256;
+            return at;
+        };
+        const size_t o_xyz = take((size_t)L * 24), o_q = take((size_t)L * 8), o_rot = take((size_t)P * 24),
+                     o_tr = take((size_t)P * 24), o_E = take((size_t)P * 8), o_f = take((size_t)P),
+                     o_F = take((size_t)P * 96);
+        RS_TRY(ensure_buffer(&ctx->io_buf, &ctx->io_bytes, off));
+        char* b = (char*)ctx->io_buf;
+        d_xyz = (const double*)(b + o_xyz);
+        d_q = (const double*)(b + o_q);
+        d_rot = (const double*)(b + o_rot);
+        d_trans = (const double*)(b + o_tr);
+        double* F = (double*)(b + o_F);
+        o = FdOut{(double*)(b + o_E), (uint8_t*)(b + o_f), F, F + 3 * P, F + 6 * P, F + 9 * P};
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_xyz, lig_xyz, (size_t)L * 24, cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_q, lig_q, (size_t)L * 8, cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_rot, rotvec, (size_t)P * 24, cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_trans, trans, (size_t)P * 24, cudaMemcpyHostToDevice, st));
+    }
+    RS_TRY(launch_prep_ligand(L, d_xyz, d_q, (float4*)lig.y, (float2*)lig.yd, (double*)lig.y64, (double*)lig.q64, st));
+    EvalLaunch a;
+    a.prot = prot->view;
+    a.lig = lig;
+    a.rot = d_rot;
+    a.trans = d_trans;
+    a.P = P;
+    RS_TRY(ensure_buffer(&ctx->eval_buf, &ctx->eval_bytes, sorted_fd_scratch_bytes(P, L, prot->n)));
+    a.ws = ctx->eval_buf;
+    a.ws_bytes = ctx->eval_bytes;
+    const long long PC = sorted_fd_chunk_poses(a.ws_bytes, L, prot->n);
+    RS_TRY(ensure_buffer(&ctx->fd_buf, &ctx->fd_bytes, fd_pose_bytes(std::max<long long>(PC, 1))));
+    RS_TRY(launch_sorted_fd(a, hs, r0, ctx->fd_buf, o, st));
+    if (mem_flags == RS_MEM_HOST) {
+        RS_TRY_CUDA(cudaMemcpyAsync(E_out, o.E, (size_t)P * 8, cudaMemcpyDeviceToHost, st));
+        if (flags_out) RS_TRY_CUDA(cudaMemcpyAsync(flags_out, o.flags, (size_t)P, cudaMemcpyDeviceToHost, st));
+        RS_TRY_CUDA(cudaMemcpyAsync(F_out, o.F, (size_t)P * 24, cudaMemcpyDeviceToHost, st));
+        RS_TRY_CUDA(cudaMemcpyAsync(F0_out, o.F0, (size_t)P * 24, cudaMemcpyDeviceToHost, st));
+        RS_TRY_CUDA(cudaMemcpyAsync(Fphi_out, o.Fphi, (size_t)P * 24, cudaMemcpyDeviceToHost, st));
+        RS_TRY_CUDA(cudaMemcpyAsync(M_out, o.M, (size_t)P * 24, cudaMemcpyDeviceToHost, st));
+        RS_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    return RS_OK;
+}

@@ -32,6 +32,22 @@ size_t ligand_scratch_bytes(int L);
 size_t sorted_scratch_bytes(long long P, int L, int n, bool grad);
 long long sorted_chunk_poses(size_t ws_bytes, int L, int n, bool grad);
 rs_status launch_sorted(const EvalLaunch& a, bool grad, cudaStream_t st);
+// Finite-difference forces (Eq. differ_ligand) and their rigid-cluster resultants
+// (Eq. Field_Xcenter, Eq. Field_phi) of a.P poses given by rotation vectors (a.rot)
+// on the cell-grouped path; a.ws/a.ws_bytes as for launch_sorted (sized by
+// sorted_fd_scratch_bytes), vbuf: fd_pose_bytes(sorted_fd_chunk_poses(...)) bytes.
+struct FdOut {
+    double* E;
+    uint8_t* flags;  // may be NULL
+    double* F;       // [P][3] sum_l F_l
+    double* F0;      // [P][3] radial resultant
+    double* Fphi;    // [P][3] tangential resultant at radius r0
+    double* M;       // [P][3] sum_l r_l x F_l
+};
+long long sorted_fd_chunk_poses(size_t ws_bytes, int L, int n);
+size_t sorted_fd_scratch_bytes(long long P, int L, int n);
+size_t fd_pose_bytes(long long PC);
+rs_status launch_sorted_fd(const EvalLaunch& a, double h, double r0, void* vbuf, const FdOut& o, cudaStream_t st);
 LigandView carve_ligand(void* base, int L);
 
 }  // namespace rs

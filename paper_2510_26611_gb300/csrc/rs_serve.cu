@@ -480,7 +480,7 @@ constexpr long long kServeChunkAtoms = 1LL << 21;
 // serves many atoms and the pipeline's launches are amortised); other requests take
 // the per-block kernel (measured faster for 2048-pose requests).
 constexpr double kDenseAtomsPerCell = 64.0;
-constexpr double kDenseMinAtoms = 1048576.0;
+constexpr long long kDenseMinAtoms = 1LL << 20;
 
 template <int RP, int NT>
 rs_status launch_group(const PairDesc* d_desc, const BatchItem* d_items, int nitems, int* d_counter,
@@ -592,7 +592,8 @@ void launch(rs_server* S, std::vector<Request*>& ready, int si) {
         if (status != RS_OK) break;
         std::vector<int> dense, sparse;
         for (int i : g.second)
-            ((double)desc[i].P * desc[i].lig.L >= std::max(kDenseMinAtoms, kDenseAtomsPerCell * desc[i].prot.n)
+            ((double)desc[i].P * desc[i].lig.L >=
+                     std::max((double)S->prm.group_min_atoms, S->prm.group_atoms_per_cell * desc[i].prot.n)
                  ? dense
                  : sparse)
                 .push_back(i);
@@ -814,6 +815,8 @@ void rs_serve_params_default(rs_serve_params* p) {
     p->max_inflight_launches = 2;
     p->idle_wait_ms = 2;
     p->inject_alloc_failures = 0;
+    p->group_min_atoms = rs::kDenseMinAtoms;
+    p->group_atoms_per_cell = rs::kDenseAtomsPerCell;
 }
 
 rs_status rs_serve_create(int device, const rs_serve_params* prm, rs_server** out) {
@@ -828,6 +831,8 @@ rs_status rs_serve_create(int device, const rs_serve_params* prm, rs_server** ou
     RS_CHECK_ARG(p.max_inflight_launches >= 1 && p.max_inflight_launches <= 8,
                  "rs_serve_create: max_inflight_launches must be in [1, 8]");
     RS_CHECK_ARG(p.inject_alloc_failures >= 0, "rs_serve_create: inject_alloc_failures < 0");
+    RS_CHECK_ARG(p.group_min_atoms >= 0 && p.group_atoms_per_cell >= 0.0,
+                 "rs_serve_create: negative grouping threshold");
     rs_ctx* ctx = nullptr;
     rs_ctx* bctx = nullptr;
     RS_TRY(rs_ctx_create(device, &ctx));

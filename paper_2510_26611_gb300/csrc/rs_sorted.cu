@@ -325,6 +325,39 @@ unsigned atoms_grid(long long M) {
     return (unsigned)std::max<long long>(1, std::min<long long>(need, resident));
 }
 
+// Per-atom contributions of the pc poses whose setups are in s.ps: short range and
+// vdW, cell keys, key scan, scatter and the W form (into s.contrib and s.pflag).
+template <bool GRAD>
+rs_status sorted_chunk_contrib(const EvalLaunch& a, const SortedScratch& s, int pc, cudaStream_t st) {
+    const int L = a.lig.L, n = a.prot.n;
+    const long long M = (long long)pc * L;
+    RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)n * kSub * 4, st));
+    {
+        const unsigned grid = atoms_grid<GRAD>(M);
+        int dev = 0;
+        RS_TRY_CUDA(cudaGetDevice(&dev));
+        unsigned long long* ctr = short_counters(dev, GRAD);
+        if (!ctr) {
+            set_error("sorted pose path: no counters on device %d", dev);
+            return RS_ERR_CUDA;
+        }
+        ::rs::KernelTimer kt__(GRAD ? "k_sorted_atoms_grad" : "k_sorted_atoms", st, 0.0, true, a.events);
+        k_sorted_atoms<GRAD><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag, s.rec,
+                                                                    s.shortv, s.count, ctr);
+    }
+    {
+        ::rs::KernelTimer kt__("k_key_scan", st, 0.0, false, a.events);
+        launch_key_scan(n * kSub, s.count, s.bsum, s.off, st);
+        note_launch(2);  // three kernels under one timer
+    }
+    {
+        ::rs::KernelTimer kt__("k_sorted_scatter", st, 0.0, false, a.events);
+        k_sorted_scatter<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, kSub, s.rec, s.off, s.srt);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
+    return dispatch_sorted_wform<GRAD>(a, s, M, st);
+}
+
 template <bool GRAD>
 rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
     const int L = a.lig.L, n = a.prot.n;
@@ -336,38 +369,13 @@ rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
     constexpr int NC = GRAD ? 7 : 1;
     for (long long p0 = 0; p0 < a.P; p0 += PC) {
         const int pc = (int)std::min<long long>(PC, a.P - p0);
-        const long long M = (long long)pc * L;
         SortedScratch s = carve(a.ws, pc, L, n, GRAD);
-        RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)n * kSub * 4, st));
         {
             ::rs::KernelTimer kt__("k_sorted_poses", st, 0.0, false, a.events);
             k_sorted_poses<<<(pc + 127) / 128, 128, 0, st>>>(a.prot, a.rot, a.trans, p0, pc, GRAD, a.skip, s.ps,
                                                               s.pflag);
         }
-        {
-            const unsigned grid = atoms_grid<GRAD>(M);
-            int dev = 0;
-            RS_TRY_CUDA(cudaGetDevice(&dev));
-            unsigned long long* ctr = short_counters(dev, GRAD);
-            if (!ctr) {
-                set_error("sorted pose path: no counters on device %d", dev);
-                return RS_ERR_CUDA;
-            }
-            ::rs::KernelTimer kt__(GRAD ? "k_sorted_atoms_grad" : "k_sorted_atoms", st, 0.0, true, a.events);
-            k_sorted_atoms<GRAD><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag, s.rec,
-                                                                        s.shortv, s.count, ctr);
-        }
-        {
-            ::rs::KernelTimer kt__("k_key_scan", st, 0.0, false, a.events);
-            launch_key_scan(n * kSub, s.count, s.bsum, s.off, st);
-            note_launch(2);  // three kernels under one timer
-        }
-        {
-            ::rs::KernelTimer kt__("k_sorted_scatter", st, 0.0, false, a.events);
-            k_sorted_scatter<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, kSub, s.rec, s.off, s.srt);
-        }
-        RS_TRY_CUDA(cudaGetLastError());
-        RS_TRY(dispatch_sorted_wform<GRAD>(a, s, M, st));
+        RS_TRY(sorted_chunk_contrib<GRAD>(a, s, pc, st));
         {
             ::rs::KernelTimer kt__("k_sorted_reduce", st, 0.0, false, a.events);
             k_sorted_reduce<NC><<<(unsigned)((pc * 32LL + 255) / 256), 256, 0, st>>>(
@@ -376,6 +384,114 @@ rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
         RS_TRY_CUDA(cudaGetLastError());
     }
     return RS_OK;
+}
+
+// ------------------------------------------------------------------ FD forces
+// The backward differences of Eq. differ_ligand need the potential at x_l and at
+// x_l - h e_i (i = 1..3) for every atom l.  Those points are the atoms of the same
+// rigid ligand under four translations of the pose, so each pose becomes four
+// evaluation poses (k = 0: the pose; k = i: translation t - h e_i) and the chunk
+// pipeline above gives the charge-weighted potentials q_l phi at all of them.
+
+// Evaluation poses v = 4 (p - p0) + k of the chunk's poses p0 .. p0 + pc - 1.
+__global__ void k_fd_expand(const double* __restrict__ rot, const double* __restrict__ trans, long long p0, int pc,
+                            double h, double* __restrict__ vrot, double* __restrict__ vtrans) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= 4 * pc) return;
+    const long long p = p0 + (v >> 2);
+    const int k = v & 3;
+    for (int a = 0; a < 3; ++a) {
+        vrot[3 * v + a] = rot[3 * p + a];
+        vtrans[3 * v + a] = k == a + 1 ? trans[3 * p + a] - h : trans[3 * p + a];
+    }
+}
+
+// r0 of Eq. Field_phi: the given radius, or (r0 = 0) the RMS distance of the
+// ligand atoms from their centre.  One warp.
+__global__ void k_fd_radius(LigandView lig, double r0, double* __restrict__ out) {
+    double s = 0.0;
+    for (int j = threadIdx.x; j < lig.L; j += 32) {
+        const double* y = lig.y64 + 3 * (size_t)j;
+        s = fma(y[2], y[2], fma(y[1], y[1], y[0] * y[0])) + s;
+    }
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *out = r0 > 0.0 ? r0 : sqrt(s / lig.L);
+}
+
+// One warp per pose: per atom F_l = (c_0 - c_i) / h from the contributions
+// c = q_l phi of its four evaluation poses (Eq. differ_ligand), the split of F_l
+// along v_l = r_l / |r_l| (r_l = R y_l), and the pose sums
+//   E, Fsum = sum F_l, F0 = sum of the radial parts (Eq. Field_Xcenter),
+//   Fphi = sum (|r_l| / r0) x tangential part (Eq. Field_phi), M = sum r_l x F_l.
+// The differences c_0 - c_i cancel most of their operands' digits and are taken in
+// FP64 (as is E); the quotients keep ~2^-24 of F_l in FP32, and the split and the
+// vector sums run in FP32 (FP64 throughput is a small fraction of FP32's here).
+__global__ void k_fd_reduce(const PoseSetup* __restrict__ ps, int pc, LigandView lig, long long p0,
+                            const double* __restrict__ contrib, const int* __restrict__ pflag, double inv_h,
+                            const double* __restrict__ r0p, FdOut o) {
+    const int lane = threadIdx.x & 31;
+    const long long pl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (pl >= pc) return;
+    const int L = lig.L;
+    const PoseSetup& q = ps[4 * pl];
+    const double r0 = *r0p;
+    const float inv_r0 = r0 > 0.0 ? (float)(1.0 / r0) : 0.f;
+    const double* c0 = contrib + (size_t)(4 * pl) * L;
+    double E = 0.0;
+    float s[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) s[c] = 0.f;
+    for (int j = lane; j < L; j += 32) {
+        const double e0 = c0[j];
+        float F[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) F[i] = (float)((e0 - c0[(size_t)(i + 1) * L + j]) * inv_h);
+        const float4 y = lig.y[j];
+        float r[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) r[a] = fmaf(q.Rf[3 * a + 2], y.z, fmaf(q.Rf[3 * a + 1], y.y, q.Rf[3 * a] * y.x));
+        const float rn = sqrtf(fmaf(r[2], r[2], fmaf(r[1], r[1], r[0] * r[0])));
+        float Fr[3];
+        if (rn > 0.f) {
+            const float ir = 1.f / rn;
+            const float v0 = r[0] * ir, v1 = r[1] * ir, v2 = r[2] * ir;
+            const float d = fmaf(F[2], v2, fmaf(F[1], v1, F[0] * v0));
+            Fr[0] = d * v0;
+            Fr[1] = d * v1;
+            Fr[2] = d * v2;
+        } else {
+            Fr[0] = F[0];
+            Fr[1] = F[1];
+            Fr[2] = F[2];
+        }
+        const float sc = rn * inv_r0;
+        E += e0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            s[a] += F[a];
+            s[3 + a] += Fr[a];
+            s[6 + a] = fmaf(sc, F[a] - Fr[a], s[6 + a]);
+        }
+        s[9] += r[1] * F[2] - r[2] * F[1];
+        s[10] += r[2] * F[0] - r[0] * F[2];
+        s[11] += r[0] * F[1] - r[1] * F[0];
+    }
+    E = warp_sum(E);
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+    if (lane == 0) {
+        const long long p = p0 + pl;
+        o.E[p] = E;
+        if (o.flags) o.flags[p] = (uint8_t)pflag[4 * pl];
+        for (int a = 0; a < 3; ++a) {
+            o.F[3 * p + a] = s[a];
+            o.F0[3 * p + a] = s[3 + a];
+            o.Fphi[3 * p + a] = s[6 + a];
+            o.M[3 * p + a] = s[9 + a];
+        }
+    }
 }
 
 }  // namespace
@@ -400,6 +516,53 @@ size_t sorted_scratch_bytes(long long P, int L, int n, bool grad) {
 rs_status launch_sorted(const EvalLaunch& a, bool grad, cudaStream_t st) {
     if (a.P <= 0) return RS_OK;
     return grad ? run_sorted<true>(a, st) : run_sorted<false>(a, st);
+}
+
+long long sorted_fd_chunk_poses(size_t ws_bytes, int L, int n) { return sorted_chunk_poses(ws_bytes, L, n, false) / 4; }
+
+size_t sorted_fd_scratch_bytes(long long P, int L, int n) {
+    return sorted_scratch_bytes(4 * std::max<long long>(P, 1), L, n, false);
+}
+
+size_t fd_pose_bytes(long long PC) { return (size_t)PC * 4 * 3 * 8 * 2 + 256; }
+
+rs_status launch_sorted_fd(const EvalLaunch& a, double h, double r0, void* vbuf, const FdOut& o, cudaStream_t st) {
+    if (a.P <= 0) return RS_OK;
+    const int L = a.lig.L, n = a.prot.n;
+    const long long PC = sorted_fd_chunk_poses(a.ws_bytes, L, n);
+    if (PC < 1) {
+        set_error("finite-difference forces: scratch of %zu bytes too small", a.ws_bytes);
+        return RS_ERR_INVALID;
+    }
+    double* vrot = (double*)vbuf;
+    double* vtrans = vrot + PC * 12;
+    double* r0d = vtrans + PC * 12;
+    {
+        ::rs::KernelTimer kt__("k_fd_radius", st, 0.0, false, a.events);
+        k_fd_radius<<<1, 32, 0, st>>>(a.lig, r0, r0d);
+    }
+    for (long long p0 = 0; p0 < a.P; p0 += PC) {
+        const int pc = (int)std::min<long long>(PC, a.P - p0);
+        const int pv = 4 * pc;
+        SortedScratch s = carve(a.ws, pv, L, n, false);
+        {
+            ::rs::KernelTimer kt__("k_fd_expand", st, 0.0, false, a.events);
+            k_fd_expand<<<(pv + 127) / 128, 128, 0, st>>>(a.rot, a.trans, p0, pc, h, vrot, vtrans);
+        }
+        {
+            ::rs::KernelTimer kt__("k_sorted_poses", st, 0.0, false, a.events);
+            k_sorted_poses<<<(pv + 127) / 128, 128, 0, st>>>(a.prot, vrot, vtrans, 0, pv, true, nullptr, s.ps,
+                                                              s.pflag);
+        }
+        RS_TRY(sorted_chunk_contrib<false>(a, s, pv, st));
+        {
+            ::rs::KernelTimer kt__("k_fd_reduce", st, 0.0, false, a.events);
+            k_fd_reduce<<<(unsigned)((pc * 32LL + 255) / 256), 256, 0, st>>>(s.ps, pc, a.lig, p0, s.contrib,
+                                                                              s.pflag, 1.0 / h, r0d, o);
+        }
+        RS_TRY_CUDA(cudaGetLastError());
+    }
+    return RS_OK;
 }
 
 }  // namespace rs

@@ -82,7 +82,8 @@ class rs_result(C.Structure):
 class rs_serve_params(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_queue", C.c_int32),
                 ("max_inflight_launches", C.c_int32), ("idle_wait_ms", C.c_int32),
-                ("inject_alloc_failures", C.c_int32)]
+                ("inject_alloc_failures", C.c_int32), ("group_min_atoms", C.c_int64),
+                ("group_atoms_per_cell", C.c_double)]
 
 
 class rs_serve_stats(C.Structure):
@@ -110,6 +111,8 @@ def _load() -> C.CDLL:
         "rs_energy_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
         "rs_energy_grad_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp, C.c_int, vp]),
         "rs_energy_poses_noalloc": (st, [vp, i32, vp, vp, i64, vp, vp, vp, vp, vp]),
+        "rs_fd_forces_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, C.c_double, C.c_double, vp, vp, vp,
+                                    vp, vp, vp, C.c_int, vp]),
         "rs_pgd_run": (st, [vp, vp, i32, vp, vp, i64, vp, vp, i32, C.c_double, C.c_double, i32,
                             vp, vp, vp, vp]),
         "rs_batch_create": (st, [vp, i32, C.POINTER(rs_pair), i32, C.POINTER(vp)]),
@@ -313,6 +316,39 @@ def rs_energy_grad_poses(ctx, prot, lig_xyz, lig_q, rotvec, trans, E_out=None, d
     returns (E, dE_dt, dE_dw, flags)."""
     return _pose_call(True, ctx, prot, lig_xyz, lig_q, rotvec, trans, E_out, flags_out, dE_dt,
                       dE_dw, stream)
+
+
+def rs_fd_forces_poses(ctx, prot, lig_xyz, lig_q, rotvec, trans, h: float = 0.0, r0: float = 0.0,
+                       stream=None) -> dict:
+    """The paper's backward-difference atom forces (Eq. differ_ligand) and their
+    rigid-cluster resultants (Eq. Field_Xcenter, Eq. Field_phi) for poses given by
+    rotation vectors.  Returns a dict with E, F (sum of atom forces), F0 (radial),
+    Fphi (tangential at radius r0), M (moment about the centre) and flags, as CUDA
+    tensors when rotvec is one, numpy arrays otherwise."""
+    if _is_cuda(rotvec):
+        import torch
+        dev = rotvec.device
+        lx, lq = _dev(lig_xyz.to(dev), np.float64), _dev(lig_q.to(dev), np.float64)
+        r, t = _dev(rotvec, np.float64), _dev(trans, np.float64)
+        P = int(r.shape[0])
+        new = lambda *shape: torch.empty(shape, dtype=torch.float64, device=dev)
+        f = torch.empty(P, dtype=torch.uint8, device=dev)
+        mem, sp = RS_MEM_DEVICE, _stream_ptr(stream)
+    else:
+        lx, lq = _host(lig_xyz, np.float64), _host(lig_q, np.float64)
+        r, t = _host(rotvec, np.float64), _host(trans, np.float64)
+        P = int(r.shape[0])
+        new = lambda *shape: np.empty(shape)
+        f = np.empty(P, dtype=np.uint8)
+        mem, sp = RS_MEM_HOST, None
+    L = int(lq.shape[0])
+    if tuple(lx.shape) != (L, 3) or tuple(r.shape) != (P, 3) or tuple(t.shape) != (P, 3):
+        raise RSError(RS_ERR_INVALID, "shape mismatch in pose arguments")
+    out = {"E": new(P), "F": new(P, 3), "F0": new(P, 3), "Fphi": new(P, 3), "M": new(P, 3), "flags": f}
+    _check(_lib.rs_fd_forces_poses(ctx, prot, L, _ptr(lx), _ptr(lq), P, _ptr(r), _ptr(t), float(h), float(r0),
+                                   _ptr(out["E"]), _ptr(out["F"]), _ptr(out["F0"]), _ptr(out["Fphi"]),
+                                   _ptr(out["M"]), _ptr(f), mem, sp))
+    return out
 
 
 def rs_energy_poses_noalloc(prot, lig_xyz, lig_q, quat, trans, E_out=None, flags_out=None,
@@ -647,6 +683,9 @@ class Protein:
 
     def energies(self, lig_xyz, lig_q, quat, trans, **kw):
         return rs_energy_poses(self.ctx.handle, self.handle, lig_xyz, lig_q, quat, trans, **kw)
+
+    def fd_forces(self, lig_xyz, lig_q, rotvec, trans, **kw):
+        return rs_fd_forces_poses(self.ctx.handle, self.handle, lig_xyz, lig_q, rotvec, trans, **kw)
 
     def energies_grad(self, lig_xyz, lig_q, rotvec, trans, **kw):
         return rs_energy_grad_poses(self.ctx.handle, self.handle, lig_xyz, lig_q, rotvec, trans, **kw)
