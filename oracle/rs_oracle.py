@@ -46,6 +46,7 @@ __all__ = [
     "long_range_factors", "rhosvd", "RSModel", "build_model", "potential",
     "short_range", "min_distances", "energies_from_atoms", "pose_energies", "pose_gradients",
     "coulomb_energies", "coulomb_gradients", "pgd_step", "feasible_topk", "fd_forces",
+    "ppiem_directions", "contact_offsets", "ppiem_scan",
     "FLAG_CLASH", "FLAG_OUT_OF_GRID", "tolerance_scale",
 ]
 
@@ -541,6 +542,91 @@ def fd_forces(model: RSModel, lig_xyz, lig_q, rotvec, trans, h: float | None = N
         out["dE_dw"][sl] = np.einsum("pji,pj->pi", left_jacobian(rotvec[sl]), M)
         out["flags"][sl], _ = _flags(model, x)
     return out
+
+
+# ----------------------------------------------------------------------------
+# Pose scan of Algorithm PPIEM (Sec. 3.4, steps A0-A7)
+# ----------------------------------------------------------------------------
+def ppiem_directions(n_theta: int, n_phi: int) -> np.ndarray:
+    """Orbit positions of the ligand centre around the protein centre (A0, A5): unit
+    vectors at polar angles (a + 1/2) pi / n_theta and azimuths 2 pi b / n_phi,
+    index a * n_phi + b."""
+    th = (np.arange(n_theta) + 0.5) * math.pi / n_theta
+    ph = np.arange(n_phi) * 2.0 * math.pi / n_phi
+    T, F = np.meshgrid(th, ph, indexing="ij")
+    return np.stack([np.sin(T) * np.cos(F), np.sin(T) * np.sin(F), np.cos(T)], axis=-1).reshape(-1, 3)
+
+
+def contact_offsets(prot_xyz, sigma: float, lig_xyz, quat, x_P, u):
+    """Step A3: the ligand (rotated by quat about its centre) approaches the protein
+    along the line x_P + s u from s = +inf; the result is the first s at which some
+    ligand-protein distance reaches sigma, i.e. the largest upper end of the
+    intervals {s : |x_P + s u + R y_j - x_m| < sigma} over all atom pairs:
+      w = x_m - x_P - R y_j,  c = u . w,  q = |w|^2 - c^2 (squared distance of x_m
+      from atom j's line),  s_jm = c + sqrt(sigma^2 - q)  for q < sigma^2.
+    Brute force over all pairs; -inf where no pair blocks.  quat (P, 4), u (P, 3)."""
+    prot = np.asarray(prot_xyz, np.float64)
+    y = ligand_frame(lig_xyz)
+    R = quat_to_rot(quat)
+    u = np.asarray(u, np.float64)
+    P = u.shape[0]
+    out = np.full(P, -np.inf)
+    s2 = sigma * sigma
+    for p in range(P):
+        ry = R[p] @ y.T                                   # (3, L)
+        w = prot[:, None, :] - (np.asarray(x_P)[None, None, :] + ry.T[None, :, :])   # (N, L, 3)
+        c = w @ u[p]
+        q = (w * w).sum(axis=2) - c * c
+        hit = q < s2
+        if hit.any():
+            out[p] = (c[hit] + np.sqrt(s2 - q[hit])).max()
+    return out
+
+
+def ppiem_scan(model: RSModel, lig_xyz, lig_q, quats, n_theta: int, n_phi: int, x_P=None,
+               margin: float = 1e-6):
+    """Steps A2-A6 of Algorithm PPIEM for every orbit direction u_d (A5) and every
+    self-rotation q_r (A4): the contact offset s*_dr (A3), the pose
+    (q_r, x_P + (s*_dr + margin sigma) u_d) just outside contact, its energy and flags.
+    A6 reads as: per direction the lowest feasible energy over the self-rotations
+    (ties: lowest r), then the directions whose lowest energy is a local minimum over
+    their grid neighbours (a +- 1 in theta without wrap, b +- 1 in phi with wrap;
+    ties broken by the lower direction index).  x_P defaults to the protein's
+    geometric centre (A2).  A direction with no contact has s* = -inf, energy +inf
+    and flag 4."""
+    quats = np.asarray(quats, np.float64)
+    U = ppiem_directions(n_theta, n_phi)
+    D, Rn = U.shape[0], quats.shape[0]
+    if x_P is None:
+        x_P = model.prot_xyz.mean(axis=0)
+    x_P = np.asarray(x_P, np.float64)
+    qq = np.tile(quats, (D, 1))
+    uu = np.repeat(U, Rn, axis=0)
+    s = contact_offsets(model.prot_xyz, model.sigma, lig_xyz, qq, x_P, uu)
+    E = np.full(D * Rn, np.inf)
+    flags = np.full(D * Rn, 4, dtype=np.uint8)
+    ok = np.isfinite(s)
+    if ok.any():
+        t = x_P[None, :] + (s[ok] + margin * model.sigma)[:, None] * uu[ok]
+        ev = pose_energies(model, lig_xyz, lig_q, qq[ok], t)
+        E[ok], flags[ok] = ev["E"], ev["flags"]
+    E2, F2 = E.reshape(D, Rn), flags.reshape(D, Rn)
+    Ef = np.where(F2 == 0, E2, np.inf)
+    best = np.argmin(Ef, axis=1)                         # first index among equal minima
+    E_best = Ef[np.arange(D), best]
+    best = np.where(np.isfinite(E_best), best, -1)
+    is_min = np.zeros(D, dtype=bool)
+    for a in range(n_theta):
+        for b in range(n_phi):
+            d = a * n_phi + b
+            if not np.isfinite(E_best[d]):
+                continue
+            nbs = [a2 * n_phi + b for a2 in (a - 1, a + 1) if 0 <= a2 < n_theta]
+            nbs += [a * n_phi + (b - 1) % n_phi, a * n_phi + (b + 1) % n_phi]
+            is_min[d] = all(E_best[d] < E_best[e] or (E_best[d] == E_best[e] and d < e)
+                            for e in nbs if e != d)
+    return {"dirs": U, "s": s.reshape(D, Rn), "E": E2, "flags": F2, "E_best": E_best,
+            "rot_best": best, "is_min": is_min, "x_P": x_P}
 
 
 # ----------------------------------------------------------------------------

@@ -27,7 +27,7 @@ import numpy as np
 __all__ = [
     "Workload", "ball_uniform", "mixed_charges", "shoemake_quaternions",
     "shell_translations", "ellipsoid_lattice", "sphere_lattice",
-    "plain_small", "plain_protein", "batch_pairs", "pgd_start", "tiny",
+    "plain_small", "plain_protein", "batch_pairs", "pgd_start", "tiny", "euler_grid_quaternions",
     "random_rotvecs", "serve_pool", "serve_request", "poisson_arrivals", "WORKLOADS",
 ]
 
@@ -270,6 +270,31 @@ def serve_request(rng: np.random.Generator, prot: dict, P: int = 2048) -> dict:
     return {"lig_xyz": ball_uniform(rng, L, r_l), "lig_q": rng.normal(0.0, 0.3, L),
             "quat": shoemake_quaternions(rng, P),
             "trans": shell_translations(rng, P, prot["r_p"], prot["r_p"] + 2.0 * r_l + 3.0)}
+
+
+def euler_grid_quaternions(m_L: int) -> np.ndarray:
+    """Self-rotations of the ligand for a pose scan with angular step 2 pi / m_L
+    (m_L even): ZYZ Euler angles alpha, gamma in {2 pi i / m_L} and beta at the
+    midpoints (k + 1/2) 2 pi / m_L of [0, pi]; m_L^3 / 2 unit quaternions (w, x, y, z),
+    alpha slowest."""
+    if m_L < 2 or m_L % 2:
+        raise ValueError("m_L must be even and >= 2")
+    step = 2.0 * math.pi / m_L
+    out = []
+    for i in range(m_L):
+        for k in range(m_L // 2):
+            for g in range(m_L):
+                a, b, c = i * step, (k + 0.5) * step, g * step
+                # q = q_z(a) q_y(b) q_z(c)
+                ca, sa = math.cos(a / 2), math.sin(a / 2)
+                cb, sb = math.cos(b / 2), math.sin(b / 2)
+                cc, sc = math.cos(c / 2), math.sin(c / 2)
+                w = ca * cb * cc - sa * cb * sc
+                x = ca * sb * sc - sa * sb * cc
+                y = ca * sb * cc + sa * sb * sc
+                z = ca * cb * sc + sa * cb * cc
+                out.append((w, x, y, z))
+    return np.asarray(out, dtype=np.float64)
 
 
 def poisson_arrivals(rng: np.random.Generator, rate: float, duration: float) -> np.ndarray:
