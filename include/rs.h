@@ -188,6 +188,30 @@ rs_status rs_fd_forces_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
                              double* E_out, double* F_out, double* F0_out, double* Fphi_out,
                              double* M_out, uint8_t* flags_out, int mem_flags, void* stream);
 
+/* Pose scan of Algorithm PPIEM (Sec. 3.4, steps A0-A7).
+ *   Orbit directions (A0, A5): u_d at polar angle (a + 1/2) pi / n_theta and azimuth
+ *   2 pi b / n_phi, d = a n_phi + b (D = n_theta n_phi <= 65535).  Self-rotations (A4):
+ *   the caller's unit quaternions quats [n_rot][4] (w, x, y, z).  x_P [3]: the centre
+ *   the ligand approaches (A2); NULL takes the protein's geometric centre.
+ *   Contact (A3): for each (d, r) the ligand centre moves along x_P + s u_d from far
+ *   outside; s*_dr is the first s at which a ligand-protein distance reaches sigma,
+ *   the largest c + sqrt(sigma^2 - q) over atom pairs with q < sigma^2, where
+ *   w = x_m - x_P - R_r y_j, c = u_d . w, q = |w|^2 - c^2 (FP64; -inf if no pair
+ *   blocks).  The pose (q_r, x_P + (s*_dr + margin sigma) u_d) (margin 0: 1e-6) is
+ *   evaluated as by rs_energy_poses.
+ *   Outputs: s_out, E_out, flags_out [D][n_rot] (each may be NULL; no contact:
+ *   s = -inf, E = +inf, flag 4); E_best [D] lowest feasible energy of direction d
+ *   (+inf if none), rot_best [D] its rotation (lowest index among ties, -1 if none),
+ *   t_best [D][3] its translation; is_min [D] 1 where E_best[d] is a local minimum
+ *   over the neighbours a +- 1 (no wrap) and b +- 1 (wrapping), ties to the lower d.
+ * Device scratch ~16 D N + 100 D n_rot bytes plus the pose path's.  mem_flags and
+ * stream as for rs_energy_poses. */
+rs_status rs_ppiem_scan(rs_ctx* ctx, const rs_protein* prot, int32_t L, const double* lig_xyz,
+                        const double* lig_q, int32_t n_theta, int32_t n_phi, int32_t n_rot,
+                        const double* quats, const double* x_P, double margin, double* s_out,
+                        double* E_out, uint8_t* flags_out, double* E_best, int32_t* rot_best,
+                        double* t_best, uint8_t* is_min, int mem_flags, void* stream);
+
 /* Constrained energy minimisation of Eq. Energy_Min (Sec. 3.4) by projected
  * gradient descent on (translation, rotation vector), `nsteps` steps for every
  * pose.  Each step: gradient g by rs_energy_grad_poses; trial poses

@@ -604,12 +604,13 @@ def ppiem_scan(model: RSModel, lig_xyz, lig_q, quats, n_theta: int, n_phi: int, 
     uu = np.repeat(U, Rn, axis=0)
     s = contact_offsets(model.prot_xyz, model.sigma, lig_xyz, qq, x_P, uu)
     E = np.full(D * Rn, np.inf)
+    S_ref = np.zeros(D * Rn)      # tolerance scale sum_j |q_j phi_j| of each pose
     flags = np.full(D * Rn, 4, dtype=np.uint8)
     ok = np.isfinite(s)
     if ok.any():
         t = x_P[None, :] + (s[ok] + margin * model.sigma)[:, None] * uu[ok]
         ev = pose_energies(model, lig_xyz, lig_q, qq[ok], t)
-        E[ok], flags[ok] = ev["E"], ev["flags"]
+        E[ok], flags[ok], S_ref[ok] = ev["E"], ev["flags"], ev["S_ref"]
     E2, F2 = E.reshape(D, Rn), flags.reshape(D, Rn)
     Ef = np.where(F2 == 0, E2, np.inf)
     best = np.argmin(Ef, axis=1)                         # first index among equal minima
@@ -626,7 +627,7 @@ def ppiem_scan(model: RSModel, lig_xyz, lig_q, quats, n_theta: int, n_phi: int, 
             is_min[d] = all(E_best[d] < E_best[e] or (E_best[d] == E_best[e] and d < e)
                             for e in nbs if e != d)
     return {"dirs": U, "s": s.reshape(D, Rn), "E": E2, "flags": F2, "E_best": E_best,
-            "rot_best": best, "is_min": is_min, "x_P": x_P}
+            "rot_best": best, "is_min": is_min, "x_P": x_P, "S_ref": S_ref.reshape(D, Rn)}
 
 
 # ----------------------------------------------------------------------------

@@ -96,22 +96,28 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
                 float u0[4] = {x0.x, x0.y, x0.z, x0.w}, w0[4] = {x0n.x, x0n.y, x0n.z, x0n.w};
                 float u1[4] = {x1.x, x1.y, x1.z, x1.w}, w1[4] = {x1n.x, x1n.y, x1n.z, x1n.w};
                 float u2[4] = {x2.x, x2.y, x2.z, x2.w}, w2[4] = {x2n.x, x2n.y, x2n.z, x2n.w};
-                float s = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                float s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     float d0 = w0[u] - u0[u], d1 = w1[u] - u1[u], d2 = w2[u] - u2[u];
                     float l0 = fmaf(cf[0], d0, u0[u]);
                     float l1 = fmaf(cf[1], d1, u1[u]);
                     float l2 = fmaf(cf[2], d2, u2[u]);
+                    // the term l0 l1 l2 with both product roundings recovered by FMA,
+                    // each term summed into the pair: the rank terms cancel strongly at
+                    // close range, where FP32 partial sums lost ~1e-5 of the energy
                     float l12 = l1 * l2;
-                    s = fmaf(l0, l12, s);
+                    const float e12 = fmaf(l1, l2, -l12);
+                    const float t = l0 * l12;
+                    const float et = fmaf(l0, l12, -t);
+                    acc.add(t);
+                    acc.lo += fmaf(l0, e12, et);
                     if constexpr (GRAD) {
                         s1 = fmaf(d0, l12, s1);
                         s2 = fmaf(l0 * d1, l2, s2);
                         s3 = fmaf(l0 * l1, d2, s3);
                     }
                 }
-                acc.add(s);
                 if constexpr (GRAD) {
                     acc1.add(s1);
                     acc2.add(s2);

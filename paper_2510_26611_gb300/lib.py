@@ -113,6 +113,8 @@ def _load() -> C.CDLL:
         "rs_energy_poses_noalloc": (st, [vp, i32, vp, vp, i64, vp, vp, vp, vp, vp]),
         "rs_fd_forces_poses": (st, [vp, vp, i32, vp, vp, i64, vp, vp, C.c_double, C.c_double, vp, vp, vp,
                                     vp, vp, vp, C.c_int, vp]),
+        "rs_ppiem_scan": (st, [vp, vp, i32, vp, vp, i32, i32, i32, vp, vp, C.c_double, vp, vp, vp, vp, vp,
+                               vp, vp, C.c_int, vp]),
         "rs_pgd_run": (st, [vp, vp, i32, vp, vp, i64, vp, vp, i32, C.c_double, C.c_double, i32,
                             vp, vp, vp, vp]),
         "rs_batch_create": (st, [vp, i32, C.POINTER(rs_pair), i32, C.POINTER(vp)]),
@@ -348,6 +350,43 @@ def rs_fd_forces_poses(ctx, prot, lig_xyz, lig_q, rotvec, trans, h: float = 0.0,
     _check(_lib.rs_fd_forces_poses(ctx, prot, L, _ptr(lx), _ptr(lq), P, _ptr(r), _ptr(t), float(h), float(r0),
                                    _ptr(out["E"]), _ptr(out["F"]), _ptr(out["F0"]), _ptr(out["Fphi"]),
                                    _ptr(out["M"]), _ptr(f), mem, sp))
+    return out
+
+
+def rs_ppiem_scan(ctx, prot, lig_xyz, lig_q, quats, n_theta: int, n_phi: int, x_P=None,
+                  margin: float = 0.0, stream=None) -> dict:
+    """Pose scan of Algorithm PPIEM: contact offsets, energies and flags of every
+    (orbit direction, self-rotation) pair, the best rotation per direction and the
+    local minima over the direction grid.  CUDA tensors in, CUDA tensors out (host
+    arrays otherwise).  Keys: s, E, flags ([D, n_rot]); E_best, rot_best, t_best,
+    is_min ([D])."""
+    D = int(n_theta) * int(n_phi)
+    if _is_cuda(quats):
+        import torch
+        dev = quats.device
+        lx, lq = _dev(lig_xyz.to(dev), np.float64), _dev(lig_q.to(dev), np.float64)
+        qu = _dev(quats, np.float64)
+        xp = _dev(x_P.to(dev), np.float64) if x_P is not None else None
+        f64 = lambda *sh: torch.empty(sh, dtype=torch.float64, device=dev)
+        u8 = lambda *sh: torch.empty(sh, dtype=torch.uint8, device=dev)
+        i32 = lambda *sh: torch.empty(sh, dtype=torch.int32, device=dev)
+        mem, sp = RS_MEM_DEVICE, _stream_ptr(stream)
+    else:
+        lx, lq, qu = _host(lig_xyz, np.float64), _host(lig_q, np.float64), _host(quats, np.float64)
+        xp = _host(x_P, np.float64) if x_P is not None else None
+        f64 = lambda *sh: np.empty(sh)
+        u8 = lambda *sh: np.empty(sh, dtype=np.uint8)
+        i32 = lambda *sh: np.empty(sh, dtype=np.int32)
+        mem, sp = RS_MEM_HOST, None
+    L, R = int(lq.shape[0]), int(qu.shape[0])
+    if tuple(lx.shape) != (L, 3) or tuple(qu.shape) != (R, 4):
+        raise RSError(RS_ERR_INVALID, "shape mismatch in scan arguments")
+    out = {"s": f64(D, R), "E": f64(D, R), "flags": u8(D, R), "E_best": f64(D), "rot_best": i32(D),
+           "t_best": f64(D, 3), "is_min": u8(D)}
+    _check(_lib.rs_ppiem_scan(ctx, prot, L, _ptr(lx), _ptr(lq), int(n_theta), int(n_phi), R, _ptr(qu),
+                              _ptr(xp) if xp is not None else None, float(margin), _ptr(out["s"]),
+                              _ptr(out["E"]), _ptr(out["flags"]), _ptr(out["E_best"]), _ptr(out["rot_best"]),
+                              _ptr(out["t_best"]), _ptr(out["is_min"]), mem, sp))
     return out
 
 
@@ -683,6 +722,9 @@ class Protein:
 
     def energies(self, lig_xyz, lig_q, quat, trans, **kw):
         return rs_energy_poses(self.ctx.handle, self.handle, lig_xyz, lig_q, quat, trans, **kw)
+
+    def ppiem_scan(self, lig_xyz, lig_q, quats, n_theta, n_phi, **kw):
+        return rs_ppiem_scan(self.ctx.handle, self.handle, lig_xyz, lig_q, quats, n_theta, n_phi, **kw)
 
     def fd_forces(self, lig_xyz, lig_q, rotvec, trans, **kw):
         return rs_fd_forces_poses(self.ctx.handle, self.handle, lig_xyz, lig_q, rotvec, trans, **kw)
