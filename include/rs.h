@@ -162,6 +162,20 @@ rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
                                double* E_out, double* dE_dt, double* dE_dw,
                                uint8_t* flags_out, int mem_flags, void* stream);
 
+/* Local-box handle: scheme (C) of Sec. 3.2 (Table 1).  The Tucker potential of
+ * `parent` restricted to the grid nodes of the box [lo, hi] (Angstrom, per axis; the
+ * interpolation cells that meet the box, at most 511 per axis) and re-truncated by an
+ * HOSVD of that node tensor: per axis rank r = #{s_i > eps s_1} (r_1, r_2 <= 32).
+ * Node-tensor error <= s_1 sqrt(sum over axes of sv_tail^2) (rs_protein_get_info
+ * reports ranks, sv_tail and sv_gap of the local HOSVD).  The handle evaluates like
+ * any Tucker protein on the same grid; an atom outside the box's cells is flagged
+ * out of grid (bit 1) and its value is meaningless.  It shares the parent's
+ * short-range data: rs_protein_free on the parent is deferred until its local
+ * handles are freed (handles of one family must not be freed concurrently).
+ * RS_ERR_INVALID for a canonical or local parent, an empty box or eps not in [0, 1). */
+rs_status rs_protein_local_box(rs_ctx* ctx, rs_protein* parent, const double* lo, const double* hi,
+                               double eps, rs_protein** out);
+
 /* The paper's finite-difference force and its rigid-cluster resultants, for
  * comparison with the exact gradient of rs_energy_grad_poses.
  *   Per atom l and axis i (Eq. differ_ligand, Sec. 3.3):

@@ -46,7 +46,7 @@ __all__ = [
     "long_range_factors", "rhosvd", "RSModel", "build_model", "potential",
     "short_range", "min_distances", "energies_from_atoms", "pose_energies", "pose_gradients",
     "coulomb_energies", "coulomb_gradients", "pgd_step", "feasible_topk", "fd_forces",
-    "ppiem_directions", "contact_offsets", "ppiem_scan",
+    "ppiem_directions", "contact_offsets", "ppiem_scan", "box_cells", "local_box_model",
     "FLAG_CLASH", "FLAG_OUT_OF_GRID", "tolerance_scale",
 ]
 
@@ -264,6 +264,9 @@ class RSModel:
     V: list = field(default_factory=list)     # Tucker factors (n x r_l) x3
     beta: np.ndarray | None = None
     svals: list = field(default_factory=list)
+    # a local model (scheme C): per axis the interpolation cells [lo, hi] it covers;
+    # a point outside them is flagged out of grid
+    cells: tuple | None = None
 
     @property
     def h(self) -> float:
@@ -291,6 +294,50 @@ def build_model(prot_xyz, prot_q, n: int, b: float, sigma: float, R_l: int,
         if not keep_canonical:
             m.U, m.xi = [], None
     return m
+
+
+def box_cells(model: RSModel, lo, hi):
+    """Interpolation cells [c_lo, c_hi] per axis that cover the box [lo, hi] (A)."""
+    out = []
+    for ax in range(3):
+        c0 = int(min(max(math.floor((lo[ax] + model.b) / model.h), 0), model.n - 2))
+        c1 = int(min(max(math.ceil((hi[ax] + model.b) / model.h) - 1, c0), model.n - 2))
+        out.append((c0, c1))
+    return tuple(out)
+
+
+def local_box_model(model: RSModel, lo, hi, eps: float = 1e-7, cap: int = 32) -> RSModel:
+    """Scheme (C) of Sec. 3.2 (Table 1): the global Tucker potential restricted to the
+    grid nodes of the box [lo, hi] and re-truncated there by an HOSVD of the restricted
+    node tensor T_Pi: per axis the leading left singular vectors of its mode
+    unfolding, rank r = #{s_i > eps s_1} (at most cap), core = T_Pi projected on them.
+    The factor rows outside the box are zero; points outside its cells are flagged.
+    The node-tensor error is at most sqrt(sum over axes of the dropped s_i^2)."""
+    assert model.kind == "tucker"
+    cells = box_cells(model, lo, hi)
+    rows = [np.arange(c0, c1 + 2) for c0, c1 in cells]           # the cells' nodes
+    Vr = [model.V[ax][rows[ax]] for ax in range(3)]
+    T = np.einsum("abc,ia,jb,kc->ijk", model.beta, Vr[0], Vr[1], Vr[2], optimize=True)
+    U, svals = [], []
+    for ax in range(3):
+        M = np.moveaxis(T, ax, 0).reshape(T.shape[ax], -1)
+        Ul, sv, _ = np.linalg.svd(M, full_matrices=False)
+        r = int(np.count_nonzero(sv > eps * sv[0])) if sv[0] > 0 else 0
+        r = max(1, min(r, cap))
+        U.append(Ul[:, :r])
+        svals.append(sv)
+    core = np.einsum("ijk,ia,jb,kc->abc", T, U[0], U[1], U[2], optimize=True)
+    V = []
+    for ax in range(3):
+        F = np.zeros((model.n, U[ax].shape[1]))
+        F[rows[ax]] = U[ax]
+        V.append(F)
+    dropped = math.sqrt(sum(float((sv[U[ax].shape[1]:] ** 2).sum()) for ax, sv in enumerate(svals)))
+    out = RSModel("tucker", model.n, model.b, model.sigma, model.table, model.prot_xyz, model.prot_q,
+                  V=V, beta=core, svals=svals, cells=cells)
+    out.trunc_bound = dropped
+    out.node_tensor_norm = float(np.linalg.norm(T))
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -396,7 +443,13 @@ def _flags(model: RSModel, x: np.ndarray) -> np.ndarray:
     P, L, _ = x.shape
     flat = x.reshape(-1, 3)
     dmin = min_distances(model.prot_xyz, flat).reshape(P, L).min(axis=1)
-    inside = np.all((flat >= -model.b) & (flat <= model.b), axis=1).reshape(P, L).all(axis=1)
+    ok = (flat >= -model.b) & (flat <= model.b)
+    if model.cells is not None:
+        for ax in range(3):
+            i, _, _ = interp_weights(flat[:, ax], model.n, model.b)
+            lo, hi = model.cells[ax]
+            ok[:, ax] &= (i >= lo) & (i <= hi)
+    inside = np.all(ok, axis=1).reshape(P, L).all(axis=1)
     flags = np.zeros(P, dtype=np.uint8)
     flags[dmin < model.sigma] |= FLAG_CLASH
     flags[~inside] |= FLAG_OUT_OF_GRID

@@ -100,6 +100,10 @@ struct ProteinView {
     int nf0, nf1, nf2;
     float fo0, fo1, fo2;     // fine-grid origin
     float inv_fine;          // 1 / f
+    // a local-box handle (scheme C): its tables cover the interpolation cells
+    // [cell_lo, cell_hi] per axis only; an atom outside them counts as out of grid
+    int box;
+    int cell_lo[3], cell_hi[3];
 };
 
 // A prepared ligand on the device: coordinates about the geometric centre.
@@ -138,6 +142,11 @@ struct rs_protein {
     std::vector<void*> allocations;   // device buffers owned by the handle
     size_t device_bytes = 0;
     int subspace_steps = 0;           // Tucker build: subspace-iteration steps taken
+    // local-box handles share their parent's short-range data: the parent is freed
+    // only when it and all of its local handles have been freed
+    rs_protein* parent = nullptr;
+    int children = 0;
+    bool released = false;            // rs_protein_free called while children lived
 };
 
 struct rs_ctx {

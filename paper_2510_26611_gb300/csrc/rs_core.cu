@@ -267,10 +267,19 @@ void rs_ctx_destroy(rs_ctx* c) {
 
 void rs_protein_free(rs_protein* p) {
     if (!p) return;
+    if (p->children > 0) {  // local-box handles still read its short-range data
+        p->released = true;
+        return;
+    }
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
     for (void* a : p->allocations) cudaFree(a);
+    rs_protein* parent = p->parent;
     delete p;
+    if (parent && --parent->children == 0 && parent->released) {
+        parent->released = false;
+        rs_protein_free(parent);
+    }
 }
 
 rs_status rs_protein_get_info(const rs_protein* p, rs_protein_info* o) {

@@ -254,27 +254,35 @@ __global__ void __launch_bounds__(512) k_scan_bin(ScanView v) {
 }
 
 // One protein atom against line p (FP32 screen, FP64 value near the line's best).
-// Returns false when the walk of a front-to-back sorted cell can stop.
+// Returns false when the walk of a front-to-back sorted cell can stop.  bestf is
+// the FP64 best rounded down to FP32, so the per-pair tests stay on the FP32 pipe
+// (FP64 throughput is a small fraction of it here).
 __device__ __forceinline__ bool contact_pair(const ProteinView& P, const ScanView& v, float4 a, const float pf[3],
                                              const float uf[3], const double p[3], const double u[3], float s2,
-                                             double& best) {
+                                             float sigf, double& best, float& bestf) {
     const float w0 = a.x - pf[0], w1 = a.y - pf[1], w2 = a.z - pf[2];
     const float c = fmaf(uf[2], w2, fmaf(uf[1], w1, uf[0] * w0));
     // every candidate is <= c + sigma; the FP32 c is within 1e-3 A of the FP64 one
-    if ((double)(c + (float)v.sigma + 1e-3f) < best) return false;
+    if (c + sigf + 1e-3f < bestf) return false;
     const float wsq = fmaf(w2, w2, fmaf(w1, w1, w0 * w0));
     const float q = fmaf(-c, c, wsq);
     // FP32 error of q: a few ulps of |w|^2 + c^2 plus the coordinates' rounding
     const float band = 1e-6f * (wsq + c * c) + 1e-4f;
     if (q < s2 + band) {
         const float cand = c + sqrtf(fmaxf(s2 - q, 0.f));
-        if ((double)(cand + sqrtf(band) + 2e-3f) >= best) {
+        if (cand + sqrtf(band) + 2e-3f >= bestf) {
             // the FP64 pair, as the definition writes it
             const double4 b = P.atoms64[__float_as_int(a.w)];
             const double x0 = b.x - p[0], x1 = b.y - p[1], x2 = b.z - p[2];
             const double cc = u[0] * x0 + u[1] * x1 + u[2] * x2;
             const double qq = (x0 * x0 + x1 * x1 + x2 * x2) - cc * cc;
-            if (qq < v.sig2) best = fmax(best, cc + sqrt(v.sig2 - qq));
+            if (qq < v.sig2) {
+                const double cand64 = cc + sqrt(v.sig2 - qq);
+                if (cand64 > best) {
+                    best = cand64;
+                    bestf = __double2float_rd(best);
+                }
+            }
         }
     }
     return true;
@@ -306,12 +314,14 @@ __global__ void __launch_bounds__(kLines) k_scan_contact(ProteinView P, ScanView
     // pose's current maximum and shares its own after the first cell
     long long* kp = v.keys + (size_t)d * v.n_rot + r;
     double best = dkey_inv(*(volatile long long*)kp);
+    float bestf = __double2float_rd(best);
+    const float sigf = (float)v.sigma;
     const int* cb = v.cbeg + (size_t)d * kCellsMax * kCellsMax;
     const int* ce = v.cend + (size_t)d * kCellsMax * kCellsMax;
     if (cb[0] < 0) {
         const float4* list = v.flist + (size_t)d * v.N;
         const int cnt = v.fcount[d];
-        for (int e = 0; e < cnt; ++e) contact_pair(P, v, list[e], pf, uf, p, u, s2, best);
+        for (int e = 0; e < cnt; ++e) contact_pair(P, v, list[e], pf, uf, p, u, s2, sigf, best, bestf);
     } else {
         const double* B = v.basis + 6 * d;
         const float a1 = (float)(B[0] * o[0] + B[1] * o[1] + B[2] * o[2]);
@@ -326,8 +336,11 @@ __global__ void __launch_bounds__(kLines) k_scan_contact(ProteinView P, ScanView
             if (c1 < 0 || c2 < 0 || c1 >= pg.nc || c2 >= pg.nc) continue;
             const int c = c2 * pg.nc + c1;
             for (int e = cb[c]; e < ce[c]; ++e)
-                if (!contact_pair(P, v, list[e], pf, uf, p, u, s2, best)) break;
-            if (k == 0 && best > kNoContact) best = fmax(best, dkey_inv(atomicMax(kp, dkey(best))));
+                if (!contact_pair(P, v, list[e], pf, uf, p, u, s2, sigf, best, bestf)) break;
+            if (k == 0 && best > kNoContact) {
+                best = fmax(best, dkey_inv(atomicMax(kp, dkey(best))));
+                bestf = __double2float_rd(best);
+            }
         }
     }
     if (best > kNoContact) atomicMax(kp, dkey(best));

@@ -70,8 +70,12 @@ bool symeig_host(int n, const double* A, double* lam, double* W) {
         for (;;) {
             int m = l;
             for (; m + 1 < n; ++m) {
+                // negligible against its neighbours; after 30 sweeps also against the
+                // matrix (scaled to max |a_ij| = 1): the couplings between the (near-)zero
+                // eigenvalues of a rank-deficient matrix stay at rounding level, where
+                // the relative test never holds
                 double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-                if (std::fabs(e[m]) <= 1e-16 * dd) break;
+                if (std::fabs(e[m]) <= 1e-16 * dd || (iter > 30 && std::fabs(e[m]) <= 4e-16 * n)) break;
             }
             if (m == l) break;
             if (++iter > 60) {

@@ -115,6 +115,7 @@ def _load() -> C.CDLL:
                                     vp, vp, vp, C.c_int, vp]),
         "rs_ppiem_scan": (st, [vp, vp, i32, vp, vp, i32, i32, i32, vp, vp, C.c_double, vp, vp, vp, vp, vp,
                                vp, vp, C.c_int, vp]),
+        "rs_protein_local_box": (st, [vp, vp, vp, vp, C.c_double, C.POINTER(vp)]),
         "rs_pgd_run": (st, [vp, vp, i32, vp, vp, i64, vp, vp, i32, C.c_double, C.c_double, i32,
                             vp, vp, vp, vp]),
         "rs_batch_create": (st, [vp, i32, C.POINTER(rs_pair), i32, C.POINTER(vp)]),
@@ -351,6 +352,16 @@ def rs_fd_forces_poses(ctx, prot, lig_xyz, lig_q, rotvec, trans, h: float = 0.0,
                                    _ptr(out["E"]), _ptr(out["F"]), _ptr(out["F0"]), _ptr(out["Fphi"]),
                                    _ptr(out["M"]), _ptr(f), mem, sp))
     return out
+
+
+def rs_protein_local_box(ctx: int, parent: int, lo, hi, eps: float = 1e-7) -> int:
+    """Local-box handle of a Tucker protein (scheme C): its potential restricted to
+    the box [lo, hi] and re-truncated to lower ranks there; free with rs_protein_free."""
+    l = np.ascontiguousarray(lo, dtype=np.float64).reshape(3)
+    h = np.ascontiguousarray(hi, dtype=np.float64).reshape(3)
+    out = C.c_void_p()
+    _check(_lib.rs_protein_local_box(ctx, parent, l.ctypes.data, h.ctypes.data, float(eps), C.byref(out)))
+    return out.value
 
 
 def rs_ppiem_scan(ctx, prot, lig_xyz, lig_q, quats, n_theta: int, n_phi: int, x_P=None,
@@ -715,10 +726,14 @@ class Context:
 class Protein:
     """Owns an rs_protein built by Algorithm TEP."""
 
-    def __init__(self, ctx: Context, xyz, q, params: rs_params | None = None, stream=None):
+    def __init__(self, ctx: Context, xyz, q, params: rs_params | None = None, stream=None, handle=None):
         self.ctx = ctx
-        self.handle = rs_build_protein(ctx.handle, xyz, q, params, stream)
+        self.handle = handle if handle is not None else rs_build_protein(ctx.handle, xyz, q, params, stream)
         self.info = rs_protein_get_info(self.handle)
+
+    def local_box(self, lo, hi, eps: float = 1e-7) -> "Protein":
+        """A local-box handle (scheme C) on [lo, hi]; see rs_protein_local_box."""
+        return Protein(self.ctx, None, None, handle=rs_protein_local_box(self.ctx.handle, self.handle, lo, hi, eps))
 
     def energies(self, lig_xyz, lig_q, quat, trans, **kw):
         return rs_energy_poses(self.ctx.handle, self.handle, lig_xyz, lig_q, quat, trans, **kw)

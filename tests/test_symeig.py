@@ -43,3 +43,15 @@ def test_hard_cases():
     D = np.diag([3.0, -1.0, 2.0])
     l, W = lib.rs_symeig_host(D)
     assert np.allclose(l, [3.0, 2.0, -1.0])
+
+
+@pytest.mark.parametrize("n,r", [(73, 12), (144, 12), (40, 1)])
+def test_rank_deficient_gram(n, r):
+    # a Gram of rank r << n: most eigenvalues are (near) zero and the couplings between
+    # them shrink toward rounding level, where only an absolute deflation test ends QL
+    rng = np.random.default_rng(n + r)
+    X = rng.normal(size=(n, r)) * (10.0 ** rng.uniform(-3, 3, size=(1, r)))
+    A = X @ X.T
+    l, W = lib.rs_symeig_host(A)
+    _check(A, l, W)
+    assert np.all(np.abs(l[r:]) <= 1e-12 * l[0])
