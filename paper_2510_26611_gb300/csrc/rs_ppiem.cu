@@ -66,6 +66,9 @@ struct ScanView {
     int* cbeg;              // [D][kCellsMax^2] cell ranges in fsort
     int* cend;
     float* grid;            // [3] plane grid: half width G, cell side cs, cells per side nc
+    double* lp64;           // [n_rot L][3] line points x_P + R_r y_j (FP64)
+    float4* lp32;           // [n_rot L] the same in FP32, and R_r y_j in FP32 (.w unused)
+    float4* lo32;
 };
 
 struct PlaneGrid {
@@ -253,36 +256,53 @@ __global__ void __launch_bounds__(512) k_scan_bin(ScanView v) {
     }
 }
 
-// One protein atom against line p (FP32 screen, FP64 value near the line's best).
-// Returns false when the walk of a front-to-back sorted cell can stop.  bestf is
-// the FP64 best rounded down to FP32, so the per-pair tests stay on the FP32 pipe
-// (FP64 throughput is a small fraction of it here).
+// Line points of every (rotation, ligand atom): they do not depend on the direction.
+__global__ void k_scan_lines(ScanView v) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long long)v.n_rot * v.L) return;
+    const int r = (int)(g / v.L), j = (int)(g - (long long)r * v.L);
+    const double* R = v.rots + 9 * r;
+    const double* y = v.y64 + 3 * (size_t)j;
+    double o[3], p[3];
+    for (int a = 0; a < 3; ++a) {
+        o[a] = fma(R[3 * a + 2], y[2], fma(R[3 * a + 1], y[1], R[3 * a] * y[0]));
+        p[a] = v.xP[a] + o[a];
+        v.lp64[3 * g + a] = p[a];
+    }
+    v.lp32[g] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.f);
+    v.lo32[g] = make_float4((float)o[0], (float)o[1], (float)o[2], 0.f);
+}
+
+// One protein atom against line p.  Every candidate is <= c + sigma, and the FP32 c
+// is within 1e-3 A of the FP64 one, so a front-to-back walk of a cell stops (returns
+// false) once c + sigma + 1e-3 falls below lb, a lower bound of the line's answer.
+// The FP32 q errs by at most band (a few ulps of |w|^2 + c^2 plus the coordinates'
+// rounding), hence the FP32 candidate by at most tol = sqrt(band) + 2e-3 A.
+//   PASS 0 (FP32 only): pairs with q < sigma^2 - band block in FP64 too, so their
+//                       candidate - tol is a lower bound: lb = max of those.
+//   PASS 1: the pairs that may block (q < sigma^2 + band) and may reach lb
+//           (candidate + tol >= lb) get the FP64 value of the definition.
+template <int PASS>
 __device__ __forceinline__ bool contact_pair(const ProteinView& P, const ScanView& v, float4 a, const float pf[3],
-                                             const float uf[3], const double p[3], const double u[3], float s2,
-                                             float sigf, double& best, float& bestf) {
+                                             const float uf[3], const double* __restrict__ p, const double* u,
+                                             float s2, float sigf, float& lb, double& best) {
     const float w0 = a.x - pf[0], w1 = a.y - pf[1], w2 = a.z - pf[2];
     const float c = fmaf(uf[2], w2, fmaf(uf[1], w1, uf[0] * w0));
-    // every candidate is <= c + sigma; the FP32 c is within 1e-3 A of the FP64 one
-    if (c + sigf + 1e-3f < bestf) return false;
+    if (c + sigf + 1e-3f < lb) return false;
     const float wsq = fmaf(w2, w2, fmaf(w1, w1, w0 * w0));
     const float q = fmaf(-c, c, wsq);
-    // FP32 error of q: a few ulps of |w|^2 + c^2 plus the coordinates' rounding
     const float band = 1e-6f * (wsq + c * c) + 1e-4f;
     if (q < s2 + band) {
+        const float tol = sqrtf(band) + 2e-3f;
         const float cand = c + sqrtf(fmaxf(s2 - q, 0.f));
-        if (cand + sqrtf(band) + 2e-3f >= bestf) {
-            // the FP64 pair, as the definition writes it
+        if (PASS == 0) {
+            if (q < s2 - band) lb = fmaxf(lb, cand - tol);
+        } else if (cand + tol >= lb) {
             const double4 b = P.atoms64[__float_as_int(a.w)];
             const double x0 = b.x - p[0], x1 = b.y - p[1], x2 = b.z - p[2];
             const double cc = u[0] * x0 + u[1] * x1 + u[2] * x2;
             const double qq = (x0 * x0 + x1 * x1 + x2 * x2) - cc * cc;
-            if (qq < v.sig2) {
-                const double cand64 = cc + sqrt(v.sig2 - qq);
-                if (cand64 > best) {
-                    best = cand64;
-                    bestf = __double2float_rd(best);
-                }
-            }
+            if (qq < v.sig2) best = fmax(best, cc + sqrt(v.sig2 - qq));
         }
     }
     return true;
@@ -295,52 +315,55 @@ __global__ void __launch_bounds__(kLines) k_scan_contact(ProteinView P, ScanView
     const long long lines = (long long)v.n_rot * v.L;
     if (g >= lines) return;
     const int r = (int)(g / v.L), j = (int)(g - (long long)r * v.L);
-    const double u[3] = {v.dirs[3 * d], v.dirs[3 * d + 1], v.dirs[3 * d + 2]};
-    // line point p = x_P + R_r y_j (FP64, and FP32 for the screen)
-    double p[3], o[3];
-    {
-        const double* R = v.rots + 9 * r;
-        const double* y = v.y64 + 3 * (size_t)j;
-        for (int a = 0; a < 3; ++a) {
-            o[a] = fma(R[3 * a + 2], y[2], fma(R[3 * a + 1], y[1], R[3 * a] * y[0]));
-            p[a] = v.xP[a] + o[a];
-        }
-    }
-    const float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
+    (void)j;
+    const double* u = v.dirs + 3 * d;
+    // line point p = x_P + R_r y_j: FP64 (read only for the FP64 pairs) and FP32
+    const double* p = v.lp64 + 3 * g;
+    const float4 pl = v.lp32[g], ol = v.lo32[g];
+    const float pf[3] = {pl.x, pl.y, pl.z};
     const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
-    const float s2 = (float)v.sig2;
-    // the pose's offset is the maximum over its lines: a candidate below what another
-    // line of the pose already found cannot matter, so the walk starts from the
-    // pose's current maximum and shares its own after the first cell
+    const float s2 = (float)v.sig2, sigf = (float)v.sigma;
+    // the pose's offset is the maximum over its lines: a candidate below a lower bound
+    // of another line's answer cannot matter, so the lines of a pose share their
+    // lower bounds through the pose's key (an FP64 maximum at the end, which is never
+    // below a lower bound)
     long long* kp = v.keys + (size_t)d * v.n_rot + r;
-    double best = dkey_inv(*(volatile long long*)kp);
-    float bestf = __double2float_rd(best);
-    const float sigf = (float)v.sigma;
+    float lb = __double2float_rd(dkey_inv(*(volatile long long*)kp));
+    double best = kNoContact;
     const int* cb = v.cbeg + (size_t)d * kCellsMax * kCellsMax;
     const int* ce = v.cend + (size_t)d * kCellsMax * kCellsMax;
     if (cb[0] < 0) {
         const float4* list = v.flist + (size_t)d * v.N;
         const int cnt = v.fcount[d];
-        for (int e = 0; e < cnt; ++e) contact_pair(P, v, list[e], pf, uf, p, u, s2, sigf, best, bestf);
+        for (int e = 0; e < cnt; ++e) contact_pair<0>(P, v, list[e], pf, uf, p, u, s2, sigf, lb, best);
+        for (int e = 0; e < cnt; ++e) contact_pair<1>(P, v, list[e], pf, uf, p, u, s2, sigf, lb, best);
     } else {
+        // the line's foot in the plane grid (FP32: the cells carry a 1e-3 A margin)
         const double* B = v.basis + 6 * d;
-        const float a1 = (float)(B[0] * o[0] + B[1] * o[1] + B[2] * o[2]);
-        const float a2 = (float)(B[3] * o[0] + B[4] * o[1] + B[5] * o[2]);
+        const float a1 = fmaf((float)B[2], ol.z, fmaf((float)B[1], ol.y, (float)B[0] * ol.x));
+        const float a2 = fmaf((float)B[5], ol.z, fmaf((float)B[4], ol.y, (float)B[3] * ol.x));
         const PlaneGrid pg(v.grid);
         const int i1 = pg.idx(a1), i2 = pg.idx(a2);
         const float4* list = v.fsort + (size_t)d * v.N;
         // the line's own cell first (it usually holds the contact), then its 8 neighbours
-        for (int k = 0; k < 9; ++k) {
-            const int dd = k == 0 ? 4 : (k <= 4 ? k - 1 : k);
-            const int c1 = i1 + dd % 3 - 1, c2 = i2 + dd / 3 - 1;
-            if (c1 < 0 || c2 < 0 || c1 >= pg.nc || c2 >= pg.nc) continue;
-            const int c = c2 * pg.nc + c1;
-            for (int e = cb[c]; e < ce[c]; ++e)
-                if (!contact_pair(P, v, list[e], pf, uf, p, u, s2, sigf, best, bestf)) break;
-            if (k == 0 && best > kNoContact) {
-                best = fmax(best, dkey_inv(atomicMax(kp, dkey(best))));
-                bestf = __double2float_rd(best);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int k = 0; k < 9; ++k) {
+                const int dd = k == 0 ? 4 : (k <= 4 ? k - 1 : k);
+                const int c1 = i1 + dd % 3 - 1, c2 = i2 + dd / 3 - 1;
+                if (c1 < 0 || c2 < 0 || c1 >= pg.nc || c2 >= pg.nc) continue;
+                const int c = c2 * pg.nc + c1;
+                if (pass == 0) {
+                    for (int e = cb[c]; e < ce[c]; ++e)
+                        if (!contact_pair<0>(P, v, list[e], pf, uf, p, u, s2, sigf, lb, best)) break;
+                    if (k == 0 && lb > -INFINITY)
+                        lb = fmaxf(lb, __double2float_rd(dkey_inv(atomicMax(kp, dkey((double)lb)))));
+                } else {
+                    for (int e = cb[c]; e < ce[c]; ++e)
+                        if (!contact_pair<1>(P, v, list[e], pf, uf, p, u, s2, sigf, lb, best)) break;
+                }
             }
+            if (pass == 0 && lb > -INFINITY)
+                lb = fmaxf(lb, __double2float_rd(dkey_inv(atomicMax(kp, dkey((double)lb)))));
         }
     }
     if (best > kNoContact) atomicMax(kp, dkey(best));
@@ -467,7 +490,8 @@ extern "C" rs_status rs_ppiem_scan(rs_ctx* ctx, const rs_protein* prot, int32_t 
                  o_Eb = take((size_t)D * 8), o_rb = take((size_t)D * 4), o_tb = take((size_t)D * 24),
                  o_im = take((size_t)D), o_bas = take((size_t)D * 48), o_fs = take((size_t)D * N * 16),
                  o_cb = take((size_t)D * kCellsMax * kCellsMax * 4), o_ce = take((size_t)D * kCellsMax * kCellsMax * 4),
-                 o_grid = take(16);
+                 o_grid = take(16), o_lp64 = take((size_t)n_rot * L * 24), o_lp32 = take((size_t)n_rot * L * 16),
+                 o_lo32 = take((size_t)n_rot * L * 16);
     RS_TRY(ensure_buffer(&ctx->fd_buf, &ctx->fd_bytes, off));
     char* B = (char*)ctx->fd_buf;
     const double *d_lx = lig_xyz, *d_lq = lig_q, *d_qu = quats, *d_xin = x_P;
@@ -519,6 +543,9 @@ extern "C" rs_status rs_ppiem_scan(rs_ctx* ctx, const rs_protein* prot, int32_t 
     v.cbeg = (int*)(B + o_cb);
     v.cend = (int*)(B + o_ce);
     v.grid = (float*)(B + o_grid);
+    v.lp64 = (double*)(B + o_lp64);
+    v.lp32 = (float4*)(B + o_lp32);
+    v.lo32 = (float4*)(B + o_lo32);
     double* pq = (double*)(B + o_pq);
     double* pt = (double*)(B + o_pt);
     {
@@ -528,6 +555,11 @@ extern "C" rs_status rs_ppiem_scan(rs_ctx* ctx, const rs_protein* prot, int32_t 
     {
         ::rs::KernelTimer kt__("k_scan_filter", st, 0.0, false);
         k_scan_filter<<<(unsigned)((D * 32 + 255) / 256), 256, 0, st>>>(prot->view, v);
+    }
+    {
+        const long long lines = (long long)n_rot * L;
+        ::rs::KernelTimer kt__("k_scan_lines", st, 0.0, false);
+        k_scan_lines<<<(unsigned)((lines + 255) / 256), 256, 0, st>>>(v);
     }
     {
         const size_t smem = (size_t)kBinCap * 12;
