@@ -80,6 +80,10 @@ typedef struct rs_params {
     int32_t tucker_cap; /* 0: keep the unreduced canonical rank N*R_l; >0: RHOSVD to
                            Tucker ranks <= tucker_cap (<= 32)                          */
     double  eps_r;      /* RHOSVD keeps singular values > eps_r * s_1 (default 1e-7)  */
+    int32_t galerkin;   /* 0: collocation (factor entries are the Gaussians' values at
+                           the nodes); 1: Galerkin (their averages over the node's cell
+                           [x_i - h/2, x_i + h/2], Sec. 2, Eq. galten), canonical form
+                           only (tucker_cap = 0, else RS_ERR_UNSUPPORTED)               */
 } rs_params;
 
 /* Read-only description of a built protein potential. */
@@ -161,6 +165,17 @@ rs_status rs_energy_grad_poses(rs_ctx* ctx, const rs_protein* prot, int32_t L,
                                const double* rotvec, const double* trans,
                                double* E_out, double* dE_dt, double* dE_dw,
                                uint8_t* flags_out, int mem_flags, void* stream);
+
+/* A molecular complex against a ligand molecule (Sec. 5.1, Eq. EnergySum_Mcomplex):
+ * E_p = sum_j q_j (phi_1 + ... + phi_nmol)(x_j), each phi_i the RS potential of
+ * molecule mols[i] (each on its own grid and parameters, Tucker or canonical); a pose's
+ * flags are the OR of its flags against every molecule.  Arguments as for
+ * rs_energy_poses; 1 <= nmol <= 64.  Energies equal the sum, in molecule order, of
+ * rs_energy_poses over the molecules. */
+rs_status rs_energy_poses_complex(rs_ctx* ctx, int32_t nmol, const rs_protein* const* mols, int32_t L,
+                                  const double* lig_xyz, const double* lig_q, int64_t P,
+                                  const double* quat, const double* trans, double* E_out,
+                                  uint8_t* flags_out, int mem_flags, void* stream);
 
 /* Local-box handle: scheme (C) of Sec. 3.2 (Table 1).  The Tucker potential of
  * `parent` restricted to the grid nodes of the box [lo, hi] (Angstrom, per axis; the

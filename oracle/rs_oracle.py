@@ -47,6 +47,7 @@ __all__ = [
     "short_range", "min_distances", "energies_from_atoms", "pose_energies", "pose_gradients",
     "coulomb_energies", "coulomb_gradients", "pgd_step", "feasible_topk", "fd_forces",
     "ppiem_directions", "contact_offsets", "ppiem_scan", "box_cells", "local_box_model",
+    "complex_energies",
     "FLAG_CLASH", "FLAG_OUT_OF_GRID", "tolerance_scale",
 ]
 
@@ -208,18 +209,34 @@ def posed_atoms(lig_xyz: np.ndarray, R: np.ndarray, trans: np.ndarray) -> np.nda
 # ----------------------------------------------------------------------------
 # Long-range canonical factors (Sec. 2 Eq. Long-Range_Sum; TEP step 3)
 # ----------------------------------------------------------------------------
-def long_range_factors(prot_xyz, prot_q, table: SincTable, n: int, b: float):
+def long_range_factors(prot_xyz, prot_q, table: SincTable, n: int, b: float, galerkin: bool = False):
     """U^(l)[i, (m,k)] = exp(-t_k^2 (x_i - x_m^l)^2) over the long-range terms and
     weights xi_(m,k) = z_m a_k: the rank N*R_l canonical sum of shifted
-    long-range Gaussians (Sec. 2, Eq. Long-Range_Sum; TEP step 3)."""
+    long-range Gaussians (Sec. 2, Eq. Long-Range_Sum; TEP step 3).
+    galerkin: the entries are instead the Gaussians' averages over the node's cell
+    [x_i - h/2, x_i + h/2] (the projection of Sec. 2, Eq. galten, per axis),
+    sqrt(pi)/(2 t h) (erf(t (d + h/2)) - erf(t (d - h/2))), and 1 for t = 0."""
+    from scipy.special import erf, erfc
     x = grid_nodes(n, b)
+    h = 2.0 * b / (n - 1)
     prot_xyz = np.asarray(prot_xyz, dtype=np.float64)
     tl, al = table.t[table.is_long], table.a[table.is_long]
     N, Rl = prot_xyz.shape[0], tl.size
     U = []
     for ax in range(3):
         d = x[:, None, None] - prot_xyz[None, :, ax, None]
-        U.append(np.exp(-(tl[None, None, :] ** 2) * d * d).reshape(n, N * Rl))
+        if not galerkin:
+            U.append(np.exp(-(tl[None, None, :] ** 2) * d * d).reshape(n, N * Rl))
+            continue
+        t = tl[None, None, :]
+        ts = np.where(t > 0, t, 1.0)
+        A, B = ts * (d - 0.5 * h), ts * (d + 0.5 * h)
+        # erf(B) - erf(A) without cancellation in the tails: through erfc when both
+        # arguments have the same sign
+        diff = np.where(A >= 0, erfc(np.abs(A)) - erfc(np.abs(B)),
+                        np.where(B <= 0, erfc(np.abs(B)) - erfc(np.abs(A)), erf(B) - erf(A)))
+        avg = math.sqrt(math.pi) / (2.0 * ts * h) * diff
+        U.append(np.where(t > 0, avg, 1.0).reshape(n, N * Rl))
     xi = (np.asarray(prot_q, dtype=np.float64)[:, None] * al[None, :]).ravel()
     return U, xi
 
@@ -281,11 +298,12 @@ class RSModel:
 
 def build_model(prot_xyz, prot_q, n: int, b: float, sigma: float, R_l: int,
                 tucker_cap: int = 0, eps_r: float = 1e-7, r_min: float = 0.5,
-                tau: float = 4.0, keep_canonical: bool = False) -> RSModel:
+                tau: float = 4.0, keep_canonical: bool = False, galerkin: bool = False) -> RSModel:
     """Algorithm TEP (Sec. 3.4): sinc table, shifted long-range Gaussians,
-    optional rank reduction.  tucker_cap = 0 keeps the unreduced canonical form."""
+    optional rank reduction.  tucker_cap = 0 keeps the unreduced canonical form;
+    galerkin takes cell averages for the factor entries (collocation otherwise)."""
     table = sinc_table(b, sigma, R_l, r_min=r_min, tau=tau)
-    U, xi = long_range_factors(prot_xyz, prot_q, table, n, b)
+    U, xi = long_range_factors(prot_xyz, prot_q, table, n, b, galerkin=galerkin)
     m = RSModel("canonical", n, b, sigma, table, np.asarray(prot_xyz, np.float64),
                 np.asarray(prot_q, np.float64), U=U, xi=xi)
     if tucker_cap > 0:
@@ -487,6 +505,24 @@ def pose_energies(model: RSModel, lig_xyz, lig_q, quat, trans, chunk: int = 2048
         for k in out:
             out[k][sl] = r[k]
     return out
+
+
+def complex_energies(models, lig_xyz, lig_q, quat, trans) -> dict:
+    """A molecular complex M_1..M_{P-1} against a ligand molecule (Sec. 5.1, Eq.
+    EnergySum_Mcomplex): E_p = sum_j q_j (sum over the molecules of their RS
+    potentials)(x_j); a pose is flagged when it is flagged against any molecule."""
+    quat = np.asarray(quat, dtype=np.float64)
+    trans = np.asarray(trans, dtype=np.float64)
+    q = np.asarray(lig_q, dtype=np.float64)
+    x = posed_atoms(lig_xyz, quat_to_rot(quat), trans)
+    P, L, _ = x.shape
+    phi = np.zeros((P, L))
+    flags = np.zeros(P, dtype=np.uint8)
+    for m in models:
+        pl, ps, _, _ = potential(m, x.reshape(-1, 3))
+        phi += (pl + ps).reshape(P, L)
+        flags |= _flags(m, x)[0]
+    return {"E": (q[None, :] * phi).sum(axis=1), "S_ref": np.abs(q[None, :] * phi).sum(axis=1), "flags": flags}
 
 
 def pose_gradients(model: RSModel, lig_xyz, lig_q, rotvec, trans, chunk: int = 1024):

@@ -246,11 +246,30 @@ __global__ void k_nb_lists(int pass, int nf0, int nf1, int nf2, double fo0, doub
 }
 
 // ---------------------------------------------------- unreduced canonical factors
+// Collocation: the Gaussian's value at the node.  Galerkin (Sec. 2, Eq. galten, read as
+// the average over the node's cell): (1/h) int_{x_i-h/2}^{x_i+h/2} exp(-t^2 (x - x_m)^2) dx
+// = sqrt(pi) / (2 t h) (erf(t (d + h/2)) - erf(t (d - h/2))), d = x_i - x_m; 1 for t = 0.
+__device__ __forceinline__ double factor_entry(double t, double d, double h, int galerkin) {
+    if (!galerkin) return exp(-t * t * d * d);
+    if (t == 0.0) return 1.0;
+    const double th = t * h;
+    if (th < 1e-3) {
+        // the cell is narrow against the Gaussian: midpoint value times the average of
+        // exp(-t^2 (2 d s + s^2)) over s in [-h/2, h/2], to second order in t h
+        const double g = exp(-t * t * d * d);
+        return g * (1.0 + th * th * (2.0 * t * t * d * d - 1.0) / 12.0);
+    }
+    // erf(B) - erf(A) without cancellation in the tails (erfc when the signs agree)
+    const double A = t * (d - 0.5 * h), B = t * (d + 0.5 * h);
+    const double diff = A >= 0.0 ? erfc(A) - erfc(B) : (B <= 0.0 ? erfc(-B) - erfc(-A) : erf(B) - erf(A));
+    return 0.886226925452758014 / th * diff;
+}
+
 __global__ void k_canon_factors(int n, double b, double h, int N, int Rl,
                                 const double* __restrict__ xyz, const double* __restrict__ q,
                                 const double* __restrict__ tl, const double* __restrict__ al,
                                 int ld, float* __restrict__ F0, float* __restrict__ F1,
-                                float* __restrict__ F2) {
+                                float* __restrict__ F2, int galerkin) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (r >= ld) return;
@@ -263,11 +282,11 @@ __global__ void k_canon_factors(int n, double b, double h, int N, int Rl,
     }
     int m = r / Rl, k = r - m * Rl;
     double xi = -b + i * h;
-    double t2 = tl[k] * tl[k];
+    const double t = tl[k];
     double d0 = xi - xyz[3 * (size_t)m], d1 = xi - xyz[3 * (size_t)m + 1], d2 = xi - xyz[3 * (size_t)m + 2];
-    F0[o] = (float)exp(-t2 * d0 * d0);
-    F1[o] = (float)exp(-t2 * d1 * d1);
-    F2[o] = (float)(exp(-t2 * d2 * d2) * q[m] * al[k]);
+    F0[o] = (float)factor_entry(t, d0, h, galerkin);
+    F1[o] = (float)factor_entry(t, d1, h, galerkin);
+    F2[o] = (float)(factor_entry(t, d2, h, galerkin) * q[m] * al[k]);
 }
 
 // ------------------------------------------------------------- pair exponential
@@ -1274,7 +1293,7 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
 }
 
 static rs_status build_canonical(rs_protein* P, cudaStream_t st, const double* d_xyz,
-                                 const double* d_q, const double* d_tl, const double* d_al) {
+                                 const double* d_q, const double* d_tl, const double* d_al, int galerkin) {
     const int N = P->N, Rl = P->R_l, n = P->n;
     size_t R = (size_t)N * Rl;
     size_t ld = (R + 127) / 128 * 128;
@@ -1289,7 +1308,7 @@ static rs_status build_canonical(rs_protein* P, cudaStream_t st, const double* d
     {
         ::rs::KernelTimer kt__("k_canon_factors", st, work, true);
         k_canon_factors<<<g, kBlock, 0, st>>>(n, P->b, P->h, N, Rl, d_xyz, d_q, d_tl, d_al, (int)ld,
-                                             F[0], F[1], F[2]);
+                                             F[0], F[1], F[2], galerkin);
     }
     RS_TRY_CUDA(cudaGetLastError());
     ProteinView& v = P->view;
@@ -1725,6 +1744,11 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
     RS_CHECK_ARG(prm->n >= 3 && prm->n <= 16385, "rs_build_protein: n=%d out of range [3, 16385]", prm->n);
     RS_CHECK_ARG(prm->b > 0 && prm->sigma > 0, "rs_build_protein: b and sigma must be > 0");
     RS_CHECK_ARG(prm->tucker_cap >= 0, "rs_build_protein: tucker_cap must be >= 0");
+    RS_CHECK_ARG(prm->galerkin == 0 || prm->galerkin == 1, "rs_build_protein: galerkin=%d not 0 or 1", prm->galerkin);
+    if (prm->galerkin && prm->tucker_cap > 0) {
+        set_error("rs_build_protein: Galerkin factors are built for the canonical form only (tucker_cap = 0)");
+        return RS_ERR_UNSUPPORTED;
+    }
     RS_CHECK_ARG(mem_flags == RS_MEM_HOST || mem_flags == RS_MEM_DEVICE,
                  "rs_build_protein: bad mem_flags %d", mem_flags);
     RS_TRY_CUDA(cudaSetDevice(ctx->device));
@@ -1782,7 +1806,7 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
 
     if ((s = build_cells(P, st, d_xyz, d_q, S)) != RS_OK) return fail_out(s);
     if (prm->tucker_cap == 0) {
-        s = build_canonical(P, st, d_xyz, d_q, d_tl, d_al);
+        s = build_canonical(P, st, d_xyz, d_q, d_tl, d_al, prm->galerkin);
     } else {
         std::vector<double> cz(N);
         for (int i = 0; i < N; ++i) cz[i] = std::pow(std::fabs(hq[i]), 2.0 / 3.0);

@@ -215,6 +215,7 @@ void rs_params_default(rs_params* p) {
     p->short_tol = 1e-9;
     p->tucker_cap = 0;
     p->eps_r = 1e-7;
+    p->galerkin = 0;
 }
 
 rs_status rs_ctx_create(int device, rs_ctx** out) {

@@ -512,3 +512,100 @@ extern "C" rs_status rs_fd_forces_poses(rs_ctx* ctx, const rs_protein* prot, int
     }
     return RS_OK;
 }
+
+namespace rs {
+namespace {
+// E += E_p, flags |= flags_p (one molecule's contribution to the complex).
+__global__ void k_complex_acc(long long P, const double* __restrict__ Ep, const uint8_t* __restrict__ fp,
+                              double* __restrict__ E, uint8_t* __restrict__ F, int first) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    E[i] = first ? Ep[i] : E[i] + Ep[i];
+    F[i] = first ? fp[i] : (uint8_t)(F[i] | fp[i]);
+}
+}  // namespace
+}  // namespace rs
+
+// A molecular complex against a ligand molecule (Sec. 5.1, Eq. EnergySum_Mcomplex):
+// the pose path per molecule, summed on the device in molecule order.
+extern "C" rs_status rs_energy_poses_complex(rs_ctx* ctx, int32_t nmol, const rs_protein* const* mols, int32_t L,
+                                             const double* lig_xyz, const double* lig_q, int64_t P,
+                                             const double* quat, const double* trans, double* E_out,
+                                             uint8_t* flags_out, int mem_flags, void* stream) {
+    using namespace rs;
+    clear_error();
+    RS_CHECK_ARG(ctx && mols && nmol >= 1 && nmol <= 64, "NULL context or molecule list, or nmol=%d not in [1, 64]",
+                 nmol);
+    for (int i = 0; i < nmol; ++i) {
+        RS_CHECK_ARG(mols[i], "molecule %d is NULL", i);
+        RS_CHECK_ARG(mols[i]->device == ctx->device, "molecule %d on device %d, context on %d", i, mols[i]->device,
+                     ctx->device);
+    }
+    RS_CHECK_ARG(L >= 1 && L <= 4096, "L=%d out of range [1, 4096]", L);
+    RS_CHECK_ARG(P >= 0 && P <= 0x7fffffffLL, "P=%lld out of range", (long long)P);
+    RS_CHECK_ARG(mem_flags == RS_MEM_HOST || mem_flags == RS_MEM_DEVICE, "bad mem_flags %d", mem_flags);
+    if (P == 0) return RS_OK;
+    RS_CHECK_ARG(lig_xyz && lig_q && quat && trans && E_out, "NULL input or output pointer");
+    RS_TRY_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    RS_TRY(ensure_buffer(&ctx->lig_buf, &ctx->lig_bytes, ligand_scratch_bytes(L) + 1024));
+    LigandView lig = carve_ligand(ctx->lig_buf, L);
+    // staging: inputs (host calls), the sums, one molecule's energies and flags
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off += (bytes + 255) / 256 * 256;
+        return at;
+    };
+    const size_t o_xyz = take((size_t)L * 24), o_q = take((size_t)L * 8), o_rot = take((size_t)P * 32),
+                 o_tr = take((size_t)P * 24), o_E = take((size_t)P * 8), o_F = take((size_t)P),
+                 o_Ep = take((size_t)P * 8), o_Fp = take((size_t)P);
+    RS_TRY(ensure_buffer(&ctx->fd_buf, &ctx->fd_bytes, off));
+    char* b = (char*)ctx->fd_buf;
+    const double *d_xyz = lig_xyz, *d_q = lig_q, *d_rot = quat, *d_trans = trans;
+    double* d_E = E_out;
+    uint8_t* d_F = (uint8_t*)(b + o_F);
+    if (mem_flags == RS_MEM_DEVICE && flags_out) d_F = flags_out;
+    if (mem_flags == RS_MEM_HOST) {
+        d_xyz = (const double*)(b + o_xyz);
+        d_q = (const double*)(b + o_q);
+        d_rot = (const double*)(b + o_rot);
+        d_trans = (const double*)(b + o_tr);
+        d_E = (double*)(b + o_E);
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_xyz, lig_xyz, (size_t)L * 24, cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_q, lig_q, (size_t)L * 8, cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_rot, quat, (size_t)P * 32, cudaMemcpyHostToDevice, st));
+        RS_TRY_CUDA(cudaMemcpyAsync((void*)d_trans, trans, (size_t)P * 24, cudaMemcpyHostToDevice, st));
+    }
+    RS_TRY(launch_prep_ligand(L, d_xyz, d_q, (float4*)lig.y, (float2*)lig.yd, (double*)lig.y64, (double*)lig.q64, st));
+    double* Ep = (double*)(b + o_Ep);
+    uint8_t* Fp = (uint8_t*)(b + o_Fp);
+    for (int i = 0; i < nmol; ++i) {
+        const rs_protein* prot = mols[i];
+        EvalLaunch a;
+        a.prot = prot->view;
+        a.lig = lig;
+        a.rot = d_rot;
+        a.trans = d_trans;
+        a.P = P;
+        a.E = Ep;
+        a.flags = Fp;
+        if (prot->view.kind == 1) {
+            RS_TRY(ensure_buffer(&ctx->eval_buf, &ctx->eval_bytes, sorted_scratch_bytes(P, L, prot->n, false)));
+            a.ws = ctx->eval_buf;
+            a.ws_bytes = ctx->eval_bytes;
+        }
+        RS_TRY(launch_eval(a, false, st));
+        {
+            ::rs::KernelTimer kt__("k_complex_acc", st, 0.0, false);
+            k_complex_acc<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(P, Ep, Fp, d_E, d_F, i == 0);
+        }
+        RS_TRY_CUDA(cudaGetLastError());
+    }
+    if (mem_flags == RS_MEM_HOST) {
+        RS_TRY_CUDA(cudaMemcpyAsync(E_out, d_E, (size_t)P * 8, cudaMemcpyDeviceToHost, st));
+        if (flags_out) RS_TRY_CUDA(cudaMemcpyAsync(flags_out, d_F, (size_t)P, cudaMemcpyDeviceToHost, st));
+        RS_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    return RS_OK;
+}

@@ -43,7 +43,7 @@ class RSError(RuntimeError):
 class rs_params(C.Structure):
     _fields_ = [("n", C.c_int32), ("b", C.c_double), ("sigma", C.c_double), ("R_l", C.c_int32),
                 ("r_min", C.c_double), ("tau", C.c_double), ("short_tol", C.c_double),
-                ("tucker_cap", C.c_int32), ("eps_r", C.c_double)]
+                ("tucker_cap", C.c_int32), ("eps_r", C.c_double), ("galerkin", C.c_int32)]
 
 
 class rs_protein_info(C.Structure):
@@ -116,6 +116,7 @@ def _load() -> C.CDLL:
         "rs_ppiem_scan": (st, [vp, vp, i32, vp, vp, i32, i32, i32, vp, vp, C.c_double, vp, vp, vp, vp, vp,
                                vp, vp, C.c_int, vp]),
         "rs_protein_local_box": (st, [vp, vp, vp, vp, C.c_double, C.POINTER(vp)]),
+        "rs_energy_poses_complex": (st, [vp, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
         "rs_pgd_run": (st, [vp, vp, i32, vp, vp, i64, vp, vp, i32, C.c_double, C.c_double, i32,
                             vp, vp, vp, vp]),
         "rs_batch_create": (st, [vp, i32, C.POINTER(rs_pair), i32, C.POINTER(vp)]),
@@ -352,6 +353,34 @@ def rs_fd_forces_poses(ctx, prot, lig_xyz, lig_q, rotvec, trans, h: float = 0.0,
                                    _ptr(out["E"]), _ptr(out["F"]), _ptr(out["F0"]), _ptr(out["Fphi"]),
                                    _ptr(out["M"]), _ptr(f), mem, sp))
     return out
+
+
+def rs_energy_poses_complex(ctx, mols, lig_xyz, lig_q, quat, trans, stream=None):
+    """Energies of a ligand molecule against a complex of molecules (the sum of their
+    RS potentials, Eq. EnergySum_Mcomplex); mols: protein handles.  Returns (E, flags)
+    as CUDA tensors when quat is one, numpy arrays otherwise."""
+    arr = (C.c_void_p * len(mols))(*[int(m) for m in mols])
+    if _is_cuda(quat):
+        import torch
+        dev = quat.device
+        lx, lq = _dev(lig_xyz.to(dev), np.float64), _dev(lig_q.to(dev), np.float64)
+        r, t = _dev(quat, np.float64), _dev(trans, np.float64)
+        P = int(r.shape[0])
+        E = torch.empty(P, dtype=torch.float64, device=dev)
+        f = torch.empty(P, dtype=torch.uint8, device=dev)
+        mem, sp = RS_MEM_DEVICE, _stream_ptr(stream)
+    else:
+        lx, lq = _host(lig_xyz, np.float64), _host(lig_q, np.float64)
+        r, t = _host(quat, np.float64), _host(trans, np.float64)
+        P = int(r.shape[0])
+        E, f = np.empty(P), np.empty(P, dtype=np.uint8)
+        mem, sp = RS_MEM_HOST, None
+    L = int(lq.shape[0])
+    if tuple(lx.shape) != (L, 3) or tuple(r.shape) != (P, 4) or tuple(t.shape) != (P, 3):
+        raise RSError(RS_ERR_INVALID, "shape mismatch in pose arguments")
+    _check(_lib.rs_energy_poses_complex(ctx, len(mols), arr, L, _ptr(lx), _ptr(lq), P, _ptr(r), _ptr(t), _ptr(E),
+                                        _ptr(f), mem, sp))
+    return E, f
 
 
 def rs_protein_local_box(ctx: int, parent: int, lo, hi, eps: float = 1e-7) -> int:
