@@ -187,7 +187,11 @@ rs_status rs_energy_poses_complex(rs_ctx* ctx, int32_t nmol, const rs_protein* c
  * out of grid (bit 1) and its value is meaningless.  It shares the parent's
  * short-range data: rs_protein_free on the parent is deferred until its local
  * handles are freed (handles of one family must not be freed concurrently).
- * RS_ERR_INVALID for a canonical or local parent, an empty box or eps not in [0, 1). */
+ * RS_ERR_INVALID for a canonical or local parent, an empty box or eps not in [0, 1).
+ * A local-box handle is evaluated by rs_energy_poses, rs_energy_grad_poses, rs_pgd_run,
+ * rs_fd_forces_poses, rs_ppiem_scan and rs_energy_poses_complex (the box flags are
+ * set by a pass after the pose kernels); rs_batch_create and rs_energy_poses_noalloc
+ * return RS_ERR_UNSUPPORTED for it. */
 rs_status rs_protein_local_box(rs_ctx* ctx, rs_protein* parent, const double* lo, const double* hi,
                                double eps, rs_protein** out);
 

@@ -297,6 +297,10 @@ rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int
         const rs_pair& p = pairs[i];
         RS_CHECK_ARG(p.prot, "rs_batch_create: pair %d has no protein", i);
         RS_CHECK_ARG(p.prot->device == ctx->device, "rs_batch_create: pair %d on another device", i);
+        if (p.prot->view.box) {
+            set_error("rs_batch_create: pair %d uses a local-box handle (not batched; use rs_energy_poses)", i);
+            return RS_ERR_UNSUPPORTED;
+        }
         RS_CHECK_ARG(p.L >= 1 && p.L <= 4096, "rs_batch_create: pair %d L=%d out of range", i, p.L);
         RS_CHECK_ARG(p.P >= 0 && p.P <= 0x7fffffffLL, "rs_batch_create: pair %d P out of range", i);
         RS_CHECK_ARG(p.lig_xyz && p.lig_q && (p.P == 0 || (p.quat && p.trans && p.E_out)),

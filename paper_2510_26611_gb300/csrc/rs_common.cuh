@@ -101,7 +101,9 @@ struct ProteinView {
     float fo0, fo1, fo2;     // fine-grid origin
     float inv_fine;          // 1 / f
     // a local-box handle (scheme C): its tables cover the interpolation cells
-    // [cell_lo, cell_hi] per axis only; an atom outside them counts as out of grid
+    // [cell_lo, cell_hi] per axis only; a pose with an atom outside them is flagged out
+    // of grid by a pass after the evaluation (launch_box_flags), which keeps the test
+    // out of the pose kernels' per-atom geometry
     int box;
     int cell_lo[3], cell_hi[3];
 };

@@ -287,7 +287,51 @@ rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* 
     return RS_OK;
 }
 
+namespace {
+// One thread per pose: the atoms' cells by the pose kernels' own geometry helpers, so
+// the decision is the one their interpolation took.
+__global__ void k_box_flags(ProteinView P, LigandView lig, const double* __restrict__ rot,
+                            const double* __restrict__ trans, long long Ptot, bool rotvec,
+                            const uint8_t* __restrict__ skip, uint8_t* __restrict__ flags) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Ptot || (skip && skip[p])) return;
+    PoseSetup q;
+    setup_pose(P, rot, trans, p, rotvec, q);
+    bool out = false;
+    for (int j = 0; j < lig.L && !out; ++j) {
+        dev::F2 x[3];
+        atom_position(q, lig.yd + 3 * j, x);
+        for (int a = 0; a < 3; ++a) {
+            int ci;
+            float cf;
+            bool ins;
+            dev::axis_cell(x[a], dev::F2{P.b_h, P.b_l}, dev::F2{P.inv_h_h, P.inv_h_l}, P.n, ci, cf, ins);
+            out = out || ci < P.cell_lo[a] || ci > P.cell_hi[a];
+        }
+    }
+    if (out) flags[p] |= RS_FLAG_OUT_OF_GRID;
+}
+}  // namespace
+
+rs_status launch_box_flags(const ProteinView& P, const LigandView& lig, const double* rot, const double* trans,
+                           long long Ptot, bool rotvec, const uint8_t* skip, uint8_t* flags, cudaStream_t st) {
+    if (!P.box || !flags || Ptot <= 0) return RS_OK;
+    {
+        ::rs::KernelTimer kt__("k_box_flags", st, 0.0, false);
+        k_box_flags<<<(unsigned)((Ptot + 127) / 128), 128, 0, st>>>(P, lig, rot, trans, Ptot, rotvec, skip, flags);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
+rs_status launch_eval_paths(const EvalLaunch& a, bool grad, cudaStream_t st);
+
 rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st) {
+    RS_TRY(launch_eval_paths(a, grad, st));
+    return launch_box_flags(a.prot, a.lig, a.rot, a.trans, a.P, grad, a.skip, a.flags, st);
+}
+
+rs_status launch_eval_paths(const EvalLaunch& a, bool grad, cudaStream_t st) {
     if (a.P <= 0) return RS_OK;
     // the cell-grouped path pays six launches and a sort per chunk and one slab load
     // per (warp, cell): it is taken for batches of at least 2^17 pose-atoms that
@@ -501,6 +545,7 @@ extern "C" rs_status rs_fd_forces_poses(rs_ctx* ctx, const rs_protein* prot, int
     const long long PC = sorted_fd_chunk_poses(a.ws_bytes, L, prot->n);
     RS_TRY(ensure_buffer(&ctx->fd_buf, &ctx->fd_bytes, fd_pose_bytes(std::max<long long>(PC, 1))));
     RS_TRY(launch_sorted_fd(a, hs, r0, ctx->fd_buf, o, st));
+    RS_TRY(launch_box_flags(a.prot, a.lig, a.rot, a.trans, P, true, nullptr, o.flags, st));
     if (mem_flags == RS_MEM_HOST) {
         RS_TRY_CUDA(cudaMemcpyAsync(E_out, o.E, (size_t)P * 8, cudaMemcpyDeviceToHost, st));
         if (flags_out) RS_TRY_CUDA(cudaMemcpyAsync(flags_out, o.flags, (size_t)P, cudaMemcpyDeviceToHost, st));

@@ -26,6 +26,11 @@ struct EvalLaunch {
 rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, float2* yd, double* y64,
                              double* q64, cudaStream_t st, bool events = true);
 rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st);
+// Local-box handles: OR the out-of-grid flag into flags[p] for every pose (not skipped)
+// with an atom whose interpolation cell lies outside the handle's box (no-op for
+// other handles or NULL flags).
+rs_status launch_box_flags(const ProteinView& P, const LigandView& lig, const double* rot, const double* trans,
+                           long long Ptot, bool rotvec, const uint8_t* skip, uint8_t* flags, cudaStream_t st);
 size_t ligand_scratch_bytes(int L);
 // Cell-grouped Tucker path (rs_sorted.cu): scratch for P poses (capped at one chunk)
 // and the number of poses one chunk of ws_bytes holds.

@@ -64,6 +64,10 @@ extern "C" rs_status rs_energy_poses_noalloc(const rs_protein* prot, int32_t L,
     using namespace rs;
     clear_error();
     RS_CHECK_ARG(prot, "rs_energy_poses_noalloc: NULL protein");
+    if (prot->view.box) {
+        set_error("rs_energy_poses_noalloc: local-box handles are not supported (use rs_energy_poses)");
+        return RS_ERR_UNSUPPORTED;
+    }
     RS_CHECK_ARG(L >= 1, "rs_energy_poses_noalloc: L=%d must be >= 1", L);
     if (L > kNoAllocMaxL) {
         set_error("rs_energy_poses_noalloc: L=%d exceeds the fixed scratch limit of %d atoms",

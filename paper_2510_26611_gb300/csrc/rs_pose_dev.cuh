@@ -338,8 +338,6 @@ __device__ __forceinline__ void atom_geometry(const ProteinView& P, const Ligand
     atom_position64(q, lig.y64 + 3 * j, x64);
     for (int a = 0; a < 3; ++a)
         dev::axis_cell(x[a], F2{P.b_h, P.b_l}, F2{P.inv_h_h, P.inv_h_l}, P.n, ci[a], cf[a], ins[a]);
-    if (P.box)
-        for (int a = 0; a < 3; ++a) ins[a] = ins[a] && ci[a] >= P.cell_lo[a] && ci[a] <= P.cell_hi[a];
 }
 
 // Per-atom contributions to the pose sums from the long-range value (pair sums

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, GRAD ? 3 : 5)
 // Tensor-core W form (rs_tc_dev.cuh): CTA b walks a contiguous run of the sorted
 // records of evaluated poses.
 template <int RP, bool GRAD>
-__global__ void __launch_bounds__(tc::kTileRows, GRAD ? 3 : 4)
+__global__ void __launch_bounds__(tc::kTileRows, 4)
     k_sorted_tc(const __grid_constant__ ProteinView P, const __grid_constant__ LigandView lig,
                 const AtomRec* __restrict__ srt, const int* __restrict__ off, const double* __restrict__ shortv,
                 double* __restrict__ contrib, int* __restrict__ err) {
