@@ -213,7 +213,7 @@ int num_sms() {
 
 template <int RP, bool GRAD>
 rs_status launch_tucker(const EvalLaunch& a, cudaStream_t st) {
-    int PB = a.PB > 0 ? a.PB : std::min(128, std::max(1, 512 / a.lig.L));
+    int PB = a.PB > 0 ? a.PB : std::min(128, std::max(1, 256 / a.lig.L));  // ~256 pose-atoms per block
     size_t sm = wform_smem<RP, GRAD>(PB, a.lig.L);
     while (sm > 160 * 1024 && PB > 1) {
         PB = std::max(1, PB / 2);
