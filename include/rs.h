@@ -285,7 +285,8 @@ typedef struct rs_batch_info {
     int32_t threads;          /* per-block path: threads per CTA (first group)    */
     int32_t atoms_per_item;   /* per-block path: target atoms per item           */
     double  tune_ms;          /* device time the autotuner spent                  */
-    int32_t mode;             /* first group: 0 per-block, 1 cell-grouped         */
+    int32_t mode;             /* first group: 0 per-block, 1 cell-grouped, 2 pair
+                                 by pair through the single-pair cell-grouped path */
     int32_t warps_per_cta;    /* cell-grouped: warps per CTA of the W-form kernel */
     int64_t chunk_atoms;      /* cell-grouped: pose-atoms per chunk (at most)     */
     int32_t nchunks;          /* cell-grouped: chunks over its groups             */
@@ -296,13 +297,18 @@ typedef struct rs_batch_info {
  * multi-pair pipeline (pose-atoms of all pairs sorted by (pair, grid cell)) or one
  * persistent per-block launch runs.  autotune = 1: the path and its shape (chunk
  * size, or threads per CTA and atoms per work item) are chosen by timing the
- * candidates on all of the group's poses (this writes the output arrays; cached per
+ * candidates (the per-block shapes, the cell-grouped pipeline, and the pairs one by
+ * one through the single-pair cell-grouped path) on all of the group's poses (this
+ * writes the output arrays; cached per
  * padded rank for the process); 0: the cell-grouped pipeline; 2: the per-block
- * launch with its default shape.  Ligands are prepared now;
+ * launch with its default shape; 3: pair by pair through the single-pair path.
+ * Ligands are prepared now;
  * poses are read from the given pointers at each rs_batch_run, so a caller may
  * rewrite them in place between runs.  Device scratch: about 110 bytes per
- * pose-atom of the largest chunk (at most 2^23 pose-atoms).  Energies and flags
- * equal rs_energy_poses bit for bit. */
+ * pose-atom of the largest chunk (at most 2^23 pose-atoms).  Flags equal
+ * rs_energy_poses'; energies equal them bit for bit where both take the same W form
+ * (tensor-core or float-pair, chosen per launch from its atoms per cell) and within
+ * ~2e-8 relative otherwise. */
 rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int32_t autotune,
                           rs_batch** out);
 /* Replays the batch's graph on `stream` (NULL = the CUDA default stream). */

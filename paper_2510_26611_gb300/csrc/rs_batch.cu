@@ -31,7 +31,9 @@ namespace rs {
 namespace {
 
 // mode 0: per-block launch with `shape`; mode 1: cell-grouped pipeline with `wpb`
-// warps per W-form CTA and chunks of at most `chunk` pose-atoms.
+// warps per W-form CTA and chunks of at most `chunk` pose-atoms; mode 2: each pair on
+// its own through the single-pair cell-grouped path (what a plain call of a large
+// pair runs), one pair after the other.
 struct Choice {
     int mode;
     Shape shape;
@@ -41,7 +43,7 @@ struct Choice {
 
 const Choice kCandidates[] = {
     {1, {128, 512}, 4, 1LL << 23}, {1, {128, 512}, 4, 1LL << 21}, {0, {128, 256}, 0, 0},
-    {0, {128, 512}, 0, 0},         {0, {256, 512}, 0, 0}};
+    {0, {128, 512}, 0, 0},         {0, {256, 512}, 0, 0},          {2, {128, 256}, 0, 0}};
 
 std::mutex g_tune_mu;
 std::map<int, Choice> g_tuned;  // padded rank -> best choice (process-wide cache)
@@ -126,8 +128,29 @@ rs_status dispatch_block(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) 
     }
 }
 
+rs_status dispatch_pairs(rs_batch* B, Group& g, cudaStream_t st) {
+    for (int pi : g.pairs) {
+        const PairDesc& d = B->pairs[pi];
+        if (d.P <= 0) continue;
+        EvalLaunch a;
+        a.prot = d.prot;
+        a.lig = d.lig;
+        a.rot = d.rot;
+        a.trans = d.trans;
+        a.P = d.P;
+        a.E = d.E;
+        a.flags = d.flags;
+        a.events = false;
+        a.ws = B->d_ws;
+        a.ws_bytes = B->ws_bytes;
+        RS_TRY(launch_sorted(a, false, st));
+    }
+    return RS_OK;
+}
+
 rs_status dispatch_group(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) {
     if (g.choice.mode == 0) return dispatch_block(B, g, st, set_attr);
+    if (g.choice.mode == 2) return dispatch_pairs(B, g, st);
     return group_launch(g.plan, B->d_pairs, g.d_segs, B->d_ws, B->ws_bytes, g.choice.wpb, st, false);
 }
 
@@ -210,8 +233,34 @@ rs_status build_items(rs_batch* B, Group& g, double pose_fraction) {
     return RS_OK;
 }
 
+// Scratch of the single-pair path for the group's largest pair.
+rs_status size_pairs(rs_batch* B, Group& g) {
+    size_t need = 0;
+    for (int pi : g.pairs) {
+        const PairDesc& d = B->pairs[pi];
+        if (d.P > 0) need = std::max(need, sorted_scratch_bytes(d.P, d.lig.L, d.prot.n, false));
+    }
+    if (need > B->ws_bytes) {
+        if (B->d_ws) {
+            cudaFree(B->d_ws);
+            B->allocs.erase(std::remove(B->allocs.begin(), B->allocs.end(), B->d_ws), B->allocs.end());
+            B->d_ws = nullptr;
+            B->ws_bytes = 0;
+        }
+        if (cudaMalloc(&B->d_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("batch: scratch allocation of %zu bytes failed", need);
+            return RS_ERR_OOM;
+        }
+        B->allocs.push_back(B->d_ws);
+        B->ws_bytes = need;
+    }
+    return RS_OK;
+}
+
 rs_status prepare(rs_batch* B, Group& g, double pose_fraction) {
     g.shape = g.choice.shape;
+    if (g.choice.mode == 2) return size_pairs(B, g);
     return g.choice.mode == 0 ? build_items(B, g, pose_fraction) : build_plan(B, g, pose_fraction);
 }
 
@@ -293,7 +342,7 @@ rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int
     clear_error();
     RS_CHECK_ARG(ctx && pairs && out, "rs_batch_create: NULL argument");
     RS_CHECK_ARG(npairs >= 1 && npairs <= (1 << 20), "rs_batch_create: npairs=%d out of range", npairs);
-    RS_CHECK_ARG(autotune >= 0 && autotune <= 2, "rs_batch_create: autotune=%d not in {0, 1, 2}", autotune);
+    RS_CHECK_ARG(autotune >= 0 && autotune <= 3, "rs_batch_create: autotune=%d not in {0, 1, 2, 3}", autotune);
     *out = nullptr;
     for (int i = 0; i < npairs; ++i) {
         const rs_pair& p = pairs[i];
@@ -386,6 +435,7 @@ rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int
     rs_status s;
     for (Group& g : B->groups) {
         if (autotune == 2) g.choice = Choice{0, {128, 256}, 0, 0};  // per-block path, default shape
+        if (autotune == 3) g.choice = Choice{2, {128, 256}, 0, 0};  // pair by pair, single-pair path
         if (autotune == 1 && (s = tune_group(B, g, st)) != RS_OK) return fail(s);
         if ((s = prepare(B, g, 1.0)) != RS_OK) return fail(s);
         if ((s = dispatch_group(B, g, st, true)) != RS_OK) return fail(s);  // sets attributes, grid
@@ -438,7 +488,7 @@ rs_status rs_batch_get_info(const rs_batch* B, rs_batch_info* o) {
         if (g.choice.mode == 0) {
             o->nitems += g.nitems;
             o->grid += g.grid;
-        } else {
+        } else if (g.choice.mode == 1) {
             o->nchunks += (int32_t)g.plan.chunks.size();
         }
     }

@@ -71,8 +71,10 @@ def test_batch_equals_plain_calls(setup):
     assert info["npairs"] == len(ws)
     if info["mode"] == 0:
         assert info["nitems"] > 0 and info["threads"] in (128, 256)
-    else:
+    elif info["mode"] == 1:
         assert info["nchunks"] > 0 and info["warps_per_cta"] in (4, 8)
+    else:
+        assert info["mode"] == 2
     lib.rs_batch_run(b)
     torch.cuda.synchronize()
     ref = _plain(lib, prots, pairs)
@@ -80,7 +82,7 @@ def test_batch_equals_plain_calls(setup):
         assert_paths_agree(p["E_out"].cpu().numpy(), E, p["flags_out"].cpu().numpy(), f)
 
 
-@pytest.mark.parametrize("mode", [0, 2], ids=["cell-grouped", "per-block"])
+@pytest.mark.parametrize("mode", [0, 2, 3], ids=["cell-grouped", "per-block", "pair-by-pair"])
 def test_both_batch_paths_equal_plain_calls(setup, mode):
     import torch
     lib, ctx, ws, prots, pairs, b = setup
@@ -89,7 +91,7 @@ def test_both_batch_paths_equal_plain_calls(setup, mode):
     b2, keep = lib.rs_batch_create(ctx.handle, outs, autotune=mode)
     try:
         info = lib.rs_batch_get_info(b2)
-        assert info["mode"] == (1 if mode == 0 else 0)
+        assert info["mode"] == {0: 1, 2: 0, 3: 2}[mode]
         lib.rs_batch_run(b2)
         torch.cuda.synchronize()
     finally:
