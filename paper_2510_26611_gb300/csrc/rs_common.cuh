@@ -165,7 +165,8 @@ struct rs_ctx {
     // Per-atom arrays of the cell-grouped pose path.
     void* eval_buf = nullptr;
     size_t eval_bytes = 0;
-    // Evaluation poses of the finite-difference forces.
+    // Scratch of the finite-difference forces (evaluation poses), the pose scan and
+    // the molecular-complex call (staging and per-molecule results).
     void* fd_buf = nullptr;
     size_t fd_bytes = 0;
     // Build workspace, grown to the largest build seen (one build at a time).
