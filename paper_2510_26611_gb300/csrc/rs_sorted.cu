@@ -48,14 +48,15 @@ __global__ void k_sorted_poses(ProteinView P, const double* __restrict__ rot,
 
 // One thread per pose-atom; the short range of a warp's 32 atoms is taken
 // together (short_coop), so the pair work of near pairs keeps all lanes busy.  Warps
-// are persistent: warp w takes the 32-atom chunks w, w + W, ... (W warps in the
-// grid), so a warp whose atoms had few neighbours moves on at once instead of
-// idling until its CTA's slowest warp is done.
+// are persistent and take 32-atom chunks from a launch-wide cursor, so a warp whose
+// atoms had few neighbours moves on at once, and the chunks with many near pairs
+// spread over all warps instead of over the ones a fixed stride assigns them to.
 template <bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     k_sorted_atoms(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
                    int* __restrict__ pflag, AtomRec* __restrict__ rec, double* __restrict__ shortv,
-                   int* __restrict__ count, unsigned long long* __restrict__ counters) {
+                   int* __restrict__ count, unsigned long long* __restrict__ counters,
+                   unsigned long long* __restrict__ cursor) {
     __shared__ NearQueue<GRAD> queues[kWarpsPerBlock];
     const int L = lig.L;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -63,8 +64,11 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     long long natoms = 0;
     const long long M = (long long)PC * L;
     const long long nchunk = (M + 31) / 32;
-    const long long nw = (long long)gridDim.x * kWarpsPerBlock;
-    for (long long c = (long long)blockIdx.x * kWarpsPerBlock + wib; c < nchunk; c += nw) {
+    for (;;) {
+        unsigned long long cu = 0;
+        if (lane == 0) cu = atomicAdd(cursor, 1ULL);
+        const long long c = (long long)__shfl_sync(0xffffffffu, cu, 0);
+        if (c >= nchunk) break;
         const long long g = c * 32 + lane;
         const bool in_range = g < M;
         const int pl = in_range ? (int)(g / L) : 0;
@@ -207,6 +211,7 @@ struct SortedScratch {
     int* count;
     int* off;
     int* bsum;  // segment sums of the key scan
+    unsigned long long* cursor;  // work cursor of the atoms kernel
 };
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -216,7 +221,7 @@ size_t chunk_bytes(long long PC, int L, int n, bool grad) {
     const int NC = grad ? 7 : 1;
     return align256(PC * sizeof(PoseSetup)) + align256(PC * 4) + 2 * align256(M * sizeof(AtomRec)) +
            align256(M * 8 * (grad ? 4 : 1)) + align256(M * 8 * NC) + align256((size_t)n * kSub * 4) +
-           align256(((size_t)n * kSub + 1) * 4) + align256(key_scan_ints((long long)n * kSub) * 4);
+           align256(((size_t)n * kSub + 1) * 4) + align256(key_scan_ints((long long)n * kSub) * 4) + 256;
 }
 
 SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
@@ -238,6 +243,7 @@ SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
     s.count = (int*)take((size_t)n * kSub * 4);
     s.off = (int*)take(((size_t)n * kSub + 1) * 4);
     s.bsum = (int*)take(key_scan_ints((long long)n * kSub) * 4);
+    s.cursor = (unsigned long long*)take(8);
     return s;
 }
 
@@ -332,6 +338,7 @@ rs_status sorted_chunk_contrib(const EvalLaunch& a, const SortedScratch& s, int 
     const int L = a.lig.L, n = a.prot.n;
     const long long M = (long long)pc * L;
     RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)n * kSub * 4, st));
+    RS_TRY_CUDA(cudaMemsetAsync(s.cursor, 0, 8, st));
     {
         const unsigned grid = atoms_grid<GRAD>(M);
         int dev = 0;
@@ -343,7 +350,7 @@ rs_status sorted_chunk_contrib(const EvalLaunch& a, const SortedScratch& s, int 
         }
         ::rs::KernelTimer kt__(GRAD ? "k_sorted_atoms_grad" : "k_sorted_atoms", st, 0.0, true, a.events);
         k_sorted_atoms<GRAD><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag, s.rec,
-                                                                    s.shortv, s.count, ctr);
+                                                                    s.shortv, s.count, ctr, s.cursor);
     }
     {
         ::rs::KernelTimer kt__("k_key_scan", st, 0.0, false, a.events);
