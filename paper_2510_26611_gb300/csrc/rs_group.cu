@@ -68,14 +68,18 @@ template <int WPB>
 __global__ void __launch_bounds__(32 * WPB)
     k_group_atoms(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, int nseg, long long natom,
                   int ksub, const PoseSetup* __restrict__ ps, int* __restrict__ pflag,
-                  AtomRec* __restrict__ rec, double* __restrict__ shortv, int* __restrict__ count) {
+                  AtomRec* __restrict__ rec, double* __restrict__ shortv, int* __restrict__ count,
+                  unsigned long long* __restrict__ cursor) {
     __shared__ NearQueue<false> queues[WPB];
     __shared__ int lane_pair[WPB][32];
-    // persistent warps: warp w takes the 32-atom chunks w, w + W, ...
+    // persistent warps taking 32-atom chunks from a launch-wide cursor
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long nchunk = (natom + 31) / 32;
-    const long long nw = (long long)gridDim.x * WPB;
-    for (long long c = (long long)blockIdx.x * WPB + wib; c < nchunk; c += nw) {
+    for (;;) {
+        unsigned long long cu = 0;
+        if (lane == 0) cu = atomicAdd(cursor, 1ULL);
+        const long long c = (long long)__shfl_sync(0xffffffffu, cu, 0);
+        if (c >= nchunk) break;
         const long long g = c * 32 + lane;
         const bool in_range = g < natom;
         int s = 0, q = 0, j = 0;
@@ -235,6 +239,7 @@ struct GroupScratch {
     int* count;
     int* off;
     int* bsum;
+    unsigned long long* cursor;  // work cursor of the atoms kernel
 };
 
 // nkey counts cells; the sort uses nkey * ksub sub-bucket keys.
@@ -242,7 +247,7 @@ size_t chunk_scratch(int npose, long long natom, int nkey, int ksub) {
     nkey *= ksub;
     return align256((size_t)npose * sizeof(PoseSetup)) + align256((size_t)npose * 4) +
            2 * align256((size_t)natom * sizeof(AtomRec)) + 2 * align256((size_t)natom * 8) +
-           align256((size_t)nkey * 4) + align256((size_t)(nkey + 1) * 4) + align256(key_scan_ints(nkey) * 4);
+           align256((size_t)nkey * 4) + align256((size_t)(nkey + 1) * 4) + align256(key_scan_ints(nkey) * 4) + 256;
 }
 
 GroupScratch carve_group(void* base, int npose, long long natom, int nkey, int ksub) {
@@ -263,6 +268,7 @@ GroupScratch carve_group(void* base, int npose, long long natom, int nkey, int k
     s.count = (int*)take((size_t)nkey * 4);
     s.off = (int*)take((size_t)(nkey + 1) * 4);
     s.bsum = (int*)take(key_scan_ints(nkey) * 4);
+    s.cursor = (unsigned long long*)take(8);
     return s;
 }
 
@@ -393,6 +399,7 @@ rs_status group_launch(const GroupPlan& G, const PairDesc* d_pairs, const GroupS
         const int nseg = ch.seg_end - ch.seg_begin;
         GroupScratch s = carve_group(ws, ch.npose, ch.natom, ch.nkey, ch.ksub);
         RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)ch.nkey * ch.ksub * 4, st));
+        RS_TRY_CUDA(cudaMemsetAsync(s.cursor, 0, 8, st));
         {
             ::rs::KernelTimer kt__("k_group_poses", st, 0.0, false, events);
             k_group_poses<<<(ch.npose + 127) / 128, 128, 0, st>>>(d_pairs, segs, nseg, ch.npose, s.ps, s.pflag);
@@ -411,7 +418,7 @@ rs_status group_launch(const GroupPlan& G, const PairDesc* d_pairs, const GroupS
             const long long grid = std::max<long long>(1, std::min<long long>((ch.natom + 127) / 128, res));
             ::rs::KernelTimer kt__("k_group_atoms", st, 0.0, true, events);
             k_group_atoms<4><<<(unsigned)grid, 128, 0, st>>>(d_pairs, segs, nseg, ch.natom, ch.ksub, s.ps, s.pflag, s.rec,
-                                                            s.shortv, s.count);
+                                                            s.shortv, s.count, s.cursor);
         }
         {
             ::rs::KernelTimer kt__("k_key_scan", st, 0.0, false, events);
