@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--poses", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="step mode: skip the served, batched and PGD sub-measurements")
     ap.add_argument("--mode", choices=["step", "batch", "pgd", "serve", "fd", "ppiem", "localbox", "complex"],
                     default="step",
                     help="step: the protein-scale hot-path step (default); batch: 64 uneven "
@@ -149,17 +151,27 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ roofline
-def peaks() -> dict:
+def peaks(sm_count: int | None = None) -> dict:
+    """Denominators: HBM copy bandwidth from MEASURED_PEAKS.json (measured), and the
+    FP32 pipe derived from the SM count, 128 FP32 lanes per SM and the maximum SM
+    clock (no FP32 figure is measured)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sms = sm_count if sm_count else 152
     try:
         m = json.load(open(path))
-        return {"hbm_gbs": m["hbm_gbs"], "sm_max_mhz": m.get("sm_max_mhz", 2070.0), "src": "measured"}
+        return {"hbm_gbs": m["hbm_gbs"], "sm_max_mhz": m.get("sm_max_mhz", 2070.0), "src": "measured",
+                "sms": sms}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback", "sms": sms}
+
+
+def fp32_pipe_peak(pk: dict) -> float:
+    """FP32 pipe instructions per second (FADD/FMUL/FFMA = 1 each), in T op/s."""
+    return pk["sms"] * 128 * pk["sm_max_mhz"] * 1e6 / 1e12
 
 
 # Kernel -> (bound, unit of its reported work).  "fp32ops": FP32 pipe operations
-# (FADD, FMUL, FFMA each 1), peak 152 SMs x 128 lanes x max SM clock; "fp32": FP32
+# (FADD, FMUL, FFMA each 1), peak SMs x 128 lanes x max SM clock; "fp32": FP32
 # flops (FMA = 2), peak twice that; FP64 ALU peak: 1.25 TFLOP/s (GB300 table).
 KERNEL_KIND = {
     "k_eval_wform": ("alu", "fp32ops"), "k_eval_wform_grad": ("alu", "fp32ops"),
@@ -171,9 +183,49 @@ KERNEL_KIND = {
     "k_gram": ("alu", "fp64"), "k_gemm_gq": ("alu", "fp32ops"), "k_canon_factors": ("hbm", "bytes"),
 }
 
+# Pose kernels whose unit is one pose-atom (one ligand atom of one pose).
+POSE_ATOM_KERNELS = ("k_sorted_tc", "k_sorted_tc_grad", "k_sorted_wform", "k_sorted_wform_grad",
+                     "k_sorted_atoms", "k_sorted_atoms_grad")
 
-def roofline(timings: dict, pk: dict, name: str | None = None) -> dict:
-    """Roofline of the kernel with the largest timed share (or of `name`)."""
+# DRAM bytes (read + write) per pose-atom from one ncu capture of the kernel on a
+# small case of the same workload, with the digest of the kernel's sources at that
+# capture; a kernel whose sources changed since reports traffic null.
+TRAFFIC = {}
+TRAFFIC_SOURCES = ("rs_sorted.cu", "rs_sorted_dev.cuh", "rs_tc.cuh", "rs_tc_dev.cuh", "rs_pose_dev.cuh",
+                   "rs_common.cuh")
+
+
+def kernel_sources_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2510_26611_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_flops_per_pose_atom(name: str, ranks) -> float | None:
+    """FP32 flops one pose-atom needs by the Tucker form's own arithmetic (FMA = 2):
+    energy 9 (r1 + r2 + r3) + 2 r1 r2 r3 + 30 (three two-row lerps, the r1 r2 r3 core
+    contraction, pose transform and index); energy and gradient together
+    4 r1 r2 r3 + 18 (r1 + r2 + r3) + 8 r1 r2 + 60 (the core contracted with the lerped
+    axis-3 row and with its slope, both lerps of every axis, the r1 r2 finish of the
+    value and the three partials, transform, torque and chain rule)."""
+    r1, r2, r3 = ranks
+    if name in ("k_sorted_tc", "k_sorted_wform"):
+        return 9.0 * (r1 + r2 + r3) + 2.0 * r1 * r2 * r3 + 30.0
+    if name in ("k_sorted_tc_grad", "k_sorted_wform_grad"):
+        return 4.0 * r1 * r2 * r3 + 18.0 * (r1 + r2 + r3) + 8.0 * r1 * r2 + 60.0
+    return None
+
+
+def roofline(timings: dict, pk: dict, name: str | None = None, pose_atoms_per_launch: float | None = None,
+             ranks=None) -> dict:
+    """Roofline of the kernel with the largest timed share (or of `name`).
+
+    achieved = the kernel's algorithmic FP32 flops per launch (pose-atoms per launch x
+    the per-pose-atom count of the Tucker form) / its average launch time, against the
+    FP32 FMA peak; the library's instruction-level work model is reported beside it."""
     if not timings or (name is not None and name not in timings):
         return None
     if name is None:
@@ -191,94 +243,173 @@ def roofline(timings: dict, pk: dict, name: str | None = None) -> dict:
         note = "FP64 ALU, nominal 1.25 TFLOP/s"
     elif unit == "fp32ops":
         ach = work / per_launch_s / 1e12
-        peak = 152 * 128 * pk["sm_max_mhz"] * 1e6 / 1e12
+        peak = fp32_pipe_peak(pk)
         u = "Top/s"
-        note = "FP32 pipe, 152 SMs x 128 lanes x max SM clock (FADD/FMUL/FFMA = 1 op)"
+        note = f"FP32 pipe, {pk['sms']} SMs x 128 lanes x max SM clock (FADD/FMUL/FFMA = 1 op)"
     else:
         ach = work / per_launch_s / 1e12
-        peak = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        peak = 2 * fp32_pipe_peak(pk)
         u = "TFLOP/s"
-        note = "FP32 ALU, 152 SMs x 128 lanes x 2 x max SM clock"
+        note = f"FP32 ALU, {pk['sms']} SMs x 128 lanes x 2 x max SM clock"
     total = sum(r["ms"] for r in timings.values())
-    return {"kernel": name, "bound": bound, "achieved": round(ach, 4), "peak": round(peak, 3),
-            "unit": u, "frac": round(ach / peak, 4), "traffic": None, "peak_src": note + f" ({pk['src']})",
-            "avg_launch_ms": round(per_launch_s * 1e3, 4),
-            "share_of_timed_kernels": round(rec["ms"] / total, 4) if total > 0 else None}
+    instr = {"achieved": round(ach, 4), "peak": round(peak, 3), "unit": u, "frac": round(ach / peak, 4),
+             "peak_src": note + f" ({pk['src']} clock)", "work": "the library's instruction-level work model"}
+    out = {"kernel": name, "bound": bound, "achieved": instr["achieved"], "peak": instr["peak"], "unit": u,
+           "frac": instr["frac"], "traffic": None, "peak_src": instr["peak_src"],
+           "avg_launch_ms": round(per_launch_s * 1e3, 4),
+           "share_of_timed_kernels": round(rec["ms"] / total, 4) if total > 0 else None}
+    alg = algorithmic_flops_per_pose_atom(name, ranks) if ranks else None
+    if alg is not None and pose_atoms_per_launch:
+        flops = alg * pose_atoms_per_launch
+        a = flops / per_launch_s / 1e12
+        p = 2 * fp32_pipe_peak(pk)
+        out.update({"bound": "alu", "achieved": round(a, 4), "peak": round(p, 3), "unit": "TFLOP/s",
+                    "frac": round(a / p, 4),
+                    "peak_src": (f"FP32 FMA, {pk['sms']} SMs x 128 lanes x 2 flops x max SM clock "
+                                 f"(derived from unit counts and the {pk['src']} clock)"),
+                    "work": (f"algorithmic: {alg:.0f} FP32 flops per pose-atom (Tucker ranks "
+                             f"{tuple(ranks)}) x {pose_atoms_per_launch:.0f} pose-atoms per launch"),
+                    "instruction_model": instr})
+        t = TRAFFIC.get(name)
+        if t is not None:
+            if t["sources"] == kernel_sources_digest():
+                out["traffic"] = round(t["bytes_per_pose_atom"] * pose_atoms_per_launch)
+                out["traffic_src"] = t["profile"]
+            else:
+                out["traffic_src"] = "kernel changed since its ncu capture: traffic withheld"
+    return out
 
 
 # ------------------------------------------------------------------ CPU baseline (the oracle)
+# Runs in its own process on the host cores only (CUDA hidden).  One step of the same
+# kind as the GPU step on a bounded sample: one FP64 TEP build of the protein, then
+# energies and gradients of the first P_s poses.  Optionally it also reports, on the
+# first P_e poses, the errors of the method against exact Coulomb, of the Tucker
+# rank cap against the unreduced RS potential, and of the GPU's energies (read from a
+# file) against the oracle's reduced form.
 ORACLE_SNIPPET = r"""
 import json, os, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
 import oracle as O
-sys.path.insert(0, {root!r})
 from bench import workload
-P_full, P_s = {P}, {Ps}
+P_full, P_s, P_e, gpu_path = {P}, {Ps}, {Pe}, {gpu!r}
 w, rv = workload(P_full)
 idx = np.arange(P_s)
 t0 = time.perf_counter()
-m = O.build_model(w.prot_xyz, w.prot_q, w.n, w.b, w.sigma, w.R_l, tucker_cap=w.tucker_cap)
+m = O.build_model(w.prot_xyz, w.prot_q, w.n, w.b, w.sigma, w.R_l, tucker_cap=w.tucker_cap,
+                  keep_canonical=P_e > 0)
 t1 = time.perf_counter()
 O.pose_energies(m, w.lig_xyz, w.lig_q, w.quat[idx], w.trans[idx])
 t2 = time.perf_counter()
 O.pose_gradients(m, w.lig_xyz, w.lig_q, rv[idx], w.trans[idx])
 t3 = time.perf_counter()
-print(json.dumps({{"build_s": t1 - t0, "energy_s": t2 - t1, "grad_s": t3 - t2}}))
+out = {{"build_s": t1 - t0, "energy_s": t2 - t1, "grad_s": t3 - t2}}
+if P_e > 0:
+    sl = slice(0, P_e)
+    q, t = w.quat[sl], w.trans[sl]
+    tuck = O.pose_energies(m, w.lig_xyz, w.lig_q, q, t)
+    m.kind = "canonical"
+    full = O.pose_energies(m, w.lig_xyz, w.lig_q, q, t)
+    coul = O.coulomb_energies(w.prot_xyz, w.prot_q, w.lig_xyz, w.lig_q, q, t)
+    scale = O.tolerance_scale(full["E"], full["S_ref"])
+    feas = full["flags"] == 0
+    def stats(a, b):
+        e = np.abs(a - b) / scale
+        r = {{"median": float(np.median(e)), "max": float(e.max())}}
+        if feas.any():
+            r.update({{"feasible_median": float(np.median(e[feas])), "feasible_max": float(e[feas].max())}})
+        return r
+    err = {{"poses": P_e, "feasible": int(feas.sum()),
+            "denominator": "max(|E_RS|, 1e-2 sum_j |q_j phi_RS(x_j)|) of the unreduced RS energy",
+            "rs_unreduced_vs_coulomb": stats(full["E"], coul),
+            "tucker_vs_rs_unreduced": stats(tuck["E"], full["E"]),
+            "tucker_vs_coulomb": stats(tuck["E"], coul)}}
+    if gpu_path:
+        g = np.load(gpu_path)[:P_e]
+        ts = O.tolerance_scale(tuck["E"], tuck["S_ref"])
+        eg = np.abs(g - tuck["E"]) / ts
+        err["gpu_vs_oracle_tucker"] = {{"median": float(np.median(eg)), "max": float(eg.max()),
+                                        "denominator": "max(|E|, 1e-2 S) of the oracle's Tucker form"}}
+        err["gpu_vs_coulomb"] = stats(g, coul)
+    out["errors"] = err
+print(json.dumps(out))
 """
 
 
-def oracle_sample(P: int, P_s: int, threads: int) -> dict:
+def oracle_sample(P: int, P_s: int, threads: int, P_e: int = 0, gpu_path: str = "") -> dict:
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    code = ORACLE_SNIPPET.format(root=ROOT, P=P, Ps=P_s)
+    code = ORACLE_SNIPPET.format(root=ROOT, P=P, Ps=P_s, Pe=P_e, gpu=gpu_path)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     t = json.loads(r.stdout.strip().splitlines()[-1])
+    step_s = t["build_s"] + t["energy_s"] + t["grad_s"]
     per_pose = (t["energy_s"] + t["grad_s"]) / P_s
-    step_s = t["build_s"] + per_pose * P
-    return {"value": P / step_s, "step_s": step_s, "timings": t, "P_s": P_s}
+    return {"value": P_s / step_s, "step_s": step_s, "timings": t, "P_s": P_s,
+            "full_workload_estimate": P / (t["build_s"] + per_pose * P)}
 
 
-def cpu_baseline(P: int) -> dict:
+CPU_SAMPLE_POSES = 10_000     # the CPU-baseline step: one build + this many poses
+REF_SAMPLE_POSES = 4_000      # the reference arm's step (K + W of them must end in minutes)
+ERROR_SAMPLE_POSES = 100      # poses for the error report (unreduced RS form: rank 60000)
+
+
+def cpu_baseline(P: int, gpu_path: str = "") -> tuple[dict, dict | None]:
     cores = os.cpu_count() or 1
-    P_s = 400
-    r = oracle_sample(P, P_s, cores)
-    return {"value": round(r["value"], 3), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"one FP64 TEP build (RHOSVD) plus energies and gradients of the first "
-                       f"{P_s} poses, per-pose time scaled to P={P}; numpy/BLAS threads={cores}"),
-            "timings_s": {k: round(v, 3) for k, v in r["timings"].items()}}
-
-
+    r = oracle_sample(P, CPU_SAMPLE_POSES, cores, P_e=ERROR_SAMPLE_POSES, gpu_path=gpu_path)
+    t = r["timings"]
+    cpu = {"value": round(r["value"], 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": (f"one step of the same kind as the GPU step, measured: one FP64 TEP build "
+                      f"(RHOSVD) plus energies and gradients of the first {CPU_SAMPLE_POSES} of the "
+                      f"{P} poses; value = {CPU_SAMPLE_POSES} poses / measured step time; "
+                      f"numpy/BLAS threads={cores}"),
+           "ms_per_step": round(1e3 * r["step_s"], 1),
+           "timings_s": {k: round(v, 3) for k, v in t.items() if k.endswith("_s")},
+           "full_workload_estimate": {
+               "value": round(r["full_workload_estimate"], 3),
+               "how": f"one build + per-pose time x {P} poses (estimate, not measured)"}}
+    return cpu, t.get("errors")
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
+    """The oracle as it stands on the host cores, on this arm's workload, metric and
+    unit: each step is one FP64 TEP build plus energies and gradients of the first
+    REF_SAMPLE_POSES poses (a bounded sample of the 1e5-pose step), timed as a whole;
+    value = poses evaluated / measured time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     P = args.poses
     cores = os.cpu_count() or 1
-    P_s = 100
-    vals, steps_s = [], []
+    P_s = min(REF_SAMPLE_POSES, P)
+    steps_s, est = [], []
+    t_all = time.perf_counter()
     for it in range(args.warmup + args.steps):
         r = oracle_sample(P, P_s, cores)
         if it >= args.warmup:
-            vals.append(r["value"])
             steps_s.append(r["step_s"])
-    value = statistics.mean(vals)
+            est.append(r["full_workload_estimate"])
+    wall = time.perf_counter() - t_all
+    value = P_s * len(steps_s) / sum(steps_s)
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * statistics.mean(steps_s), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "poses": P},
+            "config": {"workload": WORKLOAD, "poses": P, "poses_evaluated_per_step": P_s},
             "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores,
                              "kind": "oracle",
-                             "sample": (f"each step: one FP64 TEP build plus energies and gradients of "
-                                        f"{P_s} poses, per-pose time scaled to P={P}")},
+                             "sample": (f"each step, measured: one FP64 TEP build plus energies and "
+                                        f"gradients of the first {P_s} of the {P} poses; value = "
+                                        f"{P_s} x steps / measured time; numpy/BLAS threads={cores}")},
+            "full_workload_estimate": {
+                "value": round(statistics.mean(est), 3),
+                "how": f"one build + per-pose time x {P} poses (estimate, not measured)"},
+            "wall_s": round(wall, 1),
             "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -286,7 +417,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ batching mode
-def run_batch(args):
+def measure_batch(args) -> dict:
     """64 protein-ligand pairs (N log-uniform in [500, 20000], L in [10, 200], n matched
     to the box), 1e4 poses each: one persistent graph-captured launch against 64
     sequential plain launches."""
@@ -333,8 +464,10 @@ def run_batch(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(c) for a, c in ev) / args.steps
 
-    ms_plain = timeit(plain)
-    ms_batch = timeit(batched)
+    with ClockSampler(0) as clk:
+        ms_plain = timeit(plain)
+        ms_batch = timeit(batched)
+    clocks = clk.summary()
     # batched vs plain: flags identical; energies equal, or within the W-form path
     # tolerance where the two take different long-range kernels (relative to
     # max(|E|, median |E|) per pair)
@@ -362,17 +495,21 @@ def run_batch(args):
                        "pairs": len(ws), "poses": P_tot, "atom_evaluations": atoms,
                        "n_hist": {str(n): sum(1 for w in ws if w.n == n) for n in sorted({w.n for w in ws})}},
             "batch_info": info, "build_s_total": round(build_s, 3),
-            "launch_calls": {"batched": 1, "plain": len(pairs)}}
-    print(json.dumps(line), flush=True)
+            "launch_calls": {"batched": 1, "plain": len(pairs)}, "clocks": clocks}
     lib.rs_batch_free(b)
     for h in prots:
         lib.rs_protein_free(h)
     ctx.close()
+    return line
+
+
+def run_batch(args):
+    print(json.dumps(measure_batch(args)), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------ differentiation mode
-def run_pgd(args):
+def measure_pgd(args) -> dict:
     """Constrained minimisation (Eq. Energy_Min): protein N=10000, ligand L=100, n=2049,
     4096 feasible starting poses, 50 projected-gradient steps (adjoint + backtracking)."""
     import torch
@@ -408,10 +545,12 @@ def run_pgd(args):
     torch.cuda.synchronize()
     launches0 = lib.rs_stats_kernel_launches()
     a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    E, f, acc = lib.rs_pgd_run(ctx.handle, holder["prot"], lx, lq, rv, tr, nsteps)
-    c.record()
-    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        a.record()
+        E, f, acc = lib.rs_pgd_run(ctx.handle, holder["prot"], lx, lq, rv, tr, nsteps)
+        c.record()
+        torch.cuda.synchronize()
+    clocks = clk.summary()
     ms = a.elapsed_time(c)
     launches = lib.rs_stats_kernel_launches() - launches0
     # what one step is made of: a gradient pass and an energy pass over all poses
@@ -439,10 +578,14 @@ def run_pgd(args):
                        "all_final_feasible": bool((f.cpu().numpy() == 0).all()),
                        "accepted_last_step": float((acc.cpu().numpy() >= 0).mean())},
             "gpu_launches": int(launches), "build_s": round(build_s, 3),
-            "kernels_ms_one_gradient_and_one_energy_pass": kernels}
-    print(json.dumps(line), flush=True)
+            "kernels_ms_one_gradient_and_one_energy_pass": kernels, "clocks": clocks}
     lib.rs_protein_free(holder["prot"])
     ctx.close()
+    return line
+
+
+def run_pgd(args):
+    print(json.dumps(measure_pgd(args)), flush=True)
     return 0
 
 
@@ -909,7 +1052,7 @@ def _run_plain(args, lib, pool, arrivals, picks):
     return lat, lat_warm, poses, wall
 
 
-def run_serve(args):
+def measure_serve(args) -> dict:
     """Serving (Poisson stream of docking requests against a pool of 64 proteins,
     grids n = 1025 ... 16385, 2048 poses per request): p50/p99 latency and poses/s of
     the serving loop beside the plain per-request path on the same stream."""
@@ -933,9 +1076,10 @@ def run_serve(args):
               "resident_bytes": st["used_bytes"], "wall_s": round(wall, 2),
               "cold_start": {"latency": _percentiles(cold_ms), "builds": st["builds"],
                              "wall_s": round(cold_wall, 2)}}
-    plain_lat, plain_warm, plain_poses, plain_wall = _run_plain(args, lib, pool, arrivals, picks)
+    with ClockSampler(0) as clk_plain:
+        plain_lat, plain_warm, plain_poses, plain_wall = _run_plain(args, lib, pool, arrivals, picks)
     plain = {"poses_per_s": round(plain_poses / plain_wall, 1), "latency": _percentiles(plain_lat),
-             "wall_s": round(plain_wall, 2)}
+             "wall_s": round(plain_wall, 2), "clocks": clk_plain.summary()}
     line = {"metric": "served p50/p99 latency and poses/s vs the plain per-request path",
             "value": served["poses_per_s"], "unit": "poses/s", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic",
@@ -957,7 +1101,11 @@ def run_serve(args):
             "p99_ratio_plain_over_served": (round(plain["latency"]["p99_ms"] / served["latency"]["p99_ms"], 3)
                                             if served["latency"]["p99_ms"] and plain["latency"]["p99_ms"] else None),
             "gpu_launches": int(launches), "clocks": clocks}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_serve(args):
+    print(json.dumps(measure_serve(args)), flush=True)
     return 0
 
 
@@ -990,6 +1138,10 @@ def run_ours(args):
     gt = torch.empty((P, 3), dtype=torch.float64, device=dev)
     gw = torch.empty((P, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    h0 = lib.rs_build_protein(ctx.handle, xyz, q, params)
+    ranks = lib.rs_protein_get_info(h0)["rank"]
+    lib.rs_protein_free(h0)
 
     def step():
         h = lib.rs_build_protein(ctx.handle, xyz, q, params)
@@ -1078,16 +1230,33 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": round(1e3 * float(te.item()), 3)}
 
+    pose_atoms = {k: args.steps * P * w.L / max(timings[k]["launches"], 1)
+                  for k in POSE_ATOM_KERNELS if k in timings}
+    E_host = E.cpu().numpy()
+    ctx.close()
     if rank == 0:
-        pk = peaks()
-        rf = roofline(timings, pk)
-        cpu = None
+        pk = peaks(sm_count)
+        top_name = max(timings.items(), key=lambda kv: kv[1]["ms"])[0] if timings else None
+        rf = roofline(timings, pk, pose_atoms_per_launch=pose_atoms.get(top_name), ranks=ranks)
+        cpu, errors = None, None
         if world == 1 and not args.no_cpu_baseline:
+            fd, gpu_path = tempfile.mkstemp(suffix=".npy")
+            os.close(fd)
+            np.save(gpu_path, E_host[:ERROR_SAMPLE_POSES])
             try:
-                cpu = cpu_baseline(P)
+                cpu, errors = cpu_baseline(P, gpu_path)
             except Exception as e:  # report, do not hide
                 cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                        "sample": f"failed: {type(e).__name__}: {str(e)[-300:]}"}
+            finally:
+                os.remove(gpu_path)
+        extras = {}
+        if world == 1 and not args.no_extras:
+            for key, fn in (("served", measure_serve), ("batch", measure_batch), ("pgd", measure_pgd)):
+                try:
+                    extras[key] = fn(args)
+                except Exception as e:  # report, do not hide
+                    extras[key] = {"failed": f"{type(e).__name__}: {str(e)[-300:]}"}
         top = sorted(timings.values(), key=lambda r: -r["ms"])[:8]
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
@@ -1098,10 +1267,9 @@ def run_ours(args):
                            "l2": "flushed between steps (256 MiB write, outside the timed events)",
                            "parallelism": f"{world} independent ranks, poses split (no collective)"},
                 "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "roofline_pose_kernels": {k: roofline(timings, pk, k) for k in
-                                          ("k_sorted_atoms_grad", "k_sorted_atoms", "k_sorted_tc_grad",
-                                           "k_sorted_tc", "k_sorted_wform_grad", "k_sorted_wform")
-                                          if k in timings},
+                "roofline_pose_kernels": {k: roofline(timings, pk, k, pose_atoms.get(k), ranks)
+                                          for k in POSE_ATOM_KERNELS if k in timings},
+                "model_errors": errors,
                 "short_range_work_per_step": {
                     k: {"atoms": v["atoms"] / args.steps, "candidates": v["candidates"] / args.steps,
                         "near_pairs": v["near"] / args.steps,
@@ -1109,8 +1277,8 @@ def run_ours(args):
                     for k, v in short_work.items()},
                 "clocks": clocks,
                 "kernels_ms_per_step": {r["name"]: round(r["ms"] / args.steps, 4) for r in top}}
+        line.update(extras)
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

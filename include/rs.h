@@ -321,8 +321,9 @@ rs_status rs_batch_get_info(const rs_batch* batch, rs_batch_info* out);
  * cudaMalloc/cudaFree because those can synchronise the device, or a plug-in whose
  * host application owns all device memory).  The paper has no counterpart: this
  * is an interface choice.  Differences from rs_energy_poses:
- *   - every array pointer is device memory on the protein's GPU (no host mode);
- *     no context is needed; the call sets the protein's device current and
+ *   - every array pointer is device memory on the protein's GPU, or managed
+ *     memory (no host mode); anything else (a host pointer, another GPU's memory)
+ *     returns RS_ERR_INVALID before any launch; no context is needed; the call sets the protein's device current and
  *     enqueues on `stream` (NULL = the CUDA default stream);
  *   - the per-call scratch is a fixed array in the library's device image
  *     (288 KiB on every GPU that loads the library, kept until exit), so
@@ -387,6 +388,8 @@ typedef struct rs_serve_params {
                                       it has at least this many pose-atoms and ...       */
     double  group_atoms_per_cell;  /* ... at least this many per axis-3 grid cell; other
                                       requests take the per-block kernel (both >= 0)     */
+    int32_t hold_builds;           /* test hook: nonzero keeps protein builds from
+                                      starting until rs_serve_release_builds            */
 } rs_serve_params;
 
 typedef struct rs_serve_stats {
@@ -416,6 +419,9 @@ rs_status rs_serve_poll(rs_server* s, uint64_t req_id, rs_result* out);
 rs_status rs_serve_wait(rs_server* s, uint64_t req_id, int32_t timeout_ms, rs_result* out);
 /* Removes a request that has not been admitted yet (RS_ERR_BUSY once admitted). */
 rs_status rs_serve_cancel(rs_server* s, uint64_t req_id);
+/* Lets protein builds start on a server created with hold_builds (a test hook:
+ * requests of proteins that are not resident stay queued until then). */
+rs_status rs_serve_release_builds(rs_server* s);
 rs_status rs_serve_get_stats(rs_server* s, rs_serve_stats* out);
 /* Finishes launched work, drops queued requests and frees everything. */
 void      rs_serve_destroy(rs_server* s);
@@ -457,6 +463,14 @@ rs_status rs_timing_get(int index, char* name, size_t name_len, double* total_ms
  * Process-wide; takes effect for launches (and batch plans) made afterwards.
  * Returns the previous mode. */
 int       rs_set_wform_kernel(int mode);
+/* Block products Y = G Q of the Tucker build's subspace iteration (RHOSVD, Sec. 1,
+ * Algorithm TEP step 4): mode 1 (default) runs them on the tensor cores (tcgen05
+ * MMAs on six exact BF16 slices per operand, exact FP32 sums per 64-wide K chunk,
+ * ~2^-46 of the chunk's row and column maxima) when the block size is a multiple
+ * of 16; mode 0 always runs the float-pair GEMM on the FP32 pipes (~2^-47).
+ * Process-wide; takes effect for builds started afterwards.  Returns the previous
+ * mode. */
+int       rs_set_build_gemm_kernel(int mode);
 /* Number of tensor-core tiles on `device` whose MMAs did not complete within the
  * kernel's bounded wait (their energies were set to NaN); 0 in normal operation. */
 rs_status rs_tc_error_count(int device, int32_t* out);

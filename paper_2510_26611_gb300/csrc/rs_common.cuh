@@ -181,6 +181,7 @@ rs_status ensure_buffer(void** buf, size_t* cap, size_t need);
 int* tc_error_flag(int device);
 // W-form kernel of the cell-grouped pose paths: 1 tensor cores, 0 float pairs.
 int wform_kernel_mode();
+int build_gemm_mode();
 // Work counters of the sorted atoms kernels on a device (atoms, candidates, near
 // pairs; one triple for energies, one for gradients), in the same device buffer.
 unsigned long long* short_counters(int device, bool grad);

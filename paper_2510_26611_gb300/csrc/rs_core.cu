@@ -29,6 +29,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_tc_mu;
 int* g_tc_flag[kMaxDevices] = {};
 std::atomic<int> g_wform_mode{1};
+std::atomic<int> g_build_gemm_mode{1};
 }  // namespace
 
 int* tc_error_flag(int device) {
@@ -51,6 +52,7 @@ int* tc_error_flag(int device) {
 }
 
 int wform_kernel_mode() { return g_wform_mode.load(std::memory_order_relaxed); }
+int build_gemm_mode() { return g_build_gemm_mode.load(std::memory_order_relaxed); }
 
 double short_work_ops(bool grad, double atoms, double cand, double near) {
     return 230.0 * atoms + 6.0 * cand + (grad ? 179.0 : 121.0) * near;
@@ -313,6 +315,10 @@ rs_status rs_protein_get_info(const rs_protein* p, rs_protein_info* o) {
 
 int rs_set_wform_kernel(int mode) {
     return rs::g_wform_mode.exchange(mode ? 1 : 0);
+}
+
+int rs_set_build_gemm_kernel(int mode) {
+    return rs::g_build_gemm_mode.exchange(mode ? 1 : 0);
 }
 
 rs_status rs_tc_error_count(int device, int32_t* out) {

@@ -54,6 +54,28 @@ rs_status scratch_for(int device, void** out) {
     return RS_OK;
 }
 
+// The caller's buffers must be memory this GPU can address: device memory on
+// `device`, or managed memory.  A host pointer (or another GPU's memory) handed to
+// the kernels would fault and poison the context, so it is refused here, on the
+// host, before anything is launched.  cudaPointerGetAttributes allocates nothing.
+rs_status check_on_device(const void* p, int device, const char* what) {
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("rs_energy_poses_noalloc: %s is not a CUDA pointer (%s)", what,
+                  cudaGetErrorString(e));
+        return RS_ERR_INVALID;
+    }
+    if (a.type == cudaMemoryTypeManaged) return RS_OK;
+    if (a.type != cudaMemoryTypeDevice || a.device != device) {
+        set_error("rs_energy_poses_noalloc: %s must be device memory on GPU %d "
+                  "(pointer type %d on device %d)", what, device, (int)a.type, a.device);
+        return RS_ERR_INVALID;
+    }
+    return RS_OK;
+}
+
 }  // namespace
 }  // namespace rs
 
@@ -80,6 +102,12 @@ extern "C" rs_status rs_energy_poses_noalloc(const rs_protein* prot, int32_t L,
     RS_CHECK_ARG(lig_xyz && lig_q && quat && trans && E_out,
                  "rs_energy_poses_noalloc: NULL input or output pointer");
     RS_TRY_CUDA(cudaSetDevice(prot->device));
+    RS_TRY(check_on_device(lig_xyz, prot->device, "lig_xyz"));
+    RS_TRY(check_on_device(lig_q, prot->device, "lig_q"));
+    RS_TRY(check_on_device(quat, prot->device, "quat"));
+    RS_TRY(check_on_device(trans, prot->device, "trans"));
+    RS_TRY(check_on_device(E_out, prot->device, "E_out"));
+    if (flags_out) RS_TRY(check_on_device(flags_out, prot->device, "flags_out"));
     void* scratch = nullptr;
     RS_TRY(scratch_for(prot->device, &scratch));
     cudaStream_t st = (cudaStream_t)stream;

@@ -213,6 +213,7 @@ struct rs_server {
     std::deque<rs::BuildJob> bjobs;
     std::vector<rs::BuildDone> bdone;
     bool bstop = false;
+    bool bhold = false;  // test hook: builds wait until released
     // scheduler-thread state
     std::map<uint64_t, rs::ProteinEntry> cache;
     rs::Pool dev, pinned;
@@ -301,7 +302,8 @@ void builder_main(rs_server* S) {
         BuildJob job;
         {
             std::unique_lock<std::mutex> lk(S->bmu);
-            while (S->bjobs.empty() && !S->bstop) S->bcv.wait_for(lk, std::chrono::milliseconds(50));
+            while ((S->bjobs.empty() || S->bhold) && !S->bstop)
+                S->bcv.wait_for(lk, std::chrono::milliseconds(50));
             if (S->bstop) return;
             job = S->bjobs.front();
             S->bjobs.pop_front();
@@ -852,6 +854,7 @@ rs_status rs_serve_create(int device, const rs_serve_params* prm, rs_server** ou
     S->budget = p.mem_budget_bytes ? (size_t)p.mem_budget_bytes : fr / 2;
     S->inject_left = p.inject_alloc_failures;
     S->dev.inject = &S->inject_left;
+    S->bhold = p.hold_builds != 0;
     S->pinned.host = true;
     // one stream per in-flight launch plus one for protein builds
     for (int i = 0; i <= p.max_inflight_launches; ++i) {
@@ -872,6 +875,18 @@ rs_status rs_serve_create(int device, const rs_serve_params* prm, rs_server** ou
     S->worker = std::thread(worker_main, S);
     S->builder = std::thread(builder_main, S);
     *out = S;
+    return RS_OK;
+}
+
+rs_status rs_serve_release_builds(rs_server* S) {
+    using namespace rs;
+    clear_error();
+    RS_CHECK_ARG(S, "rs_serve_release_builds: NULL server");
+    {
+        std::lock_guard<std::mutex> lk(S->bmu);
+        S->bhold = false;
+    }
+    S->bcv.notify_all();
     return RS_OK;
 }
 

@@ -83,7 +83,7 @@ class rs_serve_params(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_queue", C.c_int32),
                 ("max_inflight_launches", C.c_int32), ("idle_wait_ms", C.c_int32),
                 ("inject_alloc_failures", C.c_int32), ("group_min_atoms", C.c_int64),
-                ("group_atoms_per_cell", C.c_double)]
+                ("group_atoms_per_cell", C.c_double), ("hold_builds", C.c_int32)]
 
 
 class rs_serve_stats(C.Structure):
@@ -130,10 +130,12 @@ def _load() -> C.CDLL:
         "rs_serve_poll": (st, [vp, C.c_uint64, C.POINTER(rs_result)]),
         "rs_serve_wait": (st, [vp, C.c_uint64, i32, C.POINTER(rs_result)]),
         "rs_serve_cancel": (st, [vp, C.c_uint64]),
+        "rs_serve_release_builds": (st, [vp]),
         "rs_serve_get_stats": (st, [vp, C.POINTER(rs_serve_stats)]),
         "rs_serve_destroy": (None, [vp]),
         "rs_symeig_host": (st, [i32, vp, vp, vp]),
         "rs_set_wform_kernel": (C.c_int, [C.c_int]),
+        "rs_set_build_gemm_kernel": (C.c_int, [C.c_int]),
         "rs_tc_error_count": (st, [C.c_int, C.POINTER(i32)]),
         "rs_diag_tc_contract": (st, [i32, i32, vp, vp, vp, vp, vp]),
         "rs_diag_tc_launch": (st, [C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)]),
@@ -440,6 +442,8 @@ def rs_energy_poses_noalloc(prot, lig_xyz, lig_q, quat, trans, E_out=None, flags
     for x in (lig_xyz, lig_q, quat, trans):
         if not _is_cuda(x):
             raise RSError(RS_ERR_INVALID, "rs_energy_poses_noalloc takes CUDA tensors only")
+    if len({x.device for x in (lig_xyz, lig_q, quat, trans)}) != 1:
+        raise RSError(RS_ERR_INVALID, "rs_energy_poses_noalloc: tensors on different GPUs")
     lx, lq = _dev(lig_xyz, np.float64), _dev(lig_q, np.float64)
     r, t = _dev(quat, np.float64), _dev(trans, np.float64)
     P, L = int(r.shape[0]), int(lq.shape[0])
@@ -447,6 +451,8 @@ def rs_energy_poses_noalloc(prot, lig_xyz, lig_q, quat, trans, E_out=None, flags
         raise RSError(RS_ERR_INVALID, "shape mismatch in pose arguments")
     E = E_out if E_out is not None else torch.empty(P, dtype=torch.float64, device=r.device)
     f = flags_out if flags_out is not None else torch.empty(P, dtype=torch.uint8, device=r.device)
+    if E.device != r.device or f.device != r.device:
+        raise RSError(RS_ERR_INVALID, "rs_energy_poses_noalloc: outputs on another device")
     _check(_lib.rs_energy_poses_noalloc(prot, L, _ptr(lx), _ptr(lq), P, _ptr(r), _ptr(t),
                                         _ptr(E), _ptr(f), _stream_ptr(stream)))
     return E, f
@@ -520,6 +526,12 @@ def rs_set_wform_kernel(mode: int) -> int:
     """W-form kernel of the cell-grouped pose paths: 1 tensor cores (default), 0 float
     pairs on the FP32 pipes.  Returns the previous mode."""
     return int(_lib.rs_set_wform_kernel(int(mode)))
+
+
+def rs_set_build_gemm_kernel(mode: int) -> int:
+    """Block products G Q of the Tucker build: 1 tensor cores (default), 0 float pairs
+    on the FP32 pipes.  Returns the previous mode."""
+    return int(_lib.rs_set_build_gemm_kernel(int(mode)))
 
 
 def rs_tc_error_count(device: int = 0) -> int:
@@ -715,6 +727,9 @@ class Server:
         if s == RS_OK:
             self._keep.pop(rid, None)
         return s
+
+    def release_builds(self):
+        _check(_lib.rs_serve_release_builds(self.handle))
 
     def stats(self) -> dict:
         return rs_serve_get_stats(self.handle)

@@ -79,9 +79,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(rs_request), offsetof(rs_request, params),
          offsetof(rs_request, L), offsetof(rs_request, P), offsetof(rs_request, trans),
          sizeof(rs_result));
-  printf("%zu %zu %zu %zu %zu\n", offsetof(rs_result, message), sizeof(rs_serve_params),
-         offsetof(rs_serve_params, inject_alloc_failures), sizeof(rs_serve_stats),
-         offsetof(rs_serve_stats, mean_requests_per_launch));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(rs_result, message), sizeof(rs_serve_params),
+         offsetof(rs_serve_params, inject_alloc_failures), offsetof(rs_serve_params, hold_builds),
+         sizeof(rs_serve_stats), offsetof(rs_serve_stats, mean_requests_per_launch));
   printf("%zu %zu %zu\n", sizeof(rs_batch_info), offsetof(rs_batch_info, chunk_atoms),
          offsetof(rs_batch_info, nchunks));
   return 0;
@@ -94,7 +94,7 @@ int main(void) {
     R, Z, S, T = lib.rs_request, lib.rs_result, lib.rs_serve_params, lib.rs_serve_stats
     B = lib.rs_batch_info
     want = [C.sizeof(R), R.params.offset, R.L.offset, R.P.offset, R.trans.offset, C.sizeof(Z),
-            Z.message.offset, C.sizeof(S), S.inject_alloc_failures.offset, C.sizeof(T),
+            Z.message.offset, C.sizeof(S), S.inject_alloc_failures.offset, S.hold_builds.offset, C.sizeof(T),
             T.mean_requests_per_launch.offset, C.sizeof(B), B.chunk_atoms.offset, B.nchunks.offset]
     assert got == want
 

@@ -168,17 +168,19 @@ def test_over_budget_and_injected_failures_fail_only_that_request(setup):
 
 def test_cancel_wait_timeout_and_empty_request(setup):
     lib, prots, ligs, params, reqs, plain, _ = setup
-    srv = lib.Server(0)
+    srv = lib.Server(0, hold_builds=1)
     try:
         r = next(r for r in reqs if r["pi"] == 2 and r["quat"].shape[0] > 1)
         a = _submit(lib, srv, prots, ligs, params, r)
         b = _submit(lib, srv, prots, ligs, params, r)
-        # both wait for their protein's build: b is still queued and can be cancelled
+        # the protein's build is held, so both stay queued: b can be cancelled and a
+        # cannot have finished
         assert srv.cancel(b) == lib.RS_OK
         assert srv.cancel(b) == lib.RS_ERR_INVALID  # unknown now
         with pytest.raises(lib.RSError) as ei:
             lib.rs_serve_wait(srv.handle, a, 0)
         assert ei.value.status in (lib.RS_ERR_TIMEOUT,)
+        srv.release_builds()
         res = srv.wait(a)
         assert res["status"] == lib.RS_OK
         assert srv.cancel(a) == lib.RS_ERR_INVALID  # finished and released
