@@ -21,6 +21,7 @@
 
 #include "rs_common.cuh"
 #include "rs_diag.cuh"
+#include "rs_tc_gemm.cuh"
 
 namespace rs {
 namespace {
@@ -503,6 +504,8 @@ __global__ void k_init_block(int n, int p, double* __restrict__ Q) {
 // accumulators per thread; KS slices give enough CTAs to fill the GPU for n ~ 1000.
 constexpr int kGemmKS = 8;
 constexpr int kGemmRows = 64;
+// Largest grid of the tensor-core G Q (its slices take 12 bytes per Gram entry).
+constexpr int kTcGemmMaxN = 4097;
 
 __global__ void __launch_bounds__(256) k_gemm_gq(int n, int p, const float2* __restrict__ G,
                                                   const float2* __restrict__ Q, double* __restrict__ Yp) {
@@ -564,11 +567,13 @@ __global__ void __launch_bounds__(256) k_gemm_gq(int n, int p, const float2* __r
     }
 }
 
-// Y = sum over the K slices of Yp (fixed order), and with Sp != nullptr the partial
+// Y = sum over the nks K slices of Yp (FP64) or Yp2 (float pairs) in a fixed order, and
+// with Sp != nullptr the partial
 // Gram of each 16-row block, Sp[ax][blk] = Y_blk^T Y_blk (p x p, FP64), so CholQR
 // needs no separate pass over Y.  CTA: 16 rows of one axis.
-__global__ void __launch_bounds__(256) k_gemm_reduce(int n, int p, const double* __restrict__ Yp,
-                                                      double* __restrict__ Y, double* __restrict__ Sp) {
+__global__ void __launch_bounds__(256) k_gemm_reduce(int n, int p, int nks, const double* __restrict__ Yp,
+                                                      const float2* __restrict__ Yp2, double* __restrict__ Y,
+                                                      double* __restrict__ Sp) {
     __shared__ double Ys[16][49];
     const int ax = blockIdx.y;
     const int i0 = blockIdx.x * 16;
@@ -577,7 +582,16 @@ __global__ void __launch_bounds__(256) k_gemm_reduce(int n, int p, const double*
         const int gi = i0 + r;
         double v = 0.0;
         if (gi < n) {
-            for (int ks = 0; ks < kGemmKS; ++ks) v += Yp[(((size_t)ks * 3 + ax) * n + gi) * p + c];
+            if (Yp2) {  // float-pair partials (tensor-core GEMM), summed in pair arithmetic
+                dev::F2 acc{0.f, 0.f};
+                for (int ks = 0; ks < nks; ++ks) {
+                    const float2 t = Yp2[(((size_t)ks * 3 + ax) * n + gi) * p + c];
+                    acc = dev::df_add(acc, dev::F2{t.x, t.y});
+                }
+                v = dev::df_to(acc);
+            } else {
+                for (int ks = 0; ks < nks; ++ks) v += Yp[(((size_t)ks * 3 + ax) * n + gi) * p + c];
+            }
             Y[((size_t)ax * n + gi) * p + c] = v;
         }
         Ys[r][c] = v;
@@ -659,19 +673,24 @@ __global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restri
         double t = 0.0;
         for (int i = threadIdx.x; i < p; i += 32) t += A[i][i];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) red[0] = rel_shift * t;
+        if (threadIdx.x == 0) {
+            red[0] = rel_shift * t;
+            red[1] = 1e-14 * t;
+        }
     }
     __syncthreads();
     if (threadIdx.x < p) A[threadIdx.x][threadIdx.x] += red[0];
     __syncthreads();
     for (int k = 0; k < p; ++k) {
         if (threadIdx.x == 0) {
-            double d = A[k][k];
-            if (!(d > 0.0)) {
-                fail[ax] = 1;
-                d = 1e-300;
-            }
-            const double r = rsqrt(d);
+            // S is a Gram matrix: a pivot at or below 1e-14 of its trace belongs to a
+            // direction the block does not span (a rank-deficient block, e.g. a protein
+            // with fewer Gaussian terms than the block size); its column of Q becomes 0
+            // (R[k][k] = 0, rk = 0) instead of amplifying rounding noise.  Only a NaN
+            // pivot is a failure.
+            const double d = A[k][k];
+            if (d != d) fail[ax] = 1;
+            const double r = d > red[1] ? rsqrt(d) : 0.0;
             rk[k] = r;
             A[k][k] = d * r;
         }
@@ -1415,6 +1434,33 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         set_error("grid too small for tucker_cap %d (n=%d)", cap, n);
         return RS_ERR_UNSUPPORTED;
     }
+    // G Q on the tensor cores for block sizes that are multiples of 16 (the MMA's N)
+    const int p16 = (p + 15) / 16 * 16;
+    const bool use_tc = build_gemm_mode() == 1 && n <= kTcGemmMaxN && p16 <= std::min(48, n);
+    if (use_tc) p = p16;
+    const int MT = (n + tcg::kM - 1) / tcg::kM, KC = (n + tcg::kK - 1) / tcg::kK;
+    uint8_t *d_As = nullptr, *d_Bs = nullptr;
+    float *d_ainv = nullptr, *d_binv = nullptr;
+    int* d_tcerr = nullptr;
+    if (use_tc) {
+        int dev = 0;
+        RS_TRY_CUDA(cudaGetDevice(&dev));
+        d_tcerr = tc_error_flag(dev);
+        if (!d_tcerr) {
+            set_error("tensor-core build GEMM: no error flag on device %d", dev);
+            return RS_ERR_CUDA;
+        }
+        RS_TRY(S.get(&d_As, (size_t)3 * MT * KC * tcg::kS * tcg::kSliceA));
+        RS_TRY(S.get(&d_ainv, (size_t)3 * KC * MT * tcg::kM));
+        RS_TRY(S.get(&d_Bs, (size_t)3 * KC * tcg::kS * p * tcg::kK * 2));
+        RS_TRY(S.get(&d_binv, (size_t)3 * KC * p));
+        {
+            ::rs::KernelTimer kt__("k_slice_rows", st, 0.0, false);
+            tcg::k_slice_rows<<<dim3(MT, KC, 3), tcg::kM, 0, st>>>(n, MT, KC, d_G, d_As, d_ainv);
+        }
+        RS_TRY_CUDA(cudaGetLastError());
+    }
+    const int nks = use_tc ? KC : kGemmKS;
     double *d_Q, *d_Y, *d_Sm, *d_Ri, *d_W;
     int* d_fail;
     RS_TRY(S.get(&d_Q, (size_t)3 * n * p));
@@ -1432,9 +1478,11 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     }
     dim3 gq((n + kGemmRows - 1) / kGemmRows, kGemmKS, 3);
     const int nblk = (n + 15) / 16;
-    double *d_Sp, *d_Yp;
+    double *d_Sp, *d_Yp = nullptr;
+    float2* d_Yp2 = nullptr;
     RS_TRY(S.get(&d_Sp, (size_t)3 * nblk * p * p));
-    RS_TRY(S.get(&d_Yp, (size_t)kGemmKS * 3 * n * p));
+    if (use_tc) RS_TRY(S.get(&d_Yp2, (size_t)nks * 3 * n * p));
+    else RS_TRY(S.get(&d_Yp, (size_t)nks * 3 * n * p));
     // CholQR2 of Yin (d_Q or d_Y): shifted CholQR then plain CholQR; every pass reads
     // one buffer and writes the other, and the result ends in d_Q.
     auto cholqr_pass = [&](const double* src, double* dst, double shift) -> rs_status {
@@ -1452,8 +1500,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         }
         {
             ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
-            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(n, p, src, d_Ri, dst,
-                                                                                 dst == d_Q ? d_Q2 : nullptr);
+            k_apply_rinv<<<dim3(blocks_for((size_t)n * p), 3), kBlock, 0, st>>>(
+                n, p, src, d_Ri, dst, dst == d_Q ? d_Q2 : nullptr);
         }
         RS_TRY_CUDA(cudaGetLastError());
         return RS_OK;
@@ -1469,15 +1517,45 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     };
     RS_TRY(orthonormalize(d_Q));
     work = 3.0 * 13.0 * n * (double)n * p;  // FP32 pipe ops per G Q (one Dot2 step per product)
-    // one subspace step: Y = G Q with partial Grams, S = Y^T Y, shifted Cholesky, Q = Y R^-1
-    auto step = [&]() -> rs_status {
-        {
+    // Y partials of G Q per K slice into d_Yp: float-pair GEMM, or slices of Q and the
+    // tensor-core GEMM
+    auto gemm_gq = [&]() -> rs_status {
+        if (!use_tc) {
             ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
             k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q2, d_Yp);
+        } else {
+            // BF16 MMA flops of the 21 slice products
+            const double tflops = 2.0 * 21.0 * 3.0 * (double)MT * tcg::kM * (double)KC * tcg::kK * p;
+            switch (p) {
+#define RS_GQ_CASE(NP)                                                                                    \
+    case NP: {                                                                                            \
+        {                                                                                                 \
+            ::rs::KernelTimer kt__("k_slice_cols", st, 0.0, false);                                       \
+            tcg::k_slice_cols<NP><<<dim3(KC, 3), NP, 0, st>>>(n, KC, d_Q2, d_Bs, d_binv);                 \
+        }                                                                                                 \
+        RS_TRY_CUDA(cudaFuncSetAttribute(tcg::k_tc_gemm<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)tcg::GemmShape<NP>::SMEM));                                 \
+        ::rs::KernelTimer kt__("k_tc_gemm", st, tflops, true);                                            \
+        tcg::k_tc_gemm<NP><<<dim3(MT, KC, 3), tcg::kM, tcg::GemmShape<NP>::SMEM, st>>>(                   \
+            n, MT, KC, d_As, d_ainv, d_Bs, d_binv, d_Yp2, d_tcerr);                                       \
+        break;                                                                                            \
+    }
+                RS_GQ_CASE(16) RS_GQ_CASE(32) RS_GQ_CASE(48)
+#undef RS_GQ_CASE
+                default:
+                    set_error("tensor-core build GEMM: block size %d", p);
+                    return RS_ERR_UNSUPPORTED;
+            }
         }
+        RS_TRY_CUDA(cudaGetLastError());
+        return RS_OK;
+    };
+    // one subspace step: Y = G Q with partial Grams, S = Y^T Y, shifted Cholesky, Q = Y R^-1
+    auto step = [&]() -> rs_status {
+        RS_TRY(gemm_gq());
         {
             ::rs::KernelTimer kt__("k_gemm_reduce", st, 0.0, false);
-            k_gemm_reduce<<<dim3(nblk, 3), 256, 0, st>>>(n, p, d_Yp, d_Y, d_Sp);
+            k_gemm_reduce<<<dim3(nblk, 3), 256, 0, st>>>(n, p, nks, d_Yp, d_Yp2, d_Y, d_Sp);
         }
         {
             ::rs::KernelTimer kt__("k_sum_gram", st, 0.0, false);
@@ -1496,13 +1574,10 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     };
     auto ritz = [&](std::vector<double>& lam_out) -> rs_status {
         RS_TRY(orthonormalize(d_Q));
-        {
-            ::rs::KernelTimer kt__("k_gemm_gq", st, work, true);
-            k_gemm_gq<<<gq, 256, 0, st>>>(n, p, d_G, d_Q2, d_Yp);
-        }
+        RS_TRY(gemm_gq());
         {
             ::rs::KernelTimer kt__("k_gemm_reduce", st, 0.0, false);
-            k_gemm_reduce<<<dim3(nblk, 3), 256, 0, st>>>(n, p, d_Yp, d_Y, nullptr);
+            k_gemm_reduce<<<dim3(nblk, 3), 256, 0, st>>>(n, p, nks, d_Yp, d_Yp2, d_Y, nullptr);
         }
         {
             ::rs::KernelTimer kt__("k_atb", st, 0.0, false);
