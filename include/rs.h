@@ -463,11 +463,13 @@ rs_status rs_timing_get(int index, char* name, size_t name_len, double* total_ms
  * Process-wide; takes effect for launches (and batch plans) made afterwards.
  * Returns the previous mode. */
 int       rs_set_wform_kernel(int mode);
-/* Block products Y = G Q of the Tucker build's subspace iteration (RHOSVD, Sec. 1,
- * Algorithm TEP step 4): mode 1 (default) runs them on the tensor cores (tcgen05
- * MMAs on six exact BF16 slices per operand, exact FP32 sums per 64-wide K chunk,
- * ~2^-46 of the chunk's row and column maxima) when the block size is a multiple
- * of 16; mode 0 always runs the float-pair GEMM on the FP32 pipes (~2^-47).
+/* GEMM-shaped steps of the Tucker build (RHOSVD, Sec. 1, Algorithm TEP step 4): the
+ * block products Y = G Q of the subspace iteration and the projections of the
+ * shifted Gaussians on the factor basis.  Mode 1 (default) runs them on the tensor
+ * cores (tcgen05 MMAs on six exact BF16 slices per operand, exact FP32 sums per K
+ * chunk, ~2^-45 of the chunk's row and column maxima; G Q for grids up to 4097 and
+ * block sizes that are multiples of 16); mode 0 runs the float-pair kernels on the
+ * FP32 pipes (~2^-47).
  * Process-wide; takes effect for builds started afterwards.  Returns the previous
  * mode. */
 int       rs_set_build_gemm_kernel(int mode);

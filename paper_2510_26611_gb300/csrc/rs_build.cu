@@ -1113,6 +1113,281 @@ __global__ void __launch_bounds__(1024) k_core(int Rtot, int Rl, int CH,
     for (int c = 0; c < RP; ++c) out[c] = dev::df_to(acc[c]);
 }
 
+// ------------------------------------------------------------- tensor-core projection
+// k_project on tcgen05: for one axis, one long-range term k and 128 atoms m (in grid-row
+// order), C'[a, (m, k)] = sum_i Wp[i, a] g_k(x_i - x_m) is the GEMM (atoms x grid rows) x
+// (grid rows x a) with K = the grid rows of the CTA's window, cut into 32-row chunks.
+// The Gaussians are generated per chunk in float pairs (seeds by the pair exponential,
+// then the ratio recurrence g_{i+1} = g_i rho_i, rho_{i+1} = rho_i e^{-2 t^2 h^2}) and cut
+// into six exact BF16 slices straight into the A tile (scale per atom and chunk from the
+// largest Gaussian value in the chunk); Wp's slices per (column, chunk) are made once
+// per build (k_slice_wp).  The 21 slice products go to six TMEM accumulators, one per
+// diagonal (integer K-sums below 32 * 147456 < 2^24: exact), combined error-free per
+// chunk into float pairs and summed over the chunks in pair arithmetic.  Rows outside
+// an atom's own window (where its Gaussian is below e^-46 of the peak) are zero, as in
+// the float-pair kernel.
+constexpr int kPK = 32;                        // grid rows per K chunk
+constexpr uint32_t kPSBO = kPK * 16;           // bytes between 8-row groups of a tile
+constexpr uint32_t kPSliceA = 128 * kPK * 2;   // one slice of the A tile (8 KB)
+
+template <int NP>
+struct ProjShape {
+    static constexpr uint32_t SLICE_B = NP * kPK * 2;
+    static constexpr uint32_t A_BYTES = tcg::kS * kPSliceA;
+    static constexpr uint32_t B_BYTES = tcg::kS * SLICE_B;
+    static constexpr uint32_t BAR_OFF = A_BYTES + B_BYTES;  // [0] B copy, [1] MMAs
+    static constexpr uint32_t SLOT_OFF = BAR_OFF + 16;
+    static constexpr uint32_t BINV_OFF = SLOT_OFF + 16;
+    static constexpr uint32_t WIN_OFF = BINV_OFF + NP * 4;  // window bounds, 2 x 128 ints
+    static constexpr uint32_t SMEM = WIN_OFF + 2 * 128 * 4;
+    static constexpr uint32_t COLS = tcg::kS * NP;
+    static constexpr uint32_t NCOL = COLS <= 128 ? 128 : 256;
+};
+
+// B slices of Wp (n x RP float pairs per axis), K = the grid row: chunk kc of axis ax at
+// out + (ax KC + kc) B_BYTES (rows a >= RP zero), binv[(ax KC + kc) NP + a] = 1 / scale.
+template <int NP>
+__global__ void __launch_bounds__(NP) k_slice_wp(int n, int RP, int KC, const float2* __restrict__ Wp,
+                                                  uint8_t* __restrict__ out, float* __restrict__ binv) {
+    using Sh = ProjShape<NP>;
+    const int kc = blockIdx.x, ax = blockIdx.y, a = threadIdx.x;
+    const int i0 = kc * kPK;
+    const float2* Wa = Wp + (size_t)ax * n * RP;
+    float m = 0.f;
+    if (a < RP)
+        for (int i = i0; i < min(n, i0 + kPK); ++i) m = fmaxf(m, fabsf(Wa[(size_t)i * RP + a].x));
+    float sc, inv;
+    tc::row_scale(m, sc, inv);
+    binv[((size_t)ax * KC + kc) * NP + a] = inv;
+    uint8_t* tile = out + ((size_t)ax * KC + kc) * Sh::B_BYTES;
+#pragma unroll 1
+    for (int g = 0; g < kPK / 8; ++g) {
+        uint32_t w[tcg::kS][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float lo[tcg::kS], hi[tcg::kS];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int i = i0 + g * 8 + e + hh;
+                const float2 v = (a < RP && i < n) ? Wa[(size_t)i * RP + a] : make_float2(0.f, 0.f);
+                tcg::slice6(__fmul_rn(v.x, sc), __fmul_rn(v.y, sc), hh ? hi : lo);
+            }
+#pragma unroll
+            for (int u = 0; u < tcg::kS; ++u) w[u][e / 2] = tc::pack_bf16x2(lo[u], hi[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < tcg::kS; ++u)
+            *reinterpret_cast<uint4*>(tile + u * Sh::SLICE_B + tc::kmajor_offset(a, g * 8, kPSBO)) =
+                make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
+    }
+}
+
+template <int RP, int NP>
+__global__ void __launch_bounds__(128) k_project_tc(int n, double b, double h, int N, int Rl, int KC,
+                                                     const double* __restrict__ xyz,
+                                                     const double* __restrict__ tl,
+                                                     const int* __restrict__ perm,
+                                                     const float2* __restrict__ etab,
+                                                     const uint8_t* __restrict__ Bs,
+                                                     const float* __restrict__ binv,
+                                                     float2* __restrict__ Cp2, int* __restrict__ err) {
+    using dev::F2;
+    using Sh = ProjShape<NP>;
+    extern __shared__ __align__(16) uint8_t smem_p[];
+    uint8_t* sA = smem_p;
+    uint8_t* sB = smem_p + Sh::A_BYTES;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_p + Sh::BAR_OFF);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem_p + Sh::SLOT_OFF);
+    float* sbinv = reinterpret_cast<float*>(smem_p + Sh::BINV_OFF);
+    int* wlo = reinterpret_cast<int*>(smem_p + Sh::WIN_OFF);
+    int* whi = wlo + 128;
+    const int k = blockIdx.y, ax = blockIdx.z, tid = threadIdx.x, warp = tid >> 5;
+    const int mo = blockIdx.x * 128 + tid;
+    const bool valid = mo < N;
+    const int m = valid ? perm[(size_t)ax * N + mo] : 0;  // atoms in grid-row order
+    const double t2 = tl[k] * tl[k];
+    const double xm = valid ? xyz[3 * (size_t)m + ax] : 0.0;
+    int lo = n, hi = -1;
+    if (valid) {
+        if (t2 == 0.0) {
+            lo = 0;
+            hi = n - 1;
+        } else {
+            const double hw = sqrt(46.0 / t2);
+            const double l = fmax(ceil((xm - hw + b) / h), 0.0), u = fmin(floor((xm + hw + b) / h), (double)(n - 1));
+            if (l <= u) {
+                lo = (int)l;
+                hi = (int)u;
+            }
+        }
+    }
+    wlo[tid] = lo;
+    whi[tid] = hi;
+    if (warp == 0) tc::tmem_alloc(slot, Sh::NCOL);
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::mbar_init(bar + 1, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    for (int o = 64; o > 0; o >>= 1) {
+        if (tid < o) {
+            wlo[tid] = min(wlo[tid], wlo[tid + o]);
+            whi[tid] = max(whi[tid], whi[tid + o]);
+        }
+        __syncthreads();
+    }
+    const int ulo = wlo[0], uhi = whi[0];
+    const uint32_t tmem = *slot;
+    const uint32_t tl_lane = tmem + ((uint32_t)(warp * 32) << 16);
+    // pair constants of this atom's Gaussian: -t^2, h, the offset of row 0 (x_0 - x_m)
+    // and the ratio factor e^{-2 t^2 h^2}
+    const F2 nt2 = dev::df_from(-t2);
+    const F2 hp = dev::df_from(h);
+    const F2 base = dev::df_from(-b - xm);
+    const bool direct = t2 * h * h > 8.0;
+    const F2 cq = direct ? F2{0.f, 0.f} : df_exp(dev::df_from(-2.0 * t2 * h * h), etab);
+    const int ipeak = valid ? (int)rint((xm + b) / h) : 0;  // grid row nearest the atom
+    auto offset = [&](int i) { return dev::df_add(base, dev::df_mul(hp, F2{(float)i, 0.f})); };
+    auto gauss = [&](F2 d) { return df_exp(dev::df_mul(nt2, dev::df_mul(d, d)), etab); };
+    F2 acc[RP];
+#pragma unroll
+    for (int a = 0; a < RP; ++a) acc[a] = F2{0.f, 0.f};
+    uint32_t phase = 0;
+    bool failed = false;
+    const int kc0 = ulo <= uhi ? ulo / kPK : 0, kc1 = ulo <= uhi ? uhi / kPK : -1;
+    for (int kc = kc0; kc <= kc1; ++kc) {
+        const int i0 = kc * kPK;
+        if (tid == 0) {
+            tc::mbar_arrive_expect_tx(bar, Sh::B_BYTES);
+            tc::bulk_g2s(sB, Bs + ((size_t)ax * KC + kc) * Sh::B_BYTES, Sh::B_BYTES, bar);
+        }
+        if (tid < NP) sbinv[tid] = binv[((size_t)ax * KC + kc) * NP + tid];
+        // this atom's row of the A tile
+        const int ia = max(lo, i0), ib = min(hi, i0 + kPK - 1);
+        float ainv = 0.f;
+        if (ia <= ib) {
+            const int ip = min(max(ipeak, ia), ib);  // the chunk's row nearest the peak
+            const F2 gmax = gauss(offset(ip));
+            float sc;
+            tc::row_scale(__fmul_rn(gmax.h, 1.00000095367431640625f), sc, ainv);
+            F2 g = gauss(offset(ia));
+            F2 rho{0.f, 0.f};
+            if (!direct) {
+                const F2 d0 = offset(ia);
+                // rho_i = e^{-t^2 (2 d_i h + h^2)}
+                const F2 arg = dev::df_add(dev::df_mul(F2{2.f, 0.f}, dev::df_mul(d0, hp)), dev::df_mul(hp, hp));
+                rho = df_exp(dev::df_mul(nt2, arg), etab);
+            }
+#pragma unroll 1
+            for (int gq = 0; gq < kPK / 8; ++gq) {
+                uint32_t w[tcg::kS][4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    float slo[tcg::kS], shi[tcg::kS];
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int i = i0 + gq * 8 + e + hh;
+                        F2 val{0.f, 0.f};
+                        if (i >= ia && i <= ib) {
+                            if (direct) {
+                                val = gauss(offset(i));
+                            } else {
+                                val = g;
+                                g = dev::df_mul(g, rho);
+                                rho = dev::df_mul(rho, cq);
+                            }
+                        }
+                        tcg::slice6(__fmul_rn(val.h, sc), __fmul_rn(val.l, sc), hh ? shi : slo);
+                    }
+#pragma unroll
+                    for (int u = 0; u < tcg::kS; ++u) w[u][e / 2] = tc::pack_bf16x2(slo[u], shi[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < tcg::kS; ++u)
+                    *reinterpret_cast<uint4*>(sA + u * kPSliceA + tc::kmajor_offset(tid, gq * 8, kPSBO)) =
+                        make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
+            }
+        } else {
+#pragma unroll
+            for (int gq = 0; gq < kPK / 8; ++gq)
+#pragma unroll
+                for (int u = 0; u < tcg::kS; ++u)
+                    *reinterpret_cast<uint4*>(sA + u * kPSliceA + tc::kmajor_offset(tid, gq * 8, kPSBO)) =
+                        make_uint4(0u, 0u, 0u, 0u);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        const bool loaded = tc::mbar_wait_bounded(bar, phase);
+        if (tid == 0 && loaded) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NP);
+            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+            for (int d = 0; d < tcg::kS; ++d)
+#pragma unroll
+                for (int u = 0; u <= d; ++u) {
+                    const int v = d - u;
+#pragma unroll
+                    for (int ks = 0; ks < kPK / 16; ++ks) {
+                        const uint64_t ad = tc::smem_desc(a0 + u * kPSliceA + ks * 2 * tc::kLBO, tc::kLBO, kPSBO);
+                        const uint64_t bd = tc::smem_desc(b0 + v * Sh::SLICE_B + ks * 2 * tc::kLBO, tc::kLBO, kPSBO);
+                        tc::mma_bf16(tmem + (uint32_t)(d * NP), ad, bd, idesc, (u == 0 && ks == 0) ? 0u : 1u);
+                    }
+                }
+            tc::mma_commit(bar + 1);
+        }
+        const bool ok = loaded && tc::mbar_wait_bounded(bar + 1, phase);
+        phase ^= 1u;
+        failed = __syncthreads_or(!ok);
+        tc::fence_after_sync();
+        if (failed) {
+            if (!loaded && tid == 0) tc::mbar_wait_bounded(bar, phase ^ 1u);  // a copy still landing
+            break;
+        }
+#pragma unroll
+        for (int c0 = 0; c0 < NP; c0 += 16) {
+            if (c0 < RP) {
+                float x[tcg::kS][16];
+#pragma unroll
+                for (int d = 0; d < tcg::kS; d += 2)
+                    tc::tmem_ld16x2(tl_lane + d * NP + c0, tl_lane + (d + 1) * NP + c0, x[d], x[d + 1]);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    if (c0 + c < RP) {
+                        F2 sum{ldexpf(x[tcg::kS - 1][c], -8 * (tcg::kS - 1)), 0.f};
+#pragma unroll
+                        for (int d = tcg::kS - 2; d >= 0; --d) sum = dev::df_add(sum, F2{ldexpf(x[d][c], -8 * d), 0.f});
+                        const float scl = __fmul_rn(ainv, sbinv[c0 + c]);
+                        acc[c0 + c] = dev::df_add(acc[c0 + c], F2{__fmul_rn(sum.h, scl), __fmul_rn(sum.l, scl)});
+                    }
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(err, 1);
+#pragma unroll
+        for (int a = 0; a < RP; ++a) acc[a] = F2{__int_as_float(-1), 0.f};
+    }
+    if (valid) {
+        const size_t Rp = (size_t)N * Rl, col = (size_t)m * Rl + k;
+#pragma unroll
+        for (int a = 0; a < RP; ++a) {
+            float sh, sl;
+            dev::two_sum(acc[a].h, acc[a].l, sh, sl);
+            Cp2[((size_t)ax * RP + a) * Rp + col] = make_float2(sh, sl);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, Sh::NCOL);
+}
+
 // Piecewise-cubic table of the short-range radial function f(s) = sum_short a_k
 // exp(-t_k^2 s): on [j hs, (j+1) hs] the Hermite cubic of f and hs f' at both ends,
 // in u = s/hs - j, as Horner coefficients (FP64, stored as float pairs):
@@ -1147,19 +1422,43 @@ __global__ void k_to_float(size_t len, const double* __restrict__ in, float* __r
     if (i < len) out[i] = (float)in[i];
 }
 
+// Inputs of the tensor-core projection (use = false: the float-pair kernel).
+struct ProjTc {
+    bool use = false;
+    const float2* etab = nullptr;  // the pair exponential's table
+    uint8_t* Bs = nullptr;         // slices of Wp, 3 x KC x ProjShape<32>::B_BYTES
+    float* binv = nullptr;         // their scales, 3 x KC x 32
+    int* err = nullptr;
+};
+
 template <int RP>
 rs_status launch_project_core(cudaStream_t st, int n, double b, double h, int N, int Rl,
                               const double* xyz, const double* q, const double* tl,
                               const double* al, const int* perm, const float2* Wp2, float2* Cp2, double* Bp,
-                              int nchunk, int CH, double proj_points) {
+                              int nchunk, int CH, double proj_points, const ProjTc& tcp) {
     dim3 gp((N + 127) / 128, Rl, 3);
-    // FP32 pipe ops per active (row, atom, term): two pair products (9 each) and RP
-    // Dot2 steps (13 each)
-    double work = proj_points * (18.0 + 13.0 * RP);
-    {
+    if (tcp.use) {
+        constexpr int NP = RP <= 16 ? 16 : 32;
+        const int KC = (n + kPK - 1) / kPK;
+        {
+            ::rs::KernelTimer kt__("k_slice_wp", st, 0.0, false);
+            k_slice_wp<NP><<<dim3(KC, 3), NP, 0, st>>>(n, RP, KC, Wp2, tcp.Bs, tcp.binv);
+        }
+        auto kern = k_project_tc<RP, NP>;
+        RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ProjShape<NP>::SMEM));
+        // the projection's algorithmic flops: one product and one sum per (row, column, a)
+        ::rs::KernelTimer kt__("k_project_tc", st, 2.0 * RP * proj_points, true);
+        kern<<<gp, 128, ProjShape<NP>::SMEM, st>>>(n, b, h, N, Rl, KC, xyz, tl, perm, tcp.etab, tcp.Bs, tcp.binv,
+                                                  Cp2, tcp.err);
+    } else {
+        // FP32 pipe ops per active (row, atom, term): two pair products (9 each) and RP
+        // Dot2 steps (13 each)
+        const double work = proj_points * (18.0 + 13.0 * RP);
         ::rs::KernelTimer kt__("k_project", st, work, true);
         k_project<RP><<<gp, 128, 0, st>>>(n, b, h, N, Rl, xyz, tl, perm, Wp2, Cp2);
     }
+    double work;
     // FP32 pipe ops per column and (a, b): two pair products (9 each) and RP Dot2 steps
     work = (double)N * Rl * RP * RP * (18.0 + 13.0 * RP);
     RS_TRY_CUDA(cudaGetLastError());
@@ -1174,12 +1473,12 @@ rs_status launch_project_core(cudaStream_t st, int n, double b, double h, int N,
 rs_status dispatch_project_core(int RP, cudaStream_t st, int n, double b, double h, int N, int Rl,
                                 const double* xyz, const double* q, const double* tl,
                                 const double* al, const int* perm, const float2* Wp2, float2* Cp2, double* Bp,
-                                int nchunk, int CH, double proj_points) {
+                                int nchunk, int CH, double proj_points, const ProjTc& tcp) {
     switch (RP) {
 #define RS_CASE(R)                                                                                       \
     case R:                                                                                              \
         return launch_project_core<R>(st, n, b, h, N, Rl, xyz, q, tl, al, perm, Wp2, Cp2, Bp, nchunk, CH, \
-                                      proj_points);
+                                      proj_points, tcp);
         RS_CASE(4) RS_CASE(8) RS_CASE(12) RS_CASE(16) RS_CASE(20) RS_CASE(24) RS_CASE(28) RS_CASE(32)
 #undef RS_CASE
         default:
@@ -1719,8 +2018,23 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         note_launch(4);  // the timer counts one of the five launches
     }
     RS_TRY_CUDA(cudaGetLastError());
+    ProjTc tcp;
+    if (build_gemm_mode() == 1) {
+        const int KCp = (n + kPK - 1) / kPK;
+        int dev = 0;
+        RS_TRY_CUDA(cudaGetDevice(&dev));
+        tcp.use = true;
+        tcp.etab = d_etab;
+        tcp.err = tc_error_flag(dev);
+        if (!tcp.err) {
+            set_error("tensor-core projection: no error flag on device %d", dev);
+            return RS_ERR_CUDA;
+        }
+        RS_TRY(S.get(&tcp.Bs, (size_t)3 * KCp * ProjShape<32>::B_BYTES));
+        RS_TRY(S.get(&tcp.binv, (size_t)3 * KCp * 32));
+    }
     RS_TRY(dispatch_project_core(RP, st, n, b, h, N, Rl, d_xyz, d_q, d_tl, d_al, d_perm, d_Wp, d_Cp, d_Bp,
-                                 nchunk, CH, proj_points));
+                                 nchunk, CH, proj_points, tcp));
     size_t blen = (size_t)RP * RP * RP;
     {
         ::rs::KernelTimer kt__("k_sum_chunks", st, 0.0, false);
