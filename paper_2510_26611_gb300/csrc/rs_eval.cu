@@ -83,8 +83,7 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
             float cf[3];
             bool ins[3];
             F2 x[3];
-            double x64[3];
-            atom_geometry(P, lig, q, j, ry, x, x64, ci, cf, ins);
+            atom_geometry(P, lig, q, j, ry, x, ci, cf, ins);
             const float4* a0 = Fa0 + (size_t)ci[0] * ld4;
             const float4* a1 = Fa1 + (size_t)ci[1] * ld4;
             const float4* a2 = Fa2 + (size_t)ci[2] * ld4;
@@ -134,7 +133,7 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
             // short range split over lanes
             F2 phs{0.f, 0.f}, gs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             int clash = 0;
-            short_vdw<GRAD>(P, x, x64, lane, 32, phs, gs, clash);
+            short_vdw<GRAD>(P, x, AtomRef{&q, lig.y64 + 3 * j}, lane, 32, phs, gs, clash);
             phi += warp_sum(dev::df_to(phs));
             if constexpr (GRAD)
                 for (int a = 0; a < 3; ++a) gl[a] += warp_sum(dev::df_to(gs[a]));

@@ -94,11 +94,10 @@ __global__ void __launch_bounds__(32 * WPB)
         const PairDesc& pd = pairs[sg.pair];
         float ry[3] = {0.f, 0.f, 0.f};
         F2 x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        double x64[3] = {0.0, 0.0, 0.0};
         int ci[3] = {0, 0, 0};
         float cf[3] = {0.f, 0.f, 0.f};
         bool ins[3] = {true, true, true};
-        if (in_range) atom_geometry(pd.prot, pd.lig, ps[q], j, ry, x, x64, ci, cf, ins);
+        if (in_range) atom_geometry(pd.prot, pd.lig, ps[q], j, ry, x, ci, cf, ins);
         F2 php{0.f, 0.f}, gp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         int clash = 0;
         // the lanes of a warp may belong to different pairs: each near pair is evaluated
@@ -107,7 +106,8 @@ __global__ void __launch_bounds__(32 * WPB)
         __syncwarp();
         lp[lane] = sg.pair;
         __syncwarp();
-        short_coop_with<false>([&](int l) -> const ProteinView& { return pairs[lp[l]].prot; }, in_range, x, x64,
+        short_coop_with<false>([&](int l) -> const ProteinView& { return pairs[lp[l]].prot; }, in_range, x,
+                               AtomRef{&ps[q], pd.lig.y64 + 3 * j},
                                queues[wib], php, gp, clash);
         if (!in_range) continue;
         AtomRec r;

@@ -22,6 +22,25 @@ struct PoseSetup {
     int valid;
 };
 
+// FP64 position x = t + R y (12 FP64 operations; used only for vdW decisions
+// inside the sigma band, where the FP64 oracle's decision must be reproduced).
+__device__ __forceinline__ void atom_position64(const PoseSetup& q, const double* __restrict__ y64,
+                                                double x64[3]) {
+    const double y0 = y64[0], y1 = y64[1], y2 = y64[2];
+    for (int r = 0; r < 3; ++r)
+        x64[r] = __dadd_rn(q.t[r], fma(q.R[3 * r + 2], y2, fma(q.R[3 * r + 1], y1, __dmul_rn(q.R[3 * r], y0))));
+}
+
+// Where an atom's FP64 position comes from: its pose's FP64 setup and its FP64
+// ligand coordinates.  The position is formed only for the rare pair that falls
+// inside the +-1e-4 sigma^2 band (GB300 runs FP64 at 1/64 of its FP32 rate, and
+// every other decision is taken in FP32 or pair arithmetic).
+struct AtomRef {
+    const PoseSetup* q;
+    const double* y64;
+    __device__ __forceinline__ void pos64(double x64[3]) const { atom_position64(*q, y64, x64); }
+};
+
 __device__ __forceinline__ void setup_pose(const ProteinView& P, const double* __restrict__ rot,
                                            const double* __restrict__ trans, long long p,
                                            bool rotvec, PoseSetup& ps) {
@@ -70,7 +89,7 @@ __device__ __forceinline__ int short_screen(const ProteinView& P, const float xf
 // w = z_m, the radial function value fv = f(d2) and (gradients) fgr = 2 w f'(d2),
 // so the pair adds w fv to phi and fgr f to grad phi.
 template <bool GRAD>
-__device__ __forceinline__ int short_pair(const ProteinView& P, const F2 x[3], const double x64[3], int k,
+__device__ __forceinline__ int short_pair(const ProteinView& P, const F2 x[3], const AtomRef& ref, int k,
                                           int bits, F2 f[3], F2& w, F2& fv, F2& fgr) {
     const float4 ah = P.atoms[k], al = P.atoms_lo[k];
     f[0] = dev::df_sub(x[0], F2{ah.x, al.x});
@@ -88,7 +107,9 @@ __device__ __forceinline__ int short_pair(const ProteinView& P, const F2 x[3], c
             out = 1;
         } else {
             // inside the +-1e-4 sigma^2 band: the decision is taken in FP64 from the
-            // FP64 position and atom record (C-11)
+            // FP64 position and atom record
+            double x64[3];
+            ref.pos64(x64);
             const double4 a64 = P.atoms64[k];
             const double e0 = __dsub_rn(x64[0], a64.x), e1 = __dsub_rn(x64[1], a64.y),
                          e2 = __dsub_rn(x64[2], a64.z);
@@ -138,7 +159,7 @@ __device__ __forceinline__ void short_accumulate(F2 w, F2 fv, F2 fgr, const F2 f
 // (callers pass zeros) in candidate order; with nl = 1 the sums equal those of
 // short_coop for the same atom bit for bit.
 template <bool GRAD>
-__device__ __noinline__ void short_vdw(const ProteinView& P, const F2 x[3], const double x64[3], int lane,
+__device__ __noinline__ void short_vdw(const ProteinView& P, const F2 x[3], const AtomRef ref, int lane,
                                        int nl, F2& phi, F2 g[3], int& clash) {
     const float xf[3] = {x[0].h, x[1].h, x[2].h};
     int s, e;
@@ -147,7 +168,7 @@ __device__ __noinline__ void short_vdw(const ProteinView& P, const F2 x[3], cons
         const int bits = short_screen(P, xf, P.nb_atoms[j]);
         if (!(bits & 3)) continue;
         F2 f[3], w, fv{0.f, 0.f}, fgr{0.f, 0.f};
-        const int out = short_pair<GRAD>(P, x, x64, P.nb_idx[j], bits, f, w, fv, fgr);
+        const int out = short_pair<GRAD>(P, x, ref, P.nb_idx[j], bits, f, w, fv, fgr);
         if (out & 1) clash = 1;
         if (out & 2) short_accumulate<GRAD>(w, fv, fgr, f, phi, g);
     }
@@ -162,7 +183,8 @@ struct NearQueue {
     float2 w[32], fv[32], fgr[GRAD ? 32 : 1];
     float2 f[GRAD ? 3 : 1][32];
     float2 x[3][32]; // pair positions of the warp's atoms
-    double x64[3][32];  // FP64 positions (decisions inside the sigma band)
+    const PoseSetup* rq[32];  // where the atoms' FP64 positions come from (decisions
+    const double* ry64[32];   // inside the sigma band)
     int ls[32];         // first entry of each lane's candidate list
     int lstart[32];     // prefix of the lanes' list lengths over the warp
     int seg0[32], seg1[32];  // per owner lane: its entries [seg0, seg1) of a processed batch
@@ -182,7 +204,7 @@ struct ShortCounts {
 };
 
 template <bool GRAD, class ProtOf>
-__device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], const double x64[3],
+__device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], const AtomRef& ref,
                                 NearQueue<GRAD>& Q, F2& phi, F2 g[3], int& clash, ShortCounts* cnt = nullptr) {
     const int lane = threadIdx.x & 31;
     const ProteinView& P = prot_of(lane);
@@ -194,8 +216,9 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
         for (int a = 0; a < 3; ++a) {
             xf[a] = x[a].h;
             Q.x[a][lane] = make_float2(x[a].h, x[a].l);
-            Q.x64[a][lane] = x64[a];
         }
+        Q.rq[lane] = ref.q;
+        Q.ry64[lane] = ref.y64;
         int le;
         short_list(P, xf, ls, le);
         total = le - ls;
@@ -225,9 +248,9 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
             if (lane == m - 1 || Q.owner[lane + 1] != o) Q.seg1[o] = lane + 1;
             const F2 xo[3] = {F2{Q.x[0][o].x, Q.x[0][o].y}, F2{Q.x[1][o].x, Q.x[1][o].y},
                               F2{Q.x[2][o].x, Q.x[2][o].y}};
-            const double xo64[3] = {Q.x64[0][o], Q.x64[1][o], Q.x64[2][o]};
+            const AtomRef ro{Q.rq[o], Q.ry64[o]};
             F2 f[3], w, fv{0.f, 0.f}, fgr{0.f, 0.f};
-            const int out = short_pair<GRAD>(prot_of(o), xo, xo64, Q.k[lane], Q.bits[lane], f, w, fv, fgr);
+            const int out = short_pair<GRAD>(prot_of(o), xo, ro, Q.k[lane], Q.bits[lane], f, w, fv, fgr);
             Q.bits[lane] = out;
             Q.w[lane] = make_float2(w.h, w.l);
             Q.fv[lane] = make_float2(fv.h, fv.l);
@@ -297,10 +320,10 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
 
 // The same for a warp whose atoms all belong to protein P.
 template <bool GRAD>
-__device__ __forceinline__ void short_coop(const ProteinView& P, bool active, const F2 x[3], const double x64[3],
+__device__ __forceinline__ void short_coop(const ProteinView& P, bool active, const F2 x[3], const AtomRef& ref,
                                            NearQueue<GRAD>& Q, F2& phi, F2 g[3], int& clash,
                                            ShortCounts* cnt = nullptr) {
-    short_coop_with<GRAD>([&](int) -> const ProteinView& { return P; }, active, x, x64, Q, phi, g, clash, cnt);
+    short_coop_with<GRAD>([&](int) -> const ProteinView& { return P; }, active, x, ref, Q, phi, g, clash, cnt);
 }
 
 // Atom position x = R y + t in float-pair arithmetic (Dot2 of the pair rows of R
@@ -316,26 +339,16 @@ __device__ __forceinline__ void atom_position(const PoseSetup& q, const float2* 
     }
 }
 
-// FP64 position x = t + R y (12 FP64 operations; used only for vdW decisions
-// inside the sigma band, where the FP64 oracle's decision must be reproduced).
-__device__ __forceinline__ void atom_position64(const PoseSetup& q, const double* __restrict__ y64,
-                                                double x64[3]) {
-    const double y0 = y64[0], y1 = y64[1], y2 = y64[2];
-    for (int r = 0; r < 3; ++r)
-        x64[r] = __dadd_rn(q.t[r], fma(q.R[3 * r + 2], y2, fma(q.R[3 * r + 1], y1, __dmul_rn(q.R[3 * r], y0))));
-}
-
 // Geometry of ligand atom j in pose q: rotated offset R y in FP32 (torque arm of
-// the gradient), pair and FP64 positions, and per axis the interpolation cell,
-// fraction and whether the coordinate lies inside [-b, b].
+// the gradient), pair position, and per axis the interpolation cell, fraction and
+// whether the coordinate lies inside [-b, b].
 __device__ __forceinline__ void atom_geometry(const ProteinView& P, const LigandView& lig,
                                               const PoseSetup& q, int j, float ry[3],
-                                              F2 x[3], double x64[3], int ci[3], float cf[3], bool ins[3]) {
+                                              F2 x[3], int ci[3], float cf[3], bool ins[3]) {
     float4 yq = lig.y[j];
     for (int r = 0; r < 3; ++r)
         ry[r] = __fmaf_rn(q.Rf[3 * r + 2], yq.z, __fmaf_rn(q.Rf[3 * r + 1], yq.y, __fmul_rn(q.Rf[3 * r], yq.x)));
     atom_position(q, lig.yd + 3 * j, x);
-    atom_position64(q, lig.y64 + 3 * j, x64);
     for (int a = 0; a < 3; ++a)
         dev::axis_cell(x[a], F2{P.b_h, P.b_l}, F2{P.inv_h_h, P.inv_h_l}, P.n, ci[a], cf[a], ins[a]);
 }
@@ -468,12 +481,11 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
         float cf[3] = {0.f, 0.f, 0.f};
         bool ins[3] = {true, true, true};
         F2 x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        double x64[3] = {0.0, 0.0, 0.0};
-        if (valid) atom_geometry(P, lig, ps[pl], j, ry, x, x64, ci, cf, ins);
+        if (valid) atom_geometry(P, lig, ps[pl], j, ry, x, ci, cf, ins);
         // short range and vdW of the warp's atoms
         F2 phs{0.f, 0.f}, gs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         int clash = 0;
-        short_coop<GRAD>(P, valid, x, x64, queues[tid >> 5], phs, gs, clash);
+        short_coop<GRAD>(P, valid, x, AtomRef{&ps[pl], lig.y64 + 3 * j}, queues[tid >> 5], phs, gs, clash);
         if (!valid) continue;
         // v1 (axis 1) into this thread's shared-memory column; v2 (axis 2) in registers
         {

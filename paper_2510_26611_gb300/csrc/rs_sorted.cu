@@ -76,14 +76,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
         const bool valid = in_range && ps[pl].valid;
         float ry[3] = {0.f, 0.f, 0.f};
         F2 x[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        double x64[3] = {0.0, 0.0, 0.0};
         int ci[3] = {0, 0, 0};
         float cf[3] = {0.f, 0.f, 0.f};
         bool ins[3] = {true, true, true};
-        if (valid) atom_geometry(P, lig, ps[pl], j, ry, x, x64, ci, cf, ins);
+        if (valid) atom_geometry(P, lig, ps[pl], j, ry, x, ci, cf, ins);
         F2 php{0.f, 0.f}, gp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         int clash = 0;
-        short_coop<GRAD>(P, valid, x, x64, queues[wib], php, gp, clash, &sc);
+        short_coop<GRAD>(P, valid, x, AtomRef{&ps[pl], lig.y64 + 3 * j}, queues[wib], php, gp, clash, &sc);
         natoms += __popc(__ballot_sync(0xffffffffu, valid));
         if (!in_range) continue;
         AtomRec r;
