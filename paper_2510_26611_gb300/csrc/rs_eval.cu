@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
     constexpr int NC = GRAD ? 7 : 1;
     extern __shared__ __align__(16) unsigned char smem[];
     PoseSetup* ps = (PoseSetup*)smem;
-    double* contrib = (double*)(ps + PB);
+    float2* contrib = (float2*)(ps + PB);
     int* pflag = (int*)(contrib + (size_t)PB * lig.L * NC);
     const int L = lig.L;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
@@ -72,10 +72,10 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
         __syncthreads();
         for (int g = warp; g < PB * L; g += nw) {
             int pl = g / L, j = g - pl * L;
-            double* cj = contrib + (size_t)g * NC;
+            float2* cj = contrib + (size_t)g * NC;
             const PoseSetup& q = ps[pl];
             if (!q.valid) {
-                if (lane < NC) cj[lane] = 0.0;
+                if (lane < NC) cj[lane] = make_float2(0.f, 0.f);
                 continue;
             }
             float ry[3];
@@ -142,17 +142,23 @@ __global__ void __launch_bounds__(256) k_eval_canon(ProteinView P, LigandView li
                 int fl = clash ? RS_FLAG_CLASH : 0;
                 if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
                 if (fl) atomicOr(&pflag[pl], fl);
+                // the canonical path sums its rank terms in FP64; its contributions
+                // are stored as float pairs like every other path's
+                auto put = [&](int c, double v) {
+                    const dev::F2 p = dev::df_from(v);
+                    cj[c] = make_float2(p.h, p.l);
+                };
                 double qj = lig.q64[j];
-                cj[0] = qj * phi;
+                put(0, qj * phi);
                 if constexpr (GRAD) {
                     double g0 = qj * gl[0], g1 = qj * gl[1], g2 = qj * gl[2];
-                    cj[1] = g0;
-                    cj[2] = g1;
-                    cj[3] = g2;
+                    put(1, g0);
+                    put(2, g1);
+                    put(3, g2);
                     double r0 = ry[0], r1 = ry[1], r2 = ry[2];
-                    cj[4] = r1 * g2 - r2 * g1;
-                    cj[5] = r2 * g0 - r0 * g2;
-                    cj[6] = r0 * g1 - r1 * g0;
+                    put(4, r1 * g2 - r2 * g1);
+                    put(5, r2 * g0 - r0 * g2);
+                    put(6, r0 * g1 - r1 * g0);
                 }
             }
         }

@@ -68,7 +68,7 @@ template <int WPB>
 __global__ void __launch_bounds__(32 * WPB)
     k_group_atoms(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, int nseg, long long natom,
                   int ksub, const PoseSetup* __restrict__ ps, int* __restrict__ pflag,
-                  AtomRec* __restrict__ rec, double* __restrict__ shortv, int* __restrict__ count,
+                  AtomRec* __restrict__ rec, float2* __restrict__ shortv, int* __restrict__ count,
                   unsigned long long* __restrict__ cursor) {
     __shared__ NearQueue<false> queues[WPB];
     __shared__ int lane_pair[WPB][32];
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(32 * WPB)
         int fl = clash ? RS_FLAG_CLASH : 0;
         if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
         if (fl) atomicOr(&pflag[q], fl);
-        shortv[g] = dev::df_to(php);
+        shortv[g] = make_float2(php.h, php.l);
         r.i1 = ci[0];
         r.i2 = ci[1];
         r.i3 = sg.cell_base + ci[2];
@@ -135,8 +135,8 @@ __global__ void __launch_bounds__(32 * WPB)
 template <int RP, int WPB>
 __global__ void __launch_bounds__(32 * WPB, 20 / WPB)
     k_group_wform(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs,
-                  const AtomRec* __restrict__ srt, long long natom, const double* __restrict__ shortv,
-                  double* __restrict__ contrib) {
+                  const AtomRec* __restrict__ srt, long long natom, const float2* __restrict__ shortv,
+                  float2* __restrict__ contrib) {
     extern __shared__ float4 sm4[];
     constexpr int SLAB4 = RP * RP / 4;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -204,8 +204,8 @@ struct TcGroup {
 template <int RP>
 __global__ void __launch_bounds__(tc::kTileRows, 4)
     k_group_tc(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, const AtomRec* __restrict__ srt,
-               const int* __restrict__ off, int ksub, long long natom, const double* __restrict__ shortv,
-               double* __restrict__ contrib, int* __restrict__ err) {
+               const int* __restrict__ off, int ksub, long long natom, const float2* __restrict__ shortv,
+               float2* __restrict__ contrib, int* __restrict__ err) {
     extern __shared__ __align__(16) uint8_t smem_tc[];
     const long long per = (natom + gridDim.x - 1) / gridDim.x;
     const long long s0 = (long long)blockIdx.x * per, s1 = std::min<long long>(natom, s0 + per);
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(tc::kTileRows, 4)
 }
 
 __global__ void k_group_reduce(const PairDesc* __restrict__ pairs, const GroupSeg* __restrict__ segs, int nseg,
-                               int npose, const PoseSetup* __restrict__ ps, const double* __restrict__ contrib,
+                               int npose, const PoseSetup* __restrict__ ps, const float2* __restrict__ contrib,
                                const int* __restrict__ pflag) {
     const int lane = threadIdx.x & 31;
     const long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -234,8 +234,8 @@ struct GroupScratch {
     int* pflag;
     AtomRec* rec;
     AtomRec* srt;
-    double* shortv;
-    double* contrib;
+    float2* shortv;
+    float2* contrib;
     int* count;
     int* off;
     int* bsum;
@@ -263,8 +263,8 @@ GroupScratch carve_group(void* base, int npose, long long natom, int nkey, int k
     s.pflag = (int*)take((size_t)npose * 4);
     s.rec = (AtomRec*)take((size_t)natom * sizeof(AtomRec));
     s.srt = (AtomRec*)take((size_t)natom * sizeof(AtomRec));
-    s.shortv = (double*)take((size_t)natom * 8);
-    s.contrib = (double*)take((size_t)natom * 8);
+    s.shortv = (float2*)take((size_t)natom * 8);
+    s.contrib = (float2*)take((size_t)natom * 8);
     s.count = (int*)take((size_t)nkey * 4);
     s.off = (int*)take((size_t)(nkey + 1) * 4);
     s.bsum = (int*)take(key_scan_ints(nkey) * 4);

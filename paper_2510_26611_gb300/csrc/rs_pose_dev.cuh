@@ -353,27 +353,34 @@ __device__ __forceinline__ void atom_geometry(const ProteinView& P, const Ligand
         dev::axis_cell(x[a], F2{P.b_h, P.b_l}, F2{P.inv_h_h, P.inv_h_l}, P.n, ci[a], cf[a], ins[a]);
 }
 
-// Per-atom contributions to the pose sums from the long-range value (pair sums
-// phi, g1..g3 of the W-form loop) and the short-range sums: q_j phi_j and, for
-// gradients, q_j grad phi_j and the torque arm (R y_j) x q_j grad phi_j.
+// Per-atom contributions to the pose sums (float pairs) from the long-range value
+// (pair sums phi, g1..g3 of the W-form loop) and the short-range sums: q_j phi_j
+// and, for gradients, q_j grad phi_j and the torque arm (R y_j) x q_j grad phi_j.
 template <bool GRAD>
 __device__ __forceinline__ void atom_contrib(const ProteinView& P, dev::F2 phi, dev::F2 g1, dev::F2 g2,
-                                             dev::F2 g3, double phs, const double gs[3], double qj,
-                                             const float ry[3], double* cj) {
-    double ph = __dadd_rn(__dadd_rn((double)phi.h, (double)phi.l), phs);
-    cj[0] = __dmul_rn(qj, ph);
+                                             dev::F2 g3, dev::F2 phs, const dev::F2 gs[3], double qd,
+                                             const float ry[3], float2* cj) {
+    // float-pair arithmetic throughout (~2^-47): GB300 runs FP64 at 1/64 of its FP32
+    // rate, and these few operations per atom were a large share of the FP64 pipe
+    const F2 qj = dev::df_from(qd);
+    const F2 e = dev::df_mul(qj, dev::df_add(phi, phs));
+    cj[0] = make_float2(e.h, e.l);
     if constexpr (GRAD) {
-        double gl0 = __dadd_rn(__dmul_rn(__dadd_rn((double)g1.h, (double)g1.l), P.inv_h), gs[0]);
-        double gl1 = __dadd_rn(__dmul_rn(__dadd_rn((double)g2.h, (double)g2.l), P.inv_h), gs[1]);
-        double gl2 = __dadd_rn(__dmul_rn(__dadd_rn((double)g3.h, (double)g3.l), P.inv_h), gs[2]);
-        double g0 = __dmul_rn(qj, gl0), g1d = __dmul_rn(qj, gl1), g2d = __dmul_rn(qj, gl2);
-        cj[1] = g0;
-        cj[2] = g1d;
-        cj[3] = g2d;
-        double r0 = ry[0], r1 = ry[1], r2 = ry[2];
-        cj[4] = __dsub_rn(__dmul_rn(r1, g2d), __dmul_rn(r2, g1d));
-        cj[5] = __dsub_rn(__dmul_rn(r2, g0), __dmul_rn(r0, g2d));
-        cj[6] = __dsub_rn(__dmul_rn(r0, g1d), __dmul_rn(r1, g0));
+        const F2 ih{P.inv_h_h, P.inv_h_l};
+        const F2 g[3] = {g1, g2, g3};
+        F2 gq[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gq[a] = dev::df_mul(qj, dev::df_add(dev::df_mul(g[a], ih), gs[a]));
+            cj[1 + a] = make_float2(gq[a].h, gq[a].l);
+        }
+        const F2 r0{ry[0], 0.f}, r1{ry[1], 0.f}, r2{ry[2], 0.f};
+        const F2 t0 = dev::df_sub(dev::df_mul(r1, gq[2]), dev::df_mul(r2, gq[1]));
+        const F2 t1 = dev::df_sub(dev::df_mul(r2, gq[0]), dev::df_mul(r0, gq[2]));
+        const F2 t2 = dev::df_sub(dev::df_mul(r0, gq[1]), dev::df_mul(r1, gq[0]));
+        cj[4] = make_float2(t0.h, t0.l);
+        cj[5] = make_float2(t1.h, t1.l);
+        cj[6] = make_float2(t2.h, t2.l);
     }
 }
 
@@ -383,19 +390,30 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum over the atoms of one pose of its per-atom contributions [L][NC], by one
-// warp: lane-strided partial sums, then a butterfly; every lane ends with s.
+// Butterfly sum of float pairs over a warp (every lane ends with the same pair:
+// the pair sum is commutative).
+__device__ __forceinline__ F2 warp_sum_pair(F2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = dev::df_add(v, F2{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+    return v;
+}
+
+// Sum over the atoms of one pose of its per-atom contributions [L][NC] (float
+// pairs), by one warp: lane-strided pair sums, then a butterfly; every lane ends
+// with s (FP64).
 template <int NC>
-__device__ __forceinline__ void pose_sums(const double* __restrict__ cpose, int L, int lane, double s[NC]) {
+__device__ __forceinline__ void pose_sums(const float2* __restrict__ cpose, int L, int lane, double s[NC]) {
+    F2 acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) s[c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[c] = F2{0.f, 0.f};
     for (int j = lane; j < L; j += 32) {
-        const double* cj = cpose + (size_t)j * NC;
+        const float2* cj = cpose + (size_t)j * NC;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) s[c] = __dadd_rn(s[c], cj[c]);
+        for (int c = 0; c < NC; ++c) acc[c] = dev::df_add(acc[c], F2{cj[c].x, cj[c].y});
     }
 #pragma unroll
-    for (int c = 0; c < NC; ++c) s[c] = warp_sum(s[c]);
+    for (int c = 0; c < NC; ++c) s[c] = dev::df_to(warp_sum_pair(acc[c]));
 }
 
 // Outputs of one pose from its sums: E, flags and, for gradients, dE/dt and
@@ -416,7 +434,7 @@ __device__ __forceinline__ void write_pose(const PoseSetup& q, const double s[NC
 // Reduction of per-atom contributions to per-pose outputs (one warp per pose).
 template <int NC>
 __device__ void reduce_poses(const ProteinView& P, int PB, int L, long long p0, long long Ptot,
-                             const PoseSetup* ps, const double* contrib, const int* pflag,
+                             const PoseSetup* ps, const float2* contrib, const int* pflag,
                              double* __restrict__ E, uint8_t* __restrict__ flags,
                              double* __restrict__ gt, double* __restrict__ gw) {
     int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
@@ -452,7 +470,7 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
     constexpr int NV = GRAD ? 4 : 2;  // per-thread smem planes: v1h, v1l (, dv1h, dv1l)
     float* v1s = (float*)smem;                                   // [NV][RP][NT]
     PoseSetup* ps = (PoseSetup*)(v1s + NV * RP * NT);
-    double* contrib = (double*)(ps + PB);
+    float2* contrib = (float2*)(ps + PB);
     int* pflag = (int*)(contrib + (size_t)PB * lig.L * NC);
     NearQueue<GRAD>* queues = (NearQueue<GRAD>*)((((uintptr_t)(pflag + PB)) + 15) / 16 * 16);
     const int L = lig.L;
@@ -470,11 +488,11 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
         const int g = base + tid;
         const bool in_range = g < PB * L;
         const int pl = in_range ? g / L : 0, j = in_range ? g - pl * L : 0;
-        double* cj = contrib + (size_t)g * NC;
+        float2* cj = contrib + (size_t)g * NC;
         const bool valid = in_range && ps[pl].valid;
         if (in_range && !valid) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) cj[c] = 0.0;
+            for (int c = 0; c < NC; ++c) cj[c] = make_float2(0.f, 0.f);
         }
         float ry[3] = {0.f, 0.f, 0.f};
         int ci[3] = {0, 0, 0};
@@ -573,8 +591,7 @@ __device__ __forceinline__ void wform_block(const ProteinView& P, const LigandVi
         int fl = clash ? RS_FLAG_CLASH : 0;
         if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
         if (fl) atomicOr(&pflag[pl], fl);
-        const double gsd[3] = {dev::df_to(gs[0]), dev::df_to(gs[1]), dev::df_to(gs[2])};
-        atom_contrib<GRAD>(P, phi, g1, g2, g3, dev::df_to(phs), gsd, lig.q64[j], ry, cj);
+        atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, lig.q64[j], ry, cj);
     }
     __syncthreads();
     reduce_poses<NC>(P, PB, L, p0, Ptot, ps, contrib, pflag, E, flags, gt, gw);

@@ -54,7 +54,7 @@ __global__ void k_sorted_poses(ProteinView P, const double* __restrict__ rot,
 template <bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     k_sorted_atoms(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
-                   int* __restrict__ pflag, AtomRec* __restrict__ rec, double* __restrict__ shortv,
+                   int* __restrict__ pflag, AtomRec* __restrict__ rec, float2* __restrict__ shortv,
                    int* __restrict__ count, unsigned long long* __restrict__ counters,
                    unsigned long long* __restrict__ cursor) {
     __shared__ NearQueue<GRAD> queues[kWarpsPerBlock];
@@ -97,12 +97,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
         int fl = clash ? RS_FLAG_CLASH : 0;
         if (!(ins[0] && ins[1] && ins[2])) fl |= RS_FLAG_OUT_OF_GRID;
         if (fl) atomicOr(&pflag[pl], fl);
-        if constexpr (GRAD) {
-            double4 v = make_double4(dev::df_to(php), dev::df_to(gp[0]), dev::df_to(gp[1]), dev::df_to(gp[2]));
-            reinterpret_cast<double4*>(shortv)[g] = v;
-        } else {
-            shortv[g] = dev::df_to(php);
-        }
+        store_short_value<GRAD>(shortv, g, php, gp);
         r.i1 = ci[0];
         r.i2 = ci[1];
         r.i3 = ci[2];
@@ -130,7 +125,7 @@ template <int RP, bool GRAD>
 // more registers and measured 14 % slower).
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, GRAD ? 3 : 5)
     k_sorted_wform(ProteinView P, LigandView lig, const AtomRec* __restrict__ srt, const int* __restrict__ off,
-                   const double* __restrict__ shortv, double* __restrict__ contrib) {
+                   const float2* __restrict__ shortv, float2* __restrict__ contrib) {
     extern __shared__ float4 sm4[];
     constexpr int SLAB4 = RP * RP / 4;  // float4 per plane
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -176,8 +171,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, GRAD ? 3 : 5)
 template <int RP, bool GRAD>
 __global__ void __launch_bounds__(tc::kTileRows, 4)
     k_sorted_tc(const __grid_constant__ ProteinView P, const __grid_constant__ LigandView lig,
-                const AtomRec* __restrict__ srt, const int* __restrict__ off, const double* __restrict__ shortv,
-                double* __restrict__ contrib, int* __restrict__ err) {
+                const AtomRec* __restrict__ srt, const int* __restrict__ off, const float2* __restrict__ shortv,
+                float2* __restrict__ contrib, int* __restrict__ err) {
     extern __shared__ __align__(16) uint8_t smem_tc[];
     const long long Mv = off[(P.n - 1) * kSub];
     const long long per = (Mv + gridDim.x - 1) / gridDim.x;
@@ -188,7 +183,7 @@ __global__ void __launch_bounds__(tc::kTileRows, 4)
 
 template <int NC>
 __global__ void k_sorted_reduce(const PoseSetup* __restrict__ ps, int PC, int L, long long p0,
-                                const double* __restrict__ contrib, const int* __restrict__ pflag,
+                                const float2* __restrict__ contrib, const int* __restrict__ pflag,
                                 double* __restrict__ E, uint8_t* __restrict__ flags, double* __restrict__ gt,
                                 double* __restrict__ gw) {
     const int lane = threadIdx.x & 31;
@@ -205,8 +200,8 @@ struct SortedScratch {
     int* pflag;
     AtomRec* rec;
     AtomRec* srt;
-    double* shortv;
-    double* contrib;
+    float2* shortv;
+    float2* contrib;
     int* count;
     int* off;
     int* bsum;  // segment sums of the key scan
@@ -237,8 +232,8 @@ SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
     s.pflag = (int*)take(PC * 4);
     s.rec = (AtomRec*)take(M * sizeof(AtomRec));
     s.srt = (AtomRec*)take(M * sizeof(AtomRec));
-    s.shortv = (double*)take(M * 8 * (grad ? 4 : 1));
-    s.contrib = (double*)take(M * 8 * NC);
+    s.shortv = (float2*)take(M * 8 * (grad ? 4 : 1));
+    s.contrib = (float2*)take(M * 8 * NC);
     s.count = (int*)take((size_t)n * kSub * 4);
     s.off = (int*)take(((size_t)n * kSub + 1) * 4);
     s.bsum = (int*)take(key_scan_ints((long long)n * kSub) * 4);
@@ -430,10 +425,11 @@ __global__ void k_fd_radius(LigandView lig, double r0, double* __restrict__ out)
 //   E, Fsum = sum F_l, F0 = sum of the radial parts (Eq. Field_Xcenter),
 //   Fphi = sum (|r_l| / r0) x tangential part (Eq. Field_phi), M = sum r_l x F_l.
 // The differences c_0 - c_i cancel most of their operands' digits and are taken in
-// FP64 (as is E); the quotients keep ~2^-24 of F_l in FP32, and the split and the
-// vector sums run in FP32 (FP64 throughput is a small fraction of FP32's here).
+// float-pair arithmetic (E is summed exactly as the pose sums of the other paths);
+// the quotients keep ~2^-24 of F_l in FP32, and the split and the vector sums run
+// in FP32 (FP64 throughput is a small fraction of FP32's here).
 __global__ void k_fd_reduce(const PoseSetup* __restrict__ ps, int pc, LigandView lig, long long p0,
-                            const double* __restrict__ contrib, const int* __restrict__ pflag, double inv_h,
+                            const float2* __restrict__ contrib, const int* __restrict__ pflag, double inv_h,
                             const double* __restrict__ r0p, FdOut o) {
     const int lane = threadIdx.x & 31;
     const long long pl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -442,16 +438,20 @@ __global__ void k_fd_reduce(const PoseSetup* __restrict__ ps, int pc, LigandView
     const PoseSetup& q = ps[4 * pl];
     const double r0 = *r0p;
     const float inv_r0 = r0 > 0.0 ? (float)(1.0 / r0) : 0.f;
-    const double* c0 = contrib + (size_t)(4 * pl) * L;
-    double E = 0.0;
+    const float2* c0 = contrib + (size_t)(4 * pl) * L;
+    const float ih = (float)inv_h;
     float s[12];
 #pragma unroll
     for (int c = 0; c < 12; ++c) s[c] = 0.f;
     for (int j = lane; j < L; j += 32) {
-        const double e0 = c0[j];
+        const F2 e0{c0[j].x, c0[j].y};
         float F[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) F[i] = (float)((e0 - c0[(size_t)(i + 1) * L + j]) * inv_h);
+        for (int i = 0; i < 3; ++i) {
+            const float2 ci = c0[(size_t)(i + 1) * L + j];
+            const F2 d = dev::df_sub(e0, F2{ci.x, ci.y});
+            F[i] = __fmul_rn(__fadd_rn(d.h, d.l), ih);
+        }
         const float4 y = lig.y[j];
         float r[3];
 #pragma unroll
@@ -471,7 +471,6 @@ __global__ void k_fd_reduce(const PoseSetup* __restrict__ ps, int pc, LigandView
             Fr[2] = F[2];
         }
         const float sc = rn * inv_r0;
-        E += e0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             s[a] += F[a];
@@ -482,7 +481,9 @@ __global__ void k_fd_reduce(const PoseSetup* __restrict__ ps, int pc, LigandView
         s[10] += r[2] * F[0] - r[0] * F[2];
         s[11] += r[0] * F[1] - r[1] * F[0];
     }
-    E = warp_sum(E);
+    double E1[1];
+    pose_sums<1>(c0, L, lane, E1);
+    const double E = E1[0];
 #pragma unroll
     for (int c = 0; c < 12; ++c)
 #pragma unroll

@@ -140,13 +140,42 @@ __global__ void k_sorted_scatter(long long M, int ksub, const AtomRec* __restric
 }
 
 
+// Short-range value of a pose-atom (float pairs): phi_s (energies) or phi_s and its
+// gradient (4 pairs) at index slot.
+template <bool GRAD>
+__device__ __forceinline__ void short_value(const float2* __restrict__ shortv, long long slot, dev::F2& phs,
+                                            dev::F2 gs[3]) {
+    if constexpr (GRAD) {
+        const float4 a = reinterpret_cast<const float4*>(shortv)[2 * slot];
+        const float4 b = reinterpret_cast<const float4*>(shortv)[2 * slot + 1];
+        phs = dev::F2{a.x, a.y};
+        gs[0] = dev::F2{a.z, a.w};
+        gs[1] = dev::F2{b.x, b.y};
+        gs[2] = dev::F2{b.z, b.w};
+    } else {
+        const float2 v = shortv[slot];
+        phs = dev::F2{v.x, v.y};
+    }
+}
+
+template <bool GRAD>
+__device__ __forceinline__ void store_short_value(float2* __restrict__ shortv, long long slot, dev::F2 phs,
+                                                  const dev::F2 gs[3]) {
+    if constexpr (GRAD) {
+        reinterpret_cast<float4*>(shortv)[2 * slot] = make_float4(phs.h, phs.l, gs[0].h, gs[0].l);
+        reinterpret_cast<float4*>(shortv)[2 * slot + 1] = make_float4(gs[1].h, gs[1].l, gs[2].h, gs[2].l);
+    } else {
+        shortv[slot] = make_float2(phs.h, phs.l);
+    }
+}
+
 // Long range of one atom from its record (ligand atom j), with the axis-3 slab of
 // its cell in shared memory (planes Wh, Wl, Dh, Dl of RP x RP floats); writes its
 // contributions at slot r.slot.
 template <int RP, bool GRAD>
 __device__ __forceinline__ void sorted_atom(const ProteinView& P, const LigandView& lig, const AtomRec& r, int j,
-                                            const float* __restrict__ slab, const double* __restrict__ shortv,
-                                            double* __restrict__ contrib) {
+                                            const float* __restrict__ slab, const float2* __restrict__ shortv,
+                                            float2* __restrict__ contrib) {
     using dev::F2;
     constexpr int NC = GRAD ? 7 : 1;
     const bool in1 = r.bits & 1, in2 = r.bits & 2, in3 = r.bits & 4;
@@ -212,16 +241,8 @@ __device__ __forceinline__ void sorted_atom(const ProteinView& P, const LigandVi
             dev::df_fma_acc(g3, va, u3);
         }
     }
-    double phs, gs[3] = {0.0, 0.0, 0.0};
-    if constexpr (GRAD) {
-        double4 v = reinterpret_cast<const double4*>(shortv)[r.slot];
-        phs = v.x;
-        gs[0] = v.y;
-        gs[1] = v.z;
-        gs[2] = v.w;
-    } else {
-        phs = shortv[r.slot];
-    }
+    F2 phs, gs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    short_value<GRAD>(shortv, r.slot, phs, gs);
     const float ry[3] = {r.ry0, r.ry1, r.ry2};
     atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, lig.q64[j], ry, contrib + (size_t)r.slot * NC);
 }

@@ -134,7 +134,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t& phase, const At
 template <int RP, bool GRAD, class Src>
 __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __restrict__ srt,
                                                const int* __restrict__ off, int ksub, long long s0, long long s1,
-                                               const double* __restrict__ shortv, double* __restrict__ contrib,
+                                               const float2* __restrict__ shortv, float2* __restrict__ contrib,
                                                uint8_t* smem, int* __restrict__ err) {
     using S = tc::Shape<RP>;
     using Lay = TcLayout<RP, GRAD>;
@@ -187,18 +187,8 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
         (void)in3;
         const float f3 = r.f3;
         // short-range value (DRAM) and the axis-1 rows (L2), issued now
-        double phs = 0.0, gs[3] = {0.0, 0.0, 0.0};
-        if (act) {
-            if constexpr (GRAD) {
-                const double4 v = reinterpret_cast<const double4*>(shortv)[r.slot];
-                phs = v.x;
-                gs[0] = v.y;
-                gs[1] = v.z;
-                gs[2] = v.w;
-            } else {
-                phs = shortv[r.slot];
-            }
-        }
+        F2 phs{0.f, 0.f}, gs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        if (act) short_value<GRAD>(shortv, r.slot, phs, gs);
         F2 va[RP];
         F2 dva[GRAD ? RP : 1];
         F2 phi{0.f, 0.f}, g1{0.f, 0.f}, g2{0.f, 0.f}, g3{0.f, 0.f};
@@ -287,7 +277,7 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
         }
         if (!ok) {
             if (act)
-                for (int c = 0; c < NC; ++c) contrib[(size_t)r.slot * NC + c] = __longlong_as_double(-1LL);
+                for (int c = 0; c < NC; ++c) contrib[(size_t)r.slot * NC + c] = make_float2(__int_as_float(-1), 0.f);
             if (tid == 0) atomicExch(err, 1);
             break;
         }
