@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="step mode: skip the served, batched and PGD sub-measurements")
-    ap.add_argument("--mode", choices=["step", "batch", "pgd", "serve", "fd", "ppiem", "localbox", "complex"],
+    ap.add_argument("--mode", choices=["step", "build", "batch", "pgd", "serve", "fd", "ppiem", "localbox", "complex"],
                     default="step",
                     help="step: the protein-scale hot-path step (default); batch: 64 uneven "
                          "pairs in one persistent graph launch vs 64 plain launches; pgd: "
@@ -190,7 +190,12 @@ POSE_ATOM_KERNELS = ("k_sorted_tc", "k_sorted_tc_grad", "k_sorted_wform", "k_sor
 # DRAM bytes (read + write) per pose-atom from one ncu capture of the kernel on a
 # small case of the same workload, with the digest of the kernel's sources at that
 # capture; a kernel whose sources changed since reports traffic null.
-TRAFFIC = {}
+TRAFFIC = {
+    name: {"bytes_per_pose_atom": b, "sources": "45bf52164af71775",
+           "profile": "profiles/pose_kernels_dram_protein_p100000.md"}
+    for name, b in (("k_sorted_tc_grad", 285.9), ("k_sorted_tc", 111.9), ("k_sorted_atoms_grad", 74.3),
+                    ("k_sorted_atoms", 51.3))
+}
 TRAFFIC_SOURCES = ("rs_sorted.cu", "rs_sorted_dev.cuh", "rs_tc.cuh", "rs_tc_dev.cuh", "rs_pose_dev.cuh",
                    "rs_common.cuh")
 
@@ -505,6 +510,48 @@ def measure_batch(args) -> dict:
 
 def run_batch(args):
     print(json.dumps(measure_batch(args)), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ build mode
+def run_build(args):
+    """Algorithm TEP alone: the protein-scale Tucker build (N=3000, n=1025, rank <= 20),
+    timed per build with CUDA events, then once more per kernel (timing events on)."""
+    import torch
+    from paper_2510_26611_gb300 import lib
+    dev = torch.device("cuda", 0)
+    w, _ = workload(16)
+    ctx = lib.Context(0)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    xyz, q = T(w.prot_xyz), T(w.prot_q)
+    prm = lib.rs_params_default(n=w.n, b=w.b, sigma=w.sigma, R_l=w.R_l, tucker_cap=w.tucker_cap)
+    for _ in range(args.warmup):
+        lib.rs_protein_free(lib.rs_build_protein(ctx.handle, xyz, q, prm))
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        for a, b in ev:
+            a.record()
+            lib.rs_protein_free(lib.rs_build_protein(ctx.handle, xyz, q, prm))
+            b.record()
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    lib.rs_timing_reset()
+    lib.rs_timing_enable(2)
+    h = lib.rs_build_protein(ctx.handle, xyz, q, prm)
+    info = lib.rs_protein_get_info(h)
+    lib.rs_protein_free(h)
+    torch.cuda.synchronize()
+    kernels = {k: {"ms": round(v["ms"], 4), "launches": v["launches"]}
+               for k, v in sorted(lib.rs_timing_all().items(), key=lambda kv: -kv[1]["ms"])}
+    lib.rs_timing_enable(0)
+    line = {"metric": "Tucker build (Algorithm TEP) time", "value": round(ms, 4), "unit": "ms",
+            "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": WORKLOAD.split("; P=")[0], "n": w.n, "protein_atoms": w.N},
+            "ranks": info["rank"], "clocks": clk.summary(),
+            "kernels_one_build_with_timing_events": kernels}
+    print(json.dumps(line), flush=True)
+    ctx.close()
     return 0
 
 
@@ -1288,6 +1335,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "build":
+        return run_build(args)
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "pgd":
