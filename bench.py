@@ -180,7 +180,7 @@ KERNEL_KIND = {
     "k_sorted_tc": ("alu", "fp32ops"), "k_sorted_tc_grad": ("alu", "fp32ops"), "k_group_tc": ("alu", "fp32ops"),
     "k_sorted_atoms": ("alu", "fp32ops"), "k_sorted_atoms_grad": ("alu", "fp32ops"),
     "k_project": ("alu", "fp32ops"), "k_core": ("alu", "fp32ops"), "k_gauss_dsum": ("alu", "fp32ops"),
-    "k_gram": ("alu", "fp64"), "k_gemm_gq": ("alu", "fp32ops"), "k_canon_factors": ("hbm", "bytes"),
+    "k_gram": ("alu", "fp32ops"), "k_gemm_gq": ("alu", "fp32ops"), "k_canon_factors": ("hbm", "bytes"),
 }
 
 # Pose kernels whose unit is one pose-atom (one ligand atom of one pose).

@@ -433,36 +433,57 @@ __global__ void __launch_bounds__(128) k_gauss_dsum(int n, double b, double h, i
         if (s0 + s < S) out[s0 + s] = dev::df_to(acc[s]);
 }
 
+// out[i] = sum over the chunks of in[c][i] (FP64, four interleaved partial sums in a
+// fixed order: the dependent FP64 add chain is GB300's cost here); out2 (if not null)
+// gets the sums as float pairs.
 __global__ void k_sum_chunks(size_t len, int nchunk, const double* __restrict__ in,
-                             double* __restrict__ out) {
+                             double* __restrict__ out, float2* __restrict__ out2) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
-    double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += in[(size_t)c * len + i];
-    out[i] = s;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    int c = 0;
+    for (; c + 4 <= nchunk; c += 4)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] += in[(size_t)(c + u) * len + i];
+    for (; c < nchunk; ++c) s[c & 3] += in[(size_t)c * len + i];
+    const double v = (s[0] + s[1]) + (s[2] + s[3]);
+    out[i] = v;
+    if (out2) {
+        const dev::F2 p = dev::df_from(v);
+        out2[i] = make_float2(p.h, p.l);
+    }
 }
 
+// WE[k][d] = |a_k|^{2/3} exp(-t_k^2 (d h)^2 / 2) as float pairs (the distance factor
+// of the product identity with its weight).
 __global__ void k_exp_table(int n, double h, int Rl, const double* __restrict__ tl,
-                            double* __restrict__ E) {
+                            const double* __restrict__ w2, float2* __restrict__ WE) {
     int d = blockIdx.x * blockDim.x + threadIdx.x;
     int k = blockIdx.y;
     if (d >= n) return;
     double x = d * h;
-    E[(size_t)k * n + d] = exp(-0.5 * tl[k] * tl[k] * x * x);
+    const dev::F2 p = dev::df_from(w2[k] * exp(-0.5 * tl[k] * tl[k] * x * x));
+    WE[(size_t)k * n + d] = make_float2(p.h, p.l);
 }
 
-__global__ void k_gram(int n, int Rl, const double* __restrict__ w2, const double* __restrict__ E,
-                       const double* __restrict__ D, float2* __restrict__ G) {
+// G[i, j] = sum_k WE[k][|i - j|] D[k][i + j] in float-pair arithmetic: every term is
+// positive, so the pair sum keeps ~2^-47 of G (GB300's FP64 rate made the FP64
+// version of this 3 n^2 R_l-term sum throughput-bound).
+__global__ void k_gram(int n, int Rl, const float2* __restrict__ WE, const float2* __restrict__ D2,
+                       float2* __restrict__ G) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     int ax = blockIdx.z;
     if (j >= n) return;
     const int S = 2 * n - 1;
     int d = abs(i - j);
-    const double* Dax = D + (size_t)ax * Rl * S;
-    double s = 0.0;
-    for (int k = 0; k < Rl; ++k) s += w2[k] * E[(size_t)k * n + d] * Dax[(size_t)k * S + i + j];
-    const dev::F2 g = dev::df_from(s);
+    const float2* Dax = D2 + (size_t)ax * Rl * S;
+    dev::F2 s{0.f, 0.f};
+    for (int k = 0; k < Rl; ++k) {
+        const float2 a = WE[(size_t)k * n + d], b = Dax[(size_t)k * S + i + j];
+        dev::df_fma_acc(s, dev::F2{a.x, a.y}, dev::F2{b.x, b.y});
+    }
+    const dev::F2 g = dev::df_norm(s);
     G[((size_t)ax * n + i) * n + j] = make_float2(g.h, g.l);
 }
 
@@ -601,10 +622,10 @@ __global__ void __launch_bounds__(256) k_gemm_reduce(int n, int p, int nks, cons
     double* out = Sp + ((size_t)ax * gridDim.x + blockIdx.x) * p * p;
     for (int e = threadIdx.x; e < p * p; e += 256) {
         int a = e / p, c = e % p;
-        double s = 0.0;
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int rr = 0; rr < 16; ++rr) s += Ys[rr][a] * Ys[rr][c];
-        out[e] = s;
+        for (int rr = 0; rr < 16; ++rr) s[rr & 3] = fma(Ys[rr][a], Ys[rr][c], s[rr & 3]);
+        out[e] = (s[0] + s[1]) + (s[2] + s[3]);
     }
 }
 
@@ -614,9 +635,13 @@ __global__ void k_sum_gram(int nblk, int p, const double* __restrict__ Sp, doubl
     int ax = blockIdx.y;
     if (e >= p * p) return;
     const double* src = Sp + (size_t)ax * nblk * p * p + e;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += src[(size_t)b * p * p];
-    S[(size_t)ax * p * p + e] = s;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};  // four interleaved partial sums, fixed order
+    int b = 0;
+    for (; b + 4 <= nblk; b += 4)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] += src[(size_t)(b + u) * p * p];
+    for (; b < nblk; ++b) s[b & 3] += src[(size_t)b * p * p];
+    S[(size_t)ax * p * p + e] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 // Partial products Sp[ax][blk] = A_blk^T B_blk (p x p) of 16-row blocks of A and
@@ -636,42 +661,56 @@ __global__ void __launch_bounds__(256) k_atb(int n, int p, const double* __restr
     double* out = Sp + ((size_t)ax * gridDim.x + blockIdx.x) * p * p;
     for (int e = threadIdx.x; e < p * p; e += 256) {
         const int a = e / p, c = e % p;
-        double s = 0.0;
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int r = 0; r < 16; ++r) s += As[r][a] * Bs[r][c];
-        out[e] = s;
+        for (int r = 0; r < 16; ++r) s[r & 3] = fma(As[r][a], Bs[r][c], s[r & 3]);
+        out[e] = (s[0] + s[1]) + (s[2] + s[3]);
     }
 }
 
-// Cholesky S + shift*I = R^T R (R upper) and Rinv = R^{-1}; one CTA per axis.
-// GB300 runs FP64 at 1/64 of its FP32 rate, so a p x p factorisation is bound by the
-// latency of its sequential FP64 chain: each of the p steps keeps one pivot
-// operation (one reciprocal square root, by one thread) and one barrier, and every
-// other operation is spread over the 16 x 16 thread tile.
+// Cholesky S + shift*I = R^T R (R upper) and Rinv = R^{-1} (p <= 48) in float-pair
+// arithmetic: one CTA per axis, 256 threads over a 16 x 16 tile, one pivot operation
+// and two barriers per step.
 //   Cholesky, right-looking: step k takes rk = 1/sqrt(A[k][k]), writes row k of R
 //   (A[k][j] rk) and updates the trailing upper triangle by A[k][i] A[k][j] rk^2.
 //   Inverse, by rows from the bottom: X[k][k] = rk, X[k][j] = -rk acc[k][j], and
 //   acc[i][j] += R[i][k] X[k][j] for i < k <= j, one barrier per row.
-__global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restrict__ S,
-                                                    double rel_shift,
-                                                    double* __restrict__ Rinv,
-                                                    int* __restrict__ fail) {
-    __shared__ double A[48][49];   // factorised in place; upper triangle ends as R
-    __shared__ double X[48][49];   // accumulators, then R^{-1}
-    __shared__ double rk[48];      // 1 / R[k][k]
-    __shared__ double red[32];
+// S is a Gram matrix: a pivot at or below 1e-14 of its trace belongs to a direction
+// the block does not span (a rank-deficient block, e.g. a protein with fewer Gaussian
+// terms than the block size); its column of Q becomes 0 (R[k][k] = 0, rk = 0) instead
+// of amplifying rounding noise, and only a NaN pivot is a failure.  GB300 takes ~40 cycles per dependent FP64 FMA and ~450 for an
+// FP64 reciprocal square root against ~4 per FP32 operation, and each step's chain
+// (pivot -> row scale -> trailing update) sets the time, so the chain runs on the
+// FP32 pipes: the pivot's reciprocal square root is an FP32 seed refined by one Newton
+// step in pairs (~2^-45).  Pair accuracy suffices: Q = Y R^-1 spans Y's columns for any
+// nonsingular R as long as the product itself is taken accurately (k_apply_rinv,
+// FP64), and R only has to orthonormalise to ~1e-13 (the condition of S times 2^-47).
+__device__ __forceinline__ dev::F2 pair_rsqrt(dev::F2 d) {
+    using dev::F2;
+    const float y = rsqrtf(d.h);
+    const F2 e = dev::df_sub(F2{1.f, 0.f}, dev::df_mul(d, dev::df_mul(F2{y, 0.f}, F2{y, 0.f})));
+    return dev::df_add(F2{y, 0.f}, dev::df_mul(F2{0.5f * y, 0.f}, e));  // y + y (1 - d y^2) / 2
+}
+
+__global__ void __launch_bounds__(256) k_chol_pair(int p, const double* __restrict__ S, double rel_shift,
+                                                   double* __restrict__ Rinv, int* __restrict__ fail) {
+    using dev::F2;
+    __shared__ float2 A[48][49];   // factorised in place; upper triangle ends as R
+    __shared__ float2 X[48][49];   // accumulators, then R^{-1}
+    __shared__ float2 rk[48];      // 1 / R[k][k]
+    __shared__ double red[2];
     const int ax = blockIdx.x;
     const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
     const double* Sa = S + (size_t)ax * p * p;
     for (int i = ty; i < p; i += 16)
         for (int j = tx; j < p; j += 16) {
-            A[i][j] = Sa[i * p + j];
-            X[i][j] = 0.0;
+            const F2 v = dev::df_from(Sa[i * p + j]);
+            A[i][j] = make_float2(v.h, v.l);
+            X[i][j] = make_float2(0.f, 0.f);
         }
-    __syncthreads();
-    if (threadIdx.x < 32) {  // shift = rel_shift * trace, a warp reduction
+    if (threadIdx.x < 32) {  // shift = rel_shift * trace; null pivots at or below 1e-14 of it
         double t = 0.0;
-        for (int i = threadIdx.x; i < p; i += 32) t += A[i][i];
+        for (int i = threadIdx.x; i < p; i += 32) t += Sa[(size_t)i * p + i];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (threadIdx.x == 0) {
             red[0] = rel_shift * t;
@@ -679,48 +718,64 @@ __global__ void __launch_bounds__(256) k_chol_rinv(int p, const double* __restri
         }
     }
     __syncthreads();
-    if (threadIdx.x < p) A[threadIdx.x][threadIdx.x] += red[0];
+    const F2 shift = dev::df_from(red[0]);
+    const float thresh = (float)red[1];
+    if (threadIdx.x < p) {
+        const F2 d = dev::df_add(F2{A[threadIdx.x][threadIdx.x].x, A[threadIdx.x][threadIdx.x].y}, shift);
+        A[threadIdx.x][threadIdx.x] = make_float2(d.h, d.l);
+    }
     __syncthreads();
     for (int k = 0; k < p; ++k) {
         if (threadIdx.x == 0) {
-            // S is a Gram matrix: a pivot at or below 1e-14 of its trace belongs to a
-            // direction the block does not span (a rank-deficient block, e.g. a protein
-            // with fewer Gaussian terms than the block size); its column of Q becomes 0
-            // (R[k][k] = 0, rk = 0) instead of amplifying rounding noise.  Only a NaN
-            // pivot is a failure.
-            const double d = A[k][k];
-            if (d != d) fail[ax] = 1;
-            const double r = d > red[1] ? rsqrt(d) : 0.0;
-            rk[k] = r;
-            A[k][k] = d * r;
+            const F2 d{A[k][k].x, A[k][k].y};
+            if (d.h != d.h) fail[ax] = 1;
+            const F2 r = d.h > thresh ? pair_rsqrt(d) : F2{0.f, 0.f};
+            rk[k] = make_float2(r.h, r.l);
+            const F2 dr = dev::df_mul(d, r);
+            A[k][k] = make_float2(dr.h, dr.l);
         }
         __syncthreads();
-        const double r = rk[k], r2 = r * r;
-        // row k of R (read below only through the unscaled A[k][.] of this step)
+        const F2 r{rk[k].x, rk[k].y};
+        const F2 r2 = dev::df_mul(r, r);
         for (int i = k + 1 + ty; i < p; i += 16) {
-            const double aki = A[k][i] * r2;
+            const F2 aki = dev::df_mul(F2{A[k][i].x, A[k][i].y}, r2);
             for (int j = k + 1 + tx; j < p; j += 16)
-                if (j >= i) A[i][j] -= aki * A[k][j];
+                if (j >= i) {
+                    const F2 v = dev::df_sub(F2{A[i][j].x, A[i][j].y}, dev::df_mul(aki, F2{A[k][j].x, A[k][j].y}));
+                    A[i][j] = make_float2(v.h, v.l);
+                }
         }
         __syncthreads();
-        if (threadIdx.x > k && threadIdx.x < p) A[k][threadIdx.x] *= r;
+        if (threadIdx.x > k && threadIdx.x < p) {
+            const F2 v = dev::df_mul(F2{A[k][threadIdx.x].x, A[k][threadIdx.x].y}, r);
+            A[k][threadIdx.x] = make_float2(v.h, v.l);
+        }
     }
     __syncthreads();
     // R^{-1}, rows from the bottom; X[k][.] is final once acc[k][.] has all rows > k
     for (int k = p - 1; k >= 0; --k) {
-        const double r = rk[k];
+        const F2 r{rk[k].x, rk[k].y};
         for (int i = ty; i < k; i += 16)
             for (int j = k + tx; j < p; j += 16) {
-                const double xkj = j == k ? r : -r * X[k][j];
-                X[i][j] += A[i][k] * xkj;
+                const F2 xkj = j == k ? r : dev::df_mul(F2{-r.h, -r.l}, F2{X[k][j].x, X[k][j].y});
+                const F2 v = dev::df_add(F2{X[i][j].x, X[i][j].y}, dev::df_mul(F2{A[i][k].x, A[i][k].y}, xkj));
+                X[i][j] = make_float2(v.h, v.l);
             }
         __syncthreads();
-        if (threadIdx.x >= k && threadIdx.x < p) X[k][threadIdx.x] = threadIdx.x == k ? r : -r * X[k][threadIdx.x];
+        if (threadIdx.x >= k && threadIdx.x < p) {
+            const F2 v = threadIdx.x == k ? r : dev::df_mul(F2{-r.h, -r.l}, F2{X[k][threadIdx.x].x, X[k][threadIdx.x].y});
+            X[k][threadIdx.x] = make_float2(v.h, v.l);
+        }
         __syncthreads();
     }
     double* Ra = Rinv + (size_t)ax * p * p;
     for (int i = ty; i < p; i += 16)
-        for (int j = tx; j < p; j += 16) Ra[i * p + j] = j >= i ? X[i][j] : 0.0;
+        for (int j = tx; j < p; j += 16) Ra[i * p + j] = j >= i ? dev::df_to(F2{X[i][j].x, X[i][j].y}) : 0.0;
+}
+
+// Shifted Cholesky and inverse of the three p x p Grams of a CholQR pass.
+void launch_chol(int p, const double* S, double rel_shift, double* Rinv, int* fail, cudaStream_t st) {
+    k_chol_pair<<<3, 256, 0, st>>>(p, S, rel_shift, Rinv, fail);  // p <= 48
 }
 
 // Q = Y Rinv (Rinv upper triangular), n x p; Q2 (if not null) gets Q as float pairs.
@@ -733,8 +788,9 @@ __global__ void k_apply_rinv(int n, int p, const double* __restrict__ Y,
     int i = (int)(idx / p), c = (int)(idx % p);
     const double* Ya = Y + ((size_t)ax * n + i) * p;
     const double* Ra = Rinv + (size_t)ax * p * p;
-    double s = 0.0;
-    for (int k = 0; k <= c; ++k) s += Ya[k] * Ra[(size_t)k * p + c];
+    double t[4] = {0.0, 0.0, 0.0, 0.0};  // four interleaved partial sums, fixed order
+    for (int k = 0; k <= c; ++k) t[k & 3] = fma(Ya[k], Ra[(size_t)k * p + c], t[k & 3]);
+    const double s = (t[0] + t[1]) + (t[2] + t[3]);
     Q[((size_t)ax * n + i) * p + c] = s;
     if (Q2) {
         const dev::F2 q = dev::df_from(s);
@@ -768,19 +824,22 @@ __global__ void __launch_bounds__(512) k_skeleton(int n, int RP, const int* __re
                                                    double* __restrict__ M,
                                                    int* __restrict__ Sidx,
                                                    double* __restrict__ Ainv,
-                                                   int* __restrict__ fail) {
+                                                   int* __restrict__ fail, bool use_smem) {
     __shared__ float red_v[512];
     __shared__ int red_i[512];
     __shared__ float piv[RS_MAX_TUCKER];
     __shared__ int sel[RS_MAX_TUCKER];
     __shared__ double A[RS_MAX_TUCKER][2 * RS_MAX_TUCKER + 1];
+    extern __shared__ float rows_sm[];  // the residual rows when they fit (n RP floats)
     int ax = blockIdx.x;
     int r = r_ax[ax];
     const double* Va = V + (size_t)ax * n * RP;
     // The selection runs in FP32: it only has to pick well-conditioned rows (the
     // basis change V V[S,:]^-1 and the core transform use the exact FP64 rows), and
-    // GB300's FP64 rate made the FP64 version the build's slowest serial kernel.
-    float* Ma = reinterpret_cast<float*>(M) + (size_t)ax * n * RP;
+    // GB300's FP64 rate made the FP64 version the build's slowest serial kernel.  The
+    // residual rows live in shared memory when the launch provides it (every step
+    // reads and rewrites all of them).
+    float* Ma = use_smem ? rows_sm : reinterpret_cast<float*>(M) + (size_t)ax * n * RP;
     for (size_t e = threadIdx.x; e < (size_t)n * RP; e += blockDim.x) Ma[e] = (float)Va[e];
     __syncthreads();
     for (int step = 0; step < r; ++step) {
@@ -841,19 +900,33 @@ __global__ void __launch_bounds__(512) k_skeleton(int n, int RP, const int* __re
         A[i][j] = (j < r) ? Va[(size_t)sel[i] * RP + j] : ((j - r) == i ? 1.0 : 0.0);
     }
     __syncthreads();
+    __shared__ int pivrow;
     for (int k = 0; k < r; ++k) {
-        if (threadIdx.x == 0) {
-            int best = k;
-            for (int i = k + 1; i < r; ++i)
-                if (fabs(A[i][k]) > fabs(A[best][k])) best = i;
-            if (best != k)
-                for (int j = 0; j < 2 * r; ++j) {
-                    double t = A[k][j];
-                    A[k][j] = A[best][j];
-                    A[best][j] = t;
+        if (threadIdx.x < 32) {  // partial pivoting: warp argmax of |A[i][k]|, i >= k (lowest i on ties)
+            const int i = k + (int)threadIdx.x;
+            double v = i < r ? fabs(A[i][k]) : -1.0;
+            int bi = i;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (v2 > v || (v2 == v && i2 < bi)) {
+                    v = v2;
+                    bi = i2;
                 }
-            if (!(fabs(A[k][k]) > 0.0)) fail[ax] = 3;
+            }
+            if (threadIdx.x == 0) {
+                pivrow = bi;
+                if (!(v > 0.0)) fail[ax] = 3;
+            }
         }
+        __syncthreads();
+        const int best = pivrow;
+        if (best != k)
+            for (int j = threadIdx.x; j < 2 * r; j += blockDim.x) {
+                const double t = A[k][j];
+                A[k][j] = A[best][j];
+                A[best][j] = t;
+            }
         __syncthreads();
         double d = A[k][k];
         __syncthreads();
@@ -1654,7 +1727,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     }
     const int Sh = 2 * n - 1;
     // 1. Gram matrices
-    double *d_cz, *d_w2, *d_E, *d_Dp, *d_D, *d_tr;
+    double *d_cz, *d_w2, *d_Dp, *d_D, *d_tr;
+    float2 *d_WE, *d_D2;
     float2* d_G;
     RS_TRY(S.get(&d_cz, N));
     RS_TRY(S.get(&d_w2, Rl));
@@ -1666,7 +1740,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     int nmc = (N + kMC - 1) / kMC;
     RS_TRY(S.get(&d_Dp, (size_t)nmc * 3 * Rl * Sh));
     RS_TRY(S.get(&d_D, (size_t)3 * Rl * Sh));
-    RS_TRY(S.get(&d_E, (size_t)Rl * n));
+    RS_TRY(S.get(&d_WE, (size_t)Rl * n));
+    RS_TRY(S.get(&d_D2, (size_t)3 * Rl * Sh));
     RS_TRY(S.get(&d_G, (size_t)3 * n * n));
     RS_TRY(S.get(&d_tr, 3));
     long long threads = (long long)nsc * Rl * 3 * nmc;
@@ -1708,16 +1783,16 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     size_t dlen = (size_t)3 * Rl * Sh;
     {
         ::rs::KernelTimer kt__("k_sum_chunks", st, 0.0, false);
-        k_sum_chunks<<<blocks_for(dlen), kBlock, 0, st>>>(dlen, nmc, d_Dp, d_D);
+        k_sum_chunks<<<blocks_for(dlen), kBlock, 0, st>>>(dlen, nmc, d_Dp, d_D, d_D2);
     }
     {
         ::rs::KernelTimer kt__("k_exp_table", st, 0.0, false);
-        k_exp_table<<<dim3(blocks_for(n), Rl), kBlock, 0, st>>>(n, h, Rl, d_tl, d_E);
+        k_exp_table<<<dim3(blocks_for(n), Rl), kBlock, 0, st>>>(n, h, Rl, d_tl, d_w2, d_WE);
     }
-    work = 3.0 * n * (double)n * Rl * 3.0;  // FP64 flops
+    work = 3.0 * n * (double)n * Rl * 8.0;  // FP32 pipe ops (one Dot2 step per term)
     {
         ::rs::KernelTimer kt__("k_gram", st, work, true);
-        k_gram<<<dim3(blocks_for(n), n, 3), kBlock, 0, st>>>(n, Rl, d_w2, d_E, d_D, d_G);
+        k_gram<<<dim3(blocks_for(n), n, 3), kBlock, 0, st>>>(n, Rl, d_WE, d_D2, d_G);
     }
     {
         ::rs::KernelTimer kt__("k_trace", st, 0.0, false);
@@ -1794,8 +1869,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
             k_sum_gram<<<dim3(blocks_for((size_t)p * p), 3), kBlock, 0, st>>>(nblk, p, d_Sp, d_Sm);
         }
         {
-            ::rs::KernelTimer kt__("k_chol_rinv", st, 0.0, false);
-            k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, shift, d_Ri, d_fail);
+            ::rs::KernelTimer kt__("k_chol", st, 0.0, false);
+            launch_chol(p, d_Sm, shift, d_Ri, d_fail, st);
         }
         {
             ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
@@ -1861,8 +1936,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
             k_sum_gram<<<dim3(blocks_for((size_t)p * p), 3), kBlock, 0, st>>>(nblk, p, d_Sp, d_Sm);
         }
         {
-            ::rs::KernelTimer kt__("k_chol_rinv", st, 0.0, false);
-            k_chol_rinv<<<3, 256, 0, st>>>(p, d_Sm, 1e-13, d_Ri, d_fail);
+            ::rs::KernelTimer kt__("k_chol", st, 0.0, false);
+            launch_chol(p, d_Sm, 1e-13, d_Ri, d_fail, st);
         }
         {
             ::rs::KernelTimer kt__("k_apply_rinv", st, 0.0, false);
@@ -1969,8 +2044,14 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     }
     // 3. skeleton basis
     {
+        // the residual rows in shared memory when they fit beside the kernel's static arrays
+        const size_t rows_bytes = (size_t)n * RP * sizeof(float);
+        const bool rows_smem = rows_bytes <= 192 * 1024;
+        if (rows_smem)
+            RS_TRY_CUDA(cudaFuncSetAttribute(k_skeleton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_bytes));
         ::rs::KernelTimer kt__("k_skeleton", st, 0.0, false);
-        k_skeleton<<<3, 512, 0, st>>>(n, RP, d_rax, d_V, d_M, d_S, d_Ainv, d_fail);
+        k_skeleton<<<3, 512, rows_smem ? rows_bytes : 0, st>>>(n, RP, d_rax, d_V, d_M, d_S, d_Ainv, d_fail,
+                                                               rows_smem);
     }
     double* d_Vs;
     RS_TRY(S.get(&d_Vs, (size_t)3 * n * RP));
@@ -1982,7 +2063,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY_CUDA(cudaGetLastError());
     // 4. projections and core
     const int Rtot = N * Rl;
-    const int CH = 512;
+    const int CH = 512;  // columns per k_core CTA (192 measured slower: more partial cores)
     const int nchunk = (Rtot + CH - 1) / CH;
     double *d_Bp, *d_B;
     float2* d_Cp;
@@ -2038,7 +2119,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     size_t blen = (size_t)RP * RP * RP;
     {
         ::rs::KernelTimer kt__("k_sum_chunks", st, 0.0, false);
-        k_sum_chunks<<<blocks_for(blen), kBlock, 0, st>>>(blen, nchunk, d_Bp, d_B);
+        k_sum_chunks<<<blocks_for(blen), kBlock, 0, st>>>(blen, nchunk, d_Bp, d_B, nullptr);
     }
     float* core;
     RS_TRY(device_alloc(P, (void**)&core, blen * sizeof(float)));
