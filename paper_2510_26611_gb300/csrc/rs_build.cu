@@ -344,12 +344,15 @@ __device__ __forceinline__ dev::F2 df_div(dev::F2 a, dev::F2 b) {
 //         = sum_k |a_k|^(2/3) e^{-t^2 (x_i-x_i')^2 / 2} D_k(y_{i+i'}),
 // D_k(y) = sum_m |z_m|^(2/3) e^{-2 t^2 (y - x_m)^2},  y_s = -b + s h/2 (half grid).
 // One thread: SC half-grid points, one (axis, k), MC atoms.  Each Gaussian is
-// walked from its point nearest to x_m outwards with the exact ratio recurrence
-// g_{s+1} = g_s rho_s, rho_{s+1} = rho_s c, all in float pairs on the FP32 pipes:
-// the atom records are float pairs (k_dsum_atoms), the two seeds per (atom, chunk)
-// are pair exponentials (df_exp) and the backward ratio a pair quotient, so the loop
-// runs no FP64 instruction (GB300's FP64 rate is 1/64 of FP32); about 2^-46 relative
-// per seed and 2^-47 per step, at most 31 steps from a seed.
+// walked forwards through the chunk from its first point within reach (e^-50 of the
+// peak: the whole chunk for an atom to its left, the rising side for one to its right)
+// with the exact ratio recurrence g_{s+1} = g_s rho_s, rho_{s+1} = rho_s c, all in float
+// pairs on the FP32 pipes: the atom records are float pairs (k_dsum_atoms), the two
+// seeds per (atom, chunk) are pair exponentials (df_exp), so the loop runs no FP64
+// instruction (GB300's FP64 rate is 1/64 of FP32); about 2^-46 relative per seed and
+// 2^-47 per step, at most 31 steps from a seed.  The walk starts at a value at least
+// e^-50 of the peak and only grows towards it, so no seed underflows; values below
+// that on the rising side are left out (the float-pair sums carry ~e^-32 of the peak).
 constexpr int kSC = 32;
 constexpr int kMC = 128;
 
@@ -386,6 +389,8 @@ __global__ void __launch_bounds__(128) k_gauss_dsum(int n, double b, double h, i
     const F2 y0 = dev::df_from(-b + s0 * delta), dl = dev::df_from(delta), t2p = dev::df_from(t2);
     const F2 t2d = dev::df_from(t2 * delta), cqp = dev::df_from(exp(-2.0 * t2 * delta * delta));
     const float inv_delta = (float)(1.0 / delta);
+    // reach: the Gaussian is below e^-50 of its peak where |y - x_m| > R
+    const float R = t2 > 0.0 ? (float)sqrt(50.0 / t2) : INFINITY;
     F2 acc[kSC];
 #pragma unroll
     for (int s = 0; s < kSC; ++s) acc[s] = F2{0.f, 0.f};
@@ -393,37 +398,23 @@ __global__ void __launch_bounds__(128) k_gauss_dsum(int n, double b, double h, i
     int m_end = min(N, (mc + 1) * kMC);
     for (int m = mc * kMC; m < m_end; ++m) {
         const float4 a = pa[m];
-        float u = __fmul_rn(__fsub_rn(a.x, y0.h), inv_delta);
-        u = fminf(fmaxf(u, 0.f), (float)(kSC - 1));
-        const float sp_f = rintf(u);
-        const int sp = (int)sp_f;
-        // dp = y0 + sp delta - x_m; arg = t2 dp^2
-        const F2 dp = dev::df_sub(dev::df_add(y0, dev::df_mul(F2{sp_f, 0.f}, dl)), F2{a.x, a.y});
+        // the chunk's points within reach of x_m, in units of delta from y0
+        const float plo = __fmul_rn(__fsub_rn(__fsub_rn(a.x, R), y0.h), inv_delta);
+        const float phi = __fmul_rn(__fsub_rn(__fadd_rn(a.x, R), y0.h), inv_delta);
+        if (plo > (float)(kSC - 1) || phi < 0.f) continue;  // the whole chunk is out of reach
+        const int ss = plo > 0.f ? (int)ceilf(plo) : 0;
+        // dp = y0 + ss delta - x_m; g_ss = z e^{-t2 dp^2}; rho_ss = e^{-t2 delta (2 dp + delta)}
+        const F2 dp = dev::df_sub(dev::df_add(y0, dev::df_mul(F2{(float)ss, 0.f}, dl)), F2{a.x, a.y});
         const F2 arg = dev::df_mul(t2p, dev::df_mul(dp, dp));
-        if (arg.h > 50.f) continue;  // the whole chunk is below e^-50 of the peak
-        // forward ratio e1 = exp(-t2 (2 dp delta + delta^2)) = exp(-t2 delta (2 dp + delta))
         const F2 a1 = dev::df_mul(t2d, dev::df_add(F2{2.f * dp.h, 2.f * dp.l}, dl));
-        const F2 e1 = df_exp(F2{-a1.h, -a1.l}, etab);
-        const F2 g0 = dev::df_mul(F2{a.z, a.w}, df_exp(F2{-arg.h, -arg.l}, etab));
-        const F2 rb = df_div(cqp, e1);
-        F2 g = g0, r = e1;
+        F2 r = df_exp(F2{-a1.h, -a1.l}, etab);
+        F2 g = dev::df_mul(F2{a.z, a.w}, df_exp(F2{-arg.h, -arg.l}, etab));
 #pragma unroll
         for (int s = 0; s < kSC; ++s) {
-            if (s == sp) dev::df_acc(acc[s], g0);
-            if (s > sp) {
+            if (s >= ss) {
+                dev::df_acc(acc[s], g);
                 g = dev::df_mul(g, r);
                 r = dev::df_mul(r, cqp);
-                dev::df_acc(acc[s], g);
-            }
-        }
-        g = g0;
-        r = rb;
-#pragma unroll
-        for (int s = kSC - 1; s >= 0; --s) {
-            if (s < sp) {
-                g = dev::df_mul(g, r);
-                r = dev::df_mul(r, cqp);
-                dev::df_acc(acc[s], g);
             }
         }
     }
@@ -1189,49 +1180,66 @@ __global__ void __launch_bounds__(1024) k_core(int Rtot, int Rl, int CH,
 // ------------------------------------------------------------- tensor-core projection
 // k_project on tcgen05: for one axis, one long-range term k and 128 atoms m (in grid-row
 // order), C'[a, (m, k)] = sum_i Wp[i, a] g_k(x_i - x_m) is the GEMM (atoms x grid rows) x
-// (grid rows x a) with K = the grid rows of the CTA's window, cut into 32-row chunks.
-// The Gaussians are generated per chunk in float pairs (seeds by the pair exponential,
-// then the ratio recurrence g_{i+1} = g_i rho_i, rho_{i+1} = rho_i e^{-2 t^2 h^2}) and cut
-// into six exact BF16 slices straight into the A tile (scale per atom and chunk from the
-// largest Gaussian value in the chunk); Wp's slices per (column, chunk) are made once
-// per build (k_slice_wp).  The 21 slice products go to six TMEM accumulators, one per
-// diagonal (integer K-sums below 32 * 147456 < 2^24: exact), combined error-free per
-// chunk into float pairs and summed over the chunks in pair arithmetic.  Rows outside
-// an atom's own window (where its Gaussian is below e^-46 of the peak) are zero, as in
-// the float-pair kernel.
-constexpr int kPK = 32;                        // grid rows per K chunk
+// (grid rows x a) with K = the grid rows of the CTA's window, cut into 16-row chunks.
+// The Gaussians are generated per chunk in float pairs (seeds by the pair exponential
+// every 32 rows, then the ratio recurrence g_{i+1} = g_i rho_i, rho_{i+1} = rho_i
+// e^{-2 t^2 h^2}) and cut into six exact BF16 slices straight into the A tile; Wp's
+// slices per (column, chunk) are made once per build (k_slice_wp).  The 21 slice
+// products go to six TMEM accumulators, one per diagonal.  Six consecutive chunks (a
+// 96-row group) share one scale per atom (from the largest Gaussian value of the group
+// in the atom's window) and one per column of Wp, so the accumulators run over the
+// whole group: a diagonal's integer K-sum stays below 96 * 122880 < 2^24 (diagonal 5,
+// |d_0| <= 32, |d_1|, |d_2| <= 128, |d_3| <= 160, |d_4|, |d_5| <= 256: exact), and the
+// six diagonals are combined error-free into a float pair once per group and summed
+// over the groups in pair arithmetic.  Rows outside an atom's own window (where its
+// Gaussian is below e^-46 of the peak) are zero, as in the float-pair kernel.
+//
+// Warp roles: warps 0-3 own one atom per thread (the A rows), warp 4 copies Wp's
+// slices and issues the MMAs.  The chunks run through a ring of kPS stages of A and B
+// tiles with mbarriers instead of CTA-wide barriers: a row warp announces its rows of
+// a stage (full), the issuer waits for all four and for the B copy, issues and commits
+// (mma); a row warp reuses a stage once its MMAs have completed and reads TMEM at the
+// end of a group, after which it announces that the accumulators may be overwritten
+// (drained).  So each warp runs ahead to the next chunk as soon as its own rows are
+// written, and the MMAs of one chunk overlap the rows of the next ones.
+constexpr int kPK = 16;                        // grid rows per K chunk (one MMA K step)
+constexpr int kPG = 6;                         // chunks per scale group (96 rows)
+constexpr int kPS = 3;                         // stages of the ring
 constexpr uint32_t kPSBO = kPK * 16;           // bytes between 8-row groups of a tile
-constexpr uint32_t kPSliceA = 128 * kPK * 2;   // one slice of the A tile (8 KB)
+constexpr uint32_t kPSliceA = 128 * kPK * 2;   // one slice of an A tile (4 KB)
 
 template <int NP>
 struct ProjShape {
     static constexpr uint32_t SLICE_B = NP * kPK * 2;
-    static constexpr uint32_t A_BYTES = tcg::kS * kPSliceA;
-    static constexpr uint32_t B_BYTES = tcg::kS * SLICE_B;
-    static constexpr uint32_t BAR_OFF = A_BYTES + B_BYTES;  // [0] B copy, [1] MMAs
-    static constexpr uint32_t SLOT_OFF = BAR_OFF + 16;
-    static constexpr uint32_t BINV_OFF = SLOT_OFF + 16;
-    static constexpr uint32_t WIN_OFF = BINV_OFF + NP * 4;  // window bounds, 2 x 128 ints
+    static constexpr uint32_t A_BYTES = tcg::kS * kPSliceA;  // one A stage
+    static constexpr uint32_t B_BYTES = tcg::kS * SLICE_B;   // one B stage (one chunk)
+    static constexpr uint32_t B_OFF = kPS * A_BYTES;
+    // barriers: full[kPS], ld[kPS], mma[kPS], drained
+    static constexpr uint32_t BAR_OFF = B_OFF + kPS * B_BYTES;
+    static constexpr uint32_t SLOT_OFF = BAR_OFF + (3 * kPS + 1) * 8;
+    static constexpr uint32_t ABORT_OFF = SLOT_OFF + 4;
+    static constexpr uint32_t WIN_OFF = SLOT_OFF + 16;  // window bounds, 2 x 128 ints
     static constexpr uint32_t SMEM = WIN_OFF + 2 * 128 * 4;
     static constexpr uint32_t COLS = tcg::kS * NP;
     static constexpr uint32_t NCOL = COLS <= 128 ? 128 : 256;
 };
 
 // B slices of Wp (n x RP float pairs per axis), K = the grid row: chunk kc of axis ax at
-// out + (ax KC + kc) B_BYTES (rows a >= RP zero), binv[(ax KC + kc) NP + a] = 1 / scale.
+// out + (ax KC + kc) B_BYTES (rows a >= RP zero); the scale of column a is shared by the
+// chunk's 96-row group g = kc / kPG: binv[(ax KG + g) NP + a] = 1 / scale.
 template <int NP>
-__global__ void __launch_bounds__(NP) k_slice_wp(int n, int RP, int KC, const float2* __restrict__ Wp,
+__global__ void __launch_bounds__(NP) k_slice_wp(int n, int RP, int KC, int KG, const float2* __restrict__ Wp,
                                                   uint8_t* __restrict__ out, float* __restrict__ binv) {
     using Sh = ProjShape<NP>;
     const int kc = blockIdx.x, ax = blockIdx.y, a = threadIdx.x;
-    const int i0 = kc * kPK;
+    const int i0 = kc * kPK, grp = kc / kPG, g0 = grp * kPG * kPK;
     const float2* Wa = Wp + (size_t)ax * n * RP;
     float m = 0.f;
     if (a < RP)
-        for (int i = i0; i < min(n, i0 + kPK); ++i) m = fmaxf(m, fabsf(Wa[(size_t)i * RP + a].x));
+        for (int i = g0; i < min(n, g0 + kPG * kPK); ++i) m = fmaxf(m, fabsf(Wa[(size_t)i * RP + a].x));
     float sc, inv;
     tc::row_scale(m, sc, inv);
-    binv[((size_t)ax * KC + kc) * NP + a] = inv;
+    if (kc % kPG == 0) binv[((size_t)ax * KG + grp) * NP + a] = inv;
     uint8_t* tile = out + ((size_t)ax * KC + kc) * Sh::B_BYTES;
 #pragma unroll 1
     for (int g = 0; g < kPK / 8; ++g) {
@@ -1255,8 +1263,57 @@ __global__ void __launch_bounds__(NP) k_slice_wp(int n, int RP, int KC, const fl
     }
 }
 
+// The Gaussian of one atom on a chunk's rows ia..ib (others zero) as six slices into
+// row `row` of an A stage.  DIRECT: every value by the pair exponential; else the ratio
+// recurrence (g, rho) continues from the previous row.
+struct ProjGauss {
+    dev::F2 nt2, hp, base, cq;
+    const float2* etab;
+    __device__ __forceinline__ dev::F2 offset(int i) const {
+        return dev::df_add(base, dev::df_mul(hp, dev::F2{(float)i, 0.f}));
+    }
+    __device__ __forceinline__ dev::F2 gauss(dev::F2 d) const {
+        return df_exp(dev::df_mul(nt2, dev::df_mul(d, d)), etab);
+    }
+};
+
+template <bool DIRECT>
+__device__ __forceinline__ void proj_row(const ProjGauss& G, uint8_t* sA, int row, int i0, int ia, int ib, float sc,
+                                         dev::F2& g, dev::F2& rho) {
+    using dev::F2;
+#pragma unroll
+    for (int gq = 0; gq < kPK / 8; ++gq) {
+        uint32_t w[tcg::kS][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float slo[tcg::kS], shi[tcg::kS];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int i = i0 + gq * 8 + e + hh;
+                F2 val{0.f, 0.f};
+                if (i >= ia && i <= ib) {
+                    if (DIRECT) {
+                        val = G.gauss(G.offset(i));
+                    } else {
+                        val = g;
+                        g = dev::df_mul(g, rho);
+                        rho = dev::df_mul(rho, G.cq);
+                    }
+                }
+                tcg::slice6(__fmul_rn(val.h, sc), __fmul_rn(val.l, sc), hh ? shi : slo);
+            }
+#pragma unroll
+            for (int u = 0; u < tcg::kS; ++u) w[u][e / 2] = tc::pack_bf16x2(slo[u], shi[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < tcg::kS; ++u)
+            *reinterpret_cast<uint4*>(sA + u * kPSliceA + tc::kmajor_offset(row, gq * 8, kPSBO)) =
+                make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
+    }
+}
+
 template <int RP, int NP>
-__global__ void __launch_bounds__(128) k_project_tc(int n, double b, double h, int N, int Rl, int KC,
+__global__ void __launch_bounds__(160, 2) k_project_tc(int n, double b, double h, int N, int Rl, int KC, int KG,
                                                      const double* __restrict__ xyz,
                                                      const double* __restrict__ tl,
                                                      const int* __restrict__ perm,
@@ -1267,16 +1324,18 @@ __global__ void __launch_bounds__(128) k_project_tc(int n, double b, double h, i
     using dev::F2;
     using Sh = ProjShape<NP>;
     extern __shared__ __align__(16) uint8_t smem_p[];
-    uint8_t* sA = smem_p;
-    uint8_t* sB = smem_p + Sh::A_BYTES;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_p + Sh::BAR_OFF);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_p + Sh::BAR_OFF);  // rows written (4 arrivals)
+    uint64_t* ldb = full + kPS;                                          // B copy landed
+    uint64_t* mmb = ldb + kPS;                                           // MMAs complete
+    uint64_t* drained = mmb + kPS;                                       // TMEM read (4 arrivals)
     uint32_t* slot = reinterpret_cast<uint32_t*>(smem_p + Sh::SLOT_OFF);
-    float* sbinv = reinterpret_cast<float*>(smem_p + Sh::BINV_OFF);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem_p + Sh::ABORT_OFF);
     int* wlo = reinterpret_cast<int*>(smem_p + Sh::WIN_OFF);
     int* whi = wlo + 128;
-    const int k = blockIdx.y, ax = blockIdx.z, tid = threadIdx.x, warp = tid >> 5;
+    const int k = blockIdx.y, ax = blockIdx.z, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool rows = warp < 4;  // warps 0-3: one atom per thread; warp 4: copies and MMAs
     const int mo = blockIdx.x * 128 + tid;
-    const bool valid = mo < N;
+    const bool valid = rows && mo < N;
     const int m = valid ? perm[(size_t)ax * N + mo] : 0;  // atoms in grid-row order
     const double t2 = tl[k] * tl[k];
     const double xm = valid ? xyz[3 * (size_t)m + ax] : 0.0;
@@ -1294,12 +1353,19 @@ __global__ void __launch_bounds__(128) k_project_tc(int n, double b, double h, i
             }
         }
     }
-    wlo[tid] = lo;
-    whi[tid] = hi;
+    if (rows) {
+        wlo[tid] = lo;
+        whi[tid] = hi;
+    }
     if (warp == 0) tc::tmem_alloc(slot, Sh::NCOL);
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
-        tc::mbar_init(bar + 1, 1);
+        for (int q = 0; q < kPS; ++q) {
+            tc::mbar_init(full + q, 4);
+            tc::mbar_init(ldb + q, 1);
+            tc::mbar_init(mmb + q, 1);
+        }
+        tc::mbar_init(drained, 4);
+        *abort_flag = 0;
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -1313,147 +1379,151 @@ __global__ void __launch_bounds__(128) k_project_tc(int n, double b, double h, i
     }
     const int ulo = wlo[0], uhi = whi[0];
     const uint32_t tmem = *slot;
-    const uint32_t tl_lane = tmem + ((uint32_t)(warp * 32) << 16);
-    // pair constants of this atom's Gaussian: -t^2, h, the offset of row 0 (x_0 - x_m)
-    // and the ratio factor e^{-2 t^2 h^2}
-    const F2 nt2 = dev::df_from(-t2);
-    const F2 hp = dev::df_from(h);
-    const F2 base = dev::df_from(-b - xm);
-    const bool direct = t2 * h * h > 8.0;
-    const F2 cq = direct ? F2{0.f, 0.f} : df_exp(dev::df_from(-2.0 * t2 * h * h), etab);
-    const int ipeak = valid ? (int)rint((xm + b) / h) : 0;  // grid row nearest the atom
-    auto offset = [&](int i) { return dev::df_add(base, dev::df_mul(hp, F2{(float)i, 0.f})); };
-    auto gauss = [&](F2 d) { return df_exp(dev::df_mul(nt2, dev::df_mul(d, d)), etab); };
+    const int c0 = ulo <= uhi ? ulo / kPK : 0, nch = ulo <= uhi ? uhi / kPK - c0 + 1 : 0;
     F2 acc[RP];
 #pragma unroll
     for (int a = 0; a < RP; ++a) acc[a] = F2{0.f, 0.f};
-    uint32_t phase = 0;
-    bool failed = false;
-    const int kc0 = ulo <= uhi ? ulo / kPK : 0, kc1 = ulo <= uhi ? uhi / kPK : -1;
-    for (int kc = kc0; kc <= kc1; ++kc) {
-        const int i0 = kc * kPK;
-        if (tid == 0) {
-            tc::mbar_arrive_expect_tx(bar, Sh::B_BYTES);
-            tc::bulk_g2s(sB, Bs + ((size_t)ax * KC + kc) * Sh::B_BYTES, Sh::B_BYTES, bar);
-        }
-        if (tid < NP) sbinv[tid] = binv[((size_t)ax * KC + kc) * NP + tid];
-        // this atom's row of the A tile
-        const int ia = max(lo, i0), ib = min(hi, i0 + kPK - 1);
-        float ainv = 0.f;
-        if (ia <= ib) {
-            const int ip = min(max(ipeak, ia), ib);  // the chunk's row nearest the peak
-            const F2 gmax = gauss(offset(ip));
-            float sc;
-            tc::row_scale(__fmul_rn(gmax.h, 1.00000095367431640625f), sc, ainv);
-            F2 g = gauss(offset(ia));
-            F2 rho{0.f, 0.f};
-            if (!direct) {
-                const F2 d0 = offset(ia);
-                // rho_i = e^{-t^2 (2 d_i h + h^2)}
-                const F2 arg = dev::df_add(dev::df_mul(F2{2.f, 0.f}, dev::df_mul(d0, hp)), dev::df_mul(hp, hp));
-                rho = df_exp(dev::df_mul(nt2, arg), etab);
+    if (!rows) {
+        // ---- issuer: lane 0 of warp 4
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NP);
+            int last_ld = -1, last_mma = -1, grp = -1;
+            bool ok = true;
+            for (int j = 0; j < nch && ok; ++j) {
+                const int s = j % kPS, c = c0 + j;
+                const uint32_t ph = (uint32_t)(j / kPS) & 1u;
+                const bool gfirst = j == 0 || c % kPG == 0;
+                uint8_t* sA = smem_p + s * Sh::A_BYTES;
+                uint8_t* sB = smem_p + Sh::B_OFF + s * Sh::B_BYTES;
+                // stage s was last read by the MMAs of chunk j - kPS
+                if (j >= kPS) ok = tc::mbar_wait_bounded(mmb + s, ph ^ 1u);
+                if (!ok || *abort_flag) break;
+                tc::mbar_arrive_expect_tx(ldb + s, Sh::B_BYTES);
+                tc::bulk_g2s(sB, Bs + ((size_t)ax * KC + c) * Sh::B_BYTES, Sh::B_BYTES, ldb + s);
+                last_ld = j;
+                ok = tc::mbar_wait_bounded(full + s, ph) && tc::mbar_wait_bounded(ldb + s, ph);
+                // a new group overwrites the accumulators: the row warps have read them
+                if (ok && gfirst && grp >= 0) ok = tc::mbar_wait_bounded(drained, (uint32_t)grp & 1u);
+                if (!ok || *abort_flag) break;
+                if (gfirst) ++grp;
+                tc::fence_after_sync();
+                const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+                for (int d = 0; d < tcg::kS; ++d)
+#pragma unroll
+                    for (int u = 0; u <= d; ++u) {
+                        const uint64_t ad = tc::smem_desc(a0 + u * kPSliceA, tc::kLBO, kPSBO);
+                        const uint64_t bd = tc::smem_desc(b0 + (d - u) * Sh::SLICE_B, tc::kLBO, kPSBO);
+                        tc::mma_bf16(tmem + (uint32_t)(d * NP), ad, bd, idesc, (gfirst && u == 0) ? 0u : 1u);
+                    }
+                tc::mma_commit(mmb + s);
+                last_mma = j;
             }
-#pragma unroll 1
-            for (int gq = 0; gq < kPK / 8; ++gq) {
-                uint32_t w[tcg::kS][4];
+            if (!ok || *abort_flag) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+                // a copy or MMAs may still be in flight: wait for them (bounded)
+                if (last_ld >= 0) tc::mbar_wait_bounded(ldb + last_ld % kPS, (uint32_t)(last_ld / kPS) & 1u);
+                if (last_mma >= 0) tc::mbar_wait_bounded(mmb + last_mma % kPS, (uint32_t)(last_mma / kPS) & 1u);
+            }
+        }
+    } else {
+        // ---- row warps: one atom per thread
+        ProjGauss G;
+        G.nt2 = dev::df_from(-t2);
+        G.hp = dev::df_from(h);
+        G.base = dev::df_from(-b - xm);
+        G.etab = etab;
+        const bool direct = t2 * h * h > 8.0;
+        G.cq = direct ? F2{0.f, 0.f} : df_exp(dev::df_from(-2.0 * t2 * h * h), etab);
+        const int ipeak = valid ? (int)rint((xm + b) / h) : 0;  // grid row nearest the atom
+        const uint32_t tl_lane = tmem + ((uint32_t)(warp * 32) << 16);
+        float sc = 0.f, ainv = 0.f;     // the atom's scale in the current group
+        F2 g{0.f, 0.f}, rho{0.f, 0.f};  // the recurrence, carried from chunk to chunk
+        bool ok = true;
+        for (int j = 0; j < nch; ++j) {
+            const int s = j % kPS, c = c0 + j, i0 = c * kPK;
+            const uint32_t ph = (uint32_t)(j / kPS) & 1u;
+            const bool gfirst = j == 0 || c % kPG == 0;
+            const bool glast = j == nch - 1 || c % kPG == kPG - 1;
+            uint8_t* sA = smem_p + s * Sh::A_BYTES;
+            if (j >= kPS) ok = tc::mbar_wait_bounded(mmb + s, ph ^ 1u);  // stage s free
+            if (__any_sync(0xffffffffu, !ok) || *abort_flag) {
+                ok = false;
+                break;
+            }
+            if (gfirst) {  // the atom's scale over the group's rows of its window
+                const int g0 = (c / kPG) * kPG * kPK;
+                const int ga = max(lo, g0), gb = min(hi, g0 + kPG * kPK - 1);
+                sc = 0.f;
+                ainv = 0.f;
+                if (ga <= gb) {
+                    const int ip = min(max(ipeak, ga), gb);  // the group's row nearest the peak
+                    const F2 gmax = G.gauss(G.offset(ip));
+                    tc::row_scale(__fmul_rn(gmax.h, 1.00000095367431640625f), sc, ainv);
+                }
+            }
+            const int ia = max(lo, i0), ib = min(hi, i0 + kPK - 1);
+            if (direct) {
+                proj_row<true>(G, sA, tid, i0, ia, ib, sc, g, rho);
+            } else {
+                // seed at the window's first row and every 32 rows; else continue the walk
+                if (ia <= ib && (ia == lo || (c & 1) == 0)) {
+                    const F2 d0 = G.offset(ia);
+                    g = G.gauss(d0);
+                    // rho_i = e^{-t^2 (2 d_i h + h^2)}
+                    const F2 arg = dev::df_add(dev::df_mul(F2{2.f, 0.f}, dev::df_mul(d0, G.hp)), dev::df_mul(G.hp, G.hp));
+                    rho = df_exp(dev::df_mul(G.nt2, arg), etab);
+                }
+                proj_row<false>(G, sA, tid, i0, ia, ib, sc, g, rho);
+            }
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(full + s);
+            if (glast) {
+                ok = tc::mbar_wait_bounded(mmb + s, ph);  // every MMA of the group
+                if (__any_sync(0xffffffffu, !ok)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const float* bi = binv + ((size_t)ax * KG + c / kPG) * NP;
 #pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    float slo[tcg::kS], shi[tcg::kS];
+                for (int cb = 0; cb < NP; cb += 8) {
+                    if (cb < RP) {
+                        float x[tcg::kS][8];
+                        tcg::tmem_ld8x3(tl_lane + cb, NP, x[0], x[1], x[2]);
+                        tcg::tmem_ld8x3(tl_lane + 3 * NP + cb, NP, x[3], x[4], x[5]);
 #pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const int i = i0 + gq * 8 + e + hh;
-                        F2 val{0.f, 0.f};
-                        if (i >= ia && i <= ib) {
-                            if (direct) {
-                                val = gauss(offset(i));
-                            } else {
-                                val = g;
-                                g = dev::df_mul(g, rho);
-                                rho = dev::df_mul(rho, cq);
+                        for (int q = 0; q < 8; ++q) {
+                            if (cb + q < RP) {
+                                const F2 sum = tcg::combine6(x[0][q], x[1][q], x[2][q], x[3][q], x[4][q], x[5][q]);
+                                const float scl = __fmul_rn(ainv, __ldg(bi + cb + q));
+                                acc[cb + q] =
+                                    dev::df_add(acc[cb + q], F2{__fmul_rn(sum.h, scl), __fmul_rn(sum.l, scl)});
                             }
                         }
-                        tcg::slice6(__fmul_rn(val.h, sc), __fmul_rn(val.l, sc), hh ? shi : slo);
-                    }
-#pragma unroll
-                    for (int u = 0; u < tcg::kS; ++u) w[u][e / 2] = tc::pack_bf16x2(slo[u], shi[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < tcg::kS; ++u)
-                    *reinterpret_cast<uint4*>(sA + u * kPSliceA + tc::kmajor_offset(tid, gq * 8, kPSBO)) =
-                        make_uint4(w[u][0], w[u][1], w[u][2], w[u][3]);
-            }
-        } else {
-#pragma unroll
-            for (int gq = 0; gq < kPK / 8; ++gq)
-#pragma unroll
-                for (int u = 0; u < tcg::kS; ++u)
-                    *reinterpret_cast<uint4*>(sA + u * kPSliceA + tc::kmajor_offset(tid, gq * 8, kPSBO)) =
-                        make_uint4(0u, 0u, 0u, 0u);
-        }
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        const bool loaded = tc::mbar_wait_bounded(bar, phase);
-        if (tid == 0 && loaded) {
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NP);
-            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-#pragma unroll
-            for (int d = 0; d < tcg::kS; ++d)
-#pragma unroll
-                for (int u = 0; u <= d; ++u) {
-                    const int v = d - u;
-#pragma unroll
-                    for (int ks = 0; ks < kPK / 16; ++ks) {
-                        const uint64_t ad = tc::smem_desc(a0 + u * kPSliceA + ks * 2 * tc::kLBO, tc::kLBO, kPSBO);
-                        const uint64_t bd = tc::smem_desc(b0 + v * Sh::SLICE_B + ks * 2 * tc::kLBO, tc::kLBO, kPSBO);
-                        tc::mma_bf16(tmem + (uint32_t)(d * NP), ad, bd, idesc, (u == 0 && ks == 0) ? 0u : 1u);
                     }
                 }
-            tc::mma_commit(bar + 1);
-        }
-        const bool ok = loaded && tc::mbar_wait_bounded(bar + 1, phase);
-        phase ^= 1u;
-        failed = __syncthreads_or(!ok);
-        tc::fence_after_sync();
-        if (failed) {
-            if (!loaded && tid == 0) tc::mbar_wait_bounded(bar, phase ^ 1u);  // a copy still landing
-            break;
-        }
-#pragma unroll
-        for (int c0 = 0; c0 < NP; c0 += 16) {
-            if (c0 < RP) {
-                float x[tcg::kS][16];
-#pragma unroll
-                for (int d = 0; d < tcg::kS; d += 2)
-                    tc::tmem_ld16x2(tl_lane + d * NP + c0, tl_lane + (d + 1) * NP + c0, x[d], x[d + 1]);
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    if (c0 + c < RP) {
-                        F2 sum{ldexpf(x[tcg::kS - 1][c], -8 * (tcg::kS - 1)), 0.f};
-#pragma unroll
-                        for (int d = tcg::kS - 2; d >= 0; --d) sum = dev::df_add(sum, F2{ldexpf(x[d][c], -8 * d), 0.f});
-                        const float scl = __fmul_rn(ainv, sbinv[c0 + c]);
-                        acc[c0 + c] = dev::df_add(acc[c0 + c], F2{__fmul_rn(sum.h, scl), __fmul_rn(sum.l, scl)});
-                    }
-                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(drained);
             }
         }
-        tc::fence_before_sync();
-        __syncthreads();
-    }
-    if (failed) {
-        if (tid == 0) atomicExch(err, 1);
+        if (!ok) {
+            *abort_flag = 1;
+            if (tid == 0) atomicExch(err, 1);
 #pragma unroll
-        for (int a = 0; a < RP; ++a) acc[a] = F2{__int_as_float(-1), 0.f};
-    }
-    if (valid) {
-        const size_t Rp = (size_t)N * Rl, col = (size_t)m * Rl + k;
+            for (int a = 0; a < RP; ++a) acc[a] = F2{__int_as_float(-1), 0.f};
+        }
+        if (valid) {
+            const size_t Rp = (size_t)N * Rl, col = (size_t)m * Rl + k;
 #pragma unroll
-        for (int a = 0; a < RP; ++a) {
-            float sh, sl;
-            dev::two_sum(acc[a].h, acc[a].l, sh, sl);
-            Cp2[((size_t)ax * RP + a) * Rp + col] = make_float2(sh, sl);
+            for (int a = 0; a < RP; ++a) {
+                float sh, sl;
+                dev::two_sum(acc[a].h, acc[a].l, sh, sl);
+                Cp2[((size_t)ax * RP + a) * Rp + col] = make_float2(sh, sl);
+            }
         }
     }
     tc::fence_before_sync();
@@ -1499,8 +1569,8 @@ __global__ void k_to_float(size_t len, const double* __restrict__ in, float* __r
 struct ProjTc {
     bool use = false;
     const float2* etab = nullptr;  // the pair exponential's table
-    uint8_t* Bs = nullptr;         // slices of Wp, 3 x KC x ProjShape<32>::B_BYTES
-    float* binv = nullptr;         // their scales, 3 x KC x 32
+    uint8_t* Bs = nullptr;         // slices of Wp, 3 x KC x ProjShape<32>::B_BYTES (16-row chunks)
+    float* binv = nullptr;         // their scales, 3 x KG x 32 (96-row groups)
     int* err = nullptr;
 };
 
@@ -1512,18 +1582,18 @@ rs_status launch_project_core(cudaStream_t st, int n, double b, double h, int N,
     dim3 gp((N + 127) / 128, Rl, 3);
     if (tcp.use) {
         constexpr int NP = RP <= 16 ? 16 : 32;
-        const int KC = (n + kPK - 1) / kPK;
+        const int KC = (n + kPK - 1) / kPK, KG = (KC + kPG - 1) / kPG;
         {
             ::rs::KernelTimer kt__("k_slice_wp", st, 0.0, false);
-            k_slice_wp<NP><<<dim3(KC, 3), NP, 0, st>>>(n, RP, KC, Wp2, tcp.Bs, tcp.binv);
+            k_slice_wp<NP><<<dim3(KC, 3), NP, 0, st>>>(n, RP, KC, KG, Wp2, tcp.Bs, tcp.binv);
         }
         auto kern = k_project_tc<RP, NP>;
         RS_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)ProjShape<NP>::SMEM));
         // the projection's algorithmic flops: one product and one sum per (row, column, a)
         ::rs::KernelTimer kt__("k_project_tc", st, 2.0 * RP * proj_points, true);
-        kern<<<gp, 128, ProjShape<NP>::SMEM, st>>>(n, b, h, N, Rl, KC, xyz, tl, perm, tcp.etab, tcp.Bs, tcp.binv,
-                                                  Cp2, tcp.err);
+        kern<<<gp, 160, ProjShape<NP>::SMEM, st>>>(n, b, h, N, Rl, KC, KG, xyz, tl, perm, tcp.etab, tcp.Bs,
+                                                  tcp.binv, Cp2, tcp.err);
     } else {
         // FP32 pipe ops per active (row, atom, term): two pair products (9 each) and RP
         // Dot2 steps (13 each)
@@ -1760,10 +1830,10 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         ::rs::KernelTimer kt__("k_gauss_dsum", st, 0.0, true);
         k_gauss_dsum<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(n, b, h, N, Rl, d_pk, d_tl, d_etab,
                                                                          nsc, nmc, d_Dp);
-        // FP32 pipe ops: 26 per half-grid point of the pair walks (two pair products,
-        // one pair sum) plus ~320 for the seeds (two pair exponentials, a pair
-        // quotient, the offsets) of every chunk within e^-50 of a Gaussian's peak
-        // (closed form per term; only when timed).
+        // FP32 pipe ops: 26 per half-grid point of the pair walk (two pair products,
+        // one pair sum) plus ~200 for the seeds (two pair exponentials, the offsets)
+        // of every chunk within e^-50 of a Gaussian's peak (closed form per term;
+        // only when timed).
         if (kt__.active()) {
             const double delta = 0.5 * h;
             double w = 0.0;
@@ -1773,7 +1843,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
                 for (size_t e = 0; e < xyz_host.size(); ++e) {
                     double lo = std::max(0.0, std::floor((xyz_host[e] - reach + b) / delta / kSC));
                     double hi = std::min((double)(nsc - 1), std::floor((xyz_host[e] + reach + b) / delta / kSC));
-                    if (hi >= lo) w += (hi - lo + 1) * (kSC * 26.0 + 320.0);
+                    if (hi >= lo) w += (hi - lo + 1) * (kSC * 26.0 + 200.0);
                 }
             }
             kt__.set_work(w);
@@ -2112,7 +2182,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
             return RS_ERR_CUDA;
         }
         RS_TRY(S.get(&tcp.Bs, (size_t)3 * KCp * ProjShape<32>::B_BYTES));
-        RS_TRY(S.get(&tcp.binv, (size_t)3 * KCp * 32));
+        RS_TRY(S.get(&tcp.binv, (size_t)3 * ((KCp + kPG - 1) / kPG) * 32));
     }
     RS_TRY(dispatch_project_core(RP, st, n, b, h, N, Rl, d_xyz, d_q, d_tl, d_al, d_perm, d_Wp, d_Cp, d_Bp,
                                  nchunk, CH, proj_points, tcp));

@@ -69,6 +69,42 @@ __device__ __forceinline__ void slice6(float h, float l, float (&d)[kS]) {
     }
 }
 
+// sum_d x_d 2^(-8d) of the six diagonal sums (exact integers in FP32), smallest term
+// first, into a float pair; every weight is a power of two, so each product is exact.
+__device__ __forceinline__ dev::F2 combine6(float x0, float x1, float x2, float x3, float x4, float x5) {
+    dev::F2 s{__fmul_rn(x5, 0x1p-40f), 0.f};
+    s = dev::df_add(s, dev::F2{__fmul_rn(x4, 0x1p-32f), 0.f});
+    s = dev::df_add(s, dev::F2{__fmul_rn(x3, 0x1p-24f), 0.f});
+    s = dev::df_add(s, dev::F2{__fmul_rn(x2, 0x1p-16f), 0.f});
+    s = dev::df_add(s, dev::F2{__fmul_rn(x1, 0x1p-8f), 0.f});
+    return dev::df_add(s, dev::F2{x0, 0.f});
+}
+
+// Three 8-column TMEM loads (32 lanes x 32 bits: thread t reads lane base + t) at
+// t, t + stride, t + 2 stride and the wait for them, in one statement so no use of the
+// values precedes the wait.
+__device__ __forceinline__ void tmem_ld8x3(uint32_t t, uint32_t stride, float (&a)[8], float (&b)[8],
+                                           float (&c)[8]) {
+    uint32_t x[24];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7]),
+          "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]), "=r"(x[14]), "=r"(x[15]),
+          "=r"(x[16]), "=r"(x[17]), "=r"(x[18]), "=r"(x[19]), "=r"(x[20]), "=r"(x[21]), "=r"(x[22]),
+          "=r"(x[23])
+        : "r"(t), "r"(t + stride), "r"(t + 2 * stride)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        a[i] = __uint_as_float(x[i]);
+        b[i] = __uint_as_float(x[8 + i]);
+        c[i] = __uint_as_float(x[16 + i]);
+    }
+}
+
 // Power-of-two scale for a chunk whose largest magnitude is m: s with m s < 32, and
 // 1/s; zero chunks (or m below 2^-119) get s = inv = 0.
 __device__ __forceinline__ void chunk_scale(float m, float& s, float& inv) { tc::row_scale(m, s, inv); }
@@ -233,10 +269,7 @@ __global__ void __launch_bounds__(kM, 1) k_tc_gemm(int n, int MT, int KC, const 
             if (i < n) {
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
-                    // sum_d acc_d 2^(-8d), smallest first, error-free into a pair
-                    dev::F2 s{ldexpf(acc[kS - 1][c], -8 * (kS - 1)), 0.f};
-#pragma unroll
-                    for (int d = kS - 2; d >= 0; --d) s = dev::df_add(s, dev::F2{ldexpf(acc[d][c], -8 * d), 0.f});
+                    const dev::F2 s = combine6(acc[0][c], acc[1][c], acc[2][c], acc[3][c], acc[4][c], acc[5][c]);
                     const float sc = __fmul_rn(ai, bi[c0 + c]);
                     out[c0 + c] = make_float2(__fmul_rn(s.h, sc), __fmul_rn(s.l, sc));
                 }
