@@ -174,30 +174,36 @@ __device__ __noinline__ void short_vdw(const ProteinView& P, const F2 x[3], cons
     }
 }
 
-// Per-warp queue of screened near pairs (short_coop).
+// Per-warp queue of screened near pairs (short_coop): up to kNearCap pairs in the
+// order of the warp's candidate list, with their terms once evaluated.
+constexpr int kNearCap = 96;
 template <bool GRAD>
 struct NearQueue {
-    int owner[64];   // lane whose atom the pair belongs to
-    int k[64];       // protein atom (cell-sorted index)
-    int bits[64];    // screen bits, then the pair's outcome bits
-    float2 w[32], fv[32], fgr[GRAD ? 32 : 1];
-    float2 f[GRAD ? 3 : 1][32];
+    int owner[kNearCap];   // lane whose atom the pair belongs to
+    int k[kNearCap];       // protein atom (cell-sorted index)
+    int bits[kNearCap];    // screen bits, then the pair's outcome bits
+    float2 w[kNearCap], fv[kNearCap], fgr[GRAD ? kNearCap : 1];
+    float2 f[GRAD ? 3 : 1][GRAD ? kNearCap : 1];
     float2 x[3][32]; // pair positions of the warp's atoms
     const PoseSetup* rq[32];  // where the atoms' FP64 positions come from (decisions
     const double* ry64[32];   // inside the sigma band)
     int ls[32];         // first entry of each lane's candidate list
     int lstart[32];     // prefix of the lanes' list lengths over the warp
-    int seg0[32], seg1[32];  // per owner lane: its entries [seg0, seg1) of a processed batch
+    int seg0[32], seg1[32];  // per owner lane: its entries [seg0, seg1) of the queue
 };
 
 // Short range and vdW decision for the 32 atoms of a warp (one per lane).  The
 // candidate lists of all 32 atoms form one list (lane by lane, each lane's in its own
-// candidate order) that the lanes screen in FP32 32 at a time, and the near pairs
-// are then evaluated in pair arithmetic one pair per lane: atoms with very
-// different numbers of candidates or near pairs still keep every lane busy.  Every lane of the warp must call it; lanes with
-// active = false contribute no atom.  prot_of(l) is the protein of lane l's atom
-// (lanes may belong to different proteins).  Each atom's sums are accumulated in
-// its own candidate order, so they equal short_vdw's (nl = 1) bit for bit.
+// candidate order) that the lanes screen in FP32 32 at a time; the near pairs queue
+// up in list order and are evaluated in pair arithmetic one pair per lane, 32 at a
+// time, so atoms with very different numbers of candidates or near pairs still keep
+// every lane busy.  When the queue is full (and at the end) each lane adds the terms
+// of its own atom's pairs, which sit contiguously in the queue, in list order: one
+// pass over the longest run instead of one per 32 pairs.  Every lane of the warp
+// must call it; lanes with active = false contribute no atom.  prot_of(l) is the
+// protein of lane l's atom (lanes may belong to different proteins).  Each atom's
+// sums are accumulated in its own candidate order, so they equal short_vdw's (nl = 1)
+// bit for bit.
 // Candidates screened and near pairs evaluated by a warp (warp-uniform counts).
 struct ShortCounts {
     long long cand = 0, near = 0;
@@ -235,29 +241,38 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
     const int grand = __shfl_sync(full, incl, 31);
     if (cnt) cnt->cand += grand;
     __syncwarp();
-    int qn = 0;  // entries in the queue (the same in every lane)
+    int qn = 0;     // entries in the queue (the same in every lane)
+    int pdone = 0;  // entries whose terms are evaluated
+    // terms of entries [pdone, pdone + m), one per lane
     auto process = [&](int m) {
-        __syncwarp();
-        Q.seg0[lane] = 0;
-        Q.seg1[lane] = 0;
-        __syncwarp();
         if (lane < m) {
-            const int o = Q.owner[lane];
-            // a batch holds its entries in list order, so each owner's are contiguous
-            if (lane == 0 || Q.owner[lane - 1] != o) Q.seg0[o] = lane;
-            if (lane == m - 1 || Q.owner[lane + 1] != o) Q.seg1[o] = lane + 1;
+            const int e = pdone + lane;
+            const int o = Q.owner[e];
             const F2 xo[3] = {F2{Q.x[0][o].x, Q.x[0][o].y}, F2{Q.x[1][o].x, Q.x[1][o].y},
                               F2{Q.x[2][o].x, Q.x[2][o].y}};
             const AtomRef ro{Q.rq[o], Q.ry64[o]};
             F2 f[3], w, fv{0.f, 0.f}, fgr{0.f, 0.f};
-            const int out = short_pair<GRAD>(prot_of(o), xo, ro, Q.k[lane], Q.bits[lane], f, w, fv, fgr);
-            Q.bits[lane] = out;
-            Q.w[lane] = make_float2(w.h, w.l);
-            Q.fv[lane] = make_float2(fv.h, fv.l);
+            const int out = short_pair<GRAD>(prot_of(o), xo, ro, Q.k[e], Q.bits[e], f, w, fv, fgr);
+            Q.bits[e] = out;
+            Q.w[e] = make_float2(w.h, w.l);
+            Q.fv[e] = make_float2(fv.h, fv.l);
             if constexpr (GRAD) {
-                Q.fgr[lane] = make_float2(fgr.h, fgr.l);
-                for (int a = 0; a < 3; ++a) Q.f[a][lane] = make_float2(f[a].h, f[a].l);
+                Q.fgr[e] = make_float2(fgr.h, fgr.l);
+                for (int a = 0; a < 3; ++a) Q.f[a][e] = make_float2(f[a].h, f[a].l);
             }
+        }
+        pdone += m;
+    };
+    // every queued pair's term into its owner's sums (in queue order), then empty the queue
+    auto flush = [&]() {
+        if (pdone < qn) process(qn - pdone);
+        Q.seg0[lane] = 0;
+        Q.seg1[lane] = 0;
+        __syncwarp();
+        for (int e = lane; e < qn; e += 32) {
+            const int o = Q.owner[e];
+            if (e == 0 || Q.owner[e - 1] != o) Q.seg0[o] = e;
+            if (e == qn - 1 || Q.owner[e + 1] != o) Q.seg1[o] = e + 1;
         }
         __syncwarp();
         if (active)
@@ -275,8 +290,11 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
                 }
             }
         __syncwarp();
+        qn = 0;
+        pdone = 0;
     };
     for (int base = 0; base < grand; base += 32) {
+        if (qn > kNearCap - 32) flush();  // room for a whole screened batch
         const int e = base + lane;
         int bits = 0, k = 0, o = 0;
         if (e < grand) {
@@ -304,18 +322,13 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
         }
         qn += __popc(m);
         if (cnt) cnt->near += __popc(m);
-        if (qn >= 32) {
+        __syncwarp();
+        if (qn - pdone >= 32) {
             process(32);
-            qn -= 32;
-            if (lane < qn) {  // move the overflow to the front
-                Q.owner[lane] = Q.owner[32 + lane];
-                Q.k[lane] = Q.k[32 + lane];
-                Q.bits[lane] = Q.bits[32 + lane];
-            }
             __syncwarp();
         }
     }
-    if (qn > 0) process(qn);
+    if (qn > 0) flush();
 }
 
 // The same for a warp whose atoms all belong to protein P.

@@ -52,7 +52,7 @@ __global__ void k_sorted_poses(ProteinView P, const double* __restrict__ rot,
 // atoms had few neighbours moves on at once, and the chunks with many near pairs
 // spread over all warps instead of over the ones a fixed stride assigns them to.
 template <bool GRAD>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, GRAD ? 6 : 8)
     k_sorted_atoms(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
                    int* __restrict__ pflag, AtomRec* __restrict__ rec, float2* __restrict__ shortv,
                    int* __restrict__ count, unsigned long long* __restrict__ counters,
