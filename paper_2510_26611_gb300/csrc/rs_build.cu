@@ -68,6 +68,29 @@ struct Scratch {
     }
 };
 
+// Several arrays of one protein in one device allocation (256-byte aligned parts):
+// add() records a pointer and its element count, alloc() makes the allocation (owned
+// by the protein) and sets the pointers.
+struct DeviceArena {
+    std::vector<std::pair<void**, size_t>> parts;  // (pointer, bytes)
+    template <class T>
+    void add(T** p, size_t count) {
+        parts.emplace_back(reinterpret_cast<void**>(p), (count * sizeof(T) + 255) / 256 * 256);
+    }
+    rs_status alloc(rs_protein* P) {
+        size_t total = 0;
+        for (auto& pr : parts) total += pr.second;
+        void* base = nullptr;
+        RS_TRY(device_alloc(P, &base, total));
+        char* c = static_cast<char*>(base);
+        for (auto& pr : parts) {
+            *pr.first = c;
+            c += pr.second;
+        }
+        return RS_OK;
+    }
+};
+
 }  // namespace
 bool symeig_host(int n, const double* A, double* lam, double* W);
 namespace {
@@ -82,31 +105,6 @@ inline void split_host(double v, float& h, float& l) {
 }
 
 // ------------------------------------------------------------------ cell list
-__global__ void k_bbox(int N, const double* __restrict__ xyz, double* __restrict__ out) {
-    __shared__ double sm[6][kBlock];
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int i = threadIdx.x; i < N; i += blockDim.x)
-        for (int a = 0; a < 3; ++a) {
-            double v = xyz[3 * (size_t)i + a];
-            lo[a] = fmin(lo[a], v);
-            hi[a] = fmax(hi[a], v);
-        }
-    for (int a = 0; a < 3; ++a) {
-        sm[a][threadIdx.x] = lo[a];
-        sm[3 + a][threadIdx.x] = hi[a];
-    }
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int a = 0; a < 3; ++a) {
-                sm[a][threadIdx.x] = fmin(sm[a][threadIdx.x], sm[a][threadIdx.x + s]);
-                sm[3 + a][threadIdx.x] = fmax(sm[3 + a][threadIdx.x], sm[3 + a][threadIdx.x + s]);
-            }
-        __syncthreads();
-    }
-    if (threadIdx.x < 6) out[threadIdx.x] = sm[threadIdx.x][0];
-}
-
 __global__ void k_cell_count(int N, const double* __restrict__ xyz, double co0, double co1,
                              double co2, double inv_cell, int nc0, int nc1, int nc2,
                              int* __restrict__ cell_of, int* __restrict__ count) {
@@ -1634,18 +1632,15 @@ rs_status dispatch_project_core(int RP, cudaStream_t st, int n, double b, double
 
 // ------------------------------------------------------------------ build steps
 static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz,
-                             const double* d_q, Scratch& S) {
+                             const double* d_q, const std::vector<double>& hxyz, Scratch& S) {
     const int N = P->N;
-    double* d_bb;
-    RS_TRY(S.get(&d_bb, 6));
-    {
-        ::rs::KernelTimer kt__("k_bbox", st, 0.0, false);
-        k_bbox<<<1, kBlock, 0, st>>>(N, d_xyz, d_bb);
-    }
-    RS_TRY_CUDA(cudaGetLastError());
-    double bb[6];
-    RS_TRY_CUDA(cudaMemcpyAsync(bb, d_bb, sizeof(bb), cudaMemcpyDeviceToHost, st));
-    RS_TRY_CUDA(cudaStreamSynchronize(st));
+    // bounding box of the charges (min and max are exact: the same on host and device)
+    double bb[6] = {hxyz[0], hxyz[1], hxyz[2], hxyz[0], hxyz[1], hxyz[2]};
+    for (int i = 1; i < N; ++i)
+        for (int a = 0; a < 3; ++a) {
+            bb[a] = std::min(bb[a], hxyz[3 * (size_t)i + a]);
+            bb[3 + a] = std::max(bb[3 + a], hxyz[3 * (size_t)i + a]);
+        }
     double cell = std::max(P->table.r_c, P->sigma) * (1.0 + 1e-4) + 1e-4;
     int nc[3];
     double co[3];
@@ -1667,9 +1662,13 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
     RS_TRY(S.get(&d_start, ncell + 1));
     float4 *d_atoms, *d_atoms_lo;
     double4* d_atoms64;
-    RS_TRY(device_alloc(P, (void**)&d_atoms, (size_t)N * sizeof(float4)));
-    RS_TRY(device_alloc(P, (void**)&d_atoms_lo, (size_t)N * sizeof(float4)));
-    RS_TRY(device_alloc(P, (void**)&d_atoms64, (size_t)N * sizeof(double4)));
+    {
+        DeviceArena ar;
+        ar.add(&d_atoms, N);
+        ar.add(&d_atoms_lo, N);
+        ar.add(&d_atoms64, N);
+        RS_TRY(ar.alloc(P));
+    }
     RS_TRY_CUDA(cudaMemsetAsync(d_count, 0, ncell * sizeof(int), st));
     RS_TRY_CUDA(cudaMemsetAsync(d_cursor, 0, ncell * sizeof(int), st));
     {
@@ -1726,8 +1725,12 @@ static rs_status build_cells(rs_protein* P, cudaStream_t st, const double* d_xyz
     RS_TRY_CUDA(cudaStreamSynchronize(st));
     float4* d_nb_atoms;
     int* d_nb_idx;
-    RS_TRY(device_alloc(P, (void**)&d_nb_atoms, (size_t)std::max(total, 1) * sizeof(float4)));
-    RS_TRY(device_alloc(P, (void**)&d_nb_idx, (size_t)std::max(total, 1) * sizeof(int)));
+    {
+        DeviceArena ar;
+        ar.add(&d_nb_atoms, std::max(total, 1));
+        ar.add(&d_nb_idx, std::max(total, 1));
+        RS_TRY(ar.alloc(P));
+    }
     {
         ::rs::KernelTimer kt__("k_nb_lists", st, 0.0, false);
         k_nb_lists<<<blocks_for(nfine * 32), kBlock, 0, st>>>(1, nf[0], nf[1], nf[2], fo[0], fo[1], fo[2], f,
@@ -2016,7 +2019,12 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         RS_TRY_CUDA(cudaGetLastError());
         return RS_OK;
     };
-    auto ritz = [&](std::vector<double>& lam_out) -> rs_status {
+    // host copies of the Rayleigh-Ritz matrices and eigenvectors (alive for the whole
+    // build, so the copy of the eigenvectors needs no wait)
+    std::vector<double> H((size_t)3 * p * p), Wh((size_t)3 * p * p);
+    // one Rayleigh-Ritz step; fail_out (if not null) gets the orthonormalisation flags
+    // and tr_out the Gram traces in the same device round trip
+    auto ritz = [&](std::vector<double>& lam_out, int* fail_out, double* tr_out) -> rs_status {
         RS_TRY(orthonormalize(d_Q));
         RS_TRY(gemm_gq());
         {
@@ -2033,8 +2041,9 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         }
         RS_TRY_CUDA(cudaGetLastError());
         // p x p eigenproblems on the host (FP64): a few microseconds each
-        std::vector<double> H((size_t)3 * p * p), Wh((size_t)3 * p * p);
         RS_TRY_CUDA(cudaMemcpyAsync(H.data(), d_Sm, H.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (fail_out) RS_TRY_CUDA(cudaMemcpyAsync(fail_out, d_fail, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (tr_out) RS_TRY_CUDA(cudaMemcpyAsync(tr_out, d_tr, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
         RS_TRY_CUDA(cudaStreamSynchronize(st));
         lam_out.resize((size_t)3 * p);
         for (int a = 0; a < 3; ++a)
@@ -2044,7 +2053,6 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
                 return RS_ERR_CUDA;
             }
         RS_TRY_CUDA(cudaMemcpyAsync(d_W, Wh.data(), Wh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        RS_TRY_CUDA(cudaStreamSynchronize(st));  // Wh is released on return
         return RS_OK;
     };
     // Subspace iteration converges like (lambda_{p+1} / lambda_r)^T.  After a few
@@ -2054,7 +2062,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     const int warm = 6;
     for (int it = 0; it < warm; ++it) RS_TRY(step());
     std::vector<double> lam_est;
-    RS_TRY(ritz(lam_est));
+    RS_TRY(ritz(lam_est, nullptr, nullptr));
     int more = 0;
     for (int a = 0; a < 3; ++a) {
         const double* la = lam_est.data() + (size_t)a * p;
@@ -2067,13 +2075,9 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     more = std::min(std::max(more, 2), 60);
     for (int it = 0; it < more; ++it) RS_TRY(step());
     P->subspace_steps = warm + more;
-    std::vector<double> lam_unused;
-    RS_TRY(ritz(lam_unused));
-    std::vector<double> lam = lam_unused, tr(3);
+    std::vector<double> lam, tr(3);
     int fail[3];
-    RS_TRY_CUDA(cudaMemcpyAsync(tr.data(), d_tr, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    RS_TRY_CUDA(cudaMemcpyAsync(fail, d_fail, sizeof(fail), cudaMemcpyDeviceToHost, st));
-    RS_TRY_CUDA(cudaStreamSynchronize(st));
+    RS_TRY(ritz(lam, fail, tr.data()));
     if (fail[0] || fail[1] || fail[2]) {
         set_error("orthonormalisation failed in the subspace iteration");
         return RS_ERR_CUDA;
@@ -2191,8 +2195,21 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         ::rs::KernelTimer kt__("k_sum_chunks", st, 0.0, false);
         k_sum_chunks<<<blocks_for(blen), kBlock, 0, st>>>(blen, nchunk, d_Bp, d_B, nullptr);
     }
-    float* core;
-    RS_TRY(device_alloc(P, (void**)&core, blen * sizeof(float)));
+    // the protein's evaluation tables, in one allocation: core, float-pair rows of V1'
+    // and V2', W = V3' core_(3)^T, and its tensor-core B image with scales
+    float *core, *vt0, *vt1, *wt, *wsc;
+    uint16_t* wtc;
+    size_t vplane = (size_t)n * RP, wplane = (size_t)n * RP * RP;
+    {
+        DeviceArena ar;
+        ar.add(&core, blen);
+        ar.add(&vt0, 4 * vplane);
+        ar.add(&vt1, 4 * vplane);
+        ar.add(&wt, 4 * wplane);
+        ar.add(&wtc, tc_bimage_bytes(n, RP) / sizeof(uint16_t));
+        ar.add(&wsc, tc_bscale_bytes(n, RP) / sizeof(float));
+        RS_TRY(ar.alloc(P));
+    }
     {
         ::rs::KernelTimer kt__("k_to_float", st, 0.0, false);
         k_to_float<<<blocks_for(blen), kBlock, 0, st>>>(blen, d_B, core);
@@ -2205,11 +2222,6 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         return RS_ERR_CUDA;
     }
     // 5. evaluation tables: float-pair rows of V1', V2' and of W = V3' core_(3)^T
-    float *vt0, *vt1, *wt;
-    size_t vplane = (size_t)n * RP, wplane = (size_t)n * RP * RP;
-    RS_TRY(device_alloc(P, (void**)&vt0, 4 * vplane * sizeof(float)));
-    RS_TRY(device_alloc(P, (void**)&vt1, 4 * vplane * sizeof(float)));
-    RS_TRY(device_alloc(P, (void**)&wt, 4 * wplane * sizeof(float)));
     {
         ::rs::KernelTimer kt__("k_pair_rows", st, 0.0, false);
         k_pair_rows<<<dim3(blocks_for(vplane), 2), kBlock, 0, st>>>(n, RP, d_Vs, vt0, vt1);
@@ -2219,10 +2231,6 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         k_wtable<<<dim3(blocks_for((size_t)RP * RP), n), kBlock, 0, st>>>(n, RP, d_Vs + 2 * vplane, d_B, wt);
     }
     RS_TRY_CUDA(cudaGetLastError());
-    uint16_t* wtc;
-    float* wsc;
-    RS_TRY(device_alloc(P, (void**)&wtc, tc_bimage_bytes(n, RP)));
-    RS_TRY(device_alloc(P, (void**)&wsc, tc_bscale_bytes(n, RP)));
     RS_TRY(tc_build_bimage(n, RP, wt, wtc, wsc, st));
     RS_TRY_CUDA(cudaStreamSynchronize(st));
     ProteinView& v = P->view;
@@ -2312,16 +2320,31 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
     P->K = (int)P->table.t.size();
 
     Scratch S(ctx);
-    // inputs on the device (and on the host, for the small host-side parts)
-    std::vector<double> hq(N);
+    // inputs on the device and on the host (the small host-side parts: bounding box,
+    // charge weights, work estimates); host inputs need no device round trip
+    std::vector<double> hq(N), hxyz((size_t)3 * N);
     double *d_xyz = nullptr, *d_q = nullptr;
     if ((s = S.get(&d_xyz, (size_t)3 * N)) != RS_OK) return fail_out(s);
     if ((s = S.get(&d_q, (size_t)N)) != RS_OK) return fail_out(s);
-    cudaMemcpyKind kind = mem_flags == RS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    if (cudaMemcpyAsync(d_xyz, xyz, (size_t)3 * N * sizeof(double), kind, st) != cudaSuccess ||
-        cudaMemcpyAsync(d_q, q, (size_t)N * sizeof(double), kind, st) != cudaSuccess ||
-        cudaMemcpyAsync(hq.data(), d_q, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
+    bool copied;
+    if (mem_flags == RS_MEM_HOST) {
+        std::memcpy(hxyz.data(), xyz, hxyz.size() * sizeof(double));
+        std::memcpy(hq.data(), q, hq.size() * sizeof(double));
+        copied = cudaMemcpyAsync(d_xyz, hxyz.data(), hxyz.size() * sizeof(double), cudaMemcpyHostToDevice, st) ==
+                     cudaSuccess &&
+                 cudaMemcpyAsync(d_q, hq.data(), hq.size() * sizeof(double), cudaMemcpyHostToDevice, st) ==
+                     cudaSuccess;
+    } else {
+        copied = cudaMemcpyAsync(d_xyz, xyz, hxyz.size() * sizeof(double), cudaMemcpyDeviceToDevice, st) ==
+                     cudaSuccess &&
+                 cudaMemcpyAsync(d_q, q, hq.size() * sizeof(double), cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+                 cudaMemcpyAsync(hxyz.data(), xyz, hxyz.size() * sizeof(double), cudaMemcpyDeviceToHost, st) ==
+                     cudaSuccess &&
+                 cudaMemcpyAsync(hq.data(), q, hq.size() * sizeof(double), cudaMemcpyDeviceToHost, st) ==
+                     cudaSuccess &&
+                 cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    if (!copied) {
         set_error("rs_build_protein: input copy failed: %s", cudaGetErrorString(cudaGetLastError()));
         return fail_out(RS_ERR_CUDA);
     }
@@ -2344,17 +2367,12 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
     cudaMemcpyAsync(d_tl, tl.data(), Rl * sizeof(double), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_al, al.data(), Rl * sizeof(double), cudaMemcpyHostToDevice, st);
 
-    if ((s = build_cells(P, st, d_xyz, d_q, S)) != RS_OK) return fail_out(s);
+    if ((s = build_cells(P, st, d_xyz, d_q, hxyz, S)) != RS_OK) return fail_out(s);
     if (prm->tucker_cap == 0) {
         s = build_canonical(P, st, d_xyz, d_q, d_tl, d_al, prm->galerkin);
     } else {
         std::vector<double> cz(N);
         for (int i = 0; i < N; ++i) cz[i] = std::pow(std::fabs(hq[i]), 2.0 / 3.0);
-        std::vector<double> hxyz((size_t)3 * N);
-        if (cudaMemcpy(hxyz.data(), d_xyz, hxyz.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
-            set_error("rs_build_protein: coordinate copy failed");
-            return fail_out(RS_ERR_CUDA);
-        }
         s = build_tucker(P, st, d_xyz, d_q, d_tl, d_al, tl, al, cz, hxyz, prm->tucker_cap,
                          prm->eps_r > 0 ? prm->eps_r : 0.0, S);
     }
