@@ -187,14 +187,15 @@ KERNEL_KIND = {
 POSE_ATOM_KERNELS = ("k_sorted_tc", "k_sorted_tc_grad", "k_sorted_wform", "k_sorted_wform_grad",
                      "k_sorted_atoms", "k_sorted_atoms_grad")
 
-# DRAM bytes (read + write) per pose-atom from one ncu capture of the kernel on a
-# small case of the same workload, with the digest of the kernel's sources at that
-# capture; a kernel whose sources changed since reports traffic null.
+# DRAM bytes (read + write) per pose-atom from one ncu capture of the kernel at the
+# bench's own size (one-pass DRAM metrics, so the full-size launch is captured), with
+# the digest of the kernel's sources at that capture; a kernel whose sources changed
+# since reports traffic null.
 TRAFFIC = {
-    name: {"bytes_per_pose_atom": b, "sources": "45bf52164af71775",
+    name: {"bytes_per_pose_atom": b, "sources": "0d6651d3aa535ffa",
            "profile": "profiles/pose_kernels_dram_protein_p100000.md"}
-    for name, b in (("k_sorted_tc_grad", 285.9), ("k_sorted_tc", 111.9), ("k_sorted_atoms_grad", 74.3),
-                    ("k_sorted_atoms", 51.3))
+    for name, b in (("k_sorted_tc_grad", 222.7), ("k_sorted_tc", 111.8), ("k_sorted_atoms_grad", 74.3),
+                    ("k_sorted_atoms", 51.9))
 }
 TRAFFIC_SOURCES = ("rs_sorted.cu", "rs_sorted_dev.cuh", "rs_tc.cuh", "rs_tc_dev.cuh", "rs_pose_dev.cuh",
                    "rs_common.cuh")

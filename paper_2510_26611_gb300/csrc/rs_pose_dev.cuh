@@ -141,15 +141,28 @@ __device__ __forceinline__ int short_pair(const ProteinView& P, const F2 x[3], c
     return out;
 }
 
-// Accumulation of one pair's term into an atom's sums (Dot2), in candidate order.
+// The term of one pair inside the cutoff: e = w fv (the potential) and, for
+// gradients, ge = fgr f (its gradient), each a pair product (~2^-47).
 template <bool GRAD>
-__device__ __forceinline__ void short_accumulate(F2 w, F2 fv, F2 fgr, const F2 f[3], F2& phi, F2 g[3]) {
-    dev::df_fma_acc(phi, w, fv);
-    if constexpr (GRAD) {
-        dev::df_fma_acc(g[0], fgr, f[0]);
-        dev::df_fma_acc(g[1], fgr, f[1]);
-        dev::df_fma_acc(g[2], fgr, f[2]);
-    }
+struct PairTerm {
+    F2 e;
+    F2 ge[GRAD ? 3 : 1];
+};
+template <bool GRAD>
+__device__ __forceinline__ PairTerm<GRAD> short_term(F2 w, F2 fv, F2 fgr, const F2 f[3]) {
+    PairTerm<GRAD> t;
+    t.e = dev::df_mul(w, fv);
+    if constexpr (GRAD)
+        for (int a = 0; a < 3; ++a) t.ge[a] = dev::df_mul(fgr, f[a]);
+    return t;
+}
+
+// Accumulation of one pair's term into an atom's sums (pair sums), in candidate order.
+template <bool GRAD>
+__device__ __forceinline__ void short_accumulate(const PairTerm<GRAD>& t, F2& phi, F2 g[3]) {
+    dev::df_acc(phi, t.e);
+    if constexpr (GRAD)
+        for (int a = 0; a < 3; ++a) dev::df_acc(g[a], t.ge[a]);
 }
 
 // Short-range part and vdW decision for one atom; candidates split over
@@ -170,7 +183,7 @@ __device__ __noinline__ void short_vdw(const ProteinView& P, const F2 x[3], cons
         F2 f[3], w, fv{0.f, 0.f}, fgr{0.f, 0.f};
         const int out = short_pair<GRAD>(P, x, ref, P.nb_idx[j], bits, f, w, fv, fgr);
         if (out & 1) clash = 1;
-        if (out & 2) short_accumulate<GRAD>(w, fv, fgr, f, phi, g);
+        if (out & 2) short_accumulate<GRAD>(short_term<GRAD>(w, fv, fgr, f), phi, g);
     }
 }
 
@@ -182,9 +195,10 @@ struct NearQueue {
     int owner[kNearCap];   // lane whose atom the pair belongs to
     int k[kNearCap];       // protein atom (cell-sorted index)
     int bits[kNearCap];    // screen bits, then the pair's outcome bits
-    float2 w[kNearCap], fv[kNearCap], fgr[GRAD ? kNearCap : 1];
-    float2 f[GRAD ? 3 : 1][GRAD ? kNearCap : 1];
+    float2 term[GRAD ? 4 : 1][kNearCap];  // the pair's term: e, then (gradients) ge[0..2]
     float2 x[3][32]; // pair positions of the warp's atoms
+    float2 acc[GRAD ? 4 : 1][GRAD ? 32 : 1];  // (gradients) the atoms' sums during a flush
+    int clash[GRAD ? 32 : 1];
     const PoseSetup* rq[32];  // where the atoms' FP64 positions come from (decisions
     const double* ry64[32];   // inside the sigma band)
     int ls[32];         // first entry of each lane's candidate list
@@ -254,11 +268,11 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
             F2 f[3], w, fv{0.f, 0.f}, fgr{0.f, 0.f};
             const int out = short_pair<GRAD>(prot_of(o), xo, ro, Q.k[e], Q.bits[e], f, w, fv, fgr);
             Q.bits[e] = out;
-            Q.w[e] = make_float2(w.h, w.l);
-            Q.fv[e] = make_float2(fv.h, fv.l);
-            if constexpr (GRAD) {
-                Q.fgr[e] = make_float2(fgr.h, fgr.l);
-                for (int a = 0; a < 3; ++a) Q.f[a][e] = make_float2(f[a].h, f[a].l);
+            if (out & 2) {
+                const PairTerm<GRAD> t = short_term<GRAD>(w, fv, fgr, f);
+                Q.term[0][e] = make_float2(t.e.h, t.e.l);
+                if constexpr (GRAD)
+                    for (int a = 0; a < 3; ++a) Q.term[1 + a][e] = make_float2(t.ge[a].h, t.ge[a].l);
             }
         }
         pdone += m;
@@ -275,20 +289,38 @@ __device__ void short_coop_with(ProtOf prot_of, bool active, const F2 x[3], cons
             if (e == qn - 1 || Q.owner[e + 1] != o) Q.seg1[o] = e + 1;
         }
         __syncwarp();
-        if (active)
-            for (int e = Q.seg0[lane], e1 = Q.seg1[lane]; e < e1; ++e) {
-                const int out = Q.bits[e];
-                if (out & 1) clash = 1;
-                if (out & 2) {
-                    F2 f[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-                    F2 fgr{0.f, 0.f};
-                    if constexpr (GRAD) {
-                        fgr = F2{Q.fgr[e].x, Q.fgr[e].y};
-                        for (int a = 0; a < 3; ++a) f[a] = F2{Q.f[a][e].x, Q.f[a][e].y};
-                    }
-                    short_accumulate<GRAD>(F2{Q.w[e].x, Q.w[e].y}, F2{Q.fv[e].x, Q.fv[e].y}, fgr, f, phi, g);
+        if constexpr (!GRAD) {
+            if (active)
+                for (int e = Q.seg0[lane], e1 = Q.seg1[lane]; e < e1; ++e) {
+                    const int out = Q.bits[e];
+                    if (out & 1) clash = 1;
+                    if (out & 2) dev::df_acc(phi, F2{Q.term[0][e].x, Q.term[0][e].y});
                 }
+        } else {
+            // four sums per atom (phi, g): one lane per (atom, sum), eight atoms at a time,
+            // each sum still taken over the atom's pairs in queue order
+            Q.acc[0][lane] = make_float2(phi.h, phi.l);
+            for (int a = 0; a < 3; ++a) Q.acc[1 + a][lane] = make_float2(g[a].h, g[a].l);
+            Q.clash[lane] = 0;
+            __syncwarp();
+            const int c = lane & 3;
+            for (int pass = 0; pass < 4; ++pass) {
+                const int o = pass * 8 + (lane >> 2);
+                F2 sum{Q.acc[c][o].x, Q.acc[c][o].y};
+                int cl = 0;
+                for (int e = Q.seg0[o], e1 = Q.seg1[o]; e < e1; ++e) {
+                    const int out = Q.bits[e];
+                    cl |= out & 1;
+                    if (out & 2) dev::df_acc(sum, F2{Q.term[c][e].x, Q.term[c][e].y});
+                }
+                Q.acc[c][o] = make_float2(sum.h, sum.l);
+                if (c == 0 && cl) Q.clash[o] = 1;
             }
+            __syncwarp();
+            phi = F2{Q.acc[0][lane].x, Q.acc[0][lane].y};
+            for (int a = 0; a < 3; ++a) g[a] = F2{Q.acc[1 + a][lane].x, Q.acc[1 + a][lane].y};
+            if (active && Q.clash[lane]) clash = 1;
+        }
         __syncwarp();
         qn = 0;
         pdone = 0;
@@ -412,16 +444,16 @@ __device__ __forceinline__ F2 warp_sum_pair(F2 v) {
     return v;
 }
 
-// Sum over the atoms of one pose of its per-atom contributions [L][NC] (float
-// pairs), by one warp: lane-strided pair sums, then a butterfly; every lane ends
-// with s (FP64).
-template <int NC>
+// Sum over the atoms of one pose of its per-atom contributions [L][CS] (NC float
+// pairs per atom, CS >= NC apart), by one warp: lane-strided pair sums, then a
+// butterfly; every lane ends with s (FP64).
+template <int NC, int CS = NC>
 __device__ __forceinline__ void pose_sums(const float2* __restrict__ cpose, int L, int lane, double s[NC]) {
     F2 acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = F2{0.f, 0.f};
     for (int j = lane; j < L; j += 32) {
-        const float2* cj = cpose + (size_t)j * NC;
+        const float2* cj = cpose + (size_t)j * CS;
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = dev::df_add(acc[c], F2{cj[c].x, cj[c].y});
     }

@@ -189,8 +189,9 @@ __global__ void k_sorted_reduce(const PoseSetup* __restrict__ ps, int PC, int L,
     const int lane = threadIdx.x & 31;
     const long long pl = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (pl >= PC || !ps[pl].valid) return;
+    constexpr int CS = kContribStride<NC == 7>;
     double s[NC];
-    pose_sums<NC>(contrib + (size_t)pl * L * NC, L, lane, s);
+    pose_sums<NC, CS>(contrib + (size_t)pl * L * CS, L, lane, s);
     if (lane == 0) write_pose<NC>(ps[pl], s, pflag[pl], p0 + pl, E, flags, gt, gw);
 }
 
@@ -212,15 +213,15 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t chunk_bytes(long long PC, int L, int n, bool grad) {
     const long long M = PC * L;
-    const int NC = grad ? 7 : 1;
+    const int CS = grad ? kContribStride<true> : kContribStride<false>;
     return align256(PC * sizeof(PoseSetup)) + align256(PC * 4) + 2 * align256(M * sizeof(AtomRec)) +
-           align256(M * 8 * (grad ? 4 : 1)) + align256(M * 8 * NC) + align256((size_t)n * kSub * 4) +
+           align256(M * 8 * (grad ? 4 : 1)) + align256(M * 8 * CS) + align256((size_t)n * kSub * 4) +
            align256(((size_t)n * kSub + 1) * 4) + align256(key_scan_ints((long long)n * kSub) * 4) + 256;
 }
 
 SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
     const long long M = PC * L;
-    const int NC = grad ? 7 : 1;
+    const int CS = grad ? kContribStride<true> : kContribStride<false>;
     char* p = (char*)base;
     SortedScratch s;
     auto take = [&](size_t b) {
@@ -233,7 +234,7 @@ SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
     s.rec = (AtomRec*)take(M * sizeof(AtomRec));
     s.srt = (AtomRec*)take(M * sizeof(AtomRec));
     s.shortv = (float2*)take(M * 8 * (grad ? 4 : 1));
-    s.contrib = (float2*)take(M * 8 * NC);
+    s.contrib = (float2*)take(M * 8 * CS);
     s.count = (int*)take((size_t)n * kSub * 4);
     s.off = (int*)take(((size_t)n * kSub + 1) * 4);
     s.bsum = (int*)take(key_scan_ints((long long)n * kSub) * 4);

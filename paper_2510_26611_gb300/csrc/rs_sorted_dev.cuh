@@ -169,6 +169,23 @@ __device__ __forceinline__ void store_short_value(float2* __restrict__ shortv, l
     }
 }
 
+// Per-atom contributions of the cell-grouped paths in global memory: NC = 7 float
+// pairs per atom for gradients, stored 8 apart (64 bytes, a whole number of 32-byte
+// sectors, so the scattered per-atom writes never leave a sector partly written, which
+// would make the L2 fetch the rest of it from DRAM); 1 for energies.
+template <bool GRAD>
+constexpr int kContribStride = GRAD ? 8 : 1;
+
+// Contributions of one atom (atom_contrib) at their slot of the cell-grouped layout.
+template <bool GRAD>
+__device__ __forceinline__ void store_contrib(const ProteinView& P, dev::F2 phi, dev::F2 g1, dev::F2 g2, dev::F2 g3,
+                                              dev::F2 phs, const dev::F2 gs[3], double qd, const float ry[3],
+                                              float2* __restrict__ contrib, long long slot) {
+    float2* cj = contrib + (size_t)slot * kContribStride<GRAD>;
+    atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, qd, ry, cj);
+    if constexpr (GRAD) cj[7] = make_float2(0.f, 0.f);
+}
+
 // Long range of one atom from its record (ligand atom j), with the axis-3 slab of
 // its cell in shared memory (planes Wh, Wl, Dh, Dl of RP x RP floats); writes its
 // contributions at slot r.slot.
@@ -177,7 +194,6 @@ __device__ __forceinline__ void sorted_atom(const ProteinView& P, const LigandVi
                                             const float* __restrict__ slab, const float2* __restrict__ shortv,
                                             float2* __restrict__ contrib) {
     using dev::F2;
-    constexpr int NC = GRAD ? 7 : 1;
     const bool in1 = r.bits & 1, in2 = r.bits & 2, in3 = r.bits & 4;
     F2 v2[RP];
     F2 dv2[GRAD ? RP : 1];
@@ -244,7 +260,7 @@ __device__ __forceinline__ void sorted_atom(const ProteinView& P, const LigandVi
     F2 phs, gs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     short_value<GRAD>(shortv, r.slot, phs, gs);
     const float ry[3] = {r.ry0, r.ry1, r.ry2};
-    atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, lig.q64[j], ry, contrib + (size_t)r.slot * NC);
+    store_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, lig.q64[j], ry, contrib, r.slot);
 }
 
 }  // namespace

@@ -277,15 +277,15 @@ __device__ __forceinline__ void tc_wform_range(const Src& src, const AtomRec* __
         }
         if (!ok) {
             if (act)
-                for (int c = 0; c < NC; ++c) contrib[(size_t)r.slot * NC + c] = make_float2(__int_as_float(-1), 0.f);
+                for (int c = 0; c < NC; ++c)
+                    contrib[(size_t)r.slot * kContribStride<GRAD> + c] = make_float2(__int_as_float(-1), 0.f);
             if (tid == 0) atomicExch(err, 1);
             break;
         }
         if (act) {
             const int j = src.atom(r, sg);
             const float ry[3] = {r.ry0, r.ry1, r.ry2};
-            atom_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, src.ligand(sg).q64[j], ry,
-                               contrib + (size_t)r.slot * NC);
+            store_contrib<GRAD>(P, phi, g1, g2, g3, phs, gs, src.ligand(sg).q64[j], ry, contrib, r.slot);
         }
         tc::fence_before_sync();
         __syncthreads();
