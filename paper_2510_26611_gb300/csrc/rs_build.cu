@@ -658,12 +658,12 @@ __global__ void __launch_bounds__(256) k_atb(int n, int p, const double* __restr
 }
 
 // Cholesky S + shift*I = R^T R (R upper) and Rinv = R^{-1} (p <= 48) in float-pair
-// arithmetic: one CTA per axis, 256 threads over a 16 x 16 tile, one pivot operation
-// and two barriers per step.
-//   Cholesky, right-looking: step k takes rk = 1/sqrt(A[k][k]), writes row k of R
-//   (A[k][j] rk) and updates the trailing upper triangle by A[k][i] A[k][j] rk^2.
+// arithmetic: one CTA per axis, 256 threads over a 16 x 16 tile, one barrier per step.
+//   Cholesky, right-looking: step k takes rk = 1/sqrt(A[k][k]) (in every thread) and
+//   updates the trailing upper triangle by A[k][i] A[k][j] rk^2; row k of R is
+//   A[k][j] rk, formed where it is used.
 //   Inverse, by rows from the bottom: X[k][k] = rk, X[k][j] = -rk acc[k][j], and
-//   acc[i][j] += R[i][k] X[k][j] for i < k <= j, one barrier per row.
+//   acc[i][j] += R[i][k] X[k][j] for i < k <= j.
 // S is a Gram matrix: a pivot at or below 1e-14 of its trace belongs to a direction
 // the block does not span (a rank-deficient block, e.g. a protein with fewer Gaussian
 // terms than the block size); its column of Q becomes 0 (R[k][k] = 0, rk = 0) instead
@@ -684,7 +684,7 @@ __device__ __forceinline__ dev::F2 pair_rsqrt(dev::F2 d) {
 __global__ void __launch_bounds__(256) k_chol_pair(int p, const double* __restrict__ S, double rel_shift,
                                                    double* __restrict__ Rinv, int* __restrict__ fail) {
     using dev::F2;
-    __shared__ float2 A[48][49];   // factorised in place; upper triangle ends as R
+    __shared__ float2 A[48][49];   // factorised in place; R[k][j] = A[k][j] rk[k] (j > k)
     __shared__ float2 X[48][49];   // accumulators, then R^{-1}
     __shared__ float2 rk[48];      // 1 / R[k][k]
     __shared__ double red[2];
@@ -715,16 +715,14 @@ __global__ void __launch_bounds__(256) k_chol_pair(int p, const double* __restri
     }
     __syncthreads();
     for (int k = 0; k < p; ++k) {
+        // every thread takes the pivot's reciprocal square root itself (the same value),
+        // so the step needs one barrier; row k stays unscaled (R[k][j] = A[k][j] rk)
+        const F2 d{A[k][k].x, A[k][k].y};
+        const F2 r = d.h > thresh ? pair_rsqrt(d) : F2{0.f, 0.f};
         if (threadIdx.x == 0) {
-            const F2 d{A[k][k].x, A[k][k].y};
             if (d.h != d.h) fail[ax] = 1;
-            const F2 r = d.h > thresh ? pair_rsqrt(d) : F2{0.f, 0.f};
             rk[k] = make_float2(r.h, r.l);
-            const F2 dr = dev::df_mul(d, r);
-            A[k][k] = make_float2(dr.h, dr.l);
         }
-        __syncthreads();
-        const F2 r{rk[k].x, rk[k].y};
         const F2 r2 = dev::df_mul(r, r);
         for (int i = k + 1 + ty; i < p; i += 16) {
             const F2 aki = dev::df_mul(F2{A[k][i].x, A[k][i].y}, r2);
@@ -735,28 +733,30 @@ __global__ void __launch_bounds__(256) k_chol_pair(int p, const double* __restri
                 }
         }
         __syncthreads();
-        if (threadIdx.x > k && threadIdx.x < p) {
-            const F2 v = dev::df_mul(F2{A[k][threadIdx.x].x, A[k][threadIdx.x].y}, r);
-            A[k][threadIdx.x] = make_float2(v.h, v.l);
-        }
     }
-    __syncthreads();
-    // R^{-1}, rows from the bottom; X[k][.] is final once acc[k][.] has all rows > k
+    // R^{-1}, rows from the bottom: step k adds row k's part to the rows above (X[k][.]
+    // taken from its sums, complete once every row below k has been added) and makes
+    // row k + 1 final, which no thread reads in this step: one barrier per step
+    auto final_x = [&](int k, int j) {
+        const F2 rr{rk[k].x, rk[k].y};
+        const F2 v = j == k ? rr : dev::df_mul(F2{-rr.h, -rr.l}, F2{X[k][j].x, X[k][j].y});
+        X[k][j] = make_float2(v.h, v.l);
+    };
     for (int k = p - 1; k >= 0; --k) {
         const F2 r{rk[k].x, rk[k].y};
-        for (int i = ty; i < k; i += 16)
+        for (int i = ty; i < k; i += 16) {
+            const F2 rik = dev::df_mul(F2{A[i][k].x, A[i][k].y}, F2{rk[i].x, rk[i].y});  // R[i][k]
             for (int j = k + tx; j < p; j += 16) {
                 const F2 xkj = j == k ? r : dev::df_mul(F2{-r.h, -r.l}, F2{X[k][j].x, X[k][j].y});
-                const F2 v = dev::df_add(F2{X[i][j].x, X[i][j].y}, dev::df_mul(F2{A[i][k].x, A[i][k].y}, xkj));
+                const F2 v = dev::df_add(F2{X[i][j].x, X[i][j].y}, dev::df_mul(rik, xkj));
                 X[i][j] = make_float2(v.h, v.l);
             }
-        __syncthreads();
-        if (threadIdx.x >= k && threadIdx.x < p) {
-            const F2 v = threadIdx.x == k ? r : dev::df_mul(F2{-r.h, -r.l}, F2{X[k][threadIdx.x].x, X[k][threadIdx.x].y});
-            X[k][threadIdx.x] = make_float2(v.h, v.l);
         }
+        if (k + 1 < p && threadIdx.x > k && threadIdx.x < p) final_x(k + 1, threadIdx.x);
         __syncthreads();
     }
+    if (threadIdx.x < p) final_x(0, threadIdx.x);
+    __syncthreads();
     double* Ra = Rinv + (size_t)ax * p * p;
     for (int i = ty; i < p; i += 16)
         for (int j = tx; j < p; j += 16) Ra[i * p + j] = j >= i ? dev::df_to(F2{X[i][j].x, X[i][j].y}) : 0.0;

@@ -11,9 +11,10 @@ namespace rs {
 namespace {
 
 // For every axis-3 cell i and column nn = 2a + t of B (t = 0: row a of W[i], t = 1:
-// row a of D[i]; K = the axis-2 index b): the BF16 slices of the row relative
-// to its power-of-two scale (FP64, exact for the 48-bit pair values), written in the
-// canonical K-major layout the MMA reads; csc = 2^(E-kTopBits), the inverse scale.
+// row a of D[i]; K = the axis-2 index b): the BF16 slices of the row (float pairs)
+// relative to its power-of-two scale, cut exactly in FP32 by slice5 (the same
+// slicing as the A rows of the pose kernels), written in the canonical K-major layout
+// the MMA reads, eight K values per 16-byte store; csc = the inverse scale.
 __global__ void k_tc_bimage(int n, int RP, const float* __restrict__ wt, uint16_t* __restrict__ img,
                             float* __restrict__ csc) {
     const int KP = tc::kp_of(RP), NP = tc::np_of(RP);
@@ -22,34 +23,38 @@ __global__ void k_tc_bimage(int n, int RP, const float* __restrict__ wt, uint16_
     if (nn >= NP) return;
     const size_t plane = (size_t)n * RP * RP;
     const int a = nn >> 1, t = nn & 1;
-    double x[32];
-    double m = 0.0;
-    for (int b = 0; b < 32; ++b) {
-        double v = 0.0;
-        if (a < RP && b < RP) {
-            const size_t o = ((size_t)i * RP + a) * RP + b;
-            v = (double)wt[2 * t * plane + o] + (double)wt[(2 * t + 1) * plane + o];
-        }
-        x[b] = v;
-        m = fmax(m, fabs(v));
-    }
-    int E = 0;
-    frexp(m, &E);  // m < 2^E
-    const bool zero = !(m > 0x1p-119);
-    const double s = zero ? 0.0 : ldexp(1.0, tc::kTopBits - E);
+    const float* wh = wt + 2 * t * plane + ((size_t)i * RP + a) * RP;
+    const float* wl = wt + (2 * t + 1) * plane + ((size_t)i * RP + a) * RP;
+    const bool row = a < RP;
+    float m = 0.f;
+    if (row)
+        for (int b = 0; b < RP; ++b) m = fmaxf(m, fabsf(wh[b]));
+    float s, inv;
+    tc::row_scale(m, s, inv);
     const size_t slice = (size_t)NP * KP;
     uint16_t* base = img + (size_t)i * tc::kSlices * slice;
     const uint32_t sbo = (uint32_t)KP * 16;
-    for (int b = 0; b < KP; ++b) {
-        double y = b < RP ? x[b] * s : 0.0;
-        for (int j = 0; j < tc::kSlices; ++j) {
-            const double d = rint(y);
-            y = (y - d) * 256.0;
-            const __nv_bfloat16 hb = __float2bfloat16_rn((float)ldexp(d, -8 * j));
-            base[j * slice + tc::kmajor_offset(nn, b, sbo) / 2] = __bfloat16_as_ushort(hb);
+    for (int k8 = 0; k8 < KP; k8 += 8) {
+        uint32_t w[tc::kSlices][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float lo[tc::kSlices], hi[tc::kSlices];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int b = k8 + e + hh;
+                const dev::F2 x = (row && b < RP) ? dev::F2{__fmul_rn(wh[b], s), __fmul_rn(wl[b], s)}
+                                                  : dev::F2{0.f, 0.f};
+                tc::slice5(x, hh ? hi : lo);
+            }
+#pragma unroll
+            for (int j = 0; j < tc::kSlices; ++j) w[j][e / 2] = tc::pack_bf16x2(lo[j], hi[j]);
         }
+#pragma unroll
+        for (int j = 0; j < tc::kSlices; ++j)
+            *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(base + j * slice) +
+                                      tc::kmajor_offset(nn, k8, sbo)) = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
     }
-    csc[(size_t)i * NP + nn] = zero ? 0.f : (float)ldexp(1.0, E - tc::kTopBits);
+    csc[(size_t)i * NP + nn] = inv;
 }
 
 // One tile of the contraction: rows v (pairs from FP64), B image of cell 0.
