@@ -1132,7 +1132,7 @@ __global__ void __launch_bounds__(128) k_project(int n, double b, double h, int 
 // Partial cores over column chunks: Bp[chunk][a][b][c] = sum_r xi_r C'1[a,r] C'2[b,r] C'3[c,r],
 // in float-pair arithmetic; CTA: RP*RP threads, thread = (a, b), CH columns per CTA.
 template <int RP>
-__global__ void __launch_bounds__(1024) k_core(int Rtot, int Rl, int CH,
+__global__ void __launch_bounds__(RP * RP, 1) k_core(int Rtot, int Rl, int CH,
                                                const double* __restrict__ q,
                                                const double* __restrict__ al,
                                                const float2* __restrict__ Cp2,
@@ -2137,7 +2137,10 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY_CUDA(cudaGetLastError());
     // 4. projections and core
     const int Rtot = N * Rl;
-    const int CH = 512;  // columns per k_core CTA (192 measured slower: more partial cores)
+    // columns per k_core CTA: about 152 CTAs (one wave of one CTA per SM on GB300; the
+    // accumulators of a thread stay in registers), a multiple of the 32-column tile;
+    // a function of the problem only, so the partial cores' order is fixed
+    const int CH = ((Rtot + 151) / 152 + 31) / 32 * 32;
     const int nchunk = (Rtot + CH - 1) / CH;
     double *d_Bp, *d_B;
     float2* d_Cp;
