@@ -1279,7 +1279,7 @@ template <bool DIRECT>
 __device__ __forceinline__ void proj_row(const ProjGauss& G, uint8_t* sA, int row, int i0, int ia, int ib, float sc,
                                          dev::F2& g, dev::F2& rho) {
     using dev::F2;
-#pragma unroll
+#pragma unroll 1
     for (int gq = 0; gq < kPK / 8; ++gq) {
         uint32_t w[tcg::kS][4];
 #pragma unroll
