@@ -7,10 +7,10 @@
 // warp stages a slab in shared memory once and every atom of that cell reads it
 // there as a broadcast.  The launch sequence per chunk of poses is
 //   k_sorted_poses   pose setups (rotation, Jacobian) of the chunk
-//   k_sorted_atoms   per atom: FP64 position, cells, fractions, short range and
-//                    vdW (flags), a 48-byte record, and its rank in a per-cell count
+//   k_sorted_keys    per atom: its sort key and its rank in a per-key count
 //   key scan         exclusive scan of the per-key counts (three kernels)
-//   k_sorted_scatter records to their cell-sorted positions
+//   k_sorted_atoms   per atom: position, cells, fractions, short range and vdW
+//                    (flags), and a 48-byte record written at its sorted position
 //   k_sorted_wform   per warp: a contiguous run of sorted atoms; slab of the current
 //                    cell in shared memory; long range + contributions per atom
 //   k_sorted_reduce  per pose: sums over its atoms (one warp per pose)
@@ -46,6 +46,31 @@ __global__ void k_sorted_poses(ProteinView P, const double* __restrict__ rot,
     else ps[pl].valid = 0;
 }
 
+// Sort key and rank of every pose-atom of the chunk, kr[g] = (key, rank) (key
+// (n - 1) kSub: a skipped pose).  The key comes from the same position and cell
+// arithmetic as the atom's record in k_sorted_atoms, which places the record at
+// off[key] + rank: the (key, rank) pairs are distinct, so the positions are a
+// permutation of the chunk's atoms.
+__global__ void k_sorted_keys(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
+                              int* __restrict__ count, int2* __restrict__ kr) {
+    const long long M = (long long)PC * lig.L;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M) return;
+    const int pl = (int)(g / lig.L), j = (int)(g - (long long)pl * lig.L);
+    int key = (P.n - 1) * kSub;
+    if (ps[pl].valid) {
+        F2 x[3];
+        atom_position(ps[pl], lig.yd + 3 * j, x);
+        int i2, i3;
+        float f;
+        bool in;
+        dev::axis_cell(x[1], F2{P.b_h, P.b_l}, F2{P.inv_h_h, P.inv_h_l}, P.n, i2, f, in);
+        dev::axis_cell(x[2], F2{P.b_h, P.b_l}, F2{P.inv_h_h, P.inv_h_l}, P.n, i3, f, in);
+        key = i3 * kSub + sub_bucket(i2, P.n, kSub);
+    }
+    kr[g] = make_int2(key, atomicAdd(&count[key], 1));
+}
+
 // One thread per pose-atom; the short range of a warp's 32 atoms is taken
 // together (short_coop), so the pair work of near pairs keeps all lanes busy.  Warps
 // are persistent and take 32-atom chunks from a launch-wide cursor, so a warp whose
@@ -54,8 +79,8 @@ __global__ void k_sorted_poses(ProteinView P, const double* __restrict__ rot,
 template <bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, GRAD ? 6 : 8)
     k_sorted_atoms(ProteinView P, LigandView lig, const PoseSetup* __restrict__ ps, int PC,
-                   int* __restrict__ pflag, AtomRec* __restrict__ rec, float2* __restrict__ shortv,
-                   int* __restrict__ count, unsigned long long* __restrict__ counters,
+                   int* __restrict__ pflag, const int2* __restrict__ kr, const int* __restrict__ off,
+                   AtomRec* __restrict__ srt, float2* __restrict__ shortv, unsigned long long* __restrict__ counters,
                    unsigned long long* __restrict__ cursor) {
     __shared__ NearQueue<GRAD> queues[kWarpsPerBlock];
     const int L = lig.L;
@@ -87,11 +112,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, GRAD ? 6 : 8)
         if (!in_range) continue;
         AtomRec r;
         r.slot = (int)g;
+        const int2 kg = kr[g];
+        r.rank = kg.y;
+        AtomRec* dst = srt + off[kg.x] + kg.y;
         if (!valid) {
             r.i3 = P.n - 1;
             r.bits = 0;
-            r.rank = atomicAdd(&count[(P.n - 1) * kSub], 1);
-            rec[g] = r;
+            *dst = r;
             continue;
         }
         int fl = clash ? RS_FLAG_CLASH : 0;
@@ -108,8 +135,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, GRAD ? 6 : 8)
         r.ry0 = ry[0];
         r.ry1 = ry[1];
         r.ry2 = ry[2];
-        r.rank = atomicAdd(&count[rec_key(r, kSub)], 1);
-        rec[g] = r;
+        *dst = r;
     }
     if (lane == 0 && natoms > 0) {  // work counters of the launch (diagnostics)
         atomicAdd(&counters[0], (unsigned long long)natoms);
@@ -199,7 +225,7 @@ __global__ void k_sorted_reduce(const PoseSetup* __restrict__ ps, int PC, int L,
 struct SortedScratch {
     PoseSetup* ps;
     int* pflag;
-    AtomRec* rec;
+    int2* kr;     // sort key of each atom and its rank among the atoms of that key
     AtomRec* srt;
     float2* shortv;
     float2* contrib;
@@ -214,7 +240,7 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 size_t chunk_bytes(long long PC, int L, int n, bool grad) {
     const long long M = PC * L;
     const int CS = grad ? kContribStride<true> : kContribStride<false>;
-    return align256(PC * sizeof(PoseSetup)) + align256(PC * 4) + 2 * align256(M * sizeof(AtomRec)) +
+    return align256(PC * sizeof(PoseSetup)) + align256(PC * 4) + align256(M * 8) + align256(M * sizeof(AtomRec)) +
            align256(M * 8 * (grad ? 4 : 1)) + align256(M * 8 * CS) + align256((size_t)n * kSub * 4) +
            align256(((size_t)n * kSub + 1) * 4) + align256(key_scan_ints((long long)n * kSub) * 4) + 256;
 }
@@ -231,7 +257,7 @@ SortedScratch carve(void* base, long long PC, int L, int n, bool grad) {
     };
     s.ps = (PoseSetup*)take(PC * sizeof(PoseSetup));
     s.pflag = (int*)take(PC * 4);
-    s.rec = (AtomRec*)take(M * sizeof(AtomRec));
+    s.kr = (int2*)take(M * 8);
     s.srt = (AtomRec*)take(M * sizeof(AtomRec));
     s.shortv = (float2*)take(M * 8 * (grad ? 4 : 1));
     s.contrib = (float2*)take(M * 8 * CS);
@@ -287,10 +313,15 @@ rs_status launch_sorted_tc(const EvalLaunch& a, const SortedScratch& s, long lon
     return RS_OK;
 }
 
+// The W-form kernel of a chunk of M atoms: the tensor-core form when the call's full
+// chunks (M_call atoms each) fill its tiles, else the float-pair form.  Every chunk of
+// a call takes the same form, so a pose's result does not depend on which chunk (or
+// which position in the batch) holds it.
 template <bool GRAD>
-rs_status dispatch_sorted_wform(const EvalLaunch& a, const SortedScratch& s, long long M, cudaStream_t st) {
+rs_status dispatch_sorted_wform(const EvalLaunch& a, const SortedScratch& s, long long M, long long M_call,
+                                cudaStream_t st) {
     const bool tcore = wform_kernel_mode() == 1 && a.prot.Wtc != nullptr &&
-                       (double)M >= kTcMinAtomsPerCell * (double)(a.prot.n - 1);
+                       (double)M_call >= kTcMinAtomsPerCell * (double)(a.prot.n - 1);
     switch (a.prot.R) {
 #define RS_CASE(R)                                                                          \
     case R:                                                                                 \
@@ -326,14 +357,25 @@ unsigned atoms_grid(long long M) {
     return (unsigned)std::max<long long>(1, std::min<long long>(need, resident));
 }
 
-// Per-atom contributions of the pc poses whose setups are in s.ps: short range and
-// vdW, cell keys, key scan, scatter and the W form (into s.contrib and s.pflag).
+// Per-atom contributions of the pc poses whose setups are in s.ps: sort keys, key
+// scan, short range and vdW with the records at their sorted positions, and the W
+// form (into s.contrib and s.pflag).
 template <bool GRAD>
-rs_status sorted_chunk_contrib(const EvalLaunch& a, const SortedScratch& s, int pc, cudaStream_t st) {
+rs_status sorted_chunk_contrib(const EvalLaunch& a, const SortedScratch& s, int pc, long long pc_call,
+                               cudaStream_t st) {
     const int L = a.lig.L, n = a.prot.n;
     const long long M = (long long)pc * L;
     RS_TRY_CUDA(cudaMemsetAsync(s.count, 0, (size_t)n * kSub * 4, st));
     RS_TRY_CUDA(cudaMemsetAsync(s.cursor, 0, 8, st));
+    {
+        ::rs::KernelTimer kt__("k_sorted_keys", st, 0.0, false, a.events);
+        k_sorted_keys<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(a.prot, a.lig, s.ps, pc, s.count, s.kr);
+    }
+    {
+        ::rs::KernelTimer kt__("k_key_scan", st, 0.0, false, a.events);
+        launch_key_scan(n * kSub, s.count, s.bsum, s.off, st);
+        note_launch(2);  // three kernels under one timer
+    }
     {
         const unsigned grid = atoms_grid<GRAD>(M);
         int dev = 0;
@@ -344,20 +386,11 @@ rs_status sorted_chunk_contrib(const EvalLaunch& a, const SortedScratch& s, int 
             return RS_ERR_CUDA;
         }
         ::rs::KernelTimer kt__(GRAD ? "k_sorted_atoms_grad" : "k_sorted_atoms", st, 0.0, true, a.events);
-        k_sorted_atoms<GRAD><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag, s.rec,
-                                                                    s.shortv, s.count, ctr, s.cursor);
-    }
-    {
-        ::rs::KernelTimer kt__("k_key_scan", st, 0.0, false, a.events);
-        launch_key_scan(n * kSub, s.count, s.bsum, s.off, st);
-        note_launch(2);  // three kernels under one timer
-    }
-    {
-        ::rs::KernelTimer kt__("k_sorted_scatter", st, 0.0, false, a.events);
-        k_sorted_scatter<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, kSub, s.rec, s.off, s.srt);
+        k_sorted_atoms<GRAD><<<grid, 32 * kWarpsPerBlock, 0, st>>>(a.prot, a.lig, s.ps, pc, s.pflag, s.kr, s.off,
+                                                                    s.srt, s.shortv, ctr, s.cursor);
     }
     RS_TRY_CUDA(cudaGetLastError());
-    return dispatch_sorted_wform<GRAD>(a, s, M, st);
+    return dispatch_sorted_wform<GRAD>(a, s, M, pc_call * L, st);
 }
 
 template <bool GRAD>
@@ -377,7 +410,7 @@ rs_status run_sorted(const EvalLaunch& a, cudaStream_t st) {
             k_sorted_poses<<<(pc + 127) / 128, 128, 0, st>>>(a.prot, a.rot, a.trans, p0, pc, GRAD, a.skip, s.ps,
                                                               s.pflag);
         }
-        RS_TRY(sorted_chunk_contrib<GRAD>(a, s, pc, st));
+        RS_TRY(sorted_chunk_contrib<GRAD>(a, s, pc, std::min<long long>(PC, a.P), st));
         {
             ::rs::KernelTimer kt__("k_sorted_reduce", st, 0.0, false, a.events);
             k_sorted_reduce<NC><<<(unsigned)((pc * 32LL + 255) / 256), 256, 0, st>>>(
@@ -505,7 +538,8 @@ __global__ void k_fd_reduce(const PoseSetup* __restrict__ ps, int pc, LigandView
 }  // namespace
 
 long long sorted_chunk_poses(size_t ws_bytes, int L, int n, bool grad) {
-    long long lo = 0, hi = std::max<long long>(1, (long long)(ws_bytes / ((size_t)L * 96 + 256)) + 1);
+    // upper bound: an atom takes at least its 48-byte record
+    long long lo = 0, hi = std::max<long long>(1, (long long)(ws_bytes / ((size_t)L * sizeof(AtomRec))) + 1);
     // largest PC whose carve fits (chunk_bytes is increasing in PC)
     while (lo < hi) {
         long long mid = (lo + hi + 1) / 2;
@@ -562,7 +596,7 @@ rs_status launch_sorted_fd(const EvalLaunch& a, double h, double r0, void* vbuf,
             k_sorted_poses<<<(pv + 127) / 128, 128, 0, st>>>(a.prot, vrot, vtrans, 0, pv, true, nullptr, s.ps,
                                                               s.pflag);
         }
-        RS_TRY(sorted_chunk_contrib<false>(a, s, pv, st));
+        RS_TRY(sorted_chunk_contrib<false>(a, s, pv, 4 * std::min<long long>(PC, a.P), st));
         {
             ::rs::KernelTimer kt__("k_fd_reduce", st, 0.0, false, a.events);
             k_fd_reduce<<<(unsigned)((pc * 32LL + 255) / 256), 256, 0, st>>>(s.ps, pc, a.lig, p0, s.contrib,
