@@ -53,3 +53,23 @@ def test_fullsize_gradients_sample(full):
     # the gradient call's energies equal the energy call's for the same rotations
     assert np.allclose(Eg.cpu().numpy()[idx], ref_e["E"][idx],
                        rtol=0, atol=1e-5 * np.abs(ref_e["E"][idx]).max())
+
+
+def test_two_chunk_call_is_order_independent(full):
+    """A call larger than one chunk (2^23 pose-atoms): 167 772 + 1000 poses, the second
+    chunk far below the tensor-core form's fill threshold on its own.  Every chunk of a
+    call takes the same W-form kernel, so permuting the poses permutes the energies bit
+    for bit; the small chunk's poses also match the oracle."""
+    lib, ctx, h, w, rv, m, ref, T = full
+    from bench import workload
+    P = (1 << 23) // w.L + 1000
+    w2, _ = workload(P)
+    E1, f1 = lib.rs_energy_poses(ctx.handle, h, T(w2.lig_xyz), T(w2.lig_q), T(w2.quat), T(w2.trans))
+    perm = np.random.default_rng(11).permutation(P)
+    E2, f2 = lib.rs_energy_poses(ctx.handle, h, T(w2.lig_xyz), T(w2.lig_q), T(w2.quat[perm]), T(w2.trans[perm]))
+    E1, f1, E2, f2 = (x.cpu().numpy() for x in (E1, f1, E2, f2))
+    assert np.array_equal(E2, E1[perm]) and np.array_equal(f2, f1[perm])
+    idx = np.arange(P - 300, P)  # poses of the second chunk of the first call
+    sub = O.pose_energies(m, w2.lig_xyz, w2.lig_q, w2.quat[idx], w2.trans[idx])
+    assert_energies(E1[idx], sub)
+    assert_flags(f1[idx], sub)
