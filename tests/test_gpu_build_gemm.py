@@ -112,3 +112,44 @@ def test_rank_deficient_gram_builds_in_both_modes():
             assert_flags(np.asarray(f), ref)
     finally:
         ctx.close()
+
+
+def test_narrow_gaussians_take_direct_values_in_the_projection():
+    """A coarse grid (h = 0.5 A) and a small sigma (0.4 A): the two narrowest long-range
+    terms have t^2 h^2 > 8, where the projection evaluates every Gaussian value by the
+    pair exponential instead of the ratio recurrence.  Both build GEMMs against the
+    oracle's RHOSVD."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_26611_gb300 import lib
+    rng = np.random.default_rng(65)
+    prot, r_p = W.sphere_lattice(rng, 60)
+    zq = W.mixed_charges(rng, 60, 0.3, 0.08)
+    lig = W.ball_uniform(rng, 12, 2.0)
+    lq = rng.normal(0.0, 0.3, 12)
+    P = 400
+    quat = W.shoemake_quaternions(rng, P)
+    trans = W.shell_translations(rng, P, r_p, r_p + 4.0)
+    n, b, sigma, Rl, cap = 65, 16.0, 0.4, 14, 8
+    tab = O.sinc_table(b, sigma, Rl)
+    t_long = np.asarray(tab.t)[np.asarray(tab.is_long)]
+    assert (t_long ** 2 * (2 * b / (n - 1)) ** 2 > 8.0).sum() >= 2
+    m = O.build_model(prot, zq, n, b, sigma, Rl, tucker_cap=cap)
+    ref = O.pose_energies(m, lig, lq, quat, trans)
+    prm = lib.rs_params_default(n=n, b=b, sigma=sigma, R_l=Rl, tucker_cap=cap)
+    ctx = lib.Context(0)
+    try:
+        for mode in (1, 0):
+            old = lib.rs_set_build_gemm_kernel(mode)
+            try:
+                pr = lib.Protein(ctx, prot, zq, prm)
+            finally:
+                lib.rs_set_build_gemm_kernel(old)
+            E, f = pr.energies(lig, lq, quat, trans)
+            assert list(pr.info["rank"]) == [v.shape[1] for v in m.V]
+            pr.close()
+            assert_energies(np.asarray(E), ref)
+            assert_flags(np.asarray(f), ref)
+    finally:
+        ctx.close()
