@@ -228,6 +228,35 @@ def test_clash_boundary_decided_in_fp64(L, small):
     assert f[0] & 1 and not (f[1] & 1)
 
 
+def test_edge_cases_through_the_cell_grouped_path(L, small_tucker):
+    """A single-atom ligand in 2^17 + 10 poses, so the call takes the cell-grouped path
+    with the tensor-core W form (sort keys, records at their sorted positions): random
+    placements plus atoms outside the grid beyond each kind of face, far away, just
+    inside a face, on a face, and at sigma (1 +- 1e-9) and (1 +- 1e-6) from the outermost
+    protein atom; every flag and energy against the oracle."""
+    w, m, prot, _ = small_tucker
+    rng = np.random.default_rng(17)
+    P0 = (1 << 17) + 10
+    trans = rng.uniform(-0.9 * w.b, 0.9 * w.b, (P0, 3))
+    a = w.prot_xyz[np.argmax(np.linalg.norm(w.prot_xyz, axis=1))]
+    d = a / np.linalg.norm(a)
+    edge = [[w.b + 8.0, 0.0, 0.0], [0.0, -(w.b + 8.0), 0.0], [0.0, 0.0, w.b + 1e-3], [1e6, 0.0, 0.0],
+            [w.b - 1e-3, 0.5, 0.5], [-w.b, 0.0, 0.0]]
+    edge += [a + d * w.sigma * (1 + e) for e in (-1e-9, 1e-9, -1e-6, 1e-6)]
+    idx = rng.choice(P0, len(edge), replace=False)
+    trans[idx] = np.asarray(edge)
+    quat = W.shoemake_quaternions(rng, P0)
+    lig, q = np.zeros((1, 3)), np.array([0.8])
+    ref = O.pose_energies(m, lig, q, quat, trans)
+    E, f = prot.energies(lig, q, quat, trans)
+    assert_flags(f, ref)
+    assert_energies(E, ref)
+    for i in idx[:4]:
+        assert f[i] & L.RS_FLAG_OUT_OF_GRID
+    assert not (f[idx[4]] & L.RS_FLAG_OUT_OF_GRID)
+    assert f[idx[6]] & 1 and not (f[idx[7]] & 1)
+
+
 def test_invalid_arguments(L, ctx, small):
     w, m, prot, _ = small
     with pytest.raises(L.RSError) as ei:
