@@ -1446,7 +1446,7 @@ __global__ void __launch_bounds__(160, 2) k_project_tc(int n, double b, double h
             const bool glast = j == nch - 1 || c % kPG == kPG - 1;
             uint8_t* sA = smem_p + s * Sh::A_BYTES;
             if (j >= kPS) ok = tc::mbar_wait_bounded(mmb + s, ph ^ 1u);  // stage s free
-            if (__any_sync(0xffffffffu, !ok) || *abort_flag) {
+            if (__any_sync(0xffffffffu, !ok || *abort_flag != 0)) {  // one decision per warp
                 ok = false;
                 break;
             }
