@@ -47,7 +47,7 @@ __all__ = [
     "short_range", "min_distances", "energies_from_atoms", "pose_energies", "pose_gradients",
     "coulomb_energies", "coulomb_gradients", "pgd_step", "feasible_topk", "fd_forces",
     "ppiem_directions", "contact_offsets", "ppiem_scan", "box_cells", "local_box_model",
-    "complex_energies",
+    "complex_energies", "add_and_compress",
     "FLAG_CLASH", "FLAG_OUT_OF_GRID", "tolerance_scale",
 ]
 
@@ -504,6 +504,48 @@ def pose_energies(model: RSModel, lig_xyz, lig_q, quat, trans, chunk: int = 2048
         r = energies_from_atoms(model, x, lig_q)
         for k in out:
             out[k][sl] = r[k]
+    return out
+
+
+def add_and_compress(models, cap: int, eps_r: float = 1e-7) -> RSModel:
+    """Add-and-compress (Sec. 3.4, Algorithm TEP step 4; Sec. 5.1, the complex of
+    Eq. EnergySum_Mcomplex): the long-range Tucker tensors of several molecules on one
+    grid, T = sum_p beta_p x_1 V1_p x_2 V2_p x_3 V3_p, summed and re-truncated.  Per
+    axis the factor matrices side by side are orthonormalised, [V_l^(1) ... V_l^(P)] =
+    Q_l R_l (thin QR), so that T = C x_l Q_l exactly with
+    C = sum_p beta_p x_l R_l[:, columns of p]; an HOSVD of the small core C keeps per
+    axis the leading left singular vectors of its mode unfolding (r = #{s_i > eps_r
+    s_1}, at most cap): V_l = Q_l U_l, core = C x_l U_l^T.  The short range is that of
+    the union of the molecules' atoms (their sinc table is shared)."""
+    m0 = models[0]
+    for m in models:
+        assert m.kind == "tucker" and m.n == m0.n and m.b == m0.b and m.sigma == m0.sigma
+        assert np.array_equal(m.table.t, m0.table.t) and np.array_equal(m.table.a, m0.table.a)
+    Q, Rf, cols = [], [], []
+    for ax in range(3):
+        A = np.concatenate([m.V[ax] for m in models], axis=1)
+        q, r = np.linalg.qr(A)
+        Q.append(q)
+        Rf.append(r)
+        cols.append(np.cumsum([0] + [m.V[ax].shape[1] for m in models]))
+    C = np.zeros(tuple(q.shape[1] for q in Q))
+    for p, m in enumerate(models):
+        Rp = [Rf[ax][:, cols[ax][p]:cols[ax][p + 1]] for ax in range(3)]
+        C += np.einsum("abc,ia,jb,kc->ijk", m.beta, Rp[0], Rp[1], Rp[2], optimize=True)
+    U, svals = [], []
+    for ax in range(3):
+        M = np.moveaxis(C, ax, 0).reshape(C.shape[ax], -1)
+        Ul, sv, _ = np.linalg.svd(M, full_matrices=False)
+        r = int(np.count_nonzero(sv > eps_r * sv[0])) if sv[0] > 0 else 0
+        r = max(1, min(r, cap))
+        U.append(Ul[:, :r])
+        svals.append(sv)
+    core = np.einsum("ijk,ia,jb,kc->abc", C, U[0], U[1], U[2], optimize=True)
+    V = [Q[ax] @ U[ax] for ax in range(3)]
+    xyz = np.concatenate([m.prot_xyz for m in models], axis=0)
+    q = np.concatenate([m.prot_q for m in models], axis=0)
+    out = RSModel("tucker", m0.n, m0.b, m0.sigma, m0.table, xyz, q, V=V, beta=core, svals=svals)
+    out.trunc_bound = math.sqrt(sum(float((sv[U[ax].shape[1]:] ** 2).sum()) for ax, sv in enumerate(svals)))
     return out
 
 
