@@ -904,7 +904,8 @@ def run_complex(args):
     """Sec. 5.1, Eq. EnergySum_Mcomplex: the step's protein split into two molecules
     (by the sign of x), each built on its own; energies of P poses against the complex
     (one pose pass per molecule, summed on the device) timed beside the single molecule
-    built on the union.  Then the Galerkin factors (Eq. galten) against collocation
+    built on the union and beside the add-and-compressed sum of the two Tucker tensors
+    (TEP step 4: one pose pass against one handle).  Then the Galerkin factors (Eq. galten) against collocation
     on the small canonical workload: energies/s of both and their difference."""
     import torch
     import workloads as W
@@ -941,7 +942,19 @@ def run_complex(args):
     ms_c, (Ec, Fc), clocks, launches = timed(
         lambda: lib.rs_energy_poses_complex(ctx.handle, [m.handle for m in mols], lx, lq, tq, tt))
     ms_u, (Eu, Fu), _, _ = timed(lambda: union.energies(lx, lq, tq, tt))
+    # add-and-compress (TEP step 4): the two molecules' Tucker tensors summed and
+    # re-truncated into one handle (host wall clock of the whole call: QR and HOSVD
+    # on the host, cardinal basis, tables and the union's short range on the device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    acp = lib.Protein.add_compress(ctx, mols, w.tucker_cap)
+    torch.cuda.synchronize()
+    ms_build_ac = (time.perf_counter() - t0) * 1e3
+    ms_a, (Ea, Fa), _, _ = timed(lambda: acp.energies(lx, lq, tq, tt))
+    ac_info = acp.info
+    acp.close()
     Ec, Eu, Fc, Fu = Ec.cpu().numpy(), Eu.cpu().numpy(), Fc.cpu().numpy(), Fu.cpu().numpy()
+    Ea, Fa = Ea.cpu().numpy(), Fa.cpu().numpy()
     scale = np.maximum(np.abs(Eu), np.median(np.abs(Eu)))
     for m in mols:
         m.close()
@@ -972,6 +985,13 @@ def run_complex(args):
             "max_rel_diff_complex_vs_union_tucker": float((np.abs(Ec - Eu) / scale).max()),
             "median_rel_diff_complex_vs_union_tucker": float(np.median(np.abs(Ec - Eu) / scale)),
             "flags_equal_complex_vs_union": bool(np.array_equal(Fc, Fu)),
+            "add_compress": {"ranks": list(ac_info["rank"]), "sv_tail": [float(x) for x in ac_info["sv_tail"]],
+                             "build_ms_wall": round(ms_build_ac, 3),
+                             "poses_per_s": round(P / (ms_a / 1e3), 3), "ms_per_step": round(ms_a, 4),
+                             "max_rel_diff_vs_complex": float((np.abs(Ea - Ec) / scale).max()),
+                             "median_rel_diff_vs_complex": float(np.median(np.abs(Ea - Ec) / scale)),
+                             "max_rel_diff_vs_union_tucker": float((np.abs(Ea - Eu) / scale).max()),
+                             "flags_equal_vs_complex": bool(np.array_equal(Fa, Fc))},
             "galerkin": {"workload": "plain_small canonical (N=200, n=257, R = 4000), 2e4 poses with centres "
                                      "within 12 A of the protein's centre",
                          "collocation_poses_per_s": round(ws.P / (res[0][0] / 1e3), 3),

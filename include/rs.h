@@ -195,6 +195,30 @@ rs_status rs_energy_poses_complex(rs_ctx* ctx, int32_t nmol, const rs_protein* c
 rs_status rs_protein_local_box(rs_ctx* ctx, rs_protein* parent, const double* lo, const double* hi,
                                double eps, rs_protein** out);
 
+/* Add-and-compress: the long-range Tucker tensors of several molecules on one grid,
+ * summed and re-truncated into one Tucker handle (Algorithm TEP, step 4, Sec. 3.4:
+ * sums of Tucker tensors re-compressed by an HOSVD of the small core; Sec. 5.1, the
+ * complex potential of Eq. EnergySum_Mcomplex as one tensor).  With T_p = beta_p x_l
+ * V_l^(p) the parts' tensors, per axis [V_l^(1) ... V_l^(count)] = Q_l R_l (thin QR,
+ * FP64 on the host), C = sum_p beta_p x_l R_l[:, columns of p], and the HOSVD of C
+ * keeps per axis r_l = #{s_i > eps_r s_1} (1 <= r_l <= tucker_cap) leading singular
+ * vectors U_l: V_l = Q_l U_l, core = C x_l U_l^T, then the cardinal basis and
+ * evaluation tables as rs_build_protein makes them.  Long-range error (Frobenius, on
+ * the grid) <= s_1 sqrt(sum over axes of sv_tail^2) (rs_protein_get_info: ranks,
+ * sv_tail and sv_gap of this HOSVD; subspace_steps 0).  The short range is that of
+ * the union of the parts' atoms.
+ *   parts: count (1..16) Tucker-reduced handles (not local-box handles) built on
+ *   this context's device with the same n, b, sigma, R_l and sinc table; the sum of
+ *   their ranks per axis <= 128 and of their atoms <= 2^22.  The parts are only read
+ *   and stay owned by the caller; *out is a new handle (free with rs_protein_free).
+ *   stream: the CUDA stream of the device work (NULL: the default stream); the call
+ *   synchronises it before returning.
+ * RS_ERR_INVALID for a NULL or mismatched part, count, tucker_cap not in [1, 32]
+ * or eps_r not in [0, 1); RS_ERR_OOM / RS_ERR_CUDA as for
+ * rs_build_protein (no handle is returned then). */
+rs_status rs_protein_add_compress(rs_ctx* ctx, const rs_protein* const* parts, int32_t count, int32_t tucker_cap,
+                                  double eps_r, void* stream, rs_protein** out);
+
 /* The paper's finite-difference force and its rigid-cluster resultants, for
  * comparison with the exact gradient of rs_energy_grad_poses.
  *   Per atom l and axis i (Eq. differ_ligand, Sec. 3.3):

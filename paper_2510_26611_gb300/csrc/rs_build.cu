@@ -184,6 +184,19 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ start, int* __res
     }
 }
 
+// The FP64 atom records (x, y, z, q) of a built protein back to flat coordinates
+// [N][3] and charges [N] (the inputs of the cell build), for the union of molecules.
+__global__ void k_split_atoms64(int N, const double4* __restrict__ atoms64, double* __restrict__ xyz,
+                                double* __restrict__ q) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double4 r = atoms64[i];
+    xyz[3 * (size_t)i] = r.x;
+    xyz[3 * (size_t)i + 1] = r.y;
+    xyz[3 * (size_t)i + 2] = r.z;
+    q[i] = r.w;
+}
+
 // Short-range candidate lists.  Fine cell c (box [lo, lo + f] per axis) lists every
 // atom whose distance to the box is at most R, visiting the coarse cells (side >= R)
 // that can hold such atoms in increasing id order, so each list is in cell-sorted
@@ -1786,6 +1799,159 @@ static rs_status build_canonical(rs_protein* P, cudaStream_t st, const double* d
     return RS_OK;
 }
 
+// The short-range terms of the protein's sinc table, the tabulated short-range sum
+// (cubic Hermite) and the decision bands of the vdW check, into P->view.
+static rs_status finish_short_range(rs_protein* P, cudaStream_t st) {
+    ProteinView& v = P->view;
+    v.n = P->n;
+    v.b = P->b;
+    v.h = P->h;
+    v.inv_h = 1.0 / P->h;
+    v.Ks = 0;
+    for (int k = 0; k < P->K; ++k)
+        if (!P->table.is_long[k]) {
+            v.ts2[v.Ks] = P->table.t[k] * P->table.t[k];
+            v.as[v.Ks] = P->table.a[k];
+            ++v.Ks;
+        }
+    double rc = P->table.r_c;
+    v.rc2 = rc * rc;
+    v.rc2_hi = (float)(rc * rc * (1.0 + 1e-4));
+    v.stab2 = nullptr;
+    v.stab_n = 0;
+    v.stab_inv_h = 0.0;
+    if (v.Ks > 0 && rc > 0) {
+        // spacing from the cubic Hermite bound |f - p| <= hs^4/384 max|f''''| with
+        // max|f''''| <= sum a_k t_k^8 (at s = 0), for 1e-10 relative to f(0)
+        double f0 = 0.0, f4 = 0.0;
+        for (int q = 0; q < v.Ks; ++q) {
+            f0 += v.as[q];
+            f4 += v.as[q] * std::pow(v.ts2[q], 4.0);
+        }
+        double hs = std::pow(384.0 * 1e-10 * f0 / std::max(f4, 1e-300), 0.25);
+        double smax = (double)v.rc2_hi * (1.0 + 1e-6);
+        int M = (int)std::ceil(smax / hs) + 2;
+        if (M > (1 << 22)) {
+            set_error("short-range table of %d entries is too large", M);
+            return RS_ERR_UNSUPPORTED;
+        }
+        float4* tab = nullptr;
+        RS_TRY(device_alloc(P, (void**)&tab, (size_t)2 * (M - 1) * sizeof(float4)));
+        {
+            ::rs::KernelTimer kt__("k_short_table", st, 0.0, false);
+            k_short_table<<<blocks_for((size_t)M), kBlock, 0, st>>>(v, M, hs, tab);
+        }
+        RS_TRY_CUDA(cudaGetLastError());
+        v.stab2 = tab;
+        v.stab_n = M;
+        v.stab_inv_h = 1.0 / hs;
+        split_host(v.stab_inv_h, v.stab_ih_h, v.stab_ih_l);
+    }
+    v.sig2 = P->sigma * P->sigma;
+    v.sig2_lo = (float)(v.sig2 * (1.0 - 1e-4));
+    v.sig2_hi = (float)(v.sig2 * (1.0 + 1e-4));
+    split_host(v.sig2, v.sig2_ph, v.sig2_pl);
+    split_host(v.rc2, v.rc2_ph, v.rc2_pl);
+    split_host(v.b, v.b_h, v.b_l);
+    split_host(v.inv_h, v.inv_h_h, v.inv_h_l);
+    return RS_OK;
+}
+
+// Cardinal (skeleton) basis of the Tucker factors V (3 x n x RP, FP64, columns >= r_ax
+// zero): pivoted Gram-Schmidt picks r rows S per axis (k_skeleton), Vs = V V[S,:]^-1
+// and Wp = V V[S,:]^T (k_skeleton_apply).  d_M, d_Ainv, d_S, d_Wp: scratch of
+// 3 n RP, 3 RP^2, 3 RS_MAX_TUCKER and 3 n RP; *d_Vs is taken from S.
+static rs_status skeleton_basis(cudaStream_t st, int n, int RP, const int* d_rax, const double* d_V, double* d_M,
+                                double* d_Ainv, int* d_S, float2* d_Wp, int* d_fail, Scratch& S, double** d_Vs) {
+    {
+        // the residual rows in shared memory when they fit beside the kernel's static arrays
+        const size_t rows_bytes = (size_t)n * RP * sizeof(float);
+        const bool rows_smem = rows_bytes <= 192 * 1024;
+        if (rows_smem)
+            RS_TRY_CUDA(cudaFuncSetAttribute(k_skeleton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_bytes));
+        ::rs::KernelTimer kt__("k_skeleton", st, 0.0, false);
+        k_skeleton<<<3, 512, rows_smem ? rows_bytes : 0, st>>>(n, RP, d_rax, d_V, d_M, d_S, d_Ainv, d_fail,
+                                                               rows_smem);
+    }
+    RS_TRY(S.get(d_Vs, (size_t)3 * n * RP));
+    {
+        ::rs::KernelTimer kt__("k_skeleton_apply", st, 0.0, false);
+        k_skeleton_apply<<<dim3(blocks_for((size_t)n * RP), 3), kBlock, 0, st>>>(
+            n, RP, d_rax, d_V, d_Ainv, d_S, *d_Vs, d_Wp);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
+    return RS_OK;
+}
+
+// The evaluation tables of a Tucker handle from its cardinal factors Vs (3 x n x RP)
+// and core beta' (RP^3), both FP64 on the device: float-pair rows of V1', V2', the
+// W form W = V3' beta'_(3)^T with its tensor-core B image, the core in FP32, and FP64
+// copies of Vs and beta' kept with the handle (for add-and-compress).  Checks the
+// skeleton's failure flags (one stream synchronisation) and sets P->view.
+static rs_status tucker_tables(rs_protein* P, cudaStream_t st, int n, int RP, const double* d_Vs, const double* d_B,
+                               const int* d_fail) {
+    const size_t blen = (size_t)RP * RP * RP;
+    float *core, *vt0, *vt1, *wt, *wsc;
+    uint16_t* wtc;
+    double *fac64, *core64;
+    size_t vplane = (size_t)n * RP, wplane = (size_t)n * RP * RP;
+    {
+        DeviceArena ar;
+        ar.add(&core, blen);
+        ar.add(&vt0, 4 * vplane);
+        ar.add(&vt1, 4 * vplane);
+        ar.add(&wt, 4 * wplane);
+        ar.add(&wtc, tc_bimage_bytes(n, RP) / sizeof(uint16_t));
+        ar.add(&wsc, tc_bscale_bytes(n, RP) / sizeof(float));
+        ar.add(&fac64, 3 * vplane);
+        ar.add(&core64, blen);
+        RS_TRY(ar.alloc(P));
+    }
+    {
+        ::rs::KernelTimer kt__("k_to_float", st, 0.0, false);
+        k_to_float<<<blocks_for(blen), kBlock, 0, st>>>(blen, d_B, core);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
+    RS_TRY_CUDA(cudaMemcpyAsync(fac64, d_Vs, 3 * vplane * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    RS_TRY_CUDA(cudaMemcpyAsync(core64, d_B, blen * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int fail[3];
+    RS_TRY_CUDA(cudaMemcpyAsync(fail, d_fail, sizeof(fail), cudaMemcpyDeviceToHost, st));
+    RS_TRY_CUDA(cudaStreamSynchronize(st));
+    if (fail[0] || fail[1] || fail[2]) {
+        set_error("skeleton selection failed (rank-deficient factor basis)");
+        return RS_ERR_CUDA;
+    }
+    // evaluation tables: float-pair rows of V1', V2' and of W = V3' core_(3)^T
+    {
+        ::rs::KernelTimer kt__("k_pair_rows", st, 0.0, false);
+        k_pair_rows<<<dim3(blocks_for(vplane), 2), kBlock, 0, st>>>(n, RP, d_Vs, vt0, vt1);
+    }
+    {
+        ::rs::KernelTimer kt__("k_wtable", st, 0.0, false);
+        k_wtable<<<dim3(blocks_for((size_t)RP * RP), n), kBlock, 0, st>>>(n, RP, d_Vs + 2 * vplane, d_B, wt);
+    }
+    RS_TRY_CUDA(cudaGetLastError());
+    RS_TRY(tc_build_bimage(n, RP, wt, wtc, wsc, st));
+    RS_TRY_CUDA(cudaStreamSynchronize(st));
+    ProteinView& v = P->view;
+    v.kind = 1;
+    v.Wtc = wtc;
+    v.Wsc = wsc;
+    v.ld = RP;
+    v.R = RP;
+    for (int a = 0; a < 3; ++a) v.F[a] = nullptr;
+    for (int k = 0; k < 4; ++k) {
+        v.Wt[k] = wt + k * wplane;
+        v.Vt[0][k] = vt0 + k * vplane;
+        v.Vt[1][k] = vt1 + k * vplane;
+    }
+    v.core = core;
+    P->fac64 = fac64;
+    P->core64 = core64;
+    P->kind = 1;
+    return RS_OK;
+}
+
 static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xyz,
                               const double* d_q, const double* d_tl, const double* d_al,
                               const std::vector<double>& tl_host, const std::vector<double>& al_host,
@@ -2117,24 +2283,8 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         k_ritz_vectors<<<dim3(blocks_for((size_t)n * RP), 3), kBlock, 0, st>>>(n, p, RP, d_rax, d_Q, d_W, d_V);
     }
     // 3. skeleton basis
-    {
-        // the residual rows in shared memory when they fit beside the kernel's static arrays
-        const size_t rows_bytes = (size_t)n * RP * sizeof(float);
-        const bool rows_smem = rows_bytes <= 192 * 1024;
-        if (rows_smem)
-            RS_TRY_CUDA(cudaFuncSetAttribute(k_skeleton, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_bytes));
-        ::rs::KernelTimer kt__("k_skeleton", st, 0.0, false);
-        k_skeleton<<<3, 512, rows_smem ? rows_bytes : 0, st>>>(n, RP, d_rax, d_V, d_M, d_S, d_Ainv, d_fail,
-                                                               rows_smem);
-    }
     double* d_Vs;
-    RS_TRY(S.get(&d_Vs, (size_t)3 * n * RP));
-    {
-        ::rs::KernelTimer kt__("k_skeleton_apply", st, 0.0, false);
-        k_skeleton_apply<<<dim3(blocks_for((size_t)n * RP), 3), kBlock, 0, st>>>(
-            n, RP, d_rax, d_V, d_Ainv, d_S, d_Vs, d_Wp);
-    }
-    RS_TRY_CUDA(cudaGetLastError());
+    RS_TRY(skeleton_basis(st, n, RP, d_rax, d_V, d_M, d_Ainv, d_S, d_Wp, d_fail, S, &d_Vs));
     // 4. projections and core
     const int Rtot = N * Rl;
     // columns per k_core CTA: about 152 CTAs (one wave of one CTA per SM on GB300; the
@@ -2198,59 +2348,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         ::rs::KernelTimer kt__("k_sum_chunks", st, 0.0, false);
         k_sum_chunks<<<blocks_for(blen), kBlock, 0, st>>>(blen, nchunk, d_Bp, d_B, nullptr);
     }
-    // the protein's evaluation tables, in one allocation: core, float-pair rows of V1'
-    // and V2', W = V3' core_(3)^T, and its tensor-core B image with scales
-    float *core, *vt0, *vt1, *wt, *wsc;
-    uint16_t* wtc;
-    size_t vplane = (size_t)n * RP, wplane = (size_t)n * RP * RP;
-    {
-        DeviceArena ar;
-        ar.add(&core, blen);
-        ar.add(&vt0, 4 * vplane);
-        ar.add(&vt1, 4 * vplane);
-        ar.add(&wt, 4 * wplane);
-        ar.add(&wtc, tc_bimage_bytes(n, RP) / sizeof(uint16_t));
-        ar.add(&wsc, tc_bscale_bytes(n, RP) / sizeof(float));
-        RS_TRY(ar.alloc(P));
-    }
-    {
-        ::rs::KernelTimer kt__("k_to_float", st, 0.0, false);
-        k_to_float<<<blocks_for(blen), kBlock, 0, st>>>(blen, d_B, core);
-    }
-    RS_TRY_CUDA(cudaGetLastError());
-    RS_TRY_CUDA(cudaMemcpyAsync(fail, d_fail, sizeof(fail), cudaMemcpyDeviceToHost, st));
-    RS_TRY_CUDA(cudaStreamSynchronize(st));
-    if (fail[0] || fail[1] || fail[2]) {
-        set_error("skeleton selection failed (rank-deficient factor basis)");
-        return RS_ERR_CUDA;
-    }
-    // 5. evaluation tables: float-pair rows of V1', V2' and of W = V3' core_(3)^T
-    {
-        ::rs::KernelTimer kt__("k_pair_rows", st, 0.0, false);
-        k_pair_rows<<<dim3(blocks_for(vplane), 2), kBlock, 0, st>>>(n, RP, d_Vs, vt0, vt1);
-    }
-    {
-        ::rs::KernelTimer kt__("k_wtable", st, 0.0, false);
-        k_wtable<<<dim3(blocks_for((size_t)RP * RP), n), kBlock, 0, st>>>(n, RP, d_Vs + 2 * vplane, d_B, wt);
-    }
-    RS_TRY_CUDA(cudaGetLastError());
-    RS_TRY(tc_build_bimage(n, RP, wt, wtc, wsc, st));
-    RS_TRY_CUDA(cudaStreamSynchronize(st));
-    ProteinView& v = P->view;
-    v.kind = 1;
-    v.Wtc = wtc;
-    v.Wsc = wsc;
-    v.ld = RP;
-    v.R = RP;
-    for (int a = 0; a < 3; ++a) v.F[a] = nullptr;
-    for (int k = 0; k < 4; ++k) {
-        v.Wt[k] = wt + k * wplane;
-        v.Vt[0][k] = vt0 + k * vplane;
-        v.Vt[1][k] = vt1 + k * vplane;
-    }
-    v.core = core;
-    P->kind = 1;
-    return RS_OK;
+    return tucker_tables(P, st, n, RP, d_Vs, d_B, d_fail);
 }
 
 }  // namespace rs
@@ -2381,65 +2479,327 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
     }
     if (s != RS_OK) return fail_out(s);
 
-    // short-range terms and decision bands
-    ProteinView& v = P->view;
-    v.n = P->n;
-    v.b = P->b;
-    v.h = P->h;
-    v.inv_h = 1.0 / P->h;
-    v.Ks = 0;
-    for (int k = 0; k < P->K; ++k)
-        if (!P->table.is_long[k]) {
-            v.ts2[v.Ks] = P->table.t[k] * P->table.t[k];
-            v.as[v.Ks] = P->table.a[k];
-            ++v.Ks;
-        }
-    double rc = P->table.r_c;
-    v.rc2 = rc * rc;
-    v.rc2_hi = (float)(rc * rc * (1.0 + 1e-4));
-    v.stab2 = nullptr;
-    v.stab_n = 0;
-    v.stab_inv_h = 0.0;
-    if (v.Ks > 0 && rc > 0) {
-        // spacing from the cubic Hermite bound |f - p| <= hs^4/384 max|f''''| with
-        // max|f''''| <= sum a_k t_k^8 (at s = 0), for 1e-10 relative to f(0)
-        double f0 = 0.0, f4 = 0.0;
-        for (int q = 0; q < v.Ks; ++q) {
-            f0 += v.as[q];
-            f4 += v.as[q] * std::pow(v.ts2[q], 4.0);
-        }
-        double hs = std::pow(384.0 * 1e-10 * f0 / std::max(f4, 1e-300), 0.25);
-        double smax = (double)v.rc2_hi * (1.0 + 1e-6);
-        int M = (int)std::ceil(smax / hs) + 2;
-        if (M > (1 << 22)) {
-            set_error("rs_build_protein: short-range table of %d entries is too large", M);
-            return fail_out(RS_ERR_UNSUPPORTED);
-        }
-        float4* tab = nullptr;
-        if ((s = device_alloc(P, (void**)&tab, (size_t)2 * (M - 1) * sizeof(float4))) != RS_OK)
-            return fail_out(s);
-        {
-            ::rs::KernelTimer kt__("k_short_table", st, 0.0, false);
-            k_short_table<<<blocks_for((size_t)M), kBlock, 0, st>>>(v, M, hs, tab);
-        }
-        if (cudaGetLastError() != cudaSuccess) {
-            set_error("rs_build_protein: short-range table launch failed");
-            return fail_out(RS_ERR_CUDA);
-        }
-        v.stab2 = tab;
-        v.stab_n = M;
-        v.stab_inv_h = 1.0 / hs;
-        split_host(v.stab_inv_h, v.stab_ih_h, v.stab_ih_l);
-    }
-    v.sig2 = P->sigma * P->sigma;
-    v.sig2_lo = (float)(v.sig2 * (1.0 - 1e-4));
-    v.sig2_hi = (float)(v.sig2 * (1.0 + 1e-4));
-    split_host(v.sig2, v.sig2_ph, v.sig2_pl);
-    split_host(v.rc2, v.rc2_ph, v.rc2_pl);
-    split_host(v.b, v.b_h, v.b_l);
-    split_host(v.inv_h, v.inv_h_h, v.inv_h_l);
+    if ((s = finish_short_range(P, st)) != RS_OK) return fail_out(s);
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("rs_build_protein: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail_out(RS_ERR_CUDA);
+    }
+    *out = P;
+    return RS_OK;
+}
+
+namespace {
+
+// Thin QR of the n x k matrix A (column j at A + j n) by classical Gram-Schmidt run
+// twice per column, the coefficients of both passes summed into R (k x k, upper
+// triangular, row-major); Q overwrites A.  A column with nothing left after the two
+// passes becomes zero with R[j][j] = 0.
+void cgs2_qr(int n, int k, double* A, double* R) {
+    std::fill(R, R + (size_t)k * k, 0.0);
+    std::vector<double> c(k);
+    for (int j = 0; j < k; ++j) {
+        double* aj = A + (size_t)j * n;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = 0; i < j; ++i) {
+                const double* qi = A + (size_t)i * n;
+                double d = 0.0;
+                for (int t = 0; t < n; ++t) d += qi[t] * aj[t];
+                c[i] = d;
+            }
+            for (int i = 0; i < j; ++i) {
+                const double* qi = A + (size_t)i * n;
+                for (int t = 0; t < n; ++t) aj[t] -= c[i] * qi[t];
+                R[(size_t)i * k + j] += c[i];
+            }
+        }
+        double nrm = 0.0;
+        for (int t = 0; t < n; ++t) nrm += aj[t] * aj[t];
+        nrm = std::sqrt(nrm);
+        R[(size_t)j * k + j] = nrm;
+        if (nrm > 0.0)
+            for (int t = 0; t < n; ++t) aj[t] /= nrm;
+    }
+}
+
+// Mode product of a d0 x d1 x d2 tensor T (row-major) with M (m x d_ax, row stride
+// ldm) along axis ax: out has d_ax replaced by m, out[.., i, ..] = sum_a M[i][a] T[.., a, ..].
+std::vector<double> mode_product(const std::vector<double>& T, const int d[3], int ax, const double* M, int m,
+                                 int ldm, int dout[3]) {
+    for (int a = 0; a < 3; ++a) dout[a] = d[a];
+    dout[ax] = m;
+    std::vector<double> out((size_t)dout[0] * dout[1] * dout[2], 0.0);
+    for (int x = 0; x < d[0]; ++x)
+        for (int y = 0; y < d[1]; ++y)
+            for (int z = 0; z < d[2]; ++z) {
+                const double v = T[((size_t)x * d[1] + y) * d[2] + z];
+                if (v == 0.0) continue;
+                const int a = ax == 0 ? x : ax == 1 ? y : z;
+                for (int i = 0; i < m; ++i) {
+                    const int ox = ax == 0 ? i : x, oy = ax == 1 ? i : y, oz = ax == 2 ? i : z;
+                    out[((size_t)ox * dout[1] + oy) * dout[2] + oz] += M[(size_t)i * ldm + a] * v;
+                }
+            }
+    return out;
+}
+
+}  // namespace
+
+extern "C" rs_status rs_protein_add_compress(rs_ctx* ctx, const rs_protein* const* parts, int32_t count,
+                                             int32_t tucker_cap, double eps_r, void* stream, rs_protein** out) {
+    using namespace rs;
+    clear_error();
+    RS_CHECK_ARG(ctx && parts && out, "rs_protein_add_compress: NULL argument");
+    *out = nullptr;
+    RS_CHECK_ARG(count >= 1 && count <= 16, "rs_protein_add_compress: count=%d out of range [1, 16]", count);
+    RS_CHECK_ARG(tucker_cap >= 1 && tucker_cap <= RS_MAX_TUCKER,
+                 "rs_protein_add_compress: tucker_cap=%d out of range [1, %d]", tucker_cap, RS_MAX_TUCKER);
+    RS_CHECK_ARG(std::isfinite(eps_r) && eps_r >= 0.0 && eps_r < 1.0,
+                 "rs_protein_add_compress: eps_r=%g not in [0, 1)", eps_r);
+    const rs_protein* p0 = parts[0];
+    int ksum[3] = {0, 0, 0};
+    long long Ntot = 0;
+    for (int p = 0; p < count; ++p) {
+        const rs_protein* M = parts[p];
+        RS_CHECK_ARG(M, "rs_protein_add_compress: parts[%d] is NULL", p);
+        RS_CHECK_ARG(M->kind == 1 && M->view.kind == 1 && M->fac64 && M->core64 && !M->view.box,
+                     "rs_protein_add_compress: parts[%d] is not a Tucker-reduced protein", p);
+        RS_CHECK_ARG(M->device == ctx->device, "rs_protein_add_compress: parts[%d] is on another device", p);
+        RS_CHECK_ARG(M->n == p0->n && M->b == p0->b && M->sigma == p0->sigma && M->R_l == p0->R_l &&
+                         M->table.t == p0->table.t && M->table.a == p0->table.a &&
+                         M->table.is_long == p0->table.is_long && M->table.r_c == p0->table.r_c,
+                     "rs_protein_add_compress: parts[%d] has another grid or sinc table than parts[0]", p);
+        for (int a = 0; a < 3; ++a) ksum[a] += M->rank[a];
+        Ntot += M->N;
+    }
+    for (int a = 0; a < 3; ++a)
+        RS_CHECK_ARG(ksum[a] <= 128, "rs_protein_add_compress: the parts' ranks on axis %d sum to %d (at most 128)",
+                     a, ksum[a]);
+    RS_CHECK_ARG(Ntot <= (1 << 22), "rs_protein_add_compress: %lld atoms in the union (at most 2^22)", Ntot);
+    RS_TRY_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = p0->n;
+    const int N = (int)Ntot;
+
+    rs_protein* P = new rs_protein();
+    P->device = ctx->device;
+    P->N = N;
+    P->n = n;
+    P->b = p0->b;
+    P->h = p0->h;
+    P->sigma = p0->sigma;
+    P->R_l = p0->R_l;
+    P->table = p0->table;
+    P->K = p0->K;
+    auto fail_out = [&](rs_status s) {
+        rs_protein_free(P);
+        return s;
+    };
+    Scratch S(ctx);
+    rs_status s;
+
+    // the parts' FP64 factors and cores on the host
+    std::vector<std::vector<double>> fac(count), core(count);
+    for (int p = 0; p < count; ++p) {
+        const int R = parts[p]->view.R;
+        fac[p].resize((size_t)3 * n * R);
+        core[p].resize((size_t)R * R * R);
+        if (cudaMemcpyAsync(fac[p].data(), parts[p]->fac64, fac[p].size() * sizeof(double), cudaMemcpyDeviceToHost,
+                            st) != cudaSuccess ||
+            cudaMemcpyAsync(core[p].data(), parts[p]->core64, core[p].size() * sizeof(double),
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            set_error("rs_protein_add_compress: factor download failed");
+            return fail_out(RS_ERR_CUDA);
+        }
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("rs_protein_add_compress: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail_out(RS_ERR_CUDA);
+    }
+
+    // 1. per axis, [V^(1) ... V^(count)] = Q R (thin QR)
+    std::vector<double> Q[3], Rf[3];
+    for (int a = 0; a < 3; ++a) {
+        const int k = ksum[a];
+        Q[a].assign((size_t)k * n, 0.0);
+        Rf[a].resize((size_t)k * k);
+        int col = 0;
+        for (int p = 0; p < count; ++p) {
+            const int R = parts[p]->view.R;
+            const double* Va = fac[p].data() + (size_t)a * n * R;
+            for (int c = 0; c < parts[p]->rank[a]; ++c, ++col)
+                for (int i = 0; i < n; ++i) Q[a][(size_t)col * n + i] = Va[(size_t)i * R + c];
+        }
+        cgs2_qr(n, k, Q[a].data(), Rf[a].data());
+    }
+    // 2. the core in the orthonormal bases: C = sum_p beta_p x_l R_l[:, columns of p]
+    std::vector<double> C((size_t)ksum[0] * ksum[1] * ksum[2], 0.0);
+    {
+        int off[3] = {0, 0, 0};
+        for (int p = 0; p < count; ++p) {
+            const int R = parts[p]->view.R;
+            int d[3] = {parts[p]->rank[0], parts[p]->rank[1], parts[p]->rank[2]};
+            std::vector<double> T((size_t)d[0] * d[1] * d[2]);
+            for (int x = 0; x < d[0]; ++x)
+                for (int y = 0; y < d[1]; ++y)
+                    for (int z = 0; z < d[2]; ++z)
+                        T[((size_t)x * d[1] + y) * d[2] + z] = core[p][((size_t)x * R + y) * R + z];
+            for (int a = 0; a < 3; ++a) {
+                int dn[3];
+                T = mode_product(T, d, a, Rf[a].data() + off[a], ksum[a], ksum[a], dn);
+                for (int e = 0; e < 3; ++e) d[e] = dn[e];
+            }
+            for (size_t e = 0; e < C.size(); ++e) C[e] += T[e];
+            for (int a = 0; a < 3; ++a) off[a] += parts[p]->rank[a];
+        }
+    }
+    // 3. HOSVD of C: the leading eigenvectors of each mode unfolding's Gram matrix
+    std::vector<double> U[3];
+    int r_ax[3], rmax = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int k = ksum[a];
+        std::vector<double> G((size_t)k * k, 0.0), lam(k), W((size_t)k * k);
+        const int d1 = a == 0 ? ksum[1] : ksum[0], d2 = a == 2 ? ksum[1] : ksum[2];
+        auto at = [&](int i, int u, int v) -> double {
+            // element of C with index i on axis a and (u, v) on the other two axes
+            if (a == 0) return C[((size_t)i * ksum[1] + u) * ksum[2] + v];
+            if (a == 1) return C[((size_t)u * ksum[1] + i) * ksum[2] + v];
+            return C[((size_t)u * ksum[1] + v) * ksum[2] + i];
+        };
+        std::vector<double> rows((size_t)k * d1 * d2);
+        for (int i = 0; i < k; ++i)
+            for (int u = 0; u < d1; ++u)
+                for (int v = 0; v < d2; ++v) rows[((size_t)i * d1 + u) * d2 + v] = at(i, u, v);
+        const size_t len = (size_t)d1 * d2;
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double g = 0.0;
+                const double* ri = rows.data() + (size_t)i * len;
+                const double* rj = rows.data() + (size_t)j * len;
+                for (size_t e = 0; e < len; ++e) g += ri[e] * rj[e];
+                G[(size_t)i * k + j] = G[(size_t)j * k + i] = g;
+            }
+        if (!symeig_host(k, G.data(), lam.data(), W.data())) {
+            set_error("rs_protein_add_compress: eigen-decomposition of the axis-%d Gram did not converge", a);
+            return fail_out(RS_ERR_CUDA);
+        }
+        const double s1 = std::sqrt(std::max(lam[0], 0.0));
+        int r = 0;
+        for (int i = 0; i < k; ++i)
+            if (std::sqrt(std::max(lam[i], 0.0)) > eps_r * s1) ++r;
+        r = std::max(1, std::min(r, (int)tucker_cap));
+        double tail = 0.0;
+        for (int i = r; i < k; ++i) tail += std::max(lam[i], 0.0);
+        P->sv_tail[a] = std::sqrt(tail / std::max(lam[0], 1e-300));
+        P->sv_gap[a] = (r < k && lam[r] > 0) ? std::sqrt(lam[r - 1] / lam[r]) : 0.0;
+        P->rank[a] = r_ax[a] = r;
+        rmax = std::max(rmax, r);
+        // U^T (r x k, row-major) for the core's mode products
+        U[a].resize((size_t)r * k);
+        for (int c = 0; c < r; ++c)
+            for (int i = 0; i < k; ++i) U[a][(size_t)c * k + i] = W[(size_t)i * k + c];
+    }
+    // core = C x_l U_l^T, V_l = Q_l U_l (rows padded to RP columns)
+    std::vector<double> B0 = C;
+    {
+        int d[3] = {ksum[0], ksum[1], ksum[2]};
+        for (int a = 0; a < 3; ++a) {
+            int dn[3];
+            B0 = mode_product(B0, d, a, U[a].data(), r_ax[a], ksum[a], dn);
+            for (int e = 0; e < 3; ++e) d[e] = dn[e];
+        }
+    }
+    const int RP = (rmax + 3) / 4 * 4;
+    std::vector<double> hV((size_t)3 * n * RP, 0.0);
+    for (int a = 0; a < 3; ++a) {
+        const int k = ksum[a];
+        for (int i = 0; i < n; ++i)
+            for (int c = 0; c < r_ax[a]; ++c) {
+                double v = 0.0;
+                for (int j = 0; j < k; ++j) v += Q[a][(size_t)j * n + i] * U[a][(size_t)c * k + j];
+                hV[((size_t)a * n + i) * RP + c] = v;
+            }
+    }
+
+    // 4. cardinal basis of the compressed factors on the device, and the core in it:
+    //    V = Vs V[S,:], so beta' = core x_l V_l[S_l,:]
+    int* d_rax;
+    double *d_V, *d_M, *d_Ainv, *d_B;
+    float2* d_Wp;
+    int *d_S, *d_fail;
+    if ((s = S.get(&d_rax, 3)) != RS_OK || (s = S.get(&d_V, (size_t)3 * n * RP)) != RS_OK ||
+        (s = S.get(&d_M, (size_t)3 * n * RP)) != RS_OK || (s = S.get(&d_Ainv, (size_t)3 * RP * RP)) != RS_OK ||
+        (s = S.get(&d_Wp, (size_t)3 * n * RP)) != RS_OK || (s = S.get(&d_S, (size_t)3 * RS_MAX_TUCKER)) != RS_OK ||
+        (s = S.get(&d_fail, 3)) != RS_OK || (s = S.get(&d_B, (size_t)RP * RP * RP)) != RS_OK)
+        return fail_out(s);
+    if (cudaMemcpyAsync(d_rax, r_ax, sizeof(r_ax), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_V, hV.data(), hV.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(d_fail, 0, 3 * sizeof(int), st) != cudaSuccess) {
+        set_error("rs_protein_add_compress: factor upload failed");
+        return fail_out(RS_ERR_CUDA);
+    }
+    double* d_Vs;
+    if ((s = skeleton_basis(st, n, RP, d_rax, d_V, d_M, d_Ainv, d_S, d_Wp, d_fail, S, &d_Vs)) != RS_OK)
+        return fail_out(s);
+    int hS[3 * RS_MAX_TUCKER];
+    if (cudaMemcpyAsync(hS, d_S, sizeof(hS), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("rs_protein_add_compress: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail_out(RS_ERR_CUDA);
+    }
+    {
+        int d[3] = {r_ax[0], r_ax[1], r_ax[2]};
+        for (int a = 0; a < 3; ++a) {
+            const int r = r_ax[a];
+            std::vector<double> A((size_t)r * r);
+            for (int i = 0; i < r; ++i) {
+                const int row = hS[a * RS_MAX_TUCKER + i];
+                if (row < 0 || row >= n) {
+                    set_error("skeleton selection failed (rank-deficient factor basis)");
+                    return fail_out(RS_ERR_CUDA);
+                }
+                for (int c = 0; c < r; ++c) A[(size_t)i * r + c] = hV[((size_t)a * n + row) * RP + c];
+            }
+            int dn[3];
+            B0 = mode_product(B0, d, a, A.data(), r, r, dn);
+            for (int e = 0; e < 3; ++e) d[e] = dn[e];
+        }
+    }
+    std::vector<double> hB((size_t)RP * RP * RP, 0.0);
+    for (int x = 0; x < r_ax[0]; ++x)
+        for (int y = 0; y < r_ax[1]; ++y)
+            for (int z = 0; z < r_ax[2]; ++z)
+                hB[((size_t)x * RP + y) * RP + z] = B0[((size_t)x * r_ax[1] + y) * r_ax[2] + z];
+    if (cudaMemcpyAsync(d_B, hB.data(), hB.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        set_error("rs_protein_add_compress: core upload failed");
+        return fail_out(RS_ERR_CUDA);
+    }
+    if ((s = tucker_tables(P, st, n, RP, d_Vs, d_B, d_fail)) != RS_OK) return fail_out(s);
+
+    // 5. the short range of the union of the molecules' atoms
+    double *d_xyz, *d_q;
+    if ((s = S.get(&d_xyz, (size_t)3 * N)) != RS_OK || (s = S.get(&d_q, (size_t)N)) != RS_OK) return fail_out(s);
+    {
+        size_t off = 0;
+        for (int p = 0; p < count; ++p) {
+            const int Np = parts[p]->N;
+            ::rs::KernelTimer kt__("k_split_atoms64", st, 0.0, false);
+            k_split_atoms64<<<blocks_for(Np), kBlock, 0, st>>>(Np, parts[p]->view.atoms64, d_xyz + 3 * off,
+                                                               d_q + off);
+            off += (size_t)Np;
+        }
+    }
+    std::vector<double> hxyz((size_t)3 * N);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(hxyz.data(), d_xyz, hxyz.size() * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("rs_protein_add_compress: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail_out(RS_ERR_CUDA);
+    }
+    if ((s = build_cells(P, st, d_xyz, d_q, hxyz, S)) != RS_OK) return fail_out(s);
+    if ((s = finish_short_range(P, st)) != RS_OK) return fail_out(s);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("rs_protein_add_compress: %s", cudaGetErrorString(cudaGetLastError()));
         return fail_out(RS_ERR_CUDA);
     }
     *out = P;

@@ -144,6 +144,10 @@ struct rs_protein {
     std::vector<void*> allocations;   // device buffers owned by the handle
     size_t device_bytes = 0;
     int subspace_steps = 0;           // Tucker build: subspace-iteration steps taken
+    // Tucker handles: FP64 cardinal factors (3 x n x R, R = view.R) and core (R^3) on
+    // the device, kept for add-and-compress
+    double* fac64 = nullptr;
+    double* core64 = nullptr;
     // local-box handles share their parent's short-range data: the parent is freed
     // only when it and all of its local handles have been freed
     rs_protein* parent = nullptr;

@@ -116,6 +116,7 @@ def _load() -> C.CDLL:
         "rs_ppiem_scan": (st, [vp, vp, i32, vp, vp, i32, i32, i32, vp, vp, C.c_double, vp, vp, vp, vp, vp,
                                vp, vp, C.c_int, vp]),
         "rs_protein_local_box": (st, [vp, vp, vp, vp, C.c_double, C.POINTER(vp)]),
+        "rs_protein_add_compress": (st, [vp, vp, i32, i32, C.c_double, vp, C.POINTER(vp)]),
         "rs_energy_poses_complex": (st, [vp, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, C.c_int, vp]),
         "rs_pgd_run": (st, [vp, vp, i32, vp, vp, i64, vp, vp, i32, C.c_double, C.c_double, i32,
                             vp, vp, vp, vp]),
@@ -392,6 +393,17 @@ def rs_protein_local_box(ctx: int, parent: int, lo, hi, eps: float = 1e-7) -> in
     h = np.ascontiguousarray(hi, dtype=np.float64).reshape(3)
     out = C.c_void_p()
     _check(_lib.rs_protein_local_box(ctx, parent, l.ctypes.data, h.ctypes.data, float(eps), C.byref(out)))
+    return out.value
+
+
+def rs_protein_add_compress(ctx: int, parts, tucker_cap: int, eps_r: float = 1e-7, stream=None) -> int:
+    """One Tucker handle for the sum of the parts' long-range tensors, re-truncated
+    (add-and-compress), with the short range of the union of their atoms; free with
+    rs_protein_free."""
+    arr = (C.c_void_p * len(parts))(*[int(m) for m in parts])
+    out = C.c_void_p()
+    _check(_lib.rs_protein_add_compress(ctx, arr, len(parts), int(tucker_cap), float(eps_r), _stream_ptr(stream),
+                                        C.byref(out)))
     return out.value
 
 
@@ -778,6 +790,12 @@ class Protein:
     def local_box(self, lo, hi, eps: float = 1e-7) -> "Protein":
         """A local-box handle (scheme C) on [lo, hi]; see rs_protein_local_box."""
         return Protein(self.ctx, None, None, handle=rs_protein_local_box(self.ctx.handle, self.handle, lo, hi, eps))
+
+    @staticmethod
+    def add_compress(ctx: Context, parts, tucker_cap: int, eps_r: float = 1e-7) -> "Protein":
+        """The sum of the parts' potentials as one Tucker protein; see rs_protein_add_compress."""
+        h = rs_protein_add_compress(ctx.handle, [p.handle for p in parts], tucker_cap, eps_r)
+        return Protein(ctx, None, None, handle=h)
 
     def energies(self, lig_xyz, lig_q, quat, trans, **kw):
         return rs_energy_poses(self.ctx.handle, self.handle, lig_xyz, lig_q, quat, trans, **kw)
