@@ -310,10 +310,12 @@ typedef struct rs_batch_info {
     int32_t atoms_per_item;   /* per-block path: target atoms per item           */
     double  tune_ms;          /* device time the autotuner spent                  */
     int32_t mode;             /* first group: 0 per-block, 1 cell-grouped, 2 pair
-                                 by pair through the single-pair cell-grouped path */
+                                 by pair through the single-pair cell-grouped path,
+                                 3 the same with pairs on concurrent streams       */
     int32_t warps_per_cta;    /* cell-grouped: warps per CTA of the W-form kernel */
     int64_t chunk_atoms;      /* cell-grouped: pose-atoms per chunk (at most)     */
     int32_t nchunks;          /* cell-grouped: chunks over its groups             */
+    int32_t streams;          /* first group: concurrent streams (mode 3), else 1 */
 } rs_batch_info;
 
 /* Algorithm PLIE (Sec. 3.4) for many pairs of uneven size, grouped by padded
@@ -321,18 +323,21 @@ typedef struct rs_batch_info {
  * multi-pair pipeline (pose-atoms of all pairs sorted by (pair, grid cell)) or one
  * persistent per-block launch runs.  autotune = 1: the path and its shape (chunk
  * size, or threads per CTA and atoms per work item) are chosen by timing the
- * candidates (the per-block shapes, the cell-grouped pipeline, and the pairs one by
- * one through the single-pair cell-grouped path) on all of the group's poses (this
- * writes the output arrays; cached per
- * padded rank for the process); 0: the cell-grouped pipeline; 2: the per-block
- * launch with its default shape; 3: pair by pair through the single-pair path.
+ * candidates (the per-block shapes, the cell-grouped pipeline, the pairs one by
+ * one through the single-pair cell-grouped path, and that path with the pairs spread
+ * over 2 or 4 concurrent streams, longest first onto the least-loaded stream, as
+ * parallel branches of the graph) on all of the group's poses (this writes the output
+ * arrays; cached per padded rank for the process); 0: the cell-grouped pipeline;
+ * 2: the per-block launch with its default shape; 3: pair by pair through the
+ * single-pair path; 4: that path on 4 concurrent streams (scratch per stream).
  * Ligands are prepared now;
  * poses are read from the given pointers at each rs_batch_run, so a caller may
  * rewrite them in place between runs.  Device scratch: about 110 bytes per
- * pose-atom of the largest chunk (at most 2^23 pose-atoms).  Flags equal
- * rs_energy_poses'; energies equal them bit for bit where both take the same W form
- * (tensor-core or float-pair, chosen per launch from its atoms per cell) and within
- * ~2e-8 relative otherwise. */
+ * pose-atom of the largest chunk (at most 2^23 pose-atoms), once per stream in
+ * mode 3.  Flags equal rs_energy_poses'; energies equal them bit for bit in modes 2
+ * and 3 (each pair through the plain call's own dispatch) and where the other paths
+ * take the same W form (tensor-core or float-pair, chosen per launch from its atoms
+ * per cell), and within ~2e-8 relative otherwise. */
 rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int32_t autotune,
                           rs_batch** out);
 /* Replays the batch's graph on `stream` (NULL = the CUDA default stream). */

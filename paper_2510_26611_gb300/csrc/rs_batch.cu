@@ -32,18 +32,26 @@ namespace {
 
 // mode 0: per-block launch with `shape`; mode 1: cell-grouped pipeline with `wpb`
 // warps per W-form CTA and chunks of at most `chunk` pose-atoms; mode 2: each pair on
-// its own through the single-pair cell-grouped path (what a plain call of a large
-// pair runs), one pair after the other.
+// its own through the single-pair dispatch (what a plain call of the pair runs: the
+// cell-grouped path when it is large, else the per-block kernel), one pair after the
+// other; mode 3: the same single-pair dispatch with the
+// pairs spread over `streams` concurrent streams (parallel branches of the graph), so
+// that one pair's serial small kernels (key scan, pose setup, reduction) and tails
+// overlap another pair's work.
 struct Choice {
     int mode;
     Shape shape;
     int wpb;
     long long chunk;
+    int streams = 1;
 };
+
+constexpr int kMaxStreams = 4;
 
 const Choice kCandidates[] = {
     {1, {128, 512}, 4, 1LL << 23}, {1, {128, 512}, 4, 1LL << 21}, {0, {128, 256}, 0, 0},
-    {0, {128, 512}, 0, 0},         {0, {256, 512}, 0, 0},          {2, {128, 256}, 0, 0}};
+    {0, {128, 512}, 0, 0},         {0, {256, 512}, 0, 0},          {2, {128, 256}, 0, 0},
+    {3, {128, 256}, 0, 0, 2},      {3, {128, 256}, 0, 0, kMaxStreams}};
 
 std::mutex g_tune_mu;
 std::map<int, Choice> g_tuned;  // padded rank -> best choice (process-wide cache)
@@ -77,6 +85,14 @@ struct rs_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // concurrent pairs (mode 3): side streams, fork/join events, one scratch region
+    // of ws_side_bytes per stream
+    cudaStream_t side[rs::kMaxStreams] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[rs::kMaxStreams] = {};
+    void* d_ws_side = nullptr;
+    size_t ws_side_bytes = 0;
+    int ws_side_count = 0;
     double tune_ms = 0.0;
     std::vector<void*> allocs;
 };
@@ -143,14 +159,65 @@ rs_status dispatch_pairs(rs_batch* B, Group& g, cudaStream_t st) {
         a.events = false;
         a.ws = B->d_ws;
         a.ws_bytes = B->ws_bytes;
-        RS_TRY(launch_sorted(a, false, st));
+        RS_TRY(launch_eval_paths(a, false, st));
     }
     return RS_OK;
+}
+
+// Pairs with poses, longest (P L) first, each onto the stream with the least work so
+// far (ties to the lower stream): a fixed assignment, so the graph and the results do
+// not depend on timing.
+std::vector<std::vector<int>> assign_streams(const rs_batch* B, const Group& g, int S) {
+    std::vector<int> order;
+    for (int pi : g.pairs)
+        if (B->pairs[pi].P > 0) order.push_back(pi);
+    auto work = [&](int pi) { return (double)B->pairs[pi].P * B->pairs[pi].lig.L; };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+    std::vector<std::vector<int>> lists(S);
+    std::vector<double> load(S, 0.0);
+    for (int pi : order) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lists[k].push_back(pi);
+        load[k] += work(pi);
+    }
+    return lists;
+}
+
+// Mode 3: fork the group's pairs from st onto the side streams and join them back.
+// The join is recorded even when a launch fails, so that a capture ends cleanly.
+rs_status dispatch_streams(rs_batch* B, Group& g, cudaStream_t st) {
+    const int S = g.choice.streams;
+    const auto lists = assign_streams(B, g, S);
+    RS_TRY_CUDA(cudaEventRecord(B->fork_ev, st));
+    for (int k = 0; k < S; ++k) RS_TRY_CUDA(cudaStreamWaitEvent(B->side[k], B->fork_ev, 0));
+    rs_status first = RS_OK;
+    for (int k = 0; k < S && first == RS_OK; ++k)
+        for (int pi : lists[k]) {
+            const PairDesc& d = B->pairs[pi];
+            EvalLaunch a;
+            a.prot = d.prot;
+            a.lig = d.lig;
+            a.rot = d.rot;
+            a.trans = d.trans;
+            a.P = d.P;
+            a.E = d.E;
+            a.flags = d.flags;
+            a.events = false;
+            a.ws = (char*)B->d_ws_side + (size_t)k * B->ws_side_bytes;
+            a.ws_bytes = B->ws_side_bytes;
+            if ((first = launch_eval_paths(a, false, B->side[k])) != RS_OK) break;
+        }
+    for (int k = 0; k < S; ++k) {
+        RS_TRY_CUDA(cudaEventRecord(B->join_ev[k], B->side[k]));
+        RS_TRY_CUDA(cudaStreamWaitEvent(st, B->join_ev[k], 0));
+    }
+    return first;
 }
 
 rs_status dispatch_group(rs_batch* B, Group& g, cudaStream_t st, bool set_attr) {
     if (g.choice.mode == 0) return dispatch_block(B, g, st, set_attr);
     if (g.choice.mode == 2) return dispatch_pairs(B, g, st);
+    if (g.choice.mode == 3) return dispatch_streams(B, g, st);
     return group_launch(g.plan, B->d_pairs, g.d_segs, B->d_ws, B->ws_bytes, g.choice.wpb, st, false);
 }
 
@@ -258,9 +325,57 @@ rs_status size_pairs(rs_batch* B, Group& g) {
     return RS_OK;
 }
 
+// Side streams, events and per-stream scratch of mode 3 (created on first use; the
+// scratch grows to the largest pair of any group and to the most streams asked).
+rs_status size_streams(rs_batch* B, Group& g) {
+    if (!B->fork_ev) {
+        for (int k = 0; k < kMaxStreams; ++k) {
+            if (cudaStreamCreateWithFlags(&B->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&B->join_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("batch: stream or event creation failed");
+                return RS_ERR_CUDA;
+            }
+        }
+        if (cudaEventCreateWithFlags(&B->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("batch: event creation failed");
+            return RS_ERR_CUDA;
+        }
+    }
+    size_t need = 0;
+    for (int pi : g.pairs) {
+        const PairDesc& d = B->pairs[pi];
+        if (d.P > 0) need = std::max(need, sorted_scratch_bytes(d.P, d.lig.L, d.prot.n, false));
+    }
+    need = (need + 255) / 256 * 256;
+    const int S = g.choice.streams;
+    if (need > B->ws_side_bytes || S > B->ws_side_count) {
+        const size_t per = std::max(need, B->ws_side_bytes);
+        const int count = std::max(S, B->ws_side_count);
+        if (B->d_ws_side) {
+            cudaFree(B->d_ws_side);
+            B->allocs.erase(std::remove(B->allocs.begin(), B->allocs.end(), B->d_ws_side), B->allocs.end());
+            B->d_ws_side = nullptr;
+            B->ws_side_bytes = 0;
+            B->ws_side_count = 0;
+        }
+        if (cudaMalloc(&B->d_ws_side, per * count) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("batch: scratch allocation of %zu bytes failed", per * count);
+            return RS_ERR_OOM;
+        }
+        B->allocs.push_back(B->d_ws_side);
+        B->ws_side_bytes = per;
+        B->ws_side_count = count;
+    }
+    return RS_OK;
+}
+
 rs_status prepare(rs_batch* B, Group& g, double pose_fraction) {
     g.shape = g.choice.shape;
     if (g.choice.mode == 2) return size_pairs(B, g);
+    if (g.choice.mode == 3) return size_streams(B, g);
     return g.choice.mode == 0 ? build_items(B, g, pose_fraction) : build_plan(B, g, pose_fraction);
 }
 
@@ -316,6 +431,11 @@ void batch_destroy(rs_batch* B) {
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+    for (int k = 0; k < kMaxStreams; ++k) {
+        if (B->side[k]) cudaStreamDestroy(B->side[k]);
+        if (B->join_ev[k]) cudaEventDestroy(B->join_ev[k]);
+    }
+    if (B->fork_ev) cudaEventDestroy(B->fork_ev);
     for (void* p : B->allocs) cudaFree(p);
     delete B;
 }
@@ -342,7 +462,7 @@ rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int
     clear_error();
     RS_CHECK_ARG(ctx && pairs && out, "rs_batch_create: NULL argument");
     RS_CHECK_ARG(npairs >= 1 && npairs <= (1 << 20), "rs_batch_create: npairs=%d out of range", npairs);
-    RS_CHECK_ARG(autotune >= 0 && autotune <= 3, "rs_batch_create: autotune=%d not in {0, 1, 2, 3}", autotune);
+    RS_CHECK_ARG(autotune >= 0 && autotune <= 4, "rs_batch_create: autotune=%d not in {0, 1, 2, 3, 4}", autotune);
     *out = nullptr;
     for (int i = 0; i < npairs; ++i) {
         const rs_pair& p = pairs[i];
@@ -436,6 +556,7 @@ rs_status rs_batch_create(rs_ctx* ctx, int32_t npairs, const rs_pair* pairs, int
     for (Group& g : B->groups) {
         if (autotune == 2) g.choice = Choice{0, {128, 256}, 0, 0};  // per-block path, default shape
         if (autotune == 3) g.choice = Choice{2, {128, 256}, 0, 0};  // pair by pair, single-pair path
+        if (autotune == 4) g.choice = Choice{3, {128, 256}, 0, 0, kMaxStreams};  // pairs on concurrent streams
         if (autotune == 1 && (s = tune_group(B, g, st)) != RS_OK) return fail(s);
         if ((s = prepare(B, g, 1.0)) != RS_OK) return fail(s);
         if ((s = dispatch_group(B, g, st, true)) != RS_OK) return fail(s);  // sets attributes, grid
@@ -499,6 +620,7 @@ rs_status rs_batch_get_info(const rs_batch* B, rs_batch_info* o) {
         o->atoms_per_item = g.choice.mode == 0 ? g.shape.atoms : 0;
         o->warps_per_cta = g.choice.mode == 1 ? g.choice.wpb : 0;
         o->chunk_atoms = g.choice.mode == 1 ? g.choice.chunk : 0;
+        o->streams = g.choice.mode == 3 ? g.choice.streams : 1;
     }
     o->tune_ms = B->tune_ms;
     return RS_OK;

@@ -26,6 +26,9 @@ struct EvalLaunch {
 rs_status launch_prep_ligand(int L, const double* xyz, const double* q, float4* y, float2* yd, double* y64,
                              double* q64, cudaStream_t st, bool events = true);
 rs_status launch_eval(const EvalLaunch& a, bool grad, cudaStream_t st);
+// The long-range and short-range passes of launch_eval without the local-box flag
+// pass: the cell-grouped path for large Tucker calls, else the per-block kernels.
+rs_status launch_eval_paths(const EvalLaunch& a, bool grad, cudaStream_t st);
 // Local-box handles: OR the out-of-grid flag into flags[p] for every pose (not skipped)
 // with an atom whose interpolation cell lies outside the handle's box (no-op for
 // other handles or NULL flags).

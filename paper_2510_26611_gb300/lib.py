@@ -64,7 +64,7 @@ class rs_batch_info(C.Structure):
     _fields_ = [("npairs", C.c_int32), ("ngroups", C.c_int32), ("nitems", C.c_int32),
                 ("grid", C.c_int32), ("threads", C.c_int32), ("atoms_per_item", C.c_int32),
                 ("tune_ms", C.c_double), ("mode", C.c_int32), ("warps_per_cta", C.c_int32),
-                ("chunk_atoms", C.c_int64), ("nchunks", C.c_int32)]
+                ("chunk_atoms", C.c_int64), ("nchunks", C.c_int32), ("streams", C.c_int32)]
 
 
 class rs_request(C.Structure):

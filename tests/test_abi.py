@@ -82,8 +82,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", offsetof(rs_result, message), sizeof(rs_serve_params),
          offsetof(rs_serve_params, inject_alloc_failures), offsetof(rs_serve_params, hold_builds),
          sizeof(rs_serve_stats), offsetof(rs_serve_stats, mean_requests_per_launch));
-  printf("%zu %zu %zu\n", sizeof(rs_batch_info), offsetof(rs_batch_info, chunk_atoms),
-         offsetof(rs_batch_info, nchunks));
+  printf("%zu %zu %zu %zu\n", sizeof(rs_batch_info), offsetof(rs_batch_info, chunk_atoms),
+         offsetof(rs_batch_info, nchunks), offsetof(rs_batch_info, streams));
   return 0;
 }
 ''')
@@ -95,7 +95,7 @@ int main(void) {
     B = lib.rs_batch_info
     want = [C.sizeof(R), R.params.offset, R.L.offset, R.P.offset, R.trans.offset, C.sizeof(Z),
             Z.message.offset, C.sizeof(S), S.inject_alloc_failures.offset, S.hold_builds.offset, C.sizeof(T),
-            T.mean_requests_per_launch.offset, C.sizeof(B), B.chunk_atoms.offset, B.nchunks.offset]
+            T.mean_requests_per_launch.offset, C.sizeof(B), B.chunk_atoms.offset, B.nchunks.offset, B.streams.offset]
     assert got == want
 
 

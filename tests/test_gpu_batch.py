@@ -1,7 +1,8 @@
 """Batched persistent launch: pairs of uneven size in one graph-captured launch give
 the same energies and flags as one plain call per pair (bit for bit where both take
-the same W-form kernel, else within the path tolerance), before and after the poses
-are rewritten in place; one pair is checked against the oracle."""
+the same W-form kernel, as the pair-by-pair modes do on one stream or on concurrent
+streams, else within the path tolerance), before and after the poses are rewritten in
+place; one pair is checked against the oracle."""
 import numpy as np
 import pytest
 
@@ -74,7 +75,7 @@ def test_batch_equals_plain_calls(setup):
     elif info["mode"] == 1:
         assert info["nchunks"] > 0 and info["warps_per_cta"] in (4, 8)
     else:
-        assert info["mode"] == 2
+        assert info["mode"] in (2, 3) and info["streams"] in ((1,) if info["mode"] == 2 else (2, 4))
     lib.rs_batch_run(b)
     torch.cuda.synchronize()
     ref = _plain(lib, prots, pairs)
@@ -82,7 +83,7 @@ def test_batch_equals_plain_calls(setup):
         assert_paths_agree(p["E_out"].cpu().numpy(), E, p["flags_out"].cpu().numpy(), f)
 
 
-@pytest.mark.parametrize("mode", [0, 2, 3], ids=["cell-grouped", "per-block", "pair-by-pair"])
+@pytest.mark.parametrize("mode", [0, 2, 3, 4], ids=["cell-grouped", "per-block", "pair-by-pair", "streams"])
 def test_both_batch_paths_equal_plain_calls(setup, mode):
     import torch
     lib, ctx, ws, prots, pairs, b = setup
@@ -91,7 +92,8 @@ def test_both_batch_paths_equal_plain_calls(setup, mode):
     b2, keep = lib.rs_batch_create(ctx.handle, outs, autotune=mode)
     try:
         info = lib.rs_batch_get_info(b2)
-        assert info["mode"] == {0: 1, 2: 0, 3: 2}[mode]
+        assert info["mode"] == {0: 1, 2: 0, 3: 2, 4: 3}[mode]
+        assert info["streams"] == (4 if mode == 4 else 1)
         lib.rs_batch_run(b2)
         torch.cuda.synchronize()
     finally:
@@ -99,6 +101,10 @@ def test_both_batch_paths_equal_plain_calls(setup, mode):
     ref = _plain(lib, prots, pairs)
     for p, (E, f) in zip(outs, ref):
         assert_paths_agree(p["E_out"].cpu().numpy(), E, p["flags_out"].cpu().numpy(), f)
+        if mode in (3, 4):
+            # the pair-by-pair modes run each pair through the plain call's own dispatch
+            assert np.array_equal(p["E_out"].cpu().numpy(), E)
+            assert np.array_equal(p["flags_out"].cpu().numpy(), f)
 
 
 def test_batch_replay_after_rewriting_poses(setup):
