@@ -631,19 +631,37 @@ __global__ void __launch_bounds__(256) k_gemm_reduce(int n, int p, int nks, cons
     }
 }
 
-// S[ax] = sum over blocks of Sp[ax][blk] in a fixed order.
-__global__ void k_sum_gram(int nblk, int p, const double* __restrict__ Sp, double* __restrict__ S) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    int ax = blockIdx.y;
-    if (e >= p * p) return;
-    const double* src = Sp + (size_t)ax * nblk * p * p + e;
-    double s[4] = {0.0, 0.0, 0.0, 0.0};  // four interleaved partial sums, fixed order
-    int b = 0;
-    for (; b + 4 <= nblk; b += 4)
+// S[ax] = sum over blocks of Sp[ax][blk] in a fixed order.  CTA: 32 consecutive entries
+// (one per lane, coalesced) of one axis; warp w adds blocks w, w + 8, ... (two
+// interleaved partial sums, so a warp has several loads in flight), then the eight
+// warps' sums are added in warp order.
+constexpr int kSumGramWarps = 8;
+__global__ void __launch_bounds__(32 * kSumGramWarps) k_sum_gram(int nblk, int p, const double* __restrict__ Sp,
+                                                                 double* __restrict__ S) {
+    __shared__ double part[kSumGramWarps][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    const int ax = blockIdx.y;
+    double s0 = 0.0, s1 = 0.0;
+    if (e < p * p) {
+        const double* src = Sp + (size_t)ax * nblk * p * p + e;
+        const size_t stride = (size_t)kSumGramWarps * p * p;
+        int b = w;
+#pragma unroll 4
+        for (; b + kSumGramWarps < nblk; b += 2 * kSumGramWarps) {
+            s0 += src[(size_t)b * p * p];
+            s1 += src[(size_t)b * p * p + stride];
+        }
+        if (b < nblk) s0 += src[(size_t)b * p * p];
+    }
+    part[w][lane] = s0 + s1;
+    __syncthreads();
+    if (w == 0 && e < p * p) {
+        double t = part[0][lane];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] += src[(size_t)(b + u) * p * p];
-    for (; b < nblk; ++b) s[b & 3] += src[(size_t)b * p * p];
-    S[(size_t)ax * p * p + e] = (s[0] + s[1]) + (s[2] + s[3]);
+        for (int q = 1; q < kSumGramWarps; ++q) t += part[q][lane];
+        S[(size_t)ax * p * p + e] = t;
+    }
 }
 
 // Partial products Sp[ax][blk] = A_blk^T B_blk (p x p) of 16-row blocks of A and
@@ -2105,7 +2123,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         }
         {
             ::rs::KernelTimer kt__("k_sum_gram", st, 0.0, false);
-            k_sum_gram<<<dim3(blocks_for((size_t)p * p), 3), kBlock, 0, st>>>(nblk, p, d_Sp, d_Sm);
+            k_sum_gram<<<dim3((p * p + 31) / 32, 3), 32 * kSumGramWarps, 0, st>>>(nblk, p, d_Sp, d_Sm);
         }
         {
             ::rs::KernelTimer kt__("k_chol", st, 0.0, false);
@@ -2172,7 +2190,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         }
         {
             ::rs::KernelTimer kt__("k_sum_gram", st, 0.0, false);
-            k_sum_gram<<<dim3(blocks_for((size_t)p * p), 3), kBlock, 0, st>>>(nblk, p, d_Sp, d_Sm);
+            k_sum_gram<<<dim3((p * p + 31) / 32, 3), 32 * kSumGramWarps, 0, st>>>(nblk, p, d_Sp, d_Sm);
         }
         {
             ::rs::KernelTimer kt__("k_chol", st, 0.0, false);
@@ -2203,7 +2221,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         }
         {
             ::rs::KernelTimer kt__("k_sum_gram", st, 0.0, false);
-            k_sum_gram<<<dim3(blocks_for((size_t)p * p), 3), kBlock, 0, st>>>(nblk, p, d_Sp, d_Sm);
+            k_sum_gram<<<dim3((p * p + 31) / 32, 3), 32 * kSumGramWarps, 0, st>>>(nblk, p, d_Sp, d_Sm);
         }
         RS_TRY_CUDA(cudaGetLastError());
         // p x p eigenproblems on the host (FP64): a few microseconds each
