@@ -2167,7 +2167,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
         RS_TRY_CUDA(cudaFuncSetAttribute(tcg::k_tc_gemm<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                          (int)tcg::GemmShape<NP>::SMEM));                                 \
         ::rs::KernelTimer kt__("k_tc_gemm", st, tflops, true);                                            \
-        tcg::k_tc_gemm<NP><<<dim3(MT, KC, 3), tcg::kM, tcg::GemmShape<NP>::SMEM, st>>>(                   \
+        tcg::k_tc_gemm<NP><<<dim3(MT, KC, 3), tcg::kGemmThreads, tcg::GemmShape<NP>::SMEM, st>>>(         \
             n, MT, KC, d_As, d_ainv, d_Bs, d_binv, d_Yp2, d_tcerr);                                       \
         break;                                                                                            \
     }

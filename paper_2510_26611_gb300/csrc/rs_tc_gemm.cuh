@@ -191,12 +191,16 @@ __global__ void __launch_bounds__(NP) k_slice_cols(int n, int KC, const float2* 
 }
 
 // Y partial of one (row tile, K chunk, axis): Yp[kc][ax][i][j] = sum over the chunk's
-// k of A[i][k] B[k][j], as a float pair (rows i < n).  CTA: kM threads; thread 0 loads the
-// operands by bulk copies and issues the MMAs; every thread finishes its own row
-// (TMEM lane).  On a load or MMA that does not complete within the bounded wait the
-// tile's outputs are NaN and *err is set.
+// k of A[i][k] B[k][j], as a float pair (rows i < n).  CTA: kGemmThreads threads; thread
+// 0 loads the operands by bulk copies and issues the MMAs; then warps w and w + 4 read
+// TMEM lanes 32 (w mod 4) .. + 31 (thread = row) and finish alternate 16-column blocks
+// of the row (two warps per scheduler for the epilogue, where six diagonals are
+// combined per column).  On a load or MMA that does not complete
+// within the bounded wait the tile's outputs are NaN and *err is set.
+constexpr int kGemmThreads = 2 * kM;
+
 template <int NP>
-__global__ void __launch_bounds__(kM, 1) k_tc_gemm(int n, int MT, int KC, const uint8_t* __restrict__ As,
+__global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(int n, int MT, int KC, const uint8_t* __restrict__ As,
                                                     const float* __restrict__ ainv, const uint8_t* __restrict__ Bs,
                                                     const float* __restrict__ binv, float2* __restrict__ Yp,
                                                     int* __restrict__ err) {
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(kM, 1) k_tc_gemm(int n, int MT, int KC, const 
     const uint32_t tmem = *slot;
     // scales for the epilogue, loaded while the copies and MMAs run
     float* sbinv = reinterpret_cast<float*>(smem_g + Sh::BINV_OFF);
-    const int row = warp * 32 + (tid & 31);
+    const int row = (warp & 3) * 32 + (tid & 31), half = warp >> 2;
     const int i = mt * kM + row;
     const float ai = ainv[((size_t)ax * KC + kc) * ((size_t)MT * kM) + i];
     if (tid < NP) sbinv[tid] = binv[((size_t)ax * KC + kc) * NP + tid];
@@ -255,13 +259,14 @@ __global__ void __launch_bounds__(kM, 1) k_tc_gemm(int n, int MT, int KC, const 
     float2* out = Yp + (((size_t)kc * 3 + ax) * n + (size_t)i) * NP;
     if (failed) {
         if (i < n)
-            for (int j = 0; j < NP; ++j) out[j] = make_float2(__int_as_float(-1), 0.f);
+            for (int j = 0; j < NP; ++j)
+                if (((j >> 4) & 1) == half) out[j] = make_float2(__int_as_float(-1), 0.f);
         if (tid == 0) atomicExch(err, 1);
     } else {
         const float* bi = sbinv;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-        for (int c0 = 0; c0 < NP; c0 += 16) {
+        for (int c0 = 16 * half; c0 < NP; c0 += 32) {
             float acc[kS][16];
 #pragma unroll
             for (int d = 0; d < kS; d += 2)
