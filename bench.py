@@ -192,10 +192,10 @@ POSE_ATOM_KERNELS = ("k_sorted_tc", "k_sorted_tc_grad", "k_sorted_wform", "k_sor
 # the digest of the kernel's sources at that capture; a kernel whose sources changed
 # since reports traffic null.
 TRAFFIC = {
-    name: {"bytes_per_pose_atom": b, "sources": "d57baa734ad31bbc",
+    name: {"bytes_per_pose_atom": b, "sources": "5cf7801ef109403d",
            "profile": "profiles/pose_kernels_dram_protein_p100000.md"}
-    for name, b in (("k_sorted_tc_grad", 223.2), ("k_sorted_tc", 112.4), ("k_sorted_atoms_grad", 90.8),
-                    ("k_sorted_atoms", 71.3))
+    for name, b in (("k_sorted_tc_grad", 223.3), ("k_sorted_tc", 112.0), ("k_sorted_atoms_grad", 90.8),
+                    ("k_sorted_atoms", 71.4))
 }
 TRAFFIC_SOURCES = ("rs_sorted.cu", "rs_sorted_dev.cuh", "rs_tc.cuh", "rs_tc_dev.cuh", "rs_pose_dev.cuh",
                    "rs_common.cuh")
