@@ -200,7 +200,8 @@ rs_status rs_protein_local_box(rs_ctx* ctx, rs_protein* parent, const double* lo
  * sums of Tucker tensors re-compressed by an HOSVD of the small core; Sec. 5.1, the
  * complex potential of Eq. EnergySum_Mcomplex as one tensor).  With T_p = beta_p x_l
  * V_l^(p) the parts' tensors, per axis [V_l^(1) ... V_l^(count)] = Q_l R_l (thin QR,
- * FP64 on the host), C = sum_p beta_p x_l R_l[:, columns of p], and the HOSVD of C
+ * FP64 on the host; a column within 1e-12 of the span of the previous ones gets a
+ * zero Q column), C = sum_p beta_p x_l R_l[:, columns of p], and the HOSVD of C
  * keeps per axis r_l = #{s_i > eps_r s_1} (1 <= r_l <= tucker_cap) leading singular
  * vectors U_l: V_l = Q_l U_l, core = C x_l U_l^T, then the cardinal basis and
  * evaluation tables as rs_build_protein makes them.  Long-range error (Frobenius, on

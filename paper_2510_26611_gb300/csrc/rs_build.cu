@@ -2508,16 +2508,27 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
 
 namespace {
 
-// Thin QR of the n x k matrix A (column j at A + j n) by classical Gram-Schmidt run
-// twice per column, the coefficients of both passes summed into R (k x k, upper
-// triangular, row-major); Q overwrites A.  A column with nothing left after the two
-// passes becomes zero with R[j][j] = 0.
-void cgs2_qr(int n, int k, double* A, double* R) {
+// Thin QR of the n x k matrix A (column j at A + j n) by classical Gram-Schmidt with
+// re-orthogonalisation: a column is projected out against the previous ones again
+// while a pass removes more than half of what is left (at most three passes), the
+// coefficients of all passes summed into R (k x k, upper triangular, row-major); Q
+// overwrites A.  A column whose remainder is at most 1e-12 of its norm lies in the span
+// of the previous ones (a molecule given twice, or sharing factor directions with
+// another): its Q column is set to zero and R[j][j] = 0, since normalising rounding
+// noise would give a direction that is not orthogonal to the others.
+void gs_qr(int n, int k, double* A, double* R) {
     std::fill(R, R + (size_t)k * k, 0.0);
     std::vector<double> c(k);
+    auto norm = [n](const double* v) {
+        double s = 0.0;
+        for (int t = 0; t < n; ++t) s += v[t] * v[t];
+        return std::sqrt(s);
+    };
     for (int j = 0; j < k; ++j) {
         double* aj = A + (size_t)j * n;
-        for (int pass = 0; pass < 2; ++pass) {
+        const double n0 = norm(aj);
+        double prev = n0, cur = n0;
+        for (int pass = 0; pass < 3 && j > 0; ++pass) {
             for (int i = 0; i < j; ++i) {
                 const double* qi = A + (size_t)i * n;
                 double d = 0.0;
@@ -2529,13 +2540,17 @@ void cgs2_qr(int n, int k, double* A, double* R) {
                 for (int t = 0; t < n; ++t) aj[t] -= c[i] * qi[t];
                 R[(size_t)i * k + j] += c[i];
             }
+            prev = cur;
+            cur = norm(aj);
+            if (cur >= 0.5 * prev) break;
         }
-        double nrm = 0.0;
-        for (int t = 0; t < n; ++t) nrm += aj[t] * aj[t];
-        nrm = std::sqrt(nrm);
-        R[(size_t)j * k + j] = nrm;
-        if (nrm > 0.0)
-            for (int t = 0; t < n; ++t) aj[t] /= nrm;
+        if (cur <= 1e-12 * n0 || cur == 0.0) {
+            for (int t = 0; t < n; ++t) aj[t] = 0.0;
+            R[(size_t)j * k + j] = 0.0;
+        } else {
+            R[(size_t)j * k + j] = cur;
+            for (int t = 0; t < n; ++t) aj[t] /= cur;
+        }
     }
 }
 
@@ -2647,7 +2662,7 @@ extern "C" rs_status rs_protein_add_compress(rs_ctx* ctx, const rs_protein* cons
             for (int c = 0; c < parts[p]->rank[a]; ++c, ++col)
                 for (int i = 0; i < n; ++i) Q[a][(size_t)col * n + i] = Va[(size_t)i * R + c];
         }
-        cgs2_qr(n, k, Q[a].data(), Rf[a].data());
+        gs_qr(n, k, Q[a].data(), Rf[a].data());
     }
     // 2. the core in the orthonormal bases: C = sum_p beta_p x_l R_l[:, columns of p]
     std::vector<double> C((size_t)ksum[0] * ksum[1] * ksum[2], 0.0);

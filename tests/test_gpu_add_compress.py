@@ -78,6 +78,34 @@ def test_two_molecules_match_the_oracle(L, ctx, kind, cap_parts, cap):
             p.close()
 
 
+def test_three_molecules_one_given_twice(L, ctx):
+    """Three parts, the first repeated (its columns add no direction to the stacked
+    factors, so the QR meets exactly dependent columns), against the oracle."""
+    w = W.plain_small(P=1500)
+    order = np.argsort(w.prot_xyz[:, 1], kind="stable")
+    thirds = np.array_split(order, 3)
+    prm = L.rs_params_default(n=w.n, b=w.b, sigma=w.sigma, R_l=w.R_l, tucker_cap=8)
+    prots, models = [], []
+    try:
+        for idx in (thirds[0], thirds[1], thirds[0]):
+            prots.append(L.Protein(ctx, w.prot_xyz[idx], w.prot_q[idx], prm))
+            models.append(O.build_model(w.prot_xyz[idx], w.prot_q[idx], w.n, w.b, w.sigma, w.R_l, tucker_cap=8))
+        ac = L.Protein.add_compress(ctx, prots, 16)
+        try:
+            ref_m = O.add_and_compress(models, 16)
+            assert list(ac.info["rank"]) == list(ref_m.ranks)
+            assert ac.info["N"] == 2 * thirds[0].size + thirds[1].size
+            E, f = ac.energies(w.lig_xyz, w.lig_q, w.quat, w.trans)
+            ref = O.pose_energies(ref_m, w.lig_xyz, w.lig_q, w.quat, w.trans)
+            assert_energies(np.asarray(E), ref)
+            assert_flags(np.asarray(f), ref)
+        finally:
+            ac.close()
+    finally:
+        for p in prots:
+            p.close()
+
+
 def test_one_molecule_recompressed_to_a_lower_rank(L, ctx):
     w = W.plain_small(P=2000)
     prm = L.rs_params_default(n=w.n, b=w.b, sigma=w.sigma, R_l=w.R_l, tucker_cap=16)
