@@ -507,8 +507,11 @@ __global__ void k_trace(int n, const float2* __restrict__ G, double* __restrict_
 }
 
 // --------------------------------------------------------- subspace iteration (FP64)
-// Deterministic start block: a hash of (axis, row, column) mapped to [-1, 1).
-__global__ void k_init_block(int n, int p, double* __restrict__ Q) {
+// Deterministic start block: a hash of (axis, row, column) mapped to [-1, 1) on a grid
+// of 2^-23, so each value is a float: Q (FP64) and Q2 (float pairs, the GEMM's operand)
+// hold the same numbers.  The block is not orthonormalised: the first subspace step's
+// CholQR of G Q spans the same columns either way.
+__global__ void k_init_block(int n, int p, double* __restrict__ Q, float2* __restrict__ Q2) {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t total = (size_t)3 * n * p;
     if (idx >= total) return;
@@ -518,7 +521,9 @@ __global__ void k_init_block(int n, int p, double* __restrict__ Q) {
     x ^= x >> 27;
     x *= 0x94D049BB133111EBull;
     x ^= x >> 31;
-    Q[idx] = (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    const double v = (double)(x >> 40) * (1.0 / 8388608.0) - 1.0;
+    Q[idx] = v;
+    Q2[idx] = make_float2((float)v, 0.f);
 }
 
 // Y[ax] = G[ax] Q[ax] (G n x n, Q n x p, p <= 48, both float pairs), split over K:
@@ -2105,7 +2110,7 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
     RS_TRY_CUDA(cudaMemsetAsync(d_fail, 0, 3 * sizeof(int), st));
     {
         ::rs::KernelTimer kt__("k_init_block", st, 0.0, false);
-        k_init_block<<<blocks_for((size_t)3 * n * p), kBlock, 0, st>>>(n, p, d_Q);
+        k_init_block<<<blocks_for((size_t)3 * n * p), kBlock, 0, st>>>(n, p, d_Q, d_Q2);
     }
     dim3 gq((n + kGemmRows - 1) / kGemmRows, kGemmKS, 3);
     const int nblk = (n + 15) / 16;
@@ -2146,7 +2151,6 @@ static rs_status build_tucker(rs_protein* P, cudaStream_t st, const double* d_xy
                                         cudaMemcpyDeviceToDevice, st));
         return RS_OK;
     };
-    RS_TRY(orthonormalize(d_Q));
     work = 3.0 * 13.0 * n * (double)n * p;  // FP32 pipe ops per G Q (one Dot2 step per product)
     // Y partials of G Q per K slice into d_Yp: float-pair GEMM, or slices of Q and the
     // tensor-core GEMM
