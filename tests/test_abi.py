@@ -58,6 +58,16 @@ def test_invalid_arguments_return_status_not_crash():
     out = C.c_void_p()
     st = lib._lib.rs_build_protein(None, 1, None, None, None, 0, None, C.byref(out))
     assert st == lib.RS_ERR_INVALID
+    # add-and-compress: NULL context or part list, before any device work
+    out = C.c_void_p(1)
+    parts = (C.c_void_p * 1)(None)
+    assert lib._lib.rs_protein_add_compress(None, parts, 1, 8, 1e-7, None, C.byref(out)) == lib.RS_ERR_INVALID
+    assert lib._lib.rs_protein_add_compress(None, None, 0, 8, 1e-7, None, C.byref(out)) == lib.RS_ERR_INVALID
+    assert lib._lib.rs_protein_add_compress(None, parts, 1, 8, 1e-7, None, None) == lib.RS_ERR_INVALID
+    assert "NULL" in lib.rs_last_error()
+    # batches and local boxes: NULL context
+    assert lib._lib.rs_batch_create(None, 1, None, 1, C.byref(out)) == lib.RS_ERR_INVALID
+    assert lib._lib.rs_protein_local_box(None, None, None, None, 1e-7, C.byref(out)) == lib.RS_ERR_INVALID
 
 
 def test_ctx_create_without_gpu_fails_cleanly():
