@@ -1178,6 +1178,24 @@ def run_serve(args):
 
 
 # ------------------------------------------------------------------ our arm
+def job_step_time(t_local: float, world: int, device) -> float:
+    """The whole job's time per step: the slowest rank's (MAX over ranks, returned on
+    every rank).  Ranks evaluate their own poses against their own protein build with
+    no data-path collective; this reduction and the barriers around the timed region
+    are the only cross-rank operations."""
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(poses_per_rank: int, world: int, seconds_per_step: float) -> float:
+    """Poses per second of the whole job: every rank's poses over the slowest rank's time."""
+    return world * poses_per_rank / seconds_per_step
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -1253,11 +1271,8 @@ def run_ours(args):
         if name in timings:
             timings[name]["work"] = c["fp32_ops"]
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * P / (ms_max / 1e3)
+    ms_max = job_step_time(ms, world, dev)
+    value = job_throughput(P, world, ms_max / 1e3)
     clocks = clk.summary()
 
     # end to end through the public API with pinned host buffers
@@ -1287,16 +1302,13 @@ def run_ours(args):
         for _ in range(args.steps):
             host_step()
         torch.cuda.synchronize()
-        t_e2e = (time.perf_counter() - t0) / args.steps
-        te = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        t_e2e = job_step_time((time.perf_counter() - t0) / args.steps, world, dev)
         L = w.L
         h2d = w.N * 32 + 2 * L * 32 + P * 32 + P * 24 + P * 24 + P * 24
         d2h = P * 8 + P + P * 8 + P * 48 + P
-        e2e = {"value": round(world * P / float(te.item()), 3), "unit": UNIT,
+        e2e = {"value": round(job_throughput(P, world, t_e2e), 3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": round(1e3 * float(te.item()), 3)}
+               "ms_per_step": round(1e3 * t_e2e, 3)}
 
     pose_atoms = {k: args.steps * P * w.L / max(timings[k]["launches"], 1)
                   for k in POSE_ATOM_KERNELS if k in timings}
