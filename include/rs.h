@@ -464,6 +464,15 @@ void      rs_serve_destroy(rs_server* s);
  * the unit eigenvector of lam[c].  RS_ERR_UNSUPPORTED if the iteration does not
  * converge. */
 rs_status rs_symeig_host(int32_t n, const double* A, double* lam, double* W);
+/* The host FP64 thin QR rs_protein_add_compress uses for the stacked factor matrices
+ * (Algorithm TEP step 4), exported so that it can be tested without a GPU: classical
+ * Gram-Schmidt, a column projected out again while a pass removes more than half of
+ * what is left (at most three passes), and a column left with at most 1e-12 of its
+ * norm taken as dependent (zero column of Q, R[j][j] = 0).  A: n x k, column-major
+ * (column j at A + j n), host memory, overwritten by Q; R: k x k row-major, upper
+ * triangular, written; A = Q R to rounding.  RS_ERR_INVALID for n < 1, k not in
+ * [1, 4096] or a NULL pointer. */
+rs_status rs_qr_host(int32_t n, int32_t k, double* A, double* R);
 /* These have no counterpart in the paper: they support measurement.
  * Number of kernels this library has launched in the process (all devices). */
 unsigned long long rs_stats_kernel_launches(void);

@@ -93,6 +93,7 @@ struct DeviceArena {
 
 }  // namespace
 bool symeig_host(int n, const double* A, double* lam, double* W);
+void gs_qr_host(int n, int k, double* A, double* R);
 namespace {
 
 inline unsigned blocks_for(size_t n, int bs = kBlock) { return (unsigned)((n + bs - 1) / bs); }
@@ -2512,52 +2513,6 @@ extern "C" rs_status rs_build_protein(rs_ctx* ctx, int32_t N, const double* xyz,
 
 namespace {
 
-// Thin QR of the n x k matrix A (column j at A + j n) by classical Gram-Schmidt with
-// re-orthogonalisation: a column is projected out against the previous ones again
-// while a pass removes more than half of what is left (at most three passes), the
-// coefficients of all passes summed into R (k x k, upper triangular, row-major); Q
-// overwrites A.  A column whose remainder is at most 1e-12 of its norm lies in the span
-// of the previous ones (a molecule given twice, or sharing factor directions with
-// another): its Q column is set to zero and R[j][j] = 0, since normalising rounding
-// noise would give a direction that is not orthogonal to the others.
-void gs_qr(int n, int k, double* A, double* R) {
-    std::fill(R, R + (size_t)k * k, 0.0);
-    std::vector<double> c(k);
-    auto norm = [n](const double* v) {
-        double s = 0.0;
-        for (int t = 0; t < n; ++t) s += v[t] * v[t];
-        return std::sqrt(s);
-    };
-    for (int j = 0; j < k; ++j) {
-        double* aj = A + (size_t)j * n;
-        const double n0 = norm(aj);
-        double prev = n0, cur = n0;
-        for (int pass = 0; pass < 3 && j > 0; ++pass) {
-            for (int i = 0; i < j; ++i) {
-                const double* qi = A + (size_t)i * n;
-                double d = 0.0;
-                for (int t = 0; t < n; ++t) d += qi[t] * aj[t];
-                c[i] = d;
-            }
-            for (int i = 0; i < j; ++i) {
-                const double* qi = A + (size_t)i * n;
-                for (int t = 0; t < n; ++t) aj[t] -= c[i] * qi[t];
-                R[(size_t)i * k + j] += c[i];
-            }
-            prev = cur;
-            cur = norm(aj);
-            if (cur >= 0.5 * prev) break;
-        }
-        if (cur <= 1e-12 * n0 || cur == 0.0) {
-            for (int t = 0; t < n; ++t) aj[t] = 0.0;
-            R[(size_t)j * k + j] = 0.0;
-        } else {
-            R[(size_t)j * k + j] = cur;
-            for (int t = 0; t < n; ++t) aj[t] /= cur;
-        }
-    }
-}
-
 // Mode product of a d0 x d1 x d2 tensor T (row-major) with M (m x d_ax, row stride
 // ldm) along axis ax: out has d_ax replaced by m, out[.., i, ..] = sum_a M[i][a] T[.., a, ..].
 std::vector<double> mode_product(const std::vector<double>& T, const int d[3], int ax, const double* M, int m,
@@ -2666,7 +2621,7 @@ extern "C" rs_status rs_protein_add_compress(rs_ctx* ctx, const rs_protein* cons
             for (int c = 0; c < parts[p]->rank[a]; ++c, ++col)
                 for (int i = 0; i < n; ++i) Q[a][(size_t)col * n + i] = Va[(size_t)i * R + c];
         }
-        gs_qr(n, k, Q[a].data(), Rf[a].data());
+        rs::gs_qr_host(n, k, Q[a].data(), Rf[a].data());
     }
     // 2. the core in the orthonormal bases: C = sum_p beta_p x_l R_l[:, columns of p]
     std::vector<double> C((size_t)ksum[0] * ksum[1] * ksum[2], 0.0);

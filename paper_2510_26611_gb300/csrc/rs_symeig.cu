@@ -4,6 +4,7 @@
 // on the tridiagonal matrix (Golub & Van Loan, "Matrix Computations", 4th ed.,
 // sections 8.3.1 and 8.3.3).  The matrices are p x p with p <= 48: the host solves
 // them in microseconds, while on the GPU one SM's FP64 pipe would spend ~1 ms.
+// Also the thin QR of stacked factor matrices used by add-and-compress.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -128,6 +129,53 @@ bool symeig_host(int n, const double* A, double* lam, double* W) {
     return ok;
 }
 
+// Thin QR of the n x k matrix A (column j at A + j n), FP64 on the host, for the
+// add-and-compress of Tucker tensors (Algorithm TEP step 4): classical Gram-Schmidt with
+// re-orthogonalisation: a column is projected out against the previous ones again
+// while a pass removes more than half of what is left (at most three passes), the
+// coefficients of all passes summed into R (k x k, upper triangular, row-major); Q
+// overwrites A.  A column whose remainder is at most 1e-12 of its norm lies in the span
+// of the previous ones (a molecule given twice, or sharing factor directions with
+// another): its Q column is set to zero and R[j][j] = 0, since normalising rounding
+// noise would give a direction that is not orthogonal to the others.
+void gs_qr_host(int n, int k, double* A, double* R) {
+    std::fill(R, R + (size_t)k * k, 0.0);
+    std::vector<double> c(k);
+    auto norm = [n](const double* v) {
+        double s = 0.0;
+        for (int t = 0; t < n; ++t) s += v[t] * v[t];
+        return std::sqrt(s);
+    };
+    for (int j = 0; j < k; ++j) {
+        double* aj = A + (size_t)j * n;
+        const double n0 = norm(aj);
+        double prev = n0, cur = n0;
+        for (int pass = 0; pass < 3 && j > 0; ++pass) {
+            for (int i = 0; i < j; ++i) {
+                const double* qi = A + (size_t)i * n;
+                double d = 0.0;
+                for (int t = 0; t < n; ++t) d += qi[t] * aj[t];
+                c[i] = d;
+            }
+            for (int i = 0; i < j; ++i) {
+                const double* qi = A + (size_t)i * n;
+                for (int t = 0; t < n; ++t) aj[t] -= c[i] * qi[t];
+                R[(size_t)i * k + j] += c[i];
+            }
+            prev = cur;
+            cur = norm(aj);
+            if (cur >= 0.5 * prev) break;
+        }
+        if (cur <= 1e-12 * n0 || cur == 0.0) {
+            for (int t = 0; t < n; ++t) aj[t] = 0.0;
+            R[(size_t)j * k + j] = 0.0;
+        } else {
+            R[(size_t)j * k + j] = cur;
+            for (int t = 0; t < n; ++t) aj[t] /= cur;
+        }
+    }
+}
+
 }  // namespace rs
 
 extern "C" rs_status rs_symeig_host(int32_t n, const double* A, double* lam, double* W) {
@@ -140,5 +188,15 @@ extern "C" rs_status rs_symeig_host(int32_t n, const double* A, double* lam, dou
         rs::set_error("rs_symeig_host: QL iteration did not converge");
         return RS_ERR_UNSUPPORTED;
     }
+    return RS_OK;
+}
+
+extern "C" rs_status rs_qr_host(int32_t n, int32_t k, double* A, double* R) {
+    rs::clear_error();
+    if (n < 1 || k < 1 || k > 4096 || !A || !R) {
+        rs::set_error("rs_qr_host: bad argument");
+        return RS_ERR_INVALID;
+    }
+    rs::gs_qr_host(n, k, A, R);
     return RS_OK;
 }

@@ -135,6 +135,7 @@ def _load() -> C.CDLL:
         "rs_serve_get_stats": (st, [vp, C.POINTER(rs_serve_stats)]),
         "rs_serve_destroy": (None, [vp]),
         "rs_symeig_host": (st, [i32, vp, vp, vp]),
+        "rs_qr_host": (st, [i32, i32, vp, vp]),
         "rs_set_wform_kernel": (C.c_int, [C.c_int]),
         "rs_set_build_gemm_kernel": (C.c_int, [C.c_int]),
         "rs_tc_error_count": (st, [C.c_int, C.POINTER(i32)]),
@@ -532,6 +533,17 @@ def rs_symeig_host(A: np.ndarray):
     W = np.empty((n, n))
     _check(_lib.rs_symeig_host(n, A.ctypes.data, lam.ctypes.data, W.ctypes.data))
     return lam, W
+
+
+def rs_qr_host(A: np.ndarray):
+    """Thin QR (Q n x k, R k x k upper) of A by the library's host routine for
+    add-and-compress; columns dependent on the previous ones give zero columns of Q."""
+    A = np.asarray(A, dtype=np.float64)
+    n, k = A.shape
+    Qc = np.ascontiguousarray(A.T)  # column-major A: row j of Qc is column j
+    R = np.empty((k, k))
+    _check(_lib.rs_qr_host(n, k, Qc.ctypes.data, R.ctypes.data))
+    return np.ascontiguousarray(Qc.T), R
 
 
 def rs_set_wform_kernel(mode: int) -> int:
