@@ -4,7 +4,8 @@ G Q products and the W form), replayed in float32 on the CPU: a float pair scale
 multiply-by-256 steps, the low word from slice 3 on.  Checked: every slice is an
 integer that BF16 holds exactly, within the stated bounds, the slices sum to the pair
 within 2^-40 of the scale, and a 64-long sum of slice products on any diagonal stays
-below 2^24, where FP32 accumulation of integers is exact."""
+below 2^24, where FP32 accumulation of integers is exact.  The pose kernels' five-slice
+form (weights stored with the slices, two accumulators) is replayed the same way."""
 import numpy as np
 
 F = np.float32
@@ -69,3 +70,34 @@ def test_diagonal_sums_stay_exact_in_fp32():
         for k in range(64):
             acc = (acc + prod[:, k].astype(F)).astype(F)
         assert np.array_equal(acc.astype(np.float64), prod.sum(axis=1))
+
+
+def slice5(h, l):
+    """The pose kernels' five slices (weights included), the low word joining at slice 2
+    through one fused multiply-add."""
+    d0 = np.rint(h).astype(F)
+    t = ((h - d0).astype(F) * F(256)).astype(F)
+    d1 = np.rint(t).astype(F)
+    # fma: (t - d1) * 256 + l * 2^16 with one rounding
+    t = (((t - d1).astype(F).astype(np.float64) * 256.0) + (l.astype(F) * F(65536.0)).astype(np.float64)).astype(F)
+    d2 = np.rint(t).astype(F)
+    t = ((t - d2).astype(F) * F(256)).astype(F)
+    d3 = np.rint(t).astype(F)
+    t = ((t - d3).astype(F) * F(256)).astype(F)
+    d4 = np.rint(t).astype(F)
+    return [d0, d1, d2, d3, d4]
+
+
+def test_pose_kernel_five_slices():
+    rng = np.random.default_rng(2)
+    h, l = _pairs(rng, 200000)
+    d = slice5(h, l)
+    for u, b in enumerate([32, 128, 128, 128, 128]):
+        assert np.all(d[u] == np.rint(d[u]))
+        assert np.abs(d[u]).max() <= b
+        assert _bf16_exact(d[u] * F(2.0 ** (-8 * u)))  # stored with its weight
+    s = sum(d[u].astype(np.float64) * 2.0 ** (-8 * u) for u in range(5))
+    x = h.astype(np.float64) + l.astype(np.float64)
+    assert np.abs(s - x).max() <= 32.0 * 2.0 ** -37
+    # diagonals 0 and 1 over a K of 32 stay exact multiples of 2^-8 below 2^24 of them
+    assert 32 * (32 * 32 + 2 * 32 * 128) < 2 ** 24
