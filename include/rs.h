@@ -206,7 +206,7 @@ rs_status rs_protein_local_box(rs_ctx* ctx, rs_protein* parent, const double* lo
  * vectors U_l: V_l = Q_l U_l, core = C x_l U_l^T, then the cardinal basis and
  * evaluation tables as rs_build_protein makes them.  Long-range error (Frobenius, on
  * the grid) <= s_1 sqrt(sum over axes of sv_tail^2) (rs_protein_get_info: ranks,
- * sv_tail and sv_gap of this HOSVD; subspace_steps 0).  The short range is that of
+ * sv_tail and sv_gap of this HOSVD).  The short range is that of
  * the union of the parts' atoms.
  *   parts: count (1..16) Tucker-reduced handles (not local-box handles) built on
  *   this context's device with the same n, b, sigma, R_l and sinc table; the sum of
